@@ -1,0 +1,17 @@
+"""Plain FP64 CPU oracle of the auxiliary Kalman sampler.
+
+TEST INFRASTRUCTURE, not part of the library. Only ``tests/``,
+``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference``
+legs of ``bench.py`` may import it. It shares no code with the CUDA path:
+it takes its inputs (model, data, seeds) as arguments and implements its
+own Philox generator.
+
+Modules:
+  philox  Philox4x32-10 + Box-Muller streams (Salmon et al. 2011).
+  kalman  Kalman filter (Alg. A.1), RTS sampler (Alg. A.2), parallel-filter
+          elements and operator (Appendix A.2.1), (G, U) backward scan
+          (Eqs. (A.11)-(A.12), Alg. A.4), Hillis-Steele scan (Alg. A.3).
+  mcmc    one auxiliary Kalman MH step (Alg. 2, first-order, Gaussian
+          dynamics) with the direct-formula acceptance ratio.
+  dense   brute-force stacked-path Gaussian (Eq. (2.2)) for tiny T·d.
+"""
