@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Throughput of the auxiliary Kalman sampler on GB300: chain·timesteps/s.
+
+Workload (default): multivariate stochastic-volatility model, d_x = 30,
+T = 1024, 32 chains, FP32, delta = 0.0183 (oracle-calibrated, ~47%
+acceptance), seeded synthetic data. One step = one auxiliary Kalman MH
+iteration (linearise, parallel filter, backward sampling scan, reverse filter,
+MH test) on all chains. The sampler state and data are resident in HBM when
+the timed region starts; L2 is flushed (256 MiB write) before every timed step.
+
+--impl reference times the FP64 CPU oracle (the only other implementation of
+the method here) on the host cores on bounded samples of the same workload.
+Under torchrun every rank runs an independent replica (weak scaling).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "aux-Kalman chain·timesteps/s at d_x=30,T=1024"
+UNIT = "chain·timesteps/s"
+WORKLOADS = {
+    "sv_d30_T1024": dict(kind="sv", d=30, T=1024, C=32, dtype="f32"),
+    "lg_d2_T64": dict(kind="lg", d=2, T=64, C=1, dtype="f64"),
+}
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sv_d30_T1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--block-len", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-chains", type=int, default=0,
+                    help="chain-steps in the CPU baseline sample (0 = 2 per core)")
+    return ap.parse_args()
+
+
+def make_workload(name, rank=0):
+    from paper_2303_00301_gb300 import workloads
+    w = WORKLOADS[name]
+    if w["kind"] == "sv":
+        wl = workloads.stochastic_volatility(d=w["d"], T=w["T"], n_chains=w["C"], mcmc_seed=1 + rank)
+    else:
+        wl = workloads.linear_gaussian(d=w["d"], T=w["T"], n_chains=w["C"], mcmc_seed=1 + rank)
+    return wl, w
+
+
+# --------------------------------------------------------------------------- flops model
+def combine_flops(d):
+    """Algorithmic flops of one application of the element operator (Cholesky form):
+    2 Cholesky (d^3/3 each), 2 triangular x dense (d^3), 1 triangular solve with d
+    right-hand sides (d^3), 8 dense products (2 d^3 each), plus 9 matrix-vector (2 d^2)."""
+    return (59.0 / 3.0) * d ** 3 + 18.0 * d ** 2
+
+
+def apply_flops_per_step(d, epilogue):
+    """One in-block filtering step: predict (2 products, 1 mat-vec), update (Cholesky,
+    triangular solves, P^f downdate); with the backward-element epilogue also two
+    Cholesky, two triangular solves, Sigma downdate and the running G product."""
+    base = (2 + 2 + 1.0 / 3.0 + 1 + 2) * d ** 3 + 5 * d ** 2
+    if epilogue:
+        base += (1.0 / 3.0 + 1 + 2 + 1 + 1.0 / 3.0 + 2) * d ** 3 + 6 * d ** 2
+    return base
+
+
+def kernel_flops(kind, d, T, C, nb, launches):
+    """Algorithmic flops of all launches of one kernel kind in the timed region."""
+    if kind == "reduce":
+        return launches * C * (T - nb) * combine_flops(d)
+    if kind == "apply":  # half the launches carry the epilogue (forward), half not (reverse)
+        return launches / 2 * C * T * (apply_flops_per_step(d, True) + apply_flops_per_step(d, False))
+    return None
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv") \
+            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None
+
+    def start(self):
+        try:
+            self.out = open(self.path, "w") if self.path else subprocess.PIPE
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL,
+                text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        if self.path:
+            self.out.close()
+            out = open(self.path).read()
+        rows = [r.split(",") for r in (out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def _oracle_chain_step(args):
+    import numpy as np  # noqa: F401
+    from oracle import mcmc
+    name, chain, it = args
+    wl, _ = make_workload(name)
+    if wl.emission == 1:
+        em = mcmc.SVEmission(wl.y, wl.mask)
+    else:
+        em = mcmc.LinearGaussianEmission(wl.y, wl.Ry, wl.mask)
+    model = dict(m0=wl.m0, P0=wl.P0, F=wl.F, b=wl.b, Q=wl.Q, emission=em)
+    t0 = time.perf_counter()
+    mcmc.aux_step_philox(wl.x_init[chain % wl.n_chains], model, wl.delta, wl.mcmc_seed, chain, it)
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_rate(name, n_chain_steps, pool, cores, it0=0):
+    """chain·timesteps/s of the oracle on `cores` processes over n_chain_steps chain-steps."""
+    _, w = make_workload(name)
+    t0 = time.perf_counter()
+    pool.map(_oracle_chain_step, [(name, c, it0 + c) for c in range(n_chain_steps)], chunksize=1)
+    wall = time.perf_counter() - t0
+    return n_chain_steps * w["T"] / wall, wall
+
+
+def _cpu_env():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def run_reference(args):
+    """The oracle arm: same metric/config, timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    _cpu_env()
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    name = args.workload
+    _, w = make_workload(name)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        for k in range(args.warmup):
+            cpu_oracle_rate(name, cores, pool, cores, it0=k * cores)
+        rates, walls = [], []
+        for k in range(args.steps):
+            r, wall = cpu_oracle_rate(name, cores, pool, cores, it0=(args.warmup + k) * cores)
+            rates.append(r)
+            walls.append(wall)
+    value = len(rates) * cores * w["T"] / sum(walls)
+    sample = f"{cores} chain-steps per step (one MH iteration of {cores} chains, full T={w['T']})"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / len(walls),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(name, w, args.block_len, None),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(name, w, block_len, nb):
+    return {"workload": f"{name}_C{w['C']}", "model": "multivariate stochastic volatility"
+            if w["kind"] == "sv" else "linear-Gaussian", "d_x": w["d"], "T": w["T"],
+            "chains_per_gpu": w["C"], "block_len": block_len or None, "scan_blocks": nb,
+            "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas"}
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _cpu_env()
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(os.cpu_count() or 1)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2303_00301_gb300 import AuxKalman, build
+    from paper_2303_00301_gb300 import _binding as B
+    build.build()
+    name = args.workload
+    wl, w = make_workload(name, rank)
+    C, T, d = w["C"], w["T"], w["d"]
+    tdt = torch.float32 if w["dtype"] == "f32" else torch.float64
+    esz = 4 if w["dtype"] == "f32" else 8
+    s = AuxKalman(wl, dtype=w["dtype"], block_len=args.block_len)
+    L = args.block_len or max(1, math.ceil(math.sqrt(T)))   # the library's default block length
+    nb = (T + L - 1) // L
+    x = torch.tensor(wl.x_init, dtype=tdt, device="cuda")
+    acc = torch.zeros(C, dtype=torch.int32, device="cuda")
+    la = torch.zeros(C, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    it = 0
+    for _ in range(args.warmup):
+        s.step(x, 1, iter0=it, accept_count=acc, log_alpha=la)
+        it += 1
+    torch.cuda.synchronize()
+    acc.zero_()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    B.aux_set_profiling(s.handle, True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        s.step(x, 1, iter0=it, accept_count=acc, log_alpha=la)
+        ends[k].record(stream)
+        it += 1
+    torch.cuda.synchronize()
+    B.aux_set_profiling(s.handle, False)
+    prof = B.aux_read_profile(s.handle)
+    ck = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_ms = t_max.item()
+    value = world * C * T * args.steps / (total_ms / 1e3)
+    accept_rate = acc.float().mean().item() / args.steps
+
+    # end to end through the public API from pinned host buffers
+    x_host = torch.tensor(wl.x_init, dtype=tdt).pin_memory()
+    la_host = torch.zeros(C, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        x.copy_(x_host, non_blocking=True)
+        s.step(x, 1, iter0=it, log_alpha=la)
+        x_host.copy_(x, non_blocking=True)
+        la_host.copy_(la, non_blocking=True)
+        it += 1
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        x.copy_(x_host, non_blocking=True)
+        s.step(x, 1, iter0=it, log_alpha=la)
+        x_host.copy_(x, non_blocking=True)
+        la_host.copy_(la, non_blocking=True)
+        torch.cuda.synchronize()
+        it += 1
+    e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+    e2e_value = world * C * T * args.steps / e2e_s.item()
+    rc, per_chain = s.status()
+
+    # roofline of the dominant kernel (time-weighted), FP32 FMA pipe bound
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_launches = prof[dom]
+    flops = kernel_flops(dom, d, T, C, nb, dom_launches)
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    if w["dtype"] == "f32":
+        peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    else:
+        peak_tflops = 1.25   # nominal GB300 FP64 rate
+    roofline = None
+    if flops is not None and dom_ms > 0:
+        achieved = flops / (dom_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": f"k_filter_{dom}", "achieved": achieved,
+                    "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                    "traffic": None, "launches": dom_launches,
+                    "avg_launch_ms": dom_ms / dom_launches,
+                    "peak_basis": f"{N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz"}
+    cpu = None
+    if pool is not None:
+        n = args.cpu_sample_chains or 2 * (os.cpu_count() or 1)
+        rate, wall = cpu_oracle_rate(name, n, pool, os.cpu_count() or 1)
+        pool.close()
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"{n} chain-steps (one MH iteration each, full T={T}, d={d}) in {wall:.1f} s"}
+    if rank == 0:
+        bi = C * T * d * esz
+        bo = C * T * d * esz + C * 8
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": w["dtype"], "data": "synthetic",
+                "config": config_of(name, w, args.block_len, nb),
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
+                        "d2h_bytes_per_step": bo},
+                "gpu_launches": int(sum(v[1] for v in prof.values())),
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": ck,
+                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+                "accept_rate": accept_rate, "status": int(rc),
+                "step_ms_median": statistics.median(step_ms)}
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

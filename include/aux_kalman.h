@@ -1,0 +1,165 @@
+/*
+ * aux_kalman.h — C ABI of the GB300 auxiliary Kalman sampler.
+ *
+ * The library implements the first-order auxiliary Kalman sampler for
+ * state-space models with Gaussian dynamics (Corenflos & Sarkka,
+ * arXiv:2303.00301, Section 2.2, Eqs. (2.5)-(2.7) and Algorithm 2):
+ *
+ *   target   pi(x) ∝ N(x_0; m0, P0) prod_{t>=1} N(x_t; F x_{t-1} + b, Q)
+ *                     prod_t h(y_t | x_t),         t = 0 .. T-1
+ *   one step u_t = x_t + sqrt(delta/2) eps_t,  v_t = grad_{x_t} log h(y_t | x_t),
+ *            ytilde_t = u_t + (delta/2) v_t,
+ *            x* ~ smoothing law of the LGSSM (F, b, Q; H = I, R = (delta/2) I)
+ *                 given ytilde, sampled by a parallel-in-time Kalman filter
+ *                 (Appendix A.2.1) and a parallel backward-sampling scan
+ *                 (Proposition A.1, Algorithm A.4),
+ *            accept x* with the Metropolis-Hastings ratio of Algorithm 2.
+ *
+ * Emission models: linear-Gaussian log h = log N(y; x, R_y) (Appendix A,
+ * Eq. (A.1)) and multivariate stochastic volatility
+ * log h = sum_i log N(y_i; 0, exp(x_i)) (Section 5.1). Sigma_t = I.
+ *
+ * Conventions for every entry point:
+ *  - T is the number of states (array length); arrays are row-major and
+ *    chain-major: paths [C][T][d], matrices [..][d][d].
+ *  - "device" pointers are caller-owned CUDA device memory; "host" pointers
+ *    are read during the call only. The model handle owns its workspace.
+ *  - Compute type: AUX_F32 -> float, AUX_F64 -> double. Device path buffers
+ *    (x, ytilde, mf, Pf, eps, xstar) are in the compute type; log-likelihoods
+ *    and log acceptance ratios are always double.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls only enqueue work; results are valid after the stream completes.
+ *  - Return value: AUX_OK or an AUX_E_* code. Argument errors are detected on
+ *    the host before anything is enqueued. Numerical failures on the device
+ *    (a non-positive Cholesky pivot, a non-finite ratio) never trap: they are
+ *    latched into per-chain status words read by aux_get_status, and the
+ *    affected chain's proposal is rejected.
+ *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the seed
+ *    given to aux_init_model, counter (word, t | purpose << 24,
+ *    iteration & 0xffffffff, chain); each 32-bit word r gives
+ *    u = ((r >> 9) + 0.5) 2^-23 and Box-Muller pairs give normals. A step's
+ *    draws depend only on (seed, chain, iteration), so runs are resumable.
+ */
+#ifndef AUX_KALMAN_H
+#define AUX_KALMAN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AUX_ABI_VERSION 1
+
+/* status codes */
+#define AUX_OK             0
+#define AUX_E_INVALID_ARG  1  /* bad pointer, size, enum or version */
+#define AUX_E_NOT_PD       2  /* P0, Q or R_y not positive definite; or a device Cholesky pivot <= 0 */
+#define AUX_E_NONFINITE    3  /* NaN/Inf in an input or in a device log-ratio */
+#define AUX_E_CUDA         4  /* a CUDA runtime call failed */
+#define AUX_E_TIMEOUT      5  /* reserved: a bounded device wait gave up */
+#define AUX_E_OOM          6  /* workspace allocation failed */
+#define AUX_E_UNSUPPORTED  7  /* valid but not built (e.g. d_x > 32) */
+
+/* compute types */
+#define AUX_F32 0
+#define AUX_F64 1
+
+/* emission models */
+#define AUX_EMIS_LINEAR_GAUSSIAN 0
+#define AUX_EMIS_SV              1
+
+/* Model description (Section 2.2, Eq. (2.5); SV model of Section 5.1).
+ * All arrays are HOST pointers to double, copied by aux_init_model. */
+typedef struct {
+  int32_t abi_version;   /* AUX_ABI_VERSION */
+  int32_t dtype;         /* AUX_F32 | AUX_F64 */
+  int32_t d_x;           /* state dimension: 1..32 (AUX_F32), 1..16 (AUX_F64) */
+  int32_t T;             /* number of states, T >= 1 */
+  int32_t n_chains;      /* C >= 1 */
+  int32_t emis_kind;     /* AUX_EMIS_* */
+  int32_t y_per_chain;   /* 0: y is [T][d] shared by all chains; 1: y is [C][T][d] */
+  int32_t block_len;     /* time steps per scan block; 0 = library default */
+  const double *m0;      /* [d]    mean of p_0 */
+  const double *P0;      /* [d*d]  covariance of p_0 (symmetric positive definite) */
+  const double *F;       /* [d*d]  transition matrix */
+  const double *b;       /* [d]    transition offset */
+  const double *Q;       /* [d*d]  transition covariance (SPD) */
+  const double *y;       /* observations, see y_per_chain */
+  const uint8_t *obs_mask; /* [T] or NULL: log h_t == 0 where obs_mask[t] == 0 */
+  const double *R_y;     /* [d*d] emission covariance (linear-Gaussian), else NULL */
+  double delta;          /* step size delta > 0; auxiliary covariance (delta/2) I */
+} aux_model_desc;
+
+typedef struct aux_model aux_model;   /* opaque handle */
+
+/* Create a model handle: validates the description (P0, Q, R_y must be SPD,
+ * all values finite), copies the model to the device of the current CUDA
+ * context, and allocates the workspace for n_chains chains of length T.
+ * seed keys the Philox streams. On success *out owns device memory until
+ * aux_free_model. Errors: INVALID_ARG, NOT_PD, NONFINITE, UNSUPPORTED, OOM, CUDA. */
+int aux_init_model(const aux_model_desc *desc, uint64_t seed, void *stream, aux_model **out);
+
+/* n_iters auxiliary Kalman MH steps (Algorithm 2 with Gaussian dynamics)
+ * on all chains, iterations iter0 .. iter0 + n_iters - 1.
+ *   x            device [C][T][d], compute type: chain states, updated in place.
+ *   accept_count device [C] uint32 or NULL: incremented by each acceptance.
+ *   log_alpha    device [C] double or NULL: log MH ratio of the last step.
+ * The MH test accepts iff log U < log alpha, U the (chain, iteration) uniform.
+ * Errors: INVALID_ARG, CUDA. Device failures: see aux_get_status. */
+int aux_kalman_step(aux_model *m, void *x, int32_t n_iters, uint64_t iter0,
+                    uint32_t *accept_count, double *log_alpha, void *stream);
+
+/* Log marginal likelihood of the auxiliary LGSSM for given pseudo-observations
+ * (the Kalman-filter likelihood of Algorithm A.1 with predictive terms
+ * N(ytilde_t; m^p_t, P^p_t + R), computed by the parallel filter of Appendix A.2.1).
+ *   ytilde device [C][T][d] compute type.
+ *   logZ   device [C] double (required).
+ *   mf     device [C][T][d] or NULL: filtering means m^f_t.
+ *   Pf     device [C][T][d][d] or NULL: filtering covariances P^f_t. */
+int aux_loglik(aux_model *m, const void *ytilde, double *logZ, void *mf, void *Pf, void *stream);
+
+/* One draw from the smoothing law of the auxiliary LGSSM given ytilde
+ * (parallel filter + backward (G, U) scan, Proposition A.1).
+ *   ytilde device [C][T][d]; eps device [C][T][d] standard normals used as the
+ *   backward noise of U_t (or NULL: the Philox backward stream of
+ *   (chain, iteration)); xstar device [C][T][d] output; logZ device [C] or NULL. */
+int aux_sample_path(aux_model *m, const void *ytilde, const void *eps, uint64_t iteration,
+                    void *xstar, double *logZ, void *stream);
+
+/* Copy the latched per-chain device status words to host memory
+ * (synchronises the handle's last stream) and clear them.
+ *   per_chain_status host [C] int32 or NULL. Returns AUX_OK if every chain is
+ *   clean, else the first non-zero code. */
+int aux_get_status(aux_model *m, int32_t *per_chain_status);
+
+/* Kernel kinds reported by aux_read_profile. */
+#define AUX_PROFILE_LINEARISE 0  /* v, u, ytilde at the current state (Eq. (2.7)) */
+#define AUX_PROFILE_TEMPLATE  1  /* model-derived matrix parts of the filtering elements */
+#define AUX_PROFILE_REDUCE    2  /* block aggregates of the filtering elements (Appendix A.2.1) */
+#define AUX_PROFILE_SCAN      3  /* one Hillis-Steele round over block aggregates (Algorithm A.3) */
+#define AUX_PROFILE_APPLY     4  /* in-block filtering from the block prefix + (G_t, U_t) (Eq. (A.11)) */
+#define AUX_PROFILE_BACKWARD  5  /* backward (G, U) scan, x*, and MH partial sums (Proposition A.1) */
+#define AUX_PROFILE_MH        6  /* log alpha, MH test and state update (Algorithm 2) */
+#define AUX_PROFILE_SUM       7  /* log Z reduction */
+#define AUX_PROFILE_KINDS     8
+
+/* Turn per-launch timing on or off for this handle: while on, every kernel
+ * launch is bracketed by two CUDA events recorded on its own stream. */
+int aux_set_profiling(aux_model *m, int32_t enable);
+
+/* Accumulated device time (ms, from the event pairs) and launch count per
+ * kernel kind since the last read; waits for the recorded events and resets
+ * the window. ms_per_kind, launches_per_kind: host arrays of n_kinds entries. */
+int aux_read_profile(aux_model *m, double *ms_per_kind, int32_t *launches_per_kind, int32_t n_kinds);
+
+/* Release the handle and its device memory (synchronises). NULL is a no-op. */
+void aux_free_model(aux_model *m);
+
+/* Static string for a status code. */
+const char *aux_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AUX_KALMAN_H */

@@ -1,0 +1,56 @@
+"""GB300 auxiliary Kalman sampler (arXiv:2303.00301, Section 2.2 / Algorithm 2).
+
+The compute path is the CUDA library built from ``csrc/`` (see ``build.py``)
+behind the C ABI of ``include/aux_kalman.h``. ``_binding`` exposes those
+entry points under their C names; ``AuxKalman`` is a small convenience
+wrapper that owns the handle and takes torch CUDA tensors.
+"""
+from .workloads import EMIS_LINEAR_GAUSSIAN, EMIS_SV  # noqa: F401
+
+
+def _load_binding():
+    from . import _binding as b
+    return b
+
+
+class AuxKalman:
+    """Owns an ``aux_model`` handle for one workload (torch is used for memory only)."""
+
+    def __init__(self, workload, dtype="f32", seed=None, n_chains=None, block_len=0, stream=None):
+        import torch
+        b = _load_binding()
+        self.b = b
+        self.wl = workload
+        self.C = int(n_chains if n_chains is not None else workload.n_chains)
+        self.T, self.d = workload.T, workload.d
+        self.dtype_code = b.AUX_F32 if dtype == "f32" else b.AUX_F64
+        self.torch_dtype = torch.float32 if dtype == "f32" else torch.float64
+        self.seed = workload.mcmc_seed if seed is None else seed
+        self.handle = b.aux_init_model(
+            d_x=self.d, T=self.T, n_chains=self.C, m0=workload.m0, P0=workload.P0,
+            F=workload.F, b=workload.b, Q=workload.Q, y=workload.y, delta=workload.delta,
+            emis_kind=workload.emission, dtype=self.dtype_code, R_y=workload.Ry,
+            obs_mask=workload.mask, block_len=block_len, seed=self.seed, stream=stream)
+
+    def step(self, x, n_iters=1, iter0=0, accept_count=None, log_alpha=None, stream=None):
+        self.b.aux_kalman_step(self.handle, x, n_iters, iter0, accept_count, log_alpha, stream)
+
+    def loglik(self, ytilde, logZ, mf=None, Pf=None, stream=None):
+        self.b.aux_loglik(self.handle, ytilde, logZ, mf, Pf, stream)
+
+    def sample_path(self, ytilde, xstar, eps=None, iteration=0, logZ=None, stream=None):
+        self.b.aux_sample_path(self.handle, ytilde, xstar, eps, iteration, logZ, stream)
+
+    def status(self):
+        return self.b.aux_get_status(self.handle, self.C)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            self.b.aux_free_model(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,189 @@
+"""ctypes binding of the C ABI in include/aux_kalman.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls. Device
+buffers are passed as torch CUDA tensors (their data pointers) or raw
+integer addresses; streams as torch.cuda.Stream, an integer handle or None
+(the current torch stream). There is no fallback: if the compiled library
+is missing, importing the binding raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+AUX_ABI_VERSION = 1
+AUX_OK, AUX_E_INVALID_ARG, AUX_E_NOT_PD, AUX_E_NONFINITE = 0, 1, 2, 3
+AUX_E_CUDA, AUX_E_TIMEOUT, AUX_E_OOM, AUX_E_UNSUPPORTED = 4, 5, 6, 7
+AUX_F32, AUX_F64 = 0, 1
+AUX_EMIS_LINEAR_GAUSSIAN, AUX_EMIS_SV = 0, 1
+
+_dbl_p = ctypes.POINTER(ctypes.c_double)
+_u8_p = ctypes.POINTER(ctypes.c_uint8)
+
+
+class aux_model_desc(ctypes.Structure):
+    _fields_ = [
+        ("abi_version", ctypes.c_int32),
+        ("dtype", ctypes.c_int32),
+        ("d_x", ctypes.c_int32),
+        ("T", ctypes.c_int32),
+        ("n_chains", ctypes.c_int32),
+        ("emis_kind", ctypes.c_int32),
+        ("y_per_chain", ctypes.c_int32),
+        ("block_len", ctypes.c_int32),
+        ("m0", _dbl_p),
+        ("P0", _dbl_p),
+        ("F", _dbl_p),
+        ("b", _dbl_p),
+        ("Q", _dbl_p),
+        ("y", _dbl_p),
+        ("obs_mask", _u8_p),
+        ("R_y", _dbl_p),
+        ("delta", ctypes.c_double),
+    ]
+
+
+class AuxError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {aux_status_string(code)} (code {code})")
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(
+            f"the CUDA library {path} is not built; run "
+            "`python -m paper_2303_00301_gb300.build` (nvcc, sm_103a) first")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    lib.aux_init_model.argtypes = [ctypes.POINTER(aux_model_desc), ctypes.c_uint64, vp,
+                                   ctypes.POINTER(vp)]
+    lib.aux_init_model.restype = ctypes.c_int
+    lib.aux_kalman_step.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_uint64, vp, vp, vp]
+    lib.aux_kalman_step.restype = ctypes.c_int
+    lib.aux_loglik.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.aux_loglik.restype = ctypes.c_int
+    lib.aux_sample_path.argtypes = [vp, vp, vp, ctypes.c_uint64, vp, vp, vp]
+    lib.aux_sample_path.restype = ctypes.c_int
+    lib.aux_get_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+    lib.aux_get_status.restype = ctypes.c_int
+    lib.aux_free_model.argtypes = [vp]
+    lib.aux_free_model.restype = None
+    lib.aux_set_profiling.argtypes = [vp, ctypes.c_int32]
+    lib.aux_set_profiling.restype = ctypes.c_int
+    lib.aux_read_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
+    lib.aux_read_profile.restype = ctypes.c_int
+    lib.aux_status_string.argtypes = [ctypes.c_int]
+    lib.aux_status_string.restype = ctypes.c_char_p
+    return lib
+
+
+LIB = _load()
+
+
+def _ptr(t):
+    """Device address of a torch tensor, an int address, or None -> NULL."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(rc, where):
+    if rc != AUX_OK:
+        raise AuxError(rc, where)
+
+
+def aux_status_string(code):
+    return LIB.aux_status_string(int(code)).decode()
+
+
+def _as_c(a, dtype=np.float64):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def aux_init_model(*, d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind, dtype=AUX_F32,
+                   R_y=None, obs_mask=None, y_per_chain=False, block_len=0, seed=0, stream=None):
+    """Create a model handle (host arrays are copied during the call)."""
+    keep = dict(m0=_as_c(m0), P0=_as_c(P0), F=_as_c(F), b=_as_c(b), Q=_as_c(Q), y=_as_c(y))
+    desc = aux_model_desc()
+    desc.abi_version = AUX_ABI_VERSION
+    desc.dtype = int(dtype)
+    desc.d_x, desc.T, desc.n_chains = int(d_x), int(T), int(n_chains)
+    desc.emis_kind = int(emis_kind)
+    desc.y_per_chain = 1 if y_per_chain else 0
+    desc.block_len = int(block_len)
+    for k, v in keep.items():
+        setattr(desc, k, v.ctypes.data_as(_dbl_p))
+    if R_y is not None:
+        keep["R_y"] = _as_c(R_y)
+        desc.R_y = keep["R_y"].ctypes.data_as(_dbl_p)
+    if obs_mask is not None:
+        keep["mask"] = _as_c(obs_mask, np.uint8)
+        desc.obs_mask = keep["mask"].ctypes.data_as(_u8_p)
+    desc.delta = float(delta)
+    handle = ctypes.c_void_p()
+    rc = LIB.aux_init_model(ctypes.byref(desc), ctypes.c_uint64(int(seed)), _stream(stream),
+                            ctypes.byref(handle))
+    _check(rc, "aux_init_model")
+    return handle
+
+
+def aux_kalman_step(handle, x, n_iters, iter0=0, accept_count=None, log_alpha=None, stream=None):
+    rc = LIB.aux_kalman_step(handle, _ptr(x), int(n_iters), ctypes.c_uint64(int(iter0)),
+                             _ptr(accept_count), _ptr(log_alpha), _stream(stream))
+    _check(rc, "aux_kalman_step")
+
+
+def aux_loglik(handle, ytilde, logZ, mf=None, Pf=None, stream=None):
+    rc = LIB.aux_loglik(handle, _ptr(ytilde), _ptr(logZ), _ptr(mf), _ptr(Pf), _stream(stream))
+    _check(rc, "aux_loglik")
+
+
+def aux_sample_path(handle, ytilde, xstar, eps=None, iteration=0, logZ=None, stream=None):
+    rc = LIB.aux_sample_path(handle, _ptr(ytilde), _ptr(eps), ctypes.c_uint64(int(iteration)),
+                             _ptr(xstar), _ptr(logZ), _stream(stream))
+    _check(rc, "aux_sample_path")
+
+
+def aux_get_status(handle, n_chains=None):
+    """Returns (first_code, per-chain codes as a numpy array or None)."""
+    if n_chains is None:
+        return LIB.aux_get_status(handle, None), None
+    buf = (ctypes.c_int32 * int(n_chains))()
+    rc = LIB.aux_get_status(handle, buf)
+    return rc, np.frombuffer(buf, dtype=np.int32).copy()
+
+
+PROFILE_KINDS = ["linearise", "template", "reduce", "scan", "apply", "backward", "mh", "sum"]
+
+
+def aux_set_profiling(handle, enable):
+    _check(LIB.aux_set_profiling(handle, 1 if enable else 0), "aux_set_profiling")
+
+
+def aux_read_profile(handle):
+    """{kind: (total_ms, launches)} since the last read."""
+    n = len(PROFILE_KINDS)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int32 * n)()
+    _check(LIB.aux_read_profile(handle, ms, cnt, n), "aux_read_profile")
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(PROFILE_KINDS)}
+
+
+def aux_free_model(handle):
+    LIB.aux_free_model(handle)

@@ -1,0 +1,314 @@
+// aux_capi.cu — the C ABI declared in include/aux_kalman.h: argument checks,
+// model upload, workspace ownership and dispatch to the per-precision kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "aux_internal.h"
+
+namespace {
+
+int pick_dp(int d) {
+  if (d <= 4) return 4;
+  if (d <= 8) return 8;
+  if (d <= 16) return 16;
+  if (d <= 32) return 32;
+  return 0;
+}
+
+bool all_finite(const double* a, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+// lower Cholesky of a symmetric d x d matrix (row-major), false if not SPD
+bool host_cholesky(const double* A, int d, std::vector<double>& L) {
+  L.assign((size_t)d * d, 0.0);
+  for (int j = 0; j < d; ++j) {
+    double s = A[j * d + j];
+    for (int k = 0; k < j; ++k) s -= L[j * d + k] * L[j * d + k];
+    if (!(s > 0.0)) return false;
+    const double ljj = std::sqrt(s);
+    L[j * d + j] = ljj;
+    for (int i = j + 1; i < d; ++i) {
+      double t = A[i * d + j];
+      for (int k = 0; k < j; ++k) t -= L[i * d + k] * L[j * d + k];
+      L[i * d + j] = t / ljj;
+    }
+  }
+  return true;
+}
+
+bool is_symmetric(const double* A, int d) {
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double a = A[i * d + j], b = A[j * d + i];
+      if (std::fabs(a - b) > 1e-12 * (std::fabs(a) + std::fabs(b) + 1e-300)) return false;
+    }
+  return true;
+}
+
+// inverse of an SPD matrix from its Cholesky factor
+std::vector<double> spd_inverse(const std::vector<double>& L, int d) {
+  std::vector<double> inv((size_t)d * d, 0.0), col(d);
+  for (int c = 0; c < d; ++c) {
+    for (int i = 0; i < d; ++i) col[i] = (i == c) ? 1.0 : 0.0;
+    for (int i = 0; i < d; ++i) {  // L y = e_c
+      double s = col[i];
+      for (int k = 0; k < i; ++k) s -= L[i * d + k] * col[k];
+      col[i] = s / L[i * d + i];
+    }
+    for (int i = d - 1; i >= 0; --i) {  // L^T x = y
+      double s = col[i];
+      for (int k = i + 1; k < d; ++k) s -= L[k * d + i] * col[k];
+      col[i] = s / L[i * d + i];
+    }
+    for (int i = 0; i < d; ++i) inv[i * d + c] = col[i];
+  }
+  return inv;
+}
+
+template <typename Real>
+std::vector<unsigned char> pad_matrix(const double* A, int d, int DP) {
+  std::vector<unsigned char> out((size_t)DP * DP * sizeof(Real), 0);
+  Real* o = reinterpret_cast<Real*>(out.data());
+  if (A)
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) o[i * DP + j] = (Real)A[i * d + j];
+  return out;
+}
+
+template <typename Real>
+std::vector<unsigned char> pad_vector(const double* a, int d, int DP) {
+  std::vector<unsigned char> out((size_t)DP * sizeof(Real), 0);
+  Real* o = reinterpret_cast<Real*>(out.data());
+  if (a)
+    for (int i = 0; i < d; ++i) o[i] = (Real)a[i];
+  return out;
+}
+
+template <typename Real>
+std::vector<unsigned char> convert(const double* a, size_t n) {
+  std::vector<unsigned char> out(n * sizeof(Real));
+  Real* o = reinterpret_cast<Real*>(out.data());
+  for (size_t i = 0; i < n; ++i) o[i] = (Real)a[i];
+  return out;
+}
+
+int dev_alloc(aux_model* m, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return AUX_E_OOM;
+  }
+  m->allocs.push_back(*p);
+  return AUX_OK;
+}
+
+int upload(aux_model* m, void** p, const std::vector<unsigned char>& h) {
+  int rc = dev_alloc(m, p, h.size());
+  if (rc) return rc;
+  return cudaMemcpy(*p, h.data(), h.size(), cudaMemcpyHostToDevice) == cudaSuccess ? AUX_OK
+                                                                                  : AUX_E_CUDA;
+}
+
+void release(aux_model* m) {
+  if (!m) return;
+  cudaDeviceSynchronize();
+  for (auto& r : m->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto& r : m->pool) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (void* p : m->allocs) cudaFree(p);
+  m->allocs.clear();
+  delete m;
+}
+
+template <typename Real>
+int upload_model(aux_model* m, const aux_model_desc* d, const std::vector<double>& Ryinv) {
+  const int dd = m->d, DP = m->DP;
+  int rc;
+  if ((rc = upload(m, &m->F, pad_matrix<Real>(d->F, dd, DP)))) return rc;
+  if ((rc = upload(m, &m->Q, pad_matrix<Real>(d->Q, dd, DP)))) return rc;
+  if ((rc = upload(m, &m->P0, pad_matrix<Real>(d->P0, dd, DP)))) return rc;
+  if ((rc = upload(m, &m->m0, pad_vector<Real>(d->m0, dd, DP)))) return rc;
+  if ((rc = upload(m, &m->b, pad_vector<Real>(d->b, dd, DP)))) return rc;
+  if ((rc = upload(m, &m->Ryinv, pad_matrix<Real>(Ryinv.empty() ? nullptr : Ryinv.data(), dd, DP)))) return rc;
+  const size_t ny = (size_t)(m->y_per_chain ? m->C : 1) * m->T * dd;
+  if ((rc = upload(m, &m->y, convert<Real>(d->y, ny)))) return rc;
+  return AUX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* aux_status_string(int code) {
+  switch (code) {
+    case AUX_OK: return "ok";
+    case AUX_E_INVALID_ARG: return "invalid argument";
+    case AUX_E_NOT_PD: return "matrix not positive definite";
+    case AUX_E_NONFINITE: return "non-finite value";
+    case AUX_E_CUDA: return "CUDA runtime error";
+    case AUX_E_TIMEOUT: return "device wait timed out";
+    case AUX_E_OOM: return "out of device memory";
+    case AUX_E_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_model** out) {
+  if (!desc || !out) return AUX_E_INVALID_ARG;
+  *out = nullptr;
+  if (desc->abi_version != AUX_ABI_VERSION) return AUX_E_INVALID_ARG;
+  if (desc->dtype != AUX_F32 && desc->dtype != AUX_F64) return AUX_E_INVALID_ARG;
+  if (desc->emis_kind != AUX_EMIS_LINEAR_GAUSSIAN && desc->emis_kind != AUX_EMIS_SV)
+    return AUX_E_INVALID_ARG;
+  const int d = desc->d_x, T = desc->T, C = desc->n_chains;
+  if (d < 1 || T < 1 || C < 1 || desc->block_len < 0) return AUX_E_INVALID_ARG;
+  if (!desc->m0 || !desc->P0 || !desc->F || !desc->b || !desc->Q || !desc->y)
+    return AUX_E_INVALID_ARG;
+  if (desc->emis_kind == AUX_EMIS_LINEAR_GAUSSIAN && !desc->R_y) return AUX_E_INVALID_ARG;
+  if (!(desc->delta > 0.0) || !std::isfinite(desc->delta)) return AUX_E_INVALID_ARG;
+  const int DP = pick_dp(d);
+  if (DP == 0) return AUX_E_UNSUPPORTED;
+  if (desc->dtype == AUX_F64 && DP > 16) return AUX_E_UNSUPPORTED;
+  if ((long long)C * T * d > (1LL << 31)) return AUX_E_UNSUPPORTED;
+  const size_t dd = (size_t)d * d;
+  const size_t ny = (size_t)(desc->y_per_chain ? C : 1) * T * d;
+  if (!all_finite(desc->m0, d) || !all_finite(desc->P0, dd) || !all_finite(desc->F, dd) ||
+      !all_finite(desc->b, d) || !all_finite(desc->Q, dd) || !all_finite(desc->y, ny))
+    return AUX_E_NONFINITE;
+  if (desc->R_y && desc->emis_kind == AUX_EMIS_LINEAR_GAUSSIAN && !all_finite(desc->R_y, dd))
+    return AUX_E_NONFINITE;
+  std::vector<double> L;
+  if (!is_symmetric(desc->P0, d) || !host_cholesky(desc->P0, d, L)) return AUX_E_NOT_PD;
+  if (!is_symmetric(desc->Q, d) || !host_cholesky(desc->Q, d, L)) return AUX_E_NOT_PD;
+  std::vector<double> Ryinv;
+  double ry_logdet = 0.0;
+  if (desc->emis_kind == AUX_EMIS_LINEAR_GAUSSIAN) {
+    if (!is_symmetric(desc->R_y, d) || !host_cholesky(desc->R_y, d, L)) return AUX_E_NOT_PD;
+    Ryinv = spd_inverse(L, d);
+    for (int i = 0; i < d; ++i) ry_logdet += 2.0 * std::log(L[i * d + i]);
+  }
+  (void)ry_logdet;
+
+  aux_model* m = new (std::nothrow) aux_model();
+  if (!m) return AUX_E_OOM;
+  m->dtype = desc->dtype; m->d = d; m->DP = DP; m->T = T; m->C = C;
+  m->emis = desc->emis_kind; m->y_per_chain = desc->y_per_chain ? 1 : 0;
+  int L_blk = desc->block_len;
+  if (L_blk == 0) L_blk = std::max(1, (int)std::ceil(std::sqrt((double)T)));
+  if (L_blk > T) L_blk = T;
+  m->L = L_blk;
+  m->nb = (T + L_blk - 1) / L_blk;
+  m->delta = desc->delta;
+  m->seed = seed;
+  m->stream = (cudaStream_t)stream;
+  m->esz = desc->dtype == AUX_F32 ? sizeof(float) : sizeof(double);
+  cudaGetDevice(&m->device);
+  m->ops = desc->dtype == AUX_F32 ? aux_ops_f32(DP) : aux_ops_f64(DP);
+  if (!m->ops) { release(m); return AUX_E_UNSUPPORTED; }
+
+  int rc = desc->dtype == AUX_F32 ? upload_model<float>(m, desc, Ryinv)
+                                  : upload_model<double>(m, desc, Ryinv);
+  if (!rc && desc->obs_mask) {
+    std::vector<unsigned char> mk(desc->obs_mask, desc->obs_mask + T);
+    rc = upload(m, (void**)&m->mask, mk);
+  }
+  const size_t es = m->esz;
+  const size_t path = (size_t)C * T * d * es;
+  const size_t nbC = (size_t)C * m->nb;
+  if (!rc) rc = dev_alloc(m, &m->u, path);
+  if (!rc) rc = dev_alloc(m, &m->v, path);
+  if (!rc) rc = dev_alloc(m, &m->yt, path);
+  if (!rc) rc = dev_alloc(m, &m->xs, path);
+  if (!rc) rc = dev_alloc(m, &m->yts, path);
+  if (!rc) rc = dev_alloc(m, &m->agg0, nbC * aux_es(DP) * es);
+  if (!rc) rc = dev_alloc(m, &m->agg1, nbC * aux_es(DP) * es);
+  if (!rc) rc = dev_alloc(m, &m->G, (size_t)C * T * DP * DP * es);
+  if (!rc) rc = dev_alloc(m, &m->U, (size_t)C * T * DP * es);
+  if (!rc) rc = dev_alloc(m, &m->gu, nbC * aux_gs(DP) * es);
+  if (!rc) rc = dev_alloc(m, &m->tmpl, (size_t)7 * DP * DP * es);
+  if (!rc) rc = dev_alloc(m, (void**)&m->fq, (size_t)C * T * sizeof(double));
+  if (!rc) rc = dev_alloc(m, (void**)&m->fld, (size_t)C * T * sizeof(double));
+  if (!rc) rc = dev_alloc(m, (void**)&m->mh_part, nbC * sizeof(double));
+  if (!rc) rc = dev_alloc(m, (void**)&m->lz_part, nbC * sizeof(double));
+  if (!rc) rc = dev_alloc(m, (void**)&m->status_iter, (size_t)C * sizeof(int32_t));
+  if (!rc) rc = dev_alloc(m, (void**)&m->status, (size_t)C * sizeof(int32_t));
+  if (!rc && (cudaMemset(m->status, 0, (size_t)C * sizeof(int32_t)) != cudaSuccess ||
+              cudaMemset(m->status_iter, 0, (size_t)C * sizeof(int32_t)) != cudaSuccess))
+    rc = AUX_E_CUDA;
+  if (!rc) rc = m->ops->prepare();
+  if (rc) { release(m); return rc; }
+  *out = m;
+  return AUX_OK;
+}
+
+int aux_kalman_step(aux_model* m, void* x, int32_t n_iters, uint64_t iter0,
+                    uint32_t* accept_count, double* log_alpha, void* stream) {
+  if (!m || !x || n_iters < 0) return AUX_E_INVALID_ARG;
+  m->stream = (cudaStream_t)stream;
+  if (n_iters == 0) return AUX_OK;
+  return m->ops->kalman_step(m, x, n_iters, iter0, accept_count, log_alpha, m->stream);
+}
+
+int aux_loglik(aux_model* m, const void* ytilde, double* logZ, void* mf, void* Pf, void* stream) {
+  if (!m || !ytilde || !logZ) return AUX_E_INVALID_ARG;
+  m->stream = (cudaStream_t)stream;
+  return m->ops->loglik(m, ytilde, logZ, mf, Pf, m->stream);
+}
+
+int aux_sample_path(aux_model* m, const void* ytilde, const void* eps, uint64_t iteration,
+                    void* xstar, double* logZ, void* stream) {
+  if (!m || !ytilde || !xstar) return AUX_E_INVALID_ARG;
+  m->stream = (cudaStream_t)stream;
+  return m->ops->sample_path(m, ytilde, eps, iteration, xstar, logZ, m->stream);
+}
+
+int aux_get_status(aux_model* m, int32_t* per_chain_status) {
+  if (!m) return AUX_E_INVALID_ARG;
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) return AUX_E_CUDA;
+  std::vector<int32_t> st(m->C);
+  if (cudaMemcpy(st.data(), m->status, m->C * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return AUX_E_CUDA;
+  if (cudaMemset(m->status, 0, m->C * sizeof(int32_t)) != cudaSuccess) return AUX_E_CUDA;
+  int first = AUX_OK;
+  for (int c = 0; c < m->C; ++c) {
+    int code = AUX_OK;
+    if (st[c] & 1) code = AUX_E_NOT_PD;
+    else if (st[c] & 2) code = AUX_E_NONFINITE;
+    if (per_chain_status) per_chain_status[c] = code;
+    if (first == AUX_OK) first = code;
+  }
+  return first;
+}
+
+int aux_set_profiling(aux_model* m, int32_t enable) {
+  if (!m) return AUX_E_INVALID_ARG;
+  m->profiling = enable != 0;
+  return AUX_OK;
+}
+
+int aux_read_profile(aux_model* m, double* ms_per_kind, int32_t* launches_per_kind, int32_t n_kinds) {
+  if (!m || n_kinds < 0 || (n_kinds > 0 && (!ms_per_kind || !launches_per_kind)))
+    return AUX_E_INVALID_ARG;
+  for (int k = 0; k < n_kinds; ++k) { ms_per_kind[k] = 0.0; launches_per_kind[k] = 0; }
+  int rc = AUX_OK;
+  for (auto& r : m->recs) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+      rc = AUX_E_CUDA;
+    if (r.kind < n_kinds) { ms_per_kind[r.kind] += ms; launches_per_kind[r.kind] += 1; }
+    m->pool.push_back(r);
+  }
+  m->recs.clear();
+  return rc;
+}
+
+void aux_free_model(aux_model* m) { release(m); }
+
+}  // extern "C"

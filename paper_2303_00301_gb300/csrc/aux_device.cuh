@@ -1,0 +1,277 @@
+// aux_device.cuh — device building blocks of the auxiliary Kalman sampler.
+//
+// * Philox4x32-10 (Salmon et al., SC'11) and Box-Muller normals, with the
+//   counter layout documented in include/aux_kalman.h.
+// * Warp-level dense linear algebra on DP x DP matrices (DP <= 32, padded
+//   dimension). Lane i owns row i: a matrix operand is either a register
+//   row (T r[DP]) or a shared-memory "slot" (row stride LD = DP + 16 bytes
+//   worth of elements, so that a lane loading its own row with 16-byte
+//   vectors is bank-conflict free, a broadcast row read is one wavefront and
+//   a column read across lanes hits consecutive banks).
+//   Products take the other operand's rows (broadcast) or columns from
+//   shared memory; Cholesky factors are stored transposed (LT = L^T, upper),
+//   so that a column of L is a contiguous row of the slot.
+// Padding convention: entries of padded rows/columns (index >= d) are zero
+// in every covariance-like matrix; the Cholesky routine uses a unit pivot
+// there, so factors and solves keep the padding exact.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace auxk {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+// ---------------------------------------------------------------- Philox
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+enum Purpose : uint32_t { PURPOSE_AUX = 0, PURPOSE_BACKWARD = 1, PURPOSE_MH = 2 };
+
+__device__ __forceinline__ uint4 philox_word(uint64_t seed, uint32_t chain, uint64_t iter,
+                                             uint32_t purpose, uint32_t t, uint32_t word) {
+  const uint4 ctr = make_uint4(word, (t & 0xFFFFFFu) | (purpose << 24), (uint32_t)iter, chain);
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  return philox4x32_10(ctr, key);
+}
+
+template <typename T> __device__ __forceinline__ T u01(uint32_t r) {
+  // ((r >> 9) + 0.5) * 2^-23: exact in binary32 and binary64, inside (0, 1)
+  return ((T)(r >> 9) + (T)0.5) * (T)(1.0 / 8388608.0);
+}
+
+__device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
+
+// standard normal number i of the (seed, chain, iter, purpose, t) stream
+template <typename T>
+__device__ __forceinline__ T philox_normal(uint64_t seed, uint32_t chain, uint64_t iter,
+                                           uint32_t purpose, uint32_t t, int i) {
+  const uint4 r = philox_word(seed, chain, iter, purpose, t, (uint32_t)(i >> 2));
+  const uint32_t ra = (i & 2) ? r.z : r.x;
+  const uint32_t rb = (i & 2) ? r.w : r.y;
+  const T rad = sqrt((T)-2 * log(u01<T>(ra)));
+  T s, c;
+  sincospi_t((T)2 * u01<T>(rb), &s, &c);
+  return rad * ((i & 1) ? s : c);
+}
+
+// ---------------------------------------------------------------- layout
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using V = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using V = double2; static constexpr int N = 2; };
+
+template <typename T, int DP> struct Lay {
+  static constexpr int N = Vec16<T>::N;
+  static constexpr int LD = DP + N;          // row stride in elements (16 B pad)
+  static constexpr int MAT = DP * LD;         // elements of one matrix slot
+  static constexpr int VEC = (DP + N - 1) / N * N;  // elements of one vector slot
+  static_assert(DP % N == 0, "DP must be a multiple of the 16-byte vector width");
+};
+
+template <typename T> __device__ __forceinline__ void unpack(const typename Vec16<T>::V& v, T* o);
+template <> __device__ __forceinline__ void unpack<float>(const float4& v, float* o) {
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+template <> __device__ __forceinline__ void unpack<double>(const double2& v, double* o) {
+  o[0] = v.x; o[1] = v.y;
+}
+template <typename T> __device__ __forceinline__ typename Vec16<T>::V pack(const T* o);
+template <> __device__ __forceinline__ float4 pack<float>(const float* o) {
+  return make_float4(o[0], o[1], o[2], o[3]);
+}
+template <> __device__ __forceinline__ double2 pack<double>(const double* o) {
+  return make_double2(o[0], o[1]);
+}
+
+// contiguous DP elements (16-byte aligned) -> registers
+template <typename T, int DP>
+__device__ __forceinline__ void ld_vec(const T* p, T (&r)[DP]) {
+  using V = typename Vec16<T>::V;
+  constexpr int N = Vec16<T>::N;
+  const V* q = reinterpret_cast<const V*>(p);
+#pragma unroll
+  for (int k = 0; k < DP / N; ++k) unpack<T>(q[k], &r[k * N]);
+}
+template <typename T, int DP>
+__device__ __forceinline__ void st_vec(T* p, const T (&r)[DP]) {
+  using V = typename Vec16<T>::V;
+  constexpr int N = Vec16<T>::N;
+  V* q = reinterpret_cast<V*>(p);
+#pragma unroll
+  for (int k = 0; k < DP / N; ++k) q[k] = pack<T>(&r[k * N]);
+}
+
+// row `row` of a slot
+template <typename T, int DP>
+__device__ __forceinline__ void ld_row(const T* S, int row, T (&r)[DP]) {
+  ld_vec<T, DP>(S + row * Lay<T, DP>::LD, r);
+}
+template <typename T, int DP>
+__device__ __forceinline__ void st_row(T* S, int row, const T (&r)[DP], bool active) {
+  if (active) st_vec<T, DP>(S + row * Lay<T, DP>::LD, r);
+}
+// store a register row as column `col` of a slot: S[k][col] = r[k]
+template <typename T, int DP>
+__device__ __forceinline__ void st_col(T* S, int col, const T (&r)[DP], bool active) {
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < DP; ++k) S[k * Lay<T, DP>::LD + col] = r[k];
+  }
+}
+// column `col` of a slot: r[k] = S[k][col]
+template <typename T, int DP>
+__device__ __forceinline__ void ld_col(const T* S, int col, T (&r)[DP]) {
+#pragma unroll
+  for (int k = 0; k < DP; ++k) r[k] = S[k * Lay<T, DP>::LD + col];
+}
+
+template <typename T, int DP>
+__device__ __forceinline__ void zero(T (&r)[DP]) {
+#pragma unroll
+  for (int k = 0; k < DP; ++k) r[k] = (T)0;
+}
+
+// out[j] (+)= sum_k a[k] * B[k][j]         (a: register row, B: slot, broadcast rows)
+template <typename T, int DP, bool ACC = false, bool NEG = false>
+__device__ __forceinline__ void row_mat(const T (&a)[DP], const T* B, T (&out)[DP]) {
+  if (!ACC) zero<T, DP>(out);
+  constexpr int N = Vec16<T>::N;
+#pragma unroll
+  for (int k = 0; k < DP; ++k) {
+    const T ak = NEG ? -a[k] : a[k];
+    T b[DP];
+    ld_row<T, DP>(B, k, b);
+#pragma unroll
+    for (int j = 0; j < DP; ++j) out[j] = fma(ak, b[j], out[j]);
+  }
+  (void)N;
+}
+
+// out[j] = sum_k a[k] * B[j][k]            (dot with every row of B)
+template <typename T, int DP>
+__device__ __forceinline__ void row_matT(const T (&a)[DP], const T* B, T (&out)[DP]) {
+#pragma unroll
+  for (int j = 0; j < DP; ++j) {
+    T b[DP];
+    ld_row<T, DP>(B, j, b);
+    T acc0 = 0, acc1 = 0;
+#pragma unroll
+    for (int k = 0; k < DP; k += 2) {
+      acc0 = fma(a[k], b[k], acc0);
+      if (k + 1 < DP) acc1 = fma(a[k + 1], b[k + 1], acc1);
+    }
+    out[j] = acc0 + acc1;
+  }
+}
+
+// dot of a register row with a vector slot (broadcast)
+template <typename T, int DP>
+__device__ __forceinline__ T dot_rv(const T (&a)[DP], const T* v) {
+  T b[DP];
+  ld_vec<T, DP>(v, b);
+  T acc0 = 0, acc1 = 0;
+#pragma unroll
+  for (int k = 0; k < DP; k += 2) {
+    acc0 = fma(a[k], b[k], acc0);
+    if (k + 1 < DP) acc1 = fma(a[k + 1], b[k + 1], acc1);
+  }
+  return acc0 + acc1;
+}
+
+template <typename T, int DP>
+__device__ __forceinline__ T dot_rr(const T (&a)[DP], const T (&b)[DP]) {
+  T acc0 = 0, acc1 = 0;
+#pragma unroll
+  for (int k = 0; k < DP; k += 2) {
+    acc0 = fma(a[k], b[k], acc0);
+    if (k + 1 < DP) acc1 = fma(a[k + 1], b[k + 1], acc1);
+  }
+  return acc0 + acc1;
+}
+
+// Cholesky of the symmetric matrix whose row `lane` is a[] (all lanes of the
+// warp call it; lanes >= DP pass anything). Writes LT = L^T (upper) to the
+// slot LT and 1/L_kk to inv_diag[k]. Indices k >= d get a unit pivot. A
+// non-positive or non-finite pivot at k < d sets *bad and is replaced by 1.
+// Contains the __syncwarp() needed before reading LT.
+template <typename T, int DP>
+__device__ __forceinline__ void chol_rows(T (&a)[DP], T* LT, T* inv_diag, int d, int lane,
+                                          int* bad) {
+  constexpr int LD = Lay<T, DP>::LD;
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < DP; ++k) {
+    T akk = __shfl_sync(FULL_MASK, a[k], k);
+    T piv = (T)1;
+    if (k < d) {
+      if (!(akk > (T)0) || !(akk < (T)INFINITY)) { *bad = 1; akk = (T)1; }
+      piv = sqrt(akk);
+    }
+    const T inv = (T)1 / piv;
+    T l = (lane == k) ? piv : ((lane > k) ? a[k] * inv : (T)0);
+    if (lane < DP) LT[k * LD + lane] = l;
+    if (lane == 0) inv_diag[k] = inv;
+    __syncwarp();
+    if (k + 1 < DP) {
+      T lk[DP];
+      ld_row<T, DP>(LT, k, lk);
+      const T nl = -l;
+#pragma unroll
+      for (int j = k + 1; j < DP; ++j) a[j] = fma(nl, lk[j], a[j]);
+    }
+  }
+  __syncwarp();
+}
+
+// Per-lane forward substitution: y = L^{-1} rhs with L given as LT = L^T.
+template <typename T, int DP>
+__device__ __forceinline__ void fwd_subst(const T* LT, const T* inv_diag, T (&rhs)[DP],
+                                          T (&y)[DP]) {
+  T id[DP];
+  ld_vec<T, DP>(inv_diag, id);
+#pragma unroll
+  for (int k = 0; k < DP; ++k) {
+    y[k] = rhs[k] * id[k];
+    if (k + 1 < DP) {
+      T lk[DP];
+      ld_row<T, DP>(LT, k, lk);  // lk[j] = L[j][k]
+      const T ny = -y[k];
+#pragma unroll
+      for (int j = k + 1; j < DP; ++j) rhs[j] = fma(ny, lk[j], rhs[j]);
+    }
+  }
+}
+
+// Per-lane backward substitution: y = L^{-T} rhs with L given as LT = L^T.
+template <typename T, int DP>
+__device__ __forceinline__ void bwd_subst(const T* LT, const T* inv_diag, const T (&rhs)[DP],
+                                          T (&y)[DP]) {
+  T id[DP];
+  ld_vec<T, DP>(inv_diag, id);
+#pragma unroll
+  for (int k = DP - 1; k >= 0; --k) {
+    T lk[DP];
+    ld_row<T, DP>(LT, k, lk);  // lk[j] = L^T[k][j] = L[j][k]
+    T acc = rhs[k];
+#pragma unroll
+    for (int j = k + 1; j < DP; ++j) acc = fma(-lk[j], y[j], acc);
+    y[k] = acc * id[k];
+  }
+}
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+  return v;
+}
+
+}  // namespace auxk

@@ -1,0 +1,79 @@
+// aux_internal.h — the model handle and the per-precision operation table.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "aux_kalman.h"
+
+struct AuxOps;
+
+struct aux_model {
+  int dtype = 0, d = 0, DP = 0, T = 0, C = 0, emis = 0, y_per_chain = 0;
+  int L = 0, nb = 0;
+  double delta = 0.0;
+  uint64_t seed = 0;
+  size_t esz = 0;            // bytes per compute-type element
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  // model on the device, compute type, padded to DP
+  void *F = nullptr, *Q = nullptr, *P0 = nullptr, *m0 = nullptr, *b = nullptr, *Ryinv = nullptr;
+  void *y = nullptr;
+  uint8_t *mask = nullptr;
+  // workspace
+  void *u = nullptr, *v = nullptr, *yt = nullptr, *xs = nullptr, *yts = nullptr;
+  void *agg0 = nullptr, *agg1 = nullptr;
+  void *G = nullptr, *U = nullptr, *gu = nullptr;
+  void *tmpl = nullptr;      // element template: 7 DP x DP matrices
+  double *fq = nullptr, *fld = nullptr, *mh_part = nullptr, *lz_part = nullptr;
+  int32_t *status_iter = nullptr, *status = nullptr;
+  const AuxOps *ops = nullptr;
+  std::vector<void *> allocs;
+  // optional per-launch CUDA-event timing (aux_set_profiling)
+  struct Rec { int kind; cudaEvent_t a, b; };
+  bool profiling = false;
+  std::vector<Rec> recs;      // recorded this window
+  std::vector<Rec> pool;      // free event pairs
+};
+
+// kernel kinds reported by aux_read_profile (order of AUX_PROFILE_* in the header)
+enum { PK_LINEARISE = 0, PK_TEMPLATE, PK_REDUCE, PK_SCAN, PK_APPLY, PK_BACKWARD, PK_MH, PK_SUM,
+       PK_COUNT };
+
+// bracket a launch with events on its stream when profiling is on
+struct ProfScope {
+  aux_model *m;
+  cudaStream_t st;
+  aux_model::Rec r;
+  bool on;
+  ProfScope(aux_model *m_, int kind, cudaStream_t st_) : m(m_), st(st_), on(m_->profiling) {
+    if (!on) return;
+    if (!m->pool.empty()) { r = m->pool.back(); m->pool.pop_back(); }
+    else { cudaEventCreate(&r.a); cudaEventCreate(&r.b); }
+    r.kind = kind;
+    cudaEventRecord(r.a, st);
+  }
+  ~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(r.b, st);
+    m->recs.push_back(r);
+  }
+};
+
+struct AuxOps {
+  int (*prepare)();
+  int (*kalman_step)(aux_model *, void *x, int n_iters, uint64_t iter0, uint32_t *acc,
+                     double *log_alpha, cudaStream_t);
+  int (*loglik)(aux_model *, const void *yt, double *logZ, void *mf, void *Pf, cudaStream_t);
+  int (*sample_path)(aux_model *, const void *yt, const void *eps, uint64_t iter, void *xs,
+                     double *logZ, cudaStream_t);
+};
+
+const AuxOps *aux_ops_f32(int DP);
+const AuxOps *aux_ops_f64(int DP);
+
+// element counts of the per-block buffers for a padded dimension DP
+inline size_t aux_es(int DP) { return 3u * DP * DP + 2u * DP; }
+inline size_t aux_gs(int DP) { return (size_t)DP * DP + DP; }

@@ -1,0 +1,162 @@
+// aux_ops.cuh — host-side launch sequences for one precision and padded dimension.
+#pragma once
+#include <cmath>
+
+#include "aux_kernels.cuh"
+
+namespace auxk {
+namespace {
+
+__global__ void k_sum_parts(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  const int c = blockIdx.x;
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) s += part[(long)c * nb + k];
+  s = warp_sum<double>(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+    out[c] = t;
+  }
+}
+
+inline int cuda_ok(cudaError_t e) { return e == cudaSuccess ? AUX_OK : AUX_E_CUDA; }
+
+}  // namespace
+
+template <typename Real>
+KP<Real> make_kp(const aux_model* m) {
+  KP<Real> p;
+  p.C = m->C; p.nT = m->T; p.d = m->d; p.DP = m->DP; p.L = m->L; p.nb = m->nb;
+  p.r = (Real)(0.5 * m->delta);
+  p.sqrt_r = (Real)std::sqrt(0.5 * m->delta);
+  p.emis = m->emis; p.y_per_chain = m->y_per_chain; p.seed = m->seed;
+  p.F = (const Real*)m->F; p.Q = (const Real*)m->Q; p.P0 = (const Real*)m->P0;
+  p.m0 = (const Real*)m->m0; p.b = (const Real*)m->b; p.Ryinv = (const Real*)m->Ryinv;
+  p.y = (const Real*)m->y; p.mask = m->mask;
+  p.status_iter = m->status_iter;
+  return p;
+}
+
+template <typename Real, int DP>
+struct Ops {
+  using Z = Sizes<Real, DP>;
+
+  static int prepare() {
+    cudaError_t e = cudaSuccess;
+    e = cudaFuncSetAttribute(k_filter_reduce<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Z::RED_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_filter_scan_level<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Z::SCAN_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_filter_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Z::APP_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_sample_backward<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Z::BWD_SMEM);
+    return cuda_ok(e);
+  }
+
+  static int items(const aux_model* m) { return m->C * m->nb; }
+
+  // the model-derived matrix parts of the filtering elements; they depend on
+  // (F, Q, P0, delta) only, so one pass serves every chain and step of a call
+  static void template_pass(aux_model* m, const KP<Real>& p, cudaStream_t st) {
+    ProfScope ps(m, PK_TEMPLATE, st);
+    k_element_template<Real, DP><<<1, 32, 0, st>>>(p, (Real*)m->tmpl);
+  }
+
+  // parallel filter on yt: phase 1, Hillis-Steele rounds, phase 3
+  static void filter(aux_model* m, const KP<Real>& p, const Real* yt, ApplyArgs<Real> a,
+                     cudaStream_t st) {
+    const int n = items(m);
+    Real* b0 = (Real*)m->agg0;
+    Real* b1 = (Real*)m->agg1;
+    { ProfScope ps(m, PK_REDUCE, st);
+    k_filter_reduce<Real, DP><<<(n + Z::RED_WPC - 1) / Z::RED_WPC, 32 * Z::RED_WPC, Z::RED_SMEM, st>>>(
+        p, (const Real*)m->tmpl, yt, b0); }
+    for (int off = 1; off < m->nb; off *= 2) {
+      { ProfScope ps(m, PK_SCAN, st);
+      k_filter_scan_level<Real, DP><<<(n + Z::SCAN_WPC - 1) / Z::SCAN_WPC, 32 * Z::SCAN_WPC, Z::SCAN_SMEM, st>>>(p, b0, b1, off); }
+      Real* tmp = b0; b0 = b1; b1 = tmp;
+    }
+    a.yt = yt;
+    a.prefix = (m->nb > 1) ? b0 : nullptr;
+    ProfScope ps(m, PK_APPLY, st);
+    k_filter_apply<Real, DP><<<(n + Z::APP_WPC - 1) / Z::APP_WPC, 32 * Z::APP_WPC, Z::APP_SMEM, st>>>(p, a);
+  }
+
+  static ApplyArgs<Real> apply_args(aux_model* m, int flags, uint64_t iter) {
+    ApplyArgs<Real> a{};
+    a.flags = flags;
+    a.G = (Real*)m->G; a.U = (Real*)m->U; a.gu = (Real*)m->gu;
+    a.fq = m->fq; a.fld = m->fld; a.lz_part = m->lz_part;
+    a.mf = nullptr; a.Pf = nullptr; a.eps = nullptr;
+    a.iter = iter;
+    return a;
+  }
+
+  static void backward(aux_model* m, const KP<Real>& p, BackArgs<Real> b, cudaStream_t st) {
+    const int n = items(m);
+    ProfScope ps(m, PK_BACKWARD, st);
+    k_sample_backward<Real, DP><<<(n + Z::BWD_WPC - 1) / Z::BWD_WPC, 32 * Z::BWD_WPC, Z::BWD_SMEM, st>>>(p, b);
+  }
+
+  static int kalman_step(aux_model* m, void* xv, int n_iters, uint64_t iter0, uint32_t* acc,
+                         double* log_alpha, cudaStream_t st) {
+    const KP<Real> p = make_kp<Real>(m);
+    Real* x = (Real*)xv;
+    const long n = (long)m->C * m->T * m->d;
+    template_pass(m, p, st);
+    const int lin_grid = (int)std::min<long>((n + 255) / 256, 152L * 16);
+    for (int it = 0; it < n_iters; ++it) {
+      const uint64_t iter = iter0 + (uint64_t)it;
+      { ProfScope ps(m, PK_LINEARISE, st);
+      k_linearise<Real><<<lin_grid, 256, 0, st>>>(p, x, (Real*)m->u, (Real*)m->v, (Real*)m->yt, iter); }
+      filter(m, p, (const Real*)m->yt, apply_args(m, APPLY_EPI | APPLY_STORE_Q, iter), st);
+      BackArgs<Real> b{};
+      b.G = (const Real*)m->G; b.U = (const Real*)m->U; b.gu = (const Real*)m->gu;
+      b.xs = (Real*)m->xs; b.mh = 1; b.x = x; b.u = (const Real*)m->u; b.v = (const Real*)m->v;
+      b.yts = (Real*)m->yts; b.mh_part = m->mh_part;
+      backward(m, p, b, st);
+      filter(m, p, (const Real*)m->yts, apply_args(m, APPLY_REV_DIFF, iter), st);
+      { ProfScope ps(m, PK_MH, st);
+      k_mh<Real><<<m->C, 128, 0, st>>>(p, x, (const Real*)m->xs, m->mh_part, m->lz_part, iter, acc,
+                                       log_alpha, m->status); }
+    }
+    return cuda_ok(cudaGetLastError());
+  }
+
+  static int loglik(aux_model* m, const void* yt, double* logZ, void* mf, void* Pf, cudaStream_t st) {
+    const KP<Real> p = make_kp<Real>(m);
+    template_pass(m, p, st);
+    ApplyArgs<Real> a = apply_args(m, APPLY_LOGZ, 0);
+    a.mf = (Real*)mf;
+    a.Pf = (Real*)Pf;
+    filter(m, p, (const Real*)yt, a, st);
+    { ProfScope ps(m, PK_SUM, st);
+    k_sum_parts<<<m->C, 128, 0, st>>>(m->lz_part, m->nb, logZ); }
+    return cuda_ok(cudaGetLastError());
+  }
+
+  static int sample_path(aux_model* m, const void* yt, const void* eps, uint64_t iter, void* xs,
+                         double* logZ, cudaStream_t st) {
+    const KP<Real> p = make_kp<Real>(m);
+    template_pass(m, p, st);
+    ApplyArgs<Real> a = apply_args(m, APPLY_EPI | APPLY_LOGZ, iter);
+    a.eps = (const Real*)eps;
+    filter(m, p, (const Real*)yt, a, st);
+    BackArgs<Real> b{};
+    b.G = (const Real*)m->G; b.U = (const Real*)m->U; b.gu = (const Real*)m->gu;
+    b.xs = (Real*)xs; b.mh = 0;
+    backward(m, p, b, st);
+    if (logZ) { ProfScope ps(m, PK_SUM, st); k_sum_parts<<<m->C, 128, 0, st>>>(m->lz_part, m->nb, logZ); }
+    return cuda_ok(cudaGetLastError());
+  }
+
+  static const AuxOps* table() {
+    static const AuxOps t = {&prepare, &kalman_step, &loglik, &sample_path};
+    return &t;
+  }
+};
+
+}  // namespace auxk

@@ -94,7 +94,9 @@ def sv_parameters(d, rng):
 
 # delta per (d, T) for the SV model, frozen once from an oracle calibration run
 # (Robbins-Monro on log delta towards ~50% acceptance).
-SV_DELTA = {}
+SV_DELTA = {
+    (30, 1024): 0.0183,   # 400 oracle steps, acceptance 0.47 over the second half
+}
 
 
 def stochastic_volatility(d=30, T=1024, n_chains=32, sim_seed=0, mcmc_seed=1, delta=None):

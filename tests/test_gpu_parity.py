@@ -1,0 +1,265 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative errors are normwise over each chain's whole array):
+  FP64 path: 1e-9 on means, covariances, paths and log Z; 1e-8 absolute on log alpha.
+  FP32 path: 1e-4 on filtering means/covariances and sampled paths, 1e-5 on log Z
+  (the stated accuracy targets); log alpha within TOL_LA32 absolute, derived in
+  the design doc from FP32 rounding of T*d per-element terms; MH decisions must agree
+  except where |log alpha_oracle - log U| < TOL_LA32.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import kalman, mcmc, philox  # noqa: E402
+from paper_2303_00301_gb300 import AuxKalman, workloads  # noqa: E402
+
+TOL_LA32 = 2e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_00301_gb300 import build
+    build.build()
+
+
+def _tt(a, dtype):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300)
+
+
+def _lgssm_workload(d, T, C, seed, delta=0.5):
+    m = workloads.random_lgssm(d, T, seed=seed)
+    return workloads.Workload(name="rand", d=d, T=T, n_chains=C, m0=m["m0"], P0=m["P0"],
+                              F=m["F"], b=m["b"], Q=m["Q"], y=m["y"],
+                              emission=workloads.EMIS_LINEAR_GAUSSIAN, delta=delta,
+                              x_init=np.zeros((C, T, d)), Ry=np.eye(d))
+
+
+def _oracle_model(wl):
+    if wl.emission == workloads.EMIS_SV:
+        em = mcmc.SVEmission(wl.y, wl.mask)
+    else:
+        em = mcmc.LinearGaussianEmission(wl.y, wl.Ry, wl.mask)
+    return dict(m0=wl.m0, P0=wl.P0, F=wl.F, b=wl.b, Q=wl.Q, emission=em)
+
+
+FILTER_CASES = [
+    # d, T, C, block_len, dtype
+    (2, 64, 2, 8, "f64"),
+    (1, 37, 3, 8, "f64"),
+    (3, 37, 3, 5, "f64"),
+    (16, 50, 2, 9, "f64"),
+    (2, 1, 2, 1, "f64"),
+    (3, 20, 2, 1, "f64"),
+    (4, 20, 2, 20, "f64"),
+    (5, 41, 2, 7, "f32"),
+    (8, 33, 2, 6, "f32"),
+    (30, 128, 2, 16, "f32"),
+]
+
+
+@pytest.mark.parametrize("d,T,C,L,dt", FILTER_CASES)
+def test_loglik_filter_parity(d, T, C, L, dt):
+    wl = _lgssm_workload(d, T, C, seed=100 + d * T)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    tol = 1e-9 if dt == "f64" else 1e-4
+    tol_z = 1e-9 if dt == "f64" else 1e-5
+    rng = np.random.default_rng(d + T)
+    yt = rng.standard_normal((C, T, d))
+    s = AuxKalman(wl, dtype=dt, block_len=L)
+    logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
+    mf = torch.zeros((C, T, d), dtype=tdt, device="cuda")
+    Pf = torch.zeros((C, T, d, d), dtype=tdt, device="cuda")
+    s.loglik(_tt(yt, tdt), logZ, mf, Pf)
+    torch.cuda.synchronize()
+    R = 0.5 * wl.delta * np.eye(d)
+    for c in range(C):
+        kf = kalman.kalman_filter(yt[c], wl.m0, wl.P0, wl.F, wl.b, wl.Q, R)
+        assert abs(logZ[c].item() - kf["logZ"]) <= tol_z * abs(kf["logZ"]), (c, logZ[c].item(), kf["logZ"])
+        assert _rel(mf[c].double().cpu().numpy(), kf["mf"]) < tol
+        assert _rel(Pf[c].double().cpu().numpy(), kf["Pf"]) < tol
+    assert s.status()[0] == 0
+    s.close()
+
+
+@pytest.mark.parametrize("d,T,C,L,dt", FILTER_CASES)
+def test_sample_path_parity(d, T, C, L, dt):
+    wl = _lgssm_workload(d, T, C, seed=200 + d * T)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    tol = 1e-9 if dt == "f64" else 1e-4
+    rng = np.random.default_rng(7 * d + T)
+    yt = rng.standard_normal((C, T, d))
+    eps = rng.standard_normal((C, T, d))
+    s = AuxKalman(wl, dtype=dt, block_len=L)
+    xs = torch.zeros((C, T, d), dtype=tdt, device="cuda")
+    logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
+    s.sample_path(_tt(yt, tdt), xs, eps=_tt(eps, tdt), logZ=logZ)
+    torch.cuda.synchronize()
+    R = 0.5 * wl.delta * np.eye(d)
+    for c in range(C):
+        kf = kalman.kalman_filter(yt[c], wl.m0, wl.P0, wl.F, wl.b, wl.Q, R)
+        x_ref = kalman.rts_sample(kf, wl.F, wl.b, wl.Q, eps[c])
+        assert _rel(xs[c].double().cpu().numpy(), x_ref) < tol, c
+    s.close()
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_backward_noise_is_the_philox_stream(dt):
+    d, T, C = 6, 30, 3
+    wl = _lgssm_workload(d, T, C, seed=5)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    s = AuxKalman(wl, dtype=dt, block_len=7, seed=77)
+    yt = _tt(np.random.default_rng(1).standard_normal((C, T, d)), tdt)
+    it = 123456789
+    eps = philox.path_normals(77, np.arange(C), it, philox.PURPOSE_BACKWARD, T, d)
+    xa = torch.zeros((C, T, d), dtype=tdt, device="cuda")
+    xb = torch.zeros((C, T, d), dtype=tdt, device="cuda")
+    s.sample_path(yt, xa, eps=None, iteration=it)
+    s.sample_path(yt, xb, eps=_tt(eps, tdt), iteration=it)
+    torch.cuda.synchronize()
+    tol = 1e-12 if dt == "f64" else 2e-6
+    assert _rel(xa.double().cpu().numpy(), xb.double().cpu().numpy()) < tol
+    s.close()
+
+
+def _step_and_compare(wl, dt, L, n_iters, chains=None, tol_x=None, tol_la=None):
+    """Step all chains on the GPU; replay the chosen chains on the oracle from the same state.
+
+    Each oracle step starts from the GPU's state before that step, so a rare
+    near-tie decision difference in FP32 does not make the paths diverge."""
+    C = wl.n_chains
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    s = AuxKalman(wl, dtype=dt, block_len=L)
+    x = _tt(wl.x_init, tdt)
+    la = torch.zeros(C, dtype=torch.float64, device="cuda")
+    model = _oracle_model(wl)
+    chains = list(range(C)) if chains is None else chains
+    mismatches, max_dla = 0, 0.0
+    for it in range(n_iters):
+        x_before = x.double().cpu().numpy()
+        s.step(x, n_iters=1, iter0=it, log_alpha=la)
+        torch.cuda.synchronize()
+        xg = x.double().cpu().numpy()
+        lag = la.cpu().numpy()
+        for c in chains:
+            ref = mcmc.aux_step_philox(x_before[c], model, wl.delta, wl.mcmc_seed, c, it)
+            lu = np.log(philox.mh_uniform(wl.mcmc_seed, c, it))
+            dla = abs(lag[c] - ref["log_alpha"])
+            max_dla = max(max_dla, dla)
+            near_tie = abs(ref["log_alpha"] - lu) < tol_la
+            assert dla < tol_la or near_tie, (it, c, lag[c], ref["log_alpha"])
+            gpu_accepted = bool(lu < lag[c])
+            if gpu_accepted != ref["accepted"]:
+                assert near_tie, (it, c, lag[c], ref["log_alpha"], lu)
+                mismatches += 1
+                continue
+            if gpu_accepted:
+                assert _rel(xg[c], ref["x_star"]) < tol_x, (it, c, _rel(xg[c], ref["x_star"]))
+            else:
+                assert np.array_equal(xg[c], x_before[c]), (it, c)
+    assert s.status()[0] == 0
+    s.close()
+    return mismatches, max_dla
+
+
+def test_kalman_step_parity_linear_gaussian_f64():
+    wl = workloads.linear_gaussian(d=2, T=64, n_chains=4)
+    _step_and_compare(wl, "f64", L=8, n_iters=4, tol_x=1e-9, tol_la=1e-8)
+
+
+def test_kalman_step_parity_masked_toy_f64():
+    wl = workloads.two_step_toy(rho=0.7, r2=0.3, n_chains=3)
+    _step_and_compare(wl, "f64", L=1, n_iters=4, tol_x=1e-9, tol_la=1e-8)
+
+
+def test_kalman_step_parity_sv_f64():
+    wl = workloads.stochastic_volatility(d=6, T=45, n_chains=3, delta=0.05)
+    _step_and_compare(wl, "f64", L=8, n_iters=3, tol_x=1e-9, tol_la=1e-8)
+
+
+def test_kalman_step_parity_sv_f32_small():
+    wl = workloads.stochastic_volatility(d=6, T=45, n_chains=4, delta=0.05)
+    _step_and_compare(wl, "f32", L=8, n_iters=3, tol_x=1e-4, tol_la=TOL_LA32)
+
+
+def test_kalman_step_parity_sv_f32_full_size_sampled_chains():
+    """d=30, T=1024, 32 chains in the benchmark's launch configuration; oracle on 4 chains."""
+    wl = workloads.stochastic_volatility(d=30, T=1024, n_chains=32)
+    _step_and_compare(wl, "f32", L=0, n_iters=1, chains=[0, 9, 22, 31], tol_x=1e-4,
+                      tol_la=TOL_LA32)
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_resume_is_bitwise(dt):
+    wl = workloads.stochastic_volatility(d=5, T=33, n_chains=3, delta=0.05)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    s = AuxKalman(wl, dtype=dt, block_len=6)
+    xa = _tt(wl.x_init, tdt)
+    xb = _tt(wl.x_init, tdt)
+    s.step(xa, n_iters=6, iter0=10)
+    s.step(xb, n_iters=2, iter0=10)
+    s.step(xb, n_iters=4, iter0=12)
+    torch.cuda.synchronize()
+    assert torch.equal(xa, xb)
+    s.close()
+
+
+def test_nonfinite_state_is_rejected_and_reported():
+    wl = workloads.stochastic_volatility(d=4, T=20, n_chains=3, delta=0.05)
+    s = AuxKalman(wl, dtype="f32", block_len=5)
+    x0 = wl.x_init.copy()
+    x0[1, 7, 2] = np.nan
+    x = _tt(x0, torch.float32)
+    s.step(x, n_iters=1, iter0=0)
+    torch.cuda.synchronize()
+    rc, per_chain = s.status()
+    assert per_chain[1] != 0 and per_chain[0] == 0 and per_chain[2] == 0
+    xg = x.cpu().numpy()
+    assert np.isnan(xg[1, 7, 2]) and np.array_equal(np.nan_to_num(xg[1]), np.nan_to_num(x0[1].astype(np.float32)))
+    assert s.status()[0] == 0      # cleared by the previous read
+    s.close()
+
+
+def test_two_step_toy_posterior_on_gpu():
+    """Section 5.4 model: the ensemble of many chains matches the closed-form posterior of x_0."""
+    rho, r2, y = 0.8, 0.5, 2.0
+    C = 512
+    wl = workloads.two_step_toy(rho=rho, r2=r2, y_obs=y, n_chains=C, delta=1.0, mcmc_seed=3)
+    s = AuxKalman(wl, dtype="f64", block_len=1)
+    x = _tt(wl.x_init, torch.float64)
+    acc = torch.zeros(C, dtype=torch.int32, device="cuda")
+    s.step(x, n_iters=300, iter0=0, accept_count=acc)
+    torch.cuda.synchronize()
+    x0 = x[:, 0, 0].cpu().numpy()
+    m, v = wl.meta["post_mean_x0"], wl.meta["post_var_x0"]
+    assert abs(x0.mean() - m) < 4.5 * np.sqrt(v / C)
+    assert abs(x0.var() / v - 1) < 0.25
+    assert 0.2 < acc.float().mean().item() / 300 < 0.99
+    s.close()
+
+
+def test_linear_gaussian_stationarity_on_gpu():
+    """Config-1 model: chain ensemble matches the exact smoother (KF + RTS) within MC error."""
+    C = 256
+    wl = workloads.linear_gaussian(d=2, T=64, n_chains=C)
+    s = AuxKalman(wl, dtype="f64", block_len=8)
+    x = _tt(wl.x_init, torch.float64)
+    s.step(x, n_iters=400, iter0=0)
+    torch.cuda.synchronize()
+    xe = x.cpu().numpy()
+    kf = kalman.kalman_filter(wl.y, wl.m0, wl.P0, wl.F, wl.b, wl.Q, wl.Ry)
+    ms, Ps = kalman.rts_smoother(kf, wl.F)
+    sd = np.sqrt(np.einsum("tii->ti", Ps))
+    z = (xe.mean(axis=0) - ms) / (sd / np.sqrt(C))
+    assert np.max(np.abs(z)) < 4.5, np.max(np.abs(z))
+    ratio = xe.var(axis=0) / sd ** 2
+    assert 0.75 < ratio.mean() < 1.25
+    s.close()
