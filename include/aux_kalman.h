@@ -60,6 +60,7 @@ extern "C" {
 #define AUX_E_TIMEOUT      5  /* reserved: a bounded device wait gave up */
 #define AUX_E_OOM          6  /* workspace allocation failed */
 #define AUX_E_UNSUPPORTED  7  /* valid but not built (e.g. d_x > 32) */
+#define AUX_E_TOO_LARGE    8  /* the problem does not fit the fixed scratch of aux_loglik_noalloc */
 
 /* compute types */
 #define AUX_F32 0
@@ -152,6 +153,31 @@ int aux_set_profiling(aux_model *m, int32_t enable);
  * kernel kind since the last read; waits for the recorded events and resets
  * the window. ms_per_kind, launches_per_kind: host arrays of n_kinds entries. */
 int aux_read_profile(aux_model *m, double *ms_per_kind, int32_t *launches_per_kind, int32_t n_kinds);
+
+/* aux_loglik without any device allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, such as code that
+ * runs inside a host callback, under an allocator it must not bypass, or in a
+ * process whose device-memory budget is fixed before it starts, and that
+ * therefore cannot create a model handle.
+ * It computes the same log marginal likelihood as aux_loglik, logZ[c] for each
+ * chain's pseudo-observations, from the host model description alone (only
+ * dtype, d_x, T, n_chains, block_len, m0, P0, F, b, Q and delta are read).
+ *   desc   host model description (see aux_model_desc).
+ *   ytilde device [C][T][d] compute type (caller-owned input).
+ *   logZ   device [C] double (caller-owned output).
+ * All scratch lives in one device array of AUX_NOALLOC_SCRATCH_BYTES that is
+ * part of the library: every GPU that loads the library holds it until the
+ * process exits. Problems needing more scratch return AUX_E_TOO_LARGE; the
+ * scratch needed is about 2 * C * ceil(T / block_len) * (3 p^2 + 2 p) elements,
+ * p = d_x rounded up to 4, 8, 16 or 32.
+ * The first call on a device does a one-time set-up for that device (it looks
+ * up the array's device address and sets kernel attributes); make that first
+ * call before any stream capture. Every call shares the array, which keeps the
+ * last call's contents: calls whose work overlaps on the GPU (other streams or
+ * host threads) race, so serialise them. The call waits for its own model
+ * upload (a few kilobytes) before enqueuing the kernels on stream. */
+#define AUX_NOALLOC_SCRATCH_BYTES (32u << 20)
+int aux_loglik_noalloc(const aux_model_desc *desc, const void *ytilde, double *logZ, void *stream);
 
 /* Release the handle and its device memory (synchronises). NULL is a no-op. */
 void aux_free_model(aux_model *m);

@@ -16,6 +16,8 @@ from . import build as _build
 AUX_ABI_VERSION = 1
 AUX_OK, AUX_E_INVALID_ARG, AUX_E_NOT_PD, AUX_E_NONFINITE = 0, 1, 2, 3
 AUX_E_CUDA, AUX_E_TIMEOUT, AUX_E_OOM, AUX_E_UNSUPPORTED = 4, 5, 6, 7
+AUX_E_TOO_LARGE = 8
+AUX_NOALLOC_SCRATCH_BYTES = 32 << 20
 AUX_F32, AUX_F64 = 0, 1
 AUX_EMIS_LINEAR_GAUSSIAN, AUX_EMIS_SV = 0, 1
 
@@ -77,6 +79,8 @@ def _load():
     lib.aux_read_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
     lib.aux_read_profile.restype = ctypes.c_int
+    lib.aux_loglik_noalloc.argtypes = [ctypes.POINTER(aux_model_desc), vp, vp, vp]
+    lib.aux_loglik_noalloc.restype = ctypes.c_int
     lib.aux_status_string.argtypes = [ctypes.c_int]
     lib.aux_status_string.restype = ctypes.c_char_p
     return lib
@@ -116,10 +120,12 @@ def _as_c(a, dtype=np.float64):
     return np.ascontiguousarray(np.asarray(a, dtype=dtype))
 
 
-def aux_init_model(*, d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind, dtype=AUX_F32,
-                   R_y=None, obs_mask=None, y_per_chain=False, block_len=0, seed=0, stream=None):
-    """Create a model handle (host arrays are copied during the call)."""
-    keep = dict(m0=_as_c(m0), P0=_as_c(P0), F=_as_c(F), b=_as_c(b), Q=_as_c(Q), y=_as_c(y))
+def _make_desc(d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind, dtype, R_y, obs_mask,
+               y_per_chain, block_len):
+    """Fill an aux_model_desc; returns it with the numpy arrays it points into."""
+    keep = dict(m0=_as_c(m0), P0=_as_c(P0), F=_as_c(F), b=_as_c(b), Q=_as_c(Q))
+    if y is not None:
+        keep["y"] = _as_c(y)
     desc = aux_model_desc()
     desc.abi_version = AUX_ABI_VERSION
     desc.dtype = int(dtype)
@@ -136,11 +142,30 @@ def aux_init_model(*, d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind, dt
         keep["mask"] = _as_c(obs_mask, np.uint8)
         desc.obs_mask = keep["mask"].ctypes.data_as(_u8_p)
     desc.delta = float(delta)
+    return desc, keep
+
+
+def aux_init_model(*, d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind, dtype=AUX_F32,
+                   R_y=None, obs_mask=None, y_per_chain=False, block_len=0, seed=0, stream=None):
+    """Create a model handle (host arrays are copied during the call)."""
+    desc, keep = _make_desc(d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind, dtype, R_y,
+                            obs_mask, y_per_chain, block_len)
     handle = ctypes.c_void_p()
     rc = LIB.aux_init_model(ctypes.byref(desc), ctypes.c_uint64(int(seed)), _stream(stream),
                             ctypes.byref(handle))
     _check(rc, "aux_init_model")
+    del keep
     return handle
+
+
+def aux_loglik_noalloc(ytilde, logZ, *, d_x, T, n_chains, m0, P0, F, b, Q, delta,
+                       dtype=AUX_F32, block_len=0, stream=None):
+    """aux_loglik without a handle or any device allocation (fixed library scratch)."""
+    desc, keep = _make_desc(d_x, T, n_chains, m0, P0, F, b, Q, None, delta, 0, dtype, None,
+                            None, False, block_len)
+    rc = LIB.aux_loglik_noalloc(ctypes.byref(desc), _ptr(ytilde), _ptr(logZ), _stream(stream))
+    _check(rc, "aux_loglik_noalloc")
+    del keep
 
 
 def aux_kalman_step(handle, x, n_iters, iter0=0, accept_count=None, log_alpha=None, stream=None):

@@ -156,6 +156,7 @@ const char* aux_status_string(int code) {
     case AUX_E_TIMEOUT: return "device wait timed out";
     case AUX_E_OOM: return "out of device memory";
     case AUX_E_UNSUPPORTED: return "unsupported configuration";
+    case AUX_E_TOO_LARGE: return "problem exceeds the fixed scratch of aux_loglik_noalloc";
     default: return "unknown status";
   }
 }
