@@ -12,12 +12,12 @@
  *            x* ~ smoothing law of the LGSSM (F, b, Q; H = I, R = (delta/2) I)
  *                 given ytilde, sampled by a parallel-in-time Kalman filter
  *                 (Appendix A.2.1) and a parallel backward-sampling scan
- *                 (Proposition A.1, Algorithm A.4),
+ *                 (Proposition A.1, parallel RTS sampler of Appendix A.2.2),
  *            accept x* with the Metropolis-Hastings ratio of Algorithm 2.
  *
  * Emission models: linear-Gaussian log h = log N(y; x, R_y) (Appendix A,
  * Eq. (A.1)) and multivariate stochastic volatility
- * log h = sum_i log N(y_i; 0, exp(x_i)) (Section 5.1). Sigma_t = I.
+ * log h = sum_i log N(y_i; 0, exp(x_i)) (Section 4.1). Sigma_t = I.
  *
  * Conventions for every entry point:
  *  - T is the number of states (array length); arrays are row-major and
@@ -70,7 +70,7 @@ extern "C" {
 #define AUX_EMIS_LINEAR_GAUSSIAN 0
 #define AUX_EMIS_SV              1
 
-/* Model description (Section 2.2, Eq. (2.5); SV model of Section 5.1).
+/* Model description (Section 2.2, Eq. (2.5); SV model of Section 4.1).
  * All arrays are HOST pointers to double, copied by aux_init_model. */
 typedef struct {
   int32_t abi_version;   /* AUX_ABI_VERSION */
@@ -112,7 +112,7 @@ int aux_kalman_step(aux_model *m, void *x, int32_t n_iters, uint64_t iter0,
                     uint32_t *accept_count, double *log_alpha, void *stream);
 
 /* Log marginal likelihood of the auxiliary LGSSM for given pseudo-observations
- * (the Kalman-filter likelihood of Algorithm A.1 with predictive terms
+ * (the likelihood of the Kalman filter algorithm, Appendix A.1, with predictive terms
  * N(ytilde_t; m^p_t, P^p_t + R), computed by the parallel filter of Appendix A.2.1).
  *   ytilde device [C][T][d] compute type.
  *   logZ   device [C] double (required).
@@ -138,8 +138,8 @@ int aux_get_status(aux_model *m, int32_t *per_chain_status);
 #define AUX_PROFILE_LINEARISE 0  /* v, u, ytilde at the current state (Eq. (2.7)) */
 #define AUX_PROFILE_TEMPLATE  1  /* model-derived matrix parts of the filtering elements */
 #define AUX_PROFILE_REDUCE    2  /* block aggregates of the filtering elements (Appendix A.2.1) */
-#define AUX_PROFILE_SCAN      3  /* one Hillis-Steele round over block aggregates (Algorithm A.3) */
-#define AUX_PROFILE_APPLY     4  /* in-block filtering from the block prefix + (G_t, U_t) (Eq. (A.11)) */
+#define AUX_PROFILE_SCAN      3  /* one Hillis-Steele round over block aggregates (Appendix A.2.1) */
+#define AUX_PROFILE_APPLY     4  /* in-block filtering from the block prefix + (G_t, U_t) (Eq. (A.14)) */
 #define AUX_PROFILE_BACKWARD  5  /* backward (G, U) scan, x*, and MH partial sums (Proposition A.1) */
 #define AUX_PROFILE_MH        6  /* log alpha, MH test and state update (Algorithm 2) */
 #define AUX_PROFILE_SUM       7  /* log Z reduction */

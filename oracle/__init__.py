@@ -8,9 +8,9 @@ own Philox generator.
 
 Modules:
   philox  Philox4x32-10 + Box-Muller streams (Salmon et al. 2011).
-  kalman  Kalman filter (Alg. A.1), RTS sampler (Alg. A.2), parallel-filter
+  kalman  Kalman filter and RTS sampler algorithms (Appendix A.1), parallel-filter
           elements and operator (Appendix A.2.1), (G, U) backward scan
-          (Eqs. (A.11)-(A.12), Alg. A.4), Hillis-Steele scan (Alg. A.3).
+          (Eqs. (A.14)-(A.15), Proposition A.1), Hillis-Steele scan (Appendix A.2.1).
   mcmc    one auxiliary Kalman MH step (Alg. 2, first-order, Gaussian
           dynamics) with the direct-formula acceptance ratio.
   dense   brute-force stacked-path Gaussian (Eq. (2.2)) for tiny T·d.

@@ -6,7 +6,7 @@ package; the product path never does. Plain, slow, sequential numpy code:
 one Python loop over time, library solves/Cholesky as single steps.
 
 Model (Appendix A, Eq. (A.1) with H_t = I and c_t = 0, as in the auxiliary
-LGSSM of Section 2.2, Eq. (2.6)):
+LGSSM of Section 2.2, Eq. (2.7)):
 
     x_0 ~ N(m0, P0),  x_t = F_{t-1} x_{t-1} + b_{t-1} + N(0, Q_{t-1}),
     y_t = x_t + N(0, R),           t = 0 .. T-1  (T = number of states).
@@ -16,23 +16,23 @@ F, b, Q may be a single (homogeneous) value or a stack over t = 0 .. T-2
 stack over t.
 
 Functions and the passages they follow:
-  kalman_filter      Kalman filter, Algorithm A.1 (Appendix A.1), with the
+  kalman_filter      the Kalman filter algorithm (Appendix A.1, Eqs. (A.3)-(A.6)), with the
                      predictive likelihood terms N(y_t; m^p_t, P^p_t + R).
-  rts_sample         Rauch-Tung-Striebel sampler, Algorithm A.2.
+  rts_sample         the Rauch-Tung-Striebel sampler algorithm (Appendix A.1, Eq. (A.10)).
   rts_smoother       marginal smoother means/covariances (same recursion,
                      Appendix A.1), used for stationarity checks.
   filter_elements,   the per-step conditional-Gaussian elements and their
   filter_combine     associative operator of the parallel Kalman filter
-                     (Appendix A.2.1, Eqs. (A.9)-(A.10); element formulas of
+                     (Appendix A.2.1, Eqs. (A.12)-(A.13); element formulas of
                      the cited Sarkka & Garcia-Fernandez construction).
                      parity unpinned by a printed value: pinned by equality
                      with kalman_filter under sequential and Hillis-Steele
                      scans.
   sequential_scan,   prefix scans over any associative operator; the second
-  hillis_steele_scan is Algorithm A.3.
+  hillis_steele_scan is the Hillis-Steele algorithm of Appendix A.2.1.
   backward_elements, (G_t, U_t) elements and operator of the parallel RTS
-  backward_combine,  sampler, Eqs. (A.11)-(A.12), Proposition A.1 and
-  suffix_scan        Algorithm A.4.
+  backward_combine,  sampler, Eqs. (A.14)-(A.15), Proposition A.1 and the
+  suffix_scan        parallel RTS sampler algorithm (Appendix A.2.2).
 """
 import numpy as np
 
@@ -54,7 +54,7 @@ def mvn_logpdf(x, mean, cov):
 
 
 def kalman_filter(y, m0, P0, F, b, Q, R):
-    """Algorithm A.1 with H = I.
+    """The Kalman filter algorithm of Appendix A.1 with H = I.
 
     Returns a dict with mf, Pf (filtered), mp, Pp (predicted; mp[0]=m0,
     Pp[0]=P0), ell (per-step predictive log-likelihood terms) and logZ.
@@ -83,7 +83,7 @@ def kalman_filter(y, m0, P0, F, b, Q, R):
 
 
 def rts_sample(kf, F, b, Q, eps):
-    """Algorithm A.2 driven by given standard normals eps [T, d].
+    """The RTS sampler algorithm of Appendix A.1 driven by given standard normals eps [T, d].
 
     x_{T-1} = m^f + chol(P^f) eps_{T-1}; for t < T-1
     x_t = m^f_t + G_t (x_{t+1} - m^p_{t+1}) + chol(P^f_t - G_t P^p_{t+1} G_t^T) eps_t,
@@ -179,7 +179,7 @@ def sequential_scan(elems, op):
 
 
 def hillis_steele_scan(elems, op):
-    """Algorithm A.3: log2 T rounds of out_t <- out_{t-2^k} op out_t."""
+    """Hillis-Steele algorithm (Appendix A.2.1): log2 T rounds of out_t <- out_{t-2^k} op out_t."""
     out = list(elems)
     T = len(out)
     k = 1
@@ -194,7 +194,7 @@ def hillis_steele_scan(elems, op):
 # ---------------------------------------------------------------------------
 
 def backward_elements(kf, F, b, Q, eps):
-    """(G_t, U_t) of Eq. (A.11): U_t = m^f_t - G_t (F_t m^f_t + b_t) + chol(Sigma_t) eps_t,
+    """(G_t, U_t) of Eq. (A.14): U_t = m^f_t - G_t (F_t m^f_t + b_t) + chol(Sigma_t) eps_t,
     Sigma_t = P^f_t - G_t (F_t P^f_t F_t^T + Q_t) G_t^T; G_{T-1} = 0 and
     U_{T-1} = m^f_{T-1} + chol(P^f_{T-1}) eps_{T-1}."""
     mf, Pf = kf["mf"], kf["Pf"]

@@ -12,8 +12,8 @@ Target (Section 2.2, Eq. (2.5) and the augmented target Eq. (2.6)):
 One step (Algorithm 2 with Gaussian dynamics, so F, b, Q are the model's):
   1. u_t = x_t + sqrt(delta/2) eps_t                 (first line of Alg. 2)
   2. v_t = grad_{x_t} gamma(x);  ytilde_t = u_t + (delta/2) v_t   (Eq. (2.7))
-  3. x* ~ q(. | u, x): Kalman filter (Alg. A.1) on ytilde with R = (delta/2) I,
-     then the RTS sampler (Alg. A.2) with the backward noise.
+  3. x* ~ q(. | u, x): Kalman filter (Appendix A.1) on ytilde with R = (delta/2) I,
+     then the RTS sampler (Appendix A.1) with the backward noise.
   4. v*, ytilde* from x*; the Kalman filter on ytilde* gives log p(ytilde*).
   5. log alpha = log pi(x*, u) + log q(x | u, x*) - log pi(x, u) - log q(x* | u, x)
      (the MRTH line of Alg. 2), with the smoothing density of each proposal
@@ -26,9 +26,9 @@ One step (Algorithm 2 with Gaussian dynamics, so F, b, Q are the model's):
 
 Emission models (gamma and its gradient):
   linear-Gaussian  log h(y|x) = log N(y; x, R_y)           (Appendix A, Eq. (A.1))
-  stochastic vol.  log h(y|x) = sum_i log N(y_i; 0, exp(x_i))  (Section 5.1)
+  stochastic vol.  log h(y|x) = sum_i log N(y_i; 0, exp(x_i))  (Section 4.1)
 An optional observation mask switches gamma_t off (gamma_t = 0, v_t = 0) at
-unobserved steps, as in the two-step model of Section 5.4.
+unobserved steps, as in the two-step model of Section 4.4.
 """
 import numpy as np
 

@@ -36,7 +36,7 @@ MASK32 = 0xFFFFFFFF
 
 # stream purposes (the ``purpose`` field of the counter)
 PURPOSE_AUX = 0        # u_t = x_t + sqrt(delta/2) * eps_t          (Alg. 2, first line)
-PURPOSE_BACKWARD = 1   # noise of U_t in the backward sampler        (Alg. A.4)
+PURPOSE_BACKWARD = 1   # noise of U_t in the backward sampler        (Appendix A.2.2)
 PURPOSE_MH = 2         # the uniform of the Metropolis-Hastings test (Alg. 2, MRTH line)
 
 

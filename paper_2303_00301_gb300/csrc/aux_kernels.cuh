@@ -8,11 +8,11 @@
 //                        (Appendix A.2.1): each block of L steps is reduced
 //                        with the operator (k_filter_reduce), the block
 //                        aggregates are scanned with Hillis-Steele rounds
-//                        (Algorithm A.3, k_filter_scan_level), and each block
+//                        (the Hillis-Steele algorithm of Appendix A.2.1, k_filter_scan_level), and each block
 //                        then applies its elements in order from the incoming
 //                        prefix (k_filter_apply), which also emits the
-//                        predictive log-likelihood terms (Algorithm A.1) and
-//                        the backward elements (G_t, U_t) of Eq. (A.11).
+//                        predictive log-likelihood terms (Kalman filter algorithm, Appendix A.1) and
+//                        the backward elements (G_t, U_t) of Eq. (A.14).
 //   backward scan        the (G, U) suffix scan of Proposition A.1, blocked the
 //                        same way (block aggregates are built in k_filter_apply,
 //                        k_sample_backward applies them), fused with the
@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::RED_WPC, 1)
 
 // ---------------------------------------------------------------------------
 // Phase 2: one Hillis-Steele round over the block aggregates of each chain
-// (Algorithm A.3): out_k = in_{k-off} (x) in_k for k >= off, else out_k = in_k.
+// (Hillis-Steele algorithm, Appendix A.2.1): out_k = in_{k-off} (x) in_k for k >= off, else out_k = in_k.
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32 * Sizes<Real, DP>::SCAN_WPC, 1)
@@ -610,8 +610,8 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::SCAN_WPC, 1)
 // ---------------------------------------------------------------------------
 // Phase 3: per block, apply the elements in order from the incoming prefix
 // (a marginal N(m^f_{s-1}, P^f_{s-1})): this is the Kalman recursion of
-// Algorithm A.1 on the block, giving m^f_t, P^f_t and the predictive terms.
-// With APPLY_EPI it also forms (G_t, U_t) of Eq. (A.11) and the block's
+// the Kalman filter algorithm (Appendix A.1) on the block, giving m^f_t, P^f_t and the predictive terms.
+// With APPLY_EPI it also forms (G_t, U_t) of Eq. (A.14) and the block's
 // backward aggregate (G_s ... G_e, U_s + G_s U_{s+1} + ...).
 // ---------------------------------------------------------------------------
 template <typename Real> struct ApplyArgs {

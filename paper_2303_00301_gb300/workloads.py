@@ -9,14 +9,14 @@ Models (all with Gaussian dynamics x_t = F x_{t-1} + b + N(0, Q), x_0 ~ N(m0, P0
 * ``linear_gaussian``: F = 0.9 I, Q = 0.1 I, P0 = I, y_t = x_t + N(0, 0.5 I),
   delta = 0.1; d = 2, T = 64, one chain by default. The emission is the
   linear-Gaussian observation model of Appendix A (Eq. (A.1)).
-* ``stochastic_volatility``: the multivariate SV model of Section 5.1 with the
+* ``stochastic_volatility``: the multivariate SV model of Section 4.1 with the
   parameter laws used here: mu = 0, Phi = diag(phi), phi_i ~ U[0.8, 0.99] iid,
   Sigma_ij = 0.5 + 0.5 [i = j] (equicorrelation 0.5, unit variances), p_0 the
   stationary law (P0_ij = Sigma_ij / (1 - phi_i phi_j), closed form since Phi
   is diagonal), y_t(i) = exp(x_t(i) / 2) eta_t(i), eta ~ N(0, 1). The paper's
   SV datasets are simulated from the model itself; this simulation stands in
   for them.
-* ``two_step_toy``: the two-step failure-mode model of Section 5.4:
+* ``two_step_toy``: the two-step failure-mode model of Section 4.4:
   x_0 ~ N(0, 1), x_1 ~ N(rho x_0, 1 - rho^2), one observation y = 5 of x_1
   with variance r^2 (the emission at t = 0 is masked out).
 
@@ -117,7 +117,7 @@ def stochastic_volatility(d=30, T=1024, n_chains=32, sim_seed=0, mcmc_seed=1, de
 
 
 def two_step_toy(rho=0.5, r2=0.1, y_obs=5.0, n_chains=1, delta=0.5, mcmc_seed=1):
-    """Section 5.4 model; exact posterior of x_0: mean rho y/(1+r2), var 1 - rho^2/(1+r2)."""
+    """Section 4.4 model; exact posterior of x_0: mean rho y/(1+r2), var 1 - rho^2/(1+r2)."""
     m0 = np.zeros(1); P0 = np.eye(1)
     F = np.array([[rho]]); b = np.zeros(1); Q = np.array([[1.0 - rho ** 2]])
     y = np.array([[0.0], [y_obs]])

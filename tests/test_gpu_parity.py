@@ -229,7 +229,7 @@ def test_nonfinite_state_is_rejected_and_reported():
 
 
 def test_two_step_toy_posterior_on_gpu():
-    """Section 5.4 model: the ensemble of many chains matches the closed-form posterior of x_0."""
+    """Section 4.4 model: the ensemble of many chains matches the closed-form posterior of x_0."""
     rho, r2, y = 0.8, 0.5, 2.0
     C = 512
     wl = workloads.two_step_toy(rho=rho, r2=r2, y_obs=y, n_chains=C, delta=1.0, mcmc_seed=3)

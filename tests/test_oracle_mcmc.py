@@ -77,7 +77,7 @@ def test_reject_keeps_state_accept_moves():
 
 
 def test_two_step_toy_posterior_closed_form():
-    """Section 5.4 model: E[x0|y] = rho y / (1 + r^2), Var = 1 - rho^2 / (1 + r^2)."""
+    """Section 4.4 model: E[x0|y] = rho y / (1 + r^2), Var = 1 - rho^2 / (1 + r^2)."""
     rho, r2, y = 0.6, 0.3, 5.0
     wl = workloads.two_step_toy(rho=rho, r2=r2, y_obs=y)
     mbar, C = dense.prior_moments(wl.m0, wl.P0, wl.F, wl.b, wl.Q, 2)
