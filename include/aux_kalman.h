@@ -136,7 +136,7 @@ int aux_get_status(aux_model *m, int32_t *per_chain_status);
 
 /* Kernel kinds reported by aux_read_profile. */
 #define AUX_PROFILE_LINEARISE 0  /* v, u, ytilde at the current state (Eq. (2.7)) */
-#define AUX_PROFILE_TEMPLATE  1  /* model-derived matrix parts of the filtering elements */
+#define AUX_PROFILE_TEMPLATE  1  /* reserved (no kernel of this kind is launched) */
 #define AUX_PROFILE_REDUCE    2  /* block aggregates of the filtering elements (Appendix A.2.1) */
 #define AUX_PROFILE_SCAN      3  /* one Hillis-Steele round over block aggregates (Appendix A.2.1) */
 #define AUX_PROFILE_APPLY     4  /* in-block filtering from the block prefix + (G_t, U_t) (Eq. (A.14)) */

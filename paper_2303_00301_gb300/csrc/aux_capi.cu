@@ -233,7 +233,6 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
   if (!rc) rc = dev_alloc(m, &m->G, (size_t)C * T * DP * DP * es);
   if (!rc) rc = dev_alloc(m, &m->U, (size_t)C * T * DP * es);
   if (!rc) rc = dev_alloc(m, &m->gu, nbC * aux_gs(DP) * es);
-  if (!rc) rc = dev_alloc(m, &m->tmpl, (size_t)7 * DP * DP * es);
   if (!rc) rc = dev_alloc(m, (void**)&m->fq, (size_t)C * T * sizeof(double));
   if (!rc) rc = dev_alloc(m, (void**)&m->fld, (size_t)C * T * sizeof(double));
   if (!rc) rc = dev_alloc(m, (void**)&m->mh_part, nbC * sizeof(double));

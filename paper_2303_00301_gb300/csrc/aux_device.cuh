@@ -268,6 +268,237 @@ __device__ __forceinline__ void bwd_subst(const T* LT, const T* inv_diag, const 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Rolled primitives. Only the inner index j (a register-array index) is
+// unrolled; the k loops run as real loops so that the code of a p = 32 kernel
+// stays inside the instruction cache. The left operand of a product is read
+// from shared memory (a contiguous row, or a column of a slot).
+// ---------------------------------------------------------------------------
+
+// out[j] (+/-)= sum_k arow[k] * B[k][j]       (arow: 16-byte aligned shared row)
+template <typename T, int DP, bool ACC = false, bool NEG = false>
+__device__ __forceinline__ void mm_row(const T* arow, const T* B, T (&out)[DP]) {
+  using V = typename Vec16<T>::V;
+  constexpr int N = Vec16<T>::N, LD = Lay<T, DP>::LD;
+  if (!ACC) zero<T, DP>(out);
+#pragma unroll 1
+  for (int k0 = 0; k0 < DP; k0 += N) {
+    T a[N];
+    unpack<T>(*reinterpret_cast<const V*>(arow + k0), a);
+#pragma unroll
+    for (int kk = 0; kk < N; ++kk) {
+      const T ak = NEG ? -a[kk] : a[kk];
+      T b[DP];
+      ld_vec<T, DP>(B + (k0 + kk) * LD, b);
+#pragma unroll
+      for (int j = 0; j < DP; ++j) out[j] = fma(ak, b[j], out[j]);
+    }
+  }
+}
+
+// out[j] (+/-)= sum_k A[k][col] * B[k][j]     (left operand: column `col` of slot A)
+template <typename T, int DP, bool ACC = false, bool NEG = false>
+__device__ __forceinline__ void mm_col(const T* A, int col, const T* B, T (&out)[DP]) {
+  constexpr int N = Vec16<T>::N, LD = Lay<T, DP>::LD;
+  if (!ACC) zero<T, DP>(out);
+#pragma unroll 1
+  for (int k0 = 0; k0 < DP; k0 += N) {
+#pragma unroll
+    for (int kk = 0; kk < N; ++kk) {
+      const T a = A[(k0 + kk) * LD + col];
+      const T ak = NEG ? -a : a;
+      T b[DP];
+      ld_vec<T, DP>(B + (k0 + kk) * LD, b);
+#pragma unroll
+      for (int j = 0; j < DP; ++j) out[j] = fma(ak, b[j], out[j]);
+    }
+  }
+}
+
+// sum_k arow[k] v[k] and sum_k A[k][col] v[k] (v: shared vector, broadcast)
+template <typename T, int DP>
+__device__ __forceinline__ T dot_row_vec(const T* arow, const T* v) {
+  T a[DP], b[DP];
+  ld_vec<T, DP>(arow, a);
+  ld_vec<T, DP>(v, b);
+  return dot_rr<T, DP>(a, b);
+}
+template <typename T, int DP>
+__device__ __forceinline__ T dot_col_vec(const T* A, int col, const T* v) {
+  T a[DP], b[DP];
+  ld_col<T, DP>(A, col, a);
+  ld_vec<T, DP>(v, b);
+  return dot_rr<T, DP>(a, b);
+}
+
+// Cholesky in "rotating" form. Lane i passes row i of the SPD matrix in a[]
+// (consumed). Before step k, a[j] holds the updated entry (i, k + j), so the
+// pivot column is always a[0] and the update shifts the row down by one:
+// a[j] <- a[j+1] - l_ik L[k+1+j][k]. Outputs:
+//   LS   (required, also the working slot): LS[k][m] = L[k+m][k] (row k of L^T
+//        starting at the diagonal), used by fsolve_rot;
+//   LRow (optional): L row-major;  LR (optional): LR[i][m] = L[i][i-(DP-1)+m]
+//        (row i right-aligned, zeros on the left), used by bsolve_rot;
+//   inv_diag[k] = 1 / L[k][k];  returns sum_k L[lane][k] eps[k] when eps != null.
+// Indices k >= d get a unit pivot; a non-positive or non-finite pivot below d
+// sets *bad and is replaced by 1.
+template <typename T, int DP>
+__device__ T chol_rot(T (&a)[DP], T* LS, T* LRow, T* LR, T* inv_diag, const T* eps, int d,
+                      int lane, int* bad) {
+  constexpr int LD = Lay<T, DP>::LD;
+  const bool act = lane < DP;
+  T acc = 0;
+  __syncwarp();
+  if (LR && act) {
+    T z[DP];
+    zero<T, DP>(z);
+    st_vec<T, DP>(LR + lane * LD, z);
+  }
+  if (LRow && act) {
+    T z[DP];
+    zero<T, DP>(z);
+    st_vec<T, DP>(LRow + lane * LD, z);
+  }
+  __syncwarp();
+#pragma unroll 1
+  for (int k = 0; k < DP; ++k) {
+    T akk = __shfl_sync(FULL_MASK, a[0], k);
+    T piv = (T)1;
+    if (k < d) {
+      if (!(akk > (T)0) || !(akk < (T)INFINITY)) { *bad = 1; akk = (T)1; }
+      piv = sqrt(akk);
+    }
+    const T inv = (T)1 / piv;
+    const T l = (lane == k) ? piv : ((lane > k) ? a[0] * inv : (T)0);
+    if (act && lane >= k) {
+      LS[k * LD + (lane - k)] = l;
+      if (LRow) LRow[lane * LD + k] = l;
+      if (LR) LR[lane * LD + (DP - 1) - (lane - k)] = l;
+    }
+    if (lane == 0) inv_diag[k] = inv;
+    if (eps) acc = fma(l, eps[k], acc);
+    __syncwarp();
+    T lk[DP];
+    ld_vec<T, DP>(LS + k * LD, lk);
+    const T nl = -l;
+#pragma unroll
+    for (int j = 0; j < DP - 1; ++j) a[j] = fma(nl, lk[j + 1], a[j + 1]);
+    a[DP - 1] = (T)0;
+  }
+  __syncwarp();
+  return acc;
+}
+
+// Two independent factorizations interleaved (ILP); outputs as in chol_rot.
+template <typename T, int DP>
+__device__ void chol_rot2(T (&a)[DP], T* LS, T* LR, T* invd, T (&b)[DP], T* LS2, T* invd2,
+                          int d, int lane, int* bad) {
+  constexpr int LD = Lay<T, DP>::LD;
+  const bool act = lane < DP;
+  __syncwarp();
+  if (LR && act) {
+    T z[DP];
+    zero<T, DP>(z);
+    st_vec<T, DP>(LR + lane * LD, z);
+  }
+  __syncwarp();
+#pragma unroll 1
+  for (int k = 0; k < DP; ++k) {
+    T akk = __shfl_sync(FULL_MASK, a[0], k);
+    T bkk = __shfl_sync(FULL_MASK, b[0], k);
+    T pa = (T)1, pb = (T)1;
+    if (k < d) {
+      if (!(akk > (T)0) || !(akk < (T)INFINITY)) { *bad = 1; akk = (T)1; }
+      if (!(bkk > (T)0) || !(bkk < (T)INFINITY)) { *bad = 1; bkk = (T)1; }
+      pa = sqrt(akk);
+      pb = sqrt(bkk);
+    }
+    const T ia = (T)1 / pa, ib = (T)1 / pb;
+    const T la = (lane == k) ? pa : ((lane > k) ? a[0] * ia : (T)0);
+    const T lb = (lane == k) ? pb : ((lane > k) ? b[0] * ib : (T)0);
+    if (act && lane >= k) {
+      LS[k * LD + (lane - k)] = la;
+      LS2[k * LD + (lane - k)] = lb;
+      if (LR) LR[lane * LD + (DP - 1) - (lane - k)] = la;
+    }
+    if (lane == 0) { invd[k] = ia; invd2[k] = ib; }
+    __syncwarp();
+    T ka[DP], kb[DP];
+    ld_vec<T, DP>(LS + k * LD, ka);
+    ld_vec<T, DP>(LS2 + k * LD, kb);
+    const T na = -la, nb = -lb;
+#pragma unroll
+    for (int j = 0; j < DP - 1; ++j) {
+      a[j] = fma(na, ka[j + 1], a[j + 1]);
+      b[j] = fma(nb, kb[j + 1], b[j + 1]);
+    }
+    a[DP - 1] = (T)0;
+    b[DP - 1] = (T)0;
+  }
+  __syncwarp();
+}
+
+// Forward solve L y = r for the lane's own r (consumed), rotating form.
+// y is written to slot Y as column `lane` (Y[k][lane]) or as row `lane` (Y[lane][k]).
+template <typename T, int DP, bool AS_COLUMN>
+__device__ __forceinline__ void fsolve_rot(const T* LS, const T* inv_diag, T (&r)[DP], T* Y,
+                                           int lane) {
+  constexpr int LD = Lay<T, DP>::LD;
+  const bool act = lane < DP;
+#pragma unroll 1
+  for (int k = 0; k < DP; ++k) {
+    const T yk = r[0] * inv_diag[k];
+    if (act) {
+      if (AS_COLUMN) Y[k * LD + lane] = yk;
+      else Y[lane * LD + k] = yk;
+    }
+    T lk[DP];
+    ld_vec<T, DP>(LS + k * LD, lk);
+    const T ny = -yk;
+#pragma unroll
+    for (int j = 0; j < DP - 1; ++j) r[j] = fma(ny, lk[j + 1], r[j + 1]);
+    r[DP - 1] = (T)0;
+  }
+}
+
+// Forward solve L y = r with the same r in every lane; y goes to the vector slot yv.
+template <typename T, int DP>
+__device__ __forceinline__ void fsolve_vec(const T* LS, const T* inv_diag, T (&r)[DP], T* yv,
+                                           int lane) {
+  constexpr int LD = Lay<T, DP>::LD;
+#pragma unroll 1
+  for (int k = 0; k < DP; ++k) {
+    const T yk = r[0] * inv_diag[k];
+    if (lane == 0) yv[k] = yk;
+    T lk[DP];
+    ld_vec<T, DP>(LS + k * LD, lk);
+    const T ny = -yk;
+#pragma unroll
+    for (int j = 0; j < DP - 1; ++j) r[j] = fma(ny, lk[j + 1], r[j + 1]);
+    r[DP - 1] = (T)0;
+  }
+}
+
+// Backward solve L^T y = r for the lane's own r (consumed), rotating from the
+// right with the right-aligned rows LR; y is written as row `lane` of slot Y.
+template <typename T, int DP>
+__device__ __forceinline__ void bsolve_rot(const T* LR, const T* inv_diag, T (&r)[DP], T* Y,
+                                           int lane) {
+  constexpr int LD = Lay<T, DP>::LD;
+  const bool act = lane < DP;
+#pragma unroll 1
+  for (int k = DP - 1; k >= 0; --k) {
+    const T yk = r[DP - 1] * inv_diag[k];
+    if (act) Y[lane * LD + k] = yk;
+    T lr[DP];
+    ld_vec<T, DP>(LR + k * LD, lr);
+    const T ny = -yk;
+#pragma unroll
+    for (int m = DP - 1; m >= 1; --m) r[m] = fma(ny, lr[m - 1], r[m - 1]);
+    r[0] = (T)0;
+  }
+}
+
 template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);

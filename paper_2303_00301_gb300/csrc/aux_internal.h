@@ -26,7 +26,6 @@ struct aux_model {
   void *u = nullptr, *v = nullptr, *yt = nullptr, *xs = nullptr, *yts = nullptr;
   void *agg0 = nullptr, *agg1 = nullptr;
   void *G = nullptr, *U = nullptr, *gu = nullptr;
-  void *tmpl = nullptr;      // element template: 7 DP x DP matrices
   double *fq = nullptr, *fld = nullptr, *mh_part = nullptr, *lz_part = nullptr;
   int32_t *status_iter = nullptr, *status = nullptr;
   const AuxOps *ops = nullptr;

@@ -6,7 +6,8 @@
 //                        ytilde_t = u_t + (delta/2) v_t                    (Eq. (2.7))
 //   parallel filter      blocked associative scan of the filtering elements
 //                        (Appendix A.2.1): each block of L steps is reduced
-//                        with the operator (k_filter_reduce), the block
+//                        with the operator (k_filter_reduce, in a form
+//                        specialised to raw elements), the block
 //                        aggregates are scanned with Hillis-Steele rounds
 //                        (the Hillis-Steele algorithm of Appendix A.2.1, k_filter_scan_level), and each block
 //                        then applies its elements in order from the incoming
@@ -61,20 +62,22 @@ template <typename Real, int DP> struct Sizes {
   static constexpr int ES = 3 * DP * DP + 2 * DP;   // global element: A, C, J, b, eta
   static constexpr int GS = DP * DP + DP;           // global backward aggregate: G, U
   static constexpr size_t SMEM_MAX = 227 * 1024;
-  // phase 1
-  static constexpr size_t RED_CTA = (5 * MAT + VEC) * sizeof(Real);
-  static constexpr size_t RED_WARP = (5 * MAT + 9 * VEC) * sizeof(Real);
-  static constexpr int RED_WPC = (SMEM_MAX - RED_CTA) / RED_WARP >= 8 ? 8 : (int)((SMEM_MAX - RED_CTA) / RED_WARP);
-  static constexpr size_t RED_SMEM = RED_CTA + RED_WPC * RED_WARP;
-  // phase 2
-  static constexpr size_t SCAN_WARP = (8 * MAT + 9 * VEC) * sizeof(Real);
-  static constexpr int SCAN_WPC = SMEM_MAX / SCAN_WARP >= 4 ? 4 : (int)(SMEM_MAX / SCAN_WARP);
-  static constexpr size_t SCAN_SMEM = SCAN_WPC * SCAN_WARP;
-  // phase 3
-  static constexpr size_t APP_CTA = (3 * MAT + VEC) * sizeof(Real);
-  static constexpr size_t APP_WARP = (4 * MAT + 7 * VEC) * sizeof(Real);
-  static constexpr int APP_WPC = (SMEM_MAX - APP_CTA) / APP_WARP >= 8 ? 8 : (int)((SMEM_MAX - APP_CTA) / APP_WARP);
-  static constexpr size_t APP_SMEM = APP_CTA + APP_WPC * APP_WARP;
+  static constexpr size_t MODEL = (3 * MAT + VEC) * sizeof(Real);   // F, F^T, Q, b
+  static constexpr int cap(size_t fixed, size_t per_warp, int want) {
+    return (SMEM_MAX - fixed) / per_warp >= (size_t)want ? want : (int)((SMEM_MAX - fixed) / per_warp);
+  }
+  // phase 1: SA SC SX SY SW SL + 5 vectors
+  static constexpr int RED_WARP_ELEMS = 6 * MAT + 5 * VEC;
+  static constexpr int RED_WPC = cap(MODEL, RED_WARP_ELEMS * sizeof(Real), 8);
+  static constexpr size_t RED_SMEM = MODEL + RED_WPC * RED_WARP_ELEMS * sizeof(Real);
+  // phase 2: SA SC SU S2 S3 S4 SAe SCe SJe + 9 vectors
+  static constexpr int SCAN_WARP_ELEMS = 9 * MAT + 9 * VEC;
+  static constexpr int SCAN_WPC = cap(0, SCAN_WARP_ELEMS * sizeof(Real), 8);
+  static constexpr size_t SCAN_SMEM = SCAN_WPC * SCAN_WARP_ELEMS * sizeof(Real);
+  // phase 3: SP SX SL SLR SY SG + 8 vectors
+  static constexpr int APP_WARP_ELEMS = 6 * MAT + 8 * VEC;
+  static constexpr int APP_WPC = cap(MODEL, APP_WARP_ELEMS * sizeof(Real), 8);
+  static constexpr size_t APP_SMEM = MODEL + APP_WPC * APP_WARP_ELEMS * sizeof(Real);
   // backward sampler
   static constexpr int BWD_WPC = 8;
   static constexpr size_t BWD_SMEM = (MAT + BWD_WPC * 3 * VEC) * sizeof(Real);
@@ -116,17 +119,17 @@ __global__ void k_linearise(KP<Real> p, const Real* __restrict__ x, Real* __rest
 }
 
 // ---------------------------------------------------------------------------
-// Element operator a_i (x) a_j (Cholesky form, see header comment).
-// Aggregate i: SA (A), SC (C), jreg (row `lane` of J), vb, veta.
-// Element j:   Ae, Ce, Je slots and vbe, vetae vectors (read only).
-// Scratch: S2, S3, S4 slots, vt (4 vectors), vdiag.
+// Element operator a_i (x) a_j in Cholesky form (see the header comment).
+// Aggregate i: SA (A), SC (C), jreg (row `lane` of J), vb, veta  (in/out).
+// Element j:   SAe, SCe, SJe slots and vbe, vetae vectors (read only).
+// Scratch: SU, S2, S3, S4 slots, vt (4 vectors), vdiag.
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
 __device__ void combine_general(Real* SA, Real* SC, Real (&jreg)[DP], Real* vb, Real* veta,
-                                const Real* Ae, const Real* Ce, const Real* Je,
-                                const Real* vbe, const Real* vetae, Real* S2, Real* S3,
+                                const Real* SAe, const Real* SCe, const Real* SJe,
+                                const Real* vbe, const Real* vetae, Real* SU, Real* S2, Real* S3,
                                 Real* S4, Real* vt, Real* vdiag, int d, int lane, int* bad) {
-  constexpr int VEC = Lay<Real, DP>::VEC;
+  constexpr int VEC = Lay<Real, DP>::VEC, LD = Lay<Real, DP>::LD;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
   Real* vr = vt;
@@ -134,146 +137,105 @@ __device__ void combine_general(Real* SA, Real* SC, Real (&jreg)[DP], Real* vb, 
   Real* vw = vt + 2 * VEC;
   Real* vrq = vt + 3 * VEC;
   __syncwarp();
-  // 1. U = chol(C_i), stored as U^T in SC
+  // 1. U = chol(C_i): rows of U in SU (S2 is the factorisation's working slot)
   {
     Real a[DP];
     ld_row<Real, DP>(SC, row, a);
-    chol_rows<Real, DP>(a, SC, vdiag, d, lane, bad);
+    chol_rot<Real, DP>(a, S2, SU, nullptr, vdiag, nullptr, d, lane, bad);
   }
-  // 2. T1 = J_j U: lane i forms column i of T1, (U^T J_j)_i = (U^T row i) J_j
-  //    (J_j symmetric), and stores it as column i, so S2 holds T1 row-major
-  Real ut[DP];
-  ld_row<Real, DP>(SC, row, ut);
+  // 2. T1 = J_j U -> S3
   {
-    Real t1c[DP];
-    row_mat<Real, DP>(ut, Je, t1c);
-    st_col<Real, DP>(S2, row, t1c, act);
+    Real t1[DP];
+    mm_row<Real, DP>(SJe + row * LD, SU, t1);
+    st_row<Real, DP>(S3, row, t1, act);
   }
   __syncwarp();
-  // 3-4. N = I + U^T T1, L = chol(N) -> L^T in S3
+  // 3-4. N = I + U^T T1 (eigenvalues >= 1); its factor in S4
   {
     Real n[DP];
-    row_mat<Real, DP>(ut, S2, n);
+    mm_col<Real, DP>(SU, row, S3, n);
 #pragma unroll
     for (int j = 0; j < DP; ++j) n[j] += (j == lane) ? (Real)1 : (Real)0;
-    chol_rows<Real, DP>(n, S3, vdiag, d, lane, bad);
+    chol_rot<Real, DP>(n, S4, nullptr, nullptr, vdiag, nullptr, d, lane, bad);
   }
-  // 5. B = U L^{-T}: row i solves L b^T = (row i of U)^T = column i of U^T
+  // 5. B = U L^{-T}: row i solves L b = (row i of U)^T; rows of B in S2
   {
-    Real rhs[DP], bro[DP];
-    ld_col<Real, DP>(SC, row, rhs);
-    fwd_subst<Real, DP>(S3, vdiag, rhs, bro);
-    __syncwarp();
-    st_row<Real, DP>(S2, row, bro, act);
+    Real r[DP];
+    ld_row<Real, DP>(SU, row, r);
+    fsolve_rot<Real, DP, false>(S4, vdiag, r, S2, lane);
   }
   __syncwarp();
-  // 6. P = A_j B, kept transposed in SC (U^T is dead): row i of P is column i of SC
+  // 6. P = A_j B, kept transposed in S3 (T1 is dead): row i of P = column i of S3
   {
-    Real ae[DP], prow[DP];
-    ld_row<Real, DP>(Ae, row, ae);
-    row_mat<Real, DP>(ae, S2, prow);
-    st_col<Real, DP>(SC, row, prow, act);
+    Real pr[DP];
+    mm_row<Real, DP>(SAe + row * LD, S2, pr);
+    __syncwarp();
+    st_col<Real, DP>(S3, row, pr, act);
   }
   // vector parts: r = eta_j - J_j b_i, s = B^T r, b_new, w = B s, rq = r - J_j w
-  Real ri, bnew;
-  {
-    Real je[DP];
-    ld_row<Real, DP>(Je, row, je);
-    ri = vetae[row] - dot_rv<Real, DP>(je, vb);
-  }
+  const Real ri = vetae[row] - dot_row_vec<Real, DP>(SJe + row * LD, vb);
   if (act) vr[lane] = ri;
   __syncwarp();
   {
-    Real bcol[DP];
-    ld_col<Real, DP>(S2, row, bcol);
-    const Real si = dot_rv<Real, DP>(bcol, vr);
+    const Real si = dot_col_vec<Real, DP>(S2, row, vr);
     if (act) vs[lane] = si;
   }
   __syncwarp();
+  const Real bnew = dot_row_vec<Real, DP>(SAe + row * LD, vb) +
+                    dot_col_vec<Real, DP>(S3, row, vs) + vbe[row];
   {
-    Real ae[DP];
-    ld_row<Real, DP>(Ae, row, ae);
-    Real prow[DP];
-    ld_col<Real, DP>(SC, row, prow);
-    bnew = dot_rv<Real, DP>(ae, vb) + dot_rv<Real, DP>(prow, vs) + vbe[row];
-  }
-  {
-    Real bro[DP];
-    ld_row<Real, DP>(S2, row, bro);
-    const Real wi = dot_rv<Real, DP>(bro, vs);
+    const Real wi = dot_row_vec<Real, DP>(S2 + row * LD, vs);
     if (act) vw[lane] = wi;
   }
   __syncwarp();
   {
-    Real je[DP];
-    ld_row<Real, DP>(Je, row, je);
-    const Real rqi = ri - dot_rv<Real, DP>(je, vw);
+    const Real rqi = ri - dot_row_vec<Real, DP>(SJe + row * LD, vw);
     if (act) vrq[lane] = rqi;
   }
-  // 7. X1 = J_j A_i -> S3 (L^T is dead)
+  __syncwarp();
+  const Real etanew = dot_col_vec<Real, DP>(SA, row, vrq) + veta[row];
+  // 7. X1 = J_j A_i -> S4 (the factor of N is dead)
   {
-    Real je[DP], x1[DP];
-    ld_row<Real, DP>(Je, row, je);
-    row_mat<Real, DP>(je, SA, x1);
+    Real x1[DP];
+    mm_row<Real, DP>(SJe + row * LD, SA, x1);
     __syncwarp();
-    st_row<Real, DP>(S3, row, x1, act);
+    st_row<Real, DP>(S4, row, x1, act);
   }
   __syncwarp();
-  // 8. Z = B^T X1 -> S4
+  // 8. Z = B^T X1 -> SU (U is dead)
   {
-    Real bcol[DP], z[DP];
-    ld_col<Real, DP>(S2, row, bcol);
-    row_mat<Real, DP>(bcol, S3, z);
-    st_row<Real, DP>(S4, row, z, act);
+    Real z[DP];
+    mm_col<Real, DP>(S2, row, S4, z);
+    __syncwarp();
+    st_row<Real, DP>(SU, row, z, act);
   }
   __syncwarp();
-  // eta_new and 9. J_new = A_i^T X1 - Z^T Z + J_i (accumulated into jreg; uses the old A_i)
-  Real etanew;
-  {
-    Real acol[DP];
-    ld_col<Real, DP>(SA, row, acol);
-    etanew = dot_rv<Real, DP>(acol, vrq) + veta[row];
-    row_mat<Real, DP, true>(acol, S3, jreg);
-  }
-  {
-    Real zc[DP];
-    ld_col<Real, DP>(S4, row, zc);
-    row_mat<Real, DP, true, true>(zc, S4, jreg);
-  }
-  __syncwarp();   // also keeps the scheduler from interleaving steps 9 and 10
+  // 9. J_new = A_i^T X1 - Z^T Z + J_i
+  mm_col<Real, DP, true>(SA, row, S4, jreg);
+  mm_col<Real, DP, true, true>(SU, row, SU, jreg);
+  __syncwarp();
   // 10. A_new = A_j A_i - P Z -> SA once every lane is done reading A_i
   {
     Real an[DP];
-    {
-      Real ae[DP];
-      ld_row<Real, DP>(Ae, row, ae);
-      row_mat<Real, DP>(ae, SA, an);
-    }
-    {
-      Real prow[DP];
-      ld_col<Real, DP>(SC, row, prow);
-      row_mat<Real, DP, true, true>(prow, S4, an);
-    }
+    mm_row<Real, DP>(SAe + row * LD, SA, an);
+    mm_col<Real, DP, true, true>(S3, row, SU, an);
     __syncwarp();
     st_row<Real, DP>(SA, row, an, act);
   }
-  // 11. C_new = P P^T + C_j (P^T is in SC); J symmetrised through S3
-  st_row<Real, DP>(S3, row, jreg, act);
-  __syncwarp();
+  // 11. C_new = P P^T + C_j -> SC; J symmetrised through S4 (X1 is dead)
   {
     Real cn[DP];
-    {
-      Real prow[DP];
-      ld_col<Real, DP>(SC, row, prow);
-      ld_row<Real, DP>(Ce, row, cn);
-      row_mat<Real, DP, true>(prow, SC, cn);
-    }
-    Real jc[DP];
-    ld_col<Real, DP>(S3, row, jc);
-#pragma unroll
-    for (int j = 0; j < DP; ++j) jreg[j] = (Real)0.5 * (jreg[j] + jc[j]);
+    ld_row<Real, DP>(SCe, row, cn);
+    mm_col<Real, DP, true>(S3, row, S3, cn);
+    st_row<Real, DP>(S4, row, jreg, act);
     __syncwarp();
     st_row<Real, DP>(SC, row, cn, act);
+  }
+  {
+    Real jc[DP];
+    ld_col<Real, DP>(S4, row, jc);
+#pragma unroll
+    for (int j = 0; j < DP; ++j) jreg[j] = (Real)0.5 * (jreg[j] + jc[j]);
   }
   if (act) {
     vb[lane] = bnew;
@@ -282,7 +244,7 @@ __device__ void combine_general(Real* SA, Real* SC, Real (&jreg)[DP], Real* vb, 
   __syncwarp();
 }
 
-// symmetrise a slot in place: S <- (S + S^T) / 2, given own row in r
+// symmetrise a register row through a slot: r <- (r + column of the stored matrix) / 2
 template <typename Real, int DP>
 __device__ __forceinline__ void symmetrise_store(Real* S, Real (&r)[DP], int lane) {
   const bool act = lane < DP;
@@ -295,160 +257,20 @@ __device__ __forceinline__ void symmetrise_store(Real* S, Real (&r)[DP], int lan
 #pragma unroll
   for (int j = 0; j < DP; ++j) r[j] = (Real)0.5 * (r[j] + c[j]);
   __syncwarp();
-  st_row<Real, DP>(S, row, r, act);
-  __syncwarp();
 }
 
-// Matrix parts of the elements (one warp, written to global memory once per
-// filter pass): for t >= 1, S = Q + R, K = Q S^{-1}, H = F^T S^{-1},
-// A_e = F - K F, C_e = Q - K Q, J_e = H F (vector parts b_e = b + K (ytilde_t - b),
-// eta_e = H (ytilde_t - b)); for t = 0, K0 = P0 (P0 + R)^{-1}, C0 = P0 - K0 P0.
-// Layout of the template: [A_e][C_e][J_e][K][H][C0][K0], DP*DP each, row-major.
+// CTA-shared model rows: F, F^T, Q (slots) and b
 template <typename Real, int DP>
-__global__ void __launch_bounds__(32) k_element_template(KP<Real> p, Real* __restrict__ tmpl) {
-  constexpr int MAT = Lay<Real, DP>::MAT, VEC = Lay<Real, DP>::VEC;
-  __shared__ __align__(16) Real W1[MAT], W2[MAT], W3[MAT], vdiag[VEC];
-  const int lane = threadIdx.x & 31;
-  const bool act = lane < DP;
-  const int row = act ? lane : 0;
-  int bad = 0;
-  Real* gAe = tmpl;
-  Real* gCe = gAe + DP * DP;
-  Real* gJe = gCe + DP * DP;
-  Real* gK = gJe + DP * DP;
-  Real* gH = gK + DP * DP;
-  Real* gC0 = gH + DP * DP;
-  Real* gK0 = gC0 + DP * DP;
-  Real q[DP], f[DP];
-  ld_vec<Real, DP>(p.Q + row * DP, q);
-  ld_vec<Real, DP>(p.F + row * DP, f);
-  {
-    Real s_[DP];
-#pragma unroll
-    for (int j = 0; j < DP; ++j) s_[j] = q[j] + ((j == lane && j < p.d) ? p.r : (Real)0);
-    chol_rows<Real, DP>(s_, W1, vdiag, p.d, lane, &bad);
+__device__ __forceinline__ void load_model_slots(const KP<Real>& p, Real* sF, Real* sFT, Real* sQ,
+                                                 Real* sb) {
+  constexpr int LD = Lay<Real, DP>::LD;
+  for (int q = threadIdx.x; q < DP * DP; q += blockDim.x) {
+    const int i = q / DP, j = q % DP;
+    sF[i * LD + j] = p.F[q];
+    sFT[j * LD + i] = p.F[q];
+    sQ[i * LD + j] = p.Q[q];
   }
-  Real kr[DP], hr[DP];
-  {
-    Real rhs[DP], y[DP];
-#pragma unroll
-    for (int j = 0; j < DP; ++j) rhs[j] = q[j];
-    fwd_subst<Real, DP>(W1, vdiag, rhs, y);
-    bwd_subst<Real, DP>(W1, vdiag, y, kr);
-#pragma unroll
-    for (int k = 0; k < DP; ++k) rhs[k] = p.F[k * DP + row];
-    fwd_subst<Real, DP>(W1, vdiag, rhs, y);
-    bwd_subst<Real, DP>(W1, vdiag, y, hr);
-  }
-  if (act) { st_vec<Real, DP>(gK + row * DP, kr); st_vec<Real, DP>(gH + row * DP, hr); }
-  __syncwarp();
-  st_row<Real, DP>(W1, row, f, act);
-  st_row<Real, DP>(W2, row, q, act);
-  __syncwarp();
-  {
-    Real a_[DP];
-#pragma unroll
-    for (int j = 0; j < DP; ++j) a_[j] = f[j];
-    row_mat<Real, DP, true, true>(kr, W1, a_);
-    if (act) st_vec<Real, DP>(gAe + row * DP, a_);
-  }
-  {
-    Real cc[DP];
-#pragma unroll
-    for (int j = 0; j < DP; ++j) cc[j] = q[j];
-    row_mat<Real, DP, true, true>(kr, W2, cc);
-    symmetrise_store<Real, DP>(W3, cc, lane);
-    if (act) st_vec<Real, DP>(gCe + row * DP, cc);
-  }
-  {
-    Real jj[DP];
-    row_mat<Real, DP>(hr, W1, jj);
-    symmetrise_store<Real, DP>(W3, jj, lane);
-    if (act) st_vec<Real, DP>(gJe + row * DP, jj);
-  }
-  // t = 0
-  Real pr[DP];
-  ld_vec<Real, DP>(p.P0 + row * DP, pr);
-  {
-    Real s_[DP];
-#pragma unroll
-    for (int j = 0; j < DP; ++j) s_[j] = pr[j] + ((j == lane && j < p.d) ? p.r : (Real)0);
-    __syncwarp();
-    chol_rows<Real, DP>(s_, W1, vdiag, p.d, lane, &bad);
-  }
-  Real k0[DP];
-  {
-    Real rhs[DP], y[DP];
-#pragma unroll
-    for (int j = 0; j < DP; ++j) rhs[j] = pr[j];
-    fwd_subst<Real, DP>(W1, vdiag, rhs, y);
-    bwd_subst<Real, DP>(W1, vdiag, y, k0);
-  }
-  if (act) st_vec<Real, DP>(gK0 + row * DP, k0);
-  __syncwarp();
-  st_row<Real, DP>(W2, row, pr, act);
-  __syncwarp();
-  {
-    Real cc[DP];
-#pragma unroll
-    for (int j = 0; j < DP; ++j) cc[j] = pr[j];
-    row_mat<Real, DP, true, true>(k0, W2, cc);
-    symmetrise_store<Real, DP>(W3, cc, lane);
-    if (act) st_vec<Real, DP>(gC0 + row * DP, cc);
-  }
-  if (bad && lane < p.C) {
-    for (int c = lane; c < p.C; c += 32) atomicOr(&p.status_iter[c], ST_NOT_PD);
-  }
-}
-
-// vector parts of element t >= 1 into vbe, vetae (uses vr as scratch)
-template <typename Real, int DP>
-__device__ __forceinline__ void element_vectors(const KP<Real>& p, const Real* ytc, int t,
-                                                const Real* tK, const Real* tH, const Real* tb,
-                                                Real* vbe, Real* vetae, Real* vr, int lane) {
-  const bool act = lane < DP;
-  const int row = act ? lane : 0;
-  const Real ri = (lane < p.d) ? ytc[(long)t * p.d + lane] - tb[lane] : (Real)0;
-  __syncwarp();
-  if (act) vr[lane] = ri;
-  __syncwarp();
-  Real kr[DP], hr[DP];
-  ld_row<Real, DP>(tK, row, kr);
-  ld_row<Real, DP>(tH, row, hr);
-  const Real be = tb[row] + dot_rv<Real, DP>(kr, vr);
-  const Real ee = dot_rv<Real, DP>(hr, vr);
-  if (act) {
-    vbe[lane] = be;
-    vetae[lane] = ee;
-  }
-  __syncwarp();
-}
-
-// The t = 0 element: A = 0, J = 0, eta = 0, C = C0, b = m0 + K0 (ytilde_0 - m0).
-template <typename Real, int DP>
-__device__ void element_zero(const KP<Real>& p, const Real* ytc, const Real* gC0, const Real* gK0,
-                             Real* SA, Real* SC, Real (&jreg)[DP], Real* vb, Real* veta, Real* vr,
-                             int lane) {
-  const bool act = lane < DP;
-  const int row = act ? lane : 0;
-  Real r[DP];
-  ld_vec<Real, DP>(gC0 + row * DP, r);
-  st_row<Real, DP>(SC, row, r, act);
-  zero<Real, DP>(r);
-  st_row<Real, DP>(SA, row, r, act);
-#pragma unroll
-  for (int j = 0; j < DP; ++j) jreg[j] = (Real)0;
-  const Real ri = (lane < p.d) ? ytc[lane] - p.m0[lane] : (Real)0;
-  __syncwarp();
-  if (act) vr[lane] = ri;
-  __syncwarp();
-  ld_vec<Real, DP>(gK0 + row * DP, r);
-  const Real b0 = p.m0[row] + dot_rv<Real, DP>(r, vr);
-  if (act) {
-    vb[lane] = b0;
-    veta[lane] = (Real)0;
-  }
-  __syncwarp();
+  if (threadIdx.x < DP) sb[threadIdx.x] = p.b[threadIdx.x];
 }
 
 // global element <-> warp slots
@@ -490,64 +312,138 @@ __device__ __forceinline__ void load_element(const Real* g, Real* SA, Real* SC, 
 
 // ---------------------------------------------------------------------------
 // Phase 1: block aggregates a_s (x) ... (x) a_e, one warp per (chain, block).
+// Applying the operator to a raw element a_t (t >= 1) is the Kalman recursion
+// conditional on the block's entry state x_{s-1}: with the aggregate
+// (A, b, C, eta, J) so far,
+//   P^p = F C F^T + Q,  m^p = F b + b_dyn,  S = P^p + R = L L^T,
+//   Y = L^{-1} P^p,  W = L^{-1} F A,  z = L^{-1} (ytilde_t - m^p),
+//   C <- P^p - Y^T Y,  A <- F A - Y^T W,  b <- m^p + Y^T z,
+//   J <- J + W^T W,    eta <- eta + W^T z,
+// starting from the identity (A = I, b = 0, C = 0, eta = 0, J = 0) so that the
+// first step reproduces a_s itself; block 0 starts from the prior (t = 0 uses
+// P^p = P0, m^p = m0, A = 0). One Cholesky factorisation per step.
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32 * Sizes<Real, DP>::RED_WPC, 1)
-    k_filter_reduce(KP<Real> p, const Real* __restrict__ tmpl, const Real* __restrict__ yt,
-                    Real* __restrict__ agg) {
+    k_filter_reduce(KP<Real> p, const Real* __restrict__ yt, Real* __restrict__ agg) {
   using Z = Sizes<Real, DP>;
-  constexpr int MAT = Z::MAT, VEC = Z::VEC;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
-  Real* tAe = sm;
-  Real* tCe = tAe + MAT;
-  Real* tJe = tCe + MAT;
-  Real* tK = tJe + MAT;
-  Real* tH = tK + MAT;
-  Real* tb = tH + MAT;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  Real* SA = tb + VEC + warp * (5 * MAT + 9 * VEC);
-  Real* SC = SA + MAT;
-  Real* S2 = SC + MAT;
-  Real* S3 = S2 + MAT;
-  Real* S4 = S3 + MAT;
-  Real* vb = S4 + MAT;
-  Real* veta = vb + VEC;
-  Real* vbe = veta + VEC;
-  Real* vetae = vbe + VEC;
-  Real* vt = vetae + VEC;
-  Real* vdiag = vt + 4 * VEC;
-  int bad = 0;
-  for (int q = threadIdx.x; q < 5 * DP * DP; q += blockDim.x) {
-    const int m = q / (DP * DP), rr = (q / DP) % DP, cc = q % DP;
-    tAe[m * MAT + rr * Lay<Real, DP>::LD + cc] = tmpl[q];
-  }
-  if (threadIdx.x < DP) tb[threadIdx.x] = p.b[threadIdx.x];
+  Real* sF = sm;
+  Real* sFT = sF + MAT;
+  Real* sQ = sFT + MAT;
+  Real* sb = sQ + MAT;
+  load_model_slots<Real, DP>(p, sF, sFT, sQ, sb);
   __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.x * Z::RED_WPC + warp;
   if (item >= p.C * p.nb) return;
   const int c = item / p.nb, k = item % p.nb;
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
-  const Real* ytc = yt + (long)c * p.nT * p.d;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
+  Real* SA = sb + VEC + warp * Z::RED_WARP_ELEMS;
+  Real* SC = SA + MAT;
+  Real* SX = SC + MAT;
+  Real* SY = SX + MAT;
+  Real* SW = SY + MAT;
+  Real* SL = SW + MAT;
+  Real* vb = SL + MAT;
+  Real* veta = vb + VEC;
+  Real* vr = veta + VEC;
+  Real* vz = vr + VEC;
+  Real* vdiag = vz + VEC;
+  const Real* ytc = yt + (long)c * p.nT * p.d;
+  int bad = 0;
   Real jreg[DP];
-  if (k == 0) {
-    element_zero<Real, DP>(p, ytc, tmpl + 5 * DP * DP, tmpl + 6 * DP * DP, SA, SC, jreg, vb, veta,
-                           vt, lane);
-  } else {
+  zero<Real, DP>(jreg);
+  {
     Real r[DP];
-    ld_row<Real, DP>(tAe, row, r);
+#pragma unroll
+    for (int j = 0; j < DP; ++j) r[j] = (k > 0 && j == lane) ? (Real)1 : (Real)0;
     st_row<Real, DP>(SA, row, r, act);
-    ld_row<Real, DP>(tCe, row, r);
+    zero<Real, DP>(r);
     st_row<Real, DP>(SC, row, r, act);
-    ld_row<Real, DP>(tJe, row, jreg);
-    element_vectors<Real, DP>(p, ytc, s, tK, tH, tb, vb, veta, vt, lane);
+    if (act) { vb[lane] = (Real)0; veta[lane] = (Real)0; }
   }
-  for (int t = s + 1; t <= e; ++t) {
-    element_vectors<Real, DP>(p, ytc, t, tK, tH, tb, vbe, vetae, vt, lane);
-    combine_general<Real, DP>(SA, SC, jreg, vb, veta, tAe, tCe, tJe, vbe, vetae, S2, S3, S4, vt,
-                              vdiag, p.d, lane, &bad);
+  __syncwarp();
+  for (int t = s; t <= e; ++t) {
+    Real pprow[DP];
+    Real mpi;
+    if (t == 0) {
+      ld_vec<Real, DP>(p.P0 + row * DP, pprow);
+      mpi = p.m0[row];
+      Real z0[DP];
+      zero<Real, DP>(z0);
+      st_row<Real, DP>(SX, row, z0, act);          // F A = 0 for the prior
+    } else {
+      Real xr[DP];
+      mm_row<Real, DP>(sF + row * LD, SC, xr);      // X = F C
+      __syncwarp();
+      st_row<Real, DP>(SX, row, xr, act);
+      __syncwarp();
+      mm_row<Real, DP>(SX + row * LD, sFT, pprow);  // P^p = X F^T + Q
+      Real qr[DP];
+      ld_row<Real, DP>(sQ, row, qr);
+#pragma unroll
+      for (int j = 0; j < DP; ++j) pprow[j] += qr[j];
+      symmetrise_store<Real, DP>(SY, pprow, lane);
+      mpi = dot_row_vec<Real, DP>(sF + row * LD, vb) + sb[row];
+      Real fa[DP];
+      mm_row<Real, DP>(sF + row * LD, SA, fa);      // F A
+      __syncwarp();
+      st_row<Real, DP>(SX, row, fa, act);
+    }
+    __syncwarp();
+    {
+      Real s_[DP];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) s_[j] = pprow[j] + ((j == lane && j < p.d) ? p.r : (Real)0);
+      chol_rot<Real, DP>(s_, SL, nullptr, nullptr, vdiag, nullptr, p.d, lane, &bad);
+    }
+    const Real rres = (lane < p.d) ? ytc[(long)t * p.d + lane] - mpi : (Real)0;
+    if (act) vr[lane] = rres;
+    __syncwarp();
+    {
+      Real rr[DP];
+      ld_vec<Real, DP>(vr, rr);
+      fsolve_vec<Real, DP>(SL, vdiag, rr, vz, lane);
+    }
+    {
+      Real rr[DP];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) rr[j] = pprow[j];
+      fsolve_rot<Real, DP, true>(SL, vdiag, rr, SY, lane);   // Y as columns
+    }
+    {
+      Real rr[DP];
+      ld_col<Real, DP>(SX, row, rr);
+      fsolve_rot<Real, DP, true>(SL, vdiag, rr, SW, lane);   // W as columns
+    }
+    __syncwarp();
+    {
+      Real cn[DP];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) cn[j] = pprow[j];
+      mm_col<Real, DP, true, true>(SY, row, SY, cn);
+      st_row<Real, DP>(SC, row, cn, act);
+    }
+    {
+      Real an[DP];
+      ld_row<Real, DP>(SX, row, an);
+      mm_col<Real, DP, true, true>(SY, row, SW, an);
+      st_row<Real, DP>(SA, row, an, act);
+    }
+    mm_col<Real, DP, true>(SW, row, SW, jreg);
+    const Real bnew = mpi + dot_col_vec<Real, DP>(SY, row, vz);
+    const Real etanew = veta[row] + dot_col_vec<Real, DP>(SW, row, vz);
+    __syncwarp();
+    if (act) {
+      vb[lane] = bnew;
+      veta[lane] = etanew;
+    }
+    __syncwarp();
   }
   store_element<Real, DP>(agg + (long)item * Z::ES, SA, SC, jreg, vb, veta, lane);
   if (bad && lane == 0) atomicOr(&p.status_iter[c], ST_NOT_PD);
@@ -555,7 +451,8 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::RED_WPC, 1)
 
 // ---------------------------------------------------------------------------
 // Phase 2: one Hillis-Steele round over the block aggregates of each chain
-// (Hillis-Steele algorithm, Appendix A.2.1): out_k = in_{k-off} (x) in_k for k >= off, else out_k = in_k.
+// (the prefix-sum algorithm of Appendix A.2.1):
+// out_k = in_{k-off} (x) in_k for k >= off, else out_k = in_k.
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32 * Sizes<Real, DP>::SCAN_WPC, 1)
@@ -581,9 +478,10 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::SCAN_WPC, 1)
     }
     return;
   }
-  Real* SA = sm + warp * (8 * MAT + 9 * VEC);
+  Real* SA = sm + warp * Z::SCAN_WARP_ELEMS;
   Real* SC = SA + MAT;
-  Real* S2 = SC + MAT;
+  Real* SU = SC + MAT;
+  Real* S2 = SU + MAT;
   Real* S3 = S2 + MAT;
   Real* S4 = S3 + MAT;
   Real* SAe = S4 + MAT;
@@ -601,7 +499,7 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::SCAN_WPC, 1)
   load_element<Real, DP>(g_in, SAe, SCe, je, vbe, vetae, lane);
   st_row<Real, DP>(SJe, row, je, act);
   __syncwarp();
-  combine_general<Real, DP>(SA, SC, jreg, vb, veta, SAe, SCe, SJe, vbe, vetae, S2, S3, S4, vt,
+  combine_general<Real, DP>(SA, SC, jreg, vb, veta, SAe, SCe, SJe, vbe, vetae, SU, S2, S3, S4, vt,
                             vdiag, p.d, lane, &bad);
   store_element<Real, DP>(g_out, SA, SC, jreg, vb, veta, lane);
   if (bad && lane == 0) atomicOr(&p.status_iter[c], ST_NOT_PD);
@@ -609,10 +507,12 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::SCAN_WPC, 1)
 
 // ---------------------------------------------------------------------------
 // Phase 3: per block, apply the elements in order from the incoming prefix
-// (a marginal N(m^f_{s-1}, P^f_{s-1})): this is the Kalman recursion of
-// the Kalman filter algorithm (Appendix A.1) on the block, giving m^f_t, P^f_t and the predictive terms.
+// (a marginal N(m^f_{s-1}, P^f_{s-1})): the Kalman filter algorithm of
+// Appendix A.1 on the block, giving m^f_t, P^f_t and the predictive terms.
 // With APPLY_EPI it also forms (G_t, U_t) of Eq. (A.14) and the block's
-// backward aggregate (G_s ... G_e, U_s + G_s U_{s+1} + ...).
+// backward aggregate (G_s ... G_e, U_s + G_s U_{s+1} + ...). The predicted
+// covariance P^p_{t+1} is factorised once for both uses (G_t needs its
+// factor, the update at t+1 needs that of P^p_{t+1} + R): a dual Cholesky.
 // ---------------------------------------------------------------------------
 template <typename Real> struct ApplyArgs {
   const Real* yt;
@@ -634,37 +534,36 @@ template <typename Real, int DP>
 __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
     k_filter_apply(KP<Real> p, ApplyArgs<Real> a) {
   using Z = Sizes<Real, DP>;
-  constexpr int MAT = Z::MAT, VEC = Z::VEC;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
   Real* sF = sm;
   Real* sFT = sF + MAT;
   Real* sQ = sFT + MAT;
   Real* sb = sQ + MAT;
+  load_model_slots<Real, DP>(p, sF, sFT, sQ, sb);
+  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
-  for (int q = threadIdx.x; q < DP * DP; q += blockDim.x) {
-    sF[(q / DP) * Lay<Real, DP>::LD + q % DP] = p.F[q];
-    sFT[(q % DP) * Lay<Real, DP>::LD + q / DP] = p.F[q];
-    sQ[(q / DP) * Lay<Real, DP>::LD + q % DP] = p.Q[q];
-  }
-  if (threadIdx.x < DP) sb[threadIdx.x] = p.b[threadIdx.x];
-  __syncthreads();
   const int item = blockIdx.x * Z::APP_WPC + warp;
   if (item >= p.C * p.nb) return;
   const int c = item / p.nb, k = item % p.nb;
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
-  Real* SP = sb + VEC + warp * (4 * MAT + 7 * VEC);
+  Real* SP = sb + VEC + warp * Z::APP_WARP_ELEMS;
   Real* SX = SP + MAT;
   Real* SL = SX + MAT;
-  Real* SY = SL + MAT;
-  Real* vm = SY + MAT;
+  Real* SLR = SL + MAT;
+  Real* SY = SLR + MAT;
+  Real* SG = SY + MAT;
+  Real* vm = SG + MAT;
   Real* vmp = vm + VEC;
   Real* vr = vmp + VEC;
-  Real* veps = vr + VEC;
+  Real* vz = vr + VEC;
+  Real* veps = vz + VEC;
   Real* vU = veps + VEC;
-  Real* vdiag = vU + VEC;
+  Real* vdA = vU + VEC;
+  Real* vdB = vdA + VEC;
   const Real* ytc = a.yt + (long)c * p.nT * p.d;
   const bool epi = a.flags & APPLY_EPI;
   int bad = 0;
@@ -678,39 +577,19 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
 
   // X = F P^f (slot SX), P^p = X F^T + Q (symmetrised, pprow), m^p = F m^f + b (vmp)
   auto predict = [&]() {
-    Real fr[DP], xr[DP];
-    ld_row<Real, DP>(sF, row, fr);
-    row_mat<Real, DP>(fr, SP, xr);
-    const Real mpi = dot_rv<Real, DP>(fr, vm) + sb[row];
+    Real xr[DP];
+    mm_row<Real, DP>(sF + row * LD, SP, xr);
+    const Real mpi = dot_row_vec<Real, DP>(sF + row * LD, vm) + sb[row];
     __syncwarp();
     st_row<Real, DP>(SX, row, xr, act);
     if (act) vmp[lane] = mpi;
     __syncwarp();
-    row_mat<Real, DP>(xr, sFT, pprow);
+    mm_row<Real, DP>(SX + row * LD, sFT, pprow);
     Real qr[DP];
     ld_row<Real, DP>(sQ, row, qr);
 #pragma unroll
     for (int j = 0; j < DP; ++j) pprow[j] += qr[j];
     symmetrise_store<Real, DP>(SY, pprow, lane);
-  };
-
-  auto store_backward = [&](int t, const Real (&grow)[DP], Real ui) {
-    Real* Gt = a.G + ((long)c * p.nT + t) * DP * DP;
-    if (act) {
-      st_vec<Real, DP>(Gt + row * DP, grow);
-      a.U[((long)c * p.nT + t) * DP + lane] = ui;
-    }
-    __syncwarp();
-    if (act) vU[lane] = ui;
-    __syncwarp();
-    uhat += dot_rv<Real, DP>(ghat, vU);
-    st_row<Real, DP>(SY, row, grow, act);
-    __syncwarp();
-    Real gn[DP];
-    row_mat<Real, DP>(ghat, SY, gn);
-#pragma unroll
-    for (int j = 0; j < DP; ++j) ghat[j] = gn[j];
-    __syncwarp();
   };
 
   auto backward_noise = [&](int t) {
@@ -724,74 +603,82 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
     __syncwarp();
   };
 
-  // epilogue for state t (uses X = F P^f_t in SX, P^p_{t+1} in pprow, m^p_{t+1} in vmp,
-  // m^f_t in vm, P^f_t in SP): G_t = P^f F^T (P^p)^{-1}, Sigma_t = P^f - G P^p G^T,
-  // U_t = m^f_t - G_t m^p_{t+1} + chol(Sigma_t) eps_t.
-  auto epilogue = [&](int t) {
-    {
-      Real a_[DP];
-#pragma unroll
-      for (int j = 0; j < DP; ++j) a_[j] = pprow[j];
-      chol_rows<Real, DP>(a_, SL, vdiag, p.d, lane, &bad);   // L_p^T
-    }
-    Real ytr[DP];   // row j of Y^T, Y = L_p^{-1} X
-    {
-      Real xc[DP];
-      ld_col<Real, DP>(SX, row, xc);
-      fwd_subst<Real, DP>(SL, vdiag, xc, ytr);
+  // G row in SX (row-major), U_t -> global and the running aggregate
+  auto store_backward = [&](int t, Real ui) {
+    Real grow[DP];
+    ld_row<Real, DP>(SX, row, grow);
+    if (act) {
+      st_vec<Real, DP>(a.G + ((long)c * p.nT + t) * DP * DP + row * DP, grow);
+      a.U[((long)c * p.nT + t) * DP + lane] = ui;
+      vU[lane] = ui;
     }
     __syncwarp();
-    st_col<Real, DP>(SY, row, ytr, act);     // SY = Y row-major
+    {
+      Real uu[DP];
+      ld_vec<Real, DP>(vU, uu);
+      uhat += dot_rr<Real, DP>(ghat, uu);
+    }
+    st_row<Real, DP>(SY, row, ghat, act);
+    __syncwarp();
+    mm_row<Real, DP>(SY + row * LD, SX, ghat);
+    __syncwarp();
+  };
+
+  // epilogue for state t, after P^p_{t+1} has been factorised (LS in SL, LR in SLR,
+  // inverse diagonal in vdA); uses X = F P^f_t (SX), m^p_{t+1} (vmp), m^f_t (vm), P^f_t (SP):
+  // Y = L_p^{-1} X, Sigma_t = P^f - Y^T Y, G_t^T = L_p^{-T} Y, U_t = m^f - G m^p + chol(Sigma) eps.
+  auto epilogue = [&](int t) {
+    {
+      Real rr[DP];
+      ld_col<Real, DP>(SX, row, rr);
+      fsolve_rot<Real, DP, true>(SL, vdA, rr, SY, lane);   // SY = Y (columns)
+    }
     __syncwarp();
     Real sig[DP];
     ld_row<Real, DP>(SP, row, sig);
-    row_mat<Real, DP, true, true>(ytr, SY, sig);   // Sigma = P^f - Y^T Y
-    Real grow[DP];
-    bwd_subst<Real, DP>(SL, vdiag, ytr, grow);                // row of G = (L_p^{-T} Y)^T
-    chol_rows<Real, DP>(sig, SX, vdiag, p.d, lane, &bad);     // L_Sigma^T (X is dead)
+    mm_col<Real, DP, true, true>(SY, row, SY, sig);
+    {
+      Real rr[DP];
+      ld_col<Real, DP>(SY, row, rr);
+      bsolve_rot<Real, DP>(SLR, vdA, rr, SX, lane);       // SX = G (rows); X is dead
+    }
     backward_noise(t);
-    Real lc[DP];
-    ld_col<Real, DP>(SX, row, lc);
-    const Real ui = vm[row] - dot_rv<Real, DP>(grow, vmp) + dot_rv<Real, DP>(lc, veps);
-    store_backward(t, grow, ui);
+    const Real le = chol_rot<Real, DP>(sig, SL, nullptr, nullptr, vdA, veps, p.d, lane, &bad);
+    const Real ui = vm[row] - dot_row_vec<Real, DP>(SX + row * LD, vmp) + le;
+    store_backward(t, ui);
   };
 
-  // measurement update at t from (vmp, pprow): m^f, P^f, predictive terms
+  // measurement update at t from (vmp, pprow), with the factor of P^p + R in SG / vdB
   auto update = [&](int t) {
-    {
-      Real s_[DP];
-#pragma unroll
-      for (int j = 0; j < DP; ++j) s_[j] = pprow[j] + ((j == lane && j < p.d) ? p.r : (Real)0);
-      chol_rows<Real, DP>(s_, SL, vdiag, p.d, lane, &bad);   // L_S^T
-    }
     const Real rres = (lane < p.d) ? ytc[(long)t * p.d + lane] - vmp[lane] : (Real)0;
     __syncwarp();
     if (act) vr[lane] = rres;
     __syncwarp();
-    Real z[DP];
     {
       Real rr[DP];
       ld_vec<Real, DP>(vr, rr);
-      fwd_subst<Real, DP>(SL, vdiag, rr, z);
+      fsolve_vec<Real, DP>(SG, vdB, rr, vz, lane);
     }
-    Real ys[DP];
     {
-      Real rhs[DP];
+      Real rr[DP];
 #pragma unroll
-      for (int j = 0; j < DP; ++j) rhs[j] = pprow[j];
-      fwd_subst<Real, DP>(SL, vdiag, rhs, ys);
+      for (int j = 0; j < DP; ++j) rr[j] = pprow[j];
+      fsolve_rot<Real, DP, true>(SG, vdB, rr, SY, lane);   // SY = Y_s (columns)
     }
-    const Real mfi = vmp[row] + dot_rr<Real, DP>(ys, z);
-    const Real qz = dot_rr<Real, DP>(z, z);
-    Real lg = (lane < p.d) ? log(SL[lane * Lay<Real, DP>::LD + lane]) : (Real)0;
+    __syncwarp();
+    const Real mfi = vmp[row] + dot_col_vec<Real, DP>(SY, row, vz);
+    Real qz;
+    {
+      Real zz[DP];
+      ld_vec<Real, DP>(vz, zz);
+      qz = dot_rr<Real, DP>(zz, zz);
+    }
+    Real lg = (lane < p.d) ? -log(vdB[lane]) : (Real)0;
     lg = warp_sum<Real>(lg);
-    __syncwarp();
-    st_col<Real, DP>(SY, row, ys, act);      // SY = Y_s row-major
-    __syncwarp();
     Real pf[DP];
 #pragma unroll
     for (int j = 0; j < DP; ++j) pf[j] = pprow[j];
-    row_mat<Real, DP, true, true>(ys, SY, pf);     // P^f = P^p - Y_s^T Y_s
+    mm_col<Real, DP, true, true>(SY, row, SY, pf);
     __syncwarp();
     st_row<Real, DP>(SP, row, pf, act);
     if (act) vm[lane] = mfi;
@@ -809,6 +696,14 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
     }
   };
 
+  // factor of S = P^p + R only (SG / vdB)
+  auto factor_S = [&]() {
+    Real s_[DP];
+#pragma unroll
+    for (int j = 0; j < DP; ++j) s_[j] = pprow[j] + ((j == lane && j < p.d) ? p.r : (Real)0);
+    chol_rot<Real, DP>(s_, SG, nullptr, nullptr, vdB, nullptr, p.d, lane, &bad);
+  };
+
   // ---- block start
   if (k == 0) {
     ld_vec<Real, DP>(p.P0 + row * DP, pprow);
@@ -823,28 +718,44 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
     __syncwarp();
     predict();
   }
+  factor_S();
   update(s);
   for (int t = s + 1; t <= e; ++t) {
     predict();
-    if (epi) epilogue(t - 1);
+    if (epi) {
+      Real a_[DP], s_[DP];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) {
+        a_[j] = pprow[j];
+        s_[j] = pprow[j] + ((j == lane && j < p.d) ? p.r : (Real)0);
+      }
+      chol_rot2<Real, DP>(a_, SL, SLR, vdA, s_, SG, vdB, p.d, lane, &bad);
+      epilogue(t - 1);
+    } else {
+      factor_S();
+    }
     update(t);
   }
   if (epi) {
     if (e < p.nT - 1) {
       predict();
+      Real a_[DP];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) a_[j] = pprow[j];
+      chol_rot<Real, DP>(a_, SL, nullptr, SLR, vdA, nullptr, p.d, lane, &bad);
       epilogue(e);
     } else {
       // last state: G_{T-1} = 0, U_{T-1} = m^f + chol(P^f) eps
       Real pf[DP];
       ld_row<Real, DP>(SP, row, pf);
-      chol_rows<Real, DP>(pf, SX, vdiag, p.d, lane, &bad);
       backward_noise(e);
-      Real lc[DP];
-      ld_col<Real, DP>(SX, row, lc);
-      const Real ui = vm[row] + dot_rv<Real, DP>(lc, veps);
+      const Real le = chol_rot<Real, DP>(pf, SL, nullptr, nullptr, vdA, veps, p.d, lane, &bad);
       Real g0[DP];
       zero<Real, DP>(g0);
-      store_backward(e, g0, ui);
+      __syncwarp();
+      st_row<Real, DP>(SX, row, g0, act);
+      __syncwarp();
+      store_backward(e, vm[row] + le);
     }
     Real* gk = a.gu + ((long)c * p.nb + k) * Z::GS;
     if (act) {

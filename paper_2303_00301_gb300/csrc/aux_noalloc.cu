@@ -3,7 +3,7 @@
 // under an allocator it must not bypass, inside a host callback, or in a
 // process whose device-memory budget is fixed up front).
 //
-// Its scratch (padded model, element template, block aggregates, partial sums,
+// Its scratch (padded model, block aggregates, partial sums,
 // status words) lives in one file-scope device array of AUX_NOALLOC_SCRATCH_BYTES.
 // The array is part of the library's module: every GPU that loads the library
 // holds it until the process exits. All calls share it, so calls whose work
@@ -36,7 +36,7 @@ size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
 // byte offsets of the scratch regions for one problem size
 struct Layout {
-  size_t F, Q, P0, m0, b, Ryinv, tmpl, agg0, agg1, lz, st_iter, st, total;
+  size_t F, Q, P0, m0, b, Ryinv, agg0, agg1, lz, st_iter, st, total;
 };
 
 Layout layout(int DP, int C, int nb, size_t esz) {
@@ -49,7 +49,6 @@ Layout layout(int DP, int C, int nb, size_t esz) {
   L.m0 = o; o += vec;
   L.b = o; o += vec;
   L.Ryinv = o; o += mat;
-  L.tmpl = o; o += align256((size_t)7 * DP * DP * esz);
   L.agg0 = o; o += align256((size_t)C * nb * aux_es(DP) * esz);
   L.agg1 = o; o += align256((size_t)C * nb * aux_es(DP) * esz);
   L.lz = o; o += align256((size_t)C * nb * sizeof(double));
@@ -191,7 +190,7 @@ extern "C" int aux_loglik_noalloc(const aux_model_desc* desc, const void* ytilde
   m.stream = st; m.device = dev; m.ops = ops;
   m.F = base + lay.F; m.Q = base + lay.Q; m.P0 = base + lay.P0;
   m.m0 = base + lay.m0; m.b = base + lay.b; m.Ryinv = base + lay.Ryinv;
-  m.tmpl = base + lay.tmpl; m.agg0 = base + lay.agg0; m.agg1 = base + lay.agg1;
+  m.agg0 = base + lay.agg0; m.agg1 = base + lay.agg1;
   m.lz_part = reinterpret_cast<double*>(base + lay.lz);
   m.status_iter = reinterpret_cast<int32_t*>(base + lay.st_iter);
   m.status = reinterpret_cast<int32_t*>(base + lay.st);

@@ -58,12 +58,6 @@ struct Ops {
 
   static int items(const aux_model* m) { return m->C * m->nb; }
 
-  // the model-derived matrix parts of the filtering elements; they depend on
-  // (F, Q, P0, delta) only, so one pass serves every chain and step of a call
-  static void template_pass(aux_model* m, const KP<Real>& p, cudaStream_t st) {
-    ProfScope ps(m, PK_TEMPLATE, st);
-    k_element_template<Real, DP><<<1, 32, 0, st>>>(p, (Real*)m->tmpl);
-  }
 
   // parallel filter on yt: phase 1, Hillis-Steele rounds, phase 3
   static void filter(aux_model* m, const KP<Real>& p, const Real* yt, ApplyArgs<Real> a,
@@ -73,7 +67,7 @@ struct Ops {
     Real* b1 = (Real*)m->agg1;
     { ProfScope ps(m, PK_REDUCE, st);
     k_filter_reduce<Real, DP><<<(n + Z::RED_WPC - 1) / Z::RED_WPC, 32 * Z::RED_WPC, Z::RED_SMEM, st>>>(
-        p, (const Real*)m->tmpl, yt, b0); }
+        p, yt, b0); }
     for (int off = 1; off < m->nb; off *= 2) {
       { ProfScope ps(m, PK_SCAN, st);
       k_filter_scan_level<Real, DP><<<(n + Z::SCAN_WPC - 1) / Z::SCAN_WPC, 32 * Z::SCAN_WPC, Z::SCAN_SMEM, st>>>(p, b0, b1, off); }
@@ -106,7 +100,6 @@ struct Ops {
     const KP<Real> p = make_kp<Real>(m);
     Real* x = (Real*)xv;
     const long n = (long)m->C * m->T * m->d;
-    template_pass(m, p, st);
     const int lin_grid = (int)std::min<long>((n + 255) / 256, 152L * 16);
     for (int it = 0; it < n_iters; ++it) {
       const uint64_t iter = iter0 + (uint64_t)it;
@@ -128,7 +121,6 @@ struct Ops {
 
   static int loglik(aux_model* m, const void* yt, double* logZ, void* mf, void* Pf, cudaStream_t st) {
     const KP<Real> p = make_kp<Real>(m);
-    template_pass(m, p, st);
     ApplyArgs<Real> a = apply_args(m, APPLY_LOGZ, 0);
     a.mf = (Real*)mf;
     a.Pf = (Real*)Pf;
@@ -141,7 +133,6 @@ struct Ops {
   static int sample_path(aux_model* m, const void* yt, const void* eps, uint64_t iter, void* xs,
                          double* logZ, cudaStream_t st) {
     const KP<Real> p = make_kp<Real>(m);
-    template_pass(m, p, st);
     ApplyArgs<Real> a = apply_args(m, APPLY_EPI | APPLY_LOGZ, iter);
     a.eps = (const Real*)eps;
     filter(m, p, (const Real*)yt, a, st);
