@@ -59,29 +59,43 @@ def make_workload(name, rank=0):
 
 
 # --------------------------------------------------------------------------- flops model
+# Algorithmic flops in the unpadded dimension d (2 per multiply-add): a dense
+# d x d product is 2 d^3, a triangular solve with d right-hand sides or a
+# triangular x dense product d^3, a Cholesky factorisation d^3 / 3, a
+# matrix-vector product 2 d^2. With a diagonal F (the SV model) the products
+# F C, F C F^T, F A and F P^f are O(d^2) and counted as such.
 def combine_flops(d):
-    """Algorithmic flops of one application of the element operator (Cholesky form):
-    2 Cholesky (d^3/3 each), 2 triangular x dense (d^3), 1 triangular solve with d
-    right-hand sides (d^3), 8 dense products (2 d^3 each), plus 9 matrix-vector (2 d^2)."""
+    """Element operator, Cholesky form: 2 Cholesky, 2 triangular x dense, 1
+    triangular solve with d right-hand sides, 8 dense products, 9 mat-vec."""
     return (59.0 / 3.0) * d ** 3 + 18.0 * d ** 2
 
 
-def apply_flops_per_step(d, epilogue):
-    """One in-block filtering step: predict (2 products, 1 mat-vec), update (Cholesky,
-    triangular solves, P^f downdate); with the backward-element epilogue also two
-    Cholesky, two triangular solves, Sigma downdate and the running G product."""
-    base = (2 + 2 + 1.0 / 3.0 + 1 + 2) * d ** 3 + 5 * d ** 2
+def reduce_flops_per_step(d, fdiag):
+    """Conditional Kalman step: Cholesky of S, 2 triangular solves (Y, W), 3 products
+    (Y^T Y, Y^T W, W^T W); with a dense F also F C, (F C) F^T and F A."""
+    f = (1.0 / 3.0 + 2 + 6) * d ** 3 + 7 * d ** 2
+    return f + (0.0 if fdiag else 6.0 * d ** 3) + (3 * d ** 2 if fdiag else 0.0)
+
+
+def apply_flops_per_step(d, epilogue, fdiag):
+    """In-block Kalman step: Cholesky of S, 1 triangular solve, P^f downdate; with the
+    backward-element epilogue also the Cholesky of P^p and Sigma, a forward and a
+    backward triangular solve, the Sigma downdate and the running G product; with a
+    dense F the prediction F P^f F^T (two products)."""
+    f = (1.0 / 3.0 + 1 + 2) * d ** 3 + 5 * d ** 2
     if epilogue:
-        base += (1.0 / 3.0 + 1 + 2 + 1 + 1.0 / 3.0 + 2) * d ** 3 + 6 * d ** 2
-    return base
+        f += (1.0 / 3.0 + 1 + 2 + 1 + 1.0 / 3.0 + 2) * d ** 3 + 6 * d ** 2
+    return f + (0.0 if fdiag else 4.0 * d ** 3) + (3 * d ** 2 if fdiag else 0.0)
 
 
-def kernel_flops(kind, d, T, C, nb, launches):
-    """Algorithmic flops of all launches of one kernel kind in the timed region."""
+def kernel_flops(kind, d, T, C, nb, launches, fdiag):
+    """Algorithmic flops of all launches of one kernel kind in the timed region
+    (each MH step runs the filter twice: forward with the epilogue, reverse without)."""
     if kind == "reduce":
-        return launches * C * (T - nb) * combine_flops(d)
-    if kind == "apply":  # half the launches carry the epilogue (forward), half not (reverse)
-        return launches / 2 * C * T * (apply_flops_per_step(d, True) + apply_flops_per_step(d, False))
+        return launches * C * T * reduce_flops_per_step(d, fdiag)
+    if kind == "apply":
+        return launches / 2 * C * T * (apply_flops_per_step(d, True, fdiag) +
+                                       apply_flops_per_step(d, False, fdiag))
     return None
 
 
@@ -200,6 +214,7 @@ def config_of(name, w, block_len, nb):
 
 # --------------------------------------------------------------------------- GPU arm
 def run_ours(args):
+    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -293,7 +308,8 @@ def run_ours(args):
     # roofline of the dominant kernel (time-weighted), FP32 FMA pipe bound
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_launches = prof[dom]
-    flops = kernel_flops(dom, d, T, C, nb, dom_launches)
+    fdiag = bool(np.all(wl.F == np.diag(np.diag(wl.F))))
+    flops = kernel_flops(dom, d, T, C, nb, dom_launches, fdiag)
     peaks = {}
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pp):
@@ -307,6 +323,7 @@ def run_ours(args):
     if flops is not None and dom_ms > 0:
         achieved = flops / (dom_ms / 1e3) / 1e12
         roofline = {"bound": "alu", "kernel": f"k_filter_{dom}", "achieved": achieved,
+                    "flops_per_launch": flops / dom_launches, "diagonal_F": fdiag,
                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                     "traffic": None, "launches": dom_launches,
                     "avg_launch_ms": dom_ms / dom_launches,

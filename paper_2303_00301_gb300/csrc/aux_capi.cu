@@ -208,6 +208,10 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
   m->nb = (T + L_blk - 1) / L_blk;
   m->delta = desc->delta;
   m->seed = seed;
+  m->fdiag = 1;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      if (i != j && desc->F[i * d + j] != 0.0) m->fdiag = 0;
   m->stream = (cudaStream_t)stream;
   m->esz = desc->dtype == AUX_F32 ? sizeof(float) : sizeof(double);
   cudaGetDevice(&m->device);

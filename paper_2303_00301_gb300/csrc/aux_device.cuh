@@ -461,6 +461,39 @@ __device__ __forceinline__ void fsolve_rot(const T* LS, const T* inv_diag, T (&r
   }
 }
 
+// Forward solves with one factor and several right-hand sides in one pass (one
+// row of LS feeds every system): r1 and r2 are per lane (results written as
+// columns `lane` of Y1 and Y2), rv is the same in every lane (result to yv).
+template <typename T, int DP, bool TWO>
+__device__ __forceinline__ void fsolve_multi(const T* LS, const T* inv_diag, T (&r1)[DP], T* Y1,
+                                             T (&r2)[DP], T* Y2, T (&rv)[DP], T* yv, int lane) {
+  constexpr int LD = Lay<T, DP>::LD;
+  const bool act = lane < DP;
+#pragma unroll 1
+  for (int k = 0; k < DP; ++k) {
+    const T id = inv_diag[k];
+    const T y1 = r1[0] * id;
+    const T y2 = TWO ? r2[0] * id : (T)0;
+    const T yvk = rv[0] * id;
+    if (act) {
+      Y1[k * LD + lane] = y1;
+      if (TWO) Y2[k * LD + lane] = y2;
+    }
+    if (lane == 0) yv[k] = yvk;
+    T lk[DP];
+    ld_vec<T, DP>(LS + k * LD, lk);
+#pragma unroll
+    for (int j = 0; j < DP - 1; ++j) {
+      r1[j] = fma(-y1, lk[j + 1], r1[j + 1]);
+      if (TWO) r2[j] = fma(-y2, lk[j + 1], r2[j + 1]);
+      rv[j] = fma(-yvk, lk[j + 1], rv[j + 1]);
+    }
+    r1[DP - 1] = (T)0;
+    if (TWO) r2[DP - 1] = (T)0;
+    rv[DP - 1] = (T)0;
+  }
+}
+
 // Forward solve L y = r with the same r in every lane; y goes to the vector slot yv.
 template <typename T, int DP>
 __device__ __forceinline__ void fsolve_vec(const T* LS, const T* inv_diag, T (&r)[DP], T* yv,

@@ -13,6 +13,7 @@ struct AuxOps;
 struct aux_model {
   int dtype = 0, d = 0, DP = 0, T = 0, C = 0, emis = 0, y_per_chain = 0;
   int L = 0, nb = 0;
+  int fdiag = 0;             // F has no off-diagonal entries
   double delta = 0.0;
   uint64_t seed = 0;
   size_t esz = 0;            // bytes per compute-type element

@@ -40,6 +40,7 @@ template <typename Real> struct KP {
   Real r;        // delta / 2
   Real sqrt_r;   // sqrt(delta / 2)
   int emis, y_per_chain;
+  int fdiag;     // F is diagonal: F C, F C F^T and F A are elementwise
   uint64_t seed;
   const Real *F, *Q, *P0, *m0, *b, *Ryinv;  // [DP*DP] / [DP], zero padded
   const Real* y;                             // [T][d] or [C][T][d]
@@ -62,7 +63,7 @@ template <typename Real, int DP> struct Sizes {
   static constexpr int ES = 3 * DP * DP + 2 * DP;   // global element: A, C, J, b, eta
   static constexpr int GS = DP * DP + DP;           // global backward aggregate: G, U
   static constexpr size_t SMEM_MAX = 227 * 1024;
-  static constexpr size_t MODEL = (3 * MAT + VEC) * sizeof(Real);   // F, F^T, Q, b
+  static constexpr size_t MODEL = (3 * MAT + 2 * VEC) * sizeof(Real);   // F, F^T, Q, b, diag F
   static constexpr int cap(size_t fixed, size_t per_warp, int want) {
     return (SMEM_MAX - fixed) / per_warp >= (size_t)want ? want : (int)((SMEM_MAX - fixed) / per_warp);
   }
@@ -270,7 +271,10 @@ __device__ __forceinline__ void load_model_slots(const KP<Real>& p, Real* sF, Re
     sFT[j * LD + i] = p.F[q];
     sQ[i * LD + j] = p.Q[q];
   }
-  if (threadIdx.x < DP) sb[threadIdx.x] = p.b[threadIdx.x];
+  if (threadIdx.x < DP) {
+    sb[threadIdx.x] = p.b[threadIdx.x];
+    sb[Lay<Real, DP>::VEC + threadIdx.x] = p.F[threadIdx.x * DP + threadIdx.x];   // diag F
+  }
 }
 
 // global element <-> warp slots
@@ -343,7 +347,8 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::RED_WPC, 1)
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
-  Real* SA = sb + VEC + warp * Z::RED_WARP_ELEMS;
+  const Real* sphi = sb + VEC;
+  Real* SA = sb + 2 * VEC + warp * Z::RED_WARP_ELEMS;
   Real* SC = SA + MAT;
   Real* SX = SC + MAT;
   Real* SY = SX + MAT;
@@ -377,6 +382,22 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::RED_WPC, 1)
       Real z0[DP];
       zero<Real, DP>(z0);
       st_row<Real, DP>(SX, row, z0, act);          // F A = 0 for the prior
+    } else if (p.fdiag) {
+      // diagonal F: P^p_ij = C_ij phi_i phi_j + Q_ij, (F A)_ij = phi_i A_ij
+      Real cr[DP], ph[DP], qr[DP], ar[DP];
+      ld_row<Real, DP>(SC, row, cr);
+      ld_vec<Real, DP>(sphi, ph);
+      ld_row<Real, DP>(sQ, row, qr);
+      ld_row<Real, DP>(SA, row, ar);
+      const Real phi = sphi[row];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) {
+        pprow[j] = fma(cr[j], phi * ph[j], qr[j]);
+        ar[j] *= phi;
+      }
+      mpi = phi * vb[row] + sb[row];
+      __syncwarp();
+      st_row<Real, DP>(SX, row, ar, act);
     } else {
       Real xr[DP];
       mm_row<Real, DP>(sF + row * LD, SC, xr);      // X = F C
@@ -406,20 +427,13 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::RED_WPC, 1)
     if (act) vr[lane] = rres;
     __syncwarp();
     {
-      Real rr[DP];
-      ld_vec<Real, DP>(vr, rr);
-      fsolve_vec<Real, DP>(SL, vdiag, rr, vz, lane);
-    }
-    {
-      Real rr[DP];
+      // Y = L^{-1} P^p, W = L^{-1} F A (as columns) and z = L^{-1} r in one pass
+      Real r1[DP], r2[DP], rv[DP];
 #pragma unroll
-      for (int j = 0; j < DP; ++j) rr[j] = pprow[j];
-      fsolve_rot<Real, DP, true>(SL, vdiag, rr, SY, lane);   // Y as columns
-    }
-    {
-      Real rr[DP];
-      ld_col<Real, DP>(SX, row, rr);
-      fsolve_rot<Real, DP, true>(SL, vdiag, rr, SW, lane);   // W as columns
+      for (int j = 0; j < DP; ++j) r1[j] = pprow[j];
+      ld_col<Real, DP>(SX, row, r2);
+      ld_vec<Real, DP>(vr, rv);
+      fsolve_multi<Real, DP, true>(SL, vdiag, r1, SY, r2, SW, rv, vz, lane);
     }
     __syncwarp();
     {
@@ -550,7 +564,8 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
   if (item >= p.C * p.nb) return;
   const int c = item / p.nb, k = item % p.nb;
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
-  Real* SP = sb + VEC + warp * Z::APP_WARP_ELEMS;
+  const Real* sphi = sb + VEC;
+  Real* SP = sb + 2 * VEC + warp * Z::APP_WARP_ELEMS;
   Real* SX = SP + MAT;
   Real* SL = SX + MAT;
   Real* SLR = SL + MAT;
@@ -577,6 +592,24 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
 
   // X = F P^f (slot SX), P^p = X F^T + Q (symmetrised, pprow), m^p = F m^f + b (vmp)
   auto predict = [&]() {
+    if (p.fdiag) {
+      Real pr[DP], ph[DP], qr[DP];
+      ld_row<Real, DP>(SP, row, pr);
+      ld_vec<Real, DP>(sphi, ph);
+      ld_row<Real, DP>(sQ, row, qr);
+      const Real phi = sphi[row];
+      const Real mpi = phi * vm[row] + sb[row];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) {
+        pprow[j] = fma(pr[j], phi * ph[j], qr[j]);
+        pr[j] *= phi;                                   // X = F P^f
+      }
+      __syncwarp();
+      st_row<Real, DP>(SX, row, pr, act);
+      if (act) vmp[lane] = mpi;
+      __syncwarp();
+      return;
+    }
     Real xr[DP];
     mm_row<Real, DP>(sF + row * LD, SP, xr);
     const Real mpi = dot_row_vec<Real, DP>(sF + row * LD, vm) + sb[row];
@@ -655,15 +688,12 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
     if (act) vr[lane] = rres;
     __syncwarp();
     {
-      Real rr[DP];
-      ld_vec<Real, DP>(vr, rr);
-      fsolve_vec<Real, DP>(SG, vdB, rr, vz, lane);
-    }
-    {
-      Real rr[DP];
+      // Y_s = L_S^{-1} P^p (columns of SY) and z = L_S^{-1} r in one pass
+      Real r1[DP], rv[DP];
 #pragma unroll
-      for (int j = 0; j < DP; ++j) rr[j] = pprow[j];
-      fsolve_rot<Real, DP, true>(SG, vdB, rr, SY, lane);   // SY = Y_s (columns)
+      for (int j = 0; j < DP; ++j) r1[j] = pprow[j];
+      ld_vec<Real, DP>(vr, rv);
+      fsolve_multi<Real, DP, false>(SG, vdB, r1, SY, r1, nullptr, rv, vz, lane);
     }
     __syncwarp();
     const Real mfi = vmp[row] + dot_col_vec<Real, DP>(SY, row, vz);

@@ -188,6 +188,10 @@ extern "C" int aux_loglik_noalloc(const aux_model_desc* desc, const void* ytilde
   m.emis = desc->emis_kind; m.y_per_chain = 0;
   m.L = L_blk; m.nb = nb; m.delta = desc->delta; m.seed = 0; m.esz = esz;
   m.stream = st; m.device = dev; m.ops = ops;
+  m.fdiag = 1;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      if (i != j && desc->F[i * d + j] != 0.0) m.fdiag = 0;
   m.F = base + lay.F; m.Q = base + lay.Q; m.P0 = base + lay.P0;
   m.m0 = base + lay.m0; m.b = base + lay.b; m.Ryinv = base + lay.Ryinv;
   m.agg0 = base + lay.agg0; m.agg1 = base + lay.agg1;

@@ -33,6 +33,7 @@ KP<Real> make_kp(const aux_model* m) {
   p.r = (Real)(0.5 * m->delta);
   p.sqrt_r = (Real)std::sqrt(0.5 * m->delta);
   p.emis = m->emis; p.y_per_chain = m->y_per_chain; p.seed = m->seed;
+  p.fdiag = m->fdiag;
   p.F = (const Real*)m->F; p.Q = (const Real*)m->Q; p.P0 = (const Real*)m->P0;
   p.m0 = (const Real*)m->m0; p.b = (const Real*)m->b; p.Ryinv = (const Real*)m->Ryinv;
   p.y = (const Real*)m->y; p.mask = m->mask;
