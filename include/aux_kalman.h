@@ -128,6 +128,31 @@ int aux_loglik(aux_model *m, const void *ytilde, double *logZ, void *mf, void *P
 int aux_sample_path(aux_model *m, const void *ytilde, const void *eps, uint64_t iteration,
                     void *xstar, double *logZ, void *stream);
 
+/* Gradient of log Z (as computed by aux_loglik) with respect to
+ * theta = (mu, phi, chol Sigma, delta) of the multivariate stochastic-volatility
+ * parameterisation (Section 4.1): F = diag(phi), b = (I - F) mu, Q = L L^T with
+ * L = chol Sigma lower triangular, p_0 the stationary law (m0 = mu,
+ * P0_ij = Q_ij / (1 - phi_i phi_j)), R = (delta/2) I; ytilde is held fixed. The
+ * paper differentiates by automatic differentiation; here the gradient is
+ * Fisher's identity, the expected complete-data score under the smoothing law,
+ * with the smoother computed by the parallel backward scan of Appendix A.2.2.
+ *   ytilde      device [C][T][d] compute type.
+ *   logZ        device [C] double or NULL.
+ *   g_mu        device [C][d] double;  g_Phi device [C][d] double (d/d phi_i);
+ *   g_cholSigma device [C][d][d] double (lower triangle; upper entries 0);
+ *   g_delta     device [C] double.
+ * Errors: INVALID_ARG; UNSUPPORTED unless F is diagonal with |phi_i| < 1,
+ * m0 = (I - F)^{-1} b and P0 is the stationary covariance; OOM on the first
+ * call (it allocates C*T*d^2 elements for the backward covariances). */
+int aux_loglik_grad(aux_model *m, const void *ytilde, double *logZ, double *g_mu, double *g_Phi,
+                    double *g_cholSigma, double *g_delta, void *stream);
+
+/* Replace the model of an existing handle (same dtype, d_x, T, n_chains,
+ * emis_kind, y_per_chain): validates as aux_init_model, then overwrites the
+ * device copies of m0, P0, F, b, Q, y, R_y and delta. Synchronises the handle's
+ * last stream first. Used for parameter updates between sampler sweeps. */
+int aux_set_model_params(aux_model *m, const aux_model_desc *desc);
+
 /* Copy the latched per-chain device status words to host memory
  * (synchronises the handle's last stream) and clear them.
  *   per_chain_status host [C] int32 or NULL. Returns AUX_OK if every chain is
@@ -143,7 +168,9 @@ int aux_get_status(aux_model *m, int32_t *per_chain_status);
 #define AUX_PROFILE_BACKWARD  5  /* backward (G, U) scan, x*, and MH partial sums (Proposition A.1) */
 #define AUX_PROFILE_MH        6  /* log alpha, MH test and state update (Algorithm 2) */
 #define AUX_PROFILE_SUM       7  /* log Z reduction */
-#define AUX_PROFILE_KINDS     8
+#define AUX_PROFILE_SMOOTH    8  /* smoother aggregates and sweep with score statistics (gradient) */
+#define AUX_PROFILE_GRAD      9  /* FP64 gradient assembly per chain */
+#define AUX_PROFILE_KINDS     10
 
 /* Turn per-launch timing on or off for this handle: while on, every kernel
  * launch is bracketed by two CUDA events recorded on its own stream. */

@@ -79,6 +79,10 @@ def _load():
     lib.aux_read_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
     lib.aux_read_profile.restype = ctypes.c_int
+    lib.aux_loglik_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.aux_loglik_grad.restype = ctypes.c_int
+    lib.aux_set_model_params.argtypes = [vp, ctypes.POINTER(aux_model_desc)]
+    lib.aux_set_model_params.restype = ctypes.c_int
     lib.aux_loglik_noalloc.argtypes = [ctypes.POINTER(aux_model_desc), vp, vp, vp]
     lib.aux_loglik_noalloc.restype = ctypes.c_int
     lib.aux_status_string.argtypes = [ctypes.c_int]
@@ -158,6 +162,21 @@ def aux_init_model(*, d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind, dt
     return handle
 
 
+def aux_loglik_grad(handle, ytilde, g_mu, g_Phi, g_cholSigma, g_delta, logZ=None, stream=None):
+    rc = LIB.aux_loglik_grad(handle, _ptr(ytilde), _ptr(logZ), _ptr(g_mu), _ptr(g_Phi),
+                             _ptr(g_cholSigma), _ptr(g_delta), _stream(stream))
+    _check(rc, "aux_loglik_grad")
+
+
+def aux_set_model_params(handle, *, d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind,
+                         dtype=AUX_F32, R_y=None, obs_mask=None, y_per_chain=False, block_len=0):
+    desc, keep = _make_desc(d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind, dtype, R_y,
+                            obs_mask, y_per_chain, block_len)
+    rc = LIB.aux_set_model_params(handle, ctypes.byref(desc))
+    _check(rc, "aux_set_model_params")
+    del keep
+
+
 def aux_loglik_noalloc(ytilde, logZ, *, d_x, T, n_chains, m0, P0, F, b, Q, delta,
                        dtype=AUX_F32, block_len=0, stream=None):
     """aux_loglik without a handle or any device allocation (fixed library scratch)."""
@@ -194,7 +213,8 @@ def aux_get_status(handle, n_chains=None):
     return rc, np.frombuffer(buf, dtype=np.int32).copy()
 
 
-PROFILE_KINDS = ["linearise", "template", "reduce", "scan", "apply", "backward", "mh", "sum"]
+PROFILE_KINDS = ["linearise", "template", "reduce", "scan", "apply", "backward", "mh", "sum",
+                 "smooth", "grad"]
 
 
 def aux_set_profiling(handle, enable):

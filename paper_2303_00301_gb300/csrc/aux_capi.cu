@@ -127,43 +127,31 @@ void release(aux_model* m) {
   delete m;
 }
 
+int put(aux_model* m, void** p, const std::vector<unsigned char>& h, bool alloc) {
+  if (alloc) return upload(m, p, h);
+  return cudaMemcpy(*p, h.data(), h.size(), cudaMemcpyHostToDevice) == cudaSuccess ? AUX_OK
+                                                                                  : AUX_E_CUDA;
+}
+
 template <typename Real>
-int upload_model(aux_model* m, const aux_model_desc* d, const std::vector<double>& Ryinv) {
+int upload_model(aux_model* m, const aux_model_desc* d, const std::vector<double>& Ryinv,
+                 bool alloc) {
   const int dd = m->d, DP = m->DP;
   int rc;
-  if ((rc = upload(m, &m->F, pad_matrix<Real>(d->F, dd, DP)))) return rc;
-  if ((rc = upload(m, &m->Q, pad_matrix<Real>(d->Q, dd, DP)))) return rc;
-  if ((rc = upload(m, &m->P0, pad_matrix<Real>(d->P0, dd, DP)))) return rc;
-  if ((rc = upload(m, &m->m0, pad_vector<Real>(d->m0, dd, DP)))) return rc;
-  if ((rc = upload(m, &m->b, pad_vector<Real>(d->b, dd, DP)))) return rc;
-  if ((rc = upload(m, &m->Ryinv, pad_matrix<Real>(Ryinv.empty() ? nullptr : Ryinv.data(), dd, DP)))) return rc;
+  if ((rc = put(m, &m->F, pad_matrix<Real>(d->F, dd, DP), alloc))) return rc;
+  if ((rc = put(m, &m->Q, pad_matrix<Real>(d->Q, dd, DP), alloc))) return rc;
+  if ((rc = put(m, &m->P0, pad_matrix<Real>(d->P0, dd, DP), alloc))) return rc;
+  if ((rc = put(m, &m->m0, pad_vector<Real>(d->m0, dd, DP), alloc))) return rc;
+  if ((rc = put(m, &m->b, pad_vector<Real>(d->b, dd, DP), alloc))) return rc;
+  if ((rc = put(m, &m->Ryinv, pad_matrix<Real>(Ryinv.empty() ? nullptr : Ryinv.data(), dd, DP), alloc))) return rc;
   const size_t ny = (size_t)(m->y_per_chain ? m->C : 1) * m->T * dd;
-  if ((rc = upload(m, &m->y, convert<Real>(d->y, ny)))) return rc;
+  if ((rc = put(m, &m->y, convert<Real>(d->y, ny), alloc))) return rc;
   return AUX_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-const char* aux_status_string(int code) {
-  switch (code) {
-    case AUX_OK: return "ok";
-    case AUX_E_INVALID_ARG: return "invalid argument";
-    case AUX_E_NOT_PD: return "matrix not positive definite";
-    case AUX_E_NONFINITE: return "non-finite value";
-    case AUX_E_CUDA: return "CUDA runtime error";
-    case AUX_E_TIMEOUT: return "device wait timed out";
-    case AUX_E_OOM: return "out of device memory";
-    case AUX_E_UNSUPPORTED: return "unsupported configuration";
-    case AUX_E_TOO_LARGE: return "problem exceeds the fixed scratch of aux_loglik_noalloc";
-    default: return "unknown status";
-  }
-}
-
-int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_model** out) {
-  if (!desc || !out) return AUX_E_INVALID_ARG;
-  *out = nullptr;
+// Host validation shared by aux_init_model and aux_set_model_params; fills Ryinv.
+int validate_desc(const aux_model_desc* desc, std::vector<double>& Ryinv) {
+  if (!desc) return AUX_E_INVALID_ARG;
   if (desc->abi_version != AUX_ABI_VERSION) return AUX_E_INVALID_ARG;
   if (desc->dtype != AUX_F32 && desc->dtype != AUX_F64) return AUX_E_INVALID_ARG;
   if (desc->emis_kind != AUX_EMIS_LINEAR_GAUSSIAN && desc->emis_kind != AUX_EMIS_SV)
@@ -188,14 +176,81 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
   std::vector<double> L;
   if (!is_symmetric(desc->P0, d) || !host_cholesky(desc->P0, d, L)) return AUX_E_NOT_PD;
   if (!is_symmetric(desc->Q, d) || !host_cholesky(desc->Q, d, L)) return AUX_E_NOT_PD;
-  std::vector<double> Ryinv;
-  double ry_logdet = 0.0;
+  Ryinv.clear();
   if (desc->emis_kind == AUX_EMIS_LINEAR_GAUSSIAN) {
     if (!is_symmetric(desc->R_y, d) || !host_cholesky(desc->R_y, d, L)) return AUX_E_NOT_PD;
     Ryinv = spd_inverse(L, d);
-    for (int i = 0; i < d; ++i) ry_logdet += 2.0 * std::log(L[i * d + i]);
   }
-  (void)ry_logdet;
+  return AUX_OK;
+}
+
+// The SV parameterisation needed by aux_loglik_grad: F = diag(phi) with |phi| < 1,
+// m0 = mu = b / (1 - phi), P0_ij = Q_ij / (1 - phi_i phi_j). Fills the FP64 constants
+// [mu, phi, L, Q, Q^{-1}, P0^{-1}] when it holds.
+bool theta_constants(const aux_model_desc* desc, std::vector<double>& gc) {
+  const int d = desc->d_x;
+  std::vector<double> mu(d), phi(d), L, LP;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      if (i != j && desc->F[i * d + j] != 0.0) return false;
+  for (int i = 0; i < d; ++i) {
+    phi[i] = desc->F[i * d + i];
+    if (!(std::fabs(phi[i]) < 1.0)) return false;
+    mu[i] = desc->b[i] / (1.0 - phi[i]);
+    if (std::fabs(desc->m0[i] - mu[i]) > 1e-9 * (1.0 + std::fabs(mu[i]))) return false;
+  }
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      const double st = desc->Q[i * d + j] / (1.0 - phi[i] * phi[j]);
+      if (std::fabs(desc->P0[i * d + j] - st) > 1e-9 * (1.0 + std::fabs(st))) return false;
+    }
+  if (!host_cholesky(desc->Q, d, L) || !host_cholesky(desc->P0, d, LP)) return false;
+  const std::vector<double> Qi = spd_inverse(L, d), P0i = spd_inverse(LP, d);
+  gc.clear();
+  gc.insert(gc.end(), mu.begin(), mu.end());
+  gc.insert(gc.end(), phi.begin(), phi.end());
+  gc.insert(gc.end(), L.begin(), L.end());
+  gc.insert(gc.end(), desc->Q, desc->Q + (size_t)d * d);
+  gc.insert(gc.end(), Qi.begin(), Qi.end());
+  gc.insert(gc.end(), P0i.begin(), P0i.end());
+  return true;
+}
+
+int diag_flag(const aux_model_desc* desc) {
+  const int d = desc->d_x;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      if (i != j && desc->F[i * d + j] != 0.0) return 0;
+  return 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* aux_status_string(int code) {
+  switch (code) {
+    case AUX_OK: return "ok";
+    case AUX_E_INVALID_ARG: return "invalid argument";
+    case AUX_E_NOT_PD: return "matrix not positive definite";
+    case AUX_E_NONFINITE: return "non-finite value";
+    case AUX_E_CUDA: return "CUDA runtime error";
+    case AUX_E_TIMEOUT: return "device wait timed out";
+    case AUX_E_OOM: return "out of device memory";
+    case AUX_E_UNSUPPORTED: return "unsupported configuration";
+    case AUX_E_TOO_LARGE: return "problem exceeds the fixed scratch of aux_loglik_noalloc";
+    default: return "unknown status";
+  }
+}
+
+int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_model** out) {
+  if (!desc || !out) return AUX_E_INVALID_ARG;
+  *out = nullptr;
+  std::vector<double> Ryinv;
+  const int vrc = validate_desc(desc, Ryinv);
+  if (vrc) return vrc;
+  const int d = desc->d_x, T = desc->T, C = desc->n_chains;
+  const int DP = pick_dp(d);
 
   aux_model* m = new (std::nothrow) aux_model();
   if (!m) return AUX_E_OOM;
@@ -208,18 +263,22 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
   m->nb = (T + L_blk - 1) / L_blk;
   m->delta = desc->delta;
   m->seed = seed;
-  m->fdiag = 1;
-  for (int i = 0; i < d; ++i)
-    for (int j = 0; j < d; ++j)
-      if (i != j && desc->F[i * d + j] != 0.0) m->fdiag = 0;
+  m->fdiag = diag_flag(desc);
   m->stream = (cudaStream_t)stream;
   m->esz = desc->dtype == AUX_F32 ? sizeof(float) : sizeof(double);
   cudaGetDevice(&m->device);
   m->ops = desc->dtype == AUX_F32 ? aux_ops_f32(DP) : aux_ops_f64(DP);
   if (!m->ops) { release(m); return AUX_E_UNSUPPORTED; }
 
-  int rc = desc->dtype == AUX_F32 ? upload_model<float>(m, desc, Ryinv)
-                                  : upload_model<double>(m, desc, Ryinv);
+  int rc = desc->dtype == AUX_F32 ? upload_model<float>(m, desc, Ryinv, true)
+                                  : upload_model<double>(m, desc, Ryinv, true);
+  std::vector<double> gc;
+  m->grad_ok = theta_constants(desc, gc) ? 1 : 0;
+  if (!rc) {   // always allocated (sized for d), rewritten by aux_set_model_params
+    std::vector<unsigned char> h((size_t)(2 * d + 4 * d * d) * sizeof(double), 0);
+    if (m->grad_ok) std::memcpy(h.data(), gc.data(), gc.size() * sizeof(double));
+    rc = upload(m, (void**)&m->gconst, h);
+  }
   if (!rc && desc->obs_mask) {
     std::vector<unsigned char> mk(desc->obs_mask, desc->obs_mask + T);
     rc = upload(m, (void**)&m->mask, mk);
@@ -271,6 +330,44 @@ int aux_sample_path(aux_model* m, const void* ytilde, const void* eps, uint64_t 
   if (!m || !ytilde || !xstar) return AUX_E_INVALID_ARG;
   m->stream = (cudaStream_t)stream;
   return m->ops->sample_path(m, ytilde, eps, iteration, xstar, logZ, m->stream);
+}
+
+int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {
+  if (!m || !desc) return AUX_E_INVALID_ARG;
+  if (desc->dtype != m->dtype || desc->d_x != m->d || desc->T != m->T || desc->n_chains != m->C ||
+      desc->emis_kind != m->emis || (desc->y_per_chain ? 1 : 0) != m->y_per_chain)
+    return AUX_E_INVALID_ARG;
+  std::vector<double> Ryinv;
+  const int vrc = validate_desc(desc, Ryinv);
+  if (vrc) return vrc;
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) return AUX_E_CUDA;
+  const int rc = m->dtype == AUX_F32 ? upload_model<float>(m, desc, Ryinv, false)
+                                     : upload_model<double>(m, desc, Ryinv, false);
+  if (rc) return rc;
+  m->delta = desc->delta;
+  m->fdiag = diag_flag(desc);
+  std::vector<double> gc;
+  m->grad_ok = theta_constants(desc, gc) ? 1 : 0;
+  if (m->grad_ok &&
+      cudaMemcpy(m->gconst, gc.data(), gc.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return AUX_E_CUDA;
+  return AUX_OK;
+}
+
+int aux_loglik_grad(aux_model* m, const void* ytilde, double* logZ, double* g_mu, double* g_Phi,
+                    double* g_cholSigma, double* g_delta, void* stream) {
+  if (!m || !ytilde || !g_mu || !g_Phi || !g_cholSigma || !g_delta) return AUX_E_INVALID_ARG;
+  if (!m->grad_ok) return AUX_E_UNSUPPORTED;
+  m->stream = (cudaStream_t)stream;
+  const size_t es = m->esz, DP = m->DP, nbC = (size_t)m->C * m->nb;
+  int rc = AUX_OK;
+  if (!m->Sig) rc = dev_alloc(m, &m->Sig, (size_t)m->C * m->T * DP * DP * es);
+  if (!rc && !m->sgu) rc = dev_alloc(m, &m->sgu, nbC * (2 * DP * DP + DP) * es);
+  if (!rc && !m->gpart) rc = dev_alloc(m, &m->gpart, nbC * (2 * DP * DP + DP) * es);
+  if (!rc && !m->opart) rc = dev_alloc(m, (void**)&m->opart, nbC * sizeof(double));
+  if (!rc && !m->s0) rc = dev_alloc(m, &m->s0, (size_t)m->C * (DP * DP + DP) * es);
+  if (rc) return rc;
+  return m->ops->loglik_grad(m, ytilde, logZ, g_mu, g_Phi, g_cholSigma, g_delta, m->stream);
 }
 
 int aux_get_status(aux_model* m, int32_t* per_chain_status) {

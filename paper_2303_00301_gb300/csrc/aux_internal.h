@@ -29,6 +29,11 @@ struct aux_model {
   void *G = nullptr, *U = nullptr, *gu = nullptr;
   double *fq = nullptr, *fld = nullptr, *mh_part = nullptr, *lz_part = nullptr;
   int32_t *status_iter = nullptr, *status = nullptr;
+  // gradient (aux_loglik_grad): theta constants and lazily allocated smoother buffers
+  int grad_ok = 0;           // the model has the SV parameterisation
+  double *gconst = nullptr;  // mu, phi, L, Q, Q^{-1}, P0^{-1} (FP64, unpadded)
+  void *Sig = nullptr, *sgu = nullptr, *gpart = nullptr, *s0 = nullptr;
+  double *opart = nullptr;
   const AuxOps *ops = nullptr;
   std::vector<void *> allocs;
   // optional per-launch CUDA-event timing (aux_set_profiling)
@@ -40,7 +45,7 @@ struct aux_model {
 
 // kernel kinds reported by aux_read_profile (order of AUX_PROFILE_* in the header)
 enum { PK_LINEARISE = 0, PK_TEMPLATE, PK_REDUCE, PK_SCAN, PK_APPLY, PK_BACKWARD, PK_MH, PK_SUM,
-       PK_COUNT };
+       PK_SMOOTH, PK_GRAD, PK_COUNT };
 
 // bracket a launch with events on its stream when profiling is on
 struct ProfScope {
@@ -69,6 +74,8 @@ struct AuxOps {
   int (*loglik)(aux_model *, const void *yt, double *logZ, void *mf, void *Pf, cudaStream_t);
   int (*sample_path)(aux_model *, const void *yt, const void *eps, uint64_t iter, void *xs,
                      double *logZ, cudaStream_t);
+  int (*loglik_grad)(aux_model *, const void *yt, double *logZ, double *g_mu, double *g_phi,
+                     double *g_L, double *g_delta, cudaStream_t);
 };
 
 const AuxOps *aux_ops_f32(int DP);

@@ -54,7 +54,8 @@ enum : int {
   APPLY_EPI = 1,       // backward elements G_t, U_t and their block aggregates
   APPLY_STORE_Q = 2,   // store per-step quadratic form and log-determinant
   APPLY_REV_DIFF = 4,  // accumulate log-likelihood differences against stored terms
-  APPLY_LOGZ = 8       // accumulate log-likelihood terms
+  APPLY_LOGZ = 8,      // accumulate log-likelihood terms
+  APPLY_SMOOTH = 16    // noise-free U_t and Sigma_t stored (RTS smoother quantities)
 };
 
 template <typename Real, int DP> struct Sizes {
@@ -542,6 +543,7 @@ template <typename Real> struct ApplyArgs {
   Real* Pf;             // [C][T][d][d] or null
   const Real* eps;      // [C][T][d] or null
   uint64_t iter;
+  Real* Sig;            // [C][T][DP*DP] backward covariances (APPLY_SMOOTH) or null
 };
 
 template <typename Real, int DP>
@@ -627,7 +629,7 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
 
   auto backward_noise = [&](int t) {
     Real ei = 0;
-    if (lane < p.d) {
+    if (lane < p.d && !(a.flags & APPLY_SMOOTH)) {
       ei = a.eps ? a.eps[((long)c * p.nT + t) * p.d + lane]
                  : philox_normal<Real>(p.seed, (uint32_t)c, a.iter, PURPOSE_BACKWARD, (uint32_t)t, lane);
     }
@@ -670,6 +672,8 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
     Real sig[DP];
     ld_row<Real, DP>(SP, row, sig);
     mm_col<Real, DP, true, true>(SY, row, SY, sig);
+    if ((a.flags & APPLY_SMOOTH) && act)
+      st_vec<Real, DP>(a.Sig + ((long)c * p.nT + t) * DP * DP + row * DP, sig);
     {
       Real rr[DP];
       ld_col<Real, DP>(SY, row, rr);
@@ -778,6 +782,8 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
       // last state: G_{T-1} = 0, U_{T-1} = m^f + chol(P^f) eps
       Real pf[DP];
       ld_row<Real, DP>(SP, row, pf);
+      if ((a.flags & APPLY_SMOOTH) && act)
+        st_vec<Real, DP>(a.Sig + ((long)c * p.nT + e) * DP * DP + row * DP, pf);
       backward_noise(e);
       const Real le = chol_rot<Real, DP>(pf, SL, nullptr, nullptr, vdA, veps, p.d, lane, &bad);
       Real g0[DP];

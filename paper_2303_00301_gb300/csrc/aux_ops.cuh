@@ -2,7 +2,7 @@
 #pragma once
 #include <cmath>
 
-#include "aux_kernels.cuh"
+#include "aux_grad.cuh"
 
 namespace auxk {
 namespace {
@@ -54,6 +54,12 @@ struct Ops {
     e = cudaFuncSetAttribute(k_filter_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Z::APP_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_sample_backward<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Z::BWD_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_smooth_reduce<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GradSizes<Real, DP>::RED_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_smooth_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GradSizes<Real, DP>::APP_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_grad_final<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     return cuda_ok(e);
   }
 
@@ -145,8 +151,39 @@ struct Ops {
     return cuda_ok(cudaGetLastError());
   }
 
+  // gradient of log Z w.r.t. (mu, phi, L, delta): forward filter storing the
+  // noise-free backward elements and Sigma_t, smoother aggregates, smoother
+  // sweep with the score statistics, FP64 reduction per chain
+  static int loglik_grad(aux_model* m, const void* yt, double* logZ, double* g_mu, double* g_phi,
+                         double* g_L, double* g_delta, cudaStream_t st) {
+    using GZ = GradSizes<Real, DP>;
+    const KP<Real> p = make_kp<Real>(m);
+    ApplyArgs<Real> a = apply_args(m, APPLY_EPI | APPLY_LOGZ | APPLY_SMOOTH, 0);
+    a.Sig = (Real*)m->Sig;
+    filter(m, p, (const Real*)yt, a, st);
+    if (logZ) { ProfScope ps(m, PK_SUM, st); k_sum_parts<<<m->C, 128, 0, st>>>(m->lz_part, m->nb, logZ); }
+    SmoothArgs<Real> sa{};
+    sa.G = (const Real*)m->G; sa.U = (const Real*)m->U; sa.Sig = (const Real*)m->Sig;
+    sa.yt = (const Real*)yt; sa.sgu = (Real*)m->sgu; sa.gpart = (Real*)m->gpart;
+    sa.opart = m->opart; sa.s0 = (Real*)m->s0;
+    const int n = items(m);
+    {
+      ProfScope ps(m, PK_SMOOTH, st);
+      k_smooth_reduce<Real, DP><<<(n + GZ::WPC - 1) / GZ::WPC, 32 * GZ::WPC, GZ::RED_SMEM, st>>>(p, sa);
+      k_smooth_apply<Real, DP><<<(n + GZ::WPC - 1) / GZ::WPC, 32 * GZ::WPC, GZ::APP_SMEM, st>>>(p, sa);
+    }
+    GradOut go{g_mu, g_phi, g_L, g_delta};
+    const size_t fsm = (size_t)(5 * m->d * m->d + 2 * m->d + 32) * sizeof(double);
+    {
+      ProfScope ps(m, PK_GRAD, st);
+      k_grad_final<Real, DP><<<m->C, 256, fsm, st>>>(p, (const Real*)m->gpart, m->opart,
+                                                     (const Real*)m->s0, m->gconst, m->delta, go);
+    }
+    return cuda_ok(cudaGetLastError());
+  }
+
   static const AuxOps* table() {
-    static const AuxOps t = {&prepare, &kalman_step, &loglik, &sample_path};
+    static const AuxOps t = {&prepare, &kalman_step, &loglik, &sample_path, &loglik_grad};
     return &t;
   }
 };
