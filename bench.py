@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--workload", default="sv_d30_T1024", choices=sorted(WORKLOADS))
     ap.add_argument("--block-len", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the shared-covariance (batched) measurement")
     ap.add_argument("--cpu-sample-chains", type=int, default=0,
                     help="chain-steps in the CPU baseline sample (0 = 2 per core)")
     return ap.parse_args()
@@ -279,6 +281,44 @@ def run_ours(args):
     value = world * C * T * args.steps / (total_ms / 1e3)
     accept_rate = acc.float().mean().item() / args.steps
 
+    # the same workload in the shared-covariance (batched) execution mode
+    batched = None
+    if not args.no_batched:
+        sb = AuxKalman(wl, dtype=w["dtype"], block_len=args.block_len, shared_cov=True)
+        xb = torch.tensor(wl.x_init, dtype=tdt, device="cuda")
+        accb = torch.zeros(C, dtype=torch.int32, device="cuda")
+        itb = 0
+        for _ in range(args.warmup):
+            sb.step(xb, 1, iter0=itb, accept_count=accb)
+            itb += 1
+        torch.cuda.synchronize()
+        accb.zero_()
+        if world > 1:
+            dist.barrier()
+        B.aux_set_profiling(sb.handle, True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            sb.step(xb, 1, iter0=itb, accept_count=accb)
+            evs[k][1].record(stream)
+            itb += 1
+        torch.cuda.synchronize()
+        B.aux_set_profiling(sb.handle, False)
+        profb = B.aux_read_profile(sb.handle)
+        tb = torch.tensor([sum(a.elapsed_time(b) for a, b in evs)], dtype=torch.float64,
+                          device="cuda")
+        if world > 1:
+            dist.all_reduce(tb, op=dist.ReduceOp.MAX)
+        batched = {"mode": "shared covariance (AUX_MODE_SHARED_COV)",
+                   "value": world * C * T * args.steps / (tb.item() / 1e3), "unit": UNIT,
+                   "ms_per_step": tb.item() / args.steps,
+                   "accept_rate": accb.float().mean().item() / args.steps,
+                   "kernel_ms_per_step": {k: v[0] / args.steps for k, v in profb.items() if v[1]},
+                   "gpu_launches": int(sum(v[1] for v in profb.values()))}
+        sb.close()
+
     # end to end through the public API from pinned host buffers
     x_host = torch.tensor(wl.x_init, dtype=tdt).pin_memory()
     la_host = torch.zeros(C, dtype=torch.float64).pin_memory()
@@ -346,7 +386,7 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                         "d2h_bytes_per_step": bo},
                 "gpu_launches": int(sum(v[1] for v in prof.values())),
-                "roofline": roofline, "cpu_baseline": cpu, "clocks": ck,
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": ck, "batched": batched,
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
                 "accept_rate": accept_rate, "status": int(rc),
                 "step_ms_median": statistics.median(step_ms)}

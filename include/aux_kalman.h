@@ -66,6 +66,10 @@ extern "C" {
 #define AUX_F32 0
 #define AUX_F64 1
 
+/* execution modes (aux_set_mode) */
+#define AUX_MODE_PER_CHAIN  0  /* every chain runs its own covariance recursion (default) */
+#define AUX_MODE_SHARED_COV 1  /* chains of the model share one covariance recursion per scan block */
+
 /* emission models */
 #define AUX_EMIS_LINEAR_GAUSSIAN 0
 #define AUX_EMIS_SV              1
@@ -146,6 +150,17 @@ int aux_sample_path(aux_model *m, const void *ytilde, const void *eps, uint64_t 
  * call (it allocates C*T*d^2 elements for the backward covariances). */
 int aux_loglik_grad(aux_model *m, const void *ytilde, double *logZ, double *g_mu, double *g_Phi,
                     double *g_cholSigma, double *g_delta, void *stream);
+
+/* Choose how the filter and the backward sampler are executed. Both modes
+ * compute the same quantities. With the first-order proposal of Section 2.2
+ * and Gaussian dynamics the covariance part of every filtering element, and
+ * of every backward element, depends only on (F, Q, P0, delta), so all chains
+ * of one handle run identical covariance recursions: AUX_MODE_PER_CHAIN runs
+ * them once per chain (the general path, needed when covariances depend on
+ * the chain's state), AUX_MODE_SHARED_COV runs them once per group of chains
+ * and keeps only the per-chain vector recursions separate. aux_loglik_grad
+ * always runs per chain. Errors: INVALID_ARG. */
+int aux_set_mode(aux_model *m, int32_t mode);
 
 /* Replace the model of an existing handle (same dtype, d_x, T, n_chains,
  * emis_kind, y_per_chain): validates as aux_init_model, then overwrites the

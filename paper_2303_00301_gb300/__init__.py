@@ -16,7 +16,8 @@ def _load_binding():
 class AuxKalman:
     """Owns an ``aux_model`` handle for one workload (torch is used for memory only)."""
 
-    def __init__(self, workload, dtype="f32", seed=None, n_chains=None, block_len=0, stream=None):
+    def __init__(self, workload, dtype="f32", seed=None, n_chains=None, block_len=0, stream=None,
+                 shared_cov=False):
         import torch
         b = _load_binding()
         self.b = b
@@ -31,6 +32,8 @@ class AuxKalman:
             F=workload.F, b=workload.b, Q=workload.Q, y=workload.y, delta=workload.delta,
             emis_kind=workload.emission, dtype=self.dtype_code, R_y=workload.Ry,
             obs_mask=workload.mask, block_len=block_len, seed=self.seed, stream=stream)
+        if shared_cov:
+            b.aux_set_mode(self.handle, b.AUX_MODE_SHARED_COV)
 
     def step(self, x, n_iters=1, iter0=0, accept_count=None, log_alpha=None, stream=None):
         self.b.aux_kalman_step(self.handle, x, n_iters, iter0, accept_count, log_alpha, stream)

@@ -20,6 +20,7 @@ AUX_E_TOO_LARGE = 8
 AUX_NOALLOC_SCRATCH_BYTES = 32 << 20
 AUX_F32, AUX_F64 = 0, 1
 AUX_EMIS_LINEAR_GAUSSIAN, AUX_EMIS_SV = 0, 1
+AUX_MODE_PER_CHAIN, AUX_MODE_SHARED_COV = 0, 1
 
 _dbl_p = ctypes.POINTER(ctypes.c_double)
 _u8_p = ctypes.POINTER(ctypes.c_uint8)
@@ -79,6 +80,8 @@ def _load():
     lib.aux_read_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
     lib.aux_read_profile.restype = ctypes.c_int
+    lib.aux_set_mode.argtypes = [vp, ctypes.c_int32]
+    lib.aux_set_mode.restype = ctypes.c_int
     lib.aux_loglik_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.aux_loglik_grad.restype = ctypes.c_int
     lib.aux_set_model_params.argtypes = [vp, ctypes.POINTER(aux_model_desc)]
@@ -160,6 +163,10 @@ def aux_init_model(*, d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind, dt
     _check(rc, "aux_init_model")
     del keep
     return handle
+
+
+def aux_set_mode(handle, mode):
+    _check(LIB.aux_set_mode(handle, int(mode)), "aux_set_mode")
 
 
 def aux_loglik_grad(handle, ytilde, g_mu, g_Phi, g_cholSigma, g_delta, logZ=None, stream=None):

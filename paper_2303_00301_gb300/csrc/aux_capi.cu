@@ -295,7 +295,8 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
   if (!rc) rc = dev_alloc(m, &m->agg1, nbC * aux_es(DP) * es);
   if (!rc) rc = dev_alloc(m, &m->G, (size_t)C * T * DP * DP * es);
   if (!rc) rc = dev_alloc(m, &m->U, (size_t)C * T * DP * es);
-  if (!rc) rc = dev_alloc(m, &m->gu, nbC * aux_gs(DP) * es);
+  if (!rc) rc = dev_alloc(m, &m->gum, nbC * DP * DP * es);
+  if (!rc) rc = dev_alloc(m, &m->guv, nbC * DP * es);
   if (!rc) rc = dev_alloc(m, (void**)&m->fq, (size_t)C * T * sizeof(double));
   if (!rc) rc = dev_alloc(m, (void**)&m->fld, (size_t)C * T * sizeof(double));
   if (!rc) rc = dev_alloc(m, (void**)&m->mh_part, nbC * sizeof(double));
@@ -330,6 +331,12 @@ int aux_sample_path(aux_model* m, const void* ytilde, const void* eps, uint64_t 
   if (!m || !ytilde || !xstar) return AUX_E_INVALID_ARG;
   m->stream = (cudaStream_t)stream;
   return m->ops->sample_path(m, ytilde, eps, iteration, xstar, logZ, m->stream);
+}
+
+int aux_set_mode(aux_model* m, int32_t mode) {
+  if (!m || (mode != AUX_MODE_PER_CHAIN && mode != AUX_MODE_SHARED_COV)) return AUX_E_INVALID_ARG;
+  m->mode = mode;
+  return AUX_OK;
 }
 
 int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {

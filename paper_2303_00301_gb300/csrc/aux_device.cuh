@@ -532,6 +532,118 @@ __device__ __forceinline__ void bsolve_rot(const T* LR, const T* inv_diag, T (&r
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register-tiled product for p in {16, 32}: lane (r, q) = (lane / 4, lane % 4)
+// owns the output tile rows TR r .. TR r + TR - 1, columns TC q .. TC q + TC - 1
+// (TR = p / 8, TC = p / 4; a 4 x 8 tile at p = 32), so each k needs TR + TC
+// operand values per lane instead of p + 1.
+//   Out = Init (+/-) A^T B   when A_COLS (left operand: columns of slot A)
+//   Out = Init (+/-) A B     otherwise (left operand: rows of slot A)
+// Init may be null (zero) or equal to Out. The caller orders the slot accesses
+// (a __syncwarp() before the call if Out/Init were just written by other
+// lanes, and after it before other lanes read Out).
+// ---------------------------------------------------------------------------
+template <typename T, int DP> struct Tile {
+  static constexpr int TR = DP / 8, TC = DP / 4;
+};
+
+// N contiguous elements at an address aligned to N * sizeof(T) (N * sizeof(T) <= 16 or a
+// multiple of 16): one or more vector loads/stores
+template <typename T, int N>
+__device__ __forceinline__ void ldn(const T* p, T (&r)[N]) {
+  if constexpr (N * sizeof(T) % 16 == 0) {
+    using V = typename Vec16<T>::V;
+    constexpr int M = Vec16<T>::N;
+#pragma unroll
+    for (int q = 0; q < N / M; ++q) unpack<T>(reinterpret_cast<const V*>(p)[q], &r[q * M]);
+  } else if constexpr (N == 2 && sizeof(T) == 4) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    r[0] = v.x; r[1] = v.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) r[i] = p[i];
+  }
+}
+template <typename T, int N>
+__device__ __forceinline__ void stn(T* p, const T (&r)[N]) {
+  if constexpr (N * sizeof(T) % 16 == 0) {
+    using V = typename Vec16<T>::V;
+    constexpr int M = Vec16<T>::N;
+#pragma unroll
+    for (int q = 0; q < N / M; ++q) reinterpret_cast<V*>(p)[q] = pack<T>(&r[q * M]);
+  } else if constexpr (N == 2 && sizeof(T) == 4) {
+    *reinterpret_cast<float2*>(p) = make_float2(r[0], r[1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) p[i] = r[i];
+  }
+}
+
+template <typename T, int DP, bool A_COLS, bool NEG>
+__device__ __forceinline__ void mm_tile_regs(const T* A, const T* B, T (&acc)[Tile<T, DP>::TR][Tile<T, DP>::TC],
+                                             int lane) {
+  constexpr int TR = Tile<T, DP>::TR, TC = Tile<T, DP>::TC, LD = Lay<T, DP>::LD;
+  static_assert(DP == 16 || DP == 32, "tiled product needs p = 16 or 32");
+  const int r0 = (lane >> 2) * TR, c0 = (lane & 3) * TC;
+#pragma unroll 1
+  for (int k0 = 0; k0 < DP; k0 += 4) {
+    T a[4][TR];
+    if (A_COLS) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) ldn<T, TR>(A + (k0 + kk) * LD + r0, a[kk]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < TR; ++i) {
+        T r4[4];
+        ldn<T, 4>(A + (r0 + i) * LD + k0, r4);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) a[kk][i] = r4[kk];
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      T b[TC];
+      ldn<T, TC>(B + (k0 + kk) * LD + c0, b);
+#pragma unroll
+      for (int i = 0; i < TR; ++i) {
+        const T ai = NEG ? -a[kk][i] : a[kk][i];
+#pragma unroll
+        for (int j = 0; j < TC; ++j) acc[i][j] = fma(ai, b[j], acc[i][j]);
+      }
+    }
+  }
+}
+
+template <typename T, int DP>
+__device__ __forceinline__ void tile_load(const T* S, T (&acc)[Tile<T, DP>::TR][Tile<T, DP>::TC], int lane) {
+  constexpr int TR = Tile<T, DP>::TR, TC = Tile<T, DP>::TC, LD = Lay<T, DP>::LD;
+  const int r0 = (lane >> 2) * TR, c0 = (lane & 3) * TC;
+#pragma unroll
+  for (int i = 0; i < TR; ++i) {
+    if (S) ldn<T, TC>(S + (r0 + i) * LD + c0, acc[i]);
+    else
+#pragma unroll
+      for (int j = 0; j < TC; ++j) acc[i][j] = (T)0;
+  }
+}
+
+template <typename T, int DP>
+__device__ __forceinline__ void tile_store(T* S, const T (&acc)[Tile<T, DP>::TR][Tile<T, DP>::TC], int lane) {
+  constexpr int TR = Tile<T, DP>::TR, TC = Tile<T, DP>::TC, LD = Lay<T, DP>::LD;
+  const int r0 = (lane >> 2) * TR, c0 = (lane & 3) * TC;
+#pragma unroll
+  for (int i = 0; i < TR; ++i) stn<T, TC>(S + (r0 + i) * LD + c0, acc[i]);
+}
+
+template <typename T, int DP, bool A_COLS, bool NEG>
+__device__ __forceinline__ void mm_tile_to_slot(const T* A, const T* B, const T* Init, T* Out, int lane) {
+  T acc[Tile<T, DP>::TR][Tile<T, DP>::TC];
+  tile_load<T, DP>(Init, acc, lane);
+  mm_tile_regs<T, DP, A_COLS, NEG>(A, B, acc, lane);
+  __syncwarp();
+  tile_store<T, DP>(Out, acc, lane);
+}
+
 template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);

@@ -14,6 +14,7 @@ struct aux_model {
   int dtype = 0, d = 0, DP = 0, T = 0, C = 0, emis = 0, y_per_chain = 0;
   int L = 0, nb = 0;
   int fdiag = 0;             // F has no off-diagonal entries
+  int mode = AUX_MODE_PER_CHAIN;
   double delta = 0.0;
   uint64_t seed = 0;
   size_t esz = 0;            // bytes per compute-type element
@@ -26,7 +27,7 @@ struct aux_model {
   // workspace
   void *u = nullptr, *v = nullptr, *yt = nullptr, *xs = nullptr, *yts = nullptr;
   void *agg0 = nullptr, *agg1 = nullptr;
-  void *G = nullptr, *U = nullptr, *gu = nullptr;
+  void *G = nullptr, *U = nullptr, *gum = nullptr, *guv = nullptr;
   double *fq = nullptr, *fld = nullptr, *mh_part = nullptr, *lz_part = nullptr;
   int32_t *status_iter = nullptr, *status = nullptr;
   // gradient (aux_loglik_grad): theta constants and lazily allocated smoother buffers
@@ -83,4 +84,3 @@ const AuxOps *aux_ops_f64(int DP);
 
 // element counts of the per-block buffers for a padded dimension DP
 inline size_t aux_es(int DP) { return 3u * DP * DP + 2u * DP; }
-inline size_t aux_gs(int DP) { return (size_t)DP * DP + DP; }

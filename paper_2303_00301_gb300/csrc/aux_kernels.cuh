@@ -62,7 +62,7 @@ template <typename Real, int DP> struct Sizes {
   static constexpr int MAT = Lay<Real, DP>::MAT;
   static constexpr int VEC = Lay<Real, DP>::VEC;
   static constexpr int ES = 3 * DP * DP + 2 * DP;   // global element: A, C, J, b, eta
-  static constexpr int GS = DP * DP + DP;           // global backward aggregate: G, U
+
   static constexpr size_t SMEM_MAX = 227 * 1024;
   static constexpr size_t MODEL = (3 * MAT + 2 * VEC) * sizeof(Real);   // F, F^T, Q, b, diag F
   static constexpr int cap(size_t fixed, size_t per_warp, int want) {
@@ -121,38 +121,35 @@ __global__ void k_linearise(KP<Real> p, const Real* __restrict__ x, Real* __rest
 }
 
 // ---------------------------------------------------------------------------
-// Element operator a_i (x) a_j in Cholesky form (see the header comment).
+// Element operator a_i (x) a_j in Cholesky form (see the header comment), in
+// three parts so that the matrix parts and the per-chain vector part can run
+// on different warps (combine_general runs all three on one warp).
 // Aggregate i: SA (A), SC (C), jreg (row `lane` of J), vb, veta  (in/out).
 // Element j:   SAe, SCe, SJe slots and vbe, vetae vectors (read only).
 // Scratch: SU, S2, S3, S4 slots, vt (4 vectors), vdiag.
 // ---------------------------------------------------------------------------
+
+// matrix part 1: U = chol(C_i) (rows in SU), N = I + U^T J_j U, B = U L_N^{-T}
+// (rows in S2), P = A_j B (transposed in S3)
 template <typename Real, int DP>
-__device__ void combine_general(Real* SA, Real* SC, Real (&jreg)[DP], Real* vb, Real* veta,
-                                const Real* SAe, const Real* SCe, const Real* SJe,
-                                const Real* vbe, const Real* vetae, Real* SU, Real* S2, Real* S3,
-                                Real* S4, Real* vt, Real* vdiag, int d, int lane, int* bad) {
-  constexpr int VEC = Lay<Real, DP>::VEC, LD = Lay<Real, DP>::LD;
+__device__ void combine_matrix_1(const Real* SC, const Real* SAe, const Real* SJe, Real* SU,
+                                 Real* S2, Real* S3, Real* S4, Real* vdiag, int d, int lane,
+                                 int* bad) {
+  constexpr int LD = Lay<Real, DP>::LD;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
-  Real* vr = vt;
-  Real* vs = vt + VEC;
-  Real* vw = vt + 2 * VEC;
-  Real* vrq = vt + 3 * VEC;
   __syncwarp();
-  // 1. U = chol(C_i): rows of U in SU (S2 is the factorisation's working slot)
   {
     Real a[DP];
     ld_row<Real, DP>(SC, row, a);
     chol_rot<Real, DP>(a, S2, SU, nullptr, vdiag, nullptr, d, lane, bad);
   }
-  // 2. T1 = J_j U -> S3
   {
     Real t1[DP];
     mm_row<Real, DP>(SJe + row * LD, SU, t1);
     st_row<Real, DP>(S3, row, t1, act);
   }
   __syncwarp();
-  // 3-4. N = I + U^T T1 (eigenvalues >= 1); its factor in S4
   {
     Real n[DP];
     mm_col<Real, DP>(SU, row, S3, n);
@@ -160,22 +157,37 @@ __device__ void combine_general(Real* SA, Real* SC, Real (&jreg)[DP], Real* vb, 
     for (int j = 0; j < DP; ++j) n[j] += (j == lane) ? (Real)1 : (Real)0;
     chol_rot<Real, DP>(n, S4, nullptr, nullptr, vdiag, nullptr, d, lane, bad);
   }
-  // 5. B = U L^{-T}: row i solves L b = (row i of U)^T; rows of B in S2
   {
     Real r[DP];
     ld_row<Real, DP>(SU, row, r);
     fsolve_rot<Real, DP, false>(S4, vdiag, r, S2, lane);
   }
   __syncwarp();
-  // 6. P = A_j B, kept transposed in S3 (T1 is dead): row i of P = column i of S3
   {
     Real pr[DP];
     mm_row<Real, DP>(SAe + row * LD, S2, pr);
     __syncwarp();
     st_col<Real, DP>(S3, row, pr, act);
   }
-  // vector parts: r = eta_j - J_j b_i, s = B^T r, b_new, w = B s, rq = r - J_j w
+  __syncwarp();
+}
+
+// vector part (one chain): r = eta_j - J_j b_i, s = B^T r, b_new = A_j b_i + P s + b_j,
+// w = B s, rq = r - J_j w, eta_new = A_i^T rq + eta_i. Reads SJe, S2 (B), SAe, S3 (P^T),
+// SA (A_i, before matrix part 2 overwrites it); writes vb, veta (via the vt scratch).
+template <typename Real, int DP>
+__device__ void combine_vectors(const Real* SA, const Real* SAe, const Real* SJe, const Real* S2,
+                                const Real* S3, Real* vb, Real* veta, const Real* vbe,
+                                const Real* vetae, Real* vt, int lane) {
+  constexpr int VEC = Lay<Real, DP>::VEC, LD = Lay<Real, DP>::LD;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  Real* vr = vt;
+  Real* vs = vt + VEC;
+  Real* vw = vt + 2 * VEC;
+  Real* vrq = vt + 3 * VEC;
   const Real ri = vetae[row] - dot_row_vec<Real, DP>(SJe + row * LD, vb);
+  __syncwarp();
   if (act) vr[lane] = ri;
   __syncwarp();
   {
@@ -196,7 +208,23 @@ __device__ void combine_general(Real* SA, Real* SC, Real (&jreg)[DP], Real* vb, 
   }
   __syncwarp();
   const Real etanew = dot_col_vec<Real, DP>(SA, row, vrq) + veta[row];
-  // 7. X1 = J_j A_i -> S4 (the factor of N is dead)
+  __syncwarp();
+  if (act) {
+    vb[lane] = bnew;
+    veta[lane] = etanew;
+  }
+  __syncwarp();
+}
+
+// matrix part 2: X1 = J_j A_i, Z = B^T X1, J_new = A_i^T X1 - Z^T Z + J_i,
+// A_new = A_j A_i - P Z (-> SA), C_new = P P^T + C_j (-> SC), J symmetrised.
+template <typename Real, int DP>
+__device__ void combine_matrix_2(Real* SA, Real* SC, Real (&jreg)[DP], const Real* SAe,
+                                 const Real* SCe, const Real* SJe, Real* SU, const Real* S2,
+                                 const Real* S3, Real* S4, int lane) {
+  constexpr int LD = Lay<Real, DP>::LD;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
   {
     Real x1[DP];
     mm_row<Real, DP>(SJe + row * LD, SA, x1);
@@ -204,7 +232,6 @@ __device__ void combine_general(Real* SA, Real* SC, Real (&jreg)[DP], Real* vb, 
     st_row<Real, DP>(S4, row, x1, act);
   }
   __syncwarp();
-  // 8. Z = B^T X1 -> SU (U is dead)
   {
     Real z[DP];
     mm_col<Real, DP>(S2, row, S4, z);
@@ -212,11 +239,9 @@ __device__ void combine_general(Real* SA, Real* SC, Real (&jreg)[DP], Real* vb, 
     st_row<Real, DP>(SU, row, z, act);
   }
   __syncwarp();
-  // 9. J_new = A_i^T X1 - Z^T Z + J_i
   mm_col<Real, DP, true>(SA, row, S4, jreg);
   mm_col<Real, DP, true, true>(SU, row, SU, jreg);
   __syncwarp();
-  // 10. A_new = A_j A_i - P Z -> SA once every lane is done reading A_i
   {
     Real an[DP];
     mm_row<Real, DP>(SAe + row * LD, SA, an);
@@ -224,7 +249,6 @@ __device__ void combine_general(Real* SA, Real* SC, Real (&jreg)[DP], Real* vb, 
     __syncwarp();
     st_row<Real, DP>(SA, row, an, act);
   }
-  // 11. C_new = P P^T + C_j -> SC; J symmetrised through S4 (X1 is dead)
   {
     Real cn[DP];
     ld_row<Real, DP>(SCe, row, cn);
@@ -239,11 +263,17 @@ __device__ void combine_general(Real* SA, Real* SC, Real (&jreg)[DP], Real* vb, 
 #pragma unroll
     for (int j = 0; j < DP; ++j) jreg[j] = (Real)0.5 * (jreg[j] + jc[j]);
   }
-  if (act) {
-    vb[lane] = bnew;
-    veta[lane] = etanew;
-  }
   __syncwarp();
+}
+
+template <typename Real, int DP>
+__device__ void combine_general(Real* SA, Real* SC, Real (&jreg)[DP], Real* vb, Real* veta,
+                                const Real* SAe, const Real* SCe, const Real* SJe,
+                                const Real* vbe, const Real* vetae, Real* SU, Real* S2, Real* S3,
+                                Real* S4, Real* vt, Real* vdiag, int d, int lane, int* bad) {
+  combine_matrix_1<Real, DP>(SC, SAe, SJe, SU, S2, S3, S4, vdiag, d, lane, bad);
+  combine_vectors<Real, DP>(SA, SAe, SJe, S2, S3, vb, veta, vbe, vetae, vt, lane);
+  combine_matrix_2<Real, DP>(SA, SC, jreg, SAe, SCe, SJe, SU, S2, S3, S4, lane);
 }
 
 // symmetrise a register row through a slot: r <- (r + column of the stored matrix) / 2
@@ -364,6 +394,12 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::RED_WPC, 1)
   int bad = 0;
   Real jreg[DP];
   zero<Real, DP>(jreg);
+  constexpr int JTR = DP >= 16 ? Tile<Real, DP>::TR : 1, JTC = DP >= 16 ? Tile<Real, DP>::TC : 1;
+  Real jtile[JTR][JTC];
+#pragma unroll
+  for (int i = 0; i < JTR; ++i)
+#pragma unroll
+    for (int j = 0; j < JTC; ++j) jtile[i][j] = (Real)0;
   {
     Real r[DP];
 #pragma unroll
@@ -437,20 +473,25 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::RED_WPC, 1)
       fsolve_multi<Real, DP, true>(SL, vdiag, r1, SY, r2, SW, rv, vz, lane);
     }
     __syncwarp();
-    {
+    if constexpr (DP >= 16) {
+      // register-tiled: C = P^p - Y^T Y, A = F A - Y^T W, J += W^T W
+      st_row<Real, DP>(SC, row, pprow, act);
+      __syncwarp();
+      mm_tile_to_slot<Real, DP, true, true>(SY, SY, SC, SC, lane);
+      mm_tile_to_slot<Real, DP, true, true>(SY, SW, SX, SA, lane);
+      mm_tile_regs<Real, DP, true, false>(SW, SW, jtile, lane);
+    } else {
       Real cn[DP];
 #pragma unroll
       for (int j = 0; j < DP; ++j) cn[j] = pprow[j];
       mm_col<Real, DP, true, true>(SY, row, SY, cn);
       st_row<Real, DP>(SC, row, cn, act);
-    }
-    {
       Real an[DP];
       ld_row<Real, DP>(SX, row, an);
       mm_col<Real, DP, true, true>(SY, row, SW, an);
       st_row<Real, DP>(SA, row, an, act);
+      mm_col<Real, DP, true>(SW, row, SW, jreg);
     }
-    mm_col<Real, DP, true>(SW, row, SW, jreg);
     const Real bnew = mpi + dot_col_vec<Real, DP>(SY, row, vz);
     const Real etanew = veta[row] + dot_col_vec<Real, DP>(SW, row, vz);
     __syncwarp();
@@ -459,6 +500,12 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::RED_WPC, 1)
       veta[lane] = etanew;
     }
     __syncwarp();
+  }
+  if constexpr (DP >= 16) {
+    __syncwarp();
+    tile_store<Real, DP>(SY, jtile, lane);
+    __syncwarp();
+    ld_row<Real, DP>(SY, row, jreg);
   }
   store_element<Real, DP>(agg + (long)item * Z::ES, SA, SC, jreg, vb, veta, lane);
   if (bad && lane == 0) atomicOr(&p.status_iter[c], ST_NOT_PD);
@@ -535,7 +582,8 @@ template <typename Real> struct ApplyArgs {
   int flags;
   Real* G;              // [C][T][DP*DP]
   Real* U;              // [C][T][DP]
-  Real* gu;             // [C][nb][GS]
+  Real* gum;            // [C][nb][DP*DP] block aggregates G_s ... G_e
+  Real* guv;            // [C][nb][DP]    block aggregates U_s + G_s U_{s+1} + ...
   double* fq;           // [C][T]
   double* fld;          // [C][T]
   double* lz_part;      // [C][nb]
@@ -670,8 +718,14 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
     }
     __syncwarp();
     Real sig[DP];
-    ld_row<Real, DP>(SP, row, sig);
-    mm_col<Real, DP, true, true>(SY, row, SY, sig);
+    if constexpr (DP >= 16) {
+      mm_tile_to_slot<Real, DP, true, true>(SY, SY, SP, SL, lane);   // Sigma = P^f - Y^T Y
+      __syncwarp();
+      ld_row<Real, DP>(SL, row, sig);
+    } else {
+      ld_row<Real, DP>(SP, row, sig);
+      mm_col<Real, DP, true, true>(SY, row, SY, sig);
+    }
     if ((a.flags & APPLY_SMOOTH) && act)
       st_vec<Real, DP>(a.Sig + ((long)c * p.nT + t) * DP * DP + row * DP, sig);
     {
@@ -710,13 +764,23 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
     Real lg = (lane < p.d) ? -log(vdB[lane]) : (Real)0;
     lg = warp_sum<Real>(lg);
     Real pf[DP];
+    if constexpr (DP >= 16) {
+      __syncwarp();
+      st_row<Real, DP>(SP, row, pprow, act);
+      __syncwarp();
+      mm_tile_to_slot<Real, DP, true, true>(SY, SY, SP, SP, lane);   // P^f = P^p - Y_s^T Y_s
+      if (act) vm[lane] = mfi;
+      __syncwarp();
+      ld_row<Real, DP>(SP, row, pf);
+    } else {
 #pragma unroll
-    for (int j = 0; j < DP; ++j) pf[j] = pprow[j];
-    mm_col<Real, DP, true, true>(SY, row, SY, pf);
-    __syncwarp();
-    st_row<Real, DP>(SP, row, pf, act);
-    if (act) vm[lane] = mfi;
-    __syncwarp();
+      for (int j = 0; j < DP; ++j) pf[j] = pprow[j];
+      mm_col<Real, DP, true, true>(SY, row, SY, pf);
+      __syncwarp();
+      st_row<Real, DP>(SP, row, pf, act);
+      if (act) vm[lane] = mfi;
+      __syncwarp();
+    }
     const double q = (double)qz, ld = 2.0 * (double)lg;
     const long ct = (long)c * p.nT + t;
     if (lane == 0) {
@@ -793,10 +857,9 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
       __syncwarp();
       store_backward(e, vm[row] + le);
     }
-    Real* gk = a.gu + ((long)c * p.nb + k) * Z::GS;
     if (act) {
-      st_vec<Real, DP>(gk + row * DP, ghat);
-      gk[DP * DP + lane] = uhat;
+      st_vec<Real, DP>(a.gum + ((long)c * p.nb + k) * DP * DP + row * DP, ghat);
+      a.guv[((long)c * p.nb + k) * DP + lane] = uhat;
     }
   }
   if ((a.flags & (APPLY_REV_DIFF | APPLY_LOGZ)) && lane == 0) a.lz_part[(long)c * p.nb + k] = lz_acc;
@@ -810,9 +873,11 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
 // sum of gamma(x*) - gamma(x) + sum_t [v.(u - x*) + r|v|^2/2] - [v*.(u - x) + r|v*|^2/2].
 // ---------------------------------------------------------------------------
 template <typename Real> struct BackArgs {
-  const Real* G;
-  const Real* U;
-  const Real* gu;
+  const Real* G;        // G_t at G + c * g_cs + t * DP*DP
+  const Real* U;        // [C][T][DP]
+  const Real* gum;      // block aggregate matrices at gum + c * gm_cs + k * DP*DP
+  const Real* guv;      // [C][nb][DP]
+  long g_cs, gm_cs;     // chain strides (0 when the matrices are shared by all chains)
   Real* xs;
   int mh;
   const Real* x;
@@ -843,16 +908,14 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::BWD_WPC)
   Real* vxs = vx + VEC;
   Real xi = 0;
   if (k < p.nb - 1) {
-    const Real* gl = a.gu + ((long)c * p.nb + (p.nb - 1)) * Z::GS;
-    xi = gl[DP * DP + row];
+    xi = a.guv[((long)c * p.nb + (p.nb - 1)) * DP + row];
     for (int kk = p.nb - 2; kk > k; --kk) {
-      const Real* gk = a.gu + ((long)c * p.nb + kk) * Z::GS;
       __syncwarp();
       if (act) vx[lane] = xi;
       __syncwarp();
       Real g[DP];
-      ld_vec<Real, DP>(gk + row * DP, g);
-      xi = dot_rv<Real, DP>(g, vx) + gk[DP * DP + row];
+      ld_vec<Real, DP>(a.gum + (long)c * a.gm_cs + (long)kk * DP * DP + row * DP, g);
+      xi = dot_rv<Real, DP>(g, vx) + a.guv[((long)c * p.nb + kk) * DP + row];
     }
   }
   double acc = 0.0;
@@ -865,7 +928,7 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::BWD_WPC)
       if (act) vx[lane] = xi;
       __syncwarp();
       Real g[DP];
-      ld_vec<Real, DP>(a.G + ct * DP * DP + row * DP, g);
+      ld_vec<Real, DP>(a.G + (long)c * a.g_cs + (long)t * DP * DP + row * DP, g);
       xi = dot_rv<Real, DP>(g, vx) + a.U[ct * DP + row];
     }
     if (lane < p.d) a.xs[ct * p.d + lane] = xi;

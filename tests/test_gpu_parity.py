@@ -66,15 +66,16 @@ FILTER_CASES = [
 ]
 
 
+@pytest.mark.parametrize("shared", [False, True])
 @pytest.mark.parametrize("d,T,C,L,dt", FILTER_CASES)
-def test_loglik_filter_parity(d, T, C, L, dt):
+def test_loglik_filter_parity(d, T, C, L, dt, shared):
     wl = _lgssm_workload(d, T, C, seed=100 + d * T)
     tdt = torch.float64 if dt == "f64" else torch.float32
     tol = 1e-9 if dt == "f64" else 1e-4
     tol_z = 1e-9 if dt == "f64" else 1e-5
     rng = np.random.default_rng(d + T)
     yt = rng.standard_normal((C, T, d))
-    s = AuxKalman(wl, dtype=dt, block_len=L)
+    s = AuxKalman(wl, dtype=dt, block_len=L, shared_cov=shared)
     logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
     mf = torch.zeros((C, T, d), dtype=tdt, device="cuda")
     Pf = torch.zeros((C, T, d, d), dtype=tdt, device="cuda")
@@ -90,15 +91,16 @@ def test_loglik_filter_parity(d, T, C, L, dt):
     s.close()
 
 
+@pytest.mark.parametrize("shared", [False, True])
 @pytest.mark.parametrize("d,T,C,L,dt", FILTER_CASES)
-def test_sample_path_parity(d, T, C, L, dt):
+def test_sample_path_parity(d, T, C, L, dt, shared):
     wl = _lgssm_workload(d, T, C, seed=200 + d * T)
     tdt = torch.float64 if dt == "f64" else torch.float32
     tol = 1e-9 if dt == "f64" else 1e-4
     rng = np.random.default_rng(7 * d + T)
     yt = rng.standard_normal((C, T, d))
     eps = rng.standard_normal((C, T, d))
-    s = AuxKalman(wl, dtype=dt, block_len=L)
+    s = AuxKalman(wl, dtype=dt, block_len=L, shared_cov=shared)
     xs = torch.zeros((C, T, d), dtype=tdt, device="cuda")
     logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
     s.sample_path(_tt(yt, tdt), xs, eps=_tt(eps, tdt), logZ=logZ)
@@ -130,14 +132,14 @@ def test_backward_noise_is_the_philox_stream(dt):
     s.close()
 
 
-def _step_and_compare(wl, dt, L, n_iters, chains=None, tol_x=None, tol_la=None):
+def _step_and_compare(wl, dt, L, n_iters, chains=None, tol_x=None, tol_la=None, shared=False):
     """Step all chains on the GPU; replay the chosen chains on the oracle from the same state.
 
     Each oracle step starts from the GPU's state before that step, so a rare
     near-tie decision difference in FP32 does not make the paths diverge."""
     C = wl.n_chains
     tdt = torch.float64 if dt == "f64" else torch.float32
-    s = AuxKalman(wl, dtype=dt, block_len=L)
+    s = AuxKalman(wl, dtype=dt, block_len=L, shared_cov=shared)
     x = _tt(wl.x_init, tdt)
     la = torch.zeros(C, dtype=torch.float64, device="cuda")
     model = _oracle_model(wl)
@@ -170,31 +172,54 @@ def _step_and_compare(wl, dt, L, n_iters, chains=None, tol_x=None, tol_la=None):
     return mismatches, max_dla
 
 
-def test_kalman_step_parity_linear_gaussian_f64():
+@pytest.mark.parametrize("shared", [False, True])
+def test_kalman_step_parity_linear_gaussian_f64(shared):
     wl = workloads.linear_gaussian(d=2, T=64, n_chains=4)
-    _step_and_compare(wl, "f64", L=8, n_iters=4, tol_x=1e-9, tol_la=1e-8)
+    _step_and_compare(wl, "f64", L=8, n_iters=4, tol_x=1e-9, tol_la=1e-8, shared=shared)
 
 
-def test_kalman_step_parity_masked_toy_f64():
+@pytest.mark.parametrize("shared", [False, True])
+def test_kalman_step_parity_masked_toy_f64(shared):
     wl = workloads.two_step_toy(rho=0.7, r2=0.3, n_chains=3)
-    _step_and_compare(wl, "f64", L=1, n_iters=4, tol_x=1e-9, tol_la=1e-8)
+    _step_and_compare(wl, "f64", L=1, n_iters=4, tol_x=1e-9, tol_la=1e-8, shared=shared)
 
 
-def test_kalman_step_parity_sv_f64():
+@pytest.mark.parametrize("shared", [False, True])
+def test_kalman_step_parity_sv_f64(shared):
     wl = workloads.stochastic_volatility(d=6, T=45, n_chains=3, delta=0.05)
-    _step_and_compare(wl, "f64", L=8, n_iters=3, tol_x=1e-9, tol_la=1e-8)
+    _step_and_compare(wl, "f64", L=8, n_iters=3, tol_x=1e-9, tol_la=1e-8, shared=shared)
 
 
-def test_kalman_step_parity_sv_f32_small():
+@pytest.mark.parametrize("shared", [False, True])
+def test_kalman_step_parity_sv_f32_small(shared):
     wl = workloads.stochastic_volatility(d=6, T=45, n_chains=4, delta=0.05)
-    _step_and_compare(wl, "f32", L=8, n_iters=3, tol_x=1e-4, tol_la=TOL_LA32)
+    _step_and_compare(wl, "f32", L=8, n_iters=3, tol_x=1e-4, tol_la=TOL_LA32, shared=shared)
 
 
-def test_kalman_step_parity_sv_f32_full_size_sampled_chains():
+@pytest.mark.parametrize("shared", [False, True])
+def test_kalman_step_parity_sv_f32_full_size_sampled_chains(shared):
     """d=30, T=1024, 32 chains in the benchmark's launch configuration; oracle on 4 chains."""
     wl = workloads.stochastic_volatility(d=30, T=1024, n_chains=32)
     _step_and_compare(wl, "f32", L=0, n_iters=1, chains=[0, 9, 22, 31], tol_x=1e-4,
-                      tol_la=TOL_LA32)
+                      tol_la=TOL_LA32, shared=shared)
+
+
+def test_shared_and_per_chain_modes_agree_at_full_size():
+    """d=30, T=1024, 32 chains: both execution modes give the same step (FP32 rounding)."""
+    wl = workloads.stochastic_volatility(d=30, T=1024, n_chains=32)
+    out = []
+    for shared in (False, True):
+        s = AuxKalman(wl, dtype="f32", shared_cov=shared)
+        x = _tt(wl.x_init, torch.float32)
+        la = torch.zeros(32, dtype=torch.float64, device="cuda")
+        s.step(x, n_iters=2, iter0=0, log_alpha=la)
+        torch.cuda.synchronize()
+        out.append((x.double().cpu().numpy(), la.cpu().numpy()))
+        s.close()
+    (xa, la_a), (xb, la_b) = out
+    assert np.max(np.abs(la_a - la_b)) < TOL_LA32
+    for c in range(32):
+        assert _rel(xa[c], xb[c]) < 1e-5, c
 
 
 @pytest.mark.parametrize("dt", ["f64", "f32"])
