@@ -43,8 +43,10 @@ def parse():
     ap.add_argument("--workload", default="sv_d30_T1024", choices=sorted(WORKLOADS))
     ap.add_argument("--block-len", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batched", action="store_true",
-                    help="skip the shared-covariance (batched) measurement")
+    ap.add_argument("--mode", default="shared", choices=["per_chain", "shared", "cached"],
+                    help="execution mode of the headline number (aux_set_mode)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the measurements of the other execution modes")
     ap.add_argument("--cpu-sample-chains", type=int, default=0,
                     help="chain-steps in the CPU baseline sample (0 = 2 per core)")
     return ap.parse_args()
@@ -90,15 +92,54 @@ def apply_flops_per_step(d, epilogue, fdiag):
     return f + (0.0 if fdiag else 4.0 * d ** 3) + (3 * d ** 2 if fdiag else 0.0)
 
 
-def kernel_flops(kind, d, T, C, nb, launches, fdiag):
+def cov_apply_flops_per_step(d, fdiag):
+    """Covariance pass, in-block step: the apply step with the epilogue, plus the
+    inverse Cholesky factor W_t = chol(S_t)^{-1} and the running product
+    r W^T W F AH (two triangular x dense products)."""
+    return apply_flops_per_step(d, True, fdiag) + (1.0 / 3.0 + 2.0) * d ** 3
+
+
+def means_flops_per_step(kind, d, fdiag, epilogue=True):
+    """Per chain-timestep flops of the means kernels: triangular mat-vec d^2,
+    dense mat-vec 2 d^2. reduce/apply: W r and W^T w (+ F m); apply with the
+    epilogue also G m^p, chol(Sigma) eps (triangular) and the block prefix product."""
+    fm = 2.0 * d if fdiag else 2.0 * d ** 2
+    if kind == "reduce":
+        return 2.0 * d ** 2 + fm
+    return 2.0 * d ** 2 + fm + ((2.0 + 1.0 + 2.0) * d ** 2 if epilogue else 0.0)
+
+
+def kernel_flops(mode, kind, d, T, C, nb, launches, fdiag):
     """Algorithmic flops of all launches of one kernel kind in the timed region
     (each MH step runs the filter twice: forward with the epilogue, reverse without)."""
+    if mode == "per_chain":
+        if kind == "reduce":
+            return launches * C * T * reduce_flops_per_step(d, fdiag)
+        if kind == "apply":
+            return launches / 2 * C * T * (apply_flops_per_step(d, True, fdiag) +
+                                           apply_flops_per_step(d, False, fdiag))
+        return None
     if kind == "reduce":
-        return launches * C * T * reduce_flops_per_step(d, fdiag)
+        return launches * C * T * means_flops_per_step("reduce", d, fdiag)
     if kind == "apply":
-        return launches / 2 * C * T * (apply_flops_per_step(d, True, fdiag) +
-                                       apply_flops_per_step(d, False, fdiag))
+        return launches / 2 * C * T * (means_flops_per_step("apply", d, fdiag, True) +
+                                       means_flops_per_step("apply", d, fdiag, False))
+    if kind == "cov":
+        # one covariance pass per launch group: T reduce steps, the scan rounds, T apply steps
+        L = math.ceil(T / nb)
+        scan = sum(max(0, nb - off) for off in (2 ** j for j in range(max(0, math.ceil(math.log2(nb))))))
+        per_pass = T * reduce_flops_per_step(d, fdiag) + scan * combine_flops(d) + \
+            T * cov_apply_flops_per_step(d, fdiag)
+        return launches * per_pass
     return None
+
+
+KERNEL_NAMES = {
+    "per_chain": {"reduce": "k_filter_reduce", "apply": "k_filter_apply", "scan": "k_filter_scan_level",
+                  "backward": "k_sample_backward", "mh": "k_mh", "linearise": "k_linearise"},
+    "table": {"reduce": "k_mf_reduce", "apply": "k_mf_apply", "cov": "k_cov_reduce/scan_level/apply",
+              "backward": "k_sample_backward", "mh": "k_mh"},
+}
 
 
 # --------------------------------------------------------------------------- clocks
@@ -240,84 +281,78 @@ def run_ours(args):
     C, T, d = w["C"], w["T"], w["d"]
     tdt = torch.float32 if w["dtype"] == "f32" else torch.float64
     esz = 4 if w["dtype"] == "f32" else 8
-    s = AuxKalman(wl, dtype=w["dtype"], block_len=args.block_len)
     L = args.block_len or max(1, math.ceil(math.sqrt(T)))   # the library's default block length
     nb = (T + L - 1) // L
-    x = torch.tensor(wl.x_init, dtype=tdt, device="cuda")
-    acc = torch.zeros(C, dtype=torch.int32, device="cuda")
-    la = torch.zeros(C, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    it = 0
-    for _ in range(args.warmup):
-        s.step(x, 1, iter0=it, accept_count=acc, log_alpha=la)
-        it += 1
-    torch.cuda.synchronize()
-    acc.zero_()
-    if world > 1:
-        dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    B.aux_set_profiling(s.handle, True)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    for k in range(args.steps):
-        flush.zero_()
-        starts[k].record(stream)
-        s.step(x, 1, iter0=it, accept_count=acc, log_alpha=la)
-        ends[k].record(stream)
-        it += 1
-    torch.cuda.synchronize()
-    B.aux_set_profiling(s.handle, False)
-    prof = B.aux_read_profile(s.handle)
-    ck = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms = t_max.item()
-    value = world * C * T * args.steps / (total_ms / 1e3)
-    accept_rate = acc.float().mean().item() / args.steps
-
-    # the same workload in the shared-covariance (batched) execution mode
-    batched = None
-    if not args.no_batched:
-        sb = AuxKalman(wl, dtype=w["dtype"], block_len=args.block_len, shared_cov=True)
-        xb = torch.tensor(wl.x_init, dtype=tdt, device="cuda")
-        accb = torch.zeros(C, dtype=torch.int32, device="cuda")
-        itb = 0
+    def run_mode(mode, with_clocks):
+        """Warm-up, then args.steps timed steps (L2 flushed before each), per-launch events on."""
+        sm = AuxKalman(wl, dtype=w["dtype"], block_len=args.block_len, mode=mode)
+        xm = torch.tensor(wl.x_init, dtype=tdt, device="cuda")
+        accm = torch.zeros(C, dtype=torch.int32, device="cuda")
+        lam = torch.zeros(C, dtype=torch.float64, device="cuda")
+        itm = 0
         for _ in range(args.warmup):
-            sb.step(xb, 1, iter0=itb, accept_count=accb)
-            itb += 1
+            sm.step(xm, 1, iter0=itm, accept_count=accm, log_alpha=lam)
+            itm += 1
         torch.cuda.synchronize()
-        accb.zero_()
+        accm.zero_()
         if world > 1:
             dist.barrier()
-        B.aux_set_profiling(sb.handle, True)
+        ck = None
+        if with_clocks:
+            clocks = ClockSampler(local)
+            clocks.start()
+        B.aux_set_profiling(sm.handle, True)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
         for k in range(args.steps):
             flush.zero_()
             evs[k][0].record(stream)
-            sb.step(xb, 1, iter0=itb, accept_count=accb)
+            sm.step(xm, 1, iter0=itm, accept_count=accm, log_alpha=lam)
             evs[k][1].record(stream)
-            itb += 1
+            itm += 1
         torch.cuda.synchronize()
-        B.aux_set_profiling(sb.handle, False)
-        profb = B.aux_read_profile(sb.handle)
-        tb = torch.tensor([sum(a.elapsed_time(b) for a, b in evs)], dtype=torch.float64,
-                          device="cuda")
+        B.aux_set_profiling(sm.handle, False)
+        prof = B.aux_read_profile(sm.handle)
+        if with_clocks:
+            ck = clocks.stop()
+        step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        accept_rate_m = accm.float().mean().item() / args.steps
+        t = torch.tensor([sum(step_ms)], dtype=torch.float64, device="cuda")
         if world > 1:
-            dist.all_reduce(tb, op=dist.ReduceOp.MAX)
-        batched = {"mode": "shared covariance (AUX_MODE_SHARED_COV)",
-                   "value": world * C * T * args.steps / (tb.item() / 1e3), "unit": UNIT,
-                   "ms_per_step": tb.item() / args.steps,
-                   "accept_rate": accb.float().mean().item() / args.steps,
-                   "kernel_ms_per_step": {k: v[0] / args.steps for k, v in profb.items() if v[1]},
-                   "gpu_launches": int(sum(v[1] for v in profb.values()))}
-        sb.close()
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        # the same steps without the per-launch events (host overhead check)
+        evu = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            evu[k][0].record(stream)
+            sm.step(xm, 1, iter0=itm, accept_count=accm, log_alpha=lam)
+            evu[k][1].record(stream)
+            itm += 1
+        torch.cuda.synchronize()
+        unprof_ms = sum(e0.elapsed_time(e1) for e0, e1 in evu) / args.steps
+        res = {"mode": mode, "value": world * C * T * args.steps / (t.item() / 1e3), "unit": UNIT,
+               "ms_per_step": t.item() / args.steps, "ms_per_step_without_events": unprof_ms,
+               "step_ms_median": statistics.median(step_ms),
+               "accept_rate": accept_rate_m,
+               "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+               "gpu_launches": int(sum(v[1] for v in prof.values()))}
+        return sm, xm, lam, itm, prof, ck, res
+
+    s, x, la, it, prof, ck, head = run_mode(args.mode, True)
+    value = head["value"]
+    total_ms = head["ms_per_step"] * args.steps
+    accept_rate = head["accept_rate"]
+    others = {}
+    if not args.headline_only:
+        for mode in ("per_chain", "shared", "cached"):
+            if mode != args.mode:
+                so, _, _, _, _, _, r = run_mode(mode, False)
+                so.close()
+                others[mode] = r
 
     # end to end through the public API from pinned host buffers
     x_host = torch.tensor(wl.x_init, dtype=tdt).pin_memory()
@@ -346,10 +381,10 @@ def run_ours(args):
     rc, per_chain = s.status()
 
     # roofline of the dominant kernel (time-weighted), FP32 FMA pipe bound
-    dom = max(prof, key=lambda k: prof[k][0])
+    dom = max((k for k in prof if prof[k][1]), key=lambda k: prof[k][0])
     dom_ms, dom_launches = prof[dom]
     fdiag = bool(np.all(wl.F == np.diag(np.diag(wl.F))))
-    flops = kernel_flops(dom, d, T, C, nb, dom_launches, fdiag)
+    flops = kernel_flops(args.mode, dom, d, T, C, nb, dom_launches, fdiag)
     peaks = {}
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pp):
@@ -359,10 +394,11 @@ def run_ours(args):
         peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     else:
         peak_tflops = 1.25   # nominal GB300 FP64 rate
+    names = KERNEL_NAMES["per_chain" if args.mode == "per_chain" else "table"]
     roofline = None
     if flops is not None and dom_ms > 0:
         achieved = flops / (dom_ms / 1e3) / 1e12
-        roofline = {"bound": "alu", "kernel": f"k_filter_{dom}", "achieved": achieved,
+        roofline = {"bound": "alu", "kernel": names.get(dom, dom), "achieved": achieved,
                     "flops_per_launch": flops / dom_launches, "diagonal_F": fdiag,
                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                     "traffic": None, "launches": dom_launches,
@@ -378,18 +414,20 @@ def run_ours(args):
     if rank == 0:
         bi = C * T * d * esz
         bo = C * T * d * esz + C * 8
+        cfg = config_of(name, w, args.block_len, nb)
+        cfg["mode"] = args.mode
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": w["dtype"], "data": "synthetic",
-                "config": config_of(name, w, args.block_len, nb),
+                "dtype": w["dtype"], "data": "synthetic", "config": cfg,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                         "d2h_bytes_per_step": bo},
-                "gpu_launches": int(sum(v[1] for v in prof.values())),
-                "roofline": roofline, "cpu_baseline": cpu, "clocks": ck, "batched": batched,
-                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+                "gpu_launches": head["gpu_launches"],
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": ck,
+                "kernel_ms_per_step": head["kernel_ms_per_step"],
+                "ms_per_step_without_events": head["ms_per_step_without_events"],
                 "accept_rate": accept_rate, "status": int(rc),
-                "step_ms_median": statistics.median(step_ms)}
+                "step_ms_median": head["step_ms_median"], "other_modes": others}
         print(json.dumps(line), flush=True)
     s.close()
     if world > 1:

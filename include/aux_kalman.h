@@ -68,7 +68,8 @@ extern "C" {
 
 /* execution modes (aux_set_mode) */
 #define AUX_MODE_PER_CHAIN  0  /* every chain runs its own covariance recursion (default) */
-#define AUX_MODE_SHARED_COV 1  /* chains of the model share one covariance recursion per scan block */
+#define AUX_MODE_SHARED_COV 1  /* one covariance pass per call, shared by all chains */
+#define AUX_MODE_CACHED_COV 2  /* one covariance pass per model, reused until the model changes */
 
 /* emission models */
 #define AUX_EMIS_LINEAR_GAUSSIAN 0
@@ -151,15 +152,27 @@ int aux_sample_path(aux_model *m, const void *ytilde, const void *eps, uint64_t 
 int aux_loglik_grad(aux_model *m, const void *ytilde, double *logZ, double *g_mu, double *g_Phi,
                     double *g_cholSigma, double *g_delta, void *stream);
 
-/* Choose how the filter and the backward sampler are executed. Both modes
- * compute the same quantities. With the first-order proposal of Section 2.2
- * and Gaussian dynamics the covariance part of every filtering element, and
- * of every backward element, depends only on (F, Q, P0, delta), so all chains
- * of one handle run identical covariance recursions: AUX_MODE_PER_CHAIN runs
- * them once per chain (the general path, needed when covariances depend on
- * the chain's state), AUX_MODE_SHARED_COV runs them once per group of chains
- * and keeps only the per-chain vector recursions separate. aux_loglik_grad
- * always runs per chain. Errors: INVALID_ARG. */
+/* Choose how the filter and the backward sampler are executed. All modes
+ * compute the same quantities (the same x*, log Z and log alpha up to
+ * floating-point rounding). With the first-order proposal of Section 2.2 and
+ * Gaussian dynamics the pseudo-observation noise is R = (delta/2) I, so the
+ * covariance part of every filtering element (Appendix A.2.1) and of every
+ * backward element (Eq. (A.14)) depends only on (m0, P0, F, Q, delta): it is
+ * the same for every chain and every iteration.
+ *   AUX_MODE_PER_CHAIN   every chain runs the full element recursion
+ *                        (covariances included) in every pass.
+ *   AUX_MODE_SHARED_COV  each call runs the covariance half of the blocked
+ *                        scan once (the gains, G_t, chol(Sigma_t) and block
+ *                        aggregates, as tables of T*6*d^2 elements owned by
+ *                        the handle); each chain then runs only matrix-vector
+ *                        recursions on its means.
+ *   AUX_MODE_CACHED_COV  as SHARED_COV, but the tables are kept and reused by
+ *                        later calls until aux_set_model_params or aux_set_mode
+ *                        invalidates them.
+ * The first switch to a table mode allocates the tables (may return OOM).
+ * A factorisation failure in the covariance pass is reported for every chain
+ * (status words; the MH step rejects). aux_loglik_grad always runs per chain.
+ * Errors: INVALID_ARG, OOM. */
 int aux_set_mode(aux_model *m, int32_t mode);
 
 /* Replace the model of an existing handle (same dtype, d_x, T, n_chains,
@@ -185,7 +198,8 @@ int aux_get_status(aux_model *m, int32_t *per_chain_status);
 #define AUX_PROFILE_SUM       7  /* log Z reduction */
 #define AUX_PROFILE_SMOOTH    8  /* smoother aggregates and sweep with score statistics (gradient) */
 #define AUX_PROFILE_GRAD      9  /* FP64 gradient assembly per chain */
-#define AUX_PROFILE_KINDS     10
+#define AUX_PROFILE_COV       10 /* covariance pass of the table modes (aux_set_mode) */
+#define AUX_PROFILE_KINDS     11
 
 /* Turn per-launch timing on or off for this handle: while on, every kernel
  * launch is bracketed by two CUDA events recorded on its own stream. */

@@ -13,11 +13,20 @@ def _load_binding():
     return b
 
 
+MODES = ("per_chain", "shared", "cached")
+
+
 class AuxKalman:
-    """Owns an ``aux_model`` handle for one workload (torch is used for memory only)."""
+    """Owns an ``aux_model`` handle for one workload (torch is used for memory only).
+
+    ``mode`` selects the execution of the filter (``aux_set_mode``): "per_chain"
+    (every chain runs the full element recursion), "shared" (one covariance
+    pass per call, means per chain) or "cached" (the covariance tables are kept
+    until the model changes).
+    """
 
     def __init__(self, workload, dtype="f32", seed=None, n_chains=None, block_len=0, stream=None,
-                 shared_cov=False):
+                 mode="per_chain"):
         import torch
         b = _load_binding()
         self.b = b
@@ -32,8 +41,11 @@ class AuxKalman:
             F=workload.F, b=workload.b, Q=workload.Q, y=workload.y, delta=workload.delta,
             emis_kind=workload.emission, dtype=self.dtype_code, R_y=workload.Ry,
             obs_mask=workload.mask, block_len=block_len, seed=self.seed, stream=stream)
-        if shared_cov:
-            b.aux_set_mode(self.handle, b.AUX_MODE_SHARED_COV)
+        if mode not in MODES:
+            raise ValueError(f"mode must be one of {MODES}")
+        self.mode = mode
+        if mode != "per_chain":
+            b.aux_set_mode(self.handle, b.AUX_MODE_SHARED_COV if mode == "shared" else b.AUX_MODE_CACHED_COV)
 
     def step(self, x, n_iters=1, iter0=0, accept_count=None, log_alpha=None, stream=None):
         self.b.aux_kalman_step(self.handle, x, n_iters, iter0, accept_count, log_alpha, stream)

@@ -20,7 +20,7 @@ AUX_E_TOO_LARGE = 8
 AUX_NOALLOC_SCRATCH_BYTES = 32 << 20
 AUX_F32, AUX_F64 = 0, 1
 AUX_EMIS_LINEAR_GAUSSIAN, AUX_EMIS_SV = 0, 1
-AUX_MODE_PER_CHAIN, AUX_MODE_SHARED_COV = 0, 1
+AUX_MODE_PER_CHAIN, AUX_MODE_SHARED_COV, AUX_MODE_CACHED_COV = 0, 1, 2
 
 _dbl_p = ctypes.POINTER(ctypes.c_double)
 _u8_p = ctypes.POINTER(ctypes.c_uint8)
@@ -221,7 +221,7 @@ def aux_get_status(handle, n_chains=None):
 
 
 PROFILE_KINDS = ["linearise", "template", "reduce", "scan", "apply", "backward", "mh", "sum",
-                 "smooth", "grad"]
+                 "smooth", "grad", "cov"]
 
 
 def aux_set_profiling(handle, enable):

@@ -334,8 +334,24 @@ int aux_sample_path(aux_model* m, const void* ytilde, const void* eps, uint64_t 
 }
 
 int aux_set_mode(aux_model* m, int32_t mode) {
-  if (!m || (mode != AUX_MODE_PER_CHAIN && mode != AUX_MODE_SHARED_COV)) return AUX_E_INVALID_ARG;
+  if (!m || (mode != AUX_MODE_PER_CHAIN && mode != AUX_MODE_SHARED_COV && mode != AUX_MODE_CACHED_COV))
+    return AUX_E_INVALID_ARG;
+  if (mode != AUX_MODE_PER_CHAIN && !m->tab) {
+    const size_t es = m->esz, DD = (size_t)m->DP * m->DP;
+    int rc = dev_alloc(m, &m->tab, (size_t)6 * m->T * DD * es);
+    if (!rc) rc = dev_alloc(m, &m->btab, (size_t)2 * m->nb * DD * es);
+    if (!rc) rc = dev_alloc(m, &m->zb, (size_t)m->C * m->nb * m->DP * es);
+    if (!rc) rc = dev_alloc(m, (void**)&m->cov_ld, (size_t)m->nb * sizeof(double));
+    if (!rc) rc = dev_alloc(m, (void**)&m->cov_status, sizeof(int32_t));
+    if (rc) {
+      m->tab = m->btab = m->zb = nullptr;
+      m->cov_ld = nullptr;
+      m->cov_status = nullptr;
+      return rc;
+    }
+  }
   m->mode = mode;
+  m->cov_valid = 0;
   return AUX_OK;
 }
 
@@ -353,6 +369,7 @@ int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {
   if (rc) return rc;
   m->delta = desc->delta;
   m->fdiag = diag_flag(desc);
+  m->cov_valid = 0;
   std::vector<double> gc;
   m->grad_ok = theta_constants(desc, gc) ? 1 : 0;
   if (m->grad_ok &&

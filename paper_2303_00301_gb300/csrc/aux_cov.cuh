@@ -1,0 +1,507 @@
+// aux_cov.cuh — the covariance pass of the parallel filter.
+//
+// With the first-order proposal and Gaussian dynamics the pseudo-observation
+// model is ytilde_t = x_t + N(0, R), R = (delta/2) I (Eq. (2.7)), so the
+// covariance part of every filtering element (Appendix A.2.1), every
+// predictive and filtering covariance, every gain and every backward-sampling
+// matrix of Eq. (A.14) is a function of (m0, P0, F, Q, delta) alone: it is the
+// same for every chain and every MCMC iteration. This pass runs the matrix half
+// of the blocked scan once (one warp per scan block: conditional-filter block
+// reduction, Hillis-Steele rounds over the block aggregates, in-block filter
+// from the prefix) and writes, per step t and per block k,
+//   tab[TW][t]  = W_t = chol(S_t)^{-1},  S_t = P^p_t + R   (lower triangular)
+//   tab[TWT][t] = W_t^T
+//   tab[TG][t]  = G_t = P^f_t F^T (P^p_{t+1})^{-1}          (G_{T-1} = 0)
+//   tab[TLS][t] = chol(Sigma_t), Sigma_t = P^f_t - G_t P^p_{t+1} G_t^T
+//                 (chol(P^f_{T-1}) at t = T-1)
+//   tab[TGP][t] = G_s G_{s+1} ... G_{t-1}  (block prefix, identity at t = s)
+//   tab[TPF][t] = P^f_t
+//   btab[BAH][k] = (I - K_e) F ... (I - K_s) F,  K_t = P^p_t S_t^{-1}
+//                  (the linear part of m^f_e as a function of m^f_{s-1})
+//   btab[BGH][k] = G_s ... G_e
+//   ld[k]        = sum over the block of log det S_t (FP64)
+// Because R = r I, I - K_t = r S_t^{-1} = r W_t^T W_t, so the filtering mean
+// update is m^f_t = ytilde_t - r W_t^T W_t (ytilde_t - m^p_t) and the
+// predictive likelihood term uses |W_t (ytilde_t - m^p_t)|^2 and log det S_t:
+// the per-chain work that remains (aux_means.cuh) is matrix-vector only.
+#pragma once
+#include "aux_kernels.cuh"
+
+namespace auxk {
+
+enum { TW = 0, TWT, TG, TLS, TGP, TPF, NTAB };
+enum { BAH = 0, BGH, NBTAB };
+
+template <typename Real> struct CovArgs {
+  const Real* prefix;   // scan result [nb][3 DP^2] (A, C, J); null when nb == 1
+  Real* tab;            // [NTAB][T][DP][DP]
+  Real* btab;           // [NBTAB][nb][DP][DP]
+  double* ld;           // [nb]
+  int32_t* status;      // [1]: ST_NOT_PD when a factorisation failed
+};
+
+template <typename Real, int DP> struct CovSizes {
+  static constexpr int MAT = Lay<Real, DP>::MAT, VEC = Lay<Real, DP>::VEC;
+  static constexpr size_t MODEL = (3 * MAT + 2 * VEC) * sizeof(Real);
+  static constexpr size_t RED_SMEM = MODEL + (6 * MAT + 3 * VEC) * sizeof(Real);
+  static constexpr size_t SCAN_SMEM = (9 * MAT + VEC) * sizeof(Real);
+  static constexpr size_t APP_SMEM = MODEL + (11 * MAT + 3 * VEC) * sizeof(Real);
+};
+
+// ---------------------------------------------------------------------------
+// Block reduction: the conditional Kalman recursion of k_filter_reduce
+// (identity element in, raw elements applied in order), matrix part only.
+// aggm: [nb][3 DP^2] (A, C, J).
+// ---------------------------------------------------------------------------
+template <typename Real, int DP>
+__global__ void __launch_bounds__(32, 1) k_cov_reduce(KP<Real> p, Real* __restrict__ aggm,
+                                                     int32_t* __restrict__ status) {
+  using Z = CovSizes<Real, DP>;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  Real* sF = sm;
+  Real* sFT = sF + MAT;
+  Real* sQ = sFT + MAT;
+  Real* sb = sQ + MAT;
+  load_model_slots<Real, DP>(p, sF, sFT, sQ, sb);
+  const Real* sphi = sb + VEC;
+  Real* SA = sb + 2 * VEC;
+  Real* SC = SA + MAT;
+  Real* SX = SC + MAT;
+  Real* SY = SX + MAT;
+  Real* SW = SY + MAT;
+  Real* SL = SW + MAT;
+  Real* vdiag = SL + MAT;
+  Real* vdummy = vdiag + VEC;
+  const int lane = threadIdx.x & 31, k = blockIdx.x;
+  const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  int bad = 0;
+  Real jreg[DP];
+  zero<Real, DP>(jreg);
+  constexpr int JTR = DP >= 16 ? Tile<Real, DP>::TR : 1, JTC = DP >= 16 ? Tile<Real, DP>::TC : 1;
+  Real jtile[JTR][JTC];
+#pragma unroll
+  for (int i = 0; i < JTR; ++i)
+#pragma unroll
+    for (int j = 0; j < JTC; ++j) jtile[i][j] = (Real)0;
+  {
+    Real r[DP];
+#pragma unroll
+    for (int j = 0; j < DP; ++j) r[j] = (k > 0 && j == lane) ? (Real)1 : (Real)0;
+    st_row<Real, DP>(SA, row, r, act);
+    zero<Real, DP>(r);
+    st_row<Real, DP>(SC, row, r, act);
+  }
+  __syncwarp();
+  for (int t = s; t <= e; ++t) {
+    Real pprow[DP];
+    if (t == 0) {
+      ld_vec<Real, DP>(p.P0 + row * DP, pprow);
+      Real z0[DP];
+      zero<Real, DP>(z0);
+      st_row<Real, DP>(SX, row, z0, act);
+    } else if (p.fdiag) {
+      Real cr[DP], ph[DP], qr[DP], ar[DP];
+      ld_row<Real, DP>(SC, row, cr);
+      ld_vec<Real, DP>(sphi, ph);
+      ld_row<Real, DP>(sQ, row, qr);
+      ld_row<Real, DP>(SA, row, ar);
+      const Real phi = sphi[row];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) {
+        pprow[j] = fma(cr[j], phi * ph[j], qr[j]);
+        ar[j] *= phi;
+      }
+      __syncwarp();
+      st_row<Real, DP>(SX, row, ar, act);
+    } else {
+      Real xr[DP];
+      mm_row<Real, DP>(sF + row * LD, SC, xr);
+      __syncwarp();
+      st_row<Real, DP>(SX, row, xr, act);
+      __syncwarp();
+      mm_row<Real, DP>(SX + row * LD, sFT, pprow);
+      Real qr[DP];
+      ld_row<Real, DP>(sQ, row, qr);
+#pragma unroll
+      for (int j = 0; j < DP; ++j) pprow[j] += qr[j];
+      symmetrise_store<Real, DP>(SY, pprow, lane);
+      Real fa[DP];
+      mm_row<Real, DP>(sF + row * LD, SA, fa);
+      __syncwarp();
+      st_row<Real, DP>(SX, row, fa, act);
+    }
+    __syncwarp();
+    {
+      Real s_[DP];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) s_[j] = pprow[j] + ((j == lane && j < p.d) ? p.r : (Real)0);
+      chol_rot<Real, DP>(s_, SL, nullptr, nullptr, vdiag, nullptr, p.d, lane, &bad);
+    }
+    {
+      Real r1[DP], r2[DP], rv[DP];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) r1[j] = pprow[j];
+      ld_col<Real, DP>(SX, row, r2);
+      zero<Real, DP>(rv);
+      fsolve_multi<Real, DP, true>(SL, vdiag, r1, SY, r2, SW, rv, vdummy, lane);
+    }
+    __syncwarp();
+    st_row<Real, DP>(SC, row, pprow, act);
+    if constexpr (DP >= 16) {
+      __syncwarp();
+      mm_tile_to_slot<Real, DP, true, true>(SY, SY, SC, SC, lane);   // C = P^p - Y^T Y
+      mm_tile_to_slot<Real, DP, true, true>(SY, SW, SX, SA, lane);   // A = F A - Y^T W
+      mm_tile_regs<Real, DP, true, false>(SW, SW, jtile, lane);       // J += W^T W
+    } else {
+      __syncwarp();
+      Real cn[DP];
+      ld_row<Real, DP>(SC, row, cn);
+      mm_col<Real, DP, true, true>(SY, row, SY, cn);
+      Real an[DP];
+      ld_row<Real, DP>(SX, row, an);
+      mm_col<Real, DP, true, true>(SY, row, SW, an);
+      __syncwarp();
+      st_row<Real, DP>(SC, row, cn, act);
+      st_row<Real, DP>(SA, row, an, act);
+      mm_col<Real, DP, true>(SW, row, SW, jreg);
+    }
+    __syncwarp();
+  }
+  if constexpr (DP >= 16) {
+    tile_store<Real, DP>(SY, jtile, lane);
+    __syncwarp();
+    ld_row<Real, DP>(SY, row, jreg);
+  }
+  if (act) {
+    Real* g = aggm + (long)k * 3 * DP * DP;
+    Real r[DP];
+    ld_row<Real, DP>(SA, row, r);
+    st_vec<Real, DP>(g + row * DP, r);
+    ld_row<Real, DP>(SC, row, r);
+    st_vec<Real, DP>(g + DP * DP + row * DP, r);
+    st_vec<Real, DP>(g + 2 * DP * DP + row * DP, jreg);
+  }
+  if (bad && lane == 0) atomicOr(status, ST_NOT_PD);
+}
+
+// ---------------------------------------------------------------------------
+// One Hillis-Steele round over the block aggregates (matrix part of the
+// element operator, Appendix A.2.1).
+// ---------------------------------------------------------------------------
+template <typename Real, int DP>
+__global__ void __launch_bounds__(32, 1)
+    k_cov_scan_level(KP<Real> p, const Real* __restrict__ in_m, Real* __restrict__ out_m, int off,
+                     int32_t* __restrict__ status) {
+  using Z = CovSizes<Real, DP>;
+  constexpr int MAT = Z::MAT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  const int lane = threadIdx.x & 31, k = blockIdx.x;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  if (k < off) {
+    if (act) {
+      for (int q = row; q < 3 * DP; q += DP) {
+        Real r[DP];
+        ld_vec<Real, DP>(in_m + (long)k * 3 * DP * DP + q * DP, r);
+        st_vec<Real, DP>(out_m + (long)k * 3 * DP * DP + q * DP, r);
+      }
+    }
+    return;
+  }
+  Real* SA = sm;
+  Real* SC = SA + MAT;
+  Real* SU = SC + MAT;
+  Real* S2 = SU + MAT;
+  Real* S3 = S2 + MAT;
+  Real* S4 = S3 + MAT;
+  Real* SAe = S4 + MAT;
+  Real* SCe = SAe + MAT;
+  Real* SJe = SCe + MAT;
+  Real* vdiag = SJe + MAT;
+  int bad = 0;
+  Real jreg[DP];
+  {
+    const Real* gi = in_m + (long)(k - off) * 3 * DP * DP;
+    const Real* gj = in_m + (long)k * 3 * DP * DP;
+    Real r[DP];
+    ld_vec<Real, DP>(gi + row * DP, r);
+    st_row<Real, DP>(SA, row, r, act);
+    ld_vec<Real, DP>(gi + DP * DP + row * DP, r);
+    st_row<Real, DP>(SC, row, r, act);
+    ld_vec<Real, DP>(gi + 2 * DP * DP + row * DP, jreg);
+    ld_vec<Real, DP>(gj + row * DP, r);
+    st_row<Real, DP>(SAe, row, r, act);
+    ld_vec<Real, DP>(gj + DP * DP + row * DP, r);
+    st_row<Real, DP>(SCe, row, r, act);
+    ld_vec<Real, DP>(gj + 2 * DP * DP + row * DP, r);
+    st_row<Real, DP>(SJe, row, r, act);
+  }
+  __syncwarp();
+  combine_matrix_1<Real, DP>(SC, SAe, SJe, SU, S2, S3, S4, vdiag, p.d, lane, &bad);
+  combine_matrix_2<Real, DP>(SA, SC, jreg, SAe, SCe, SJe, SU, S2, S3, S4, lane);
+  if (act) {
+    Real* g = out_m + (long)k * 3 * DP * DP;
+    Real r[DP];
+    ld_row<Real, DP>(SA, row, r);
+    st_vec<Real, DP>(g + row * DP, r);
+    ld_row<Real, DP>(SC, row, r);
+    st_vec<Real, DP>(g + DP * DP + row * DP, r);
+    st_vec<Real, DP>(g + 2 * DP * DP + row * DP, jreg);
+  }
+  if (bad && lane == 0) atomicOr(status, ST_NOT_PD);
+}
+
+// ---------------------------------------------------------------------------
+// In-block covariance filter from the prefix P^f_{s-1}, with the tables.
+// ---------------------------------------------------------------------------
+template <typename Real, int DP>
+__global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a) {
+  using Z = CovSizes<Real, DP>;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
+  constexpr long DD = (long)DP * DP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  Real* sF = sm;
+  Real* sFT = sF + MAT;
+  Real* sQ = sFT + MAT;
+  Real* sb = sQ + MAT;
+  load_model_slots<Real, DP>(p, sF, sFT, sQ, sb);
+  const Real* sphi = sb + VEC;
+  Real* SP = sb + 2 * VEC;     // P^f
+  Real* SX = SP + MAT;         // F P^f, then G
+  Real* SL = SX + MAT;         // chol(P^p) (LS form), scratch
+  Real* SLR = SL + MAT;        // chol(P^p) (right-aligned), then chol(Sigma) row-major
+  Real* SY = SLR + MAT;        // L_S^{-1} P^p, scratch
+  Real* SG = SY + MAT;         // chol(S) (LS form)
+  Real* SGh = SG + MAT;        // G_s ... G_{t-1}
+  Real* SWm = SGh + MAT;       // W_t
+  Real* SA1 = SWm + MAT;
+  Real* SA2 = SA1 + MAT;
+  Real* SAH = SA2 + MAT;       // (I - K_t) F ... (I - K_s) F
+  Real* vdA = SAH + MAT;
+  Real* vdB = vdA + VEC;
+  Real* vsc = vdB + VEC;
+  __syncwarp();
+  const int lane = threadIdx.x & 31, k = blockIdx.x;
+  const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  int bad = 0;
+  double ld_acc = 0.0;
+  Real pprow[DP];
+  {
+    Real gi[DP];
+#pragma unroll
+    for (int j = 0; j < DP; ++j) gi[j] = (j == lane) ? (Real)1 : (Real)0;
+    st_row<Real, DP>(SGh, row, gi, act);
+    st_row<Real, DP>(SAH, row, gi, act);
+  }
+  auto store_row = [&](int tb, int t, const Real* S) {
+    if (!act) return;
+    Real r[DP];
+    ld_row<Real, DP>(S, row, r);
+    st_vec<Real, DP>(a.tab + ((long)tb * p.nT + t) * DD + row * DP, r);
+  };
+  auto predict = [&]() {   // P^p (pprow) and X = F P^f (SX) from P^f (SP)
+    if (p.fdiag) {
+      Real pr[DP], ph[DP], qr[DP];
+      ld_row<Real, DP>(SP, row, pr);
+      ld_vec<Real, DP>(sphi, ph);
+      ld_row<Real, DP>(sQ, row, qr);
+      const Real phi = sphi[row];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) {
+        pprow[j] = fma(pr[j], phi * ph[j], qr[j]);
+        pr[j] *= phi;
+      }
+      __syncwarp();
+      st_row<Real, DP>(SX, row, pr, act);
+      __syncwarp();
+      return;
+    }
+    Real xr[DP];
+    mm_row<Real, DP>(sF + row * LD, SP, xr);
+    __syncwarp();
+    st_row<Real, DP>(SX, row, xr, act);
+    __syncwarp();
+    mm_row<Real, DP>(SX + row * LD, sFT, pprow);
+    Real qr[DP];
+    ld_row<Real, DP>(sQ, row, qr);
+#pragma unroll
+    for (int j = 0; j < DP; ++j) pprow[j] += qr[j];
+    symmetrise_store<Real, DP>(SY, pprow, lane);
+  };
+  auto factor_S = [&]() {
+    Real s_[DP];
+#pragma unroll
+    for (int j = 0; j < DP; ++j) s_[j] = pprow[j] + ((j == lane && j < p.d) ? p.r : (Real)0);
+    chol_rot<Real, DP>(s_, SG, nullptr, nullptr, vdB, nullptr, p.d, lane, &bad);
+  };
+  auto factor_2 = [&]() {
+    Real a_[DP], s_[DP];
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+      a_[j] = pprow[j];
+      s_[j] = pprow[j] + ((j == lane && j < p.d) ? p.r : (Real)0);
+    }
+    chol_rot2<Real, DP>(a_, SL, SLR, vdA, s_, SG, vdB, p.d, lane, &bad);
+  };
+  // after the factor of P^p_{t+1} (SL / SLR / vdA): G_t -> SX, chol(Sigma_t) -> SLR
+  auto epilogue = [&](int t) {
+    {
+      Real rr[DP];
+      ld_col<Real, DP>(SX, row, rr);
+      fsolve_rot<Real, DP, true>(SL, vdA, rr, SY, lane);
+    }
+    __syncwarp();
+    Real sig[DP];
+    if constexpr (DP >= 16) {
+      mm_tile_to_slot<Real, DP, true, true>(SY, SY, SP, SL, lane);
+      __syncwarp();
+      ld_row<Real, DP>(SL, row, sig);
+    } else {
+      ld_row<Real, DP>(SP, row, sig);
+      mm_col<Real, DP, true, true>(SY, row, SY, sig);
+    }
+    {
+      Real rr[DP];
+      ld_col<Real, DP>(SY, row, rr);
+      bsolve_rot<Real, DP>(SLR, vdA, rr, SX, lane);
+    }
+    chol_rot<Real, DP>(sig, SL, SLR, nullptr, vdA, nullptr, p.d, lane, &bad);
+    store_row(TG, t, SX);
+    store_row(TLS, t, SLR);
+  };
+  auto ghat = [&]() {      // SGh <- SGh G_t
+    Real gn[DP];
+    mm_row<Real, DP>(SGh + row * LD, SX, gn);
+    __syncwarp();
+    st_row<Real, DP>(SGh, row, gn, act);
+    __syncwarp();
+  };
+  // W_t = L_S^{-1} (columns of the identity through the forward solve), its
+  // transpose, and the running product (I - K_t) F AH = r W^T W F AH
+  auto gain_tables = [&](int t, bool with_ah) {
+    {
+      Real r[DP];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) r[j] = (j == lane) ? (Real)1 : (Real)0;
+      fsolve_rot<Real, DP, true>(SG, vdB, r, SWm, lane);
+    }
+    __syncwarp();
+    store_row(TW, t, SWm);
+    if (act) {
+      Real c[DP];
+      ld_col<Real, DP>(SWm, row, c);
+      st_vec<Real, DP>(a.tab + ((long)TWT * p.nT + t) * DD + row * DP, c);
+    }
+    if (!with_ah) return;
+    Real x1[DP];
+    if (p.fdiag) {
+      ld_row<Real, DP>(SAH, row, x1);
+      const Real phi = sphi[row];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) x1[j] *= phi;
+    } else {
+      mm_row<Real, DP>(sF + row * LD, SAH, x1);
+    }
+    st_row<Real, DP>(SA1, row, x1, act);
+    __syncwarp();
+    Real x2[DP];
+    mm_row<Real, DP>(SWm + row * LD, SA1, x2);
+    st_row<Real, DP>(SA2, row, x2, act);
+    __syncwarp();
+    Real ah[DP];
+    mm_col<Real, DP>(SWm, row, SA2, ah);
+#pragma unroll
+    for (int j = 0; j < DP; ++j) ah[j] *= p.r;
+    st_row<Real, DP>(SAH, row, ah, act);
+    __syncwarp();
+  };
+  // Y = L_S^{-1} P^p (columns of SY), P^f -> SP, log det S
+  auto update = [&](int t) {
+    {
+      Real rr[DP];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) rr[j] = pprow[j];
+      fsolve_rot<Real, DP, true>(SG, vdB, rr, SY, lane);
+    }
+    __syncwarp();
+    if constexpr (DP >= 16) {
+      st_row<Real, DP>(SP, row, pprow, act);
+      __syncwarp();
+      mm_tile_to_slot<Real, DP, true, true>(SY, SY, SP, SP, lane);
+    } else {
+      Real pf[DP];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) pf[j] = pprow[j];
+      mm_col<Real, DP, true, true>(SY, row, SY, pf);
+      __syncwarp();
+      st_row<Real, DP>(SP, row, pf, act);
+    }
+    __syncwarp();
+    double lg = (lane < p.d) ? -log((double)vdB[lane]) : 0.0;
+    lg = warp_sum<double>(lg);
+    ld_acc += 2.0 * lg;
+    store_row(TPF, t, SP);
+    __syncwarp();
+  };
+
+  // ---- block start
+  if (k == 0) {
+    ld_vec<Real, DP>(p.P0 + row * DP, pprow);
+  } else {
+    Real r[DP];
+    ld_vec<Real, DP>(a.prefix + (long)(k - 1) * 3 * DP * DP + DP * DP + row * DP, r);
+    st_row<Real, DP>(SP, row, r, act);
+    __syncwarp();
+    predict();
+  }
+  factor_S();
+  store_row(TGP, s, SGh);
+  gain_tables(s, k > 0);
+  update(s);
+  for (int t = s + 1; t <= e; ++t) {
+    predict();
+    factor_2();
+    epilogue(t - 1);
+    ghat();
+    store_row(TGP, t, SGh);
+    gain_tables(t, true);
+    update(t);
+  }
+  if (e < p.nT - 1) {
+    predict();
+    Real a_[DP];
+#pragma unroll
+    for (int j = 0; j < DP; ++j) a_[j] = pprow[j];
+    chol_rot<Real, DP>(a_, SL, nullptr, SLR, vdA, nullptr, p.d, lane, &bad);
+    epilogue(e);
+  } else {
+    Real pf[DP], z0[DP];
+    ld_row<Real, DP>(SP, row, pf);
+    chol_rot<Real, DP>(pf, SL, SLR, nullptr, vdA, nullptr, p.d, lane, &bad);
+    zero<Real, DP>(z0);
+    st_row<Real, DP>(SX, row, z0, act);
+    __syncwarp();
+    store_row(TG, e, SX);
+    store_row(TLS, e, SLR);
+  }
+  ghat();
+  if (act) {
+    Real r[DP];
+    ld_row<Real, DP>(SGh, row, r);
+    st_vec<Real, DP>(a.btab + ((long)BGH * p.nb + k) * DD + row * DP, r);
+    ld_row<Real, DP>(SAH, row, r);
+    st_vec<Real, DP>(a.btab + ((long)BAH * p.nb + k) * DD + row * DP, r);
+  }
+  if (lane == 0) a.ld[k] = ld_acc;
+  if (bad && lane == 0) atomicOr(a.status, ST_NOT_PD);
+}
+
+}  // namespace auxk

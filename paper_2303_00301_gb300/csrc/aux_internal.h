@@ -35,6 +35,11 @@ struct aux_model {
   double *gconst = nullptr;  // mu, phi, L, Q, Q^{-1}, P0^{-1} (FP64, unpadded)
   void *Sig = nullptr, *sgu = nullptr, *gpart = nullptr, *s0 = nullptr;
   double *opart = nullptr;
+  // covariance tables of the table modes (aux_cov.cuh), allocated on the first switch
+  void *tab = nullptr, *btab = nullptr, *zb = nullptr;
+  double *cov_ld = nullptr;
+  int32_t *cov_status = nullptr;
+  int cov_valid = 0;         // the tables match the current model
   const AuxOps *ops = nullptr;
   std::vector<void *> allocs;
   // optional per-launch CUDA-event timing (aux_set_profiling)
@@ -46,7 +51,7 @@ struct aux_model {
 
 // kernel kinds reported by aux_read_profile (order of AUX_PROFILE_* in the header)
 enum { PK_LINEARISE = 0, PK_TEMPLATE, PK_REDUCE, PK_SCAN, PK_APPLY, PK_BACKWARD, PK_MH, PK_SUM,
-       PK_SMOOTH, PK_GRAD, PK_COUNT };
+       PK_SMOOTH, PK_GRAD, PK_COV, PK_COUNT };
 
 // bracket a launch with events on its stream when profiling is on
 struct ProfScope {

@@ -3,7 +3,7 @@
 #include <cmath>
 
 #include "aux_grad.cuh"
-#include "aux_shared.cuh"
+#include "aux_means.cuh"
 
 namespace auxk {
 namespace {
@@ -62,11 +62,11 @@ struct Ops {
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_grad_final<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     if (e != cudaSuccess) return AUX_E_CUDA;
-    e = cudaFuncSetAttribute(k_filter_reduce_sh<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ShSizes<Real, DP>::RED_SMEM);
+    e = cudaFuncSetAttribute(k_cov_reduce<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::RED_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
-    e = cudaFuncSetAttribute(k_filter_scan_level_sh<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ShSizes<Real, DP>::SCAN_SMEM);
+    e = cudaFuncSetAttribute(k_cov_scan_level<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::SCAN_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
-    e = cudaFuncSetAttribute(k_filter_apply_sh<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ShSizes<Real, DP>::APP_SMEM);
+    e = cudaFuncSetAttribute(k_cov_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::APP_SMEM);
     return cuda_ok(e);
   }
 
@@ -109,66 +109,78 @@ struct Ops {
     k_sample_backward<Real, DP><<<(n + Z::BWD_WPC - 1) / Z::BWD_WPC, 32 * Z::BWD_WPC, Z::BWD_SMEM, st>>>(p, b);
   }
 
-  // ---- shared-covariance mode (all chains of the model share the covariance recursion)
-  using SZ = ShSizes<Real, DP>;
-  static int sh_grid(const aux_model* m) { return m->nb * ((m->C + SZ::CW - 1) / SZ::CW); }
+  // ---- covariance tables shared by all chains (AUX_MODE_SHARED_COV, AUX_MODE_CACHED_COV)
+  using CZ = CovSizes<Real, DP>;
+  static constexpr long DD = (long)DP * DP;
 
-  static void filter_sh(aux_model* m, const KP<Real>& p, const Real* yt, ApplyShArgs<Real> a,
-                        cudaStream_t st) {
-    const int grid = sh_grid(m);
-    const size_t msz = (size_t)m->nb * 3 * DP * DP;
-    Real* b0m = (Real*)m->agg0;
-    Real* b0v = b0m + msz;
-    Real* b1m = (Real*)m->agg1;
-    Real* b1v = b1m + msz;
-    { ProfScope ps(m, PK_REDUCE, st);
-      k_filter_reduce_sh<Real, DP><<<grid, 32 * SZ::CW, SZ::RED_SMEM, st>>>(p, yt, b0m, b0v); }
+  static void cov_pass(aux_model* m, const KP<Real>& p, cudaStream_t st) {
+    ProfScope ps(m, PK_COV, st);
+    Real* b0 = (Real*)m->agg0;
+    Real* b1 = (Real*)m->agg1;
+    cudaMemsetAsync(m->cov_status, 0, sizeof(int32_t), st);
+    k_cov_reduce<Real, DP><<<m->nb, 32, CZ::RED_SMEM, st>>>(p, b0, m->cov_status);
     for (int off = 1; off < m->nb; off *= 2) {
-      { ProfScope ps(m, PK_SCAN, st);
-        k_filter_scan_level_sh<Real, DP><<<grid, 32 * SZ::CW, SZ::SCAN_SMEM, st>>>(p, b0m, b0v, b1m, b1v, off); }
-      Real* t0 = b0m; b0m = b1m; b1m = t0;
-      Real* t1 = b0v; b0v = b1v; b1v = t1;
+      k_cov_scan_level<Real, DP><<<m->nb, 32, CZ::SCAN_SMEM, st>>>(p, b0, b1, off, m->cov_status);
+      Real* tmp = b0; b0 = b1; b1 = tmp;
     }
-    a.yt = yt;
-    a.prem = (m->nb > 1) ? b0m : nullptr;
-    a.prev = b0v;
-    ProfScope ps(m, PK_APPLY, st);
-    k_filter_apply_sh<Real, DP><<<grid, 32 * SZ::CW, SZ::APP_SMEM, st>>>(p, a);
+    CovArgs<Real> a{};
+    a.prefix = (m->nb > 1) ? b0 : nullptr;
+    a.tab = (Real*)m->tab; a.btab = (Real*)m->btab; a.ld = m->cov_ld; a.status = m->cov_status;
+    k_cov_apply<Real, DP><<<m->nb, 32, CZ::APP_SMEM, st>>>(p, a);
   }
 
-  static ApplyShArgs<Real> apply_sh_args(aux_model* m, int flags, uint64_t iter) {
-    ApplyShArgs<Real> a{};
-    a.flags = flags;
-    a.G = (Real*)m->G; a.U = (Real*)m->U; a.gum = (Real*)m->gum; a.guv = (Real*)m->guv;
-    a.fq = m->fq; a.fld = m->fld; a.lz_part = m->lz_part;
-    a.mf = nullptr; a.Pf = nullptr; a.eps = nullptr;
-    a.iter = iter;
+  // the tables for this call: recomputed (shared mode) or reused while valid (cached mode)
+  static void ensure_cov(aux_model* m, const KP<Real>& p, cudaStream_t st) {
+    if (m->mode == AUX_MODE_CACHED_COV && m->cov_valid) return;
+    cov_pass(m, p, st);
+    m->cov_valid = 1;
+  }
+
+  static MeanArgs<Real> mean_args(aux_model* m) {
+    MeanArgs<Real> a{};
+    a.tab = (const Real*)m->tab; a.btab = (const Real*)m->btab; a.ld = m->cov_ld;
+    a.cov_status = m->cov_status; a.z = (Real*)m->zb;
+    a.U = (Real*)m->U; a.guv = (Real*)m->guv; a.fqb = m->fq; a.lz_part = m->lz_part;
     return a;
   }
 
-  static BackArgs<Real> back_args_sh(aux_model* m) {
+  static void means_filter(aux_model* m, const KP<Real>& p, MeanArgs<Real> a, cudaStream_t st) {
+    const int grid = (items(m) + MEAN_WPC - 1) / MEAN_WPC;
+    { ProfScope ps(m, PK_REDUCE, st);
+      k_mf_reduce<Real, DP><<<grid, 32 * MEAN_WPC, 0, st>>>(p, a); }
+    a.x = nullptr;
+    { ProfScope ps(m, PK_APPLY, st);
+      k_mf_apply<Real, DP><<<grid, 32 * MEAN_WPC, 0, st>>>(p, a); }
+  }
+
+  static BackArgs<Real> back_args_tab(aux_model* m) {
     BackArgs<Real> b{};
-    b.G = (const Real*)m->G; b.U = (const Real*)m->U; b.gum = (const Real*)m->gum;
-    b.guv = (const Real*)m->guv; b.g_cs = 0; b.gm_cs = 0;
+    b.G = (const Real*)m->tab + (long)TG * m->T * DD;
+    b.U = (const Real*)m->U;
+    b.gum = (const Real*)m->btab + (long)BGH * m->nb * DD;
+    b.guv = (const Real*)m->guv;
+    b.g_cs = 0; b.gm_cs = 0;
     return b;
   }
 
-  static int kalman_step_sh(aux_model* m, void* xv, int n_iters, uint64_t iter0, uint32_t* acc,
-                            double* log_alpha, cudaStream_t st) {
+  static int kalman_step_means(aux_model* m, void* xv, int n_iters, uint64_t iter0, uint32_t* acc,
+                               double* log_alpha, cudaStream_t st) {
     const KP<Real> p = make_kp<Real>(m);
     Real* x = (Real*)xv;
-    const long n = (long)m->C * m->T * m->d;
-    const int lin_grid = (int)std::min<long>((n + 255) / 256, 152L * 16);
+    ensure_cov(m, p, st);
     for (int it = 0; it < n_iters; ++it) {
       const uint64_t iter = iter0 + (uint64_t)it;
-      { ProfScope ps(m, PK_LINEARISE, st);
-        k_linearise<Real><<<lin_grid, 256, 0, st>>>(p, x, (Real*)m->u, (Real*)m->v, (Real*)m->yt, iter); }
-      filter_sh(m, p, (const Real*)m->yt, apply_sh_args(m, APPLY_EPI | APPLY_STORE_Q, iter), st);
-      BackArgs<Real> b = back_args_sh(m);
+      MeanArgs<Real> a = mean_args(m);
+      a.x = x; a.u = (Real*)m->u; a.v = (Real*)m->v; a.yt = (Real*)m->yt; a.iter = iter;
+      a.flags = APPLY_EPI | APPLY_STORE_Q;
+      means_filter(m, p, a, st);
+      BackArgs<Real> b = back_args_tab(m);
       b.xs = (Real*)m->xs; b.mh = 1; b.x = x; b.u = (const Real*)m->u; b.v = (const Real*)m->v;
       b.yts = (Real*)m->yts; b.mh_part = m->mh_part;
       backward(m, p, b, st);
-      filter_sh(m, p, (const Real*)m->yts, apply_sh_args(m, APPLY_REV_DIFF, iter), st);
+      MeanArgs<Real> r = mean_args(m);
+      r.yt = (Real*)m->yts; r.flags = APPLY_REV_DIFF;
+      means_filter(m, p, r, st);
       { ProfScope ps(m, PK_MH, st);
         k_mh<Real><<<m->C, 128, 0, st>>>(p, x, (const Real*)m->xs, m->mh_part, m->lz_part, iter, acc,
                                          log_alpha, m->status); }
@@ -178,7 +190,7 @@ struct Ops {
 
   static int kalman_step(aux_model* m, void* xv, int n_iters, uint64_t iter0, uint32_t* acc,
                          double* log_alpha, cudaStream_t st) {
-    if (m->mode == AUX_MODE_SHARED_COV) return kalman_step_sh(m, xv, n_iters, iter0, acc, log_alpha, st);
+    if (m->mode != AUX_MODE_PER_CHAIN) return kalman_step_means(m, xv, n_iters, iter0, acc, log_alpha, st);
     const KP<Real> p = make_kp<Real>(m);
     Real* x = (Real*)xv;
     const long n = (long)m->C * m->T * m->d;
@@ -204,11 +216,11 @@ struct Ops {
 
   static int loglik(aux_model* m, const void* yt, double* logZ, void* mf, void* Pf, cudaStream_t st) {
     const KP<Real> p = make_kp<Real>(m);
-    if (m->mode == AUX_MODE_SHARED_COV) {
-      ApplyShArgs<Real> a = apply_sh_args(m, APPLY_LOGZ, 0);
-      a.mf = (Real*)mf;
-      a.Pf = (Real*)Pf;
-      filter_sh(m, p, (const Real*)yt, a, st);
+    if (m->mode != AUX_MODE_PER_CHAIN) {
+      ensure_cov(m, p, st);
+      MeanArgs<Real> a = mean_args(m);
+      a.yt = (Real*)yt; a.flags = APPLY_LOGZ; a.mf = (Real*)mf; a.Pf = (Real*)Pf; a.status = m->status;
+      means_filter(m, p, a, st);
       { ProfScope ps(m, PK_SUM, st); k_sum_parts<<<m->C, 128, 0, st>>>(m->lz_part, m->nb, logZ); }
       return cuda_ok(cudaGetLastError());
     }
@@ -224,11 +236,13 @@ struct Ops {
   static int sample_path(aux_model* m, const void* yt, const void* eps, uint64_t iter, void* xs,
                          double* logZ, cudaStream_t st) {
     const KP<Real> p = make_kp<Real>(m);
-    if (m->mode == AUX_MODE_SHARED_COV) {
-      ApplyShArgs<Real> a = apply_sh_args(m, APPLY_EPI | APPLY_LOGZ, iter);
-      a.eps = (const Real*)eps;
-      filter_sh(m, p, (const Real*)yt, a, st);
-      BackArgs<Real> b = back_args_sh(m);
+    if (m->mode != AUX_MODE_PER_CHAIN) {
+      ensure_cov(m, p, st);
+      MeanArgs<Real> a = mean_args(m);
+      a.yt = (Real*)yt; a.flags = APPLY_EPI | APPLY_LOGZ; a.eps = (const Real*)eps; a.iter = iter;
+      a.status = m->status;
+      means_filter(m, p, a, st);
+      BackArgs<Real> b = back_args_tab(m);
       b.xs = (Real*)xs; b.mh = 0;
       backward(m, p, b, st);
       if (logZ) { ProfScope ps(m, PK_SUM, st); k_sum_parts<<<m->C, 128, 0, st>>>(m->lz_part, m->nb, logZ); }

@@ -14,7 +14,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from oracle import kalman, mcmc, philox  # noqa: E402
-from paper_2303_00301_gb300 import AuxKalman, workloads  # noqa: E402
+from paper_2303_00301_gb300 import MODES, AuxKalman, workloads  # noqa: E402
 
 TOL_LA32 = 2e-3
 
@@ -66,16 +66,16 @@ FILTER_CASES = [
 ]
 
 
-@pytest.mark.parametrize("shared", [False, True])
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("d,T,C,L,dt", FILTER_CASES)
-def test_loglik_filter_parity(d, T, C, L, dt, shared):
+def test_loglik_filter_parity(d, T, C, L, dt, mode):
     wl = _lgssm_workload(d, T, C, seed=100 + d * T)
     tdt = torch.float64 if dt == "f64" else torch.float32
     tol = 1e-9 if dt == "f64" else 1e-4
     tol_z = 1e-9 if dt == "f64" else 1e-5
     rng = np.random.default_rng(d + T)
     yt = rng.standard_normal((C, T, d))
-    s = AuxKalman(wl, dtype=dt, block_len=L, shared_cov=shared)
+    s = AuxKalman(wl, dtype=dt, block_len=L, mode=mode)
     logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
     mf = torch.zeros((C, T, d), dtype=tdt, device="cuda")
     Pf = torch.zeros((C, T, d, d), dtype=tdt, device="cuda")
@@ -91,16 +91,16 @@ def test_loglik_filter_parity(d, T, C, L, dt, shared):
     s.close()
 
 
-@pytest.mark.parametrize("shared", [False, True])
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("d,T,C,L,dt", FILTER_CASES)
-def test_sample_path_parity(d, T, C, L, dt, shared):
+def test_sample_path_parity(d, T, C, L, dt, mode):
     wl = _lgssm_workload(d, T, C, seed=200 + d * T)
     tdt = torch.float64 if dt == "f64" else torch.float32
     tol = 1e-9 if dt == "f64" else 1e-4
     rng = np.random.default_rng(7 * d + T)
     yt = rng.standard_normal((C, T, d))
     eps = rng.standard_normal((C, T, d))
-    s = AuxKalman(wl, dtype=dt, block_len=L, shared_cov=shared)
+    s = AuxKalman(wl, dtype=dt, block_len=L, mode=mode)
     xs = torch.zeros((C, T, d), dtype=tdt, device="cuda")
     logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
     s.sample_path(_tt(yt, tdt), xs, eps=_tt(eps, tdt), logZ=logZ)
@@ -132,14 +132,14 @@ def test_backward_noise_is_the_philox_stream(dt):
     s.close()
 
 
-def _step_and_compare(wl, dt, L, n_iters, chains=None, tol_x=None, tol_la=None, shared=False):
+def _step_and_compare(wl, dt, L, n_iters, chains=None, tol_x=None, tol_la=None, mode="per_chain"):
     """Step all chains on the GPU; replay the chosen chains on the oracle from the same state.
 
     Each oracle step starts from the GPU's state before that step, so a rare
     near-tie decision difference in FP32 does not make the paths diverge."""
     C = wl.n_chains
     tdt = torch.float64 if dt == "f64" else torch.float32
-    s = AuxKalman(wl, dtype=dt, block_len=L, shared_cov=shared)
+    s = AuxKalman(wl, dtype=dt, block_len=L, mode=mode)
     x = _tt(wl.x_init, tdt)
     la = torch.zeros(C, dtype=torch.float64, device="cuda")
     model = _oracle_model(wl)
@@ -172,61 +172,98 @@ def _step_and_compare(wl, dt, L, n_iters, chains=None, tol_x=None, tol_la=None, 
     return mismatches, max_dla
 
 
-@pytest.mark.parametrize("shared", [False, True])
-def test_kalman_step_parity_linear_gaussian_f64(shared):
+@pytest.mark.parametrize("mode", MODES)
+def test_kalman_step_parity_linear_gaussian_f64(mode):
     wl = workloads.linear_gaussian(d=2, T=64, n_chains=4)
-    _step_and_compare(wl, "f64", L=8, n_iters=4, tol_x=1e-9, tol_la=1e-8, shared=shared)
+    _step_and_compare(wl, "f64", L=8, n_iters=4, tol_x=1e-9, tol_la=1e-8, mode=mode)
 
 
-@pytest.mark.parametrize("shared", [False, True])
-def test_kalman_step_parity_masked_toy_f64(shared):
+@pytest.mark.parametrize("mode", MODES)
+def test_kalman_step_parity_masked_toy_f64(mode):
     wl = workloads.two_step_toy(rho=0.7, r2=0.3, n_chains=3)
-    _step_and_compare(wl, "f64", L=1, n_iters=4, tol_x=1e-9, tol_la=1e-8, shared=shared)
+    _step_and_compare(wl, "f64", L=1, n_iters=4, tol_x=1e-9, tol_la=1e-8, mode=mode)
 
 
-@pytest.mark.parametrize("shared", [False, True])
-def test_kalman_step_parity_sv_f64(shared):
+@pytest.mark.parametrize("mode", MODES)
+def test_kalman_step_parity_sv_f64(mode):
     wl = workloads.stochastic_volatility(d=6, T=45, n_chains=3, delta=0.05)
-    _step_and_compare(wl, "f64", L=8, n_iters=3, tol_x=1e-9, tol_la=1e-8, shared=shared)
+    _step_and_compare(wl, "f64", L=8, n_iters=3, tol_x=1e-9, tol_la=1e-8, mode=mode)
 
 
-@pytest.mark.parametrize("shared", [False, True])
-def test_kalman_step_parity_sv_f32_small(shared):
+@pytest.mark.parametrize("mode", MODES)
+def test_kalman_step_parity_sv_f32_small(mode):
     wl = workloads.stochastic_volatility(d=6, T=45, n_chains=4, delta=0.05)
-    _step_and_compare(wl, "f32", L=8, n_iters=3, tol_x=1e-4, tol_la=TOL_LA32, shared=shared)
+    _step_and_compare(wl, "f32", L=8, n_iters=3, tol_x=1e-4, tol_la=TOL_LA32, mode=mode)
 
 
-@pytest.mark.parametrize("shared", [False, True])
-def test_kalman_step_parity_sv_f32_full_size_sampled_chains(shared):
+@pytest.mark.parametrize("mode", MODES)
+def test_kalman_step_parity_sv_f32_full_size_sampled_chains(mode):
     """d=30, T=1024, 32 chains in the benchmark's launch configuration; oracle on 4 chains."""
     wl = workloads.stochastic_volatility(d=30, T=1024, n_chains=32)
     _step_and_compare(wl, "f32", L=0, n_iters=1, chains=[0, 9, 22, 31], tol_x=1e-4,
-                      tol_la=TOL_LA32, shared=shared)
+                      tol_la=TOL_LA32, mode=mode)
 
 
-def test_shared_and_per_chain_modes_agree_at_full_size():
-    """d=30, T=1024, 32 chains: both execution modes give the same step (FP32 rounding)."""
+def test_execution_modes_agree_at_full_size():
+    """d=30, T=1024, 32 chains: the three execution modes give the same steps (FP32 rounding)."""
     wl = workloads.stochastic_volatility(d=30, T=1024, n_chains=32)
     out = []
-    for shared in (False, True):
-        s = AuxKalman(wl, dtype="f32", shared_cov=shared)
+    for mode in MODES:
+        s = AuxKalman(wl, dtype="f32", mode=mode)
         x = _tt(wl.x_init, torch.float32)
         la = torch.zeros(32, dtype=torch.float64, device="cuda")
         s.step(x, n_iters=2, iter0=0, log_alpha=la)
         torch.cuda.synchronize()
         out.append((x.double().cpu().numpy(), la.cpu().numpy()))
+        assert s.status()[0] == 0
         s.close()
-    (xa, la_a), (xb, la_b) = out
-    assert np.max(np.abs(la_a - la_b)) < TOL_LA32
-    for c in range(32):
-        assert _rel(xa[c], xb[c]) < 1e-5, c
+    xa, la_a = out[0]
+    for xb, la_b in out[1:]:
+        assert np.max(np.abs(la_a - la_b)) < TOL_LA32
+        for c in range(32):
+            assert _rel(xa[c], xb[c]) < 1e-5, c
 
 
 @pytest.mark.parametrize("dt", ["f64", "f32"])
-def test_resume_is_bitwise(dt):
+def test_cached_tables_follow_model_updates(dt):
+    """The cached covariance tables are rebuilt after aux_set_model_params and aux_set_mode."""
+    d, T, C = 4, 29, 2
+    wl = _lgssm_workload(d, T, C, seed=31)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    tol_z = 1e-9 if dt == "f64" else 1e-5
+    yt = np.random.default_rng(3).standard_normal((C, T, d))
+    s = AuxKalman(wl, dtype=dt, block_len=6, mode="cached")
+    logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
+
+    def check(model_wl):
+        s.loglik(_tt(yt, tdt), logZ)
+        torch.cuda.synchronize()
+        R = 0.5 * model_wl.delta * np.eye(d)
+        for c in range(C):
+            ref = kalman.kalman_filter(yt[c], model_wl.m0, model_wl.P0, model_wl.F, model_wl.b,
+                                       model_wl.Q, R)["logZ"]
+            assert abs(logZ[c].item() - ref) <= tol_z * abs(ref), (c, logZ[c].item(), ref)
+
+    check(wl)
+    check(wl)                       # second call reuses the tables
+    wl2 = _lgssm_workload(d, T, C, seed=32, delta=0.37)
+    s.b.aux_set_model_params(s.handle, d_x=d, T=T, n_chains=C, m0=wl2.m0, P0=wl2.P0, F=wl2.F,
+                             b=wl2.b, Q=wl2.Q, y=wl2.y, delta=wl2.delta, emis_kind=wl2.emission,
+                             dtype=s.dtype_code, R_y=wl2.Ry, obs_mask=wl2.mask)
+    check(wl2)
+    s.b.aux_set_mode(s.handle, s.b.AUX_MODE_PER_CHAIN)
+    check(wl2)
+    s.b.aux_set_mode(s.handle, s.b.AUX_MODE_CACHED_COV)
+    check(wl2)
+    s.close()
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_resume_is_bitwise(dt, mode):
     wl = workloads.stochastic_volatility(d=5, T=33, n_chains=3, delta=0.05)
     tdt = torch.float64 if dt == "f64" else torch.float32
-    s = AuxKalman(wl, dtype=dt, block_len=6)
+    s = AuxKalman(wl, dtype=dt, block_len=6, mode=mode)
     xa = _tt(wl.x_init, tdt)
     xb = _tt(wl.x_init, tdt)
     s.step(xa, n_iters=6, iter0=10)
