@@ -303,6 +303,7 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
   if (!rc) rc = dev_alloc(m, (void**)&m->lz_part, nbC * sizeof(double));
   if (!rc) rc = dev_alloc(m, (void**)&m->status_iter, (size_t)C * sizeof(int32_t));
   if (!rc) rc = dev_alloc(m, (void**)&m->status, (size_t)C * sizeof(int32_t));
+  if (!rc) rc = dev_alloc(m, (void**)&m->accept, (size_t)C * sizeof(int32_t));
   if (!rc && (cudaMemset(m->status, 0, (size_t)C * sizeof(int32_t)) != cudaSuccess ||
               cudaMemset(m->status_iter, 0, (size_t)C * sizeof(int32_t)) != cudaSuccess))
     rc = AUX_E_CUDA;
@@ -333,19 +334,29 @@ int aux_sample_path(aux_model* m, const void* ytilde, const void* eps, uint64_t 
   return m->ops->sample_path(m, ytilde, eps, iteration, xstar, logZ, m->stream);
 }
 
+// block length of the covariance scan of the table modes: short blocks put
+// most of its critical path into the O(log T) Hillis-Steele rounds
+constexpr int kCovBlockLen = 4;
+
 int aux_set_mode(aux_model* m, int32_t mode) {
   if (!m || (mode != AUX_MODE_PER_CHAIN && mode != AUX_MODE_SHARED_COV && mode != AUX_MODE_CACHED_COV))
     return AUX_E_INVALID_ARG;
   if (mode != AUX_MODE_PER_CHAIN && !m->tab) {
     const size_t es = m->esz, DD = (size_t)m->DP * m->DP;
+    m->Lc = std::min(kCovBlockLen, m->T);
+    m->nbc = (m->T + m->Lc - 1) / m->Lc;
     int rc = dev_alloc(m, &m->tab, (size_t)6 * m->T * DD * es);
+    if (!rc) rc = dev_alloc(m, &m->cagg0, (size_t)m->nbc * 3 * DD * es);
+    if (!rc) rc = dev_alloc(m, &m->cagg1, (size_t)m->nbc * 3 * DD * es);
+    if (!rc) rc = dev_alloc(m, (void**)&m->cov_ldt, (size_t)m->T * sizeof(double));
     if (!rc) rc = dev_alloc(m, &m->btab, (size_t)2 * m->nb * DD * es);
     if (!rc) rc = dev_alloc(m, &m->zb, (size_t)m->C * m->nb * m->DP * es);
+    if (!rc) rc = dev_alloc(m, &m->ms, (size_t)m->C * m->nb * m->DP * es);
     if (!rc) rc = dev_alloc(m, (void**)&m->cov_ld, (size_t)m->nb * sizeof(double));
     if (!rc) rc = dev_alloc(m, (void**)&m->cov_status, sizeof(int32_t));
     if (rc) {
-      m->tab = m->btab = m->zb = nullptr;
-      m->cov_ld = nullptr;
+      m->tab = m->btab = m->zb = m->ms = m->cagg0 = m->cagg1 = nullptr;
+      m->cov_ld = m->cov_ldt = nullptr;
       m->cov_status = nullptr;
       return rc;
     }

@@ -6,20 +6,20 @@
 // predictive and filtering covariance, every gain and every backward-sampling
 // matrix of Eq. (A.14) is a function of (m0, P0, F, Q, delta) alone: it is the
 // same for every chain and every MCMC iteration. This pass runs the matrix half
-// of the blocked scan once (one warp per scan block: conditional-filter block
-// reduction, Hillis-Steele rounds over the block aggregates, in-block filter
-// from the prefix) and writes, per step t and per block k,
+// of the blocked scan once, with its own short block length Lc (one warp per
+// scan block: conditional-filter block reduction, Hillis-Steele rounds over
+// the block aggregates, in-block filter from the prefix), and writes, per step t,
 //   tab[TW][t]  = W_t = chol(S_t)^{-1},  S_t = P^p_t + R   (lower triangular)
 //   tab[TWT][t] = W_t^T
 //   tab[TG][t]  = G_t = P^f_t F^T (P^p_{t+1})^{-1}          (G_{T-1} = 0)
 //   tab[TLS][t] = chol(Sigma_t), Sigma_t = P^f_t - G_t P^p_{t+1} G_t^T
 //                 (chol(P^f_{T-1}) at t = T-1)
-//   tab[TGP][t] = G_s G_{s+1} ... G_{t-1}  (block prefix, identity at t = s)
-//   tab[TPF][t] = P^f_t
+//   tab[TPF][t] = P^f_t,   ldt[t] = log det S_t (FP64);
+// then k_cov_products forms, for the blocks s..e of the per-chain means pass,
+//   tab[TGP][t]  = G_s G_{s+1} ... G_{t-1}  (identity at t = s)
 //   btab[BAH][k] = (I - K_e) F ... (I - K_s) F,  K_t = P^p_t S_t^{-1}
 //                  (the linear part of m^f_e as a function of m^f_{s-1})
-//   btab[BGH][k] = G_s ... G_e
-//   ld[k]        = sum over the block of log det S_t (FP64)
+//   btab[BGH][k] = G_s ... G_e,   ld[k] = sum over the block of ldt[t].
 // Because R = r I, I - K_t = r S_t^{-1} = r W_t^T W_t, so the filtering mean
 // update is m^f_t = ytilde_t - r W_t^T W_t (ytilde_t - m^p_t) and the
 // predictive likelihood term uses |W_t (ytilde_t - m^p_t)|^2 and log det S_t:
@@ -33,10 +33,11 @@ enum { TW = 0, TWT, TG, TLS, TGP, TPF, NTAB };
 enum { BAH = 0, BGH, NBTAB };
 
 template <typename Real> struct CovArgs {
-  const Real* prefix;   // scan result [nb][3 DP^2] (A, C, J); null when nb == 1
+  const Real* prefix;   // scan result [nbc][3 DP^2] (A, C, J); null when nbc == 1
   Real* tab;            // [NTAB][T][DP][DP]
-  Real* btab;           // [NBTAB][nb][DP][DP]
-  double* ld;           // [nb]
+  Real* btab;           // [NBTAB][nb][DP][DP] (means partition)
+  double* ld;           // [nb] (means partition)
+  double* ldt;          // [T]
   int32_t* status;      // [1]: ST_NOT_PD when a factorisation failed
 };
 
@@ -45,7 +46,9 @@ template <typename Real, int DP> struct CovSizes {
   static constexpr size_t MODEL = (3 * MAT + 2 * VEC) * sizeof(Real);
   static constexpr size_t RED_SMEM = MODEL + (6 * MAT + 3 * VEC) * sizeof(Real);
   static constexpr size_t SCAN_SMEM = (9 * MAT + VEC) * sizeof(Real);
-  static constexpr size_t APP_SMEM = MODEL + (11 * MAT + 3 * VEC) * sizeof(Real);
+  static constexpr size_t APP_SMEM = MODEL + (7 * MAT + 3 * VEC) * sizeof(Real);
+  // k_cov_products: the model and up to 32 exchange slots
+  static constexpr size_t PROD_SMEM = MODEL + 32 * MAT * sizeof(Real);
 };
 
 // ---------------------------------------------------------------------------
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(32, 1)
 }
 
 // ---------------------------------------------------------------------------
-// In-block covariance filter from the prefix P^f_{s-1}, with the tables.
+// In-block covariance filter from the prefix P^f_{s-1}, with the per-step tables.
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a) {
@@ -278,29 +281,16 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
   Real* SLR = SL + MAT;        // chol(P^p) (right-aligned), then chol(Sigma) row-major
   Real* SY = SLR + MAT;        // L_S^{-1} P^p, scratch
   Real* SG = SY + MAT;         // chol(S) (LS form)
-  Real* SGh = SG + MAT;        // G_s ... G_{t-1}
-  Real* SWm = SGh + MAT;       // W_t
-  Real* SA1 = SWm + MAT;
-  Real* SA2 = SA1 + MAT;
-  Real* SAH = SA2 + MAT;       // (I - K_t) F ... (I - K_s) F
-  Real* vdA = SAH + MAT;
+  Real* SWm = SG + MAT;        // W_t
+  Real* vdA = SWm + MAT;
   Real* vdB = vdA + VEC;
-  Real* vsc = vdB + VEC;
   __syncwarp();
   const int lane = threadIdx.x & 31, k = blockIdx.x;
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
   int bad = 0;
-  double ld_acc = 0.0;
   Real pprow[DP];
-  {
-    Real gi[DP];
-#pragma unroll
-    for (int j = 0; j < DP; ++j) gi[j] = (j == lane) ? (Real)1 : (Real)0;
-    st_row<Real, DP>(SGh, row, gi, act);
-    st_row<Real, DP>(SAH, row, gi, act);
-  }
   auto store_row = [&](int tb, int t, const Real* S) {
     if (!act) return;
     Real r[DP];
@@ -377,16 +367,8 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
     store_row(TG, t, SX);
     store_row(TLS, t, SLR);
   };
-  auto ghat = [&]() {      // SGh <- SGh G_t
-    Real gn[DP];
-    mm_row<Real, DP>(SGh + row * LD, SX, gn);
-    __syncwarp();
-    st_row<Real, DP>(SGh, row, gn, act);
-    __syncwarp();
-  };
-  // W_t = L_S^{-1} (columns of the identity through the forward solve), its
-  // transpose, and the running product (I - K_t) F AH = r W^T W F AH
-  auto gain_tables = [&](int t, bool with_ah) {
+  // W_t = L_S^{-1} (columns of the identity through the forward solve) and W_t^T
+  auto gain_tables = [&](int t) {
     {
       Real r[DP];
 #pragma unroll
@@ -400,30 +382,11 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
       ld_col<Real, DP>(SWm, row, c);
       st_vec<Real, DP>(a.tab + ((long)TWT * p.nT + t) * DD + row * DP, c);
     }
-    if (!with_ah) return;
-    Real x1[DP];
-    if (p.fdiag) {
-      ld_row<Real, DP>(SAH, row, x1);
-      const Real phi = sphi[row];
-#pragma unroll
-      for (int j = 0; j < DP; ++j) x1[j] *= phi;
-    } else {
-      mm_row<Real, DP>(sF + row * LD, SAH, x1);
-    }
-    st_row<Real, DP>(SA1, row, x1, act);
-    __syncwarp();
-    Real x2[DP];
-    mm_row<Real, DP>(SWm + row * LD, SA1, x2);
-    st_row<Real, DP>(SA2, row, x2, act);
-    __syncwarp();
-    Real ah[DP];
-    mm_col<Real, DP>(SWm, row, SA2, ah);
-#pragma unroll
-    for (int j = 0; j < DP; ++j) ah[j] *= p.r;
-    st_row<Real, DP>(SAH, row, ah, act);
-    __syncwarp();
+    double lg = (lane < p.d) ? -log((double)vdB[lane]) : 0.0;
+    lg = warp_sum<double>(lg);
+    if (lane == 0) a.ldt[t] = 2.0 * lg;
   };
-  // Y = L_S^{-1} P^p (columns of SY), P^f -> SP, log det S
+  // Y = L_S^{-1} P^p (columns of SY), P^f -> SP
   auto update = [&](int t) {
     {
       Real rr[DP];
@@ -445,9 +408,6 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
       st_row<Real, DP>(SP, row, pf, act);
     }
     __syncwarp();
-    double lg = (lane < p.d) ? -log((double)vdB[lane]) : 0.0;
-    lg = warp_sum<double>(lg);
-    ld_acc += 2.0 * lg;
     store_row(TPF, t, SP);
     __syncwarp();
   };
@@ -463,16 +423,13 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
     predict();
   }
   factor_S();
-  store_row(TGP, s, SGh);
-  gain_tables(s, k > 0);
+  gain_tables(s);
   update(s);
   for (int t = s + 1; t <= e; ++t) {
     predict();
     factor_2();
     epilogue(t - 1);
-    ghat();
-    store_row(TGP, t, SGh);
-    gain_tables(t, true);
+    gain_tables(t);
     update(t);
   }
   if (e < p.nT - 1) {
@@ -492,16 +449,138 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
     store_row(TG, e, SX);
     store_row(TLS, e, SLR);
   }
-  ghat();
-  if (act) {
-    Real r[DP];
-    ld_row<Real, DP>(SGh, row, r);
-    st_vec<Real, DP>(a.btab + ((long)BGH * p.nb + k) * DD + row * DP, r);
-    ld_row<Real, DP>(SAH, row, r);
-    st_vec<Real, DP>(a.btab + ((long)BAH * p.nb + k) * DD + row * DP, r);
-  }
-  if (lane == 0) a.ld[k] = ld_acc;
   if (bad && lane == 0) atomicOr(a.status, ST_NOT_PD);
+}
+
+// ---------------------------------------------------------------------------
+// Block products of the means partition (p.L, p.nb): block k = steps s..e.
+// Warp w takes the consecutive steps of chunk w (chunk = ceil(n / warps)) and
+// forms P_w = G_t0 ... G_t1 and Q_w = M_t1 ... M_t0, M_t = (I - K_t) F =
+// r W_t^T W_t F; Hillis-Steele rounds over the warps (one shared slot each)
+// give the inclusive products, from which each warp writes G_s ... G_{t-1}
+// for its steps; the last warp holds GH_k and AH_k. One slot per warp when
+// every chunk is a single step, two otherwise (at most 16 warps then).
+// ---------------------------------------------------------------------------
+template <typename Real, int DP>
+__global__ void __launch_bounds__(1024) k_cov_products(KP<Real> p, CovArgs<Real> a) {
+  using Z = CovSizes<Real, DP>;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
+  constexpr long DD = (long)DP * DP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  Real* sF = sm;
+  Real* sFT = sF + MAT;
+  Real* sQ = sFT + MAT;
+  Real* sb = sQ + MAT;
+  load_model_slots<Real, DP>(p, sF, sFT, sQ, sb);
+  const Real* sphi = sb + VEC;
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x;
+  const int s = k * p.L, e = min(p.nT, s + p.L) - 1, n = e - s + 1;
+  const int chunk = (n + nw - 1) / nw;
+  const int spw = chunk > 1 ? 2 : 1;
+  Real* slot0 = sb + 2 * VEC;
+  Real* SX = slot0 + warp * spw * MAT;     // exchange slot
+  Real* SY = SX + (spw - 1) * MAT;         // staging slot (= SX when spw == 1)
+  const int t0 = s + warp * chunk, t1 = min(e, t0 + chunk - 1);
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  __syncthreads();
+  auto load_slot = [&](Real* S, const Real* g) {
+    __syncwarp();
+    Real r[DP];
+    ld_vec<Real, DP>(g + row * DP, r);
+    st_row<Real, DP>(S, row, r, act);
+    __syncwarp();
+  };
+  Real P[DP], Q[DP];
+#pragma unroll
+  for (int j = 0; j < DP; ++j) P[j] = Q[j] = (j == lane) ? (Real)1 : (Real)0;
+  for (int t = t0; t <= t1; ++t) {
+    // M_t row: r (W^T W F)[row]
+    load_slot(SY, a.tab + ((long)TW * p.nT + t) * DD);
+    Real mr[DP];
+    mm_col<Real, DP>(SY, row, SY, mr);
+    if (p.fdiag) {
+      Real ph[DP];
+      ld_vec<Real, DP>(sphi, ph);
+#pragma unroll
+      for (int j = 0; j < DP; ++j) mr[j] *= p.r * ph[j];
+    } else {
+      __syncwarp();
+      st_row<Real, DP>(SY, row, mr, act);
+      __syncwarp();
+      mm_row<Real, DP>(SY + row * LD, sF, mr);
+#pragma unroll
+      for (int j = 0; j < DP; ++j) mr[j] *= p.r;
+    }
+    if (t == t0) {
+#pragma unroll
+      for (int j = 0; j < DP; ++j) Q[j] = mr[j];
+    } else {   // Q <- M_t Q
+      __syncwarp();
+      st_row<Real, DP>(SY, row, mr, act);
+      st_row<Real, DP>(SX, row, Q, act);
+      __syncwarp();
+      mm_row<Real, DP>(SY + row * LD, SX, Q);
+      __syncwarp();
+      st_row<Real, DP>(SX, row, P, act);
+    }
+    load_slot(SY, a.tab + ((long)TG * p.nT + t) * DD);
+    if (t == t0) ld_row<Real, DP>(SY, row, P);
+    else mm_row<Real, DP>(SX + row * LD, SY, P);   // P <- P G_t
+  }
+  // inclusive products over the warps: P_w <- P_{w-off} P_w, Q_w <- Q_w Q_{w-off}
+  for (int off = 1; off < nw; off *= 2) {
+    Real* partner = slot0 + max(0, warp - off) * spw * MAT;
+    st_row<Real, DP>(SX, row, P, act);
+    __syncthreads();
+    Real nxt[DP];
+    if (warp >= off) mm_row<Real, DP>(partner + row * LD, SX, nxt);
+    __syncthreads();
+    if (warp >= off) {
+#pragma unroll
+      for (int j = 0; j < DP; ++j) P[j] = nxt[j];
+    }
+    st_row<Real, DP>(SX, row, Q, act);
+    __syncthreads();
+    if (warp >= off) mm_row<Real, DP>(SX + row * LD, partner, nxt);
+    __syncthreads();
+    if (warp >= off) {
+#pragma unroll
+      for (int j = 0; j < DP; ++j) Q[j] = nxt[j];
+    }
+  }
+  // G_s ... G_{t-1} for the warp's steps from the product of the earlier chunks
+  st_row<Real, DP>(SX, row, P, act);
+  __syncthreads();
+  Real R[DP];
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < DP; ++j) R[j] = (j == lane) ? (Real)1 : (Real)0;
+  } else {
+    ld_row<Real, DP>(slot0 + (warp - 1) * spw * MAT, row, R);
+  }
+  __syncthreads();
+  for (int t = t0; t <= t1; ++t) {
+    if (act) st_vec<Real, DP>(a.tab + ((long)TGP * p.nT + t) * DD + row * DP, R);
+    if (t < t1) {   // R <- R G_t
+      __syncwarp();
+      st_row<Real, DP>(SX, row, R, act);
+      load_slot(SY, a.tab + ((long)TG * p.nT + t) * DD);
+      mm_row<Real, DP>(SX + row * LD, SY, R);
+    }
+  }
+  if (warp == (n - 1) / chunk && act) {
+    st_vec<Real, DP>(a.btab + ((long)BGH * p.nb + k) * DD + row * DP, P);
+    st_vec<Real, DP>(a.btab + ((long)BAH * p.nb + k) * DD + row * DP, Q);
+  }
+  if (warp == 0) {
+    double acc = 0.0;
+    for (int t = s + lane; t <= e; t += 32) acc += a.ldt[t];
+    acc = warp_sum<double>(acc);
+    if (lane == 0) a.ld[k] = acc;
+  }
 }
 
 }  // namespace auxk

@@ -650,4 +650,31 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (16 bytes per instruction, L1 bypassed)
+// used to stage the next step's tables while the current step computes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Copy ntab row-major DP x DP matrices, src0 + j * stride (j < ntab), into
+// consecutive padded slots at dst (all threads of the CTA take part), then
+// close the copy group.
+template <typename T, int DP>
+__device__ __forceinline__ void stage_mats(T* dst, const T* src0, long stride, int ntab) {
+  constexpr int N = Vec16<T>::N, CPR = DP / N, LD = Lay<T, DP>::LD, MAT = Lay<T, DP>::MAT;
+  constexpr int PER = DP * CPR;
+  for (int q = threadIdx.x; q < ntab * PER; q += blockDim.x) {
+    const int j = q / PER, rem = q - j * PER, r = rem / CPR, cc = rem - r * CPR;
+    cp_async16(dst + j * MAT + r * LD + cc * N, src0 + j * stride + r * DP + cc * N);
+  }
+  cp_async_commit();
+}
+
 }  // namespace auxk

@@ -30,15 +30,18 @@ struct aux_model {
   void *G = nullptr, *U = nullptr, *gum = nullptr, *guv = nullptr;
   double *fq = nullptr, *fld = nullptr, *mh_part = nullptr, *lz_part = nullptr;
   int32_t *status_iter = nullptr, *status = nullptr;
+  int32_t *accept = nullptr;  // [C] this step's MH decisions
   // gradient (aux_loglik_grad): theta constants and lazily allocated smoother buffers
   int grad_ok = 0;           // the model has the SV parameterisation
   double *gconst = nullptr;  // mu, phi, L, Q, Q^{-1}, P0^{-1} (FP64, unpadded)
   void *Sig = nullptr, *sgu = nullptr, *gpart = nullptr, *s0 = nullptr;
   double *opart = nullptr;
   // covariance tables of the table modes (aux_cov.cuh), allocated on the first switch
-  void *tab = nullptr, *btab = nullptr, *zb = nullptr;
-  double *cov_ld = nullptr;
+  void *tab = nullptr, *btab = nullptr, *zb = nullptr, *ms = nullptr;
+  void *cagg0 = nullptr, *cagg1 = nullptr;   // covariance scan buffers [nbc][3 DP^2]
+  double *cov_ld = nullptr, *cov_ldt = nullptr;
   int32_t *cov_status = nullptr;
+  int Lc = 0, nbc = 0;       // block length and block count of the covariance scan
   int cov_valid = 0;         // the tables match the current model
   const AuxOps *ops = nullptr;
   std::vector<void *> allocs;

@@ -19,7 +19,7 @@
 //                        k_sample_backward applies them), fused with the
 //                        linearisation at x* and the MH partial sums.
 //   reverse filter       the same filter on ytilde* (log-likelihood terms only).
-//   k_mh                 log alpha, the MH test and the state update.
+//   k_mh, k_commit       log alpha and the MH test; x <- x* for the accepted chains.
 //
 // The element operator is evaluated in a Cholesky form: with C_i = U U^T and
 // N = I + U^T J_j U = L L^T (SPD, eigenvalues >= 1), B = U L^{-T}:
@@ -887,6 +887,68 @@ template <typename Real> struct BackArgs {
   double* mh_part;
 };
 
+// The per-step inputs of mh_step_terms for the lane's coordinate (lane < d):
+// x_t, u_t, v_t and y_t, loaded separately so that callers can fetch them early.
+template <typename Real> struct MhIn {
+  Real xo, ui, vi, yi;
+};
+
+template <typename Real>
+__device__ __forceinline__ MhIn<Real> mh_load(const KP<Real>& p, const BackArgs<Real>& a, long ct,
+                                              int t, int lane) {
+  MhIn<Real> q{(Real)0, (Real)0, (Real)0, (Real)0};
+  if (lane < p.d) {
+    const long idx = ct * p.d + lane;
+    q.xo = a.x[idx];
+    q.ui = a.u[idx];
+    q.vi = a.v[idx];
+    q.yi = p.y[(p.y_per_chain ? ct : (long)t) * p.d + lane];
+  }
+  return q;
+}
+
+// The step-t terms of log alpha for the lane's coordinate (simplified form of
+// Algorithm 2's ratio): gamma(x*) - gamma(x) + v (u - x*) + (r/2) v^2
+// - v* (u - x) - (r/2) v*^2, with v* = grad log h at x*; also writes
+// ytilde*_t = u_t + r v*_t. sRy: R_y^{-1} rows (linear-Gaussian emission),
+// vxs: a warp-private vector slot. All lanes of the warp call it.
+template <typename Real, int DP>
+__device__ __forceinline__ double mh_step_terms(const KP<Real>& p, const BackArgs<Real>& a, long ct,
+                                                int t, Real xi, const MhIn<Real>& in,
+                                                const Real* sRy, Real* vxs, int lane, int row) {
+  const bool act = lane < DP;
+  const bool obs = !p.mask || p.mask[t];
+  Real vsi = 0;
+  if (p.emis == AUX_EMIS_LINEAR_GAUSSIAN) {
+    __syncwarp();
+    if (act) vxs[lane] = (lane < p.d) ? in.yi - xi : (Real)0;
+    __syncwarp();
+    Real ry[DP];
+    ld_row<Real, DP>(sRy, row, ry);
+    vsi = dot_rv<Real, DP>(ry, vxs);
+  }
+  double acc = 0.0;
+  if (lane < p.d) {
+    const Real xo = in.xo, ui = in.ui, vi = in.vi, yi = in.yi;
+    Real gdiff = 0;
+    if (obs) {
+      if (p.emis == AUX_EMIS_SV) {
+        vsi = (Real)-0.5 + (Real)0.5 * yi * yi * exp(-xi);
+        gdiff = (Real)-0.5 * (xi - xo) - (Real)0.5 * yi * yi * (exp(-xi) - exp(-xo));
+      } else {
+        gdiff = (Real)-0.5 * (yi - xi) * vsi + (Real)0.5 * (yi - xo) * vi;
+      }
+    } else {
+      vsi = 0;
+    }
+    const Real fwd = vi * (ui - xi) + (Real)0.5 * p.r * vi * vi;
+    const Real rev = vsi * (ui - xo) + (Real)0.5 * p.r * vsi * vsi;
+    acc = (double)gdiff + (double)fwd - (double)rev;
+    a.yts[ct * p.d + lane] = ui + p.r * vsi;
+  }
+  return acc;
+}
+
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32 * Sizes<Real, DP>::BWD_WPC)
     k_sample_backward(KP<Real> p, BackArgs<Real> a) {
@@ -932,39 +994,8 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::BWD_WPC)
       xi = dot_rv<Real, DP>(g, vx) + a.U[ct * DP + row];
     }
     if (lane < p.d) a.xs[ct * p.d + lane] = xi;
-    if (a.mh) {
-      const Real* yr = p.y + (p.y_per_chain ? ct : (long)t) * p.d;
-      const bool obs = !p.mask || p.mask[t];
-      Real vsi = 0;
-      if (p.emis == AUX_EMIS_LINEAR_GAUSSIAN) {
-        __syncwarp();
-        if (act) vxs[lane] = (lane < p.d) ? yr[lane] - xi : (Real)0;
-        __syncwarp();
-        Real ry[DP];
-        ld_row<Real, DP>(sRy, row, ry);
-        vsi = dot_rv<Real, DP>(ry, vxs);
-      }
-      if (lane < p.d) {
-        const long idx = ct * p.d + lane;
-        const Real xo = a.x[idx], ui = a.u[idx], vi = a.v[idx];
-        const Real yi = yr[lane];
-        Real gdiff = 0;
-        if (obs) {
-          if (p.emis == AUX_EMIS_SV) {
-            vsi = (Real)-0.5 + (Real)0.5 * yi * yi * exp(-xi);
-            gdiff = (Real)-0.5 * (xi - xo) - (Real)0.5 * yi * yi * (exp(-xi) - exp(-xo));
-          } else {
-            gdiff = (Real)-0.5 * (yi - xi) * vsi + (Real)0.5 * (yi - xo) * vi;
-          }
-        } else {
-          vsi = 0;
-        }
-        const Real fwd = vi * (ui - xi) + (Real)0.5 * p.r * vi * vi;
-        const Real rev = vsi * (ui - xo) + (Real)0.5 * p.r * vsi * vsi;
-        acc += (double)gdiff + (double)fwd - (double)rev;
-        a.yts[idx] = ui + p.r * vsi;
-      }
-    }
+    if (a.mh) acc += mh_step_terms<Real, DP>(p, a, ct, t, xi, mh_load<Real>(p, a, ct, t, lane), sRy,
+                                             vxs, lane, row);
   }
   if (a.mh) {
     acc = warp_sum<double>(acc);
@@ -973,15 +1004,15 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::BWD_WPC)
 }
 
 // ---------------------------------------------------------------------------
-// MH test and state update, one CTA per chain.
+// MH test, one CTA per chain: log alpha from the partial sums, the Philox
+// uniform of the (chain, iteration), the accept flag for k_commit.
 // ---------------------------------------------------------------------------
 template <typename Real>
-__global__ void k_mh(KP<Real> p, Real* __restrict__ x, const Real* __restrict__ xs,
-                     const double* __restrict__ mh_part, const double* __restrict__ lz_part,
-                     uint64_t iter, uint32_t* acc_count, double* log_alpha, int32_t* status) {
+__global__ void k_mh(KP<Real> p, const double* __restrict__ mh_part,
+                     const double* __restrict__ lz_part, uint64_t iter, uint32_t* acc_count,
+                     double* log_alpha, int32_t* status, int32_t* __restrict__ accept) {
   const int c = blockIdx.x;
   __shared__ double red[32];
-  __shared__ int accept;
   double sacc = 0.0;
   for (int k = threadIdx.x; k < p.nb; k += blockDim.x)
     sacc += mh_part[(long)c * p.nb + k] + lz_part[(long)c * p.nb + k];
@@ -995,18 +1026,24 @@ __global__ void k_mh(KP<Real> p, Real* __restrict__ x, const Real* __restrict__ 
     if (!isfinite(la)) st |= ST_NONFINITE;
     const uint4 r = philox_word(p.seed, (uint32_t)c, iter, PURPOSE_MH, 0, 0);
     const double lu = log(u01<double>(r.x));
-    accept = (st == 0) && (lu < la);
+    const int acc = (st == 0) && (lu < la);
+    accept[c] = acc;
     status[c] |= st;
     if (log_alpha) log_alpha[c] = la;
-    if (acc_count && accept) acc_count[c] += 1;
+    if (acc_count && acc) acc_count[c] += 1;
   }
-  __syncthreads();
-  if (accept) {
-    const long n = (long)p.nT * p.d;
-    Real* xc = x + (long)c * n;
-    const Real* xsc = xs + (long)c * n;
-    for (long q = threadIdx.x; q < n; q += blockDim.x) xc[q] = xsc[q];
-  }
+}
+
+// ---------------------------------------------------------------------------
+// State update x <- x* for the accepted chains, over the whole grid.
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void k_commit(KP<Real> p, Real* __restrict__ x, const Real* __restrict__ xs,
+                         const int32_t* __restrict__ accept) {
+  const long per_chain = (long)p.nT * p.d;
+  const long n = (long)p.C * per_chain;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    if (accept[i / per_chain]) x[i] = xs[i];
 }
 
 }  // namespace auxk

@@ -1,19 +1,26 @@
-// aux_means.cuh — the per-chain half of the parallel filter when the
-// covariance tables of aux_cov.cuh are available: every step is a handful of
-// DP x DP matrix-vector products with matrices shared by all chains.
+// aux_means.cuh — the per-chain half of the parallel filter and of the
+// backward sampler when the covariance tables of aux_cov.cuh are available:
+// every step is a few DP x DP matrix-vector products with matrices shared by
+// all chains.
 //
 // Filtering means (Kalman filter algorithm, Appendix A.1, with H = I, R = r I):
 //   m^p_0 = m0,  m^p_t = F m^f_{t-1} + b,
 //   w_t = W_t (ytilde_t - m^p_t),  m^f_t = ytilde_t - r W_t^T w_t,
 //   log-likelihood term  -(d/2) log 2 pi - (1/2) (log det S_t + |w_t|^2).
 // The recursion is affine in m^f_{s-1} with linear part AH_k over a block, so
-// the blocked scan keeps the structure of the full filter: k_mf_reduce runs each
-// block from m^f_{s-1} = 0 (block 0 from m0) and keeps the block-end mean z_k;
-// k_mf_apply composes the aggregates of the earlier blocks (m^f_{e_k} =
-// AH_k m^f_{e_{k-1}} + z_k) and re-runs its block from the true start, with
-// the backward elements of Eq. (A.14): U_t = m^f_t - G_t m^p_{t+1} +
-// chol(Sigma_t) eps_t and the block aggregate sum_t (G_s ... G_{t-1}) U_t that
-// the (G, U) suffix scan of Proposition A.1 (k_sample_backward) consumes.
+// the blocked scan keeps the structure of the full filter (Appendix A.2.1):
+//   k_mf_reduce    each block from m^f_{s-1} = 0 (block 0 from m0): block-end z_k;
+//   k_mean_cross   per chain, m^f_{e_k} = AH_k m^f_{e_{k-1}} + z_k over the blocks;
+//   k_mf_apply     each block again from its true start, with the likelihood
+//                  terms and the backward elements of Eq. (A.14),
+//                  U_t = m^f_t - G_t m^p_{t+1} + chol(Sigma_t) eps_t, and the block
+//                  aggregate sum_t (G_s ... G_{t-1}) U_t of the (G, U) scan;
+//   k_mean_cross   (backward) per chain, x*_{s_k} = GH_k x*_{e_k + 1} + Ubar_k;
+//   k_mb_apply     x*_t = G_t x*_{t+1} + U_t inside each block (Proposition A.1),
+//                  with the MH terms at x* and ytilde*.
+// One CTA runs MEAN_WPC chains of the same block, one warp per chain (lane =
+// row), so the tables of step t are staged once per CTA in shared memory,
+// double-buffered with asynchronous copies one step ahead.
 #pragma once
 #include "aux_cov.cuh"
 
@@ -33,6 +40,7 @@ template <typename Real> struct MeanArgs {
   uint64_t iter;
   // k_mf_apply
   int flags;                  // APPLY_EPI | APPLY_STORE_Q | APPLY_REV_DIFF | APPLY_LOGZ
+  const Real* mstart;         // [C][nb][DP] m^f_{s_k - 1} (k >= 1)
   Real* U;                    // [C][T][DP]
   Real* guv;                  // [C][nb][DP]
   double* fqb;                // [C][nb] sum of |w_t|^2 over the block
@@ -43,25 +51,16 @@ template <typename Real> struct MeanArgs {
   int32_t* status;            // optional sticky per-chain status
 };
 
-constexpr int MEAN_WPC = 8;   // warps (chain-blocks) per CTA
+constexpr int MEAN_WPC = 8;   // chains (warps) per CTA
 
-// sum_j grow[j] v[j]: grow a 16-byte aligned global row (read-only path),
-// v a shared vector slot (broadcast reads)
-template <typename Real, int DP>
-__device__ __forceinline__ Real gdot(const Real* __restrict__ grow, const Real* v) {
-  using V = typename Vec16<Real>::V;
-  constexpr int N = Vec16<Real>::N;
-  Real acc[4] = {(Real)0, (Real)0, (Real)0, (Real)0};
-#pragma unroll
-  for (int q = 0; q < DP / N; ++q) {
-    Real ga[N], vb[N];
-    unpack<Real>(__ldg(reinterpret_cast<const V*>(grow) + q), ga);
-    unpack<Real>(reinterpret_cast<const V*>(v)[q], vb);
-#pragma unroll
-    for (int j = 0; j < N; ++j) acc[(q * N + j) & 3] = fma(ga[j], vb[j], acc[(q * N + j) & 3]);
+template <typename Real, int DP> struct MeanSizes {
+  static constexpr int MAT = Lay<Real, DP>::MAT, VEC = Lay<Real, DP>::VEC;
+  // two staging buffers of NT tables, R_y^{-1}, three vector slots per warp
+  static constexpr size_t smem(int nt) {
+    return (size_t)(2 * nt * MAT + MAT + MEAN_WPC * 3 * VEC) * sizeof(Real);
   }
-  return (acc[0] + acc[1]) + (acc[2] + acc[3]);
-}
+  static constexpr size_t RED = smem(2), APP = smem(5), BWD = smem(1), CROSS = smem(1);
+};
 
 // lane value -> vector slot (all lanes of the warp call it)
 template <typename Real, int DP>
@@ -76,134 +75,246 @@ template <typename Real, int DP>
 __device__ __forceinline__ Real predict_mean(const KP<Real>& p, Real m, Real* vs, int lane, int row) {
   if (p.fdiag) return fma(p.F[row * DP + row], m, p.b[row]);
   put_vec<Real, DP>(vs, m, lane);
-  return gdot<Real, DP>(p.F + row * DP, vs) + p.b[row];
+  Real f[DP];
+  ld_vec<Real, DP>(p.F + row * DP, f);
+  return dot_rv<Real, DP>(f, vs) + p.b[row];
+}
+
+// R_y^{-1} rows into a padded slot (linear-Gaussian emission)
+template <typename Real, int DP>
+__device__ __forceinline__ void load_ryinv(const KP<Real>& p, Real* sRy) {
+  constexpr int LD = Lay<Real, DP>::LD;
+  for (int q = threadIdx.x; q < DP * DP; q += blockDim.x) sRy[(q / DP) * LD + q % DP] = p.Ryinv[q];
 }
 
 // ---------------------------------------------------------------------------
 // Block-local filtering means from a zero start (block 0: from m0), optionally
 // fused with the linearisation (A1) and the auxiliary draw (A2).
+// Grid: nb * ceil(C / MEAN_WPC) CTAs; CTA (g, k) runs chains g*MEAN_WPC + warp.
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_reduce(KP<Real> p, MeanArgs<Real> a) {
-  constexpr int VEC = Lay<Real, DP>::VEC;
+  using Z = MeanSizes<Real, DP>;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
   constexpr long DD = (long)DP * DP;
-  __shared__ __align__(16) Real vsm[MEAN_WPC * 3 * VEC];
+  constexpr int NT = 2;   // W, W^T
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* buf = reinterpret_cast<Real*>(smem_raw);
+  Real* sRy = buf + 2 * NT * MAT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int item = blockIdx.x * MEAN_WPC + warp;
-  if (item >= p.C * p.nb) return;
-  const int k = item / p.C, c = item % p.C;
+  Real* vr = sRy + MAT + warp * 3 * VEC;
+  Real* vw = vr + VEC;
+  Real* vq = vw + VEC;
+  const int k = blockIdx.x % p.nb, c = (blockIdx.x / p.nb) * MEAN_WPC + warp;
+  const bool valid = c < p.C;
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
-  Real* vr = vsm + warp * 3 * VEC;
-  Real* vw = vr + VEC;
-  Real* vq = vw + VEC;
-  const Real* W = a.tab + (long)TW * p.nT * DD;
-  const Real* WT = a.tab + (long)TWT * p.nT * DD;
+  const long tstride = (long)p.nT * DD;
+  if (a.x && p.emis == AUX_EMIS_LINEAR_GAUSSIAN) load_ryinv<Real, DP>(p, sRy);
+  stage_mats<Real, DP>(buf, a.tab + (long)TW * tstride + s * DD, tstride, NT);
+  // the lane's inputs of step t, fetched one step ahead: x_t and y_t, or ytilde_t
+  auto fetch = [&](int t, Real& xv, Real& yv) {
+    xv = 0; yv = 0;
+    if (!valid || lane >= p.d) return;
+    const long ct = (long)c * p.nT + t;
+    if (a.x) {
+      xv = a.x[ct * p.d + lane];
+      yv = p.y[(p.y_per_chain ? ct : (long)t) * p.d + lane];
+    } else {
+      yv = a.yt[ct * p.d + lane];
+    }
+  };
+  Real xn, yn;
+  fetch(s, xn, yn);
   Real m = 0;
   for (int t = s; t <= e; ++t) {
-    const long ct = (long)c * p.nT + t;
-    Real yti = 0;
-    if (a.x) {
-      const Real* yr = p.y + (p.y_per_chain ? ct : (long)t) * p.d;
-      const bool obs = !p.mask || p.mask[t];
-      const Real xi = (lane < p.d) ? a.x[ct * p.d + lane] : (Real)0;
-      Real vi = 0;
-      if (p.emis == AUX_EMIS_LINEAR_GAUSSIAN) {
-        put_vec<Real, DP>(vq, (lane < p.d) ? yr[lane] - xi : (Real)0, lane);
-        vi = gdot<Real, DP>(p.Ryinv + row * DP, vq);
-      } else if (lane < p.d) {
-        vi = (Real)-0.5 + (Real)0.5 * yr[lane] * yr[lane] * exp(-xi);
+    const int cur = (t - s) & 1;
+    const Real xi = xn, yv = yn;
+    if (t < e) fetch(t + 1, xn, yn);
+    if (t < e) stage_mats<Real, DP>(buf + (cur ^ 1) * NT * MAT, a.tab + (long)TW * tstride + (t + 1) * DD, tstride, NT);
+    else cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    if (valid) {
+      const Real* sW = buf + cur * NT * MAT;
+      const Real* sWT = sW + MAT;
+      const long ct = (long)c * p.nT + t;
+      Real yti = 0;
+      if (a.x) {
+        const bool obs = !p.mask || p.mask[t];
+        Real vi = 0;
+        if (p.emis == AUX_EMIS_LINEAR_GAUSSIAN) {
+          put_vec<Real, DP>(vq, (lane < p.d) ? yv - xi : (Real)0, lane);
+          vi = dot_row_vec<Real, DP>(sRy + row * LD, vq);
+        } else if (lane < p.d) {
+          vi = (Real)-0.5 + (Real)0.5 * yv * yv * exp(-xi);
+        }
+        if (!obs) vi = 0;
+        if (lane < p.d) {
+          const Real ep = philox_normal<Real>(p.seed, (uint32_t)c, a.iter, PURPOSE_AUX, (uint32_t)t, lane);
+          const Real ui = xi + p.sqrt_r * ep;
+          yti = ui + p.r * vi;
+          a.u[ct * p.d + lane] = ui;
+          a.v[ct * p.d + lane] = vi;
+          a.yt[ct * p.d + lane] = yti;
+        }
+      } else {
+        yti = yv;
       }
-      if (!obs) vi = 0;
-      if (lane < p.d) {
-        const Real ep = philox_normal<Real>(p.seed, (uint32_t)c, a.iter, PURPOSE_AUX, (uint32_t)t, lane);
-        const Real ui = xi + p.sqrt_r * ep;
-        yti = ui + p.r * vi;
-        a.u[ct * p.d + lane] = ui;
-        a.v[ct * p.d + lane] = vi;
-        a.yt[ct * p.d + lane] = yti;
-      }
-    } else if (lane < p.d) {
-      yti = a.yt[ct * p.d + lane];
+      const Real mp = (t == 0) ? p.m0[row] : predict_mean<Real, DP>(p, m, vq, lane, row);
+      put_vec<Real, DP>(vr, act ? yti - mp : (Real)0, lane);
+      const Real wi = dot_row_vec<Real, DP>(sW + row * LD, vr);
+      put_vec<Real, DP>(vw, wi, lane);
+      m = yti - p.r * dot_row_vec<Real, DP>(sWT + row * LD, vw);
     }
-    const Real mp = (t == 0) ? p.m0[row] : predict_mean<Real, DP>(p, m, vq, lane, row);
-    put_vec<Real, DP>(vr, act ? yti - mp : (Real)0, lane);
-    const Real wi = gdot<Real, DP>(W + t * DD + row * DP, vr);
-    put_vec<Real, DP>(vw, wi, lane);
-    m = yti - p.r * gdot<Real, DP>(WT + t * DD + row * DP, vw);
+    __syncthreads();
   }
-  if (act) a.z[((long)c * p.nb + k) * DP + lane] = m;
-  if (a.x && k == 0 && lane == 0) p.status_iter[c] = *a.cov_status;
+  if (valid && act) a.z[((long)c * p.nb + k) * DP + lane] = m;
+  if (valid && a.x && k == 0 && lane == 0) p.status_iter[c] = *a.cov_status;
 }
 
 // ---------------------------------------------------------------------------
-// Filtering means from the true block start, likelihood terms, and (APPLY_EPI)
-// the backward elements U_t with the block aggregate of the (G, U) scan.
+// Composition of the block aggregates, one warp per chain.
+//   forward  (mats = AH): out[c][k] = m^f_{e_{k-1}}, k = 1 .. nb-1, from
+//            m^f_{e_0} = in[c][0] and m^f_{e_k} = AH_k m^f_{e_{k-1}} + in[c][k];
+//   backward (mats = GH): out[c][k] = x*_{e_k + 1}, k = nb-1 .. 0, from
+//            out[c][nb-1] = 0 and x*_{e_{k-1} + 1} = GH_k out[c][k] + in[c][k].
+// Grid: ceil(C / MEAN_WPC) CTAs.
+// ---------------------------------------------------------------------------
+template <typename Real, int DP>
+__global__ void __launch_bounds__(32 * MEAN_WPC)
+    k_mean_cross(KP<Real> p, const Real* __restrict__ mats, const Real* __restrict__ in,
+                 Real* __restrict__ out, int backward) {
+  using Z = MeanSizes<Real, DP>;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
+  constexpr long DD = (long)DP * DP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* buf = reinterpret_cast<Real*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Real* vq = buf + 3 * MAT + warp * 3 * VEC;
+  const int c = blockIdx.x * MEAN_WPC + warp;
+  const bool valid = c < p.C;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  const long cb = (long)(valid ? c : 0) * p.nb;
+  // matrices used, in order: forward AH_1 .. AH_{nb-2}; backward GH_{nb-1} .. GH_1
+  const int n = backward ? p.nb - 1 : max(0, p.nb - 2);
+  auto kk_of = [&](int j) { return backward ? p.nb - 1 - j : 1 + j; };
+  Real m = 0;
+  if (backward) {
+    if (valid && act) out[(cb + p.nb - 1) * DP + lane] = (Real)0;
+  } else {
+    m = in[cb * DP + row];
+    if (valid && act && p.nb > 1) out[(cb + 1) * DP + lane] = m;
+  }
+  if (n > 0) stage_mats<Real, DP>(buf, mats + kk_of(0) * DD, DD, 1);
+  Real inn = (n > 0) ? in[(cb + kk_of(0)) * DP + row] : (Real)0;
+  for (int j = 0; j < n; ++j) {
+    const int cur = j & 1, kk = kk_of(j);
+    const Real inc = inn;
+    if (j + 1 < n) {
+      inn = in[(cb + kk_of(j + 1)) * DP + row];
+      stage_mats<Real, DP>(buf + (cur ^ 1) * MAT, mats + kk_of(j + 1) * DD, DD, 1);
+    } else {
+      cp_async_commit();
+    }
+    cp_async_wait<1>();
+    __syncthreads();
+    if (valid) {
+      put_vec<Real, DP>(vq, m, lane);
+      m = dot_row_vec<Real, DP>(buf + cur * MAT + row * LD, vq) + inc;
+      if (act) out[(cb + (backward ? kk - 1 : kk + 1)) * DP + lane] = m;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Filtering means from the true block start, likelihood terms and
+// (APPLY_EPI) the backward elements with the block aggregate.
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_apply(KP<Real> p, MeanArgs<Real> a) {
-  constexpr int VEC = Lay<Real, DP>::VEC;
+  using Z = MeanSizes<Real, DP>;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
   constexpr long DD = (long)DP * DP;
-  __shared__ __align__(16) Real vsm[MEAN_WPC * 3 * VEC];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const bool epi = a.flags & APPLY_EPI;
+  const int NT = epi ? 5 : 2;   // W, W^T (, G, chol(Sigma), G_s .. G_{t-1})
+  Real* buf = reinterpret_cast<Real*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int item = blockIdx.x * MEAN_WPC + warp;
-  if (item >= p.C * p.nb) return;
-  const int k = item / p.C, c = item % p.C;
+  Real* vr = buf + 2 * 5 * MAT + MAT + warp * 3 * VEC;
+  Real* vw = vr + VEC;
+  Real* vq = vw + VEC;
+  const int k = blockIdx.x % p.nb, c = (blockIdx.x / p.nb) * MEAN_WPC + warp;
+  const bool valid = c < p.C;
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
-  Real* vr = vsm + warp * 3 * VEC;
-  Real* vw = vr + VEC;
-  Real* vq = vw + VEC;
-  const Real* W = a.tab + (long)TW * p.nT * DD;
-  const Real* WT = a.tab + (long)TWT * p.nT * DD;
-  const Real* G = a.tab + (long)TG * p.nT * DD;
-  const Real* LS = a.tab + (long)TLS * p.nT * DD;
-  const Real* GP = a.tab + (long)TGP * p.nT * DD;
-  const Real* PF = a.tab + (long)TPF * p.nT * DD;
-  const Real* AH = a.btab + (long)BAH * p.nb * DD;
-  const bool epi = a.flags & APPLY_EPI;
-  // m^f_{s-1}: compose the aggregates of blocks 0 .. k-1
-  Real m = 0;
-  if (k > 0) {
-    m = a.z[((long)c * p.nb) * DP + row];
-    for (int kk = 1; kk < k; ++kk) {
-      put_vec<Real, DP>(vq, m, lane);
-      m = gdot<Real, DP>(AH + kk * DD + row * DP, vq) + a.z[((long)c * p.nb + kk) * DP + row];
-    }
+  const long tstride = (long)p.nT * DD;
+  const Real* PF = a.tab + (long)TPF * tstride;
+  stage_mats<Real, DP>(buf, a.tab + (long)TW * tstride + s * DD, tstride, NT);
+  Real mp = 0;
+  if (valid) {
+    if (k == 0) mp = p.m0[row];
+    else mp = predict_mean<Real, DP>(p, a.mstart[((long)c * p.nb + k) * DP + row], vq, lane, row);
   }
-  Real mp = (k == 0) ? p.m0[row] : predict_mean<Real, DP>(p, m, vq, lane, row);
   double qacc = 0.0;
   Real ubar = 0;
-  for (int t = s; t <= e; ++t) {
+  // the lane's ytilde_t and (given) eps_t, fetched one step ahead
+  auto fetch = [&](int t, Real& yv, Real& ev) {
+    yv = 0; ev = 0;
+    if (!valid || lane >= p.d) return;
     const long ct = (long)c * p.nT + t;
-    const Real yti = (lane < p.d) ? a.yt[ct * p.d + lane] : (Real)0;
-    put_vec<Real, DP>(vr, act ? yti - mp : (Real)0, lane);
-    const Real wi = gdot<Real, DP>(W + t * DD + row * DP, vr);
-    if (act) qacc += (double)wi * (double)wi;
-    put_vec<Real, DP>(vw, wi, lane);
-    m = yti - p.r * gdot<Real, DP>(WT + t * DD + row * DP, vw);
-    if (a.mf && lane < p.d) a.mf[ct * p.d + lane] = m;
-    if (a.Pf && lane < p.d)
-      for (int j = 0; j < p.d; ++j) a.Pf[(ct * p.d + lane) * p.d + j] = PF[t * DD + lane * DP + j];
-    const Real mpn = (t < p.nT - 1) ? predict_mean<Real, DP>(p, m, vq, lane, row) : (Real)0;
-    if (epi) {
-      Real ei = 0;
-      if (lane < p.d)
-        ei = a.eps ? a.eps[ct * p.d + lane]
-                   : philox_normal<Real>(p.seed, (uint32_t)c, a.iter, PURPOSE_BACKWARD, (uint32_t)t, lane);
-      __syncwarp();
-      if (act) { vr[lane] = mpn; vw[lane] = ei; }
-      __syncwarp();
-      const Real ui = m - gdot<Real, DP>(G + t * DD + row * DP, vr) +
-                      gdot<Real, DP>(LS + t * DD + row * DP, vw);
-      if (act) a.U[ct * DP + lane] = ui;
-      put_vec<Real, DP>(vq, ui, lane);
-      ubar += gdot<Real, DP>(GP + t * DD + row * DP, vq);
+    yv = a.yt[ct * p.d + lane];
+    if (epi && a.eps) ev = a.eps[ct * p.d + lane];
+  };
+  Real yn, en;
+  fetch(s, yn, en);
+  for (int t = s; t <= e; ++t) {
+    const int cur = (t - s) & 1;
+    const Real yti = yn, eg = en;
+    if (t < e) fetch(t + 1, yn, en);
+    if (t < e) stage_mats<Real, DP>(buf + (cur ^ 1) * 5 * MAT, a.tab + (long)TW * tstride + (t + 1) * DD, tstride, NT);
+    else cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    if (valid) {
+      const Real* sW = buf + cur * 5 * MAT;
+      const Real* sWT = sW + MAT;
+      const long ct = (long)c * p.nT + t;
+      put_vec<Real, DP>(vr, act ? yti - mp : (Real)0, lane);
+      const Real wi = dot_row_vec<Real, DP>(sW + row * LD, vr);
+      if (act) qacc += (double)wi * (double)wi;
+      put_vec<Real, DP>(vw, wi, lane);
+      const Real m = yti - p.r * dot_row_vec<Real, DP>(sWT + row * LD, vw);
+      if (a.mf && lane < p.d) a.mf[ct * p.d + lane] = m;
+      if (a.Pf && lane < p.d)
+        for (int j = 0; j < p.d; ++j) a.Pf[(ct * p.d + lane) * p.d + j] = PF[t * DD + lane * DP + j];
+      const Real mpn = (t < p.nT - 1) ? predict_mean<Real, DP>(p, m, vq, lane, row) : (Real)0;
+      if (epi) {
+        const Real* sG = sWT + MAT;
+        const Real* sLS = sG + MAT;
+        const Real* sGP = sLS + MAT;
+        Real ei = 0;
+        if (lane < p.d)
+          ei = a.eps ? eg
+                     : philox_normal<Real>(p.seed, (uint32_t)c, a.iter, PURPOSE_BACKWARD, (uint32_t)t, lane);
+        __syncwarp();
+        if (act) { vr[lane] = mpn; vw[lane] = ei; }
+        __syncwarp();
+        const Real ui = m - dot_row_vec<Real, DP>(sG + row * LD, vr) +
+                        dot_row_vec<Real, DP>(sLS + row * LD, vw);
+        if (act) a.U[ct * DP + lane] = ui;
+        put_vec<Real, DP>(vq, ui, lane);
+        ubar += dot_row_vec<Real, DP>(sGP + row * LD, vq);
+      }
+      mp = mpn;
     }
-    mp = mpn;
+    __syncthreads();
   }
+  if (!valid) return;
   const double q = warp_sum<double>(qacc);
   if (lane == 0) {
     const long ck = (long)c * p.nb + k;
@@ -216,6 +327,63 @@ __global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_apply(KP<Real> p, MeanArgs
     if (a.status && k == 0 && *a.cov_status) atomicOr(&a.status[c], *a.cov_status);
   }
   if (epi && act) a.guv[((long)c * p.nb + k) * DP + lane] = ubar;
+}
+
+// ---------------------------------------------------------------------------
+// Backward sampling inside each block from x*_{e+1} (k_mean_cross, backward):
+// x*_t = G_t x*_{t+1} + U_t (G_{T-1} = 0), with the MH terms when b.mh.
+// ---------------------------------------------------------------------------
+template <typename Real, int DP>
+__global__ void __launch_bounds__(32 * MEAN_WPC)
+    k_mb_apply(KP<Real> p, BackArgs<Real> b, const Real* __restrict__ xnext) {
+  using Z = MeanSizes<Real, DP>;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
+  constexpr long DD = (long)DP * DP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* buf = reinterpret_cast<Real*>(smem_raw);
+  Real* sRy = buf + 2 * MAT;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Real* vx = sRy + MAT + warp * 3 * VEC;
+  Real* vxs = vx + VEC;
+  const int k = blockIdx.x % p.nb, c = (blockIdx.x / p.nb) * MEAN_WPC + warp;
+  const bool valid = c < p.C;
+  const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  if (b.mh && p.emis == AUX_EMIS_LINEAR_GAUSSIAN) load_ryinv<Real, DP>(p, sRy);
+  stage_mats<Real, DP>(buf, b.G + e * DD, DD, 1);
+  Real xi = valid ? xnext[((long)c * p.nb + k) * DP + row] : (Real)0;
+  double acc = 0.0;
+  // the lane's U_t and MH inputs, fetched one step ahead
+  const long cb = (long)(valid ? c : 0) * p.nT;
+  Real un = b.U[(cb + e) * DP + row];
+  MhIn<Real> qn = b.mh ? mh_load<Real>(p, b, cb + e, e, lane) : MhIn<Real>{};
+  for (int t = e; t >= s; --t) {
+    const int cur = (e - t) & 1;
+    const Real uc = un;
+    const MhIn<Real> qc = qn;
+    if (t > s) {
+      un = b.U[(cb + t - 1) * DP + row];
+      if (b.mh) qn = mh_load<Real>(p, b, cb + t - 1, t - 1, lane);
+      stage_mats<Real, DP>(buf + (cur ^ 1) * MAT, b.G + (t - 1) * DD, DD, 1);
+    } else {
+      cp_async_commit();
+    }
+    cp_async_wait<1>();
+    __syncthreads();
+    if (valid) {
+      const long ct = cb + t;
+      put_vec<Real, DP>(vx, xi, lane);
+      xi = dot_row_vec<Real, DP>(buf + cur * MAT + row * LD, vx) + uc;
+      if (lane < p.d) b.xs[ct * p.d + lane] = xi;
+      if (b.mh) acc += mh_step_terms<Real, DP>(p, b, ct, t, xi, qc, sRy, vxs, lane, row);
+    }
+    __syncthreads();
+  }
+  if (valid && b.mh) {
+    acc = warp_sum<double>(acc);
+    if (lane == 0) b.mh_part[(long)c * p.nb + k] = acc;
+  }
 }
 
 }  // namespace auxk

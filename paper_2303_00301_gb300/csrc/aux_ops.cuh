@@ -67,10 +67,31 @@ struct Ops {
     e = cudaFuncSetAttribute(k_cov_scan_level<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::SCAN_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_cov_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::APP_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_cov_products<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::PROD_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_mf_reduce<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::RED);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_mf_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::APP);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_mb_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::BWD);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_mean_cross<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::CROSS);
     return cuda_ok(e);
   }
 
   static int items(const aux_model* m) { return m->C * m->nb; }
+
+  // MH test per chain, then x <- x* for the accepted chains
+  static void mh_commit(aux_model* m, const KP<Real>& p, Real* x, uint64_t iter, uint32_t* acc,
+                        double* log_alpha, cudaStream_t st) {
+    ProfScope ps(m, PK_MH, st);
+    k_mh<Real><<<m->C, 128, 0, st>>>(p, m->mh_part, m->lz_part, iter, acc, log_alpha, m->status,
+                                     m->accept);
+    const long n = (long)m->C * m->T * m->d;
+    const int grid = (int)std::min<long>((n + 255) / 256, 152L * 8);
+    k_commit<Real><<<grid, 256, 0, st>>>(p, x, (const Real*)m->xs, m->accept);
+  }
 
 
   // parallel filter on yt: phase 1, Hillis-Steele rounds, phase 3
@@ -115,18 +136,24 @@ struct Ops {
 
   static void cov_pass(aux_model* m, const KP<Real>& p, cudaStream_t st) {
     ProfScope ps(m, PK_COV, st);
-    Real* b0 = (Real*)m->agg0;
-    Real* b1 = (Real*)m->agg1;
+    KP<Real> pc = p;   // the covariance scan runs on its own partition (block length Lc)
+    pc.L = m->Lc;
+    pc.nb = m->nbc;
+    Real* b0 = (Real*)m->cagg0;
+    Real* b1 = (Real*)m->cagg1;
     cudaMemsetAsync(m->cov_status, 0, sizeof(int32_t), st);
-    k_cov_reduce<Real, DP><<<m->nb, 32, CZ::RED_SMEM, st>>>(p, b0, m->cov_status);
-    for (int off = 1; off < m->nb; off *= 2) {
-      k_cov_scan_level<Real, DP><<<m->nb, 32, CZ::SCAN_SMEM, st>>>(p, b0, b1, off, m->cov_status);
+    k_cov_reduce<Real, DP><<<m->nbc, 32, CZ::RED_SMEM, st>>>(pc, b0, m->cov_status);
+    for (int off = 1; off < m->nbc; off *= 2) {
+      k_cov_scan_level<Real, DP><<<m->nbc, 32, CZ::SCAN_SMEM, st>>>(pc, b0, b1, off, m->cov_status);
       Real* tmp = b0; b0 = b1; b1 = tmp;
     }
     CovArgs<Real> a{};
-    a.prefix = (m->nb > 1) ? b0 : nullptr;
-    a.tab = (Real*)m->tab; a.btab = (Real*)m->btab; a.ld = m->cov_ld; a.status = m->cov_status;
-    k_cov_apply<Real, DP><<<m->nb, 32, CZ::APP_SMEM, st>>>(p, a);
+    a.prefix = (m->nbc > 1) ? b0 : nullptr;
+    a.tab = (Real*)m->tab; a.btab = (Real*)m->btab; a.ld = m->cov_ld; a.ldt = m->cov_ldt;
+    a.status = m->cov_status;
+    k_cov_apply<Real, DP><<<m->nbc, 32, CZ::APP_SMEM, st>>>(pc, a);
+    const int nw = m->L <= 32 ? m->L : 16;
+    k_cov_products<Real, DP><<<m->nb, 32 * nw, CZ::PROD_SMEM, st>>>(p, a);
   }
 
   // the tables for this call: recomputed (shared mode) or reused while valid (cached mode)
@@ -144,13 +171,21 @@ struct Ops {
     return a;
   }
 
+  using MZ = MeanSizes<Real, DP>;
+  static int mean_grid(const aux_model* m) { return m->nb * ((m->C + MEAN_WPC - 1) / MEAN_WPC); }
+
+  // block-local pass, composition over the blocks, in-block pass from the true starts
   static void means_filter(aux_model* m, const KP<Real>& p, MeanArgs<Real> a, cudaStream_t st) {
-    const int grid = (items(m) + MEAN_WPC - 1) / MEAN_WPC;
+    const int grid = mean_grid(m);
     { ProfScope ps(m, PK_REDUCE, st);
-      k_mf_reduce<Real, DP><<<grid, 32 * MEAN_WPC, 0, st>>>(p, a); }
+      k_mf_reduce<Real, DP><<<grid, 32 * MEAN_WPC, MZ::RED, st>>>(p, a); }
     a.x = nullptr;
+    { ProfScope ps(m, PK_SCAN, st);
+      k_mean_cross<Real, DP><<<(m->C + MEAN_WPC - 1) / MEAN_WPC, 32 * MEAN_WPC, MZ::CROSS, st>>>(
+          p, (const Real*)m->btab + (long)BAH * m->nb * DD, a.z, (Real*)m->ms, 0); }
+    a.mstart = (const Real*)m->ms;
     { ProfScope ps(m, PK_APPLY, st);
-      k_mf_apply<Real, DP><<<grid, 32 * MEAN_WPC, 0, st>>>(p, a); }
+      k_mf_apply<Real, DP><<<grid, 32 * MEAN_WPC, MZ::APP, st>>>(p, a); }
   }
 
   static BackArgs<Real> back_args_tab(aux_model* m) {
@@ -161,6 +196,15 @@ struct Ops {
     b.guv = (const Real*)m->guv;
     b.g_cs = 0; b.gm_cs = 0;
     return b;
+  }
+
+  // (G, U) suffix scan on the tables: composition over the blocks, then in-block
+  static void backward_tab(aux_model* m, const KP<Real>& p, BackArgs<Real> b, cudaStream_t st) {
+    ProfScope ps(m, PK_BACKWARD, st);
+    Real* xnext = (Real*)m->zb;
+    k_mean_cross<Real, DP><<<(m->C + MEAN_WPC - 1) / MEAN_WPC, 32 * MEAN_WPC, MZ::CROSS, st>>>(
+        p, b.gum, b.guv, xnext, 1);
+    k_mb_apply<Real, DP><<<mean_grid(m), 32 * MEAN_WPC, MZ::BWD, st>>>(p, b, xnext);
   }
 
   static int kalman_step_means(aux_model* m, void* xv, int n_iters, uint64_t iter0, uint32_t* acc,
@@ -177,13 +221,11 @@ struct Ops {
       BackArgs<Real> b = back_args_tab(m);
       b.xs = (Real*)m->xs; b.mh = 1; b.x = x; b.u = (const Real*)m->u; b.v = (const Real*)m->v;
       b.yts = (Real*)m->yts; b.mh_part = m->mh_part;
-      backward(m, p, b, st);
+      backward_tab(m, p, b, st);
       MeanArgs<Real> r = mean_args(m);
       r.yt = (Real*)m->yts; r.flags = APPLY_REV_DIFF;
       means_filter(m, p, r, st);
-      { ProfScope ps(m, PK_MH, st);
-        k_mh<Real><<<m->C, 128, 0, st>>>(p, x, (const Real*)m->xs, m->mh_part, m->lz_part, iter, acc,
-                                         log_alpha, m->status); }
+      mh_commit(m, p, x, iter, acc, log_alpha, st);
     }
     return cuda_ok(cudaGetLastError());
   }
@@ -207,9 +249,7 @@ struct Ops {
       b.yts = (Real*)m->yts; b.mh_part = m->mh_part;
       backward(m, p, b, st);
       filter(m, p, (const Real*)m->yts, apply_args(m, APPLY_REV_DIFF, iter), st);
-      { ProfScope ps(m, PK_MH, st);
-      k_mh<Real><<<m->C, 128, 0, st>>>(p, x, (const Real*)m->xs, m->mh_part, m->lz_part, iter, acc,
-                                       log_alpha, m->status); }
+      mh_commit(m, p, x, iter, acc, log_alpha, st);
     }
     return cuda_ok(cudaGetLastError());
   }
@@ -244,7 +284,7 @@ struct Ops {
       means_filter(m, p, a, st);
       BackArgs<Real> b = back_args_tab(m);
       b.xs = (Real*)xs; b.mh = 0;
-      backward(m, p, b, st);
+      backward_tab(m, p, b, st);
       if (logZ) { ProfScope ps(m, PK_SUM, st); k_sum_parts<<<m->C, 128, 0, st>>>(m->lz_part, m->nb, logZ); }
       return cuda_ok(cudaGetLastError());
     }
