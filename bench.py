@@ -2,11 +2,17 @@
 """Throughput of the auxiliary Kalman sampler on GB300: chain·timesteps/s.
 
 Workload (default): multivariate stochastic-volatility model, d_x = 30,
-T = 1024, 32 chains, FP32, delta = 0.0183 (oracle-calibrated, ~47%
+T = 1024, 32 chains, FP32, delta = 0.0183 (oracle-calibrated, ~50%
 acceptance), seeded synthetic data. One step = one auxiliary Kalman MH
 iteration (linearise, parallel filter, backward sampling scan, reverse filter,
 MH test) on all chains. The sampler state and data are resident in HBM when
 the timed region starts; L2 is flushed (256 MiB write) before every timed step.
+
+The headline mode (--mode, default "shared") recomputes the covariance half of
+the scan once per step for all chains, then runs the per-chain means; the JSON
+line also reports the "per_chain" mode (every chain runs the full element
+scan: the general path) and the "cached" mode (covariance tables kept across
+steps), each with its own roofline line, and ESS / ESJD from a long run.
 
 --impl reference times the FP64 CPU oracle (the only other implementation of
 the method here) on the host cores on bounded samples of the same workload.
@@ -47,6 +53,9 @@ def parse():
                     help="execution mode of the headline number (aux_set_mode)")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the measurements of the other execution modes")
+    ap.add_argument("--ess-iters", type=int, default=5000,
+                    help="post-burn-in iterations of the ESS / ESJD run (0 = skip)")
+    ap.add_argument("--ess-burn", type=int, default=500)
     ap.add_argument("--cpu-sample-chains", type=int, default=0,
                     help="chain-steps in the CPU baseline sample (0 = 2 per core)")
     return ap.parse_args()
@@ -93,10 +102,10 @@ def apply_flops_per_step(d, epilogue, fdiag):
 
 
 def cov_apply_flops_per_step(d, fdiag):
-    """Covariance pass, in-block step: the apply step with the epilogue, plus the
-    inverse Cholesky factor W_t = chol(S_t)^{-1} and the running product
-    r W^T W F AH (two triangular x dense products)."""
-    return apply_flops_per_step(d, True, fdiag) + (1.0 / 3.0 + 2.0) * d ** 3
+    """Covariance pass, in-block step: the apply step with the epilogue, the
+    inverse Cholesky factor W_t = chol(S_t)^{-1}, M_t = r W^T W F (triangular
+    product) and the running products M_t AH and G prefix (two dense products)."""
+    return apply_flops_per_step(d, True, fdiag) + (1.0 / 3.0 + 1.0 + 4.0) * d ** 3
 
 
 def means_flops_per_step(kind, d, fdiag, epilogue=True):
@@ -109,37 +118,111 @@ def means_flops_per_step(kind, d, fdiag, epilogue=True):
     return 2.0 * d ** 2 + fm + ((2.0 + 1.0 + 2.0) * d ** 2 if epilogue else 0.0)
 
 
-def kernel_flops(mode, kind, d, T, C, nb, launches, fdiag):
-    """Algorithmic flops of all launches of one kernel kind in the timed region
-    (each MH step runs the filter twice: forward with the epilogue, reverse without)."""
+def scan_rounds(nb):
+    """(number of Hillis-Steele rounds, combines over all rounds) for nb blocks."""
+    offs = [2 ** j for j in range(max(0, math.ceil(math.log2(nb))))] if nb > 1 else []
+    return len(offs), sum(nb - o for o in offs)
+
+
+def kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz):
+    """Algorithmic work of one launch of a kernel kind, averaged over the launches
+    of one MH step: (flops, HBM bytes). Bytes count what the algorithm must move
+    (unpadded d): tables once, per-chain vectors once; None where not modelled."""
+    vec = C * T * d * esz
+    tab = T * d * d * esz
     if mode == "per_chain":
         if kind == "reduce":
-            return launches * C * T * reduce_flops_per_step(d, fdiag)
+            return C * T * reduce_flops_per_step(d, fdiag), None
         if kind == "apply":
-            return launches / 2 * C * T * (apply_flops_per_step(d, True, fdiag) +
-                                           apply_flops_per_step(d, False, fdiag))
-        return None
-    if kind == "reduce":
-        return launches * C * T * means_flops_per_step("reduce", d, fdiag)
-    if kind == "apply":
-        return launches / 2 * C * T * (means_flops_per_step("apply", d, fdiag, True) +
-                                       means_flops_per_step("apply", d, fdiag, False))
-    if kind == "cov":
-        # one covariance pass per launch group: T reduce steps, the scan rounds, T apply steps
-        L = math.ceil(T / nb)
-        scan = sum(max(0, nb - off) for off in (2 ** j for j in range(max(0, math.ceil(math.log2(nb))))))
-        per_pass = T * reduce_flops_per_step(d, fdiag) + scan * combine_flops(d) + \
-            T * cov_apply_flops_per_step(d, fdiag)
-        return launches * per_pass
-    return None
+            return C * T * (apply_flops_per_step(d, True, fdiag) +
+                            apply_flops_per_step(d, False, fdiag)) / 2, None
+        return None, None
+    if kind == "reduce":   # forward (linearise: x, y in; u, v, ytilde out) and reverse (ytilde* in)
+        return (C * T * means_flops_per_step("reduce", d, fdiag),
+                2 * tab + (5 * vec + vec) / 2)
+    if kind == "apply":    # forward (5 tables, ytilde in, U out) and reverse (2 tables, ytilde* in)
+        return (C * T * (means_flops_per_step("apply", d, fdiag, True) +
+                         means_flops_per_step("apply", d, fdiag, False)) / 2,
+                (5 * tab + 2 * vec + 2 * tab + vec) / 2)
+    if kind == "backward":  # G table, U in, x* out, MH inputs x, u, v, y in, ytilde* out
+        return C * T * 2.0 * d ** 2, tab + 7 * vec
+    if kind == "cov_reduce":
+        return T * reduce_flops_per_step(d, fdiag), None
+    if kind == "cov_scan":
+        rounds, combines = scan_rounds(nbc)
+        return (combines * combine_flops(d) / max(1, rounds)), None
+    if kind == "cov_apply":
+        return T * cov_apply_flops_per_step(d, fdiag), None
+    if kind == "cov_products":
+        # composition of the covariance-block products (2 per covariance block) and the
+        # prefix fix-up of G_s..G_{t-1} (one product per step)
+        return (2 * nbc + T) * 2.0 * d ** 3 / 2, None
+    return None, None
 
 
 KERNEL_NAMES = {
     "per_chain": {"reduce": "k_filter_reduce", "apply": "k_filter_apply", "scan": "k_filter_scan_level",
-                  "backward": "k_sample_backward", "mh": "k_mh", "linearise": "k_linearise"},
-    "table": {"reduce": "k_mf_reduce", "apply": "k_mf_apply", "cov": "k_cov_reduce/scan_level/apply",
-              "backward": "k_sample_backward", "mh": "k_mh"},
+                  "backward": "k_sample_backward", "mh": "k_mh + k_commit", "linearise": "k_linearise"},
+    "table": {"reduce": "k_mf_reduce", "apply": "k_mf_apply", "scan": "k_mean_cross",
+              "backward": "k_mean_cross + k_mb_apply", "mh": "k_mh + k_commit",
+              "cov_reduce": "k_cov_reduce", "cov_scan": "k_cov_scan_level",
+              "cov_apply": "k_cov_apply", "cov_products": "k_cov_products"},
 }
+
+
+def roofline_line(mode, kind, prof, w, d, T, C, nb, nbc, fdiag, esz, peaks, steps, path):
+    """One roofline line for kernel kind `kind` from the per-launch event times."""
+    if kind not in prof or not prof[kind][1]:
+        return None
+    ms, launches = prof[kind]
+    avg_ms = ms / launches
+    flops, bytes_ = kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    name = KERNEL_NAMES["per_chain" if mode == "per_chain" else "table"].get(kind, kind)
+    line = {"path": path, "kernel": name, "launches": launches, "avg_launch_ms": avg_ms}
+    if bytes_ is not None and "hbm_gbs" in peaks:
+        achieved = bytes_ / (avg_ms / 1e3) / 1e9
+        line.update({"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "bytes_per_launch": bytes_, "peak_basis": "measured HBM copy bandwidth"})
+        if flops is not None:
+            line["flops_per_launch"] = flops
+        return line
+    if flops is None:
+        return None
+    if w["dtype"] == "f32":
+        peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        basis = f"{N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz"
+    else:
+        peak = 1.25
+        basis = "nominal GB300 FP64 rate"
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    line.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                 "frac": achieved / peak, "traffic": None, "flops_per_launch": flops,
+                 "diagonal_F": fdiag, "peak_basis": basis})
+    return line
+
+
+# --------------------------------------------------------------------------- ESS
+def geyer_ess(x):
+    """Effective sample size of a 1-D series by Geyer's initial monotone sequence
+    estimator (sums of consecutive autocorrelation pairs, truncated at the first
+    non-positive pair and made monotone)."""
+    import numpy as np
+    x = np.asarray(x, dtype=np.float64)
+    n = x.size
+    xc = x - x.mean()
+    var = xc.var()
+    if n < 4 or var <= 0:
+        return float(n)
+    f = np.fft.rfft(xc, 2 * n)
+    acf = np.fft.irfft(f * np.conj(f))[:n] / (n * var)
+    pairs = acf[: (n // 2) * 2].reshape(-1, 2).sum(axis=1)
+    pos = np.where(pairs <= 0)[0]
+    m = pos[0] if pos.size else pairs.size
+    gam = np.minimum.accumulate(pairs[:m]) if m > 0 else np.zeros(0)
+    tau = -1.0 + 2.0 * gam.sum()
+    return float(n / max(tau, 1e-12))
 
 
 # --------------------------------------------------------------------------- clocks
@@ -346,13 +429,14 @@ def run_ours(args):
     value = head["value"]
     total_ms = head["ms_per_step"] * args.steps
     accept_rate = head["accept_rate"]
-    others = {}
+    others, profs = {}, {args.mode: prof}
     if not args.headline_only:
         for mode in ("per_chain", "shared", "cached"):
             if mode != args.mode:
-                so, _, _, _, _, _, r = run_mode(mode, False)
+                so, _, _, _, po, _, r = run_mode(mode, False)
                 so.close()
                 others[mode] = r
+                profs[mode] = po
 
     # end to end through the public API from pinned host buffers
     x_host = torch.tensor(wl.x_init, dtype=tdt).pin_memory()
@@ -380,30 +464,69 @@ def run_ours(args):
     e2e_value = world * C * T * args.steps / e2e_s.item()
     rc, per_chain = s.status()
 
-    # roofline of the dominant kernel (time-weighted), FP32 FMA pipe bound
-    dom = max((k for k in prof if prof[k][1]), key=lambda k: prof[k][0])
-    dom_ms, dom_launches = prof[dom]
+    # roofline lines: the dominant kernel of the headline mode, and one line per
+    # path (general per-chain filter, means-only table path, covariance pass)
     fdiag = bool(np.all(wl.F == np.diag(np.diag(wl.F))))
-    flops = kernel_flops(args.mode, dom, d, T, C, nb, dom_launches, fdiag)
     peaks = {}
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pp):
         peaks = json.load(open(pp))
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    if w["dtype"] == "f32":
-        peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    else:
-        peak_tflops = 1.25   # nominal GB300 FP64 rate
-    names = KERNEL_NAMES["per_chain" if args.mode == "per_chain" else "table"]
-    roofline = None
-    if flops is not None and dom_ms > 0:
-        achieved = flops / (dom_ms / 1e3) / 1e12
-        roofline = {"bound": "alu", "kernel": names.get(dom, dom), "achieved": achieved,
-                    "flops_per_launch": flops / dom_launches, "diagonal_F": fdiag,
-                    "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                    "traffic": None, "launches": dom_launches,
-                    "avg_launch_ms": dom_ms / dom_launches,
-                    "peak_basis": f"{N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz"}
+    Lc = max(c for c in range(1, min(4, L) + 1) if L % c == 0)   # the library's covariance block
+    nbc = (T + Lc - 1) // Lc
+    dom = max((k for k in prof if prof[k][1]), key=lambda k: prof[k][0])
+    rl = lambda mode, kind, path: roofline_line(mode, kind, profs[mode], w, d, T, C, nb, nbc, fdiag,
+                                                esz, peaks, args.steps, path)
+    roofline = rl(args.mode, dom, f"dominant kernel of the {args.mode} mode")
+    lines = {}
+    if "per_chain" in profs:
+        lines["general_path"] = rl("per_chain", "apply", "per-chain element scan (general path)")
+    tmode = args.mode if args.mode != "per_chain" else ("cached" if "cached" in profs else None)
+    if tmode:
+        lines["means_path"] = rl(tmode, "apply", "means-only batched path (tables shared by all chains)")
+        cov_kinds = [k for k in ("cov_reduce", "cov_scan", "cov_apply", "cov_products")
+                     if k in profs.get("shared", {}) and profs["shared"][k][1]]
+        if cov_kinds:
+            ck_dom = max(cov_kinds, key=lambda k: profs["shared"][k][0])
+            lines["covariance_pass"] = rl("shared", ck_dom, "covariance (Riccati) pass, once per call")
+
+    # ESS and ESJD of the headline mode from a long run (outside the timed region)
+    ess = None
+    if args.ess_iters > 0 and rank == 0:
+        se = AuxKalman(wl, dtype=w["dtype"], block_len=args.block_len, mode=args.mode)
+        xe = torch.tensor(wl.x_init, dtype=tdt, device="cuda")
+        t_idx = torch.linspace(0, T - 1, 8).round().long().cuda()
+        i_idx = torch.linspace(0, d - 1, min(d, 5)).round().long().cuda()
+        tt, ii = torch.meshgrid(t_idx, i_idx, indexing="ij")
+        tt, ii = tt.reshape(-1), ii.reshape(-1)
+        trace = torch.empty((args.ess_iters, C, tt.numel()), dtype=torch.float64, device="cuda")
+        jump = torch.zeros((C, T), dtype=torch.float64, device="cuda")
+        ite = 10 ** 6
+        for _ in range(args.ess_burn):
+            se.step(xe, 1, iter0=ite)
+            ite += 1
+        xprev = xe.clone()
+        for n_ in range(args.ess_iters):
+            se.step(xe, 1, iter0=ite)
+            ite += 1
+            trace[n_] = xe[:, tt, ii].double()
+            jump += ((xe - xprev).double() ** 2).sum(-1)
+            xprev.copy_(xe)
+        torch.cuda.synchronize()
+        tr = trace.cpu().numpy()
+        se.close()
+        sec_per_iter = head["ms_per_step"] / 1e3
+        ess_pair = np.array([sum(geyer_ess(tr[:, c, j]) for c in range(C)) for j in range(tr.shape[2])])
+        esjd_t = (jump / args.ess_iters).mean(0).cpu().numpy()     # per chain, per t
+        ess = {"iterations": args.ess_iters, "burn_in": args.ess_burn, "chains": C,
+               "estimator": "Geyer initial monotone sequence, summed over chains",
+               "coordinates": f"x_t(i) for t in {t_idx.tolist()}, i in {i_idx.tolist()}",
+               "ess_min": float(ess_pair.min()), "ess_median": float(np.median(ess_pair)),
+               "ess_per_s_min": float(ess_pair.min() / (args.ess_iters * sec_per_iter)),
+               "ess_per_s_median": float(np.median(ess_pair) / (args.ess_iters * sec_per_iter)),
+               "esjd_per_s_min": float(esjd_t.min() / sec_per_iter),
+               "esjd_per_s_median": float(np.median(esjd_t) / sec_per_iter),
+               "seconds_per_iteration": sec_per_iter}
+
     cpu = None
     if pool is not None:
         n = args.cpu_sample_chains or 2 * (os.cpu_count() or 1)
@@ -423,7 +546,8 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                         "d2h_bytes_per_step": bo},
                 "gpu_launches": head["gpu_launches"],
-                "roofline": roofline, "cpu_baseline": cpu, "clocks": ck,
+                "roofline": roofline, "roofline_lines": lines, "ess": ess,
+                "cpu_baseline": cpu, "clocks": ck,
                 "kernel_ms_per_step": head["kernel_ms_per_step"],
                 "ms_per_step_without_events": head["ms_per_step_without_events"],
                 "accept_rate": accept_rate, "status": int(rc),

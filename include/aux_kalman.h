@@ -198,8 +198,11 @@ int aux_get_status(aux_model *m, int32_t *per_chain_status);
 #define AUX_PROFILE_SUM       7  /* log Z reduction */
 #define AUX_PROFILE_SMOOTH    8  /* smoother aggregates and sweep with score statistics (gradient) */
 #define AUX_PROFILE_GRAD      9  /* FP64 gradient assembly per chain */
-#define AUX_PROFILE_COV       10 /* covariance pass of the table modes (aux_set_mode) */
-#define AUX_PROFILE_KINDS     11
+#define AUX_PROFILE_COV_REDUCE   10 /* covariance pass (table modes): block aggregates */
+#define AUX_PROFILE_COV_SCAN     11 /* covariance pass: one Hillis-Steele round */
+#define AUX_PROFILE_COV_APPLY    12 /* covariance pass: in-block filter and per-step tables */
+#define AUX_PROFILE_COV_PRODUCTS 13 /* covariance pass: block products of the means partition */
+#define AUX_PROFILE_KINDS        14
 
 /* Turn per-launch timing on or off for this handle: while on, every kernel
  * launch is bracketed by two CUDA events recorded on its own stream. */

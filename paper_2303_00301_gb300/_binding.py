@@ -221,7 +221,7 @@ def aux_get_status(handle, n_chains=None):
 
 
 PROFILE_KINDS = ["linearise", "template", "reduce", "scan", "apply", "backward", "mh", "sum",
-                 "smooth", "grad", "cov"]
+                 "smooth", "grad", "cov_reduce", "cov_scan", "cov_apply", "cov_products"]
 
 
 def aux_set_profiling(handle, enable):

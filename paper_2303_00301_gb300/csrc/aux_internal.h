@@ -54,7 +54,7 @@ struct aux_model {
 
 // kernel kinds reported by aux_read_profile (order of AUX_PROFILE_* in the header)
 enum { PK_LINEARISE = 0, PK_TEMPLATE, PK_REDUCE, PK_SCAN, PK_APPLY, PK_BACKWARD, PK_MH, PK_SUM,
-       PK_SMOOTH, PK_GRAD, PK_COV, PK_COUNT };
+       PK_SMOOTH, PK_GRAD, PK_COV_REDUCE, PK_COV_SCAN, PK_COV_APPLY, PK_COV_PRODUCTS, PK_COUNT };
 
 // bracket a launch with events on its stream when profiling is on
 struct ProfScope {
