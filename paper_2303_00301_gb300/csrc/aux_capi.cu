@@ -334,8 +334,10 @@ int aux_sample_path(aux_model* m, const void* ytilde, const void* eps, uint64_t 
   return m->ops->sample_path(m, ytilde, eps, iteration, xstar, logZ, m->stream);
 }
 
-// block length of the covariance scan of the table modes: short blocks put
-// most of its critical path into the O(log T) Hillis-Steele rounds
+// longest block of the covariance scan of the table modes: short blocks put
+// most of its critical path into the O(log T) Hillis-Steele rounds; the
+// block length divides the means block length so that each means block is a
+// whole number of covariance blocks
 constexpr int kCovBlockLen = 4;
 
 int aux_set_mode(aux_model* m, int32_t mode) {
@@ -343,7 +345,9 @@ int aux_set_mode(aux_model* m, int32_t mode) {
     return AUX_E_INVALID_ARG;
   if (mode != AUX_MODE_PER_CHAIN && !m->tab) {
     const size_t es = m->esz, DD = (size_t)m->DP * m->DP;
-    m->Lc = std::min(kCovBlockLen, m->T);
+    m->Lc = 1;   // the largest divisor of the means block length that is <= kCovBlockLen
+    for (int c = std::min(kCovBlockLen, m->L); c >= 1; --c)
+      if (m->L % c == 0) { m->Lc = c; break; }
     m->nbc = (m->T + m->Lc - 1) / m->Lc;
     int rc = dev_alloc(m, &m->tab, (size_t)6 * m->T * DD * es);
     if (!rc) rc = dev_alloc(m, &m->cagg0, (size_t)m->nbc * 3 * DD * es);

@@ -15,7 +15,9 @@
 //   tab[TLS][t] = chol(Sigma_t), Sigma_t = P^f_t - G_t P^p_{t+1} G_t^T
 //                 (chol(P^f_{T-1}) at t = T-1)
 //   tab[TPF][t] = P^f_t,   ldt[t] = log det S_t (FP64);
-// then k_cov_products forms, for the blocks s..e of the per-chain means pass,
+// and, for the blocks s..e of the per-chain means pass (each a whole number of
+// covariance blocks: local products in k_cov_apply, composed by k_cov_products
+// and k_cov_gp_fix),
 //   tab[TGP][t]  = G_s G_{s+1} ... G_{t-1}  (identity at t = s)
 //   btab[BAH][k] = (I - K_e) F ... (I - K_s) F,  K_t = P^p_t S_t^{-1}
 //                  (the linear part of m^f_e as a function of m^f_{s-1})
@@ -39,6 +41,9 @@ template <typename Real> struct CovArgs {
   double* ld;           // [nb] (means partition)
   double* ldt;          // [T]
   int32_t* status;      // [1]: ST_NOT_PD when a factorisation failed
+  Real* cblk;           // [3][nbc][DP][DP]: per covariance block G_s..G_e, M_e..M_s, and the
+                        // product of the earlier covariance blocks of its means block
+  int R;                // covariance blocks per means block (means L / Lc)
 };
 
 template <typename Real, int DP> struct CovSizes {
@@ -46,9 +51,10 @@ template <typename Real, int DP> struct CovSizes {
   static constexpr size_t MODEL = (3 * MAT + 2 * VEC) * sizeof(Real);
   static constexpr size_t RED_SMEM = MODEL + (6 * MAT + 3 * VEC) * sizeof(Real);
   static constexpr size_t SCAN_SMEM = (9 * MAT + VEC) * sizeof(Real);
-  static constexpr size_t APP_SMEM = MODEL + (7 * MAT + 3 * VEC) * sizeof(Real);
-  // k_cov_products: the model and up to 32 exchange slots
-  static constexpr size_t PROD_SMEM = MODEL + 32 * MAT * sizeof(Real);
+  static constexpr size_t APP_SMEM = MODEL + (10 * MAT + 3 * VEC) * sizeof(Real);
+  static constexpr int FIX_WPC = 8;
+  static constexpr size_t PROD_SMEM = (2 * MAT) * sizeof(Real);
+  static constexpr size_t FIX_SMEM = FIX_WPC * 2 * MAT * sizeof(Real);
 };
 
 // ---------------------------------------------------------------------------
@@ -282,7 +288,10 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
   Real* SY = SLR + MAT;        // L_S^{-1} P^p, scratch
   Real* SG = SY + MAT;         // chol(S) (LS form)
   Real* SWm = SG + MAT;        // W_t
-  Real* vdA = SWm + MAT;
+  Real* SGh = SWm + MAT;       // G_s ... G_{t-1} of this covariance block
+  Real* SAH = SGh + MAT;       // M_t ... M_s of this covariance block
+  Real* SA1 = SAH + MAT;       // scratch
+  Real* vdA = SA1 + MAT;
   Real* vdB = vdA + VEC;
   __syncwarp();
   const int lane = threadIdx.x & 31, k = blockIdx.x;
@@ -291,6 +300,13 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
   const int row = act ? lane : 0;
   int bad = 0;
   Real pprow[DP];
+  {
+    Real gi[DP];
+#pragma unroll
+    for (int j = 0; j < DP; ++j) gi[j] = (j == lane) ? (Real)1 : (Real)0;
+    st_row<Real, DP>(SGh, row, gi, act);
+    st_row<Real, DP>(SAH, row, gi, act);
+  }
   auto store_row = [&](int tb, int t, const Real* S) {
     if (!act) return;
     Real r[DP];
@@ -385,6 +401,36 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
     double lg = (lane < p.d) ? -log((double)vdB[lane]) : 0.0;
     lg = warp_sum<double>(lg);
     if (lane == 0) a.ldt[t] = 2.0 * lg;
+    // M_t = (I - K_t) F = r W^T W F, then SAH <- M_t SAH
+    Real mr[DP];
+    mm_col<Real, DP>(SWm, row, SWm, mr);
+    if (p.fdiag) {
+      Real ph[DP];
+      ld_vec<Real, DP>(sphi, ph);
+#pragma unroll
+      for (int j = 0; j < DP; ++j) mr[j] *= p.r * ph[j];
+    } else {
+      st_row<Real, DP>(SA1, row, mr, act);
+      __syncwarp();
+      mm_row<Real, DP>(SA1 + row * LD, sF, mr);
+#pragma unroll
+      for (int j = 0; j < DP; ++j) mr[j] *= p.r;
+      __syncwarp();
+    }
+    st_row<Real, DP>(SA1, row, mr, act);
+    __syncwarp();
+    Real ah[DP];
+    mm_row<Real, DP>(SA1 + row * LD, SAH, ah);
+    __syncwarp();
+    st_row<Real, DP>(SAH, row, ah, act);
+    __syncwarp();
+  };
+  auto ghat = [&]() {      // SGh <- SGh G_t (G_t in SX)
+    Real gn[DP];
+    mm_row<Real, DP>(SGh + row * LD, SX, gn);
+    __syncwarp();
+    st_row<Real, DP>(SGh, row, gn, act);
+    __syncwarp();
   };
   // Y = L_S^{-1} P^p (columns of SY), P^f -> SP
   auto update = [&](int t) {
@@ -423,12 +469,15 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
     predict();
   }
   factor_S();
+  store_row(TGP, s, SGh);
   gain_tables(s);
   update(s);
   for (int t = s + 1; t <= e; ++t) {
     predict();
     factor_2();
     epilogue(t - 1);
+    ghat();
+    store_row(TGP, t, SGh);
     gain_tables(t);
     update(t);
   }
@@ -449,43 +498,38 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
     store_row(TG, e, SX);
     store_row(TLS, e, SLR);
   }
+  ghat();
+  if (act) {
+    Real r[DP];
+    ld_row<Real, DP>(SGh, row, r);
+    st_vec<Real, DP>(a.cblk + (long)k * DD + row * DP, r);
+    ld_row<Real, DP>(SAH, row, r);
+    st_vec<Real, DP>(a.cblk + ((long)p.nb + k) * DD + row * DP, r);
+  }
   if (bad && lane == 0) atomicOr(a.status, ST_NOT_PD);
 }
 
 // ---------------------------------------------------------------------------
-// Block products of the means partition (p.L, p.nb): block k = steps s..e.
-// Warp w takes the consecutive steps of chunk w (chunk = ceil(n / warps)) and
-// forms P_w = G_t0 ... G_t1 and Q_w = M_t1 ... M_t0, M_t = (I - K_t) F =
-// r W_t^T W_t F; Hillis-Steele rounds over the warps (one shared slot each)
-// give the inclusive products, from which each warp writes G_s ... G_{t-1}
-// for its steps; the last warp holds GH_k and AH_k. One slot per warp when
-// every chunk is a single step, two otherwise (at most 16 warps then).
+// Block products of the means partition (p.L, p.nb; kc = covariance blocks,
+// a.R per means block), one warp per means block k: over its covariance
+// blocks j in order, the exclusive products E_j = GHc_0 ... GHc_{j-1} (to
+// cblk[2]), GH_k = GHc_0 ... GHc_{R-1}, AH_k = AHc_{R-1} ... AHc_0, and
+// ld[k] = sum of log det S_t over the block.
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
-__global__ void __launch_bounds__(1024) k_cov_products(KP<Real> p, CovArgs<Real> a) {
-  using Z = CovSizes<Real, DP>;
-  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
+__global__ void __launch_bounds__(32) k_cov_products(KP<Real> p, CovArgs<Real> a, int nbc) {
+  constexpr int MAT = CovSizes<Real, DP>::MAT, LD = Lay<Real, DP>::LD;
   constexpr long DD = (long)DP * DP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* sm = reinterpret_cast<Real*>(smem_raw);
-  Real* sF = sm;
-  Real* sFT = sF + MAT;
-  Real* sQ = sFT + MAT;
-  Real* sb = sQ + MAT;
-  load_model_slots<Real, DP>(p, sF, sFT, sQ, sb);
-  const Real* sphi = sb + VEC;
-  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k = blockIdx.x;
-  const int s = k * p.L, e = min(p.nT, s + p.L) - 1, n = e - s + 1;
-  const int chunk = (n + nw - 1) / nw;
-  const int spw = chunk > 1 ? 2 : 1;
-  Real* slot0 = sb + 2 * VEC;
-  Real* SX = slot0 + warp * spw * MAT;     // exchange slot
-  Real* SY = SX + (spw - 1) * MAT;         // staging slot (= SX when spw == 1)
-  const int t0 = s + warp * chunk, t1 = min(e, t0 + chunk - 1);
+  Real* SX = reinterpret_cast<Real*>(smem_raw);
+  Real* SY = SX + MAT;
+  const int lane = threadIdx.x & 31, k = blockIdx.x;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
-  __syncthreads();
+  const int j0 = k * a.R, j1 = min(nbc, j0 + a.R) - 1;
+  Real P[DP], Q[DP];
+#pragma unroll
+  for (int j = 0; j < DP; ++j) P[j] = Q[j] = (j == lane) ? (Real)1 : (Real)0;
   auto load_slot = [&](Real* S, const Real* g) {
     __syncwarp();
     Real r[DP];
@@ -493,94 +537,60 @@ __global__ void __launch_bounds__(1024) k_cov_products(KP<Real> p, CovArgs<Real>
     st_row<Real, DP>(S, row, r, act);
     __syncwarp();
   };
-  Real P[DP], Q[DP];
-#pragma unroll
-  for (int j = 0; j < DP; ++j) P[j] = Q[j] = (j == lane) ? (Real)1 : (Real)0;
-  for (int t = t0; t <= t1; ++t) {
-    // M_t row: r (W^T W F)[row]
-    load_slot(SY, a.tab + ((long)TW * p.nT + t) * DD);
-    Real mr[DP];
-    mm_col<Real, DP>(SY, row, SY, mr);
-    if (p.fdiag) {
-      Real ph[DP];
-      ld_vec<Real, DP>(sphi, ph);
-#pragma unroll
-      for (int j = 0; j < DP; ++j) mr[j] *= p.r * ph[j];
-    } else {
-      __syncwarp();
-      st_row<Real, DP>(SY, row, mr, act);
-      __syncwarp();
-      mm_row<Real, DP>(SY + row * LD, sF, mr);
-#pragma unroll
-      for (int j = 0; j < DP; ++j) mr[j] *= p.r;
-    }
-    if (t == t0) {
-#pragma unroll
-      for (int j = 0; j < DP; ++j) Q[j] = mr[j];
-    } else {   // Q <- M_t Q
-      __syncwarp();
-      st_row<Real, DP>(SY, row, mr, act);
-      st_row<Real, DP>(SX, row, Q, act);
-      __syncwarp();
-      mm_row<Real, DP>(SY + row * LD, SX, Q);
-      __syncwarp();
-      st_row<Real, DP>(SX, row, P, act);
-    }
-    load_slot(SY, a.tab + ((long)TG * p.nT + t) * DD);
-    if (t == t0) ld_row<Real, DP>(SY, row, P);
-    else mm_row<Real, DP>(SX + row * LD, SY, P);   // P <- P G_t
-  }
-  // inclusive products over the warps: P_w <- P_{w-off} P_w, Q_w <- Q_w Q_{w-off}
-  for (int off = 1; off < nw; off *= 2) {
-    Real* partner = slot0 + max(0, warp - off) * spw * MAT;
+  for (int j = j0; j <= j1; ++j) {
+    if (act) st_vec<Real, DP>(a.cblk + (2L * nbc + j) * DD + row * DP, P);
+    // P <- P GHc_j
+    __syncwarp();
     st_row<Real, DP>(SX, row, P, act);
-    __syncthreads();
-    Real nxt[DP];
-    if (warp >= off) mm_row<Real, DP>(partner + row * LD, SX, nxt);
-    __syncthreads();
-    if (warp >= off) {
-#pragma unroll
-      for (int j = 0; j < DP; ++j) P[j] = nxt[j];
-    }
+    load_slot(SY, a.cblk + (long)j * DD);
+    mm_row<Real, DP>(SX + row * LD, SY, P);
+    // Q <- AHc_j Q
+    __syncwarp();
     st_row<Real, DP>(SX, row, Q, act);
-    __syncthreads();
-    if (warp >= off) mm_row<Real, DP>(SX + row * LD, partner, nxt);
-    __syncthreads();
-    if (warp >= off) {
-#pragma unroll
-      for (int j = 0; j < DP; ++j) Q[j] = nxt[j];
-    }
+    load_slot(SY, a.cblk + ((long)nbc + j) * DD);
+    mm_row<Real, DP>(SY + row * LD, SX, Q);
   }
-  // G_s ... G_{t-1} for the warp's steps from the product of the earlier chunks
-  st_row<Real, DP>(SX, row, P, act);
-  __syncthreads();
-  Real R[DP];
-  if (warp == 0) {
-#pragma unroll
-    for (int j = 0; j < DP; ++j) R[j] = (j == lane) ? (Real)1 : (Real)0;
-  } else {
-    ld_row<Real, DP>(slot0 + (warp - 1) * spw * MAT, row, R);
-  }
-  __syncthreads();
-  for (int t = t0; t <= t1; ++t) {
-    if (act) st_vec<Real, DP>(a.tab + ((long)TGP * p.nT + t) * DD + row * DP, R);
-    if (t < t1) {   // R <- R G_t
-      __syncwarp();
-      st_row<Real, DP>(SX, row, R, act);
-      load_slot(SY, a.tab + ((long)TG * p.nT + t) * DD);
-      mm_row<Real, DP>(SX + row * LD, SY, R);
-    }
-  }
-  if (warp == (n - 1) / chunk && act) {
+  if (act) {
     st_vec<Real, DP>(a.btab + ((long)BGH * p.nb + k) * DD + row * DP, P);
     st_vec<Real, DP>(a.btab + ((long)BAH * p.nb + k) * DD + row * DP, Q);
   }
-  if (warp == 0) {
-    double acc = 0.0;
-    for (int t = s + lane; t <= e; t += 32) acc += a.ldt[t];
-    acc = warp_sum<double>(acc);
-    if (lane == 0) a.ld[k] = acc;
-  }
+  const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
+  double acc = 0.0;
+  for (int t = s + lane; t <= e; t += 32) acc += a.ldt[t];
+  acc = warp_sum<double>(acc);
+  if (lane == 0) a.ld[k] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// G_s ... G_{t-1} from the covariance-block-local prefix: tab[TGP][t] <-
+// E_j tab[TGP][t] for the steps of covariance block j (not the first of its
+// means block), one warp per step.
+// ---------------------------------------------------------------------------
+template <typename Real, int DP>
+__global__ void __launch_bounds__(32 * CovSizes<Real, DP>::FIX_WPC)
+    k_cov_gp_fix(KP<Real> p, CovArgs<Real> a, int Lc, int nbc) {
+  constexpr int MAT = CovSizes<Real, DP>::MAT, LD = Lay<Real, DP>::LD;
+  constexpr int WPC = CovSizes<Real, DP>::FIX_WPC;
+  constexpr long DD = (long)DP * DP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * WPC + warp;
+  if (t >= p.nT) return;
+  const int j = t / Lc;
+  if (j % a.R == 0) return;
+  Real* SX = reinterpret_cast<Real*>(smem_raw) + warp * 2 * MAT;
+  Real* SY = SX + MAT;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  Real* gp = a.tab + ((long)TGP * p.nT + t) * DD;
+  Real r[DP];
+  ld_vec<Real, DP>(a.cblk + (2L * nbc + j) * DD + row * DP, r);
+  st_row<Real, DP>(SX, row, r, act);
+  ld_vec<Real, DP>(gp + row * DP, r);
+  st_row<Real, DP>(SY, row, r, act);
+  __syncwarp();
+  mm_row<Real, DP>(SX + row * LD, SY, r);
+  if (act) st_vec<Real, DP>(gp + row * DP, r);
 }
 
 }  // namespace auxk

@@ -68,7 +68,7 @@ struct Ops {
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_cov_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::APP_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
-    e = cudaFuncSetAttribute(k_cov_products<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::PROD_SMEM);
+    e = cudaFuncSetAttribute(k_cov_gp_fix<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::FIX_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_mf_reduce<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::RED);
     if (e != cudaSuccess) return AUX_E_CUDA;
@@ -135,15 +135,18 @@ struct Ops {
   static constexpr long DD = (long)DP * DP;
 
   static void cov_pass(aux_model* m, const KP<Real>& p, cudaStream_t st) {
-    ProfScope ps(m, PK_COV, st);
     KP<Real> pc = p;   // the covariance scan runs on its own partition (block length Lc)
     pc.L = m->Lc;
     pc.nb = m->nbc;
     Real* b0 = (Real*)m->cagg0;
     Real* b1 = (Real*)m->cagg1;
-    cudaMemsetAsync(m->cov_status, 0, sizeof(int32_t), st);
-    k_cov_reduce<Real, DP><<<m->nbc, 32, CZ::RED_SMEM, st>>>(pc, b0, m->cov_status);
+    {
+      ProfScope ps(m, PK_COV_REDUCE, st);
+      cudaMemsetAsync(m->cov_status, 0, sizeof(int32_t), st);
+      k_cov_reduce<Real, DP><<<m->nbc, 32, CZ::RED_SMEM, st>>>(pc, b0, m->cov_status);
+    }
     for (int off = 1; off < m->nbc; off *= 2) {
+      ProfScope ps(m, PK_COV_SCAN, st);
       k_cov_scan_level<Real, DP><<<m->nbc, 32, CZ::SCAN_SMEM, st>>>(pc, b0, b1, off, m->cov_status);
       Real* tmp = b0; b0 = b1; b1 = tmp;
     }
@@ -151,9 +154,18 @@ struct Ops {
     a.prefix = (m->nbc > 1) ? b0 : nullptr;
     a.tab = (Real*)m->tab; a.btab = (Real*)m->btab; a.ld = m->cov_ld; a.ldt = m->cov_ldt;
     a.status = m->cov_status;
-    k_cov_apply<Real, DP><<<m->nbc, 32, CZ::APP_SMEM, st>>>(pc, a);
-    const int nw = m->L <= 32 ? m->L : 16;
-    k_cov_products<Real, DP><<<m->nb, 32 * nw, CZ::PROD_SMEM, st>>>(p, a);
+    a.cblk = b1;   // the scan buffer not holding the prefix
+    a.R = m->L / m->Lc;
+    {
+      ProfScope ps(m, PK_COV_APPLY, st);
+      k_cov_apply<Real, DP><<<m->nbc, 32, CZ::APP_SMEM, st>>>(pc, a);
+    }
+    {
+      ProfScope ps(m, PK_COV_PRODUCTS, st);
+      k_cov_products<Real, DP><<<m->nb, 32, CZ::PROD_SMEM, st>>>(p, a, m->nbc);
+      k_cov_gp_fix<Real, DP><<<(m->T + CZ::FIX_WPC - 1) / CZ::FIX_WPC, 32 * CZ::FIX_WPC, CZ::FIX_SMEM,
+                               st>>>(p, a, m->Lc, m->nbc);
+    }
   }
 
   // the tables for this call: recomputed (shared mode) or reused while valid (cached mode)
