@@ -20,7 +20,7 @@
 //                  with the MH terms at x* and ytilde*.
 // One CTA runs MEAN_WPC chains of the same block, one warp per chain (lane =
 // row), so the tables of step t are staged once per CTA in shared memory,
-// double-buffered with asynchronous copies one step ahead.
+// with asynchronous copies one step ahead.
 #pragma once
 #include "aux_cov.cuh"
 
@@ -53,11 +53,17 @@ template <typename Real> struct MeanArgs {
 
 constexpr int MEAN_WPC = 8;   // chains (warps) per CTA
 
+// Staging buffers: step t reads buffer t % NBUF while the copies of step t+1
+// fill the next one; the buffer refilled at step t was last read at step t-2,
+// which every warp has finished once it passed the barrier of step t-1, so
+// one barrier per step suffices.
+constexpr int NBUF = 3;
+
 template <typename Real, int DP> struct MeanSizes {
   static constexpr int MAT = Lay<Real, DP>::MAT, VEC = Lay<Real, DP>::VEC;
-  // two staging buffers of NT tables, R_y^{-1}, three vector slots per warp
+  // NBUF staging buffers of NT tables, R_y^{-1}, three vector slots per warp
   static constexpr size_t smem(int nt) {
-    return (size_t)(2 * nt * MAT + MAT + MEAN_WPC * 3 * VEC) * sizeof(Real);
+    return (size_t)(NBUF * nt * MAT + MAT + MEAN_WPC * 3 * VEC) * sizeof(Real);
   }
   static constexpr size_t RED = smem(2), APP = smem(5), BWD = smem(1), CROSS = smem(1);
 };
@@ -70,14 +76,24 @@ __device__ __forceinline__ void put_vec(Real* vs, Real val, int lane) {
   __syncwarp();
 }
 
+// the lane's row constants of the dynamics: F_ii, b_i
+template <typename Real> struct RowDyn {
+  Real phi, b;
+};
+template <typename Real, int DP>
+__device__ __forceinline__ RowDyn<Real> row_dyn(const KP<Real>& p, int row) {
+  return RowDyn<Real>{p.F[row * DP + row], p.b[row]};
+}
+
 // m^p = F m + b for the lane's row, m given per lane (slot vs used for dense F)
 template <typename Real, int DP>
-__device__ __forceinline__ Real predict_mean(const KP<Real>& p, Real m, Real* vs, int lane, int row) {
-  if (p.fdiag) return fma(p.F[row * DP + row], m, p.b[row]);
+__device__ __forceinline__ Real predict_mean(const KP<Real>& p, const RowDyn<Real>& rd, Real m,
+                                             Real* vs, int lane, int row) {
+  if (p.fdiag) return fma(rd.phi, m, rd.b);
   put_vec<Real, DP>(vs, m, lane);
   Real f[DP];
   ld_vec<Real, DP>(p.F + row * DP, f);
-  return dot_rv<Real, DP>(f, vs) + p.b[row];
+  return dot_rv<Real, DP>(f, vs) + rd.b;
 }
 
 // R_y^{-1} rows into a padded slot (linear-Gaussian emission)
@@ -100,7 +116,7 @@ __global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_reduce(KP<Real> p, MeanArg
   constexpr int NT = 2;   // W, W^T
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* buf = reinterpret_cast<Real*>(smem_raw);
-  Real* sRy = buf + 2 * NT * MAT;
+  Real* sRy = buf + NBUF * NT * MAT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Real* vr = sRy + MAT + warp * 3 * VEC;
   Real* vw = vr + VEC;
@@ -110,6 +126,7 @@ __global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_reduce(KP<Real> p, MeanArg
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
+  const RowDyn<Real> rd = row_dyn<Real, DP>(p, row);
   const long tstride = (long)p.nT * DD;
   if (a.x && p.emis == AUX_EMIS_LINEAR_GAUSSIAN) load_ryinv<Real, DP>(p, sRy);
   stage_mats<Real, DP>(buf, a.tab + (long)TW * tstride + s * DD, tstride, NT);
@@ -129,10 +146,10 @@ __global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_reduce(KP<Real> p, MeanArg
   fetch(s, xn, yn);
   Real m = 0;
   for (int t = s; t <= e; ++t) {
-    const int cur = (t - s) & 1;
+    const int cur = (t - s) % NBUF, nxt = (t - s + 1) % NBUF;
     const Real xi = xn, yv = yn;
     if (t < e) fetch(t + 1, xn, yn);
-    if (t < e) stage_mats<Real, DP>(buf + (cur ^ 1) * NT * MAT, a.tab + (long)TW * tstride + (t + 1) * DD, tstride, NT);
+    if (t < e) stage_mats<Real, DP>(buf + nxt * NT * MAT, a.tab + (long)TW * tstride + (t + 1) * DD, tstride, NT);
     else cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
@@ -162,13 +179,12 @@ __global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_reduce(KP<Real> p, MeanArg
       } else {
         yti = yv;
       }
-      const Real mp = (t == 0) ? p.m0[row] : predict_mean<Real, DP>(p, m, vq, lane, row);
+      const Real mp = (t == 0) ? p.m0[row] : predict_mean<Real, DP>(p, rd, m, vq, lane, row);
       put_vec<Real, DP>(vr, act ? yti - mp : (Real)0, lane);
       const Real wi = dot_row_vec<Real, DP>(sW + row * LD, vr);
       put_vec<Real, DP>(vw, wi, lane);
       m = yti - p.r * dot_row_vec<Real, DP>(sWT + row * LD, vw);
     }
-    __syncthreads();
   }
   if (valid && act) a.z[((long)c * p.nb + k) * DP + lane] = m;
   if (valid && a.x && k == 0 && lane == 0) p.status_iter[c] = *a.cov_status;
@@ -192,7 +208,7 @@ __global__ void __launch_bounds__(32 * MEAN_WPC)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* buf = reinterpret_cast<Real*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  Real* vq = buf + 3 * MAT + warp * 3 * VEC;
+  Real* vq = buf + (NBUF + 1) * MAT + warp * 3 * VEC;
   const int c = blockIdx.x * MEAN_WPC + warp;
   const bool valid = c < p.C;
   const bool act = lane < DP;
@@ -211,11 +227,11 @@ __global__ void __launch_bounds__(32 * MEAN_WPC)
   if (n > 0) stage_mats<Real, DP>(buf, mats + kk_of(0) * DD, DD, 1);
   Real inn = (n > 0) ? in[(cb + kk_of(0)) * DP + row] : (Real)0;
   for (int j = 0; j < n; ++j) {
-    const int cur = j & 1, kk = kk_of(j);
+    const int cur = j % NBUF, nxt = (j + 1) % NBUF, kk = kk_of(j);
     const Real inc = inn;
     if (j + 1 < n) {
       inn = in[(cb + kk_of(j + 1)) * DP + row];
-      stage_mats<Real, DP>(buf + (cur ^ 1) * MAT, mats + kk_of(j + 1) * DD, DD, 1);
+      stage_mats<Real, DP>(buf + nxt * MAT, mats + kk_of(j + 1) * DD, DD, 1);
     } else {
       cp_async_commit();
     }
@@ -226,7 +242,6 @@ __global__ void __launch_bounds__(32 * MEAN_WPC)
       m = dot_row_vec<Real, DP>(buf + cur * MAT + row * LD, vq) + inc;
       if (act) out[(cb + (backward ? kk - 1 : kk + 1)) * DP + lane] = m;
     }
-    __syncthreads();
   }
 }
 
@@ -244,7 +259,7 @@ __global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_apply(KP<Real> p, MeanArgs
   const int NT = epi ? 5 : 2;   // W, W^T (, G, chol(Sigma), G_s .. G_{t-1})
   Real* buf = reinterpret_cast<Real*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  Real* vr = buf + 2 * 5 * MAT + MAT + warp * 3 * VEC;
+  Real* vr = buf + NBUF * 5 * MAT + MAT + warp * 3 * VEC;
   Real* vw = vr + VEC;
   Real* vq = vw + VEC;
   const int k = blockIdx.x % p.nb, c = (blockIdx.x / p.nb) * MEAN_WPC + warp;
@@ -252,13 +267,14 @@ __global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_apply(KP<Real> p, MeanArgs
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
+  const RowDyn<Real> rd = row_dyn<Real, DP>(p, row);
   const long tstride = (long)p.nT * DD;
   const Real* PF = a.tab + (long)TPF * tstride;
   stage_mats<Real, DP>(buf, a.tab + (long)TW * tstride + s * DD, tstride, NT);
   Real mp = 0;
   if (valid) {
     if (k == 0) mp = p.m0[row];
-    else mp = predict_mean<Real, DP>(p, a.mstart[((long)c * p.nb + k) * DP + row], vq, lane, row);
+    else mp = predict_mean<Real, DP>(p, rd, a.mstart[((long)c * p.nb + k) * DP + row], vq, lane, row);
   }
   double qacc = 0.0;
   Real ubar = 0;
@@ -273,10 +289,10 @@ __global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_apply(KP<Real> p, MeanArgs
   Real yn, en;
   fetch(s, yn, en);
   for (int t = s; t <= e; ++t) {
-    const int cur = (t - s) & 1;
+    const int cur = (t - s) % NBUF, nxt = (t - s + 1) % NBUF;
     const Real yti = yn, eg = en;
     if (t < e) fetch(t + 1, yn, en);
-    if (t < e) stage_mats<Real, DP>(buf + (cur ^ 1) * 5 * MAT, a.tab + (long)TW * tstride + (t + 1) * DD, tstride, NT);
+    if (t < e) stage_mats<Real, DP>(buf + nxt * 5 * MAT, a.tab + (long)TW * tstride + (t + 1) * DD, tstride, NT);
     else cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
@@ -292,7 +308,7 @@ __global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_apply(KP<Real> p, MeanArgs
       if (a.mf && lane < p.d) a.mf[ct * p.d + lane] = m;
       if (a.Pf && lane < p.d)
         for (int j = 0; j < p.d; ++j) a.Pf[(ct * p.d + lane) * p.d + j] = PF[t * DD + lane * DP + j];
-      const Real mpn = (t < p.nT - 1) ? predict_mean<Real, DP>(p, m, vq, lane, row) : (Real)0;
+      const Real mpn = (t < p.nT - 1) ? predict_mean<Real, DP>(p, rd, m, vq, lane, row) : (Real)0;
       if (epi) {
         const Real* sG = sWT + MAT;
         const Real* sLS = sG + MAT;
@@ -312,7 +328,6 @@ __global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_apply(KP<Real> p, MeanArgs
       }
       mp = mpn;
     }
-    __syncthreads();
   }
   if (!valid) return;
   const double q = warp_sum<double>(qacc);
@@ -341,7 +356,7 @@ __global__ void __launch_bounds__(32 * MEAN_WPC)
   constexpr long DD = (long)DP * DP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* buf = reinterpret_cast<Real*>(smem_raw);
-  Real* sRy = buf + 2 * MAT;
+  Real* sRy = buf + NBUF * MAT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Real* vx = sRy + MAT + warp * 3 * VEC;
   Real* vxs = vx + VEC;
@@ -359,13 +374,13 @@ __global__ void __launch_bounds__(32 * MEAN_WPC)
   Real un = b.U[(cb + e) * DP + row];
   MhIn<Real> qn = b.mh ? mh_load<Real>(p, b, cb + e, e, lane) : MhIn<Real>{};
   for (int t = e; t >= s; --t) {
-    const int cur = (e - t) & 1;
+    const int cur = (e - t) % NBUF, nxt = (e - t + 1) % NBUF;
     const Real uc = un;
     const MhIn<Real> qc = qn;
     if (t > s) {
       un = b.U[(cb + t - 1) * DP + row];
       if (b.mh) qn = mh_load<Real>(p, b, cb + t - 1, t - 1, lane);
-      stage_mats<Real, DP>(buf + (cur ^ 1) * MAT, b.G + (t - 1) * DD, DD, 1);
+      stage_mats<Real, DP>(buf + nxt * MAT, b.G + (t - 1) * DD, DD, 1);
     } else {
       cp_async_commit();
     }
@@ -378,7 +393,6 @@ __global__ void __launch_bounds__(32 * MEAN_WPC)
       if (lane < p.d) b.xs[ct * p.d + lane] = xi;
       if (b.mh) acc += mh_step_terms<Real, DP>(p, b, ct, t, xi, qc, sRy, vxs, lane, row);
     }
-    __syncthreads();
   }
   if (valid && b.mh) {
     acc = warp_sum<double>(acc);
