@@ -61,6 +61,18 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(value, device, world):
+    """The maximum of a float over all ranks of the process group (the value
+    itself on one rank): the bench reports the slowest replica's time."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 def make_workload(name, rank=0):
     from paper_2303_00301_gb300 import workloads
     w = WORKLOADS[name]
@@ -156,7 +168,7 @@ def kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz):
     if kind == "cov_products":
         # composition of the covariance-block products (2 per covariance block) and the
         # prefix fix-up of G_s..G_{t-1} (one product per step)
-        return (2 * nbc + T) * 2.0 * d ** 3 / 2, None
+        return (2 * nbc + T) * 2.0 * d ** 3, None
     return None, None
 
 
@@ -168,6 +180,32 @@ KERNEL_NAMES = {
               "cov_reduce": "k_cov_reduce", "cov_scan": "k_cov_scan_level",
               "cov_apply": "k_cov_apply", "cov_products": "k_cov_products"},
 }
+
+
+def source_hash():
+    """sha256 over the library sources (csrc/*.cu*, csrc/*.h, include/*.h)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2303_00301_gb300", "csrc", "*.cu*")) +
+                   glob.glob(os.path.join(ROOT, "paper_2303_00301_gb300", "csrc", "*.h")) +
+                   glob.glob(os.path.join(ROOT, "include", "*.h")))
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def dram_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when
+    the library sources changed since that capture (profiles/dram_traffic.json)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    if rec.get("source_sha256") != source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch", {}).get(kernel)
 
 
 def roofline_line(mode, kind, prof, w, d, T, C, nb, nbc, fdiag, esz, peaks, steps, path):
@@ -183,7 +221,7 @@ def roofline_line(mode, kind, prof, w, d, T, C, nb, nbc, fdiag, esz, peaks, step
     if bytes_ is not None and "hbm_gbs" in peaks:
         achieved = bytes_ / (avg_ms / 1e3) / 1e9
         line.update({"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": dram_traffic(name),
                      "bytes_per_launch": bytes_, "peak_basis": "measured HBM copy bandwidth"})
         if flops is not None:
             line["flops_per_launch"] = flops
@@ -198,7 +236,7 @@ def roofline_line(mode, kind, prof, w, d, T, C, nb, nbc, fdiag, esz, peaks, step
         basis = "nominal GB300 FP64 rate"
     achieved = flops / (avg_ms / 1e3) / 1e12
     line.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                 "frac": achieved / peak, "traffic": None, "flops_per_launch": flops,
+                 "frac": achieved / peak, "traffic": dram_traffic(name), "flops_per_launch": flops,
                  "diagonal_F": fdiag, "peak_basis": basis})
     return line
 
@@ -403,9 +441,7 @@ def run_ours(args):
             ck = clocks.stop()
         step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
         accept_rate_m = accm.float().mean().item() / args.steps
-        t = torch.tensor([sum(step_ms)], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = max_over_ranks(sum(step_ms), "cuda", world)
         # the same steps without the per-launch events (host overhead check)
         evu = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
@@ -417,8 +453,8 @@ def run_ours(args):
             itm += 1
         torch.cuda.synchronize()
         unprof_ms = sum(e0.elapsed_time(e1) for e0, e1 in evu) / args.steps
-        res = {"mode": mode, "value": world * C * T * args.steps / (t.item() / 1e3), "unit": UNIT,
-               "ms_per_step": t.item() / args.steps, "ms_per_step_without_events": unprof_ms,
+        res = {"mode": mode, "value": world * C * T * args.steps / (t_ms / 1e3), "unit": UNIT,
+               "ms_per_step": t_ms / args.steps, "ms_per_step_without_events": unprof_ms,
                "step_ms_median": statistics.median(step_ms),
                "accept_rate": accept_rate_m,
                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
@@ -458,10 +494,8 @@ def run_ours(args):
         la_host.copy_(la, non_blocking=True)
         torch.cuda.synchronize()
         it += 1
-    e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
-    e2e_value = world * C * T * args.steps / e2e_s.item()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda", world)
+    e2e_value = world * C * T * args.steps / e2e_s
     rc, per_chain = s.status()
 
     # roofline lines: the dominant kernel of the headline mode, and one line per
