@@ -29,6 +29,10 @@ Emission models (gamma and its gradient):
   stochastic vol.  log h(y|x) = sum_i log N(y_i; 0, exp(x_i))  (Section 4.1)
 An optional observation mask switches gamma_t off (gamma_t = 0, v_t = 0) at
 unobserved steps, as in the two-step model of Section 4.4.
+
+aux_step_second_order is the same step with the second-order proposal of
+Section 2.2, Eqs. (2.8)-(2.9) (the Hessian of gamma_t enters the
+pseudo-observation covariance).
 """
 import numpy as np
 
@@ -58,6 +62,11 @@ class LinearGaussianEmission:
         g = (self.y - x) @ self.Ry_inv.T
         return g * self.mask[:, None]
 
+    def hess(self, x):
+        """Hessian of log h(y_t | x_t) in x_t, [T, d, d]: -R_y^{-1} (0 where masked)."""
+        T = len(x)
+        return -self.Ry_inv[None, :, :] * self.mask[:, None, None] * np.ones((T, 1, 1))
+
 
 class SVEmission:
     """log h(y_t | x_t) = sum_i log N(y_t(i); 0, exp(x_t(i)))."""
@@ -73,6 +82,11 @@ class SVEmission:
     def grad(self, x):
         g = -0.5 + 0.5 * self.y ** 2 * np.exp(-x)
         return g * self.mask[:, None]
+
+    def hess(self, x):
+        """Hessian of log h(y_t | x_t) in x_t, [T, d, d]: diag(-y^2 exp(-x) / 2)."""
+        h = -0.5 * self.y ** 2 * np.exp(-x) * self.mask[:, None]
+        return np.einsum("ti,ij->tij", h, np.eye(x.shape[1]))
 
 
 def log_prior(x, m0, P0, F, b, Q):
@@ -123,22 +137,78 @@ def aux_step(x, model, delta, eps_aux, eps_back, log_u):
                 ytilde=yt, ytilde_star=yt_star, kf=kf)
 
 
-def aux_step_philox(x, model, delta, seed, chain, iteration):
+def second_order_obs(x, u, model, delta):
+    """Pseudo-observations of the second-order proposal (Section 2.2, the
+    expansion Eq. (2.8) and the proposal Eq. (2.9)), Sigma_t = I:
+        Lambda_t = Hessian of gamma_t at x_t,
+        Omega_t  = ((2/delta) I - Lambda_t)^{-1},
+        omega_t  = Omega_t ((2/delta) u_t + v_t - Lambda_t x_t).
+    Returns (omega [T, d], Omega [T, d, d])."""
+    em = model["emission"]
+    T, d = x.shape
+    v = em.grad(x)
+    Lam = em.hess(x)
+    Om = np.zeros((T, d, d))
+    om = np.zeros((T, d))
+    for t in range(T):
+        Om[t] = np.linalg.inv((2.0 / delta) * np.eye(d) - Lam[t])
+        om[t] = Om[t] @ ((2.0 / delta) * u[t] + v[t] - Lam[t] @ x[t])
+    return om, Om
+
+
+def aux_step_second_order(x, model, delta, eps_aux, eps_back, log_u):
+    """One auxiliary Kalman MH step with the second-order proposal.
+
+    Same augmented target as aux_step; the proposal is the smoothing law of the
+    LGSSM with the model's dynamics and observations omega_t ~ N(z_t, Omega_t)
+    (second_order_obs), sampled by the Kalman filter and RTS sampler of
+    Appendix A.1 with a time-varying observation covariance. log alpha is the
+    direct formula on full joint densities, as in aux_step.
+    """
+    m0, P0, F, b, Q = model["m0"], model["P0"], model["F"], model["b"], model["Q"]
+    em = model["emission"]
+    T, d = x.shape
+    R = 0.5 * delta * np.eye(d)
+    u = x + np.sqrt(0.5 * delta) * eps_aux
+    om, Om = second_order_obs(x, u, model, delta)
+    kf = kalman.kalman_filter(om, m0, P0, F, b, Q, Om)
+    x_star = kalman.rts_sample(kf, F, b, Q, eps_back)
+    om_s, Om_s = second_order_obs(x_star, u, model, delta)
+    kf_star = kalman.kalman_filter(om_s, m0, P0, F, b, Q, Om_s)
+
+    def log_pi(z):
+        return log_prior(z, m0, P0, F, b, Q) + em.log_h(z).sum() + _log_obs(z, u, R)
+
+    def log_q(z, obs, covs, logZ):
+        return (log_prior(z, m0, P0, F, b, Q)
+                + sum(kalman.mvn_logpdf(obs[t], z[t], covs[t]) for t in range(len(z))) - logZ)
+
+    log_alpha = (log_pi(x_star) + log_q(x, om_s, Om_s, kf_star["logZ"])
+                 - log_pi(x) - log_q(x_star, om, Om, kf["logZ"]))
+    accepted = bool(log_u < log_alpha)
+    return dict(x_new=x_star if accepted else x.copy(), x_star=x_star,
+                log_alpha=float(log_alpha), accepted=accepted,
+                logZ=kf["logZ"], logZ_star=kf_star["logZ"], u=u,
+                omega=om, Omega=Om, omega_star=om_s, Omega_star=Om_s, kf=kf)
+
+
+def aux_step_philox(x, model, delta, seed, chain, iteration, order=1):
     """aux_step with the library's Philox streams for (seed, chain, iteration)."""
     T, d = x.shape
     eps_aux = philox.path_normals(seed, chain, iteration, philox.PURPOSE_AUX, T, d)
     eps_back = philox.path_normals(seed, chain, iteration, philox.PURPOSE_BACKWARD, T, d)
     log_u = float(np.log(philox.mh_uniform(seed, chain, iteration)))
-    return aux_step(x, model, delta, eps_aux, eps_back, log_u)
+    step = aux_step if order == 1 else aux_step_second_order
+    return step(x, model, delta, eps_aux, eps_back, log_u)
 
 
-def run_chain(x0, model, delta, seed, chain, n_iters, iter0=0, keep=None):
+def run_chain(x0, model, delta, seed, chain, n_iters, iter0=0, keep=None, order=1):
     """Run n_iters steps; returns (x_final, n_accepted, kept states or None)."""
     x = np.array(x0, dtype=np.float64)
     n_acc = 0
     kept = [] if keep is not None else None
     for k in range(n_iters):
-        st = aux_step_philox(x, model, delta, seed, chain, iter0 + k)
+        st = aux_step_philox(x, model, delta, seed, chain, iter0 + k, order=order)
         x = st["x_new"]
         n_acc += st["accepted"]
         if keep is not None:
