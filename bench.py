@@ -407,9 +407,9 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def run_mode(mode, with_clocks):
+    def run_mode(mode, with_clocks, proposal=1):
         """Warm-up, then args.steps timed steps (L2 flushed before each), per-launch events on."""
-        sm = AuxKalman(wl, dtype=w["dtype"], block_len=args.block_len, mode=mode)
+        sm = AuxKalman(wl, dtype=w["dtype"], block_len=args.block_len, mode=mode, proposal=proposal)
         xm = torch.tensor(wl.x_init, dtype=tdt, device="cuda")
         accm = torch.zeros(C, dtype=torch.int32, device="cuda")
         lam = torch.zeros(C, dtype=torch.float64, device="cuda")
@@ -453,7 +453,8 @@ def run_ours(args):
             itm += 1
         torch.cuda.synchronize()
         unprof_ms = sum(e0.elapsed_time(e1) for e0, e1 in evu) / args.steps
-        res = {"mode": mode, "value": world * C * T * args.steps / (t_ms / 1e3), "unit": UNIT,
+        res = {"mode": mode, "proposal": "second order" if proposal == 2 else "first order",
+               "value": world * C * T * args.steps / (t_ms / 1e3), "unit": UNIT,
                "ms_per_step": t_ms / args.steps, "ms_per_step_without_events": unprof_ms,
                "step_ms_median": statistics.median(step_ms),
                "accept_rate": accept_rate_m,
@@ -473,6 +474,10 @@ def run_ours(args):
                 so.close()
                 others[mode] = r
                 profs[mode] = po
+        # the second-order proposal (Eqs. (2.8)-(2.9)): per-chain path, same delta
+        so, _, _, _, _, _, r = run_mode("per_chain", False, proposal=2)
+        so.close()
+        others["per_chain_second_order"] = r
 
     # end to end through the public API from pinned host buffers
     x_host = torch.tensor(wl.x_init, dtype=tdt).pin_memory()

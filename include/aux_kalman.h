@@ -175,6 +175,29 @@ int aux_loglik_grad(aux_model *m, const void *ytilde, double *logZ, double *g_mu
  * Errors: INVALID_ARG, OOM. */
 int aux_set_mode(aux_model *m, int32_t mode);
 
+/* Proposals (aux_set_proposal) */
+#define AUX_PROPOSAL_FIRST_ORDER  1  /* Eq. (2.7): R = (delta/2) I (default) */
+#define AUX_PROPOSAL_SECOND_ORDER 2  /* Eqs. (2.8)-(2.9): Hessian of log h in the pseudo-observations */
+
+/* Choose the auxiliary proposal of aux_kalman_step (Section 2.2).
+ * AUX_PROPOSAL_FIRST_ORDER linearises gamma_t = log h(y_t | x_t) to first
+ * order: pseudo-observations ytilde_t = u_t + (delta/2) v_t with covariance
+ * R = (delta/2) I (Eq. (2.7)). AUX_PROPOSAL_SECOND_ORDER adds the Hessian
+ * Lambda_t of gamma_t at x_t (Eq. (2.8)) and samples from the LGSSM with
+ * observations omega_t = Omega_t ((2/delta) u_t + v_t - Lambda_t x_t) and
+ * covariance Omega_t = ((2/delta) I - Lambda_t)^{-1} (Eq. (2.9), Sigma_t = I);
+ * the MH ratio then keeps the Omega-dependent proposal terms. The library
+ * supports diagonal Hessians (the SV emission, or a linear-Gaussian emission
+ * with diagonal R_y; with a Gaussian emission the second-order proposal is
+ * exact and every step is accepted). The second-order proposal runs in
+ * AUX_MODE_PER_CHAIN only: its covariances depend on the chain's state, so
+ * aux_kalman_step returns AUX_E_UNSUPPORTED in a table mode. The first switch
+ * to the second order allocates 2*C*T*d elements (may return OOM).
+ * aux_loglik, aux_sample_path and aux_loglik_grad are unaffected (they take
+ * pseudo-observations with R = (delta/2) I).
+ * Errors: INVALID_ARG (unknown order), UNSUPPORTED (non-diagonal Hessian), OOM. */
+int aux_set_proposal(aux_model *m, int32_t order);
+
 /* Replace the model of an existing handle (same dtype, d_x, T, n_chains,
  * emis_kind, y_per_chain): validates as aux_init_model, then overwrites the
  * device copies of m0, P0, F, b, Q, y, R_y and delta. Synchronises the handle's

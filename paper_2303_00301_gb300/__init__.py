@@ -22,11 +22,13 @@ class AuxKalman:
     ``mode`` selects the execution of the filter (``aux_set_mode``): "per_chain"
     (every chain runs the full element recursion), "shared" (one covariance
     pass per call, means per chain) or "cached" (the covariance tables are kept
-    until the model changes).
+    until the model changes). ``proposal`` is the order of the auxiliary
+    proposal (``aux_set_proposal``): 1 (first order) or 2 (second order,
+    per-chain mode only).
     """
 
     def __init__(self, workload, dtype="f32", seed=None, n_chains=None, block_len=0, stream=None,
-                 mode="per_chain"):
+                 mode="per_chain", proposal=1):
         import torch
         b = _load_binding()
         self.b = b
@@ -46,6 +48,9 @@ class AuxKalman:
         self.mode = mode
         if mode != "per_chain":
             b.aux_set_mode(self.handle, b.AUX_MODE_SHARED_COV if mode == "shared" else b.AUX_MODE_CACHED_COV)
+        self.proposal = proposal
+        if proposal != 1:
+            b.aux_set_proposal(self.handle, proposal)
 
     def step(self, x, n_iters=1, iter0=0, accept_count=None, log_alpha=None, stream=None):
         self.b.aux_kalman_step(self.handle, x, n_iters, iter0, accept_count, log_alpha, stream)

@@ -21,6 +21,7 @@ AUX_NOALLOC_SCRATCH_BYTES = 32 << 20
 AUX_F32, AUX_F64 = 0, 1
 AUX_EMIS_LINEAR_GAUSSIAN, AUX_EMIS_SV = 0, 1
 AUX_MODE_PER_CHAIN, AUX_MODE_SHARED_COV, AUX_MODE_CACHED_COV = 0, 1, 2
+AUX_PROPOSAL_FIRST_ORDER, AUX_PROPOSAL_SECOND_ORDER = 1, 2
 
 _dbl_p = ctypes.POINTER(ctypes.c_double)
 _u8_p = ctypes.POINTER(ctypes.c_uint8)
@@ -82,6 +83,8 @@ def _load():
     lib.aux_read_profile.restype = ctypes.c_int
     lib.aux_set_mode.argtypes = [vp, ctypes.c_int32]
     lib.aux_set_mode.restype = ctypes.c_int
+    lib.aux_set_proposal.argtypes = [vp, ctypes.c_int32]
+    lib.aux_set_proposal.restype = ctypes.c_int
     lib.aux_loglik_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.aux_loglik_grad.restype = ctypes.c_int
     lib.aux_set_model_params.argtypes = [vp, ctypes.POINTER(aux_model_desc)]
@@ -167,6 +170,10 @@ def aux_init_model(*, d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind, dt
 
 def aux_set_mode(handle, mode):
     _check(LIB.aux_set_mode(handle, int(mode)), "aux_set_mode")
+
+
+def aux_set_proposal(handle, order):
+    _check(LIB.aux_set_proposal(handle, int(order)), "aux_set_proposal")
 
 
 def aux_loglik_grad(handle, ytilde, g_mu, g_Phi, g_cholSigma, g_delta, logZ=None, stream=None):

@@ -224,6 +224,16 @@ int diag_flag(const aux_model_desc* desc) {
   return 1;
 }
 
+// the emission's Hessian in x_t is diagonal: SV, or linear-Gaussian with diagonal R_y
+int hess_diag_flag(const aux_model_desc* desc) {
+  if (desc->emis_kind == AUX_EMIS_SV) return 1;
+  const int d = desc->d_x;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      if (i != j && desc->R_y[i * d + j] != 0.0) return 0;
+  return 1;
+}
+
 }  // namespace
 
 extern "C" {
@@ -264,6 +274,7 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
   m->delta = desc->delta;
   m->seed = seed;
   m->fdiag = diag_flag(desc);
+  m->diag_hess = hess_diag_flag(desc);
   m->stream = (cudaStream_t)stream;
   m->esz = desc->dtype == AUX_F32 ? sizeof(float) : sizeof(double);
   cudaGetDevice(&m->device);
@@ -370,6 +381,22 @@ int aux_set_mode(aux_model* m, int32_t mode) {
   return AUX_OK;
 }
 
+int aux_set_proposal(aux_model* m, int32_t order) {
+  if (!m || (order != AUX_PROPOSAL_FIRST_ORDER && order != AUX_PROPOSAL_SECOND_ORDER))
+    return AUX_E_INVALID_ARG;
+  if (order == AUX_PROPOSAL_SECOND_ORDER) {
+    if (!m->diag_hess) return AUX_E_UNSUPPORTED;
+    if (!m->rho) {
+      const size_t path = (size_t)m->C * m->T * m->d * m->esz;
+      int rc = dev_alloc(m, &m->rho, path);
+      if (!rc) rc = dev_alloc(m, &m->rhos, path);
+      if (rc) { m->rho = m->rhos = nullptr; return rc; }
+    }
+  }
+  m->order = order;
+  return AUX_OK;
+}
+
 int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {
   if (!m || !desc) return AUX_E_INVALID_ARG;
   if (desc->dtype != m->dtype || desc->d_x != m->d || desc->T != m->T || desc->n_chains != m->C ||
@@ -378,12 +405,14 @@ int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {
   std::vector<double> Ryinv;
   const int vrc = validate_desc(desc, Ryinv);
   if (vrc) return vrc;
+  if (m->order == AUX_PROPOSAL_SECOND_ORDER && !hess_diag_flag(desc)) return AUX_E_UNSUPPORTED;
   if (cudaStreamSynchronize(m->stream) != cudaSuccess) return AUX_E_CUDA;
   const int rc = m->dtype == AUX_F32 ? upload_model<float>(m, desc, Ryinv, false)
                                      : upload_model<double>(m, desc, Ryinv, false);
   if (rc) return rc;
   m->delta = desc->delta;
   m->fdiag = diag_flag(desc);
+  m->diag_hess = hess_diag_flag(desc);
   m->cov_valid = 0;
   std::vector<double> gc;
   m->grad_ok = theta_constants(desc, gc) ? 1 : 0;

@@ -15,6 +15,8 @@ struct aux_model {
   int L = 0, nb = 0;
   int fdiag = 0;             // F has no off-diagonal entries
   int mode = AUX_MODE_PER_CHAIN;
+  int order = AUX_PROPOSAL_FIRST_ORDER;
+  int diag_hess = 0;         // the emission's Hessian is diagonal (SV, or R_y diagonal)
   double delta = 0.0;
   uint64_t seed = 0;
   size_t esz = 0;            // bytes per compute-type element
@@ -31,6 +33,7 @@ struct aux_model {
   double *fq = nullptr, *fld = nullptr, *mh_part = nullptr, *lz_part = nullptr;
   int32_t *status_iter = nullptr, *status = nullptr;
   int32_t *accept = nullptr;  // [C] this step's MH decisions
+  void *rho = nullptr, *rhos = nullptr;   // second order: [C][T][d] forward / reverse variances
   // gradient (aux_loglik_grad): theta constants and lazily allocated smoother buffers
   int grad_ok = 0;           // the model has the SV parameterisation
   double *gconst = nullptr;  // mu, phi, L, Q, Q^{-1}, P0^{-1} (FP64, unpadded)

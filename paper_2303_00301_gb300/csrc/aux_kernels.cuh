@@ -46,7 +46,16 @@ template <typename Real> struct KP {
   const Real* y;                             // [T][d] or [C][T][d]
   const uint8_t* mask;                       // [T] or null
   int32_t* status_iter;                      // [C], this step's status bits
+  int order;                                 // proposal: 1 first order, 2 second order
+  const Real* rho;   // [C][T][d] diagonal pseudo-observation variance (second order), or null: r
 };
+
+// the lane's diagonal entry of the pseudo-observation covariance at (chain, t)
+template <typename Real>
+__device__ __forceinline__ Real obs_var(const KP<Real>& p, int c, int t, int lane) {
+  if (lane >= p.d) return (Real)0;
+  return p.rho ? p.rho[((long)c * p.nT + t) * p.d + lane] : p.r;
+}
 
 enum : int { ST_NOT_PD = 1, ST_NONFINITE = 2 };
 
@@ -86,12 +95,22 @@ template <typename Real, int DP> struct Sizes {
   static_assert(RED_WPC >= 1 && SCAN_WPC >= 1 && APP_WPC >= 1, "shared memory budget");
 };
 
+// Diagonal of the Hessian of log h(y_t | x_t) at coordinate i (0 where t is not
+// observed): SV -y_i^2 exp(-x_i) / 2; linear-Gaussian -(R_y^{-1})_ii (R_y diagonal).
+template <typename Real>
+__device__ __forceinline__ Real second_order_hess(const KP<Real>& p, Real yi, int i, Real xi, int t) {
+  if (p.mask && !p.mask[t]) return (Real)0;
+  if (p.emis == AUX_EMIS_SV) return (Real)-0.5 * yi * yi * exp(-xi);
+  return -p.Ryinv[i * p.DP + i];
+}
+
 // ---------------------------------------------------------------------------
 // k_linearise: A1 + A2 at the current state.
 // ---------------------------------------------------------------------------
 template <typename Real>
 __global__ void k_linearise(KP<Real> p, const Real* __restrict__ x, Real* __restrict__ u,
-                            Real* __restrict__ v, Real* __restrict__ yt, uint64_t iter) {
+                            Real* __restrict__ v, Real* __restrict__ yt, Real* __restrict__ rho,
+                            uint64_t iter) {
   const long n = (long)p.C * p.nT * p.d;
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
        idx += (long)gridDim.x * blockDim.x) {
@@ -115,7 +134,15 @@ __global__ void k_linearise(KP<Real> p, const Real* __restrict__ x, Real* __rest
     const Real ui = xr[i] + p.sqrt_r * e;
     u[idx] = ui;
     v[idx] = vi;
-    yt[idx] = ui + p.r * vi;
+    if (p.order == 2) {
+      // second order (Eqs. (2.8)-(2.9)): Omega = (I / r - Lambda)^{-1}, omega = Omega (u / r + v - Lambda x)
+      const Real li = second_order_hess(p, yr[i], i, xr[i], t);
+      const Real om = (Real)1 / ((Real)1 / p.r - li);
+      rho[idx] = om;
+      yt[idx] = om * (ui / p.r + vi - li * xr[i]);
+    } else {
+      yt[idx] = ui + p.r * vi;
+    }
     if (t == 0 && i == 0) p.status_iter[c] = 0;
   }
 }
@@ -457,7 +484,8 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::RED_WPC, 1)
     {
       Real s_[DP];
 #pragma unroll
-      for (int j = 0; j < DP; ++j) s_[j] = pprow[j] + ((j == lane && j < p.d) ? p.r : (Real)0);
+      const Real rl = obs_var<Real>(p, c, t, lane);
+      for (int j = 0; j < DP; ++j) s_[j] = pprow[j] + (j == lane ? rl : (Real)0);
       chol_rot<Real, DP>(s_, SL, nullptr, nullptr, vdiag, nullptr, p.d, lane, &bad);
     }
     const Real rres = (lane < p.d) ? ytc[(long)t * p.d + lane] - mpi : (Real)0;
@@ -794,11 +822,12 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
     }
   };
 
-  // factor of S = P^p + R only (SG / vdB)
-  auto factor_S = [&]() {
+  // factor of S = P^p + R_t only (SG / vdB)
+  auto factor_S = [&](int t) {
     Real s_[DP];
+    const Real rl = obs_var<Real>(p, c, t, lane);
 #pragma unroll
-    for (int j = 0; j < DP; ++j) s_[j] = pprow[j] + ((j == lane && j < p.d) ? p.r : (Real)0);
+    for (int j = 0; j < DP; ++j) s_[j] = pprow[j] + (j == lane ? rl : (Real)0);
     chol_rot<Real, DP>(s_, SG, nullptr, nullptr, vdB, nullptr, p.d, lane, &bad);
   };
 
@@ -816,21 +845,22 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
     __syncwarp();
     predict();
   }
-  factor_S();
+  factor_S(s);
   update(s);
   for (int t = s + 1; t <= e; ++t) {
     predict();
     if (epi) {
       Real a_[DP], s_[DP];
+      const Real rl = obs_var<Real>(p, c, t, lane);
 #pragma unroll
       for (int j = 0; j < DP; ++j) {
         a_[j] = pprow[j];
-        s_[j] = pprow[j] + ((j == lane && j < p.d) ? p.r : (Real)0);
+        s_[j] = pprow[j] + (j == lane ? rl : (Real)0);
       }
       chol_rot2<Real, DP>(a_, SL, SLR, vdA, s_, SG, vdB, p.d, lane, &bad);
       epilogue(t - 1);
     } else {
-      factor_S();
+      factor_S(t);
     }
     update(t);
   }
@@ -885,24 +915,33 @@ template <typename Real> struct BackArgs {
   const Real* v;
   Real* yts;
   double* mh_part;
+  // second-order proposal: forward pseudo-observations and variances, reverse variances out
+  const Real* yt;
+  const Real* rho;
+  Real* rhos;
 };
 
 // The per-step inputs of mh_step_terms for the lane's coordinate (lane < d):
 // x_t, u_t, v_t and y_t, loaded separately so that callers can fetch them early.
 template <typename Real> struct MhIn {
   Real xo, ui, vi, yi;
+  Real om, rh;   // second order: omega_t and Omega_t (diagonal) at the current state
 };
 
 template <typename Real>
 __device__ __forceinline__ MhIn<Real> mh_load(const KP<Real>& p, const BackArgs<Real>& a, long ct,
                                               int t, int lane) {
-  MhIn<Real> q{(Real)0, (Real)0, (Real)0, (Real)0};
+  MhIn<Real> q{(Real)0, (Real)0, (Real)0, (Real)0, (Real)0, (Real)1};
   if (lane < p.d) {
     const long idx = ct * p.d + lane;
     q.xo = a.x[idx];
     q.ui = a.u[idx];
     q.vi = a.v[idx];
     q.yi = p.y[(p.y_per_chain ? ct : (long)t) * p.d + lane];
+    if (p.order == 2) {
+      q.om = a.yt[idx];
+      q.rh = a.rho[idx];
+    }
   }
   return q;
 }
@@ -941,10 +980,24 @@ __device__ __forceinline__ double mh_step_terms(const KP<Real>& p, const BackArg
     } else {
       vsi = 0;
     }
-    const Real fwd = vi * (ui - xi) + (Real)0.5 * p.r * vi * vi;
-    const Real rev = vsi * (ui - xo) + (Real)0.5 * p.r * vsi * vsi;
-    acc = (double)gdiff + (double)fwd - (double)rev;
-    a.yts[ct * p.d + lane] = ui + p.r * vsi;
+    if (p.order == 2) {
+      // log N(u; x*, r) - log N(u; x, r) + log N(omega*; x, Omega*) - log N(omega; x*, Omega)
+      const Real ls = second_order_hess(p, yi, lane, xi, t);
+      const Real rs = (Real)1 / ((Real)1 / p.r - ls);
+      const Real oms = rs * (ui / p.r + vsi - ls * xi);
+      const double du = (double)(ui - xo), dus = (double)(ui - xi);
+      const double d1 = (double)(oms - xo), d0 = (double)(in.om - xi);
+      acc = (double)gdiff + (du * du - dus * dus) / (2.0 * (double)p.r) +
+            0.5 * (log((double)in.rh) - log((double)rs)) - d1 * d1 / (2.0 * (double)rs) +
+            d0 * d0 / (2.0 * (double)in.rh);
+      a.yts[ct * p.d + lane] = oms;
+      a.rhos[ct * p.d + lane] = rs;
+    } else {
+      const Real fwd = vi * (ui - xi) + (Real)0.5 * p.r * vi * vi;
+      const Real rev = vsi * (ui - xo) + (Real)0.5 * p.r * vsi * vsi;
+      acc = (double)gdiff + (double)fwd - (double)rev;
+      a.yts[ct * p.d + lane] = ui + p.r * vsi;
+    }
   }
   return acc;
 }

@@ -39,6 +39,8 @@ KP<Real> make_kp(const aux_model* m) {
   p.m0 = (const Real*)m->m0; p.b = (const Real*)m->b; p.Ryinv = (const Real*)m->Ryinv;
   p.y = (const Real*)m->y; p.mask = m->mask;
   p.status_iter = m->status_iter;
+  p.order = m->order;
+  p.rho = nullptr;
   return p;
 }
 
@@ -244,23 +246,32 @@ struct Ops {
 
   static int kalman_step(aux_model* m, void* xv, int n_iters, uint64_t iter0, uint32_t* acc,
                          double* log_alpha, cudaStream_t st) {
-    if (m->mode != AUX_MODE_PER_CHAIN) return kalman_step_means(m, xv, n_iters, iter0, acc, log_alpha, st);
+    if (m->mode != AUX_MODE_PER_CHAIN) {
+      // the tables assume R = (delta/2) I; the second-order variances depend on the chain's state
+      if (m->order != 1) return AUX_E_UNSUPPORTED;
+      return kalman_step_means(m, xv, n_iters, iter0, acc, log_alpha, st);
+    }
     const KP<Real> p = make_kp<Real>(m);
+    const bool second = m->order == 2;
+    KP<Real> pf = p, pr = p;   // forward and reverse filters: the pseudo-observation variances
+    if (second) { pf.rho = (const Real*)m->rho; pr.rho = (const Real*)m->rhos; }
     Real* x = (Real*)xv;
     const long n = (long)m->C * m->T * m->d;
     const int lin_grid = (int)std::min<long>((n + 255) / 256, 152L * 16);
     for (int it = 0; it < n_iters; ++it) {
       const uint64_t iter = iter0 + (uint64_t)it;
       { ProfScope ps(m, PK_LINEARISE, st);
-      k_linearise<Real><<<lin_grid, 256, 0, st>>>(p, x, (Real*)m->u, (Real*)m->v, (Real*)m->yt, iter); }
-      filter(m, p, (const Real*)m->yt, apply_args(m, APPLY_EPI | APPLY_STORE_Q, iter), st);
+      k_linearise<Real><<<lin_grid, 256, 0, st>>>(p, x, (Real*)m->u, (Real*)m->v, (Real*)m->yt,
+                                                  (Real*)m->rho, iter); }
+      filter(m, pf, (const Real*)m->yt, apply_args(m, APPLY_EPI | APPLY_STORE_Q, iter), st);
       BackArgs<Real> b{};
       b.G = (const Real*)m->G; b.U = (const Real*)m->U; b.gum = (const Real*)m->gum;
       b.guv = (const Real*)m->guv; b.g_cs = (long)m->T * DP * DP; b.gm_cs = (long)m->nb * DP * DP;
       b.xs = (Real*)m->xs; b.mh = 1; b.x = x; b.u = (const Real*)m->u; b.v = (const Real*)m->v;
       b.yts = (Real*)m->yts; b.mh_part = m->mh_part;
+      b.yt = (const Real*)m->yt; b.rho = (const Real*)m->rho; b.rhos = (Real*)m->rhos;
       backward(m, p, b, st);
-      filter(m, p, (const Real*)m->yts, apply_args(m, APPLY_REV_DIFF, iter), st);
+      filter(m, pr, (const Real*)m->yts, apply_args(m, APPLY_REV_DIFF, iter), st);
       mh_commit(m, p, x, iter, acc, log_alpha, st);
     }
     return cuda_ok(cudaGetLastError());

@@ -132,14 +132,15 @@ def test_backward_noise_is_the_philox_stream(dt):
     s.close()
 
 
-def _step_and_compare(wl, dt, L, n_iters, chains=None, tol_x=None, tol_la=None, mode="per_chain"):
+def _step_and_compare(wl, dt, L, n_iters, chains=None, tol_x=None, tol_la=None, mode="per_chain",
+                      proposal=1):
     """Step all chains on the GPU; replay the chosen chains on the oracle from the same state.
 
     Each oracle step starts from the GPU's state before that step, so a rare
     near-tie decision difference in FP32 does not make the paths diverge."""
     C = wl.n_chains
     tdt = torch.float64 if dt == "f64" else torch.float32
-    s = AuxKalman(wl, dtype=dt, block_len=L, mode=mode)
+    s = AuxKalman(wl, dtype=dt, block_len=L, mode=mode, proposal=proposal)
     x = _tt(wl.x_init, tdt)
     la = torch.zeros(C, dtype=torch.float64, device="cuda")
     model = _oracle_model(wl)
@@ -152,7 +153,7 @@ def _step_and_compare(wl, dt, L, n_iters, chains=None, tol_x=None, tol_la=None, 
         xg = x.double().cpu().numpy()
         lag = la.cpu().numpy()
         for c in chains:
-            ref = mcmc.aux_step_philox(x_before[c], model, wl.delta, wl.mcmc_seed, c, it)
+            ref = mcmc.aux_step_philox(x_before[c], model, wl.delta, wl.mcmc_seed, c, it, order=proposal)
             lu = np.log(philox.mh_uniform(wl.mcmc_seed, c, it))
             dla = abs(lag[c] - ref["log_alpha"])
             max_dla = max(max_dla, dla)
@@ -169,7 +170,7 @@ def _step_and_compare(wl, dt, L, n_iters, chains=None, tol_x=None, tol_la=None, 
                 assert np.array_equal(xg[c], x_before[c]), (it, c)
     assert s.status()[0] == 0
     s.close()
-    return mismatches, max_dla
+    return mismatches, max_dla, lag
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -202,6 +203,48 @@ def test_kalman_step_parity_sv_f32_full_size_sampled_chains(mode):
     wl = workloads.stochastic_volatility(d=30, T=1024, n_chains=32)
     _step_and_compare(wl, "f32", L=0, n_iters=1, chains=[0, 9, 22, 31], tol_x=1e-4,
                       tol_la=TOL_LA32, mode=mode)
+
+
+# ---- second-order proposal (Section 2.2, Eqs. (2.8)-(2.9)), per-chain path
+
+def test_second_order_sv_f64():
+    wl = workloads.stochastic_volatility(d=6, T=45, n_chains=3, delta=0.05)
+    _step_and_compare(wl, "f64", L=8, n_iters=3, tol_x=1e-9, tol_la=1e-8, proposal=2)
+
+
+def test_second_order_sv_f32_small():
+    wl = workloads.stochastic_volatility(d=6, T=45, n_chains=4, delta=0.05)
+    _step_and_compare(wl, "f32", L=8, n_iters=3, tol_x=1e-4, tol_la=TOL_LA32, proposal=2)
+
+
+def test_second_order_masked_toy_f64():
+    wl = workloads.two_step_toy(rho=0.7, r2=0.3, n_chains=3)
+    _step_and_compare(wl, "f64", L=1, n_iters=4, tol_x=1e-9, tol_la=1e-8, proposal=2)
+
+
+def test_second_order_is_exact_on_the_linear_gaussian_model():
+    """With a Gaussian emission the second-order proposal is the exact conditional:
+    log alpha = 0 on the GPU as in the oracle, and every step is accepted."""
+    wl = workloads.linear_gaussian(d=2, T=64, n_chains=4)
+    _, max_dla, lag = _step_and_compare(wl, "f64", L=8, n_iters=3, tol_x=1e-9, tol_la=1e-8, proposal=2)
+    assert np.max(np.abs(lag)) < 1e-8
+
+
+def test_second_order_sv_f32_full_size_sampled_chains():
+    """d=30, T=1024, 32 chains; oracle on 3 chains."""
+    wl = workloads.stochastic_volatility(d=30, T=1024, n_chains=32)
+    _step_and_compare(wl, "f32", L=0, n_iters=1, chains=[0, 17, 31], tol_x=1e-4, tol_la=TOL_LA32,
+                      proposal=2)
+
+
+@pytest.mark.parametrize("mode", ["shared", "cached"])
+def test_second_order_is_rejected_in_table_modes(mode):
+    wl = workloads.stochastic_volatility(d=4, T=16, n_chains=2, delta=0.05)
+    s = AuxKalman(wl, dtype="f32", block_len=4, mode=mode, proposal=2)
+    x = _tt(wl.x_init, torch.float32)
+    with pytest.raises(RuntimeError, match="unsupported"):
+        s.step(x, n_iters=1, iter0=0)
+    s.close()
 
 
 def test_execution_modes_agree_at_full_size():
