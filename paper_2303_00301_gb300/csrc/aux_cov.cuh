@@ -266,6 +266,137 @@ __global__ void __launch_bounds__(32, 1)
 }
 
 // ---------------------------------------------------------------------------
+// The same round with one CTA of CW_SCAN warps per block (p >= 16): the ten
+// d x d products of the operator are split by output columns across the
+// warps, the two Cholesky factorisations and the triangular solve run on
+// warp 0. Same operator, same order of operations per output entry.
+// ---------------------------------------------------------------------------
+constexpr int CW_SCAN = 4;
+
+template <typename Real, int DP> struct CovScanMW {
+  static constexpr int MAT = Lay<Real, DP>::MAT, VEC = Lay<Real, DP>::VEC;
+  static constexpr int NC = DP / CW_SCAN;   // output columns per warp
+  // SA SC SJ SU S2 S3 S4 SN SAe SCe SJe + 2 vectors
+  static constexpr size_t SMEM = (11 * MAT + 2 * VEC) * sizeof(Real);
+};
+
+template <typename Real, int DP>
+__global__ void __launch_bounds__(32 * CW_SCAN)
+    k_cov_scan_level_mw(KP<Real> p, const Real* __restrict__ in_m, Real* __restrict__ out_m, int off,
+                        int32_t* __restrict__ status) {
+  using Z = CovScanMW<Real, DP>;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD, NC = Z::NC;
+  constexpr long DD = (long)DP * DP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, k = blockIdx.x;
+  const int nth = blockDim.x;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  const int c0 = warp * NC;
+  if (k < off) {
+    using V = typename Vec16<Real>::V;
+    constexpr int NV = 3 * (int)DD / Vec16<Real>::N;
+    const V* src = reinterpret_cast<const V*>(in_m + (long)k * 3 * DD);
+    V* dst = reinterpret_cast<V*>(out_m + (long)k * 3 * DD);
+    for (int q = threadIdx.x; q < NV; q += nth) dst[q] = src[q];
+    return;
+  }
+  Real* SA = sm;
+  Real* SC = SA + MAT;
+  Real* SJ = SC + MAT;
+  Real* SU = SJ + MAT;
+  Real* S2 = SU + MAT;
+  Real* S3 = S2 + MAT;
+  Real* S4 = S3 + MAT;
+  Real* SN = S4 + MAT;
+  Real* SAe = SN + MAT;
+  Real* SCe = SAe + MAT;
+  Real* SJe = SCe + MAT;
+  Real* vd1 = SJe + MAT;
+  Real* vd2 = vd1 + VEC;
+  // (A, C, J) of both operands straight into the padded slots (SA SC SJ and SAe SCe SJe
+  // are consecutive), all copies in flight at once
+  stage_mats<Real, DP>(SA, in_m + (long)(k - off) * 3 * DD, DD, 3);
+  stage_mats<Real, DP>(SAe, in_m + (long)k * 3 * DD, DD, 3);
+  cp_async_wait<0>();
+  __syncthreads();
+  int bad = 0;
+  auto put = [&](Real* S, const Real (&v)[NC]) {   // the warp's column slice of row `row`
+    if (act) stn<Real, NC>(S + row * LD + c0, v);
+  };
+  // U = chol(C_i): LS form in S2, rows in SU
+  if (warp == 0) {
+    Real a[DP];
+    ld_row<Real, DP>(SC, row, a);
+    chol_rot<Real, DP>(a, S2, SU, nullptr, vd1, nullptr, p.d, lane, &bad);
+  }
+  __syncthreads();
+  Real t1[NC];
+  mm_row_c<Real, DP, NC>(SJe + row * LD, SU, c0, t1);   // J_e U
+  put(S3, t1);
+  __syncthreads();
+  mm_col_c<Real, DP, NC>(SU, row, S3, c0, t1);          // N = I + U^T J_e U
+#pragma unroll
+  for (int j = 0; j < NC; ++j) t1[j] += (c0 + j == lane) ? (Real)1 : (Real)0;
+  put(SN, t1);
+  __syncthreads();
+  if (warp == 0) {   // L_N = chol(N) (LS form in S4); B = U L_N^{-T} (rows in S2)
+    Real a[DP];
+    ld_row<Real, DP>(SN, row, a);
+    chol_rot<Real, DP>(a, S4, nullptr, nullptr, vd2, nullptr, p.d, lane, &bad);
+    Real r[DP];
+    ld_row<Real, DP>(SU, row, r);
+    fsolve_rot<Real, DP, false>(S4, vd2, r, S2, lane);
+  }
+  __syncthreads();
+  mm_row_c<Real, DP, NC>(SAe + row * LD, S2, c0, t1);   // P = A_e B, stored transposed in S3
+  if (act) {
+#pragma unroll
+    for (int j = 0; j < NC; ++j) S3[(c0 + j) * LD + row] = t1[j];
+  }
+  mm_row_c<Real, DP, NC>(SJe + row * LD, SA, c0, t1);   // X1 = J_e A_i
+  put(S4, t1);
+  __syncthreads();
+  mm_col_c<Real, DP, NC>(S2, row, S4, c0, t1);          // Z = B^T X1
+  put(SU, t1);
+  __syncthreads();
+  Real jn[NC], an[NC], cn[NC];
+  ldn<Real, NC>(SJ + row * LD + c0, jn);                // J = J_i + A_i^T X1 - Z^T Z
+  mm_col_c<Real, DP, NC, true>(SA, row, S4, c0, jn);
+  mm_col_c<Real, DP, NC, true, true>(SU, row, SU, c0, jn);
+  mm_row_c<Real, DP, NC>(SAe + row * LD, SA, c0, an);   // A = A_e A_i - P Z
+  mm_col_c<Real, DP, NC, true, true>(S3, row, SU, c0, an);
+  ldn<Real, NC>(SCe + row * LD + c0, cn);               // C = C_e + P P^T
+  mm_col_c<Real, DP, NC, true>(S3, row, S3, c0, cn);
+  __syncthreads();
+  put(SA, an);
+  put(SC, cn);
+  put(SJ, jn);
+  __syncthreads();
+  {   // J symmetrised
+    Real jc[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) jc[j] = SJ[(c0 + j) * LD + row];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) jn[j] = (Real)0.5 * (jn[j] + jc[j]);
+  }
+  __syncthreads();
+  put(SJ, jn);
+  __syncthreads();
+  {   // SA SC SJ -> (A, C, J), 16-byte chunks
+    using V = typename Vec16<Real>::V;
+    constexpr int N = Vec16<Real>::N, CPR = DP / N, PER = DP * CPR;
+    V* g = reinterpret_cast<V*>(out_m + (long)k * 3 * DD);
+    for (int q = threadIdx.x; q < 3 * PER; q += nth) {
+      const int m = q / PER, rem = q - m * PER, r = rem / CPR, cc = rem - r * CPR;
+      g[q] = *reinterpret_cast<const V*>(SA + m * MAT + r * LD + cc * N);
+    }
+  }
+  if (bad && lane == 0 && warp == 0) atomicOr(status, ST_NOT_PD);
+}
+
+// ---------------------------------------------------------------------------
 // In-block covariance filter from the prefix P^f_{s-1}, with the per-step tables.
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>

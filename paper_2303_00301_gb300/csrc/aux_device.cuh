@@ -651,6 +651,47 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // ---------------------------------------------------------------------------
+// Column-sliced products for several warps sharing one d x d product: the
+// lane's row, output columns c0 .. c0 + NC - 1 (c0 a multiple of NC, NC * size
+// a multiple of 16 bytes).
+//   mm_row_c:  out[j] (+/-)= sum_k arow[k] B[k][c0 + j]     (arow: shared row)
+//   mm_col_c:  out[j] (+/-)= sum_k A[k][col] B[k][c0 + j]   (column col of slot A)
+// ---------------------------------------------------------------------------
+template <typename T, int DP, int NC, bool ACC = false, bool NEG = false>
+__device__ __forceinline__ void mm_row_c(const T* arow, const T* B, int c0, T (&out)[NC]) {
+  constexpr int LD = Lay<T, DP>::LD;
+  if (!ACC) {
+#pragma unroll
+    for (int j = 0; j < NC; ++j) out[j] = (T)0;
+  }
+#pragma unroll 4
+  for (int k = 0; k < DP; ++k) {
+    const T ak = NEG ? -arow[k] : arow[k];
+    T b[NC];
+    ldn<T, NC>(B + k * LD + c0, b);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) out[j] = fma(ak, b[j], out[j]);
+  }
+}
+
+template <typename T, int DP, int NC, bool ACC = false, bool NEG = false>
+__device__ __forceinline__ void mm_col_c(const T* A, int col, const T* B, int c0, T (&out)[NC]) {
+  constexpr int LD = Lay<T, DP>::LD;
+  if (!ACC) {
+#pragma unroll
+    for (int j = 0; j < NC; ++j) out[j] = (T)0;
+  }
+#pragma unroll 4
+  for (int k = 0; k < DP; ++k) {
+    const T ak = NEG ? -A[k * LD + col] : A[k * LD + col];
+    T b[NC];
+    ldn<T, NC>(B + k * LD + c0, b);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) out[j] = fma(ak, b[j], out[j]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Asynchronous global -> shared copies (16 bytes per instruction, L1 bypassed)
 // used to stage the next step's tables while the current step computes.
 // ---------------------------------------------------------------------------

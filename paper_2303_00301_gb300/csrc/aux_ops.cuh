@@ -70,6 +70,10 @@ struct Ops {
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_cov_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::APP_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
+    if constexpr (DP >= 16) {
+      e = cudaFuncSetAttribute(k_cov_scan_level_mw<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovScanMW<Real, DP>::SMEM);
+      if (e != cudaSuccess) return AUX_E_CUDA;
+    }
     e = cudaFuncSetAttribute(k_cov_gp_fix<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::FIX_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_mf_reduce<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::RED);
@@ -149,7 +153,11 @@ struct Ops {
     }
     for (int off = 1; off < m->nbc; off *= 2) {
       ProfScope ps(m, PK_COV_SCAN, st);
-      k_cov_scan_level<Real, DP><<<m->nbc, 32, CZ::SCAN_SMEM, st>>>(pc, b0, b1, off, m->cov_status);
+      if constexpr (DP >= 16)
+        k_cov_scan_level_mw<Real, DP><<<m->nbc, 32 * CW_SCAN, CovScanMW<Real, DP>::SMEM, st>>>(
+            pc, b0, b1, off, m->cov_status);
+      else
+        k_cov_scan_level<Real, DP><<<m->nbc, 32, CZ::SCAN_SMEM, st>>>(pc, b0, b1, off, m->cov_status);
       Real* tmp = b0; b0 = b1; b1 = tmp;
     }
     CovArgs<Real> a{};
