@@ -121,9 +121,9 @@ def cov_apply_flops_per_step(d, fdiag):
 
 
 def means_flops_per_step(kind, d, fdiag, epilogue=True):
-    """Per chain-timestep flops of the means kernels: triangular mat-vec d^2,
-    dense mat-vec 2 d^2. reduce/apply: W r and W^T w (+ F m); apply with the
-    epilogue also G m^p, chol(Sigma) eps (triangular) and the block prefix product."""
+    """Per chain-timestep flops of the means kernels: dense mat-vec 2 d^2,
+    triangular mat-vec d^2. reduce/apply: K' e (+ F m); apply with the epilogue
+    also G m^p, chol(Sigma) eps (triangular) and the block prefix product."""
     fm = 2.0 * d if fdiag else 2.0 * d ** 2
     if kind == "reduce":
         return 2.0 * d ** 2 + fm
@@ -151,11 +151,11 @@ def kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz):
         return None, None
     if kind == "reduce":   # forward (linearise: x, y in; u, v, ytilde out) and reverse (ytilde* in)
         return (C * T * means_flops_per_step("reduce", d, fdiag),
-                2 * tab + (5 * vec + vec) / 2)
-    if kind == "apply":    # forward (5 tables, ytilde in, U out) and reverse (2 tables, ytilde* in)
+                tab + (5 * vec + vec) / 2)
+    if kind == "apply":    # forward (4 tables, ytilde in, U out) and reverse (1 table, ytilde* in)
         return (C * T * (means_flops_per_step("apply", d, fdiag, True) +
                          means_flops_per_step("apply", d, fdiag, False)) / 2,
-                (5 * tab + 2 * vec + 2 * tab + vec) / 2)
+                (4 * tab + 2 * vec + tab + vec) / 2)
     if kind == "backward":  # G table, U in, x* out, MH inputs x, u, v, y in, ytilde* out
         return C * T * 2.0 * d ** 2, tab + 7 * vec
     if kind == "cov_reduce":

@@ -9,8 +9,7 @@
 // of the blocked scan once, with its own short block length Lc (one warp per
 // scan block: conditional-filter block reduction, Hillis-Steele rounds over
 // the block aggregates, in-block filter from the prefix), and writes, per step t,
-//   tab[TW][t]  = W_t = chol(S_t)^{-1},  S_t = P^p_t + R   (lower triangular)
-//   tab[TWT][t] = W_t^T
+//   tab[TK][t]  = K'_t = r S_t^{-1} = I - K_t,  S_t = P^p_t + R   (symmetric)
 //   tab[TG][t]  = G_t = P^f_t F^T (P^p_{t+1})^{-1}          (G_{T-1} = 0)
 //   tab[TLS][t] = chol(Sigma_t), Sigma_t = P^f_t - G_t P^p_{t+1} G_t^T
 //                 (chol(P^f_{T-1}) at t = T-1)
@@ -22,16 +21,17 @@
 //   btab[BAH][k] = (I - K_e) F ... (I - K_s) F,  K_t = P^p_t S_t^{-1}
 //                  (the linear part of m^f_e as a function of m^f_{s-1})
 //   btab[BGH][k] = G_s ... G_e,   ld[k] = sum over the block of ldt[t].
-// Because R = r I, I - K_t = r S_t^{-1} = r W_t^T W_t, so the filtering mean
-// update is m^f_t = ytilde_t - r W_t^T W_t (ytilde_t - m^p_t) and the
-// predictive likelihood term uses |W_t (ytilde_t - m^p_t)|^2 and log det S_t:
-// the per-chain work that remains (aux_means.cuh) is matrix-vector only.
+// Because R = r I, I - K_t = r S_t^{-1} = K'_t, so the filtering mean update
+// is m^f_t = ytilde_t - K'_t (ytilde_t - m^p_t) and the predictive likelihood
+// term uses (ytilde_t - m^p_t)^T S_t^{-1} (ytilde_t - m^p_t) = r^{-1} e^T K'_t e
+// and log det S_t: the per-chain work that remains (aux_means.cuh) is
+// matrix-vector only, one product per step for the filter.
 #pragma once
 #include "aux_kernels.cuh"
 
 namespace auxk {
 
-enum { TW = 0, TWT, TG, TLS, TGP, TPF, NTAB };
+enum { TK = 0, TG, TLS, TGP, TPF, NTAB };
 enum { BAH = 0, BGH, NBTAB };
 
 template <typename Real> struct CovArgs {
@@ -514,7 +514,8 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
     store_row(TG, t, SX);
     store_row(TLS, t, SLR);
   };
-  // W_t = L_S^{-1} (columns of the identity through the forward solve) and W_t^T
+  // K'_t = r S_t^{-1} = r W^T W with W = L_S^{-1} (columns of the identity through the
+  // forward solve); M_t = (I - K_t) F = K'_t F, then SAH <- M_t SAH
   auto gain_tables = [&](int t) {
     {
       Real r[DP];
@@ -523,29 +524,23 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
       fsolve_rot<Real, DP, true>(SG, vdB, r, SWm, lane);
     }
     __syncwarp();
-    store_row(TW, t, SWm);
-    if (act) {
-      Real c[DP];
-      ld_col<Real, DP>(SWm, row, c);
-      st_vec<Real, DP>(a.tab + ((long)TWT * p.nT + t) * DD + row * DP, c);
-    }
     double lg = (lane < p.d) ? -log((double)vdB[lane]) : 0.0;
     lg = warp_sum<double>(lg);
     if (lane == 0) a.ldt[t] = 2.0 * lg;
-    // M_t = (I - K_t) F = r W^T W F, then SAH <- M_t SAH
     Real mr[DP];
     mm_col<Real, DP>(SWm, row, SWm, mr);
+#pragma unroll
+    for (int j = 0; j < DP; ++j) mr[j] *= p.r;
+    if (act) st_vec<Real, DP>(a.tab + ((long)TK * p.nT + t) * DD + row * DP, mr);
     if (p.fdiag) {
       Real ph[DP];
       ld_vec<Real, DP>(sphi, ph);
 #pragma unroll
-      for (int j = 0; j < DP; ++j) mr[j] *= p.r * ph[j];
+      for (int j = 0; j < DP; ++j) mr[j] *= ph[j];
     } else {
       st_row<Real, DP>(SA1, row, mr, act);
       __syncwarp();
       mm_row<Real, DP>(SA1 + row * LD, sF, mr);
-#pragma unroll
-      for (int j = 0; j < DP; ++j) mr[j] *= p.r;
       __syncwarp();
     }
     st_row<Real, DP>(SA1, row, mr, act);

@@ -4,9 +4,9 @@
 // all chains.
 //
 // Filtering means (Kalman filter algorithm, Appendix A.1, with H = I, R = r I):
-//   m^p_0 = m0,  m^p_t = F m^f_{t-1} + b,
-//   w_t = W_t (ytilde_t - m^p_t),  m^f_t = ytilde_t - r W_t^T w_t,
-//   log-likelihood term  -(d/2) log 2 pi - (1/2) (log det S_t + |w_t|^2).
+//   m^p_0 = m0,  m^p_t = F m^f_{t-1} + b,  e_t = ytilde_t - m^p_t,
+//   m^f_t = ytilde_t - K'_t e_t  (K'_t = r S_t^{-1} = I - K_t),
+//   log-likelihood term  -(d/2) log 2 pi - (1/2) (log det S_t + e_t^T K'_t e_t / r).
 // The recursion is affine in m^f_{s-1} with linear part AH_k over a block, so
 // the blocked scan keeps the structure of the full filter (Appendix A.2.1):
 //   k_mf_reduce    each block from m^f_{s-1} = 0 (block 0 from m0): block-end z_k;
@@ -18,9 +18,10 @@
 //   k_mean_cross   (backward) per chain, x*_{s_k} = GH_k x*_{e_k + 1} + Ubar_k;
 //   k_mb_apply     x*_t = G_t x*_{t+1} + U_t inside each block (Proposition A.1),
 //                  with the MH terms at x* and ytilde*.
-// One CTA runs MEAN_WPC chains of the same block, one warp per chain (lane =
-// row), so the tables of step t are staged once per CTA in shared memory,
-// with asynchronous copies one step ahead.
+// One CTA runs MEAN_CHAINS chains of the same block (lane = row, MEAN_CPW
+// chains per warp), so the tables of step t are staged once per CTA in shared
+// memory, with asynchronous copies one step ahead, and each table row is read
+// from shared memory once per warp for all of its chains.
 #pragma once
 #include "aux_cov.cuh"
 
@@ -51,7 +52,8 @@ template <typename Real> struct MeanArgs {
   int32_t* status;            // optional sticky per-chain status
 };
 
-constexpr int MEAN_WPC = 8;   // chains (warps) per CTA
+constexpr int MEAN_CHAINS = 8;   // chains per CTA (all of the same scan block)
+constexpr int MEAN_CPW = 1;      // chains per warp in the reduce / apply kernels
 
 // Staging buffers: step t reads buffer t % NBUF while the copies of step t+1
 // fill the next one; the buffer refilled at step t was last read at step t-2,
@@ -63,9 +65,9 @@ template <typename Real, int DP> struct MeanSizes {
   static constexpr int MAT = Lay<Real, DP>::MAT, VEC = Lay<Real, DP>::VEC;
   // NBUF staging buffers of NT tables, R_y^{-1}, three vector slots per warp
   static constexpr size_t smem(int nt) {
-    return (size_t)(NBUF * nt * MAT + MAT + MEAN_WPC * 3 * VEC) * sizeof(Real);
+    return (size_t)(NBUF * nt * MAT + MAT + MEAN_CHAINS * 3 * VEC) * sizeof(Real);
   }
-  static constexpr size_t RED = smem(2), APP = smem(5), BWD = smem(1), CROSS = smem(1);
+  static constexpr size_t RED = smem(1), APP = smem(4), BWD = smem(1), CROSS = smem(1);
 };
 
 // lane value -> vector slot (all lanes of the warp call it)
@@ -106,35 +108,39 @@ __device__ __forceinline__ void load_ryinv(const KP<Real>& p, Real* sRy) {
 // ---------------------------------------------------------------------------
 // Block-local filtering means from a zero start (block 0: from m0), optionally
 // fused with the linearisation (A1) and the auxiliary draw (A2).
-// Grid: nb * ceil(C / MEAN_WPC) CTAs; CTA (g, k) runs chains g*MEAN_WPC + warp.
+// Grid: nb * ceil(C / MEAN_CHAINS) CTAs of MEAN_CHAINS / CPW warps; CTA (g, k)
+// runs chains g * MEAN_CHAINS + warp * CPW + j, j < CPW, of block k. A warp
+// loads each table row once per step and applies it to its CPW chains.
 // ---------------------------------------------------------------------------
-template <typename Real, int DP>
-__global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_reduce(KP<Real> p, MeanArgs<Real> a) {
+template <typename Real, int DP, int CPW>
+__global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_reduce(KP<Real> p, MeanArgs<Real> a) {
   using Z = MeanSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
   constexpr long DD = (long)DP * DP;
-  constexpr int NT = 2;   // W, W^T
+  constexpr int NT = 1;   // K'
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* buf = reinterpret_cast<Real*>(smem_raw);
   Real* sRy = buf + NBUF * NT * MAT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  Real* vr = sRy + MAT + warp * 3 * VEC;
-  Real* vw = vr + VEC;
-  Real* vq = vw + VEC;
-  const int k = blockIdx.x % p.nb, c = (blockIdx.x / p.nb) * MEAN_WPC + warp;
-  const bool valid = c < p.C;
+  Real* vbase = sRy + MAT + warp * 3 * CPW * VEC;   // per chain j: vr, vw, vq
+  const int k = blockIdx.x % p.nb, cbase = (blockIdx.x / p.nb) * MEAN_CHAINS + warp * CPW;
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
   const RowDyn<Real> rd = row_dyn<Real, DP>(p, row);
   const long tstride = (long)p.nT * DD;
   if (a.x && p.emis == AUX_EMIS_LINEAR_GAUSSIAN) load_ryinv<Real, DP>(p, sRy);
-  stage_mats<Real, DP>(buf, a.tab + (long)TW * tstride + s * DD, tstride, NT);
+  stage_mats<Real, DP>(buf, a.tab + (long)TK * tstride + s * DD, tstride, NT);
+  bool valid[CPW];
+  int cidx[CPW];
+#pragma unroll
+  for (int j = 0; j < CPW; ++j) { cidx[j] = cbase + j; valid[j] = cidx[j] < p.C; }
+  const bool any = valid[0];
   // the lane's inputs of step t, fetched one step ahead: x_t and y_t, or ytilde_t
-  auto fetch = [&](int t, Real& xv, Real& yv) {
+  auto fetch = [&](int t, int j, Real& xv, Real& yv) {
     xv = 0; yv = 0;
-    if (!valid || lane >= p.d) return;
-    const long ct = (long)c * p.nT + t;
+    if (!valid[j] || lane >= p.d) return;
+    const long ct = (long)cidx[j] * p.nT + t;
     if (a.x) {
       xv = a.x[ct * p.d + lane];
       yv = p.y[(p.y_per_chain ? ct : (long)t) * p.d + lane];
@@ -142,52 +148,68 @@ __global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_reduce(KP<Real> p, MeanArg
       yv = a.yt[ct * p.d + lane];
     }
   };
-  Real xn, yn;
-  fetch(s, xn, yn);
-  Real m = 0;
+  Real xn[CPW], yn[CPW], m[CPW];
+#pragma unroll
+  for (int j = 0; j < CPW; ++j) { fetch(s, j, xn[j], yn[j]); m[j] = 0; }
   for (int t = s; t <= e; ++t) {
     const int cur = (t - s) % NBUF, nxt = (t - s + 1) % NBUF;
-    const Real xi = xn, yv = yn;
-    if (t < e) fetch(t + 1, xn, yn);
-    if (t < e) stage_mats<Real, DP>(buf + nxt * NT * MAT, a.tab + (long)TW * tstride + (t + 1) * DD, tstride, NT);
+    Real xi[CPW], yv[CPW];
+#pragma unroll
+    for (int j = 0; j < CPW; ++j) {
+      xi[j] = xn[j]; yv[j] = yn[j];
+      if (t < e) fetch(t + 1, j, xn[j], yn[j]);
+    }
+    if (t < e) stage_mats<Real, DP>(buf + nxt * NT * MAT, a.tab + (long)TK * tstride + (t + 1) * DD, tstride, NT);
     else cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    if (valid) {
-      const Real* sW = buf + cur * NT * MAT;
-      const Real* sWT = sW + MAT;
-      const long ct = (long)c * p.nT + t;
-      Real yti = 0;
-      if (a.x) {
-        const bool obs = !p.mask || p.mask[t];
-        Real vi = 0;
-        if (p.emis == AUX_EMIS_LINEAR_GAUSSIAN) {
-          put_vec<Real, DP>(vq, (lane < p.d) ? yv - xi : (Real)0, lane);
-          vi = dot_row_vec<Real, DP>(sRy + row * LD, vq);
-        } else if (lane < p.d) {
-          vi = (Real)-0.5 + (Real)0.5 * yv * yv * exp(-xi);
+    if (any) {
+      const Real* sK = buf + cur * NT * MAT;
+      Real yti[CPW], mp[CPW];
+#pragma unroll
+      for (int j = 0; j < CPW; ++j) {
+        Real* vq = vbase + (3 * j + 2) * VEC;
+        const long ct = (long)cidx[j] * p.nT + t;
+        yti[j] = 0;
+        if (a.x) {
+          const bool obs = !p.mask || p.mask[t];
+          Real vi = 0;
+          if (p.emis == AUX_EMIS_LINEAR_GAUSSIAN) {
+            put_vec<Real, DP>(vq, (lane < p.d) ? yv[j] - xi[j] : (Real)0, lane);
+            vi = dot_row_vec<Real, DP>(sRy + row * LD, vq);
+          } else if (lane < p.d) {
+            vi = (Real)-0.5 + (Real)0.5 * yv[j] * yv[j] * exp(-xi[j]);
+          }
+          if (!obs) vi = 0;
+          if (lane < p.d && valid[j]) {
+            const Real ep = philox_normal<Real>(p.seed, (uint32_t)cidx[j], a.iter, PURPOSE_AUX, (uint32_t)t, lane);
+            const Real ui = xi[j] + p.sqrt_r * ep;
+            yti[j] = ui + p.r * vi;
+            a.u[ct * p.d + lane] = ui;
+            a.v[ct * p.d + lane] = vi;
+            a.yt[ct * p.d + lane] = yti[j];
+          }
+        } else {
+          yti[j] = yv[j];
         }
-        if (!obs) vi = 0;
-        if (lane < p.d) {
-          const Real ep = philox_normal<Real>(p.seed, (uint32_t)c, a.iter, PURPOSE_AUX, (uint32_t)t, lane);
-          const Real ui = xi + p.sqrt_r * ep;
-          yti = ui + p.r * vi;
-          a.u[ct * p.d + lane] = ui;
-          a.v[ct * p.d + lane] = vi;
-          a.yt[ct * p.d + lane] = yti;
-        }
-      } else {
-        yti = yv;
+        mp[j] = (t == 0) ? p.m0[row] : predict_mean<Real, DP>(p, rd, m[j], vq, lane, row);
       }
-      const Real mp = (t == 0) ? p.m0[row] : predict_mean<Real, DP>(p, rd, m, vq, lane, row);
-      put_vec<Real, DP>(vr, act ? yti - mp : (Real)0, lane);
-      const Real wi = dot_row_vec<Real, DP>(sW + row * LD, vr);
-      put_vec<Real, DP>(vw, wi, lane);
-      m = yti - p.r * dot_row_vec<Real, DP>(sWT + row * LD, vw);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < CPW; ++j)
+        if (act) vbase[3 * j * VEC + lane] = yti[j] - mp[j];
+      __syncwarp();
+      Real kr[DP];
+      ld_vec<Real, DP>(sK + row * LD, kr);
+#pragma unroll
+      for (int j = 0; j < CPW; ++j) m[j] = yti[j] - dot_rv<Real, DP>(kr, vbase + 3 * j * VEC);
     }
   }
-  if (valid && act) a.z[((long)c * p.nb + k) * DP + lane] = m;
-  if (valid && a.x && k == 0 && lane == 0) p.status_iter[c] = *a.cov_status;
+#pragma unroll
+  for (int j = 0; j < CPW; ++j) {
+    if (valid[j] && act) a.z[((long)cidx[j] * p.nb + k) * DP + lane] = m[j];
+    if (valid[j] && a.x && k == 0 && lane == 0) p.status_iter[cidx[j]] = *a.cov_status;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -196,10 +218,10 @@ __global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_reduce(KP<Real> p, MeanArg
 //            m^f_{e_0} = in[c][0] and m^f_{e_k} = AH_k m^f_{e_{k-1}} + in[c][k];
 //   backward (mats = GH): out[c][k] = x*_{e_k + 1}, k = nb-1 .. 0, from
 //            out[c][nb-1] = 0 and x*_{e_{k-1} + 1} = GH_k out[c][k] + in[c][k].
-// Grid: ceil(C / MEAN_WPC) CTAs.
+// Grid: ceil(C / MEAN_CHAINS) CTAs.
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
-__global__ void __launch_bounds__(32 * MEAN_WPC)
+__global__ void __launch_bounds__(32 * MEAN_CHAINS)
     k_mean_cross(KP<Real> p, const Real* __restrict__ mats, const Real* __restrict__ in,
                  Real* __restrict__ out, int backward) {
   using Z = MeanSizes<Real, DP>;
@@ -209,7 +231,7 @@ __global__ void __launch_bounds__(32 * MEAN_WPC)
   Real* buf = reinterpret_cast<Real*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Real* vq = buf + (NBUF + 1) * MAT + warp * 3 * VEC;
-  const int c = blockIdx.x * MEAN_WPC + warp;
+  const int c = blockIdx.x * MEAN_CHAINS + warp;
   const bool valid = c < p.C;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
@@ -247,109 +269,156 @@ __global__ void __launch_bounds__(32 * MEAN_WPC)
 
 // ---------------------------------------------------------------------------
 // Filtering means from the true block start, likelihood terms and
-// (APPLY_EPI) the backward elements with the block aggregate.
+// (APPLY_EPI) the backward elements with the block aggregate. Same grid and
+// chain layout as k_mf_reduce.
 // ---------------------------------------------------------------------------
-template <typename Real, int DP>
-__global__ void __launch_bounds__(32 * MEAN_WPC) k_mf_apply(KP<Real> p, MeanArgs<Real> a) {
+template <typename Real, int DP, int CPW>
+__global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_apply(KP<Real> p, MeanArgs<Real> a) {
   using Z = MeanSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
   constexpr long DD = (long)DP * DP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const bool epi = a.flags & APPLY_EPI;
-  const int NT = epi ? 5 : 2;   // W, W^T (, G, chol(Sigma), G_s .. G_{t-1})
+  const int NT = epi ? 4 : 1;   // K' (, G, chol(Sigma), G_s .. G_{t-1})
   Real* buf = reinterpret_cast<Real*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  Real* vr = buf + NBUF * 5 * MAT + MAT + warp * 3 * VEC;
-  Real* vw = vr + VEC;
-  Real* vq = vw + VEC;
-  const int k = blockIdx.x % p.nb, c = (blockIdx.x / p.nb) * MEAN_WPC + warp;
-  const bool valid = c < p.C;
+  Real* vbase = buf + NBUF * 4 * MAT + MAT + warp * 3 * CPW * VEC;   // per chain j: vr, vw, vq
+  const int k = blockIdx.x % p.nb, cbase = (blockIdx.x / p.nb) * MEAN_CHAINS + warp * CPW;
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
   const RowDyn<Real> rd = row_dyn<Real, DP>(p, row);
   const long tstride = (long)p.nT * DD;
   const Real* PF = a.tab + (long)TPF * tstride;
-  stage_mats<Real, DP>(buf, a.tab + (long)TW * tstride + s * DD, tstride, NT);
-  Real mp = 0;
-  if (valid) {
-    if (k == 0) mp = p.m0[row];
-    else mp = predict_mean<Real, DP>(p, rd, a.mstart[((long)c * p.nb + k) * DP + row], vq, lane, row);
+  stage_mats<Real, DP>(buf, a.tab + (long)TK * tstride + s * DD, tstride, NT);
+  bool valid[CPW];
+  int cidx[CPW];
+#pragma unroll
+  for (int j = 0; j < CPW; ++j) { cidx[j] = cbase + j; valid[j] = cidx[j] < p.C; }
+  const bool any = valid[0];
+  Real mp[CPW], ubar[CPW];
+  double qacc[CPW];
+#pragma unroll
+  for (int j = 0; j < CPW; ++j) {
+    ubar[j] = 0; qacc[j] = 0.0; mp[j] = 0;
+    if (valid[j]) {
+      if (k == 0) mp[j] = p.m0[row];
+      else mp[j] = predict_mean<Real, DP>(p, rd, a.mstart[((long)cidx[j] * p.nb + k) * DP + row],
+                                          vbase + (3 * j + 2) * VEC, lane, row);
+    }
   }
-  double qacc = 0.0;
-  Real ubar = 0;
   // the lane's ytilde_t and (given) eps_t, fetched one step ahead
-  auto fetch = [&](int t, Real& yv, Real& ev) {
+  auto fetch = [&](int t, int j, Real& yv, Real& ev) {
     yv = 0; ev = 0;
-    if (!valid || lane >= p.d) return;
-    const long ct = (long)c * p.nT + t;
+    if (!valid[j] || lane >= p.d) return;
+    const long ct = (long)cidx[j] * p.nT + t;
     yv = a.yt[ct * p.d + lane];
     if (epi && a.eps) ev = a.eps[ct * p.d + lane];
   };
-  Real yn, en;
-  fetch(s, yn, en);
+  Real yn[CPW], en[CPW];
+#pragma unroll
+  for (int j = 0; j < CPW; ++j) fetch(s, j, yn[j], en[j]);
   for (int t = s; t <= e; ++t) {
     const int cur = (t - s) % NBUF, nxt = (t - s + 1) % NBUF;
-    const Real yti = yn, eg = en;
-    if (t < e) fetch(t + 1, yn, en);
-    if (t < e) stage_mats<Real, DP>(buf + nxt * 5 * MAT, a.tab + (long)TW * tstride + (t + 1) * DD, tstride, NT);
+    Real yti[CPW], eg[CPW];
+#pragma unroll
+    for (int j = 0; j < CPW; ++j) {
+      yti[j] = yn[j]; eg[j] = en[j];
+      if (t < e) fetch(t + 1, j, yn[j], en[j]);
+    }
+    if (t < e) stage_mats<Real, DP>(buf + nxt * 4 * MAT, a.tab + (long)TK * tstride + (t + 1) * DD, tstride, NT);
     else cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    if (valid) {
-      const Real* sW = buf + cur * 5 * MAT;
-      const Real* sWT = sW + MAT;
-      const long ct = (long)c * p.nT + t;
-      put_vec<Real, DP>(vr, act ? yti - mp : (Real)0, lane);
-      const Real wi = dot_row_vec<Real, DP>(sW + row * LD, vr);
-      if (act) qacc += (double)wi * (double)wi;
-      put_vec<Real, DP>(vw, wi, lane);
-      const Real m = yti - p.r * dot_row_vec<Real, DP>(sWT + row * LD, vw);
-      if (a.mf && lane < p.d) a.mf[ct * p.d + lane] = m;
-      if (a.Pf && lane < p.d)
-        for (int j = 0; j < p.d; ++j) a.Pf[(ct * p.d + lane) * p.d + j] = PF[t * DD + lane * DP + j];
-      const Real mpn = (t < p.nT - 1) ? predict_mean<Real, DP>(p, rd, m, vq, lane, row) : (Real)0;
+    if (any) {
+      const Real* sK = buf + cur * 4 * MAT;
+      Real ej[CPW];
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < CPW; ++j) {
+        ej[j] = act ? yti[j] - mp[j] : (Real)0;
+        if (act) vbase[3 * j * VEC + lane] = ej[j];
+      }
+      __syncwarp();
+      Real kr[DP];
+      ld_vec<Real, DP>(sK + row * LD, kr);
+      Real m[CPW], mpn[CPW];
+#pragma unroll
+      for (int j = 0; j < CPW; ++j) {
+        const Real kv = dot_rv<Real, DP>(kr, vbase + 3 * j * VEC);
+        qacc[j] += (double)ej[j] * (double)kv;   // e^T K' e, summed over the lanes at the end
+        m[j] = yti[j] - kv;
+        const long ct = (long)cidx[j] * p.nT + t;
+        if (valid[j] && a.mf && lane < p.d) a.mf[ct * p.d + lane] = m[j];
+        if (valid[j] && a.Pf && lane < p.d)
+          for (int jj = 0; jj < p.d; ++jj) a.Pf[(ct * p.d + lane) * p.d + jj] = PF[t * DD + lane * DP + jj];
+        mpn[j] = (t < p.nT - 1) ? predict_mean<Real, DP>(p, rd, m[j], vbase + (3 * j + 2) * VEC, lane, row)
+                                : (Real)0;
+      }
       if (epi) {
-        const Real* sG = sWT + MAT;
+        const Real* sG = sK + MAT;
         const Real* sLS = sG + MAT;
         const Real* sGP = sLS + MAT;
-        Real ei = 0;
-        if (lane < p.d)
-          ei = a.eps ? eg
-                     : philox_normal<Real>(p.seed, (uint32_t)c, a.iter, PURPOSE_BACKWARD, (uint32_t)t, lane);
+        Real ei[CPW];
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) {
+          ei[j] = 0;
+          if (lane < p.d && valid[j])
+            ei[j] = a.eps ? eg[j]
+                          : philox_normal<Real>(p.seed, (uint32_t)cidx[j], a.iter, PURPOSE_BACKWARD, (uint32_t)t, lane);
+        }
         __syncwarp();
-        if (act) { vr[lane] = mpn; vw[lane] = ei; }
+#pragma unroll
+        for (int j = 0; j < CPW; ++j)
+          if (act) { vbase[3 * j * VEC + lane] = mpn[j]; vbase[(3 * j + 1) * VEC + lane] = ei[j]; }
         __syncwarp();
-        const Real ui = m - dot_row_vec<Real, DP>(sG + row * LD, vr) +
-                        dot_row_vec<Real, DP>(sLS + row * LD, vw);
-        if (act) a.U[ct * DP + lane] = ui;
-        put_vec<Real, DP>(vq, ui, lane);
-        ubar += dot_row_vec<Real, DP>(sGP + row * LD, vq);
+        Real gr[DP], lr[DP];
+        ld_vec<Real, DP>(sG + row * LD, gr);
+        ld_vec<Real, DP>(sLS + row * LD, lr);
+        Real ui[CPW];
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) {
+          ui[j] = m[j] - dot_rv<Real, DP>(gr, vbase + 3 * j * VEC) + dot_rv<Real, DP>(lr, vbase + (3 * j + 1) * VEC);
+          if (valid[j] && act) a.U[((long)cidx[j] * p.nT + t) * DP + lane] = ui[j];
+        }
+#pragma unroll
+        for (int j = 0; j < CPW; ++j)
+          if (act) vbase[(3 * j + 2) * VEC + lane] = ui[j];
+        __syncwarp();
+        ld_vec<Real, DP>(sGP + row * LD, gr);
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) ubar[j] += dot_rv<Real, DP>(gr, vbase + (3 * j + 2) * VEC);
       }
-      mp = mpn;
+#pragma unroll
+      for (int j = 0; j < CPW; ++j) mp[j] = mpn[j];
     }
   }
-  if (!valid) return;
-  const double q = warp_sum<double>(qacc);
-  if (lane == 0) {
-    const long ck = (long)c * p.nb + k;
-    if (a.flags & APPLY_STORE_Q) a.fqb[ck] = q;
-    if (a.flags & APPLY_REV_DIFF) a.lz_part[ck] = -0.5 * (a.fqb[ck] - q);
-    if (a.flags & APPLY_LOGZ) {
-      const double half_dlog2pi = 0.5 * p.d * 1.8378770664093454835606594728112;
-      a.lz_part[ck] = -((double)(e - s + 1) * half_dlog2pi + 0.5 * (a.ld[k] + q));
+#pragma unroll
+  for (int j = 0; j < CPW; ++j) {
+    if (!valid[j]) continue;
+    const double q = warp_sum<double>(qacc[j]) / (double)p.r;
+    const int c = cidx[j];
+    if (lane == 0) {
+      const long ck = (long)c * p.nb + k;
+      if (a.flags & APPLY_STORE_Q) a.fqb[ck] = q;
+      if (a.flags & APPLY_REV_DIFF) a.lz_part[ck] = -0.5 * (a.fqb[ck] - q);
+      if (a.flags & APPLY_LOGZ) {
+        const double half_dlog2pi = 0.5 * p.d * 1.8378770664093454835606594728112;
+        a.lz_part[ck] = -((double)(e - s + 1) * half_dlog2pi + 0.5 * (a.ld[k] + q));
+      }
+      if (a.status && k == 0 && *a.cov_status) atomicOr(&a.status[c], *a.cov_status);
     }
-    if (a.status && k == 0 && *a.cov_status) atomicOr(&a.status[c], *a.cov_status);
+    if (epi && act) a.guv[((long)c * p.nb + k) * DP + lane] = ubar[j];
   }
-  if (epi && act) a.guv[((long)c * p.nb + k) * DP + lane] = ubar;
 }
 
 // ---------------------------------------------------------------------------
 // Backward sampling inside each block from x*_{e+1} (k_mean_cross, backward):
 // x*_t = G_t x*_{t+1} + U_t (G_{T-1} = 0), with the MH terms when b.mh.
+// Same grid and chain layout as k_mf_reduce.
 // ---------------------------------------------------------------------------
-template <typename Real, int DP>
-__global__ void __launch_bounds__(32 * MEAN_WPC)
+template <typename Real, int DP, int CPW>
+__global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW)
     k_mb_apply(KP<Real> p, BackArgs<Real> b, const Real* __restrict__ xnext) {
   using Z = MeanSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
@@ -358,45 +427,70 @@ __global__ void __launch_bounds__(32 * MEAN_WPC)
   Real* buf = reinterpret_cast<Real*>(smem_raw);
   Real* sRy = buf + NBUF * MAT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  Real* vx = sRy + MAT + warp * 3 * VEC;
-  Real* vxs = vx + VEC;
-  const int k = blockIdx.x % p.nb, c = (blockIdx.x / p.nb) * MEAN_WPC + warp;
-  const bool valid = c < p.C;
+  Real* vbase = sRy + MAT + warp * 3 * CPW * VEC;   // per chain j: vx, vxs
+  const int k = blockIdx.x % p.nb, cbase = (blockIdx.x / p.nb) * MEAN_CHAINS + warp * CPW;
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
   if (b.mh && p.emis == AUX_EMIS_LINEAR_GAUSSIAN) load_ryinv<Real, DP>(p, sRy);
   stage_mats<Real, DP>(buf, b.G + e * DD, DD, 1);
-  Real xi = valid ? xnext[((long)c * p.nb + k) * DP + row] : (Real)0;
-  double acc = 0.0;
-  // the lane's U_t and MH inputs, fetched one step ahead
-  const long cb = (long)(valid ? c : 0) * p.nT;
-  Real un = b.U[(cb + e) * DP + row];
-  MhIn<Real> qn = b.mh ? mh_load<Real>(p, b, cb + e, e, lane) : MhIn<Real>{};
+  bool valid[CPW];
+  long cb[CPW];
+  Real xi[CPW], un[CPW];
+  MhIn<Real> qn[CPW];
+  double acc[CPW];
+#pragma unroll
+  for (int j = 0; j < CPW; ++j) {
+    const int c = cbase + j;
+    valid[j] = c < p.C;
+    cb[j] = (long)(valid[j] ? c : 0) * p.nT;
+    xi[j] = valid[j] ? xnext[((long)c * p.nb + k) * DP + row] : (Real)0;
+    acc[j] = 0.0;
+    // the lane's U_t and MH inputs, fetched one step ahead
+    un[j] = b.U[(cb[j] + e) * DP + row];
+    qn[j] = b.mh ? mh_load<Real>(p, b, cb[j] + e, e, lane) : MhIn<Real>{};
+  }
+  const bool any = valid[0];
   for (int t = e; t >= s; --t) {
     const int cur = (e - t) % NBUF, nxt = (e - t + 1) % NBUF;
-    const Real uc = un;
-    const MhIn<Real> qc = qn;
-    if (t > s) {
-      un = b.U[(cb + t - 1) * DP + row];
-      if (b.mh) qn = mh_load<Real>(p, b, cb + t - 1, t - 1, lane);
-      stage_mats<Real, DP>(buf + nxt * MAT, b.G + (t - 1) * DD, DD, 1);
-    } else {
-      cp_async_commit();
+    Real uc[CPW];
+    MhIn<Real> qc[CPW];
+#pragma unroll
+    for (int j = 0; j < CPW; ++j) {
+      uc[j] = un[j]; qc[j] = qn[j];
+      if (t > s) {
+        un[j] = b.U[(cb[j] + t - 1) * DP + row];
+        if (b.mh) qn[j] = mh_load<Real>(p, b, cb[j] + t - 1, t - 1, lane);
+      }
     }
+    if (t > s) stage_mats<Real, DP>(buf + nxt * MAT, b.G + (t - 1) * DD, DD, 1);
+    else cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    if (valid) {
-      const long ct = cb + t;
-      put_vec<Real, DP>(vx, xi, lane);
-      xi = dot_row_vec<Real, DP>(buf + cur * MAT + row * LD, vx) + uc;
-      if (lane < p.d) b.xs[ct * p.d + lane] = xi;
-      if (b.mh) acc += mh_step_terms<Real, DP>(p, b, ct, t, xi, qc, sRy, vxs, lane, row);
+    if (any) {
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < CPW; ++j)
+        if (act) vbase[3 * j * VEC + lane] = xi[j];
+      __syncwarp();
+      Real gr[DP];
+      ld_vec<Real, DP>(buf + cur * MAT + row * LD, gr);
+#pragma unroll
+      for (int j = 0; j < CPW; ++j) {
+        xi[j] = dot_rv<Real, DP>(gr, vbase + 3 * j * VEC) + uc[j];
+        const long ct = cb[j] + t;
+        if (valid[j] && lane < p.d) b.xs[ct * p.d + lane] = xi[j];
+        if (b.mh && valid[j])
+          acc[j] += mh_step_terms<Real, DP>(p, b, ct, t, xi[j], qc[j], sRy, vbase + (3 * j + 1) * VEC, lane, row);
+      }
     }
   }
-  if (valid && b.mh) {
-    acc = warp_sum<double>(acc);
-    if (lane == 0) b.mh_part[(long)c * p.nb + k] = acc;
+#pragma unroll
+  for (int j = 0; j < CPW; ++j) {
+    if (valid[j] && b.mh) {
+      const double r = warp_sum<double>(acc[j]);
+      if (lane == 0) b.mh_part[(long)(cbase + j) * p.nb + k] = r;
+    }
   }
 }
 

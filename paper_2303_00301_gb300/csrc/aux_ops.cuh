@@ -76,11 +76,11 @@ struct Ops {
     }
     e = cudaFuncSetAttribute(k_cov_gp_fix<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::FIX_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
-    e = cudaFuncSetAttribute(k_mf_reduce<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::RED);
+    e = cudaFuncSetAttribute(k_mf_reduce<Real, DP, MEAN_CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::RED);
     if (e != cudaSuccess) return AUX_E_CUDA;
-    e = cudaFuncSetAttribute(k_mf_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::APP);
+    e = cudaFuncSetAttribute(k_mf_apply<Real, DP, MEAN_CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::APP);
     if (e != cudaSuccess) return AUX_E_CUDA;
-    e = cudaFuncSetAttribute(k_mb_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::BWD);
+    e = cudaFuncSetAttribute(k_mb_apply<Real, DP, MEAN_CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::BWD);
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_mean_cross<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::CROSS);
     return cuda_ok(e);
@@ -194,20 +194,21 @@ struct Ops {
   }
 
   using MZ = MeanSizes<Real, DP>;
-  static int mean_grid(const aux_model* m) { return m->nb * ((m->C + MEAN_WPC - 1) / MEAN_WPC); }
+  static int mean_grid(const aux_model* m) { return m->nb * ((m->C + MEAN_CHAINS - 1) / MEAN_CHAINS); }
+  static constexpr int MEAN_THREADS = 32 * MEAN_CHAINS / MEAN_CPW;
 
   // block-local pass, composition over the blocks, in-block pass from the true starts
   static void means_filter(aux_model* m, const KP<Real>& p, MeanArgs<Real> a, cudaStream_t st) {
     const int grid = mean_grid(m);
     { ProfScope ps(m, PK_REDUCE, st);
-      k_mf_reduce<Real, DP><<<grid, 32 * MEAN_WPC, MZ::RED, st>>>(p, a); }
+      k_mf_reduce<Real, DP, MEAN_CPW><<<grid, MEAN_THREADS, MZ::RED, st>>>(p, a); }
     a.x = nullptr;
     { ProfScope ps(m, PK_SCAN, st);
-      k_mean_cross<Real, DP><<<(m->C + MEAN_WPC - 1) / MEAN_WPC, 32 * MEAN_WPC, MZ::CROSS, st>>>(
+      k_mean_cross<Real, DP><<<(m->C + MEAN_CHAINS - 1) / MEAN_CHAINS, 32 * MEAN_CHAINS, MZ::CROSS, st>>>(
           p, (const Real*)m->btab + (long)BAH * m->nb * DD, a.z, (Real*)m->ms, 0); }
     a.mstart = (const Real*)m->ms;
     { ProfScope ps(m, PK_APPLY, st);
-      k_mf_apply<Real, DP><<<grid, 32 * MEAN_WPC, MZ::APP, st>>>(p, a); }
+      k_mf_apply<Real, DP, MEAN_CPW><<<grid, MEAN_THREADS, MZ::APP, st>>>(p, a); }
   }
 
   static BackArgs<Real> back_args_tab(aux_model* m) {
@@ -224,9 +225,9 @@ struct Ops {
   static void backward_tab(aux_model* m, const KP<Real>& p, BackArgs<Real> b, cudaStream_t st) {
     ProfScope ps(m, PK_BACKWARD, st);
     Real* xnext = (Real*)m->zb;
-    k_mean_cross<Real, DP><<<(m->C + MEAN_WPC - 1) / MEAN_WPC, 32 * MEAN_WPC, MZ::CROSS, st>>>(
+    k_mean_cross<Real, DP><<<(m->C + MEAN_CHAINS - 1) / MEAN_CHAINS, 32 * MEAN_CHAINS, MZ::CROSS, st>>>(
         p, b.gum, b.guv, xnext, 1);
-    k_mb_apply<Real, DP><<<mean_grid(m), 32 * MEAN_WPC, MZ::BWD, st>>>(p, b, xnext);
+    k_mb_apply<Real, DP, MEAN_CPW><<<mean_grid(m), MEAN_THREADS, MZ::BWD, st>>>(p, b, xnext);
   }
 
   static int kalman_step_means(aux_model* m, void* xv, int n_iters, uint64_t iter0, uint32_t* acc,
