@@ -140,6 +140,37 @@ __device__ __forceinline__ void zero(T (&r)[DP]) {
   for (int k = 0; k < DP; ++k) r[k] = (T)0;
 }
 
+// ---------------------------------------------------------------------------
+// Fused multiply-adds over a register row, out[j] = fma(s, b[j], out[j]).
+// In single precision adjacent pairs go through one packed instruction
+// (fma.rn.f32x2: two independent fused multiply-adds, each rounded once, so
+// every element's value and order of accumulation are those of fmaf).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fma_pair(float& c0, float& c1, float a0, float a1, float b0, float b1) {
+  unsigned long long ra, rb, rc;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a0), "f"(a1));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b0), "f"(b1));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rc) : "f"(c0), "f"(c1));
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(rc) : "l"(ra), "l"(rb));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(c0), "=f"(c1) : "l"(rc));
+}
+__device__ __forceinline__ void fma_pair(double& c0, double& c1, double a0, double a1, double b0,
+                                         double b1) {
+  c0 = fma(a0, b0, c0);
+  c1 = fma(a1, b1, c1);
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void fma_row(T s, const T (&b)[N], T (&out)[N]) {
+  if constexpr (N % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < N; j += 2) fma_pair(out[j], out[j + 1], s, s, b[j], b[j + 1]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j) out[j] = fma(s, b[j], out[j]);
+  }
+}
+
 // out[j] (+)= sum_k a[k] * B[k][j]         (a: register row, B: slot, broadcast rows)
 template <typename T, int DP, bool ACC = false, bool NEG = false>
 __device__ __forceinline__ void row_mat(const T (&a)[DP], const T* B, T (&out)[DP]) {
@@ -150,8 +181,7 @@ __device__ __forceinline__ void row_mat(const T (&a)[DP], const T* B, T (&out)[D
     const T ak = NEG ? -a[k] : a[k];
     T b[DP];
     ld_row<T, DP>(B, k, b);
-#pragma unroll
-    for (int j = 0; j < DP; ++j) out[j] = fma(ak, b[j], out[j]);
+    fma_row<T, DP>(ak, b, out);
   }
   (void)N;
 }
@@ -181,8 +211,8 @@ __device__ __forceinline__ T dot_rv(const T (&a)[DP], const T* v) {
   T acc0 = 0, acc1 = 0;
 #pragma unroll
   for (int k = 0; k < DP; k += 2) {
-    acc0 = fma(a[k], b[k], acc0);
-    if (k + 1 < DP) acc1 = fma(a[k + 1], b[k + 1], acc1);
+    if (k + 1 < DP) fma_pair(acc0, acc1, a[k], a[k + 1], b[k], b[k + 1]);
+    else acc0 = fma(a[k], b[k], acc0);
   }
   return acc0 + acc1;
 }
@@ -192,8 +222,8 @@ __device__ __forceinline__ T dot_rr(const T (&a)[DP], const T (&b)[DP]) {
   T acc0 = 0, acc1 = 0;
 #pragma unroll
   for (int k = 0; k < DP; k += 2) {
-    acc0 = fma(a[k], b[k], acc0);
-    if (k + 1 < DP) acc1 = fma(a[k + 1], b[k + 1], acc1);
+    if (k + 1 < DP) fma_pair(acc0, acc1, a[k], a[k + 1], b[k], b[k + 1]);
+    else acc0 = fma(a[k], b[k], acc0);
   }
   return acc0 + acc1;
 }
@@ -290,8 +320,7 @@ __device__ __forceinline__ void mm_row(const T* arow, const T* B, T (&out)[DP]) 
       const T ak = NEG ? -a[kk] : a[kk];
       T b[DP];
       ld_vec<T, DP>(B + (k0 + kk) * LD, b);
-#pragma unroll
-      for (int j = 0; j < DP; ++j) out[j] = fma(ak, b[j], out[j]);
+      fma_row<T, DP>(ak, b, out);
     }
   }
 }
@@ -309,8 +338,7 @@ __device__ __forceinline__ void mm_col(const T* A, int col, const T* B, T (&out)
       const T ak = NEG ? -a : a;
       T b[DP];
       ld_vec<T, DP>(B + (k0 + kk) * LD, b);
-#pragma unroll
-      for (int j = 0; j < DP; ++j) out[j] = fma(ak, b[j], out[j]);
+      fma_row<T, DP>(ak, b, out);
     }
   }
 }
@@ -607,8 +635,7 @@ __device__ __forceinline__ void mm_tile_regs(const T* A, const T* B, T (&acc)[Ti
 #pragma unroll
       for (int i = 0; i < TR; ++i) {
         const T ai = NEG ? -a[kk][i] : a[kk][i];
-#pragma unroll
-        for (int j = 0; j < TC; ++j) acc[i][j] = fma(ai, b[j], acc[i][j]);
+        fma_row<T, TC>(ai, b, acc[i]);
       }
     }
   }
@@ -669,8 +696,7 @@ __device__ __forceinline__ void mm_row_c(const T* arow, const T* B, int c0, T (&
     const T ak = NEG ? -arow[k] : arow[k];
     T b[NC];
     ldn<T, NC>(B + k * LD + c0, b);
-#pragma unroll
-    for (int j = 0; j < NC; ++j) out[j] = fma(ak, b[j], out[j]);
+    fma_row<T, NC>(ak, b, out);
   }
 }
 
@@ -686,8 +712,7 @@ __device__ __forceinline__ void mm_col_c(const T* A, int col, const T* B, int c0
     const T ak = NEG ? -A[k * LD + col] : A[k * LD + col];
     T b[NC];
     ldn<T, NC>(B + k * LD + c0, b);
-#pragma unroll
-    for (int j = 0; j < NC; ++j) out[j] = fma(ak, b[j], out[j]);
+    fma_row<T, NC>(ak, b, out);
   }
 }
 

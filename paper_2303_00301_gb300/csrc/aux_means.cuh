@@ -55,11 +55,13 @@ template <typename Real> struct MeanArgs {
 constexpr int MEAN_CHAINS = 8;   // chains per CTA (all of the same scan block)
 constexpr int MEAN_CPW = 1;      // chains per warp in the reduce / apply kernels
 
-// Staging buffers: step t reads buffer t % NBUF while the copies of step t+1
-// fill the next one; the buffer refilled at step t was last read at step t-2,
-// which every warp has finished once it passed the barrier of step t-1, so
-// one barrier per step suffices.
-constexpr int NBUF = 3;
+// Staging buffers: the tables of step t + PREF are copied while step t
+// computes (PREF steps of latency cover an L2 or, right after an L2 flush, an
+// HBM read); step t reads buffer t % NBUF and the buffer refilled at step t
+// was last read at step t - 2, which every warp has finished once it passed
+// the barrier of step t - 1, so one barrier per step suffices.
+constexpr int PREF = 2;
+constexpr int NBUF = PREF + 2;
 
 template <typename Real, int DP> struct MeanSizes {
   static constexpr int MAT = Lay<Real, DP>::MAT, VEC = Lay<Real, DP>::VEC;
@@ -130,13 +132,17 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_reduce(KP<Real> p
   const RowDyn<Real> rd = row_dyn<Real, DP>(p, row);
   const long tstride = (long)p.nT * DD;
   if (a.x && p.emis == AUX_EMIS_LINEAR_GAUSSIAN) load_ryinv<Real, DP>(p, sRy);
-  stage_mats<Real, DP>(buf, a.tab + (long)TK * tstride + s * DD, tstride, NT);
+  auto stage = [&](int t) {   // the tables of step t, or an empty copy group past the block
+    if (t <= e) stage_mats<Real, DP>(buf + ((t - s) % NBUF) * NT * MAT, a.tab + (long)TK * tstride + t * DD, tstride, NT);
+    else cp_async_commit();
+  };
+  for (int q = 0; q < PREF; ++q) stage(s + q);
   bool valid[CPW];
   int cidx[CPW];
 #pragma unroll
   for (int j = 0; j < CPW; ++j) { cidx[j] = cbase + j; valid[j] = cidx[j] < p.C; }
   const bool any = valid[0];
-  // the lane's inputs of step t, fetched one step ahead: x_t and y_t, or ytilde_t
+  // the lane's inputs of step t, fetched two steps ahead: x_t and y_t, or ytilde_t
   auto fetch = [&](int t, int j, Real& xv, Real& yv) {
     xv = 0; yv = 0;
     if (!valid[j] || lane >= p.d) return;
@@ -148,20 +154,24 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_reduce(KP<Real> p
       yv = a.yt[ct * p.d + lane];
     }
   };
-  Real xn[CPW], yn[CPW], m[CPW];
+  Real x1[CPW], y1[CPW], x2[CPW], y2[CPW], m[CPW];
 #pragma unroll
-  for (int j = 0; j < CPW; ++j) { fetch(s, j, xn[j], yn[j]); m[j] = 0; }
+  for (int j = 0; j < CPW; ++j) {
+    fetch(s, j, x1[j], y1[j]);
+    if (s + 1 <= e) fetch(s + 1, j, x2[j], y2[j]);
+    m[j] = 0;
+  }
   for (int t = s; t <= e; ++t) {
-    const int cur = (t - s) % NBUF, nxt = (t - s + 1) % NBUF;
+    const int cur = (t - s) % NBUF;
     Real xi[CPW], yv[CPW];
 #pragma unroll
     for (int j = 0; j < CPW; ++j) {
-      xi[j] = xn[j]; yv[j] = yn[j];
-      if (t < e) fetch(t + 1, j, xn[j], yn[j]);
+      xi[j] = x1[j]; yv[j] = y1[j];
+      x1[j] = x2[j]; y1[j] = y2[j];
+      if (t + 2 <= e) fetch(t + 2, j, x2[j], y2[j]);
     }
-    if (t < e) stage_mats<Real, DP>(buf + nxt * NT * MAT, a.tab + (long)TK * tstride + (t + 1) * DD, tstride, NT);
-    else cp_async_commit();
-    cp_async_wait<1>();
+    stage(t + PREF);
+    cp_async_wait<PREF>();
     __syncthreads();
     if (any) {
       const Real* sK = buf + cur * NT * MAT;
@@ -246,18 +256,20 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS)
     m = in[cb * DP + row];
     if (valid && act && p.nb > 1) out[(cb + 1) * DP + lane] = m;
   }
-  if (n > 0) stage_mats<Real, DP>(buf, mats + kk_of(0) * DD, DD, 1);
-  Real inn = (n > 0) ? in[(cb + kk_of(0)) * DP + row] : (Real)0;
+  auto stage = [&](int j) {
+    if (j < n) stage_mats<Real, DP>(buf + (j % NBUF) * MAT, mats + kk_of(j) * DD, DD, 1);
+    else cp_async_commit();
+  };
+  for (int q = 0; q < PREF; ++q) stage(q);
+  Real in1 = (n > 0) ? in[(cb + kk_of(0)) * DP + row] : (Real)0;
+  Real in2 = (n > 1) ? in[(cb + kk_of(1)) * DP + row] : (Real)0;
   for (int j = 0; j < n; ++j) {
-    const int cur = j % NBUF, nxt = (j + 1) % NBUF, kk = kk_of(j);
-    const Real inc = inn;
-    if (j + 1 < n) {
-      inn = in[(cb + kk_of(j + 1)) * DP + row];
-      stage_mats<Real, DP>(buf + nxt * MAT, mats + kk_of(j + 1) * DD, DD, 1);
-    } else {
-      cp_async_commit();
-    }
-    cp_async_wait<1>();
+    const int cur = j % NBUF, kk = kk_of(j);
+    const Real inc = in1;
+    in1 = in2;
+    if (j + 2 < n) in2 = in[(cb + kk_of(j + 2)) * DP + row];
+    stage(j + PREF);
+    cp_async_wait<PREF>();
     __syncthreads();
     if (valid) {
       put_vec<Real, DP>(vq, m, lane);
@@ -290,7 +302,11 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_apply(KP<Real> p,
   const RowDyn<Real> rd = row_dyn<Real, DP>(p, row);
   const long tstride = (long)p.nT * DD;
   const Real* PF = a.tab + (long)TPF * tstride;
-  stage_mats<Real, DP>(buf, a.tab + (long)TK * tstride + s * DD, tstride, NT);
+  auto stage = [&](int t) {   // the tables of step t, or an empty copy group past the block
+    if (t <= e) stage_mats<Real, DP>(buf + ((t - s) % NBUF) * 4 * MAT, a.tab + (long)TK * tstride + t * DD, tstride, NT);
+    else cp_async_commit();
+  };
+  for (int q = 0; q < PREF; ++q) stage(s + q);
   bool valid[CPW];
   int cidx[CPW];
 #pragma unroll
@@ -307,7 +323,7 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_apply(KP<Real> p,
                                           vbase + (3 * j + 2) * VEC, lane, row);
     }
   }
-  // the lane's ytilde_t and (given) eps_t, fetched one step ahead
+  // the lane's ytilde_t and (given) eps_t, fetched two steps ahead
   auto fetch = [&](int t, int j, Real& yv, Real& ev) {
     yv = 0; ev = 0;
     if (!valid[j] || lane >= p.d) return;
@@ -315,20 +331,23 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_apply(KP<Real> p,
     yv = a.yt[ct * p.d + lane];
     if (epi && a.eps) ev = a.eps[ct * p.d + lane];
   };
-  Real yn[CPW], en[CPW];
+  Real y1[CPW], e1[CPW], y2[CPW], e2[CPW];
 #pragma unroll
-  for (int j = 0; j < CPW; ++j) fetch(s, j, yn[j], en[j]);
+  for (int j = 0; j < CPW; ++j) {
+    fetch(s, j, y1[j], e1[j]);
+    if (s + 1 <= e) fetch(s + 1, j, y2[j], e2[j]);
+  }
   for (int t = s; t <= e; ++t) {
-    const int cur = (t - s) % NBUF, nxt = (t - s + 1) % NBUF;
+    const int cur = (t - s) % NBUF;
     Real yti[CPW], eg[CPW];
 #pragma unroll
     for (int j = 0; j < CPW; ++j) {
-      yti[j] = yn[j]; eg[j] = en[j];
-      if (t < e) fetch(t + 1, j, yn[j], en[j]);
+      yti[j] = y1[j]; eg[j] = e1[j];
+      y1[j] = y2[j]; e1[j] = e2[j];
+      if (t + 2 <= e) fetch(t + 2, j, y2[j], e2[j]);
     }
-    if (t < e) stage_mats<Real, DP>(buf + nxt * 4 * MAT, a.tab + (long)TK * tstride + (t + 1) * DD, tstride, NT);
-    else cp_async_commit();
-    cp_async_wait<1>();
+    stage(t + PREF);
+    cp_async_wait<PREF>();
     __syncthreads();
     if (any) {
       const Real* sK = buf + cur * 4 * MAT;
@@ -433,11 +452,15 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW)
   const bool act = lane < DP;
   const int row = act ? lane : 0;
   if (b.mh && p.emis == AUX_EMIS_LINEAR_GAUSSIAN) load_ryinv<Real, DP>(p, sRy);
-  stage_mats<Real, DP>(buf, b.G + e * DD, DD, 1);
+  auto stage = [&](int t) {   // G_t, or an empty copy group before the block
+    if (t >= s) stage_mats<Real, DP>(buf + ((e - t) % NBUF) * MAT, b.G + t * DD, DD, 1);
+    else cp_async_commit();
+  };
+  for (int q = 0; q < PREF; ++q) stage(e - q);
   bool valid[CPW];
   long cb[CPW];
-  Real xi[CPW], un[CPW];
-  MhIn<Real> qn[CPW];
+  Real xi[CPW], u1[CPW], u2[CPW];
+  MhIn<Real> q1[CPW], q2[CPW];
   double acc[CPW];
 #pragma unroll
   for (int j = 0; j < CPW; ++j) {
@@ -446,26 +469,28 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW)
     cb[j] = (long)(valid[j] ? c : 0) * p.nT;
     xi[j] = valid[j] ? xnext[((long)c * p.nb + k) * DP + row] : (Real)0;
     acc[j] = 0.0;
-    // the lane's U_t and MH inputs, fetched one step ahead
-    un[j] = b.U[(cb[j] + e) * DP + row];
-    qn[j] = b.mh ? mh_load<Real>(p, b, cb[j] + e, e, lane) : MhIn<Real>{};
+    // the lane's U_t and MH inputs, fetched two steps ahead
+    u1[j] = b.U[(cb[j] + e) * DP + row];
+    q1[j] = b.mh ? mh_load<Real>(p, b, cb[j] + e, e, lane) : MhIn<Real>{};
+    u2[j] = (e - 1 >= s) ? b.U[(cb[j] + e - 1) * DP + row] : (Real)0;
+    q2[j] = (b.mh && e - 1 >= s) ? mh_load<Real>(p, b, cb[j] + e - 1, e - 1, lane) : MhIn<Real>{};
   }
   const bool any = valid[0];
   for (int t = e; t >= s; --t) {
-    const int cur = (e - t) % NBUF, nxt = (e - t + 1) % NBUF;
+    const int cur = (e - t) % NBUF;
     Real uc[CPW];
     MhIn<Real> qc[CPW];
 #pragma unroll
     for (int j = 0; j < CPW; ++j) {
-      uc[j] = un[j]; qc[j] = qn[j];
-      if (t > s) {
-        un[j] = b.U[(cb[j] + t - 1) * DP + row];
-        if (b.mh) qn[j] = mh_load<Real>(p, b, cb[j] + t - 1, t - 1, lane);
+      uc[j] = u1[j]; qc[j] = q1[j];
+      u1[j] = u2[j]; q1[j] = q2[j];
+      if (t - 2 >= s) {
+        u2[j] = b.U[(cb[j] + t - 2) * DP + row];
+        if (b.mh) q2[j] = mh_load<Real>(p, b, cb[j] + t - 2, t - 2, lane);
       }
     }
-    if (t > s) stage_mats<Real, DP>(buf + nxt * MAT, b.G + (t - 1) * DD, DD, 1);
-    else cp_async_commit();
-    cp_async_wait<1>();
+    stage(t - PREF);
+    cp_async_wait<PREF>();
     __syncthreads();
     if (any) {
       __syncwarp();
