@@ -407,9 +407,11 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def run_mode(mode, with_clocks, proposal=1):
+    def run_mode(mode, with_clocks, proposal=1, adapt=False):
         """Warm-up, then args.steps timed steps (L2 flushed before each), per-launch events on."""
         sm = AuxKalman(wl, dtype=w["dtype"], block_len=args.block_len, mode=mode, proposal=proposal)
+        if adapt:
+            sm.adapt_delta(True, target=0.5, gain=1.0)
         xm = torch.tensor(wl.x_init, dtype=tdt, device="cuda")
         accm = torch.zeros(C, dtype=torch.int32, device="cuda")
         lam = torch.zeros(C, dtype=torch.float64, device="cuda")
@@ -454,6 +456,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         unprof_ms = sum(e0.elapsed_time(e1) for e0, e1 in evu) / args.steps
         res = {"mode": mode, "proposal": "second order" if proposal == 2 else "first order",
+               "delta": sm.delta(), "delta_adaptation": bool(adapt),
                "value": world * C * T * args.steps / (t_ms / 1e3), "unit": UNIT,
                "ms_per_step": t_ms / args.steps, "ms_per_step_without_events": unprof_ms,
                "step_ms_median": statistics.median(step_ms),
@@ -478,6 +481,11 @@ def run_ours(args):
         so, _, _, _, _, _, r = run_mode("per_chain", False, proposal=2)
         so.close()
         others["per_chain_second_order"] = r
+        # on-device delta adaptation (pooled Robbins-Monro, target 0.5): the covariance
+        # pass reruns every step, as in the shared mode
+        so, _, _, _, _, _, r = run_mode("cached", False, adapt=True)
+        so.close()
+        others["cached_delta_adaptation"] = r
 
     # end to end through the public API from pinned host buffers
     x_host = torch.tensor(wl.x_init, dtype=tdt).pin_memory()

@@ -198,6 +198,27 @@ int aux_set_mode(aux_model *m, int32_t mode);
  * Errors: INVALID_ARG (unknown order), UNSUPPORTED (non-diagonal Hessian), OOM. */
 int aux_set_proposal(aux_model *m, int32_t order);
 
+/* On-line adaptation of delta to a target acceptance rate, on the device.
+ * The paper tunes delta to a target acceptance but states no rule (Section 4);
+ * this one is a Robbins-Monro recursion on log delta shared by the handle's
+ * chains: after the MH test of iteration k = 1, 2, ... of aux_kalman_step,
+ *   log delta <- log delta + gain k^{-0.6} (a_k - target),
+ * a_k = mean over chains of min(1, exp(log alpha)) (0 for a non-finite log
+ * alpha), log delta clamped to [-40, 40]. Every later step (and aux_loglik,
+ * aux_sample_path) uses the adapted delta; the update stays on the device
+ * (no host synchronisation). In the table modes the covariance pass then
+ * runs every iteration. Enabling starts from the handle's current delta and
+ * k = 0; disabling freezes delta at its adapted value (synchronises).
+ * aux_loglik_grad uses the handle's host delta (a theta component), i.e. the
+ * description's value or the value frozen at the last disable.
+ * enable: 0 or 1; target in (0, 1); gain > 0.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int aux_set_delta_adaptation(aux_model *m, int32_t enable, double target, double gain);
+
+/* The handle's current delta (the adapted value while adaptation is on;
+ * synchronises the handle's last stream then). Errors: INVALID_ARG, CUDA. */
+int aux_get_delta(aux_model *m, double *delta);
+
 /* Replace the model of an existing handle (same dtype, d_x, T, n_chains,
  * emis_kind, y_per_chain): validates as aux_init_model, then overwrites the
  * device copies of m0, P0, F, b, Q, y, R_y and delta. Synchronises the handle's

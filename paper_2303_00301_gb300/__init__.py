@@ -64,6 +64,13 @@ class AuxKalman:
     def status(self):
         return self.b.aux_get_status(self.handle, self.C)
 
+    def adapt_delta(self, enable=True, target=0.5, gain=1.0):
+        """On-device Robbins-Monro adaptation of delta (aux_set_delta_adaptation)."""
+        self.b.aux_set_delta_adaptation(self.handle, enable, target, gain)
+
+    def delta(self):
+        return self.b.aux_get_delta(self.handle)
+
     def close(self):
         if getattr(self, "handle", None) is not None:
             self.b.aux_free_model(self.handle)

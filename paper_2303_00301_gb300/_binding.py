@@ -85,6 +85,10 @@ def _load():
     lib.aux_set_mode.restype = ctypes.c_int
     lib.aux_set_proposal.argtypes = [vp, ctypes.c_int32]
     lib.aux_set_proposal.restype = ctypes.c_int
+    lib.aux_set_delta_adaptation.argtypes = [vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double]
+    lib.aux_set_delta_adaptation.restype = ctypes.c_int
+    lib.aux_get_delta.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.aux_get_delta.restype = ctypes.c_int
     lib.aux_loglik_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.aux_loglik_grad.restype = ctypes.c_int
     lib.aux_set_model_params.argtypes = [vp, ctypes.POINTER(aux_model_desc)]
@@ -174,6 +178,17 @@ def aux_set_mode(handle, mode):
 
 def aux_set_proposal(handle, order):
     _check(LIB.aux_set_proposal(handle, int(order)), "aux_set_proposal")
+
+
+def aux_set_delta_adaptation(handle, enable, target=0.5, gain=1.0):
+    _check(LIB.aux_set_delta_adaptation(handle, 1 if enable else 0, float(target), float(gain)),
+           "aux_set_delta_adaptation")
+
+
+def aux_get_delta(handle):
+    out = ctypes.c_double(0.0)
+    _check(LIB.aux_get_delta(handle, ctypes.byref(out)), "aux_get_delta")
+    return out.value
 
 
 def aux_loglik_grad(handle, ytilde, g_mu, g_Phi, g_cholSigma, g_delta, logZ=None, stream=None):

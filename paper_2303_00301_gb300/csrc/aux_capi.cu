@@ -315,6 +315,7 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
   if (!rc) rc = dev_alloc(m, (void**)&m->status_iter, (size_t)C * sizeof(int32_t));
   if (!rc) rc = dev_alloc(m, (void**)&m->status, (size_t)C * sizeof(int32_t));
   if (!rc) rc = dev_alloc(m, (void**)&m->accept, (size_t)C * sizeof(int32_t));
+  if (!rc) rc = dev_alloc(m, (void**)&m->la_all, (size_t)C * sizeof(double));
   if (!rc && (cudaMemset(m->status, 0, (size_t)C * sizeof(int32_t)) != cudaSuccess ||
               cudaMemset(m->status_iter, 0, (size_t)C * sizeof(int32_t)) != cudaSuccess))
     rc = AUX_E_CUDA;
@@ -397,6 +398,42 @@ int aux_set_proposal(aux_model* m, int32_t order) {
   return AUX_OK;
 }
 
+int aux_set_delta_adaptation(aux_model* m, int32_t enable, double target, double gain) {
+  if (!m) return AUX_E_INVALID_ARG;
+  if (enable) {
+    if (!(target > 0.0 && target < 1.0) || !(gain > 0.0) || !std::isfinite(gain)) return AUX_E_INVALID_ARG;
+    if (!m->delta_dev) {
+      int rc = dev_alloc(m, (void**)&m->delta_dev, sizeof(double));
+      if (!rc) rc = dev_alloc(m, (void**)&m->adapt_count, sizeof(int32_t));
+      if (rc) { m->delta_dev = nullptr; m->adapt_count = nullptr; return rc; }
+    }
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return AUX_E_CUDA;
+    const int32_t zero = 0;
+    if (cudaMemcpy(m->delta_dev, &m->delta, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->adapt_count, &zero, sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+      return AUX_E_CUDA;
+    m->adapt_target = target;
+    m->adapt_gain = gain;
+    m->adapt = 1;
+  } else if (m->adapt) {
+    // freeze at the adapted value
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return AUX_E_CUDA;
+    if (cudaMemcpy(&m->delta, m->delta_dev, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return AUX_E_CUDA;
+    m->adapt = 0;
+  }
+  m->cov_valid = 0;
+  return AUX_OK;
+}
+
+int aux_get_delta(aux_model* m, double* delta) {
+  if (!m || !delta) return AUX_E_INVALID_ARG;
+  if (!m->adapt) { *delta = m->delta; return AUX_OK; }
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) return AUX_E_CUDA;
+  return cudaMemcpy(delta, m->delta_dev, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess ? AUX_OK
+                                                                                              : AUX_E_CUDA;
+}
+
 int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {
   if (!m || !desc) return AUX_E_INVALID_ARG;
   if (desc->dtype != m->dtype || desc->d_x != m->d || desc->T != m->T || desc->n_chains != m->C ||
@@ -414,6 +451,12 @@ int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {
   m->fdiag = diag_flag(desc);
   m->diag_hess = hess_diag_flag(desc);
   m->cov_valid = 0;
+  if (m->adapt) {   // a new delta restarts the adaptation from it
+    const int32_t zero = 0;
+    if (cudaMemcpy(m->delta_dev, &m->delta, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->adapt_count, &zero, sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+      return AUX_E_CUDA;
+  }
   std::vector<double> gc;
   m->grad_ok = theta_constants(desc, gc) ? 1 : 0;
   if (m->grad_ok &&

@@ -65,6 +65,7 @@ template <typename Real, int DP> struct CovSizes {
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32, 1) k_cov_reduce(KP<Real> p, Real* __restrict__ aggm,
                                                      int32_t* __restrict__ status) {
+  refresh_delta(p);
   using Z = CovSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -401,6 +402,7 @@ __global__ void __launch_bounds__(32 * CW_SCAN)
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a) {
+  refresh_delta(p);
   using Z = CovSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
   constexpr long DD = (long)DP * DP;

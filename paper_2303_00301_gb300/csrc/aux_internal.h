@@ -34,6 +34,12 @@ struct aux_model {
   int32_t *status_iter = nullptr, *status = nullptr;
   int32_t *accept = nullptr;  // [C] this step's MH decisions
   void *rho = nullptr, *rhos = nullptr;   // second order: [C][T][d] forward / reverse variances
+  double *la_all = nullptr;  // [C] this step's log alpha
+  // on-device delta adaptation (aux_set_delta_adaptation)
+  int adapt = 0;
+  double adapt_target = 0.5, adapt_gain = 1.0;
+  double *delta_dev = nullptr;
+  int32_t *adapt_count = nullptr;
   // gradient (aux_loglik_grad): theta constants and lazily allocated smoother buffers
   int grad_ok = 0;           // the model has the SV parameterisation
   double *gconst = nullptr;  // mu, phi, L, Q, Q^{-1}, P0^{-1} (FP64, unpadded)

@@ -48,7 +48,19 @@ template <typename Real> struct KP {
   int32_t* status_iter;                      // [C], this step's status bits
   int order;                                 // proposal: 1 first order, 2 second order
   const Real* rho;   // [C][T][d] diagonal pseudo-observation variance (second order), or null: r
+  const double* delta_dev;   // adapted delta on the device, or null: r and sqrt_r as given
 };
+
+// With on-device delta adaptation the kernels take r = delta / 2 from device
+// memory (written by k_adapt_delta of the previous iteration).
+template <typename Real>
+__device__ __forceinline__ void refresh_delta(KP<Real>& p) {
+  if (p.delta_dev) {
+    const double dl = *p.delta_dev;
+    p.r = (Real)(0.5 * dl);
+    p.sqrt_r = (Real)sqrt(0.5 * dl);
+  }
+}
 
 // the lane's diagonal entry of the pseudo-observation covariance at (chain, t)
 template <typename Real>
@@ -111,6 +123,7 @@ template <typename Real>
 __global__ void k_linearise(KP<Real> p, const Real* __restrict__ x, Real* __restrict__ u,
                             Real* __restrict__ v, Real* __restrict__ yt, Real* __restrict__ rho,
                             uint64_t iter) {
+  refresh_delta(p);
   const long n = (long)p.C * p.nT * p.d;
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
        idx += (long)gridDim.x * blockDim.x) {
@@ -388,6 +401,7 @@ __device__ __forceinline__ void load_element(const Real* g, Real* SA, Real* SC, 
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32 * Sizes<Real, DP>::RED_WPC, 1)
     k_filter_reduce(KP<Real> p, const Real* __restrict__ yt, Real* __restrict__ agg) {
+  refresh_delta(p);
   using Z = Sizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -625,6 +639,7 @@ template <typename Real> struct ApplyArgs {
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
     k_filter_apply(KP<Real> p, ApplyArgs<Real> a) {
+  refresh_delta(p);
   using Z = Sizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1005,6 +1020,7 @@ __device__ __forceinline__ double mh_step_terms(const KP<Real>& p, const BackArg
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32 * Sizes<Real, DP>::BWD_WPC)
     k_sample_backward(KP<Real> p, BackArgs<Real> a) {
+  refresh_delta(p);
   using Z = Sizes<Real, DP>;
   constexpr int VEC = Z::VEC, LD = Lay<Real, DP>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1063,7 +1079,8 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::BWD_WPC)
 template <typename Real>
 __global__ void k_mh(KP<Real> p, const double* __restrict__ mh_part,
                      const double* __restrict__ lz_part, uint64_t iter, uint32_t* acc_count,
-                     double* log_alpha, int32_t* status, int32_t* __restrict__ accept) {
+                     double* log_alpha, int32_t* status, int32_t* __restrict__ accept,
+                     double* __restrict__ la_all) {
   const int c = blockIdx.x;
   __shared__ double red[32];
   double sacc = 0.0;
@@ -1082,6 +1099,7 @@ __global__ void k_mh(KP<Real> p, const double* __restrict__ mh_part,
     const int acc = (st == 0) && (lu < la);
     accept[c] = acc;
     status[c] |= st;
+    la_all[c] = la;
     if (log_alpha) log_alpha[c] = la;
     if (acc_count && acc) acc_count[c] += 1;
   }
@@ -1090,6 +1108,35 @@ __global__ void k_mh(KP<Real> p, const double* __restrict__ mh_part,
 // ---------------------------------------------------------------------------
 // State update x <- x* for the accepted chains, over the whole grid.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// On-line delta adaptation (Robbins-Monro on log delta): with a_k the mean over
+// the chains of min(1, exp(log alpha)) (0 for a non-finite log alpha),
+// log delta <- log delta + gain k^{-0.6} (a_k - target), k = 1, 2, ...; log delta
+// is kept in [-40, 40]. One CTA.
+// ---------------------------------------------------------------------------
+static __global__ void k_adapt_delta(const double* __restrict__ la_all, int C, double* __restrict__ delta,
+                                     int* __restrict__ count, double target, double gain) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    const double la = la_all[c];
+    s += isfinite(la) ? exp(fmin(0.0, la)) : 0.0;
+  }
+  s = warp_sum<double>(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) a += red[w];
+    a /= (double)C;
+    const int k = *count + 1;
+    double ld = log(*delta) + gain * pow((double)k, -0.6) * (a - target);
+    ld = fmin(40.0, fmax(-40.0, ld));
+    *delta = exp(ld);
+    *count = k;
+  }
+}
+
 template <typename Real>
 __global__ void k_commit(KP<Real> p, Real* __restrict__ x, const Real* __restrict__ xs,
                          const int32_t* __restrict__ accept) {

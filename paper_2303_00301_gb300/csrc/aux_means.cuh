@@ -116,6 +116,7 @@ __device__ __forceinline__ void load_ryinv(const KP<Real>& p, Real* sRy) {
 // ---------------------------------------------------------------------------
 template <typename Real, int DP, int CPW>
 __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_reduce(KP<Real> p, MeanArgs<Real> a) {
+  refresh_delta(p);
   using Z = MeanSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
   constexpr long DD = (long)DP * DP;
@@ -286,6 +287,7 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS)
 // ---------------------------------------------------------------------------
 template <typename Real, int DP, int CPW>
 __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_apply(KP<Real> p, MeanArgs<Real> a) {
+  refresh_delta(p);
   using Z = MeanSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
   constexpr long DD = (long)DP * DP;
@@ -439,6 +441,7 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_apply(KP<Real> p,
 template <typename Real, int DP, int CPW>
 __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW)
     k_mb_apply(KP<Real> p, BackArgs<Real> b, const Real* __restrict__ xnext) {
+  refresh_delta(p);
   using Z = MeanSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
   constexpr long DD = (long)DP * DP;

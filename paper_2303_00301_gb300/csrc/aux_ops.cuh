@@ -41,6 +41,7 @@ KP<Real> make_kp(const aux_model* m) {
   p.status_iter = m->status_iter;
   p.order = m->order;
   p.rho = nullptr;
+  p.delta_dev = m->adapt ? m->delta_dev : nullptr;
   return p;
 }
 
@@ -93,10 +94,13 @@ struct Ops {
                         double* log_alpha, cudaStream_t st) {
     ProfScope ps(m, PK_MH, st);
     k_mh<Real><<<m->C, 128, 0, st>>>(p, m->mh_part, m->lz_part, iter, acc, log_alpha, m->status,
-                                     m->accept);
+                                     m->accept, m->la_all);
     const long n = (long)m->C * m->T * m->d;
     const int grid = (int)std::min<long>((n + 255) / 256, 152L * 8);
     k_commit<Real><<<grid, 256, 0, st>>>(p, x, (const Real*)m->xs, m->accept);
+    if (m->adapt)
+      k_adapt_delta<<<1, 256, 0, st>>>(m->la_all, m->C, m->delta_dev, m->adapt_count, m->adapt_target,
+                                       m->adapt_gain);
   }
 
 
@@ -234,9 +238,11 @@ struct Ops {
                                double* log_alpha, cudaStream_t st) {
     const KP<Real> p = make_kp<Real>(m);
     Real* x = (Real*)xv;
-    ensure_cov(m, p, st);
     for (int it = 0; it < n_iters; ++it) {
       const uint64_t iter = iter0 + (uint64_t)it;
+      // an adapted delta changes the covariances every iteration
+      if (m->adapt) cov_pass(m, p, st);
+      else if (it == 0) ensure_cov(m, p, st);
       MeanArgs<Real> a = mean_args(m);
       a.x = x; a.u = (Real*)m->u; a.v = (Real*)m->v; a.yt = (Real*)m->yt; a.iter = iter;
       a.flags = APPLY_EPI | APPLY_STORE_Q;
@@ -338,7 +344,8 @@ struct Ops {
   static int loglik_grad(aux_model* m, const void* yt, double* logZ, double* g_mu, double* g_phi,
                          double* g_L, double* g_delta, cudaStream_t st) {
     using GZ = GradSizes<Real, DP>;
-    const KP<Real> p = make_kp<Real>(m);
+    KP<Real> p = make_kp<Real>(m);
+    p.delta_dev = nullptr;   // the gradient is taken at the description's delta (a theta component)
     ApplyArgs<Real> a = apply_args(m, APPLY_EPI | APPLY_LOGZ | APPLY_SMOOTH, 0);
     a.Sig = (Real*)m->Sig;
     filter(m, p, (const Real*)yt, a, st);

@@ -247,6 +247,43 @@ def test_second_order_is_rejected_in_table_modes(mode):
     s.close()
 
 
+# ---- on-device delta adaptation (pooled Robbins-Monro on log delta)
+
+@pytest.mark.parametrize("mode", MODES)
+def test_delta_adaptation_follows_the_oracle_f64(mode):
+    from oracle import calibrate_delta
+    wl = workloads.stochastic_volatility(d=3, T=20, n_chains=3, delta=0.2)
+    n, target, gain = 12, 0.5, 1.5
+    s = AuxKalman(wl, dtype="f64", block_len=4, mode=mode)
+    s.adapt_delta(True, target=target, gain=gain)
+    x = _tt(wl.x_init, torch.float64)
+    deltas = [s.delta()]
+    for k in range(n):
+        s.step(x, n_iters=1, iter0=k)
+        deltas.append(s.delta())
+    x_ref, d_ref, _ = calibrate_delta.run_chains_adaptive(wl.x_init, _oracle_model(wl), 0.2, n,
+                                                         target=target, c=gain, seed=wl.mcmc_seed)
+    assert np.max(np.abs(np.array(deltas) / d_ref - 1.0)) < 1e-9, (deltas, d_ref)
+    assert _rel(x.cpu().numpy(), x_ref) < 1e-9
+    s.adapt_delta(False)
+    assert abs(s.delta() - d_ref[-1]) < 1e-9 * d_ref[-1]
+    s.close()
+
+
+def test_delta_adaptation_reaches_the_target_f32():
+    wl = workloads.stochastic_volatility(d=8, T=64, n_chains=16, delta=2.0)
+    s = AuxKalman(wl, dtype="f32", block_len=8, mode="cached")
+    s.adapt_delta(True, target=0.4, gain=2.0)
+    x = _tt(wl.x_init, torch.float32)
+    acc = torch.zeros(16, dtype=torch.int32, device="cuda")
+    s.step(x, n_iters=150, iter0=0)
+    s.step(x, n_iters=150, iter0=150, accept_count=acc)
+    torch.cuda.synchronize()
+    rate = acc.float().mean().item() / 150
+    assert abs(rate - 0.4) < 0.1, (rate, s.delta())
+    s.close()
+
+
 def test_execution_modes_agree_at_full_size():
     """d=30, T=1024, 32 chains: the three execution modes give the same steps (FP32 rounding)."""
     wl = workloads.stochastic_volatility(d=30, T=1024, n_chains=32)
