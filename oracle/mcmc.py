@@ -27,6 +27,7 @@ One step (Algorithm 2 with Gaussian dynamics, so F, b, Q are the model's):
 Emission models (gamma and its gradient):
   linear-Gaussian  log h(y|x) = log N(y; x, R_y)           (Appendix A, Eq. (A.1))
   stochastic vol.  log h(y|x) = sum_i log N(y_i; 0, exp(x_i))  (Section 4.1)
+  Student-t        log h(y|x) = log t_nu(y; x, Sigma)      (Section 4.3)
 An optional observation mask switches gamma_t off (gamma_t = 0, v_t = 0) at
 unobserved steps, as in the two-step model of Section 4.4.
 
@@ -87,6 +88,36 @@ class SVEmission:
         """Hessian of log h(y_t | x_t) in x_t, [T, d, d]: diag(-y^2 exp(-x) / 2)."""
         h = -0.5 * self.y ** 2 * np.exp(-x) * self.mask[:, None]
         return np.einsum("ti,ij->tij", h, np.eye(x.shape[1]))
+
+
+class StudentTEmission:
+    """log h(y_t | x_t) = log t_nu(y_t; x_t, Sigma): the multivariate t with nu
+    degrees of freedom, location x_t and scale matrix Sigma (the observation
+    model of Section 4.3; it does not factorise over the coordinates)."""
+
+    def __init__(self, y, Sigma, nu, mask=None):
+        from math import lgamma
+        self.y = np.asarray(y, dtype=np.float64)
+        self.nu = float(nu)
+        self.mask = np.ones(len(self.y), bool) if mask is None else np.asarray(mask, bool)
+        self.Lam = np.linalg.inv(np.asarray(Sigma, dtype=np.float64))
+        d = self.y.shape[1]
+        self.d = d
+        self._const = (lgamma(0.5 * (self.nu + d)) - lgamma(0.5 * self.nu) - 0.5 * d * np.log(self.nu * np.pi)
+                       - 0.5 * np.linalg.slogdet(np.asarray(Sigma, dtype=np.float64))[1])
+
+    def _q(self, x):
+        r = self.y - x
+        return r, np.einsum("ti,ij,tj->t", r, self.Lam, r)
+
+    def log_h(self, x):
+        _, q = self._q(x)
+        return np.where(self.mask, self._const - 0.5 * (self.nu + self.d) * np.log1p(q / self.nu), 0.0)
+
+    def grad(self, x):
+        r, q = self._q(x)
+        g = ((self.nu + self.d) / (self.nu + q))[:, None] * (r @ self.Lam.T)
+        return g * self.mask[:, None]
 
 
 def log_prior(x, m0, P0, F, b, Q):

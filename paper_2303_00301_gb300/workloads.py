@@ -16,6 +16,13 @@ Models (all with Gaussian dynamics x_t = F x_{t-1} + b + N(0, Q), x_0 ~ N(m0, P0
   is diagonal), y_t(i) = exp(x_t(i) / 2) eta_t(i), eta ~ N(0, 1). The paper's
   SV datasets are simulated from the model itself; this simulation stands in
   for them.
+* ``spatio_temporal``: the lattice model of Section 4.3: independent random
+  walks X_t(i, j) = X_{t-1}(i, j) + N(0, sigma_X^2) on a side x side lattice
+  (d = side^2), observed through a multivariate t with nu degrees of freedom
+  whose precision matrix has entries tau^D for lattice distance D <= r_y and 0
+  beyond (D = |i - i'| + |j - j'|); sigma_X = 1, nu = 1, tau = -1/4, r_y = 1,
+  T = 1024, d = 64 as in that section. The law of X_0 is not stated; here
+  X_0 ~ N(0, sigma_X^2 I). The chains start at the simulated latent path.
 * ``two_step_toy``: the two-step failure-mode model of Section 4.4:
   x_0 ~ N(0, 1), x_1 ~ N(rho x_0, 1 - rho^2), one observation y = 5 of x_1
   with variance r^2 (the emission at t = 0 is masked out).
@@ -30,6 +37,7 @@ import numpy as np
 
 EMIS_LINEAR_GAUSSIAN = 0
 EMIS_SV = 1
+EMIS_STUDENT_T = 2
 
 
 @dataclass
@@ -44,12 +52,13 @@ class Workload:
     b: np.ndarray
     Q: np.ndarray
     y: np.ndarray                 # [T, d]
-    emission: int                 # EMIS_LINEAR_GAUSSIAN | EMIS_SV
+    emission: int                 # EMIS_LINEAR_GAUSSIAN | EMIS_SV | EMIS_STUDENT_T
     delta: float
     x_init: np.ndarray            # [C, T, d]
     mcmc_seed: int = 1
-    Ry: Optional[np.ndarray] = None
+    Ry: Optional[np.ndarray] = None     # linear-Gaussian covariance, or Student-t scale matrix
     mask: Optional[np.ndarray] = None   # [T] uint8, 1 = observed
+    nu: float = 0.0                     # Student-t degrees of freedom
     meta: dict = field(default_factory=dict)
 
     def oracle_model(self):
@@ -114,6 +123,40 @@ def stochastic_volatility(d=30, T=1024, n_chains=32, sim_seed=0, mcmc_seed=1, de
                     F=F, b=b, Q=Q, y=y, emission=EMIS_SV, delta=float(delta),
                     x_init=x_init, mcmc_seed=mcmc_seed,
                     meta=dict(phi=phi, Sigma=Sigma, x_true=x_true))
+
+
+def lattice_precision(side, tau=-0.25, r_y=1):
+    """Precision of the spatio-temporal observation noise: tau^D for D <= r_y."""
+    idx = [(i, j) for i in range(side) for j in range(side)]
+    d = len(idx)
+    Lam = np.zeros((d, d))
+    for a, (i, j) in enumerate(idx):
+        for b_, (k, l) in enumerate(idx):
+            D = abs(i - k) + abs(j - l)
+            if D <= r_y:
+                Lam[a, b_] = tau ** D
+    return Lam
+
+
+def spatio_temporal(side=8, T=1024, n_chains=1, nu=1.0, tau=-0.25, r_y=1, sigma_x=1.0, sim_seed=0,
+                    mcmc_seed=1, delta=0.05):
+    d = side * side
+    rng = np.random.default_rng(sim_seed)
+    m0 = np.zeros(d)
+    P0 = sigma_x ** 2 * np.eye(d)
+    F = np.eye(d)
+    b = np.zeros(d)
+    Q = sigma_x ** 2 * np.eye(d)
+    x_true = _simulate_dynamics(rng, m0, P0, F, b, Q, T)
+    Sigma = np.linalg.inv(lattice_precision(side, tau, r_y))
+    Ls = np.linalg.cholesky(Sigma)
+    z = rng.standard_normal((T, d)) @ Ls.T
+    w = rng.chisquare(nu, size=T)
+    y = x_true + z / np.sqrt(w / nu)[:, None]
+    x_init = np.repeat(x_true[None], n_chains, axis=0)
+    return Workload(name=f"spatio_temporal_{side}x{side}_T{T}", d=d, T=T, n_chains=n_chains, m0=m0,
+                    P0=P0, F=F, b=b, Q=Q, y=y, emission=EMIS_STUDENT_T, delta=delta, x_init=x_init,
+                    mcmc_seed=mcmc_seed, Ry=Sigma, nu=nu, meta=dict(x_true=x_true))
 
 
 def two_step_toy(rho=0.5, r2=0.1, y_obs=5.0, n_chains=1, delta=0.5, mcmc_seed=1):
