@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define AUX_ABI_VERSION 1
+#define AUX_ABI_VERSION 2
 
 /* status codes */
 #define AUX_OK             0
@@ -74,13 +74,15 @@ extern "C" {
 /* emission models */
 #define AUX_EMIS_LINEAR_GAUSSIAN 0
 #define AUX_EMIS_SV              1
+#define AUX_EMIS_STUDENT_T       2  /* multivariate t, scale R_y, nu degrees of freedom (Section 4.3) */
 
 /* Model description (Section 2.2, Eq. (2.5); SV model of Section 4.1).
  * All arrays are HOST pointers to double, copied by aux_init_model. */
 typedef struct {
   int32_t abi_version;   /* AUX_ABI_VERSION */
   int32_t dtype;         /* AUX_F32 | AUX_F64 */
-  int32_t d_x;           /* state dimension: 1..32 (AUX_F32), 1..16 (AUX_F64) */
+  int32_t d_x;           /* state dimension: 1..32 (AUX_F32), 1..16 (AUX_F64); 1..1024 with
+                            AUX_EMIS_STUDENT_T (factorised prior, see below) */
   int32_t T;             /* number of states, T >= 1 */
   int32_t n_chains;      /* C >= 1 */
   int32_t emis_kind;     /* AUX_EMIS_* */
@@ -93,9 +95,22 @@ typedef struct {
   const double *Q;       /* [d*d]  transition covariance (SPD) */
   const double *y;       /* observations, see y_per_chain */
   const uint8_t *obs_mask; /* [T] or NULL: log h_t == 0 where obs_mask[t] == 0 */
-  const double *R_y;     /* [d*d] emission covariance (linear-Gaussian), else NULL */
+  const double *R_y;     /* [d*d] emission covariance (linear-Gaussian) or scale matrix
+                            (Student-t), else NULL */
   double delta;          /* step size delta > 0; auxiliary covariance (delta/2) I */
+  double nu;             /* Student-t degrees of freedom (> 0), ignored otherwise */
 } aux_model_desc;
+
+/* Factorised prior (Section 4.3). With AUX_EMIS_STUDENT_T,
+ *   log h(y_t | x_t) = log t_nu(y_t; x_t, R_y),
+ * which does not factorise over the coordinates, and F, Q, P0 must be diagonal
+ * (else AUX_E_UNSUPPORTED). The auxiliary LGSSM then splits into d_x
+ * independent scalar LGSSMs and the library runs them as such (one thread per
+ * chain, scan block and coordinate), with the first-order proposal; the
+ * execution mode is not used (the scalar covariance tables are kept until the
+ * model changes, or recomputed every iteration while delta adapts).
+ * aux_loglik takes mf (not Pf); aux_loglik_grad, aux_set_model_params and the
+ * second-order proposal return AUX_E_UNSUPPORTED for such a handle. */
 
 typedef struct aux_model aux_model;   /* opaque handle */
 

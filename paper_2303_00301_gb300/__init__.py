@@ -5,7 +5,7 @@ behind the C ABI of ``include/aux_kalman.h``. ``_binding`` exposes those
 entry points under their C names; ``AuxKalman`` is a small convenience
 wrapper that owns the handle and takes torch CUDA tensors.
 """
-from .workloads import EMIS_LINEAR_GAUSSIAN, EMIS_SV  # noqa: F401
+from .workloads import EMIS_LINEAR_GAUSSIAN, EMIS_STUDENT_T, EMIS_SV  # noqa: F401
 
 
 def _load_binding():
@@ -42,7 +42,8 @@ class AuxKalman:
             d_x=self.d, T=self.T, n_chains=self.C, m0=workload.m0, P0=workload.P0,
             F=workload.F, b=workload.b, Q=workload.Q, y=workload.y, delta=workload.delta,
             emis_kind=workload.emission, dtype=self.dtype_code, R_y=workload.Ry,
-            obs_mask=workload.mask, block_len=block_len, seed=self.seed, stream=stream)
+            obs_mask=workload.mask, block_len=block_len, seed=self.seed, stream=stream,
+            nu=getattr(workload, "nu", 0.0))
         if mode not in MODES:
             raise ValueError(f"mode must be one of {MODES}")
         self.mode = mode

@@ -13,13 +13,13 @@ import numpy as np
 
 from . import build as _build
 
-AUX_ABI_VERSION = 1
+AUX_ABI_VERSION = 2
 AUX_OK, AUX_E_INVALID_ARG, AUX_E_NOT_PD, AUX_E_NONFINITE = 0, 1, 2, 3
 AUX_E_CUDA, AUX_E_TIMEOUT, AUX_E_OOM, AUX_E_UNSUPPORTED = 4, 5, 6, 7
 AUX_E_TOO_LARGE = 8
 AUX_NOALLOC_SCRATCH_BYTES = 32 << 20
 AUX_F32, AUX_F64 = 0, 1
-AUX_EMIS_LINEAR_GAUSSIAN, AUX_EMIS_SV = 0, 1
+AUX_EMIS_LINEAR_GAUSSIAN, AUX_EMIS_SV, AUX_EMIS_STUDENT_T = 0, 1, 2
 AUX_MODE_PER_CHAIN, AUX_MODE_SHARED_COV, AUX_MODE_CACHED_COV = 0, 1, 2
 AUX_PROPOSAL_FIRST_ORDER, AUX_PROPOSAL_SECOND_ORDER = 1, 2
 
@@ -46,6 +46,7 @@ class aux_model_desc(ctypes.Structure):
         ("obs_mask", _u8_p),
         ("R_y", _dbl_p),
         ("delta", ctypes.c_double),
+        ("nu", ctypes.c_double),
     ]
 
 
@@ -135,7 +136,7 @@ def _as_c(a, dtype=np.float64):
 
 
 def _make_desc(d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind, dtype, R_y, obs_mask,
-               y_per_chain, block_len):
+               y_per_chain, block_len, nu=0.0):
     """Fill an aux_model_desc; returns it with the numpy arrays it points into."""
     keep = dict(m0=_as_c(m0), P0=_as_c(P0), F=_as_c(F), b=_as_c(b), Q=_as_c(Q))
     if y is not None:
@@ -156,14 +157,15 @@ def _make_desc(d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind, dtype, R_
         keep["mask"] = _as_c(obs_mask, np.uint8)
         desc.obs_mask = keep["mask"].ctypes.data_as(_u8_p)
     desc.delta = float(delta)
+    desc.nu = float(nu)
     return desc, keep
 
 
 def aux_init_model(*, d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind, dtype=AUX_F32,
-                   R_y=None, obs_mask=None, y_per_chain=False, block_len=0, seed=0, stream=None):
+                   R_y=None, obs_mask=None, y_per_chain=False, block_len=0, seed=0, stream=None, nu=0.0):
     """Create a model handle (host arrays are copied during the call)."""
     desc, keep = _make_desc(d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind, dtype, R_y,
-                            obs_mask, y_per_chain, block_len)
+                            obs_mask, y_per_chain, block_len, nu)
     handle = ctypes.c_void_p()
     rc = LIB.aux_init_model(ctypes.byref(desc), ctypes.c_uint64(int(seed)), _stream(stream),
                             ctypes.byref(handle))

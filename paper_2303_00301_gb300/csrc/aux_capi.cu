@@ -154,30 +154,41 @@ int validate_desc(const aux_model_desc* desc, std::vector<double>& Ryinv) {
   if (!desc) return AUX_E_INVALID_ARG;
   if (desc->abi_version != AUX_ABI_VERSION) return AUX_E_INVALID_ARG;
   if (desc->dtype != AUX_F32 && desc->dtype != AUX_F64) return AUX_E_INVALID_ARG;
-  if (desc->emis_kind != AUX_EMIS_LINEAR_GAUSSIAN && desc->emis_kind != AUX_EMIS_SV)
+  if (desc->emis_kind != AUX_EMIS_LINEAR_GAUSSIAN && desc->emis_kind != AUX_EMIS_SV &&
+      desc->emis_kind != AUX_EMIS_STUDENT_T)
     return AUX_E_INVALID_ARG;
   const int d = desc->d_x, T = desc->T, C = desc->n_chains;
+  const bool st = desc->emis_kind == AUX_EMIS_STUDENT_T;
   if (d < 1 || T < 1 || C < 1 || desc->block_len < 0) return AUX_E_INVALID_ARG;
   if (!desc->m0 || !desc->P0 || !desc->F || !desc->b || !desc->Q || !desc->y)
     return AUX_E_INVALID_ARG;
-  if (desc->emis_kind == AUX_EMIS_LINEAR_GAUSSIAN && !desc->R_y) return AUX_E_INVALID_ARG;
+  if ((desc->emis_kind == AUX_EMIS_LINEAR_GAUSSIAN || st) && !desc->R_y) return AUX_E_INVALID_ARG;
   if (!(desc->delta > 0.0) || !std::isfinite(desc->delta)) return AUX_E_INVALID_ARG;
-  const int DP = pick_dp(d);
-  if (DP == 0) return AUX_E_UNSUPPORTED;
-  if (desc->dtype == AUX_F64 && DP > 16) return AUX_E_UNSUPPORTED;
+  if (st && (!(desc->nu > 0.0) || !std::isfinite(desc->nu))) return AUX_E_INVALID_ARG;
+  if (st) {
+    if (d > 1024) return AUX_E_UNSUPPORTED;
+    for (int i = 0; i < d; ++i)   // the factorised path needs diagonal F, Q, P0
+      for (int j = 0; j < d; ++j)
+        if (i != j && (desc->F[i * d + j] != 0.0 || desc->Q[i * d + j] != 0.0 || desc->P0[i * d + j] != 0.0))
+          return AUX_E_UNSUPPORTED;
+  } else {
+    const int DP = pick_dp(d);
+    if (DP == 0) return AUX_E_UNSUPPORTED;
+    if (desc->dtype == AUX_F64 && DP > 16) return AUX_E_UNSUPPORTED;
+  }
   if ((long long)C * T * d > (1LL << 31)) return AUX_E_UNSUPPORTED;
   const size_t dd = (size_t)d * d;
   const size_t ny = (size_t)(desc->y_per_chain ? C : 1) * T * d;
   if (!all_finite(desc->m0, d) || !all_finite(desc->P0, dd) || !all_finite(desc->F, dd) ||
       !all_finite(desc->b, d) || !all_finite(desc->Q, dd) || !all_finite(desc->y, ny))
     return AUX_E_NONFINITE;
-  if (desc->R_y && desc->emis_kind == AUX_EMIS_LINEAR_GAUSSIAN && !all_finite(desc->R_y, dd))
+  if (desc->R_y && desc->emis_kind != AUX_EMIS_SV && !all_finite(desc->R_y, dd))
     return AUX_E_NONFINITE;
   std::vector<double> L;
   if (!is_symmetric(desc->P0, d) || !host_cholesky(desc->P0, d, L)) return AUX_E_NOT_PD;
   if (!is_symmetric(desc->Q, d) || !host_cholesky(desc->Q, d, L)) return AUX_E_NOT_PD;
   Ryinv.clear();
-  if (desc->emis_kind == AUX_EMIS_LINEAR_GAUSSIAN) {
+  if (desc->emis_kind != AUX_EMIS_SV) {
     if (!is_symmetric(desc->R_y, d) || !host_cholesky(desc->R_y, d, L)) return AUX_E_NOT_PD;
     Ryinv = spd_inverse(L, d);
   }
@@ -234,6 +245,69 @@ int hess_diag_flag(const aux_model_desc* desc) {
   return 1;
 }
 
+// factorised-prior handle (Student-t emission): diagonal model vectors, the
+// inverse scale matrix, observations and the scalar tables and workspaces
+template <typename Real>
+int fact_upload(aux_model* m, const aux_model_desc* desc, const std::vector<double>& Lam) {
+  const int d = m->d;
+  std::vector<Real> mod(5 * (size_t)d), lam((size_t)d * d);
+  for (int i = 0; i < d; ++i) {
+    mod[i] = (Real)desc->F[i * d + i];
+    mod[d + i] = (Real)desc->b[i];
+    mod[2 * d + i] = (Real)desc->Q[i * d + i];
+    mod[3 * d + i] = (Real)desc->P0[i * d + i];
+    mod[4 * d + i] = (Real)desc->m0[i];
+  }
+  for (size_t q = 0; q < (size_t)d * d; ++q) lam[q] = (Real)Lam[q];
+  const size_t ny = (size_t)(m->y_per_chain ? m->C : 1) * m->T * d;
+  std::vector<Real> yv(ny);
+  for (size_t q = 0; q < ny; ++q) yv[q] = (Real)desc->y[q];
+  auto bytes = [](const auto& v) {
+    std::vector<unsigned char> h(v.size() * sizeof(v[0]));
+    std::memcpy(h.data(), v.data(), h.size());
+    return h;
+  };
+  int rc = upload(m, &m->fmodel, bytes(mod));
+  if (!rc) rc = upload(m, &m->flam, bytes(lam));
+  if (!rc) rc = upload(m, &m->y, bytes(yv));
+  return rc;
+}
+
+int fact_init(aux_model* m, const aux_model_desc* desc, const std::vector<double>& Lam) {
+  m->fact = 1;
+  m->nu = desc->nu;
+  int rc = m->dtype == AUX_F32 ? fact_upload<float>(m, desc, Lam) : fact_upload<double>(m, desc, Lam);
+  if (!rc && desc->obs_mask) {
+    std::vector<unsigned char> mk(desc->obs_mask, desc->obs_mask + m->T);
+    rc = upload(m, (void**)&m->mask, mk);
+  }
+  const size_t es = m->esz, d = m->d, T = m->T, C = m->C, nb = m->nb;
+  const size_t path = C * T * d * es, blk = C * nb * d;
+  if (!rc) rc = dev_alloc(m, &m->u, path);
+  if (!rc) rc = dev_alloc(m, &m->v, path);
+  if (!rc) rc = dev_alloc(m, &m->yt, path);
+  if (!rc) rc = dev_alloc(m, &m->xs, path);
+  if (!rc) rc = dev_alloc(m, &m->yts, path);
+  if (!rc) rc = dev_alloc(m, &m->U, path);
+  if (!rc) rc = dev_alloc(m, &m->ftab, 4 * T * d * es);
+  if (!rc) rc = dev_alloc(m, &m->fbt, 2 * nb * d * es);
+  if (!rc) rc = dev_alloc(m, (void**)&m->fldb, nb * d * sizeof(double));
+  if (!rc) rc = dev_alloc(m, &m->fz, blk * es);
+  if (!rc) rc = dev_alloc(m, &m->fms, blk * es);
+  if (!rc) rc = dev_alloc(m, &m->fub, blk * es);
+  if (!rc) rc = dev_alloc(m, (void**)&m->ffq, blk * sizeof(double));
+  if (!rc) rc = dev_alloc(m, (void**)&m->flz, blk * sizeof(double));
+  if (!rc) rc = dev_alloc(m, (void**)&m->fgam, C * T * sizeof(double));
+  if (!rc) rc = dev_alloc(m, (void**)&m->fmh, C * T * sizeof(double));
+  if (!rc) rc = dev_alloc(m, (void**)&m->status, C * sizeof(int32_t));
+  if (!rc) rc = dev_alloc(m, (void**)&m->status_iter, C * sizeof(int32_t));
+  if (!rc) rc = dev_alloc(m, (void**)&m->accept, C * sizeof(int32_t));
+  if (!rc) rc = dev_alloc(m, (void**)&m->la_all, C * sizeof(double));
+  if (!rc && (cudaMemset(m->status, 0, C * sizeof(int32_t)) != cudaSuccess)) rc = AUX_E_CUDA;
+  if (!rc) rc = aux_fact_prepare(m);
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -260,7 +334,8 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
   const int vrc = validate_desc(desc, Ryinv);
   if (vrc) return vrc;
   const int d = desc->d_x, T = desc->T, C = desc->n_chains;
-  const int DP = pick_dp(d);
+  const bool fact = desc->emis_kind == AUX_EMIS_STUDENT_T;
+  const int DP = fact ? 0 : pick_dp(d);
 
   aux_model* m = new (std::nothrow) aux_model();
   if (!m) return AUX_E_OOM;
@@ -278,6 +353,12 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
   m->stream = (cudaStream_t)stream;
   m->esz = desc->dtype == AUX_F32 ? sizeof(float) : sizeof(double);
   cudaGetDevice(&m->device);
+  if (fact) {
+    const int rc = fact_init(m, desc, Ryinv);
+    if (rc) { release(m); return rc; }
+    *out = m;
+    return AUX_OK;
+  }
   m->ops = desc->dtype == AUX_F32 ? aux_ops_f32(DP) : aux_ops_f64(DP);
   if (!m->ops) { release(m); return AUX_E_UNSUPPORTED; }
 
@@ -330,12 +411,14 @@ int aux_kalman_step(aux_model* m, void* x, int32_t n_iters, uint64_t iter0,
   if (!m || !x || n_iters < 0) return AUX_E_INVALID_ARG;
   m->stream = (cudaStream_t)stream;
   if (n_iters == 0) return AUX_OK;
+  if (m->fact) return aux_fact_kalman_step(m, x, n_iters, iter0, accept_count, log_alpha, m->stream);
   return m->ops->kalman_step(m, x, n_iters, iter0, accept_count, log_alpha, m->stream);
 }
 
 int aux_loglik(aux_model* m, const void* ytilde, double* logZ, void* mf, void* Pf, void* stream) {
   if (!m || !ytilde || !logZ) return AUX_E_INVALID_ARG;
   m->stream = (cudaStream_t)stream;
+  if (m->fact) return Pf ? AUX_E_UNSUPPORTED : aux_fact_loglik(m, ytilde, logZ, mf, m->stream);
   return m->ops->loglik(m, ytilde, logZ, mf, Pf, m->stream);
 }
 
@@ -343,6 +426,7 @@ int aux_sample_path(aux_model* m, const void* ytilde, const void* eps, uint64_t 
                     void* xstar, double* logZ, void* stream) {
   if (!m || !ytilde || !xstar) return AUX_E_INVALID_ARG;
   m->stream = (cudaStream_t)stream;
+  if (m->fact) return aux_fact_sample_path(m, ytilde, eps, iteration, xstar, logZ, m->stream);
   return m->ops->sample_path(m, ytilde, eps, iteration, xstar, logZ, m->stream);
 }
 
@@ -355,6 +439,7 @@ constexpr int kCovBlockLen = 4;
 int aux_set_mode(aux_model* m, int32_t mode) {
   if (!m || (mode != AUX_MODE_PER_CHAIN && mode != AUX_MODE_SHARED_COV && mode != AUX_MODE_CACHED_COV))
     return AUX_E_INVALID_ARG;
+  if (m->fact) { m->mode = mode; return AUX_OK; }   // the factorised path has one execution
   if (mode != AUX_MODE_PER_CHAIN && !m->tab) {
     const size_t es = m->esz, DD = (size_t)m->DP * m->DP;
     m->Lc = 1;   // the largest divisor of the means block length that is <= kCovBlockLen
@@ -386,7 +471,7 @@ int aux_set_proposal(aux_model* m, int32_t order) {
   if (!m || (order != AUX_PROPOSAL_FIRST_ORDER && order != AUX_PROPOSAL_SECOND_ORDER))
     return AUX_E_INVALID_ARG;
   if (order == AUX_PROPOSAL_SECOND_ORDER) {
-    if (!m->diag_hess) return AUX_E_UNSUPPORTED;
+    if (!m->diag_hess || m->fact) return AUX_E_UNSUPPORTED;
     if (!m->rho) {
       const size_t path = (size_t)m->C * m->T * m->d * m->esz;
       int rc = dev_alloc(m, &m->rho, path);
@@ -436,6 +521,7 @@ int aux_get_delta(aux_model* m, double* delta) {
 
 int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {
   if (!m || !desc) return AUX_E_INVALID_ARG;
+  if (m->fact) return AUX_E_UNSUPPORTED;
   if (desc->dtype != m->dtype || desc->d_x != m->d || desc->T != m->T || desc->n_chains != m->C ||
       desc->emis_kind != m->emis || (desc->y_per_chain ? 1 : 0) != m->y_per_chain)
     return AUX_E_INVALID_ARG;
@@ -468,7 +554,7 @@ int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {
 int aux_loglik_grad(aux_model* m, const void* ytilde, double* logZ, double* g_mu, double* g_Phi,
                     double* g_cholSigma, double* g_delta, void* stream) {
   if (!m || !ytilde || !g_mu || !g_Phi || !g_cholSigma || !g_delta) return AUX_E_INVALID_ARG;
-  if (!m->grad_ok) return AUX_E_UNSUPPORTED;
+  if (!m->grad_ok || m->fact) return AUX_E_UNSUPPORTED;
   m->stream = (cudaStream_t)stream;
   const size_t es = m->esz, DP = m->DP, nbC = (size_t)m->C * m->nb;
   int rc = AUX_OK;

@@ -40,6 +40,17 @@ struct aux_model {
   double adapt_target = 0.5, adapt_gain = 1.0;
   double *delta_dev = nullptr;
   int32_t *adapt_count = nullptr;
+  // factorised-prior path (aux_fact.cu): Student-t emission, diagonal F, Q, P0
+  int fact = 0;
+  double nu = 0.0;
+  void *fmodel = nullptr;    // [5][d]: diag F, b, diag Q, diag P0, m0
+  void *flam = nullptr;      // [d][d] inverse scale matrix
+  void *ftab = nullptr;      // [4][T][d]: K', G, sqrt(Sigma), block prefix of G
+  void *fbt = nullptr;       // [2][nb][d]: block products of K' f and of G
+  double *fldb = nullptr;    // [nb][d] sum of log S_t over the block
+  void *fz = nullptr, *fms = nullptr, *fub = nullptr;   // [C][nb][d]
+  double *ffq = nullptr, *flz = nullptr;                 // [C][nb][d]
+  double *fgam = nullptr, *fmh = nullptr;                // [C][T]
   // gradient (aux_loglik_grad): theta constants and lazily allocated smoother buffers
   int grad_ok = 0;           // the model has the SV parameterisation
   double *gconst = nullptr;  // mu, phi, L, Q, Q^{-1}, P0^{-1} (FP64, unpadded)
@@ -95,6 +106,13 @@ struct AuxOps {
   int (*loglik_grad)(aux_model *, const void *yt, double *logZ, double *g_mu, double *g_phi,
                      double *g_L, double *g_delta, cudaStream_t);
 };
+
+int aux_fact_prepare(aux_model *m);
+int aux_fact_kalman_step(aux_model *m, void *x, int n_iters, uint64_t iter0, uint32_t *acc,
+                         double *log_alpha, cudaStream_t st);
+int aux_fact_loglik(aux_model *m, const void *yt, double *logZ, void *mf, cudaStream_t st);
+int aux_fact_sample_path(aux_model *m, const void *yt, const void *eps, uint64_t iter, void *xs,
+                         double *logZ, cudaStream_t st);
 
 const AuxOps *aux_ops_f32(int DP);
 const AuxOps *aux_ops_f64(int DP);

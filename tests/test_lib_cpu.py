@@ -68,6 +68,12 @@ def _desc_kwargs(**over):
     (dict(dtype=5), 1),
     (dict(d_x=33, m0=np.zeros(33), P0=np.eye(33), F=np.eye(33), b=np.zeros(33), Q=np.eye(33),
           y=np.zeros((8, 33)), R_y=np.eye(33)), 7),            # beyond the built sizes
+    (dict(emis_kind=2, nu=1.0, Q=np.array([[0.1, 0.02], [0.02, 0.1]])), 7),   # Student-t needs a diagonal prior
+    (dict(emis_kind=2, nu=0.0), 1),                            # Student-t needs nu > 0
+    (dict(emis_kind=2, nu=1.0, R_y=None), 1),                  # and a scale matrix
+    (dict(emis_kind=2, nu=1.0, R_y=np.array([[1.0, 2.0], [2.0, 1.0]])), 2),
+    (dict(emis_kind=2, nu=1.0, d_x=1025, m0=np.zeros(1025), P0=np.eye(1025), F=np.eye(1025),
+          b=np.zeros(1025), Q=np.eye(1025), y=np.zeros((8, 1025)), R_y=np.eye(1025)), 7),
 ])
 def test_init_rejects_bad_descriptions_on_host(lib, over, code):
     with pytest.raises(lib.AuxError) as e:
