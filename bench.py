@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--ess-iters", type=int, default=5000,
                     help="post-burn-in iterations of the ESS / ESJD run (0 = skip)")
     ap.add_argument("--ess-burn", type=int, default=500)
+    ap.add_argument("--spatial-only", action="store_true",
+                    help="run only the lattice-model line (Section 4.3) and print it")
     ap.add_argument("--cpu-sample-chains", type=int, default=0,
                     help="chain-steps in the CPU baseline sample (0 = 2 per core)")
     return ap.parse_args()
@@ -177,7 +179,7 @@ KERNEL_NAMES = {
                   "backward": "k_sample_backward", "mh": "k_mh + k_commit", "linearise": "k_linearise"},
     "table": {"reduce": "k_mf_reduce", "apply": "k_mf_apply", "scan": "k_mean_cross",
               "backward": "k_mean_cross + k_mb_apply", "mh": "k_mh + k_commit",
-              "cov_reduce": "k_cov_reduce", "cov_scan": "k_cov_scan_level",
+              "cov_reduce": "k_cov_reduce", "cov_scan": "k_cov_scan_level_mw",
               "cov_apply": "k_cov_apply", "cov_products": "k_cov_products"},
 }
 
@@ -377,6 +379,41 @@ def config_of(name, w, block_len, nb):
 
 
 # --------------------------------------------------------------------------- GPU arm
+def run_spatial(args, flush, stream):
+    """The lattice model of Section 4.3 (factorised prior, Student-t emission, d = 64,
+    T = 1024, one chain as in the paper): delta adapted on the device to 50 %
+    acceptance during warm-up, then frozen; time per MH iteration."""
+    import torch
+    from paper_2303_00301_gb300 import AuxKalman
+    from paper_2303_00301_gb300 import workloads as W
+    wls = W.spatio_temporal(side=8, T=1024, n_chains=1, delta=0.05)
+    ss = AuxKalman(wls, dtype="f32")
+    xsp = torch.tensor(wls.x_init, dtype=torch.float32, device="cuda")
+    ss.adapt_delta(True, target=0.5, gain=1.0)
+    ss.step(xsp, 400, iter0=0)
+    ss.adapt_delta(False)
+    accs = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ss.step(xsp, 5, iter0=400)
+    torch.cuda.synchronize()
+    n_sp = max(args.steps, 50)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(n_sp)]
+    for k in range(n_sp):
+        flush.zero_()
+        evs[k][0].record(stream)
+        ss.step(xsp, 1, iter0=405 + k, accept_count=accs)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms_sp = sum(a.elapsed_time(b) for a, b in evs) / n_sp
+    out = {"workload": "spatio_temporal_8x8_T1024_C1 (Section 4.3, Student-t nu = 1)",
+           "ms_per_iteration": ms_sp, "value": wls.T / (ms_sp / 1e3), "unit": UNIT,
+           "delta": ss.delta(), "accept_rate": accs.item() / n_sp,
+           "paper_ms_per_iteration": 0.52,
+           "paper_hardware": "RTX 3090, JAX (another machine and software: context only)"}
+    ss.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -487,37 +524,9 @@ def run_ours(args):
         so.close()
         others["cached_delta_adaptation"] = r
 
-    # the lattice model of Section 4.3 (factorised prior, Student-t emission, d = 64,
-    # T = 1024, one chain as in the paper): delta adapted on the device to 50 %
-    # acceptance during warm-up, then frozen; time per MH iteration
     spatial = None
     if not args.headline_only and rank == 0:
-        from paper_2303_00301_gb300 import workloads as W
-        wls = W.spatio_temporal(side=8, T=1024, n_chains=1, delta=0.05)
-        ss = AuxKalman(wls, dtype="f32")
-        xsp = torch.tensor(wls.x_init, dtype=torch.float32, device="cuda")
-        ss.adapt_delta(True, target=0.5, gain=1.0)
-        ss.step(xsp, 400, iter0=0)
-        ss.adapt_delta(False)
-        accs = torch.zeros(1, dtype=torch.int32, device="cuda")
-        ss.step(xsp, 5, iter0=400)
-        torch.cuda.synchronize()
-        n_sp = max(args.steps, 50)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(n_sp)]
-        for k in range(n_sp):
-            flush.zero_()
-            evs[k][0].record(stream)
-            ss.step(xsp, 1, iter0=405 + k, accept_count=accs)
-            evs[k][1].record(stream)
-        torch.cuda.synchronize()
-        ms_sp = sum(a.elapsed_time(b) for a, b in evs) / n_sp
-        spatial = {"workload": "spatio_temporal_8x8_T1024_C1 (Section 4.3, Student-t nu = 1)",
-                   "ms_per_iteration": ms_sp, "value": wls.T / (ms_sp / 1e3), "unit": UNIT,
-                   "delta": ss.delta(), "accept_rate": accs.item() / n_sp,
-                   "paper_ms_per_iteration": 0.52,
-                   "paper_hardware": "RTX 3090, JAX (another machine and software: context only)"}
-        ss.close()
+        spatial = run_spatial(args, flush, stream)
 
     # end to end through the public API from pinned host buffers
     x_host = torch.tensor(wl.x_init, dtype=tdt).pin_memory()
@@ -640,6 +649,13 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.spatial_only:
+        import torch
+        from paper_2303_00301_gb300 import build
+        build.build()
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps(run_spatial(args, flush, torch.cuda.current_stream())), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
