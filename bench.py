@@ -405,9 +405,24 @@ def run_spatial(args, flush, stream):
         evs[k][1].record(stream)
     torch.cuda.synchronize()
     ms_sp = sum(a.elapsed_time(b) for a, b in evs) / n_sp
+    # the same iteration replayed from a CUDA graph (iteration index on the device)
+    ss.device_iteration(True, 405 + n_sp)
+    g = ss.capture(xsp, 1, accs)
+    evg = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(n_sp)]
+    for k in range(n_sp):
+        flush.zero_()
+        evg[k][0].record(stream)
+        g.replay()
+        evg[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms_gr = sum(a.elapsed_time(b) for a, b in evg) / n_sp
+    ss.device_iteration(False)
+    del g
     out = {"workload": "spatio_temporal_8x8_T1024_C1 (Section 4.3, Student-t nu = 1)",
-           "ms_per_iteration": ms_sp, "value": wls.T / (ms_sp / 1e3), "unit": UNIT,
-           "delta": ss.delta(), "accept_rate": accs.item() / n_sp,
+           "ms_per_iteration": ms_gr, "launch": "CUDA graph replay", "ms_per_iteration_eager": ms_sp,
+           "value": wls.T / (ms_gr / 1e3), "unit": UNIT,
+           "delta": ss.delta(), "accept_rate": accs.item() / (2 * n_sp),
            "paper_ms_per_iteration": 0.52,
            "paper_hardware": "RTX 3090, JAX (another machine and software: context only)"}
     ss.close()
@@ -444,8 +459,25 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    def timed_steps(step, n):
+        """n steps, L2 flushed before each, every step bracketed by CUDA events
+        on the launching stream; returns the per-step times in ms."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n)]
+        for k in range(n):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step(k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return [e0.elapsed_time(e1) for e0, e1 in ev]
+
     def run_mode(mode, with_clocks, proposal=1, adapt=False):
-        """Warm-up, then args.steps timed steps (L2 flushed before each), per-launch events on."""
+        """Warm-up; one profiled eager pass (per-kernel events: the kernel
+        breakdown and roofline durations); then the timed pass: the MCMC
+        iteration captured once in a CUDA graph (iteration index on the
+        device) and replayed args.steps times; then the same steps eager
+        without events, for comparison."""
         sm = AuxKalman(wl, dtype=w["dtype"], block_len=args.block_len, mode=mode, proposal=proposal)
         if adapt:
             sm.adapt_delta(True, target=0.5, gain=1.0)
@@ -458,48 +490,45 @@ def run_ours(args):
             itm += 1
         torch.cuda.synchronize()
         accm.zero_()
+        B.aux_set_profiling(sm.handle, True)
+        prof_ms = timed_steps(lambda k: sm.step(xm, 1, iter0=itm + k, accept_count=accm, log_alpha=lam),
+                              args.steps)
+        itm += args.steps
+        B.aux_set_profiling(sm.handle, False)
+        prof = B.aux_read_profile(sm.handle)
+        accept_rate_m = accm.float().mean().item() / args.steps
+        # the timed pass
+        sm.device_iteration(True, itm)
+        g = sm.capture(xm, 1, accm, lam)
+        g.replay()                                   # warm the graph up
+        torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         ck = None
         if with_clocks:
             clocks = ClockSampler(local)
             clocks.start()
-        B.aux_set_profiling(sm.handle, True)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        for k in range(args.steps):
-            flush.zero_()
-            evs[k][0].record(stream)
-            sm.step(xm, 1, iter0=itm, accept_count=accm, log_alpha=lam)
-            evs[k][1].record(stream)
-            itm += 1
-        torch.cuda.synchronize()
-        B.aux_set_profiling(sm.handle, False)
-        prof = B.aux_read_profile(sm.handle)
+        step_ms = timed_steps(lambda k: g.replay(), args.steps)
         if with_clocks:
             ck = clocks.stop()
-        step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-        accept_rate_m = accm.float().mean().item() / args.steps
+        itm = sm.iteration()
+        sm.device_iteration(False)
+        del g
         t_ms = max_over_ranks(sum(step_ms), "cuda", world)
-        # the same steps without the per-launch events (host overhead check)
-        evu = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        for k in range(args.steps):
-            flush.zero_()
-            evu[k][0].record(stream)
-            sm.step(xm, 1, iter0=itm, accept_count=accm, log_alpha=lam)
-            evu[k][1].record(stream)
-            itm += 1
-        torch.cuda.synchronize()
-        unprof_ms = sum(e0.elapsed_time(e1) for e0, e1 in evu) / args.steps
+        eager_ms = timed_steps(lambda k: sm.step(xm, 1, iter0=itm + k, accept_count=accm, log_alpha=lam),
+                               args.steps)
+        itm += args.steps
         res = {"mode": mode, "proposal": "second order" if proposal == 2 else "first order",
                "delta": sm.delta(), "delta_adaptation": bool(adapt),
                "value": world * C * T * args.steps / (t_ms / 1e3), "unit": UNIT,
-               "ms_per_step": t_ms / args.steps, "ms_per_step_without_events": unprof_ms,
+               "ms_per_step": t_ms / args.steps, "launch": "CUDA graph replay",
+               "ms_per_step_eager": sum(eager_ms) / args.steps,
+               "ms_per_step_eager_profiled": sum(prof_ms) / args.steps,
                "step_ms_median": statistics.median(step_ms),
                "accept_rate": accept_rate_m,
                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
-               "gpu_launches": int(sum(v[1] for v in prof.values()))}
+               # the profiled kernels of each step, plus the graph's iteration-counter increment
+               "gpu_launches": int(sum(v[1] for v in prof.values())) + args.steps}
         return sm, xm, lam, itm, prof, ck, res
 
     s, x, la, it, prof, ck, head = run_mode(args.mode, True)
@@ -637,7 +666,8 @@ def run_ours(args):
                 "roofline": roofline, "roofline_lines": lines, "ess": ess,
                 "cpu_baseline": cpu, "clocks": ck,
                 "kernel_ms_per_step": head["kernel_ms_per_step"],
-                "ms_per_step_without_events": head["ms_per_step_without_events"],
+                "launch": head["launch"], "ms_per_step_eager": head["ms_per_step_eager"],
+                "ms_per_step_eager_profiled": head["ms_per_step_eager_profiled"],
                 "accept_rate": accept_rate, "status": int(rc),
                 "step_ms_median": head["step_ms_median"], "other_modes": others,
                 "spatio_temporal": spatial}

@@ -230,6 +230,20 @@ int aux_set_proposal(aux_model *m, int32_t order);
  * Errors: INVALID_ARG, OOM, CUDA. */
 int aux_set_delta_adaptation(aux_model *m, int32_t enable, double target, double gain);
 
+/* Keep the MCMC iteration index on the device, so that a sequence of
+ * aux_kalman_step calls can be captured once in a CUDA graph and replayed:
+ * while enabled, iteration k of a call draws its Philox streams with the
+ * device counter's value (instead of iter0 + k) and the call's last launch of
+ * each iteration adds 1 to it. Enabling sets the counter to `start`
+ * (synchronises). Replays of a captured call are then the same steps as the
+ * eager calls with iter0 = start, start + n_iters, ... aux_sample_path keeps
+ * its explicit iteration. Errors: INVALID_ARG, OOM, CUDA. */
+int aux_set_device_iteration(aux_model *m, int32_t enable, uint64_t start);
+
+/* The device counter's current value (synchronises). Errors: INVALID_ARG (not
+ * enabled yet), CUDA. */
+int aux_get_device_iteration(aux_model *m, uint64_t *iteration);
+
 /* The handle's current delta (the adapted value while adaptation is on;
  * synchronises the handle's last stream then). Errors: INVALID_ARG, CUDA. */
 int aux_get_delta(aux_model *m, double *delta);

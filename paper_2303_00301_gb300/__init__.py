@@ -72,6 +72,33 @@ class AuxKalman:
     def delta(self):
         return self.b.aux_get_delta(self.handle)
 
+    def device_iteration(self, enable=True, start=0):
+        """Keep the MCMC iteration on the device (aux_set_device_iteration)."""
+        self.b.aux_set_device_iteration(self.handle, enable, start)
+        self._dev_iter = bool(enable)
+
+    def iteration(self):
+        return self.b.aux_get_device_iteration(self.handle)
+
+    def capture(self, x, n_iters=1, accept_count=None, log_alpha=None):
+        """Capture ``n_iters`` MCMC iterations on ``x`` into a CUDA graph.
+
+        Turns the device iteration counter on (keeping its value if it is on
+        already, else starting at 0); every ``replay()`` of the returned graph
+        then runs the next ``n_iters`` iterations. Warm the handle up with one
+        eager ``step`` first so that no one-off work (the cached covariance
+        pass) is captured."""
+        import torch
+        if not getattr(self, "_dev_iter", False):
+            self.device_iteration(True, 0)
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(g, stream=s):
+            self.step(x, n_iters, 0, accept_count, log_alpha)
+        torch.cuda.current_stream().wait_stream(s)
+        return g
+
     def close(self):
         if getattr(self, "handle", None) is not None:
             self.b.aux_free_model(self.handle)

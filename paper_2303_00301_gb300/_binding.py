@@ -90,6 +90,10 @@ def _load():
     lib.aux_set_delta_adaptation.restype = ctypes.c_int
     lib.aux_get_delta.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     lib.aux_get_delta.restype = ctypes.c_int
+    lib.aux_set_device_iteration.argtypes = [vp, ctypes.c_int32, ctypes.c_uint64]
+    lib.aux_set_device_iteration.restype = ctypes.c_int
+    lib.aux_get_device_iteration.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.aux_get_device_iteration.restype = ctypes.c_int
     lib.aux_loglik_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.aux_loglik_grad.restype = ctypes.c_int
     lib.aux_set_model_params.argtypes = [vp, ctypes.POINTER(aux_model_desc)]
@@ -190,6 +194,16 @@ def aux_set_delta_adaptation(handle, enable, target=0.5, gain=1.0):
 def aux_get_delta(handle):
     out = ctypes.c_double(0.0)
     _check(LIB.aux_get_delta(handle, ctypes.byref(out)), "aux_get_delta")
+    return out.value
+
+
+def aux_set_device_iteration(handle, enable, start=0):
+    _check(LIB.aux_set_device_iteration(handle, 1 if enable else 0, int(start)), "aux_set_device_iteration")
+
+
+def aux_get_device_iteration(handle):
+    out = ctypes.c_uint64(0)
+    _check(LIB.aux_get_device_iteration(handle, ctypes.byref(out)), "aux_get_device_iteration")
     return out.value
 
 

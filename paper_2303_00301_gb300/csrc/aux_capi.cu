@@ -511,6 +511,29 @@ int aux_set_delta_adaptation(aux_model* m, int32_t enable, double target, double
   return AUX_OK;
 }
 
+int aux_set_device_iteration(aux_model* m, int32_t enable, uint64_t start) {
+  if (!m) return AUX_E_INVALID_ARG;
+  if (enable) {
+    if (!m->iter_dev) {
+      const int rc = dev_alloc(m, (void**)&m->iter_dev, sizeof(uint64_t));
+      if (rc) { m->iter_dev = nullptr; return rc; }
+    }
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess ||
+        cudaMemcpy(m->iter_dev, &start, sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess)
+      return AUX_E_CUDA;
+  }
+  m->dev_iter = enable ? 1 : 0;
+  return AUX_OK;
+}
+
+int aux_get_device_iteration(aux_model* m, uint64_t* iteration) {
+  if (!m || !iteration || !m->iter_dev) return AUX_E_INVALID_ARG;
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) return AUX_E_CUDA;
+  return cudaMemcpy(iteration, m->iter_dev, sizeof(uint64_t), cudaMemcpyDeviceToHost) == cudaSuccess
+             ? AUX_OK
+             : AUX_E_CUDA;
+}
+
 int aux_get_delta(aux_model* m, double* delta) {
   if (!m || !delta) return AUX_E_INVALID_ARG;
   if (!m->adapt) { *delta = m->delta; return AUX_OK; }

@@ -39,7 +39,13 @@ template <typename Real> struct FP {
   const Real* y;                     // [T][d] or [C][T][d]
   const uint8_t* mask;               // [T] or null
   const double* delta_dev;           // adapted delta, or null
+  const uint64_t* iter_dev;          // MCMC iteration on the device, or null
 };
+
+template <typename Real>
+__device__ __forceinline__ uint64_t fiter(const FP<Real>& p, uint64_t iter) {
+  return p.iter_dev ? *p.iter_dev : iter;
+}
 
 template <typename Real>
 __device__ __forceinline__ void fp_refresh(FP<Real>& p) {
@@ -144,7 +150,7 @@ __global__ void k_fl_lin(FP<Real> p, const Real* __restrict__ x, Real* __restric
   if (obs) g = st_grad<Real>(p, xr, yr, es, vs, lane);
   for (int i = lane; i < p.d; i += 32) {
     const Real vi = obs ? vs[i] : (Real)0;
-    const Real ep = philox_normal<Real>(p.seed, (uint32_t)c, iter, PURPOSE_AUX, (uint32_t)t, i);
+    const Real ep = philox_normal<Real>(p.seed, (uint32_t)c, fiter(p, iter), PURPOSE_AUX, (uint32_t)t, i);
     const Real ui = xr[i] + p.sqrt_r * ep;
     u[ct * p.d + i] = ui;
     v[ct * p.d + i] = vi;
@@ -277,7 +283,7 @@ __global__ void k_fm_apply(FP<Real> p, const Real* __restrict__ tab, const doubl
     const Real mpn = (t < p.nT - 1) ? fma(f, m, b) : (Real)0;
     if (epi) {
       const Real ep = eps ? eps[idx]
-                          : philox_normal<Real>(p.seed, (uint32_t)it.c, iter, PURPOSE_BACKWARD, (uint32_t)t, it.i);
+                          : philox_normal<Real>(p.seed, (uint32_t)it.c, fiter(p, iter), PURPOSE_BACKWARD, (uint32_t)t, it.i);
       const Real u = m - tab[FG * TD + (long)t * p.d + it.i] * mpn + tab[FLS * TD + (long)t * p.d + it.i] * ep;
       U[idx] = u;
       ubar = fma(tab[FGP * TD + (long)t * p.d + it.i], u, ubar);
@@ -327,7 +333,7 @@ __global__ void k_fm_mh(FP<Real> p, const double* __restrict__ mh, const double*
     for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) la += red[w];
     int st = 0;
     if (!isfinite(la)) st |= ST_NONFINITE;
-    const uint4 r = philox_word(p.seed, (uint32_t)c, iter, PURPOSE_MH, 0, 0);
+    const uint4 r = philox_word(p.seed, (uint32_t)c, fiter(p, iter), PURPOSE_MH, 0, 0);
     const double lu = log(u01<double>(r.x));
     const int acc = (st == 0) && (lu < la);
     accept[c] = acc;
@@ -378,6 +384,7 @@ struct Fact {
     p.y = (const Real*)m->y;
     p.mask = m->mask;
     p.delta_dev = m->adapt ? m->delta_dev : nullptr;
+    p.iter_dev = nullptr;
     return p;
   }
   static int grid(long n, int bs) { return (int)((n + bs - 1) / bs); }
@@ -418,7 +425,8 @@ struct Fact {
 
   static int kalman_step(aux_model* m, void* xv, int n_iters, uint64_t iter0, uint32_t* acc,
                          double* log_alpha, cudaStream_t st) {
-    const FP<Real> p = params(m);
+    FP<Real> p = params(m);
+    if (m->dev_iter) p.iter_dev = m->iter_dev;
     Real* x = (Real*)xv;
     const long CT = (long)m->C * m->T, n = CT * m->d;
     for (int it = 0; it < n_iters; ++it) {
@@ -442,6 +450,7 @@ struct Fact {
         if (m->adapt)
           k_adapt_delta<<<1, 256, 0, st>>>(m->la_all, m->C, m->delta_dev, m->adapt_count, m->adapt_target,
                                            m->adapt_gain);
+        if (m->dev_iter) k_iter_next<<<1, 1, 0, st>>>(m->iter_dev);
       }
     }
     return ok(cudaGetLastError());

@@ -40,6 +40,9 @@ struct aux_model {
   double adapt_target = 0.5, adapt_gain = 1.0;
   double *delta_dev = nullptr;
   int32_t *adapt_count = nullptr;
+  // device-resident MCMC iteration (aux_set_device_iteration): replayable steps
+  int dev_iter = 0;
+  uint64_t *iter_dev = nullptr;
   // factorised-prior path (aux_fact.cu): Student-t emission, diagonal F, Q, P0
   int fact = 0;
   double nu = 0.0;

@@ -49,7 +49,17 @@ template <typename Real> struct KP {
   int order;                                 // proposal: 1 first order, 2 second order
   const Real* rho;   // [C][T][d] diagonal pseudo-observation variance (second order), or null: r
   const double* delta_dev;   // adapted delta on the device, or null: r and sqrt_r as given
+  const uint64_t* iter_dev;  // MCMC iteration on the device (graph replay), or null: as passed
 };
+
+// the MCMC iteration that keys the Philox streams of this step
+template <typename Real>
+__device__ __forceinline__ uint64_t iter_of(const KP<Real>& p, uint64_t iter) {
+  return p.iter_dev ? *p.iter_dev : iter;
+}
+
+// advance the device iteration counter (last launch of an MCMC iteration)
+static __global__ void k_iter_next(uint64_t* iter_dev) { *iter_dev += 1; }
 
 // With on-device delta adaptation the kernels take r = delta / 2 from device
 // memory (written by k_adapt_delta of the previous iteration).
@@ -143,7 +153,7 @@ __global__ void k_linearise(KP<Real> p, const Real* __restrict__ x, Real* __rest
         vi = acc;
       }
     }
-    const Real e = philox_normal<Real>(p.seed, (uint32_t)c, iter, PURPOSE_AUX, (uint32_t)t, i);
+    const Real e = philox_normal<Real>(p.seed, (uint32_t)c, iter_of(p, iter), PURPOSE_AUX, (uint32_t)t, i);
     const Real ui = xr[i] + p.sqrt_r * e;
     u[idx] = ui;
     v[idx] = vi;
@@ -722,7 +732,7 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
     Real ei = 0;
     if (lane < p.d && !(a.flags & APPLY_SMOOTH)) {
       ei = a.eps ? a.eps[((long)c * p.nT + t) * p.d + lane]
-                 : philox_normal<Real>(p.seed, (uint32_t)c, a.iter, PURPOSE_BACKWARD, (uint32_t)t, lane);
+                 : philox_normal<Real>(p.seed, (uint32_t)c, iter_of(p, a.iter), PURPOSE_BACKWARD, (uint32_t)t, lane);
     }
     __syncwarp();
     if (act) veps[lane] = ei;
@@ -1094,7 +1104,7 @@ __global__ void k_mh(KP<Real> p, const double* __restrict__ mh_part,
     for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) la += red[w];
     int st = p.status_iter[c];
     if (!isfinite(la)) st |= ST_NONFINITE;
-    const uint4 r = philox_word(p.seed, (uint32_t)c, iter, PURPOSE_MH, 0, 0);
+    const uint4 r = philox_word(p.seed, (uint32_t)c, iter_of(p, iter), PURPOSE_MH, 0, 0);
     const double lu = log(u01<double>(r.x));
     const int acc = (st == 0) && (lu < la);
     accept[c] = acc;

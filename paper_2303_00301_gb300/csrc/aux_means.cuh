@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_reduce(KP<Real> p
           }
           if (!obs) vi = 0;
           if (lane < p.d && valid[j]) {
-            const Real ep = philox_normal<Real>(p.seed, (uint32_t)cidx[j], a.iter, PURPOSE_AUX, (uint32_t)t, lane);
+            const Real ep = philox_normal<Real>(p.seed, (uint32_t)cidx[j], iter_of(p, a.iter), PURPOSE_AUX, (uint32_t)t, lane);
             const Real ui = xi[j] + p.sqrt_r * ep;
             yti[j] = ui + p.r * vi;
             a.u[ct * p.d + lane] = ui;
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_apply(KP<Real> p,
           ei[j] = 0;
           if (lane < p.d && valid[j])
             ei[j] = a.eps ? eg[j]
-                          : philox_normal<Real>(p.seed, (uint32_t)cidx[j], a.iter, PURPOSE_BACKWARD, (uint32_t)t, lane);
+                          : philox_normal<Real>(p.seed, (uint32_t)cidx[j], iter_of(p, a.iter), PURPOSE_BACKWARD, (uint32_t)t, lane);
         }
         __syncwarp();
 #pragma unroll

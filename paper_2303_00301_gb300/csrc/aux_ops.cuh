@@ -42,6 +42,7 @@ KP<Real> make_kp(const aux_model* m) {
   p.order = m->order;
   p.rho = nullptr;
   p.delta_dev = m->adapt ? m->delta_dev : nullptr;
+  p.iter_dev = nullptr;   // set by the MCMC step only (aux_set_device_iteration)
   return p;
 }
 
@@ -101,6 +102,7 @@ struct Ops {
     if (m->adapt)
       k_adapt_delta<<<1, 256, 0, st>>>(m->la_all, m->C, m->delta_dev, m->adapt_count, m->adapt_target,
                                        m->adapt_gain);
+    if (m->dev_iter) k_iter_next<<<1, 1, 0, st>>>(m->iter_dev);
   }
 
 
@@ -236,7 +238,8 @@ struct Ops {
 
   static int kalman_step_means(aux_model* m, void* xv, int n_iters, uint64_t iter0, uint32_t* acc,
                                double* log_alpha, cudaStream_t st) {
-    const KP<Real> p = make_kp<Real>(m);
+    KP<Real> p = make_kp<Real>(m);
+    if (m->dev_iter) p.iter_dev = m->iter_dev;
     Real* x = (Real*)xv;
     for (int it = 0; it < n_iters; ++it) {
       const uint64_t iter = iter0 + (uint64_t)it;
@@ -266,7 +269,8 @@ struct Ops {
       if (m->order != 1) return AUX_E_UNSUPPORTED;
       return kalman_step_means(m, xv, n_iters, iter0, acc, log_alpha, st);
     }
-    const KP<Real> p = make_kp<Real>(m);
+    KP<Real> p = make_kp<Real>(m);
+    if (m->dev_iter) p.iter_dev = m->iter_dev;
     const bool second = m->order == 2;
     KP<Real> pf = p, pr = p;   // forward and reverse filters: the pseudo-observation variances
     if (second) { pf.rho = (const Real*)m->rho; pr.rho = (const Real*)m->rhos; }
