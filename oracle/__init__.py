@@ -14,4 +14,6 @@ Modules:
   mcmc    one auxiliary Kalman MH step (Alg. 2, first-order, Gaussian
           dynamics) with the direct-formula acceptance ratio.
   dense   brute-force stacked-path Gaussian (Eq. (2.2)) for tiny T·d.
+  bridging  divide-and-conquer (bridging) pathwise sampler (Section 2.4.2,
+          Appendix A.2.3).
 """
