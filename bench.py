@@ -43,7 +43,7 @@ N_SM = 152
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sv_d30_T1024", choices=sorted(WORKLOADS))
@@ -138,6 +138,16 @@ def scan_rounds(nb):
     return len(offs), sum(nb - o for o in offs)
 
 
+def bridge_tree_shape(T):
+    """(levels J, internal nodes NN) of the dyadic tree over T - 1 unit intervals."""
+    cnt, levels, nodes = T - 1, 0, 0
+    while cnt > 1:
+        cnt = (cnt + 1) // 2
+        levels += 1
+        nodes += cnt
+    return levels, nodes
+
+
 def kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz):
     """Algorithmic work of one launch of a kernel kind, averaged over the launches
     of one MH step: (flops, HBM bytes). Bytes count what the algorithm must move
@@ -158,8 +168,21 @@ def kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz):
         return (C * T * (means_flops_per_step("apply", d, fdiag, True) +
                          means_flops_per_step("apply", d, fdiag, False)) / 2,
                 (4 * tab + 2 * vec + tab + vec) / 2)
-    if kind == "backward":  # G table, U in, x* out, MH inputs x, u, v, y in, ytilde* out
-        return C * T * 2.0 * d ** 2, tab + 7 * vec
+    if kind == "backward":  # G table, U in, x* out, MH inputs x, u, v, y in, ytilde* out (2 launches)
+        return C * T * 2.0 * d ** 2 / 2, (tab + 7 * vec) / 2
+    if kind == "bridge":
+        # divide-and-conquer sampler, 2 J + 2 launches per step: node offsets up the tree
+        # (E_l once per node; g_l, g_r in, g out per chain-node; 2 d^2), the two ends, the
+        # split points down the tree (G, Gamma, chol V once per node; x_k, x_m, g, g_r in,
+        # x_l out per chain-node; 5 d^2) and the MH terms (x*, x, u, v, y in, ytilde* out)
+        levels, nodes = bridge_tree_shape(T)
+        byt = (4 * nodes * d * d + 8 * C * nodes * d) * esz + 6 * vec
+        return C * nodes * 7.0 * d ** 2 / (2 * levels + 2), byt / (2 * levels + 2)
+    if kind == "bridge_tree":
+        # leaf covariances LS LS^T (d^3 per step) and, per node, E_l L_r, E_l E_r,
+        # T1 E_l^T, chol(L), G by two triangular solves, Gamma, V and chol(V)
+        levels, nodes = bridge_tree_shape(T)
+        return ((T - 1) * d ** 3 + nodes * (6 + 1.0 / 3 + 2 + 4 + 1.0 / 3) * d ** 3) / (levels + 1), None
     if kind == "cov_reduce":
         return T * reduce_flops_per_step(d, fdiag), None
     if kind == "cov_scan":
@@ -170,7 +193,7 @@ def kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz):
     if kind == "cov_products":
         # composition of the covariance-block products (2 per covariance block) and the
         # prefix fix-up of G_s..G_{t-1} (one product per step)
-        return (2 * nbc + T) * 2.0 * d ** 3, None
+        return (2 * nbc + T) * 2.0 * d ** 3 / 2, None   # 2 launches
     return None, None
 
 
@@ -180,7 +203,8 @@ KERNEL_NAMES = {
     "table": {"reduce": "k_mf_reduce", "apply": "k_mf_apply", "scan": "k_mean_cross",
               "backward": "k_mean_cross + k_mb_apply", "mh": "k_mh + k_commit",
               "cov_reduce": "k_cov_reduce", "cov_scan": "k_cov_scan_level_mw",
-              "cov_apply": "k_cov_apply", "cov_products": "k_cov_products"},
+              "cov_apply": "k_cov_apply", "cov_products": "k_cov_products",
+              "bridge": "k_bg_up + k_bx_root + k_bx_down + k_b_mh", "bridge_tree": "k_br_leaf + k_br_node"},
 }
 
 
@@ -274,18 +298,33 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv") \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None
+        if os.path.isdir(os.path.join(ROOT, "gpurun_out")):
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        else:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv", prefix="clocks_")
+            os.close(fd)
 
     def start(self):
         try:
-            self.out = open(self.path, "w") if self.path else subprocess.PIPE
+            self.out = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-i", str(self.gpu), "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL,
+                 "-i", str(self.gpu), "-lms", "100"], stdout=self.out, stderr=subprocess.DEVNULL,
                 text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # the timed region starts once the sampler is producing rows; the rows
+        # taken before it are left out of the summary
+        t0 = time.time()
+        self.skip = 0
+        while time.time() - t0 < 5.0 and self.proc.poll() is None:
+            with open(self.path) as f:
+                self.skip = f.read().count("\n")
+            if self.skip >= 1:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -296,10 +335,11 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        if self.path:
-            self.out.close()
-            out = open(self.path).read()
+        self.out.close()
+        out = open(self.path).read()
         rows = [r.split(",") for r in (out or "").strip().splitlines() if r.count(",") >= 8]
+        if len(rows) > self.skip:
+            rows = rows[self.skip:]
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
@@ -472,13 +512,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         return [e0.elapsed_time(e1) for e0, e1 in ev]
 
-    def run_mode(mode, with_clocks, proposal=1, adapt=False):
+    def run_mode(mode, with_clocks, proposal=1, adapt=False, sampler="scan"):
         """Warm-up; one profiled eager pass (per-kernel events: the kernel
         breakdown and roofline durations); then the timed pass: the MCMC
         iteration captured once in a CUDA graph (iteration index on the
         device) and replayed args.steps times; then the same steps eager
         without events, for comparison."""
-        sm = AuxKalman(wl, dtype=w["dtype"], block_len=args.block_len, mode=mode, proposal=proposal)
+        sm = AuxKalman(wl, dtype=w["dtype"], block_len=args.block_len, mode=mode, proposal=proposal,
+                       sampler=sampler)
         if adapt:
             sm.adapt_delta(True, target=0.5, gain=1.0)
         xm = torch.tensor(wl.x_init, dtype=tdt, device="cuda")
@@ -519,6 +560,7 @@ def run_ours(args):
                                args.steps)
         itm += args.steps
         res = {"mode": mode, "proposal": "second order" if proposal == 2 else "first order",
+               "sampler": "divide-and-conquer bridging" if sampler == "bridging" else "(G, U) suffix scan",
                "delta": sm.delta(), "delta_adaptation": bool(adapt),
                "value": world * C * T * args.steps / (t_ms / 1e3), "unit": UNIT,
                "ms_per_step": t_ms / args.steps, "launch": "CUDA graph replay",
@@ -552,6 +594,13 @@ def run_ours(args):
         so, _, _, _, _, _, r = run_mode("cached", False, adapt=True)
         so.close()
         others["cached_delta_adaptation"] = r
+        # the divide-and-conquer (bridging) sampler (Appendix A.2.3) in place of the scan
+        for key, mode in (("cached_bridging", "cached"), ("shared_bridging", "shared"),
+                          ("per_chain_bridging", "per_chain")):
+            so, _, _, _, po, _, r = run_mode(mode, False, sampler="bridging")
+            so.close()
+            others[key] = r
+            profs[key] = po
 
     spatial = None
     if not args.headline_only and rank == 0:
@@ -591,8 +640,9 @@ def run_ours(args):
     Lc = max(c for c in range(1, min(4, L) + 1) if L % c == 0)   # the library's covariance block
     nbc = (T + Lc - 1) // Lc
     dom = max((k for k in prof if prof[k][1]), key=lambda k: prof[k][0])
-    rl = lambda mode, kind, path: roofline_line(mode, kind, profs[mode], w, d, T, C, nb, nbc, fdiag,
-                                                esz, peaks, args.steps, path)
+    def rl(mode, kind, path, key=None):
+        return roofline_line(mode, kind, profs[key or mode], w, d, T, C, nb, nbc, fdiag, esz, peaks,
+                             args.steps, path)
     roofline = rl(args.mode, dom, f"dominant kernel of the {args.mode} mode")
     lines = {}
     if "per_chain" in profs:
@@ -605,6 +655,12 @@ def run_ours(args):
         if cov_kinds:
             ck_dom = max(cov_kinds, key=lambda k: profs["shared"][k][0])
             lines["covariance_pass"] = rl("shared", ck_dom, "covariance (Riccati) pass, once per call")
+    if "cached_bridging" in profs:
+        lines["bridging_sampler"] = rl("cached", "bridge", "divide-and-conquer sampler: offsets up, "
+                                       "split points down, MH terms (tables shared)", "cached_bridging")
+    if "shared_bridging" in profs:
+        lines["bridging_tree"] = rl("shared", "bridge_tree", "divide-and-conquer tree matrices, once "
+                                    "per covariance pass", "shared_bridging")
 
     # ESS and ESJD of the headline mode from a long run (outside the timed region)
     ess = None

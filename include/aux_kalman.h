@@ -213,6 +213,31 @@ int aux_set_mode(aux_model *m, int32_t mode);
  * Errors: INVALID_ARG (unknown order), UNSUPPORTED (non-diagonal Hessian), OOM. */
 int aux_set_proposal(aux_model *m, int32_t order);
 
+/* Pathwise samplers (aux_set_sampler) */
+#define AUX_SAMPLER_SCAN     0  /* (G, U) suffix scan, Eqs. (A.14)-(A.15), Proposition A.1 (default) */
+#define AUX_SAMPLER_BRIDGING 1  /* divide-and-conquer bridging sampler, Section 2.4.2, Appendix A.2.3 */
+
+/* Choose how aux_kalman_step and aux_sample_path draw the path from the
+ * smoothing law of the auxiliary LGSSM once the filter has run. Both samplers
+ * draw from the same law in O(log T) depth; they map the noise differently,
+ * so the same (seed, chain, iteration) gives different paths.
+ * AUX_SAMPLER_SCAN composes the backward conditionals (G_t, U_t) with a
+ * suffix scan. AUX_SAMPLER_BRIDGING builds the dyadic tree of the backward
+ * conditionals p(x_k | x_m, y) = N(E x_m + g, L) over the intervals
+ * [a 2^j, (a+1) 2^j] (clipped to T - 1), with the bridge
+ * p(x_l | x_k, x_m, y) = N(G x_k + Gamma x_m + w, V) at each split point
+ * l = (2a+1) 2^(j-1), then draws x_{T-1} from the last filtering law, x_0 given
+ * x_{T-1}, and the split points level by level from the root down; state t
+ * takes the t-th normal of the backward stream (or row t of a given eps)
+ * whatever its level. In the table modes the tree's matrices are built once
+ * per covariance pass and shared by all chains; in AUX_MODE_PER_CHAIN every
+ * chain has its own tree (both proposals). Not available for the
+ * factorised-prior model (UNSUPPORTED). The switch allocates the tree for the
+ * current mode, and aux_set_mode for a later mode (may return OOM): per
+ * chain about 5 C (T-1) DP^2 elements, shared 6 (T-1) DP^2.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM. */
+int aux_set_sampler(aux_model *m, int32_t sampler);
+
 /* On-line adaptation of delta to a target acceptance rate, on the device.
  * The paper tunes delta to a target acceptance but states no rule (Section 4);
  * this one is a Robbins-Monro recursion on log delta shared by the handle's
@@ -275,7 +300,9 @@ int aux_get_status(aux_model *m, int32_t *per_chain_status);
 #define AUX_PROFILE_COV_SCAN     11 /* covariance pass: one Hillis-Steele round */
 #define AUX_PROFILE_COV_APPLY    12 /* covariance pass: in-block filter and per-step tables */
 #define AUX_PROFILE_COV_PRODUCTS 13 /* covariance pass: block products of the means partition */
-#define AUX_PROFILE_KINDS        14
+#define AUX_PROFILE_BRIDGE_TREE  14 /* bridging sampler: leaf covariances and tree matrices, all levels */
+#define AUX_PROFILE_BRIDGE       15 /* bridging sampler: node offsets, the two ends, split points, MH terms */
+#define AUX_PROFILE_KINDS        16
 
 /* Turn per-launch timing on or off for this handle: while on, every kernel
  * launch is bracketed by two CUDA events recorded on its own stream. */

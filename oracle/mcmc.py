@@ -37,6 +37,7 @@ pseudo-observation covariance).
 """
 import numpy as np
 
+from . import bridging
 from . import kalman
 from . import philox
 
@@ -133,7 +134,18 @@ def _log_obs(z, obs, R):
     return sum(kalman.mvn_logpdf(obs[t], z[t], R) for t in range(len(z)))
 
 
-def aux_step(x, model, delta, eps_aux, eps_back, log_u):
+def _draw(kf, F, b, Q, eps, sampler):
+    """A path from the smoothing law: the RTS sampler (Appendix A.1) or the
+    divide-and-conquer sampler (Appendix A.2.3); both exact, so the MH ratio
+    below is the same for either."""
+    if sampler == "rts":
+        return kalman.rts_sample(kf, F, b, Q, eps)
+    if sampler == "bridging":
+        return bridging.dnc_sample(kf, F, b, Q, eps)
+    raise ValueError(sampler)
+
+
+def aux_step(x, model, delta, eps_aux, eps_back, log_u, sampler="rts"):
     """One auxiliary Kalman MH step from state x [T, d].
 
     model: dict with m0, P0, F, b, Q and 'emission' (an emission object).
@@ -148,7 +160,7 @@ def aux_step(x, model, delta, eps_aux, eps_back, log_u):
     v = em.grad(x)
     yt = u + 0.5 * delta * v
     kf = kalman.kalman_filter(yt, m0, P0, F, b, Q, R)
-    x_star = kalman.rts_sample(kf, F, b, Q, eps_back)
+    x_star = _draw(kf, F, b, Q, eps_back, sampler)
     v_star = em.grad(x_star)
     yt_star = u + 0.5 * delta * v_star
     kf_star = kalman.kalman_filter(yt_star, m0, P0, F, b, Q, R)
@@ -187,7 +199,7 @@ def second_order_obs(x, u, model, delta):
     return om, Om
 
 
-def aux_step_second_order(x, model, delta, eps_aux, eps_back, log_u):
+def aux_step_second_order(x, model, delta, eps_aux, eps_back, log_u, sampler="rts"):
     """One auxiliary Kalman MH step with the second-order proposal.
 
     Same augmented target as aux_step; the proposal is the smoothing law of the
@@ -203,7 +215,7 @@ def aux_step_second_order(x, model, delta, eps_aux, eps_back, log_u):
     u = x + np.sqrt(0.5 * delta) * eps_aux
     om, Om = second_order_obs(x, u, model, delta)
     kf = kalman.kalman_filter(om, m0, P0, F, b, Q, Om)
-    x_star = kalman.rts_sample(kf, F, b, Q, eps_back)
+    x_star = _draw(kf, F, b, Q, eps_back, sampler)
     om_s, Om_s = second_order_obs(x_star, u, model, delta)
     kf_star = kalman.kalman_filter(om_s, m0, P0, F, b, Q, Om_s)
 
@@ -223,23 +235,23 @@ def aux_step_second_order(x, model, delta, eps_aux, eps_back, log_u):
                 omega=om, Omega=Om, omega_star=om_s, Omega_star=Om_s, kf=kf)
 
 
-def aux_step_philox(x, model, delta, seed, chain, iteration, order=1):
+def aux_step_philox(x, model, delta, seed, chain, iteration, order=1, sampler="rts"):
     """aux_step with the library's Philox streams for (seed, chain, iteration)."""
     T, d = x.shape
     eps_aux = philox.path_normals(seed, chain, iteration, philox.PURPOSE_AUX, T, d)
     eps_back = philox.path_normals(seed, chain, iteration, philox.PURPOSE_BACKWARD, T, d)
     log_u = float(np.log(philox.mh_uniform(seed, chain, iteration)))
     step = aux_step if order == 1 else aux_step_second_order
-    return step(x, model, delta, eps_aux, eps_back, log_u)
+    return step(x, model, delta, eps_aux, eps_back, log_u, sampler=sampler)
 
 
-def run_chain(x0, model, delta, seed, chain, n_iters, iter0=0, keep=None, order=1):
+def run_chain(x0, model, delta, seed, chain, n_iters, iter0=0, keep=None, order=1, sampler="rts"):
     """Run n_iters steps; returns (x_final, n_accepted, kept states or None)."""
     x = np.array(x0, dtype=np.float64)
     n_acc = 0
     kept = [] if keep is not None else None
     for k in range(n_iters):
-        st = aux_step_philox(x, model, delta, seed, chain, iter0 + k, order=order)
+        st = aux_step_philox(x, model, delta, seed, chain, iter0 + k, order=order, sampler=sampler)
         x = st["x_new"]
         n_acc += st["accepted"]
         if keep is not None:

@@ -14,6 +14,7 @@ def _load_binding():
 
 
 MODES = ("per_chain", "shared", "cached")
+SAMPLERS = ("scan", "bridging")
 
 
 class AuxKalman:
@@ -24,11 +25,13 @@ class AuxKalman:
     pass per call, means per chain) or "cached" (the covariance tables are kept
     until the model changes). ``proposal`` is the order of the auxiliary
     proposal (``aux_set_proposal``): 1 (first order) or 2 (second order,
-    per-chain mode only).
+    per-chain mode only). ``sampler`` draws the path from the smoothing law
+    (``aux_set_sampler``): "scan" ((G, U) suffix scan) or "bridging"
+    (divide-and-conquer tree of bridging conditionals).
     """
 
     def __init__(self, workload, dtype="f32", seed=None, n_chains=None, block_len=0, stream=None,
-                 mode="per_chain", proposal=1):
+                 mode="per_chain", proposal=1, sampler="scan"):
         import torch
         b = _load_binding()
         self.b = b
@@ -52,6 +55,11 @@ class AuxKalman:
         self.proposal = proposal
         if proposal != 1:
             b.aux_set_proposal(self.handle, proposal)
+        if sampler not in SAMPLERS:
+            raise ValueError(f"sampler must be one of {SAMPLERS}")
+        self.sampler = sampler
+        if sampler != "scan":
+            b.aux_set_sampler(self.handle, b.AUX_SAMPLER_BRIDGING)
 
     def step(self, x, n_iters=1, iter0=0, accept_count=None, log_alpha=None, stream=None):
         self.b.aux_kalman_step(self.handle, x, n_iters, iter0, accept_count, log_alpha, stream)

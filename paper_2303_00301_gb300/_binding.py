@@ -22,6 +22,7 @@ AUX_F32, AUX_F64 = 0, 1
 AUX_EMIS_LINEAR_GAUSSIAN, AUX_EMIS_SV, AUX_EMIS_STUDENT_T = 0, 1, 2
 AUX_MODE_PER_CHAIN, AUX_MODE_SHARED_COV, AUX_MODE_CACHED_COV = 0, 1, 2
 AUX_PROPOSAL_FIRST_ORDER, AUX_PROPOSAL_SECOND_ORDER = 1, 2
+AUX_SAMPLER_SCAN, AUX_SAMPLER_BRIDGING = 0, 1
 
 _dbl_p = ctypes.POINTER(ctypes.c_double)
 _u8_p = ctypes.POINTER(ctypes.c_uint8)
@@ -90,6 +91,8 @@ def _load():
     lib.aux_set_delta_adaptation.restype = ctypes.c_int
     lib.aux_get_delta.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     lib.aux_get_delta.restype = ctypes.c_int
+    lib.aux_set_sampler.argtypes = [vp, ctypes.c_int32]
+    lib.aux_set_sampler.restype = ctypes.c_int
     lib.aux_set_device_iteration.argtypes = [vp, ctypes.c_int32, ctypes.c_uint64]
     lib.aux_set_device_iteration.restype = ctypes.c_int
     lib.aux_get_device_iteration.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
@@ -197,6 +200,10 @@ def aux_get_delta(handle):
     return out.value
 
 
+def aux_set_sampler(handle, sampler):
+    _check(LIB.aux_set_sampler(handle, int(sampler)), "aux_set_sampler")
+
+
 def aux_set_device_iteration(handle, enable, start=0):
     _check(LIB.aux_set_device_iteration(handle, 1 if enable else 0, int(start)), "aux_set_device_iteration")
 
@@ -259,7 +266,8 @@ def aux_get_status(handle, n_chains=None):
 
 
 PROFILE_KINDS = ["linearise", "template", "reduce", "scan", "apply", "backward", "mh", "sum",
-                 "smooth", "grad", "cov_reduce", "cov_scan", "cov_apply", "cov_products"]
+                 "smooth", "grad", "cov_reduce", "cov_scan", "cov_apply", "cov_products",
+                 "bridge_tree", "bridge"]
 
 
 def aux_set_profiling(handle, enable):

@@ -308,6 +308,29 @@ int fact_init(aux_model* m, const aux_model_desc* desc, const std::vector<double
   return rc;
 }
 
+
+// buffers of the bridging sampler for the handle's current mode (aux_set_sampler)
+int br_alloc(aux_model* m) {
+  if (m->sampler != AUX_SAMPLER_BRIDGING) return AUX_OK;
+  const size_t es = m->esz, DP = (size_t)m->DP, DD = DP * DP;
+  const int n = m->T - 1;
+  int NN = 0;
+  for (int c = n; c > 1;) { c = (c + 1) / 2; NN += c; }
+  m->br_NN = NN;
+  const size_t nn = (size_t)std::max(NN, 1);
+  int rc = AUX_OK;
+  if (!m->br_g) rc = dev_alloc(m, &m->br_g, (size_t)m->C * nn * DP * es);
+  if (!rc && m->mode != AUX_MODE_PER_CHAIN) {
+    if (!m->br_L0) rc = dev_alloc(m, &m->br_L0, (size_t)std::max(n, 1) * DD * es);
+    if (!rc && !m->br_tree) rc = dev_alloc(m, &m->br_tree, 5 * nn * DD * es);
+  }
+  if (!rc && m->mode == AUX_MODE_PER_CHAIN) {
+    if (!m->Sig) rc = dev_alloc(m, &m->Sig, (size_t)m->C * m->T * DD * es);
+    if (!rc && !m->br_ctree) rc = dev_alloc(m, &m->br_ctree, (size_t)m->C * 5 * nn * DD * es);
+  }
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -462,8 +485,23 @@ int aux_set_mode(aux_model* m, int32_t mode) {
       return rc;
     }
   }
+  const int old = m->mode;
   m->mode = mode;
+  const int rc = br_alloc(m);
+  if (rc) { m->mode = old; return rc; }
   m->cov_valid = 0;
+  m->br_valid = 0;
+  return AUX_OK;
+}
+
+int aux_set_sampler(aux_model* m, int32_t sampler) {
+  if (!m || (sampler != AUX_SAMPLER_SCAN && sampler != AUX_SAMPLER_BRIDGING)) return AUX_E_INVALID_ARG;
+  if (m->fact) return sampler == AUX_SAMPLER_SCAN ? AUX_OK : AUX_E_UNSUPPORTED;
+  const int old = m->sampler;
+  m->sampler = sampler;
+  const int rc = br_alloc(m);
+  if (rc) { m->sampler = old; return rc; }
+  m->br_valid = 0;
   return AUX_OK;
 }
 
@@ -623,7 +661,7 @@ int aux_read_profile(aux_model* m, double* ms_per_kind, int32_t* launches_per_ki
     float ms = 0.0f;
     if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
       rc = AUX_E_CUDA;
-    if (r.kind < n_kinds) { ms_per_kind[r.kind] += ms; launches_per_kind[r.kind] += 1; }
+    if (r.kind < n_kinds) { ms_per_kind[r.kind] += ms; launches_per_kind[r.kind] += r.n; }
     m->pool.push_back(r);
   }
   m->recs.clear();

@@ -416,7 +416,7 @@ struct Fact {
   }
   static void backward(aux_model* m, const FP<Real>& p, Real* xs, cudaStream_t st) {
     const long nk = (long)m->C * m->nb * m->d, nc = (long)m->C * m->d;
-    ProfScope ps(m, PK_BACKWARD, st);
+    ProfScope ps(m, PK_BACKWARD, st, 2);
     k_fm_cross<Real><<<grid(nc, 128), 128, 0, st>>>(p, (const Real*)m->fbt + (long)FGH * m->nb * m->d,
                                                     (const Real*)m->fub, (Real*)m->fz, 1);
     k_fm_back<Real><<<grid(nk, 128), 128, 0, st>>>(p, (const Real*)m->ftab, (const Real*)m->U,
@@ -442,7 +442,7 @@ struct Fact {
             p, (const Real*)m->xs, x, (const Real*)m->u, (const Real*)m->v, m->fgam, (Real*)m->yts,
             m->fmh); }
       filter(m, p, (const Real*)m->yts, APPLY_REV_DIFF, nullptr, nullptr, iter, st);
-      { ProfScope ps(m, PK_MH, st);
+      { ProfScope ps(m, PK_MH, st, 2 + (m->adapt ? 1 : 0) + (m->dev_iter ? 1 : 0));
         k_fm_mh<Real><<<m->C, 256, 0, st>>>(p, m->fmh, m->flz, iter, acc, log_alpha, m->status, m->accept,
                                             m->la_all);
         k_fm_commit<Real><<<(int)std::min<long>(grid(n, 256), 152L * 8), 256, 0, st>>>(

@@ -66,10 +66,18 @@ struct aux_model {
   int32_t *cov_status = nullptr;
   int Lc = 0, nbc = 0;       // block length and block count of the covariance scan
   int cov_valid = 0;         // the tables match the current model
+  // divide-and-conquer sampler (aux_set_sampler, aux_bridge.cuh)
+  int sampler = AUX_SAMPLER_SCAN;
+  int br_NN = 0;             // internal nodes of the tree over T - 1 intervals
+  void *br_L0 = nullptr;     // [T-1][DP^2] leaf covariances (table modes)
+  void *br_tree = nullptr;   // shared tree: E, L [NN][DP^2], bridges [NN][3][DP^2]
+  void *br_ctree = nullptr;  // per-chain trees: the same per chain
+  void *br_g = nullptr;      // [C][NN][DP] node offsets g
+  int br_valid = 0;          // the shared tree matches the covariance tables
   const AuxOps *ops = nullptr;
   std::vector<void *> allocs;
   // optional per-launch CUDA-event timing (aux_set_profiling)
-  struct Rec { int kind; cudaEvent_t a, b; };
+  struct Rec { int kind, n; cudaEvent_t a, b; };
   bool profiling = false;
   std::vector<Rec> recs;      // recorded this window
   std::vector<Rec> pool;      // free event pairs
@@ -77,7 +85,8 @@ struct aux_model {
 
 // kernel kinds reported by aux_read_profile (order of AUX_PROFILE_* in the header)
 enum { PK_LINEARISE = 0, PK_TEMPLATE, PK_REDUCE, PK_SCAN, PK_APPLY, PK_BACKWARD, PK_MH, PK_SUM,
-       PK_SMOOTH, PK_GRAD, PK_COV_REDUCE, PK_COV_SCAN, PK_COV_APPLY, PK_COV_PRODUCTS, PK_COUNT };
+       PK_SMOOTH, PK_GRAD, PK_COV_REDUCE, PK_COV_SCAN, PK_COV_APPLY, PK_COV_PRODUCTS, PK_BR_TREE,
+       PK_BRIDGE, PK_COUNT };
 
 // bracket a launch with events on its stream when profiling is on
 struct ProfScope {
@@ -85,11 +94,14 @@ struct ProfScope {
   cudaStream_t st;
   aux_model::Rec r;
   bool on;
-  ProfScope(aux_model *m_, int kind, cudaStream_t st_) : m(m_), st(st_), on(m_->profiling) {
+  // `launches`: the kernels the scope launches (counted by aux_read_profile)
+  ProfScope(aux_model *m_, int kind, cudaStream_t st_, int launches = 1)
+      : m(m_), st(st_), on(m_->profiling) {
     if (!on) return;
     if (!m->pool.empty()) { r = m->pool.back(); m->pool.pop_back(); }
     else { cudaEventCreate(&r.a); cudaEventCreate(&r.b); }
     r.kind = kind;
+    r.n = launches;
     cudaEventRecord(r.a, st);
   }
   ~ProfScope() {

@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_apply(KP<Real> p,
 #pragma unroll
         for (int j = 0; j < CPW; ++j) {
           ei[j] = 0;
-          if (lane < p.d && valid[j])
+          if (lane < p.d && valid[j] && !(a.flags & APPLY_SMOOTH))
             ei[j] = a.eps ? eg[j]
                           : philox_normal<Real>(p.seed, (uint32_t)cidx[j], iter_of(p, a.iter), PURPOSE_BACKWARD, (uint32_t)t, lane);
         }

@@ -1,7 +1,10 @@
 // aux_ops.cuh — host-side launch sequences for one precision and padded dimension.
 #pragma once
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
+#include "aux_bridge.cuh"
 #include "aux_grad.cuh"
 #include "aux_means.cuh"
 
@@ -85,6 +88,8 @@ struct Ops {
     e = cudaFuncSetAttribute(k_mb_apply<Real, DP, MEAN_CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::BWD);
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_mean_cross<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::CROSS);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_br_node<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BrSizes<Real, DP>::NODE_SMEM);
     return cuda_ok(e);
   }
 
@@ -93,7 +98,7 @@ struct Ops {
   // MH test per chain, then x <- x* for the accepted chains
   static void mh_commit(aux_model* m, const KP<Real>& p, Real* x, uint64_t iter, uint32_t* acc,
                         double* log_alpha, cudaStream_t st) {
-    ProfScope ps(m, PK_MH, st);
+    ProfScope ps(m, PK_MH, st, 2 + (m->adapt ? 1 : 0) + (m->dev_iter ? 1 : 0));
     k_mh<Real><<<m->C, 128, 0, st>>>(p, m->mh_part, m->lz_part, iter, acc, log_alpha, m->status,
                                      m->accept, m->la_all);
     const long n = (long)m->C * m->T * m->d;
@@ -147,6 +152,7 @@ struct Ops {
   static constexpr long DD = (long)DP * DP;
 
   static void cov_pass(aux_model* m, const KP<Real>& p, cudaStream_t st) {
+    m->br_valid = 0;
     KP<Real> pc = p;   // the covariance scan runs on its own partition (block length Lc)
     pc.L = m->Lc;
     pc.nb = m->nbc;
@@ -177,7 +183,7 @@ struct Ops {
       k_cov_apply<Real, DP><<<m->nbc, 32, CZ::APP_SMEM, st>>>(pc, a);
     }
     {
-      ProfScope ps(m, PK_COV_PRODUCTS, st);
+      ProfScope ps(m, PK_COV_PRODUCTS, st, 2);
       k_cov_products<Real, DP><<<m->nb, 32, CZ::PROD_SMEM, st>>>(p, a, m->nbc);
       k_cov_gp_fix<Real, DP><<<(m->T + CZ::FIX_WPC - 1) / CZ::FIX_WPC, 32 * CZ::FIX_WPC, CZ::FIX_SMEM,
                                st>>>(p, a, m->Lc, m->nbc);
@@ -229,11 +235,121 @@ struct Ops {
 
   // (G, U) suffix scan on the tables: composition over the blocks, then in-block
   static void backward_tab(aux_model* m, const KP<Real>& p, BackArgs<Real> b, cudaStream_t st) {
-    ProfScope ps(m, PK_BACKWARD, st);
+    ProfScope ps(m, PK_BACKWARD, st, 2);
     Real* xnext = (Real*)m->zb;
     k_mean_cross<Real, DP><<<(m->C + MEAN_CHAINS - 1) / MEAN_CHAINS, 32 * MEAN_CHAINS, MZ::CROSS, st>>>(
         p, b.gum, b.guv, xnext, 1);
     k_mb_apply<Real, DP, MEAN_CPW><<<mean_grid(m), MEAN_THREADS, MZ::BWD, st>>>(p, b, xnext);
+  }
+
+  // ---- divide-and-conquer (bridging) sampler (aux_bridge.cuh)
+  using BZ = BrSizes<Real, DP>;
+
+  // the levels j >= 1 of the dyadic tree over n = T - 1 intervals
+  static std::vector<BrLevel> br_levels(const aux_model* m) {
+    std::vector<BrLevel> lv;
+    int prev_cnt = m->T - 1, prev_off = 0, off = 0;
+    for (int j = 1; prev_cnt > 1; ++j) {
+      const int cnt = (prev_cnt + 1) / 2;
+      lv.push_back(BrLevel{j, off, cnt, prev_off, prev_cnt});
+      prev_off = off;
+      off += cnt;
+      prev_cnt = cnt;
+    }
+    return lv;
+  }
+
+  // shared (table modes): leaves from the tables; per chain: leaves from the filter's G and Sigma
+  static BrTree<Real> br_tree(aux_model* m, bool shared) {
+    BrTree<Real> tr{};
+    const long NN = std::max(m->br_NN, 1);
+    Real* base = (Real*)(shared ? m->br_tree : m->br_ctree);
+    const long cs = shared ? 0 : NN * DD;
+    if (shared) {
+      tr.G0 = (const Real*)m->tab + (long)TG * m->T * DD; tr.g0_cs = 0;
+      tr.L0 = (const Real*)m->br_L0; tr.l0_cs = 0;
+      tr.status = m->cov_status; tr.per_chain_status = 0;
+    } else {
+      tr.G0 = (const Real*)m->G; tr.g0_cs = (long)m->T * DD;
+      tr.L0 = (const Real*)m->Sig; tr.l0_cs = (long)m->T * DD;
+      tr.status = m->status_iter; tr.per_chain_status = 1;
+    }
+    const long nch = shared ? 1 : m->C;
+    tr.E = base;
+    tr.L = base + nch * NN * DD;
+    tr.B = base + 2 * nch * NN * DD;
+    tr.nn_cs = cs;
+    return tr;
+  }
+
+  static void br_build(aux_model* m, const KP<Real>& p, const BrTree<Real>& tr, bool shared, cudaStream_t st) {
+    const int n = m->T - 1;
+    const std::vector<BrLevel> lv = br_levels(m);
+    if (shared && n >= 1) {
+      ProfScope ps(m, PK_BR_TREE, st);
+      k_br_leaf<Real, DP><<<(n + 7) / 8, 256, 0, st>>>((const Real*)m->tab + (long)TLS * m->T * DD,
+                                                       (Real*)m->br_L0, n);
+    }
+    const int nch = shared ? 1 : m->C;
+    for (const BrLevel& l : lv) {
+      ProfScope ps(m, PK_BR_TREE, st);
+      k_br_node<Real, DP><<<nch * l.cnt, 32, BZ::NODE_SMEM, st>>>(p, tr, l);
+    }
+  }
+
+  // the table modes' tree follows the covariance tables
+  static void br_ensure_shared(aux_model* m, const KP<Real>& p, cudaStream_t st) {
+    if (m->br_valid) return;
+    br_build(m, p, br_tree(m, true), true, st);
+    m->br_valid = 1;
+  }
+
+  // node offsets up the tree, the two ends, the split points down the tree
+  static void br_sample(aux_model* m, const KP<Real>& p, const BrTree<Real>& tr, BrMeans<Real> mv,
+                        cudaStream_t st) {
+    const std::vector<BrLevel> lv = br_levels(m);
+    mv.gN = (Real*)m->br_g;
+    mv.NN = std::max(m->br_NN, 1);
+    for (const BrLevel& l : lv) {
+      ProfScope ps(m, PK_BRIDGE, st);
+      const long items = (long)m->C * l.cnt;
+      k_bg_up<Real, DP><<<(int)((items + BZ::WPC - 1) / BZ::WPC), 32 * BZ::WPC, BZ::VEC_SMEM, st>>>(p, tr, mv, l);
+    }
+    {
+      ProfScope ps(m, PK_BRIDGE, st);
+      const int rj = lv.empty() ? 0 : lv.back().j, ro = lv.empty() ? 0 : lv.back().off;
+      k_bx_root<Real, DP><<<m->C, 32, BZ::ROOT_SMEM, st>>>(p, tr, mv, rj, ro);
+    }
+    for (auto it = lv.rbegin(); it != lv.rend(); ++it) {
+      ProfScope ps(m, PK_BRIDGE, st);
+      const long items = (long)m->C * it->cnt;
+      k_bx_down<Real, DP><<<(int)((items + BZ::WPC - 1) / BZ::WPC), 32 * BZ::WPC, BZ::VEC_SMEM, st>>>(p, tr, mv, *it);
+    }
+  }
+
+  static void br_mh_terms(aux_model* m, const KP<Real>& p, const BackArgs<Real>& b, cudaStream_t st) {
+    ProfScope ps(m, PK_BRIDGE, st);
+    const long items = (long)m->C * m->nb;
+    const size_t sm = (size_t)(Lay<Real, DP>::MAT + BZ::WPC * BZ::VEC) * sizeof(Real);
+    k_b_mh<Real, DP><<<(int)((items + BZ::WPC - 1) / BZ::WPC), 32 * BZ::WPC, sm, st>>>(p, b);
+  }
+
+  static BrMeans<Real> br_means_tab(aux_model* m, Real* xs, const Real* eps, uint64_t iter) {
+    BrMeans<Real> mv{};
+    mv.U = (const Real*)m->U;
+    mv.PT = (const Real*)m->tab + (long)TPF * m->T * DD + (long)(m->T - 1) * DD;
+    mv.pt_cs = 0;
+    mv.xs = xs; mv.eps = eps; mv.iter = iter;
+    return mv;
+  }
+
+  static BrMeans<Real> br_means_chain(aux_model* m, Real* xs, const Real* eps, uint64_t iter) {
+    BrMeans<Real> mv{};
+    mv.U = (const Real*)m->U;
+    mv.PT = (const Real*)m->Sig + (long)(m->T - 1) * DD;
+    mv.pt_cs = (long)m->T * DD;
+    mv.xs = xs; mv.eps = eps; mv.iter = iter;
+    return mv;
   }
 
   static int kalman_step_means(aux_model* m, void* xv, int n_iters, uint64_t iter0, uint32_t* acc,
@@ -246,14 +362,21 @@ struct Ops {
       // an adapted delta changes the covariances every iteration
       if (m->adapt) cov_pass(m, p, st);
       else if (it == 0) ensure_cov(m, p, st);
+      const bool br = m->sampler == AUX_SAMPLER_BRIDGING;
+      if (br) br_ensure_shared(m, p, st);
       MeanArgs<Real> a = mean_args(m);
       a.x = x; a.u = (Real*)m->u; a.v = (Real*)m->v; a.yt = (Real*)m->yt; a.iter = iter;
-      a.flags = APPLY_EPI | APPLY_STORE_Q;
+      a.flags = APPLY_EPI | APPLY_STORE_Q | (br ? APPLY_SMOOTH : 0);
       means_filter(m, p, a, st);
       BackArgs<Real> b = back_args_tab(m);
       b.xs = (Real*)m->xs; b.mh = 1; b.x = x; b.u = (const Real*)m->u; b.v = (const Real*)m->v;
       b.yts = (Real*)m->yts; b.mh_part = m->mh_part;
-      backward_tab(m, p, b, st);
+      if (br) {
+        br_sample(m, p, br_tree(m, true), br_means_tab(m, (Real*)m->xs, nullptr, iter), st);
+        br_mh_terms(m, p, b, st);
+      } else {
+        backward_tab(m, p, b, st);
+      }
       MeanArgs<Real> r = mean_args(m);
       r.yt = (Real*)m->yts; r.flags = APPLY_REV_DIFF;
       means_filter(m, p, r, st);
@@ -282,14 +405,24 @@ struct Ops {
       { ProfScope ps(m, PK_LINEARISE, st);
       k_linearise<Real><<<lin_grid, 256, 0, st>>>(p, x, (Real*)m->u, (Real*)m->v, (Real*)m->yt,
                                                   (Real*)m->rho, iter); }
-      filter(m, pf, (const Real*)m->yt, apply_args(m, APPLY_EPI | APPLY_STORE_Q, iter), st);
+      const bool br = m->sampler == AUX_SAMPLER_BRIDGING;
+      ApplyArgs<Real> fa = apply_args(m, APPLY_EPI | APPLY_STORE_Q | (br ? APPLY_SMOOTH : 0), iter);
+      fa.Sig = (Real*)m->Sig;
+      filter(m, pf, (const Real*)m->yt, fa, st);
       BackArgs<Real> b{};
       b.G = (const Real*)m->G; b.U = (const Real*)m->U; b.gum = (const Real*)m->gum;
       b.guv = (const Real*)m->guv; b.g_cs = (long)m->T * DP * DP; b.gm_cs = (long)m->nb * DP * DP;
       b.xs = (Real*)m->xs; b.mh = 1; b.x = x; b.u = (const Real*)m->u; b.v = (const Real*)m->v;
       b.yts = (Real*)m->yts; b.mh_part = m->mh_part;
       b.yt = (const Real*)m->yt; b.rho = (const Real*)m->rho; b.rhos = (Real*)m->rhos;
-      backward(m, p, b, st);
+      if (br) {
+        const BrTree<Real> tr = br_tree(m, false);
+        br_build(m, pf, tr, false, st);
+        br_sample(m, p, tr, br_means_chain(m, (Real*)m->xs, nullptr, iter), st);
+        br_mh_terms(m, p, b, st);
+      } else {
+        backward(m, p, b, st);
+      }
       filter(m, pr, (const Real*)m->yts, apply_args(m, APPLY_REV_DIFF, iter), st);
       mh_commit(m, p, x, iter, acc, log_alpha, st);
     }
@@ -320,19 +453,35 @@ struct Ops {
     const KP<Real> p = make_kp<Real>(m);
     if (m->mode != AUX_MODE_PER_CHAIN) {
       ensure_cov(m, p, st);
+      const bool br = m->sampler == AUX_SAMPLER_BRIDGING;
+      if (br) br_ensure_shared(m, p, st);
       MeanArgs<Real> a = mean_args(m);
-      a.yt = (Real*)yt; a.flags = APPLY_EPI | APPLY_LOGZ; a.eps = (const Real*)eps; a.iter = iter;
+      a.yt = (Real*)yt; a.flags = APPLY_EPI | APPLY_LOGZ | (br ? APPLY_SMOOTH : 0);
+      a.eps = (const Real*)eps; a.iter = iter;
       a.status = m->status;
       means_filter(m, p, a, st);
-      BackArgs<Real> b = back_args_tab(m);
-      b.xs = (Real*)xs; b.mh = 0;
-      backward_tab(m, p, b, st);
+      if (br) {
+        br_sample(m, p, br_tree(m, true), br_means_tab(m, (Real*)xs, (const Real*)eps, iter), st);
+      } else {
+        BackArgs<Real> b = back_args_tab(m);
+        b.xs = (Real*)xs; b.mh = 0;
+        backward_tab(m, p, b, st);
+      }
       if (logZ) { ProfScope ps(m, PK_SUM, st); k_sum_parts<<<m->C, 128, 0, st>>>(m->lz_part, m->nb, logZ); }
       return cuda_ok(cudaGetLastError());
     }
-    ApplyArgs<Real> a = apply_args(m, APPLY_EPI | APPLY_LOGZ, iter);
+    const bool br = m->sampler == AUX_SAMPLER_BRIDGING;
+    ApplyArgs<Real> a = apply_args(m, APPLY_EPI | APPLY_LOGZ | (br ? APPLY_SMOOTH : 0), iter);
     a.eps = (const Real*)eps;
+    a.Sig = (Real*)m->Sig;
     filter(m, p, (const Real*)yt, a, st);
+    if (br) {
+      const BrTree<Real> tr = br_tree(m, false);
+      br_build(m, p, tr, false, st);
+      br_sample(m, p, tr, br_means_chain(m, (Real*)xs, (const Real*)eps, iter), st);
+      if (logZ) { ProfScope ps(m, PK_SUM, st); k_sum_parts<<<m->C, 128, 0, st>>>(m->lz_part, m->nb, logZ); }
+      return cuda_ok(cudaGetLastError());
+    }
     BackArgs<Real> b{};
     b.G = (const Real*)m->G; b.U = (const Real*)m->U; b.gum = (const Real*)m->gum;
     b.guv = (const Real*)m->guv; b.g_cs = (long)m->T * DP * DP; b.gm_cs = (long)m->nb * DP * DP;
@@ -360,7 +509,7 @@ struct Ops {
     sa.opart = m->opart; sa.s0 = (Real*)m->s0;
     const int n = items(m);
     {
-      ProfScope ps(m, PK_SMOOTH, st);
+      ProfScope ps(m, PK_SMOOTH, st, 2);
       k_smooth_reduce<Real, DP><<<(n + GZ::WPC - 1) / GZ::WPC, 32 * GZ::WPC, GZ::RED_SMEM, st>>>(p, sa);
       k_smooth_apply<Real, DP><<<(n + GZ::WPC - 1) / GZ::WPC, 32 * GZ::WPC, GZ::APP_SMEM, st>>>(p, sa);
     }

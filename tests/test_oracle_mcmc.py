@@ -113,14 +113,16 @@ def test_two_step_toy_chain_mean():
 
 
 @pytest.mark.slow
-def test_linear_gaussian_stationarity():
-    """Chain moments match the exact smoother of the linear-Gaussian model within MC error."""
+@pytest.mark.parametrize("sampler", ["rts", "bridging"])
+def test_linear_gaussian_stationarity(sampler):
+    """Chain moments match the exact smoother of the linear-Gaussian model within MC error
+    (with either pathwise sampler: RTS, or the divide-and-conquer sampler of Appendix A.2.3)."""
     wl = workloads.linear_gaussian(d=2, T=16)
     model = _model_from(wl)
     kf = kalman.kalman_filter(wl.y, wl.m0, wl.P0, wl.F, wl.b, wl.Q, wl.Ry)
     ms, Ps = kalman.rts_smoother(kf, wl.F)
     x, n_acc, kept = mcmc.run_chain(wl.x_init[0], model, wl.delta, seed=wl.mcmc_seed, chain=0,
-                                    n_iters=3000, keep=lambda z: z.copy())
+                                    n_iters=3000, keep=lambda z: z.copy(), sampler=sampler)
     s = np.stack(kept[300:])
     se = _batch_se(s)
     z = (s.mean(axis=0) - ms) / se
