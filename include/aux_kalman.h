@@ -213,6 +213,25 @@ int aux_set_mode(aux_model *m, int32_t mode);
  * Errors: INVALID_ARG (unknown order), UNSUPPORTED (non-diagonal Hessian), OOM. */
 int aux_set_proposal(aux_model *m, int32_t order);
 
+/* Filter forms (aux_set_filter_form) */
+#define AUX_FILTER_COVARIANCE  0  /* elements (A, b, C, eta, J), Appendix A.2.1 (default) */
+#define AUX_FILTER_SQUARE_ROOT 1  /* the same elements with C and J as triangular factors */
+
+/* Choose the arithmetic form of the per-chain parallel filter of aux_loglik.
+ * Section 4.2 reports that the parallel filter diverged in single precision
+ * and names the square-root form as the remedy (the paper ran in double
+ * precision instead). AUX_FILTER_SQUARE_ROOT carries every element's C and J
+ * as factors U U^T and Z Z^T, forms each new covariance factor by an
+ * orthogonal (Householder) triangularisation of [X1, X2] (the factor of
+ * X1 X1^T + X2 X2^T) instead of adding and subtracting covariances, and runs
+ * the in-block filter as the square-root Kalman step (Joseph form). Its
+ * results equal the covariance form's up to rounding; it costs several times
+ * more. Scope: AUX_MODE_PER_CHAIN with the first-order proposal, aux_loglik
+ * only: aux_kalman_step and aux_sample_path return AUX_E_UNSUPPORTED while it
+ * is set, and so do all calls in a table mode. Not available for the
+ * factorised-prior model (UNSUPPORTED). Errors: INVALID_ARG, UNSUPPORTED. */
+int aux_set_filter_form(aux_model *m, int32_t form);
+
 /* Pathwise samplers (aux_set_sampler) */
 #define AUX_SAMPLER_SCAN     0  /* (G, U) suffix scan, Eqs. (A.14)-(A.15), Proposition A.1 (default) */
 #define AUX_SAMPLER_BRIDGING 1  /* divide-and-conquer bridging sampler, Section 2.4.2, Appendix A.2.3 */

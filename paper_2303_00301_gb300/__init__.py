@@ -15,6 +15,7 @@ def _load_binding():
 
 MODES = ("per_chain", "shared", "cached")
 SAMPLERS = ("scan", "bridging")
+FILTER_FORMS = ("covariance", "square_root")
 
 
 class AuxKalman:
@@ -27,11 +28,13 @@ class AuxKalman:
     proposal (``aux_set_proposal``): 1 (first order) or 2 (second order,
     per-chain mode only). ``sampler`` draws the path from the smoothing law
     (``aux_set_sampler``): "scan" ((G, U) suffix scan) or "bridging"
-    (divide-and-conquer tree of bridging conditionals).
+    (divide-and-conquer tree of bridging conditionals). ``filter_form``
+    (``aux_set_filter_form``): "covariance" or "square_root" (per-chain
+    ``loglik`` only).
     """
 
     def __init__(self, workload, dtype="f32", seed=None, n_chains=None, block_len=0, stream=None,
-                 mode="per_chain", proposal=1, sampler="scan"):
+                 mode="per_chain", proposal=1, sampler="scan", filter_form="covariance"):
         import torch
         b = _load_binding()
         self.b = b
@@ -60,6 +63,11 @@ class AuxKalman:
         self.sampler = sampler
         if sampler != "scan":
             b.aux_set_sampler(self.handle, b.AUX_SAMPLER_BRIDGING)
+        if filter_form not in FILTER_FORMS:
+            raise ValueError(f"filter_form must be one of {FILTER_FORMS}")
+        self.filter_form = filter_form
+        if filter_form != "covariance":
+            b.aux_set_filter_form(self.handle, b.AUX_FILTER_SQUARE_ROOT)
 
     def step(self, x, n_iters=1, iter0=0, accept_count=None, log_alpha=None, stream=None):
         self.b.aux_kalman_step(self.handle, x, n_iters, iter0, accept_count, log_alpha, stream)

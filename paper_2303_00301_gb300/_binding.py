@@ -23,6 +23,7 @@ AUX_EMIS_LINEAR_GAUSSIAN, AUX_EMIS_SV, AUX_EMIS_STUDENT_T = 0, 1, 2
 AUX_MODE_PER_CHAIN, AUX_MODE_SHARED_COV, AUX_MODE_CACHED_COV = 0, 1, 2
 AUX_PROPOSAL_FIRST_ORDER, AUX_PROPOSAL_SECOND_ORDER = 1, 2
 AUX_SAMPLER_SCAN, AUX_SAMPLER_BRIDGING = 0, 1
+AUX_FILTER_COVARIANCE, AUX_FILTER_SQUARE_ROOT = 0, 1
 
 _dbl_p = ctypes.POINTER(ctypes.c_double)
 _u8_p = ctypes.POINTER(ctypes.c_uint8)
@@ -91,6 +92,8 @@ def _load():
     lib.aux_set_delta_adaptation.restype = ctypes.c_int
     lib.aux_get_delta.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     lib.aux_get_delta.restype = ctypes.c_int
+    lib.aux_set_filter_form.argtypes = [vp, ctypes.c_int32]
+    lib.aux_set_filter_form.restype = ctypes.c_int
     lib.aux_set_sampler.argtypes = [vp, ctypes.c_int32]
     lib.aux_set_sampler.restype = ctypes.c_int
     lib.aux_set_device_iteration.argtypes = [vp, ctypes.c_int32, ctypes.c_uint64]
@@ -198,6 +201,10 @@ def aux_get_delta(handle):
     out = ctypes.c_double(0.0)
     _check(LIB.aux_get_delta(handle, ctypes.byref(out)), "aux_get_delta")
     return out.value
+
+
+def aux_set_filter_form(handle, form):
+    _check(LIB.aux_set_filter_form(handle, int(form)), "aux_set_filter_form")
 
 
 def aux_set_sampler(handle, sampler):

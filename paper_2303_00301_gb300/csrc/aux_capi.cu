@@ -494,6 +494,13 @@ int aux_set_mode(aux_model* m, int32_t mode) {
   return AUX_OK;
 }
 
+int aux_set_filter_form(aux_model* m, int32_t form) {
+  if (!m || (form != AUX_FILTER_COVARIANCE && form != AUX_FILTER_SQUARE_ROOT)) return AUX_E_INVALID_ARG;
+  if (m->fact) return form == AUX_FILTER_COVARIANCE ? AUX_OK : AUX_E_UNSUPPORTED;
+  m->sqrt_form = form == AUX_FILTER_SQUARE_ROOT ? 1 : 0;
+  return AUX_OK;
+}
+
 int aux_set_sampler(aux_model* m, int32_t sampler) {
   if (!m || (sampler != AUX_SAMPLER_SCAN && sampler != AUX_SAMPLER_BRIDGING)) return AUX_E_INVALID_ARG;
   if (m->fact) return sampler == AUX_SAMPLER_SCAN ? AUX_OK : AUX_E_UNSUPPORTED;

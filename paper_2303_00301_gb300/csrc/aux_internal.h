@@ -74,6 +74,8 @@ struct aux_model {
   void *br_ctree = nullptr;  // per-chain trees: the same per chain
   void *br_g = nullptr;      // [C][NN][DP] node offsets g
   int br_valid = 0;          // the shared tree matches the covariance tables
+  // square-root form of the per-chain filter (aux_set_filter_form, aux_sqrt.cuh)
+  int sqrt_form = 0;
   const AuxOps *ops = nullptr;
   std::vector<void *> allocs;
   // optional per-launch CUDA-event timing (aux_set_profiling)

@@ -507,8 +507,8 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::RED_WPC, 1)
     __syncwarp();
     {
       Real s_[DP];
-#pragma unroll
       const Real rl = obs_var<Real>(p, c, t, lane);
+#pragma unroll
       for (int j = 0; j < DP; ++j) s_[j] = pprow[j] + (j == lane ? rl : (Real)0);
       chol_rot<Real, DP>(s_, SL, nullptr, nullptr, vdiag, nullptr, p.d, lane, &bad);
     }

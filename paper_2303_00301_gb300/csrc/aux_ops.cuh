@@ -7,6 +7,7 @@
 #include "aux_bridge.cuh"
 #include "aux_grad.cuh"
 #include "aux_means.cuh"
+#include "aux_sqrt.cuh"
 
 namespace auxk {
 namespace {
@@ -90,6 +91,12 @@ struct Ops {
     e = cudaFuncSetAttribute(k_mean_cross<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::CROSS);
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_br_node<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BrSizes<Real, DP>::NODE_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_sr_reduce<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SrSizes<Real, DP>::RED_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_sr_scan_level<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SrSizes<Real, DP>::RED_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_sr_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SrSizes<Real, DP>::APP_SMEM);
     return cuda_ok(e);
   }
 
@@ -129,6 +136,26 @@ struct Ops {
     a.prefix = (m->nb > 1) ? b0 : nullptr;
     ProfScope ps(m, PK_APPLY, st);
     k_filter_apply<Real, DP><<<(n + Z::APP_WPC - 1) / Z::APP_WPC, 32 * Z::APP_WPC, Z::APP_SMEM, st>>>(p, a);
+  }
+
+  // square-root form of the per-chain filter (aux_sqrt.cuh): the same three phases
+  static void sr_filter(aux_model* m, const KP<Real>& p, const Real* yt, ApplyArgs<Real> a,
+                        cudaStream_t st) {
+    using SZ = SrSizes<Real, DP>;
+    const int n = items(m);
+    Real* b0 = (Real*)m->agg0;
+    Real* b1 = (Real*)m->agg1;
+    { ProfScope ps(m, PK_REDUCE, st);
+      k_sr_reduce<Real, DP><<<n, 32, SZ::RED_SMEM, st>>>(p, yt, b0); }
+    for (int off = 1; off < m->nb; off *= 2) {
+      { ProfScope ps(m, PK_SCAN, st);
+        k_sr_scan_level<Real, DP><<<n, 32, SZ::RED_SMEM, st>>>(p, b0, b1, off); }
+      Real* tmp = b0; b0 = b1; b1 = tmp;
+    }
+    a.yt = yt;
+    a.prefix = (m->nb > 1) ? b0 : nullptr;
+    ProfScope ps(m, PK_APPLY, st);
+    k_sr_apply<Real, DP><<<n, 32, SZ::APP_SMEM, st>>>(p, a);
   }
 
   static ApplyArgs<Real> apply_args(aux_model* m, int flags, uint64_t iter) {
@@ -387,6 +414,7 @@ struct Ops {
 
   static int kalman_step(aux_model* m, void* xv, int n_iters, uint64_t iter0, uint32_t* acc,
                          double* log_alpha, cudaStream_t st) {
+    if (m->sqrt_form) return AUX_E_UNSUPPORTED;
     if (m->mode != AUX_MODE_PER_CHAIN) {
       // the tables assume R = (delta/2) I; the second-order variances depend on the chain's state
       if (m->order != 1) return AUX_E_UNSUPPORTED;
@@ -431,6 +459,7 @@ struct Ops {
 
   static int loglik(aux_model* m, const void* yt, double* logZ, void* mf, void* Pf, cudaStream_t st) {
     const KP<Real> p = make_kp<Real>(m);
+    if (m->sqrt_form && m->mode != AUX_MODE_PER_CHAIN) return AUX_E_UNSUPPORTED;
     if (m->mode != AUX_MODE_PER_CHAIN) {
       ensure_cov(m, p, st);
       MeanArgs<Real> a = mean_args(m);
@@ -442,7 +471,8 @@ struct Ops {
     ApplyArgs<Real> a = apply_args(m, APPLY_LOGZ, 0);
     a.mf = (Real*)mf;
     a.Pf = (Real*)Pf;
-    filter(m, p, (const Real*)yt, a, st);
+    if (m->sqrt_form) sr_filter(m, p, (const Real*)yt, a, st);
+    else filter(m, p, (const Real*)yt, a, st);
     { ProfScope ps(m, PK_SUM, st);
     k_sum_parts<<<m->C, 128, 0, st>>>(m->lz_part, m->nb, logZ); }
     return cuda_ok(cudaGetLastError());
@@ -450,6 +480,7 @@ struct Ops {
 
   static int sample_path(aux_model* m, const void* yt, const void* eps, uint64_t iter, void* xs,
                          double* logZ, cudaStream_t st) {
+    if (m->sqrt_form) return AUX_E_UNSUPPORTED;
     const KP<Real> p = make_kp<Real>(m);
     if (m->mode != AUX_MODE_PER_CHAIN) {
       ensure_cov(m, p, st);

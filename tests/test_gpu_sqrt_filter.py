@@ -1,0 +1,134 @@
+"""Square-root form of the per-chain parallel filter (aux_set_filter_form) against
+the FP64 oracle (oracle/sqrt_filter.py, pinned to the covariance form and the
+Kalman filter in test_oracle_sqrt_filter.py).
+
+Tolerances: FP64 1e-9 relative on m^f, P^f and log Z; FP32 1e-4 on m^f and P^f,
+1e-5 on log Z (normwise per chain), as for the covariance form.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import kalman, sqrt_filter  # noqa: E402
+from paper_2303_00301_gb300 import AuxKalman, workloads  # noqa: E402
+from paper_2303_00301_gb300 import _binding as B  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_00301_gb300 import build
+    build.build()
+
+
+def _tt(a, dtype):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300)
+
+
+def _workload(d, T, C, seed, delta=0.5, Q=None):
+    m = workloads.random_lgssm(d, T, seed=seed)
+    return workloads.Workload(name="rand", d=d, T=T, n_chains=C, m0=m["m0"], P0=m["P0"],
+                              F=m["F"], b=m["b"], Q=m["Q"] if Q is None else Q, y=m["y"],
+                              emission=workloads.EMIS_LINEAR_GAUSSIAN, delta=delta,
+                              x_init=np.zeros((C, T, d)), Ry=np.eye(d))
+
+
+def _run(wl, dt, L, yt, form):
+    C, T, d = wl.n_chains, wl.T, wl.d
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    s = AuxKalman(wl, dtype=dt, block_len=L, filter_form=form)
+    logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
+    mf = torch.zeros((C, T, d), dtype=tdt, device="cuda")
+    Pf = torch.zeros((C, T, d, d), dtype=tdt, device="cuda")
+    s.loglik(_tt(yt, tdt), logZ, mf, Pf)
+    torch.cuda.synchronize()
+    out = logZ.cpu().numpy(), mf.double().cpu().numpy(), Pf.double().cpu().numpy(), s.status()
+    s.close()
+    return out
+
+
+CASES = [
+    # d, T, C, block_len, dtype: several blocks, ragged tail, one block, T = 1
+    (2, 64, 2, 8, "f64"),
+    (1, 37, 3, 8, "f64"),
+    (3, 37, 3, 5, "f64"),
+    (4, 20, 2, 20, "f64"),
+    (3, 1, 2, 1, "f64"),
+    (16, 50, 2, 9, "f64"),
+    (5, 41, 2, 7, "f32"),
+    (8, 33, 2, 6, "f32"),
+    (30, 128, 2, 16, "f32"),
+]
+
+
+@pytest.mark.parametrize("d,T,C,L,dt", CASES)
+def test_square_root_filter_matches_the_oracle(d, T, C, L, dt):
+    wl = _workload(d, T, C, seed=700 + d * T)
+    rng = np.random.default_rng(d + 3 * T)
+    yt = rng.standard_normal((C, T, d))
+    logZ, mf, Pf, (rc, st) = _run(wl, dt, L, yt, "square_root")
+    tol = 1e-9 if dt == "f64" else 1e-4
+    tol_z = 1e-9 if dt == "f64" else 1e-5
+    R = 0.5 * wl.delta * np.eye(d)
+    for c in range(C):
+        ref = sqrt_filter.sr_filter(yt[c], wl.m0, wl.P0, wl.F, wl.b, wl.Q, R)
+        assert abs(logZ[c] - ref["logZ"]) <= tol_z * abs(ref["logZ"]), (c, logZ[c], ref["logZ"])
+        assert _rel(mf[c], ref["mf"]) < tol
+        assert _rel(Pf[c], np.einsum("tij,tkj->tik", ref["Uf"], ref["Uf"])) < tol
+    assert rc == 0 and not np.any(st)
+
+
+def test_square_root_and_covariance_forms_agree():
+    wl = _workload(6, 96, 3, seed=11)
+    yt = np.random.default_rng(2).standard_normal((3, 96, 6))
+    a = _run(wl, "f64", 12, yt, "square_root")
+    b = _run(wl, "f64", 12, yt, "covariance")
+    assert np.allclose(a[0], b[0], rtol=1e-12, atol=1e-9)
+    assert _rel(a[1], b[1]) < 1e-11 and _rel(a[2], b[2]) < 1e-11
+
+
+def test_single_precision_stays_accurate_where_the_covariance_form_loses_it():
+    """Observations far more precise than the dynamics (r = 1e-6 against Q ~ 1): P^f ~ r I
+    is a small difference of O(1) covariances in the covariance form; the square-root
+    form never forms it. Both in FP32 against the FP64 oracle."""
+    d, T, C = 8, 128, 2
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((d, d))
+    Q = A @ A.T / d + np.eye(d)
+    wl = _workload(d, T, C, seed=21, delta=2e-6, Q=Q)
+    yt = rng.standard_normal((C, T, d)) * 2.0
+    R = 0.5 * wl.delta * np.eye(d)
+    err = {}
+    for form in ("square_root", "covariance"):
+        logZ, mf, Pf, (rc, st) = _run(wl, "f32", 16, yt, form)
+        e_pf, e_z = [], []
+        for c in range(C):
+            kf = kalman.kalman_filter(yt[c], wl.m0, wl.P0, wl.F, wl.b, wl.Q, R)
+            e_pf.append(_rel(Pf[c], kf["Pf"]))
+            e_z.append(abs(logZ[c] - kf["logZ"]) / abs(kf["logZ"]))
+        err[form] = (max(e_pf), max(e_z), int(np.any(st)))
+    print("P^f rel err, log Z rel err, status:", err)
+    assert err["square_root"][0] < 1e-4 and err["square_root"][1] < 1e-5 and err["square_root"][2] == 0
+    # measured on GB300: 2.3e-7 against 1.5e-1
+    assert 100 * err["square_root"][0] < err["covariance"][0]
+
+
+def test_scope_is_reported():
+    wl = _workload(3, 20, 2, seed=1)
+    s = AuxKalman(wl, dtype="f64", block_len=5, filter_form="square_root")
+    x = _tt(wl.x_init, torch.float64)
+    with pytest.raises(B.AuxError):
+        s.step(x, 1)
+    s.close()
+    s = AuxKalman(wl, dtype="f64", block_len=5, mode="cached", filter_form="square_root")
+    logZ = torch.zeros(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.AuxError):
+        s.loglik(_tt(np.zeros((2, 20, 3)), torch.float64), logZ)
+    s.close()
