@@ -226,10 +226,13 @@ int aux_set_proposal(aux_model *m, int32_t order);
  * X1 X1^T + X2 X2^T) instead of adding and subtracting covariances, and runs
  * the in-block filter as the square-root Kalman step (Joseph form). Its
  * results equal the covariance form's up to rounding; it costs several times
- * more. Scope: AUX_MODE_PER_CHAIN with the first-order proposal, aux_loglik
- * only: aux_kalman_step and aux_sample_path return AUX_E_UNSUPPORTED while it
- * is set, and so do all calls in a table mode. Not available for the
- * factorised-prior model (UNSUPPORTED). Errors: INVALID_ARG, UNSUPPORTED. */
+ * more. With it the in-block filter also forms the backward elements of the
+ * (G, U) scan, chol(Sigma_t) by triangularisation in Joseph form, so that
+ * aux_kalman_step and aux_sample_path run on the square-root filter too.
+ * Scope: AUX_MODE_PER_CHAIN, first-order proposal, AUX_SAMPLER_SCAN; other
+ * combinations return AUX_E_UNSUPPORTED from the calls that need them (every
+ * call in a table mode). Not available for the factorised-prior model
+ * (UNSUPPORTED). Errors: INVALID_ARG, UNSUPPORTED. */
 int aux_set_filter_form(aux_model *m, int32_t form);
 
 /* Pathwise samplers (aux_set_sampler) */

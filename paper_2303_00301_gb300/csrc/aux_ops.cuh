@@ -414,7 +414,8 @@ struct Ops {
 
   static int kalman_step(aux_model* m, void* xv, int n_iters, uint64_t iter0, uint32_t* acc,
                          double* log_alpha, cudaStream_t st) {
-    if (m->sqrt_form) return AUX_E_UNSUPPORTED;
+    if (m->sqrt_form && (m->mode != AUX_MODE_PER_CHAIN || m->order != 1 || m->sampler != AUX_SAMPLER_SCAN))
+      return AUX_E_UNSUPPORTED;
     if (m->mode != AUX_MODE_PER_CHAIN) {
       // the tables assume R = (delta/2) I; the second-order variances depend on the chain's state
       if (m->order != 1) return AUX_E_UNSUPPORTED;
@@ -436,7 +437,8 @@ struct Ops {
       const bool br = m->sampler == AUX_SAMPLER_BRIDGING;
       ApplyArgs<Real> fa = apply_args(m, APPLY_EPI | APPLY_STORE_Q | (br ? APPLY_SMOOTH : 0), iter);
       fa.Sig = (Real*)m->Sig;
-      filter(m, pf, (const Real*)m->yt, fa, st);
+      if (m->sqrt_form) sr_filter(m, pf, (const Real*)m->yt, fa, st);
+      else filter(m, pf, (const Real*)m->yt, fa, st);
       BackArgs<Real> b{};
       b.G = (const Real*)m->G; b.U = (const Real*)m->U; b.gum = (const Real*)m->gum;
       b.guv = (const Real*)m->guv; b.g_cs = (long)m->T * DP * DP; b.gm_cs = (long)m->nb * DP * DP;
@@ -451,7 +453,8 @@ struct Ops {
       } else {
         backward(m, p, b, st);
       }
-      filter(m, pr, (const Real*)m->yts, apply_args(m, APPLY_REV_DIFF, iter), st);
+      if (m->sqrt_form) sr_filter(m, pr, (const Real*)m->yts, apply_args(m, APPLY_REV_DIFF, iter), st);
+      else filter(m, pr, (const Real*)m->yts, apply_args(m, APPLY_REV_DIFF, iter), st);
       mh_commit(m, p, x, iter, acc, log_alpha, st);
     }
     return cuda_ok(cudaGetLastError());
@@ -480,7 +483,8 @@ struct Ops {
 
   static int sample_path(aux_model* m, const void* yt, const void* eps, uint64_t iter, void* xs,
                          double* logZ, cudaStream_t st) {
-    if (m->sqrt_form) return AUX_E_UNSUPPORTED;
+    if (m->sqrt_form && (m->mode != AUX_MODE_PER_CHAIN || m->sampler != AUX_SAMPLER_SCAN))
+      return AUX_E_UNSUPPORTED;
     const KP<Real> p = make_kp<Real>(m);
     if (m->mode != AUX_MODE_PER_CHAIN) {
       ensure_cov(m, p, st);
@@ -505,7 +509,8 @@ struct Ops {
     ApplyArgs<Real> a = apply_args(m, APPLY_EPI | APPLY_LOGZ | (br ? APPLY_SMOOTH : 0), iter);
     a.eps = (const Real*)eps;
     a.Sig = (Real*)m->Sig;
-    filter(m, p, (const Real*)yt, a, st);
+    if (m->sqrt_form) sr_filter(m, p, (const Real*)yt, a, st);
+    else filter(m, p, (const Real*)yt, a, st);
     if (br) {
       const BrTree<Real> tr = br_tree(m, false);
       br_build(m, p, tr, false, st);

@@ -31,7 +31,9 @@
 //   k_sr_reduce      per (chain, block): the block's elements folded with the operator;
 //   k_sr_scan_level  one Hillis-Steele round over the block aggregates;
 //   k_sr_apply       per (chain, block): the square-root Kalman steps from the
-//                    block's incoming prefix, with m^f, P^f and the likelihood terms.
+//                    block's incoming prefix, with m^f, P^f, the likelihood terms
+//                    and (APPLY_EPI) the backward elements (G_t, U_t) of the
+//                    (G, U) scan, chol(Sigma_t) from tria in Joseph form.
 // The aggregates use the covariance form's layout [A, U, Z, b, eta] (same size).
 #pragma once
 #include "aux_kernels.cuh"
@@ -46,8 +48,9 @@ template <typename Real, int DP> struct SrSizes {
   // state (A, U, Z), 7 scratch slots; vectors: 2 inverse diagonals, 3 temporaries,
   // b, eta of the state and of the element, signs, tria row
   static constexpr size_t RED_SMEM = (17 * MAT + 10 * VEC + VROW) * sizeof(Real);
-  // apply: F, chol Q, U^f, U^p, K, K', Ls (LS + LR), 2 scratch; vectors
-  static constexpr size_t APP_SMEM = (11 * MAT + 8 * VEC + VROW) * sizeof(Real);
+  // apply: F, chol Q, U^f, U^p, K, K', Ls (LS + LR), P^p, 3 scratch, G, G product;
+  // vectors: inverse diagonal, m^f, m^p, innovation / noise, z, U_t, signs, tria row
+  static constexpr size_t APP_SMEM = (14 * MAT + 7 * VEC + VROW) * sizeof(Real);
 };
 
 // ---------------------------------------------------------------------------
@@ -88,6 +91,7 @@ __device__ __forceinline__ void tria_reg(T (&x)[2 * DP], T* vrow, T* vsg, int la
         d1 = fma(x[c + 1], vb, d1);
       }
       const T f = -(d0 + d1) * scale;
+      __syncwarp();   // the row is read again below, not kept in registers
 #pragma unroll
       for (int c = 0; c < K; ++c) {
         const T vc = c > j ? vrow[c] : (c == j ? v0 : (T)0);
@@ -541,14 +545,21 @@ __global__ void __launch_bounds__(32, 1) k_sr_scan_level(KP<Real> p, const Real*
 // ---------------------------------------------------------------------------
 // Phase 3: square-root Kalman steps over the block from its incoming prefix
 // (the inclusive aggregate of block k - 1: b = m^f_{s-1}, U = U^f_{s-1}).
-// Writes m^f (a.mf), P^f = U^f U^f^T (a.Pf) when given, and the block's
-// log-likelihood terms to a.lz_part (APPLY_LOGZ).
+// Writes m^f (a.mf), P^f = U^f U^f^T (a.Pf) when given, and the likelihood
+// terms (APPLY_LOGZ / APPLY_STORE_Q / APPLY_REV_DIFF as the covariance form).
+// With APPLY_EPI also the backward elements of Eq. (A.14),
+//   G_t = P^f_t F^T (P^p_{t+1})^{-1},  chol(Sigma_t) = tria([(I - G_t F) U^f_t, G_t chol Q])
+//   (Joseph form of Sigma_t = P^f_t - G_t P^p_{t+1} G_t^T),
+//   U_t = m^f_t - G_t m^p_{t+1} + chol(Sigma_t) eps_t   (G_{T-1} = 0, chol(Sigma_{T-1}) = U^f_{T-1}),
+// and the block aggregates of the (G, U) scan: G_s ... G_e and
+// sum_t (G_s ... G_{t-1}) U_t.
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32, 1) k_sr_apply(KP<Real> p, ApplyArgs<Real> a) {
   refresh_delta(p);
   using Z = SrSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
+  constexpr long DD = (long)DP * DP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
   Real* SF = sm;
@@ -559,21 +570,26 @@ __global__ void __launch_bounds__(32, 1) k_sr_apply(KP<Real> p, ApplyArgs<Real> 
   Real* SKp = SK + MAT;
   Real* SLS = SKp + MAT;
   Real* SLR = SLS + MAT;
-  Real* SP = SLR + MAT;
+  Real* SP = SLR + MAT;     // P^p of the next conditioning
   Real* SY = SP + MAT;
   Real* SW = SY + MAT;
-  Real* vx = SW + MAT;
-  Real* vm = vx + VEC;     // m^f
-  Real* vmp = vm + VEC;    // m^p
-  Real* ve = vmp + VEC;    // innovation
+  Real* SB = SW + MAT;
+  Real* SG = SB + MAT;
+  Real* SGP = SG + MAT;     // G_s ... G_{t-1}
+  Real* vx = SGP + MAT;
+  Real* vm = vx + VEC;      // m^f
+  Real* vmp = vm + VEC;     // m^p
+  Real* ve = vmp + VEC;     // innovation, then the backward noise
   Real* vz = ve + VEC;
-  Real* vsg = vz + VEC;
-  Real* vrow = vsg + 2 * VEC;
+  Real* vu = vz + VEC;      // U_t
+  Real* vsg = vu + VEC;
+  Real* vrow = vsg + VEC;
   const int lane = threadIdx.x;
   const int c = blockIdx.x / p.nb, k = blockIdx.x % p.nb;
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
+  const bool epi = a.flags & APPLY_EPI;
   const Real* ytc = a.yt + (long)c * p.nT * p.d;
   int bad = 0;
   Real r[DP], x[2 * DP];
@@ -586,52 +602,62 @@ __global__ void __launch_bounds__(32, 1) k_sr_apply(KP<Real> p, ApplyArgs<Real> 
   zero_pad_row<Real, DP>(r, p.d, lane);
   __syncwarp();
   st_row<Real, DP>(SCQ, row, r, act);
-  // the incoming filtering law
+  // P^p = U^p U^p^T into SP
+  auto form_pp = [&]() {
+    Real u[DP], pr[DP];
+    ld_row<Real, DP>(SUp, row, u);
+    row_matT<Real, DP>(u, SUp, pr);
+    st_row<Real, DP>(SP, row, pr, act);
+    __syncwarp();
+  };
+  // prediction from (m^f, U^f): m^p = F m^f + b, U^p = tria([F U^f, chol Q])
+  auto predict = [&]() {
+    Real fu[DP], cq[DP];
+    mm_row<Real, DP>(SF + row * LD, SUf, fu);
+    ld_row<Real, DP>(SCQ, row, cq);
+    tria_row<Real, DP>(fu, cq, x);
+    const Real mpi = act ? dot_row_vec<Real, DP>(SF + row * LD, vm) + p.b[lane] : (Real)0;
+    tria_reg<Real, DP>(x, vrow, vsg, lane);
+    Real up[DP];
+#pragma unroll
+    for (int cc = 0; cc < DP; ++cc) up[cc] = x[cc];
+    st_row<Real, DP>(SUp, row, up, act);
+    if (act) vmp[lane] = mpi;
+    __syncwarp();
+    form_pp();
+  };
+  // the incoming filtering law, and the prediction of step s
   if (k > 0) {
     const Real* g = a.prefix + ((long)c * p.nb + (k - 1)) * Z::ES;
     ld_vec<Real, DP>(g + DP * DP + row * DP, r);
     st_row<Real, DP>(SUf, row, r, act);
     if (act) vm[lane] = g[3 * DP * DP + lane];
-  }
-  __syncwarp();
-  double lz = 0.0;
-  const double half_log2pi = 0.91893853320467274178032973640562;
-  for (int t = s; t <= e; ++t) {
-    // prediction: m^p, U^p = tria([F U^f, chol Q]) (t = 0: m0, chol P0)
-    if (t == 0) {
-      ld_vec<Real, DP>(p.P0 + row * DP, r);
-      chol_rot<Real, DP>(r, SLS, SUp, nullptr, vx, nullptr, p.d, lane, &bad);
-      __syncwarp();
-      ld_row<Real, DP>(SUp, row, r);
-      zero_pad_row<Real, DP>(r, p.d, lane);
-      __syncwarp();
-      st_row<Real, DP>(SUp, row, r, act);
-      if (act) vmp[lane] = p.m0[lane];
-    } else {
-      Real fu[DP], cq[DP];
-      mm_row<Real, DP>(SF + row * LD, SUf, fu);
-      ld_row<Real, DP>(SCQ, row, cq);
-      tria_row<Real, DP>(fu, cq, x);
-      const Real mpi = act ? dot_row_vec<Real, DP>(SF + row * LD, vm) + p.b[lane] : (Real)0;
-      tria_reg<Real, DP>(x, vrow, vsg, lane);
-      Real up[DP];
-#pragma unroll
-      for (int cc = 0; cc < DP; ++cc) up[cc] = x[cc];
-      st_row<Real, DP>(SUp, row, up, act);
-      if (act) vmp[lane] = mpi;
-    }
     __syncwarp();
-    // P^p = U^p U^p^T (SP)
-    {
-      Real u[DP], pr[DP];
-      ld_row<Real, DP>(SUp, row, u);
-      row_matT<Real, DP>(u, SUp, pr);
-      st_row<Real, DP>(SP, row, pr, act);
-      __syncwarp();
-    }
-    // conditioning: Ls, K, K', U^f
+    predict();
+  } else {
+    ld_vec<Real, DP>(p.P0 + row * DP, r);
+    chol_rot<Real, DP>(r, SLS, SUp, nullptr, vx, nullptr, p.d, lane, &bad);
+    __syncwarp();
+    ld_row<Real, DP>(SUp, row, r);
+    zero_pad_row<Real, DP>(r, p.d, lane);
+    __syncwarp();
+    st_row<Real, DP>(SUp, row, r, act);
+    if (act) vmp[lane] = p.m0[lane];
+    __syncwarp();
+    form_pp();
+  }
+  if (epi) {
+#pragma unroll
+    for (int cc = 0; cc < DP; ++cc) r[cc] = (cc == lane) ? (Real)1 : (Real)0;
+    st_row<Real, DP>(SGP, row, r, act);
+  }
+  Real ubar = (Real)0;
+  double lz = 0.0;
+  const double half_dlog2pi = 0.91893853320467274178032973640562 * p.d;
+  for (int t = s; t <= e; ++t) {
+    const long ct = (long)c * p.nT + t;
+    // conditioning on y_t: Ls, K, K', U^f
     sr_condition<Real, DP>(p, SP, SUp, SLS, SLR, vx, SK, SKp, SY, vrow, vsg, x, lane, &bad);
-    // likelihood term with Ls: z = Ls^{-1} (y - m^p)
     const Real yi = lane < p.d ? ytc[(long)t * p.d + lane] : (Real)0;
     const Real ei = lane < p.d ? yi - vmp[lane] : (Real)0;
     if (act) ve[lane] = ei;
@@ -642,22 +668,30 @@ __global__ void __launch_bounds__(32, 1) k_sr_apply(KP<Real> p, ApplyArgs<Real> 
       fsolve_vec<Real, DP>(SLS, vx, ev, vz, lane);
     }
     __syncwarp();
-    double q = (lane < p.d) ? (double)vz[lane] * (double)vz[lane] - 2.0 * log((double)vx[lane]) : 0.0;
-    q = warp_sum<double>(q);
-    lz += -(p.d * half_log2pi + 0.5 * q);
-    // m^f = m^p + K (y - m^p); U^f
+    double qz = (lane < p.d) ? (double)vz[lane] * (double)vz[lane] : 0.0;
+    double lg = (lane < p.d) ? -log((double)vx[lane]) : 0.0;
+    qz = warp_sum<double>(qz);
+    lg = warp_sum<double>(lg);
+    const double q = qz, ld = 2.0 * lg;
+    if (lane == 0) {
+      if (a.flags & APPLY_STORE_Q) { a.fq[ct] = q; a.fld[ct] = ld; }
+      if (a.flags & APPLY_REV_DIFF) lz += -0.5 * ((a.fld[ct] - ld) + (a.fq[ct] - q));
+      if (a.flags & APPLY_LOGZ) lz += -(half_dlog2pi + 0.5 * (ld + q));
+    }
     const Real mfi = act ? vmp[lane] + dot_row_vec<Real, DP>(SK + row * LD, ve) : (Real)0;
-    Real uf[DP];
+    {
+      Real uf[DP];
 #pragma unroll
-    for (int cc = 0; cc < DP; ++cc) uf[cc] = x[cc];
-    __syncwarp();
-    st_row<Real, DP>(SUf, row, uf, act);
+      for (int cc = 0; cc < DP; ++cc) uf[cc] = x[cc];
+      __syncwarp();
+      st_row<Real, DP>(SUf, row, uf, act);
+    }
     if (act) vm[lane] = mfi;
     __syncwarp();
-    const long ct = (long)c * p.nT + t;
     if (a.mf && lane < p.d) a.mf[ct * p.d + lane] = mfi;
     if (a.Pf) {
-      Real pf[DP];
+      Real pf[DP], uf[DP];
+      ld_row<Real, DP>(SUf, row, uf);
       row_matT<Real, DP>(uf, SUf, pf);
       if (lane < p.d) {
 #pragma unroll
@@ -665,8 +699,90 @@ __global__ void __launch_bounds__(32, 1) k_sr_apply(KP<Real> p, ApplyArgs<Real> 
           if (jj < p.d) a.Pf[(ct * p.d + lane) * p.d + jj] = pf[jj];
       }
     }
+    const bool last = t == p.nT - 1;
+    if (t < e || (epi && !last)) predict();   // (m^p, U^p, P^p) of step t + 1
+    if (!epi) continue;
+    // backward element of step t
+    const Real en = (lane < p.d && !(a.flags & APPLY_SMOOTH))
+                        ? (a.eps ? a.eps[ct * p.d + lane]
+                                 : philox_normal<Real>(p.seed, (uint32_t)c, iter_of(p, a.iter), PURPOSE_BACKWARD,
+                                                       (uint32_t)t, lane))
+                        : (Real)0;
+    __syncwarp();
+    if (act) ve[lane] = en;
+    __syncwarp();
+    if (last) {
+      Real g0[DP];
+      zero<Real, DP>(g0);
+      st_row<Real, DP>(SG, row, g0, act);
+      Real uf[DP];
+      ld_row<Real, DP>(SUf, row, uf);
+#pragma unroll
+      for (int cc = 0; cc < DP; ++cc) x[cc] = uf[cc];
+      __syncwarp();
+    } else {
+      // G = P^f F^T (P^p)^{-1}: rows of (P^p^{-1} F P^f)^T through chol(P^p)
+      {
+        Real pf[DP], fp[DP], uf[DP];
+        ld_row<Real, DP>(SUf, row, uf);
+        row_matT<Real, DP>(uf, SUf, pf);
+        st_row<Real, DP>(SW, row, pf, act);
+        __syncwarp();
+        mm_row<Real, DP>(SF + row * LD, SW, fp);
+        st_row<Real, DP>(SB, row, fp, act);
+        Real pp[DP];
+        ld_row<Real, DP>(SP, row, pp);
+        chol_rot<Real, DP>(pp, SLS, nullptr, SLR, vx, nullptr, p.d, lane, &bad);
+      }
+      solve_cols<Real, DP>(SLS, SLR, vx, SB, SY, SG, lane);
+      // chol(Sigma) = tria([(I - G F) U^f, G chol Q])
+      {
+        Real gf[DP];
+        mm_row<Real, DP>(SG + row * LD, SF, gf);
+        __syncwarp();
+        st_row<Real, DP>(SW, row, gf, act);
+        __syncwarp();
+      }
+      {
+        Real a1[DP], a2[DP];
+        ld_row<Real, DP>(SUf, row, a1);
+        mm_row<Real, DP, true, true>(SW + row * LD, SUf, a1);
+        mm_row<Real, DP>(SG + row * LD, SCQ, a2);
+        tria_row<Real, DP>(a1, a2, x);
+      }
+      tria_reg<Real, DP>(x, vrow, vsg, lane);
+    }
+    // U_t = m^f - G m^p_{t+1} + chol(Sigma) eps
+    Real noise = (Real)0;
+#pragma unroll
+    for (int cc = 0; cc < DP; ++cc) noise = fma(x[cc], ve[cc], noise);
+    const Real ui = mfi - (last ? (Real)0 : dot_row_vec<Real, DP>(SG + row * LD, vmp)) + noise;
+    if (act) {
+      Real gr[DP];
+      ld_row<Real, DP>(SG, row, gr);
+      st_vec<Real, DP>(a.G + ct * DD + row * DP, gr);
+      a.U[ct * DP + lane] = ui;
+      vu[lane] = ui;
+    }
+    __syncwarp();
+    // block aggregates: ubar += (G_s ... G_{t-1}) U_t; G_s ... G_t
+    ubar += dot_row_vec<Real, DP>(SGP + row * LD, vu);
+    {
+      Real gp[DP];
+      if (last) zero<Real, DP>(gp);
+      else mm_row<Real, DP>(SGP + row * LD, SG, gp);
+      __syncwarp();
+      st_row<Real, DP>(SGP, row, gp, act);
+      __syncwarp();
+    }
   }
-  if ((a.flags & APPLY_LOGZ) && lane == 0) a.lz_part[(long)c * p.nb + k] = lz;
+  if (epi && act) {
+    Real gp[DP];
+    ld_row<Real, DP>(SGP, row, gp);
+    st_vec<Real, DP>(a.gum + ((long)c * p.nb + k) * DD + row * DP, gp);
+    a.guv[((long)c * p.nb + k) * DP + lane] = ubar;
+  }
+  if ((a.flags & (APPLY_LOGZ | APPLY_REV_DIFF)) && lane == 0) a.lz_part[(long)c * p.nb + k] = lz;
   if (bad && lane == 0) atomicOr(&p.status_iter[c], ST_NOT_PD);
 }
 

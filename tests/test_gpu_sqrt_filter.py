@@ -122,13 +122,99 @@ def test_single_precision_stays_accurate_where_the_covariance_form_loses_it():
 
 def test_scope_is_reported():
     wl = _workload(3, 20, 2, seed=1)
-    s = AuxKalman(wl, dtype="f64", block_len=5, filter_form="square_root")
     x = _tt(wl.x_init, torch.float64)
-    with pytest.raises(B.AuxError):
-        s.step(x, 1)
-    s.close()
+    for kw in (dict(mode="cached"), dict(sampler="bridging")):
+        s = AuxKalman(wl, dtype="f64", block_len=5, filter_form="square_root", **kw)
+        with pytest.raises(B.AuxError):
+            s.step(x, 1)
+        s.close()
     s = AuxKalman(wl, dtype="f64", block_len=5, mode="cached", filter_form="square_root")
     logZ = torch.zeros(2, dtype=torch.float64, device="cuda")
     with pytest.raises(B.AuxError):
         s.loglik(_tt(np.zeros((2, 20, 3)), torch.float64), logZ)
+    s.close()
+
+
+@pytest.mark.parametrize("d,T,C,L,dt", CASES)
+def test_sample_path_matches_the_rts_sampler(d, T, C, L, dt):
+    """Same filter, the backward elements in Joseph form: the (G, U) scan's path is the
+    RTS sampler's (Appendix A.1) for the same eps."""
+    wl = _workload(d, T, C, seed=900 + d * T)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    tol = 1e-9 if dt == "f64" else 1e-4
+    rng = np.random.default_rng(5 * d + T)
+    yt = rng.standard_normal((C, T, d))
+    eps = rng.standard_normal((C, T, d))
+    s = AuxKalman(wl, dtype=dt, block_len=L, filter_form="square_root")
+    xs = torch.zeros((C, T, d), dtype=tdt, device="cuda")
+    logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
+    s.sample_path(_tt(yt, tdt), xs, eps=_tt(eps, tdt), logZ=logZ)
+    torch.cuda.synchronize()
+    R = 0.5 * wl.delta * np.eye(d)
+    for c in range(C):
+        kf = kalman.kalman_filter(yt[c], wl.m0, wl.P0, wl.F, wl.b, wl.Q, R)
+        ref = kalman.rts_sample(kf, wl.F, wl.b, wl.Q, eps[c])
+        assert _rel(xs[c].double().cpu().numpy(), ref) < tol
+        assert abs(logZ[c].item() - kf["logZ"]) <= (1e-9 if dt == "f64" else 1e-5) * abs(kf["logZ"])
+    s.close()
+
+
+def _step_parity(wl, dt, L, n_iters, tol_x, tol_la):
+    from oracle import mcmc, philox
+    C = wl.n_chains
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    s = AuxKalman(wl, dtype=dt, block_len=L, filter_form="square_root")
+    x = _tt(wl.x_init, tdt)
+    la = torch.zeros(C, dtype=torch.float64, device="cuda")
+    em = mcmc.SVEmission(wl.y, wl.mask)
+    model = dict(m0=wl.m0, P0=wl.P0, F=wl.F, b=wl.b, Q=wl.Q, emission=em)
+    moved = 0
+    for it in range(n_iters):
+        x_before = x.double().cpu().numpy()
+        s.step(x, 1, iter0=it, log_alpha=la)
+        torch.cuda.synchronize()
+        xg = x.double().cpu().numpy()
+        for c in range(C):
+            ref = mcmc.aux_step_philox(x_before[c], model, wl.delta, wl.mcmc_seed, c, it)
+            lu = np.log(philox.mh_uniform(wl.mcmc_seed, c, it))
+            near = abs(ref["log_alpha"] - lu) < tol_la
+            assert abs(la[c].item() - ref["log_alpha"]) < tol_la or near
+            if bool(lu < la[c].item()) != ref["accepted"]:
+                assert near
+                continue
+            if ref["accepted"]:
+                moved += 1
+                assert _rel(xg[c], ref["x_star"]) < tol_x
+            else:
+                assert np.array_equal(xg[c], x_before[c])
+    assert s.status()[0] == 0
+    s.close()
+    return moved
+
+
+def test_kalman_step_parity_sv_f64():
+    wl = workloads.stochastic_volatility(d=5, T=40, n_chains=3, delta=0.05)
+    assert _step_parity(wl, "f64", 7, 3, 1e-9, 1e-8) > 0
+
+
+def test_kalman_step_parity_sv_f32():
+    wl = workloads.stochastic_volatility(d=8, T=64, n_chains=3, delta=0.05)
+    _step_parity(wl, "f32", 8, 3, 1e-4, 2e-3)
+
+
+def test_kalman_step_full_size_sampled_step():
+    """d = 30, T = 1024, 32 chains, FP32: one step of every chain against the oracle."""
+    wl = workloads.stochastic_volatility(d=30, T=1024, n_chains=32)
+    s = AuxKalman(wl, dtype="f32", filter_form="square_root")
+    from oracle import mcmc, philox
+    x = _tt(wl.x_init, torch.float32)
+    la = torch.zeros(32, dtype=torch.float64, device="cuda")
+    s.step(x, 1, iter0=0, log_alpha=la)
+    torch.cuda.synchronize()
+    em = mcmc.SVEmission(wl.y, wl.mask)
+    model = dict(m0=wl.m0, P0=wl.P0, F=wl.F, b=wl.b, Q=wl.Q, emission=em)
+    for c in (0, 31):
+        ref = mcmc.aux_step_philox(wl.x_init[c], model, wl.delta, wl.mcmc_seed, c, 0)
+        assert abs(la[c].item() - ref["log_alpha"]) < 2e-3
+    assert s.status()[0] == 0
     s.close()
