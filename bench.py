@@ -57,7 +57,7 @@ def parse():
                     help="post-burn-in iterations of the ESS / ESJD run (0 = skip)")
     ap.add_argument("--ess-burn", type=int, default=500)
     ap.add_argument("--spatial-only", action="store_true",
-                    help="run only the lattice-model line (Section 4.3) and print it")
+                    help="run only the lattice-model line (Section 4.2) and print it")
     ap.add_argument("--cpu-sample-chains", type=int, default=0,
                     help="chain-steps in the CPU baseline sample (0 = 2 per core)")
     return ap.parse_args()
@@ -154,6 +154,17 @@ def kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz):
     (unpadded d): tables once, per-chain vectors once; None where not modelled."""
     vec = C * T * d * esz
     tab = T * d * d * esz
+    if mode == "per_chain_sqrt":
+        # square-root form: one operator per step in the reduction (29.3 d^3: 12 products,
+        # 2 Cholesky of I + W W^T, 4 triangular solves, 2 Householder triangularisations
+        # of d x 2d at 3.3 d^3); the in-block step 17.3 d^3 (3 products, 2 triangular
+        # solves with d right-hand sides, Cholesky of S, 2 triangularisations), and the
+        # backward-element epilogue 17.7 d^3 in the forward pass only
+        if kind == "reduce":
+            return C * T * 29.3 * d ** 3, None
+        if kind == "apply":
+            return C * T * (17.3 * 2 + 17.7) * d ** 3 / 2, None
+        return None, None
     if mode == "per_chain":
         if kind == "reduce":
             return C * T * reduce_flops_per_step(d, fdiag), None
@@ -200,6 +211,8 @@ def kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz):
 KERNEL_NAMES = {
     "per_chain": {"reduce": "k_filter_reduce", "apply": "k_filter_apply", "scan": "k_filter_scan_level",
                   "backward": "k_sample_backward", "mh": "k_mh + k_commit", "linearise": "k_linearise"},
+    "per_chain_sqrt": {"reduce": "k_sr_reduce", "apply": "k_sr_apply", "scan": "k_sr_scan_level",
+                       "backward": "k_sample_backward", "mh": "k_mh + k_commit", "linearise": "k_linearise"},
     "table": {"reduce": "k_mf_reduce", "apply": "k_mf_apply", "scan": "k_mean_cross",
               "backward": "k_mean_cross + k_mb_apply", "mh": "k_mh + k_commit",
               "cov_reduce": "k_cov_reduce", "cov_scan": "k_cov_scan_level_mw",
@@ -242,7 +255,7 @@ def roofline_line(mode, kind, prof, w, d, T, C, nb, nbc, fdiag, esz, peaks, step
     avg_ms = ms / launches
     flops, bytes_ = kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    name = KERNEL_NAMES["per_chain" if mode == "per_chain" else "table"].get(kind, kind)
+    name = KERNEL_NAMES[mode if mode in ("per_chain", "per_chain_sqrt") else "table"].get(kind, kind)
     line = {"path": path, "kernel": name, "launches": launches, "avg_launch_ms": avg_ms}
     if bytes_ is not None and "hbm_gbs" in peaks:
         achieved = bytes_ / (avg_ms / 1e3) / 1e9
@@ -420,7 +433,7 @@ def config_of(name, w, block_len, nb):
 
 # --------------------------------------------------------------------------- GPU arm
 def run_spatial(args, flush, stream):
-    """The lattice model of Section 4.3 (factorised prior, Student-t emission, d = 64,
+    """The lattice model of Section 4.2 (factorised prior, Student-t emission, d = 64,
     T = 1024, one chain as in the paper): delta adapted on the device to 50 %
     acceptance during warm-up, then frozen; time per MH iteration."""
     import torch
@@ -459,7 +472,7 @@ def run_spatial(args, flush, stream):
     ms_gr = sum(a.elapsed_time(b) for a, b in evg) / n_sp
     ss.device_iteration(False)
     del g
-    out = {"workload": "spatio_temporal_8x8_T1024_C1 (Section 4.3, Student-t nu = 1)",
+    out = {"workload": "spatio_temporal_8x8_T1024_C1 (Section 4.2, Student-t nu = 1)",
            "ms_per_iteration": ms_gr, "launch": "CUDA graph replay", "ms_per_iteration_eager": ms_sp,
            "value": wls.T / (ms_gr / 1e3), "unit": UNIT,
            "delta": ss.delta(), "accept_rate": accs.item() / (2 * n_sp),
@@ -512,14 +525,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         return [e0.elapsed_time(e1) for e0, e1 in ev]
 
-    def run_mode(mode, with_clocks, proposal=1, adapt=False, sampler="scan"):
+    def run_mode(mode, with_clocks, proposal=1, adapt=False, sampler="scan", filter_form="covariance"):
         """Warm-up; one profiled eager pass (per-kernel events: the kernel
         breakdown and roofline durations); then the timed pass: the MCMC
         iteration captured once in a CUDA graph (iteration index on the
         device) and replayed args.steps times; then the same steps eager
         without events, for comparison."""
         sm = AuxKalman(wl, dtype=w["dtype"], block_len=args.block_len, mode=mode, proposal=proposal,
-                       sampler=sampler)
+                       sampler=sampler, filter_form=filter_form)
         if adapt:
             sm.adapt_delta(True, target=0.5, gain=1.0)
         xm = torch.tensor(wl.x_init, dtype=tdt, device="cuda")
@@ -561,6 +574,7 @@ def run_ours(args):
         itm += args.steps
         res = {"mode": mode, "proposal": "second order" if proposal == 2 else "first order",
                "sampler": "divide-and-conquer bridging" if sampler == "bridging" else "(G, U) suffix scan",
+               "filter_form": filter_form,
                "delta": sm.delta(), "delta_adaptation": bool(adapt),
                "value": world * C * T * args.steps / (t_ms / 1e3), "unit": UNIT,
                "ms_per_step": t_ms / args.steps, "launch": "CUDA graph replay",
@@ -601,6 +615,11 @@ def run_ours(args):
             so.close()
             others[key] = r
             profs[key] = po
+        # the square-root form of the per-chain filter (the remedy Section 4.1 names)
+        so, _, _, _, po, _, r = run_mode("per_chain", False, filter_form="square_root")
+        so.close()
+        others["per_chain_square_root"] = r
+        profs["per_chain_square_root"] = po
 
     spatial = None
     if not args.headline_only and rank == 0:
@@ -655,6 +674,11 @@ def run_ours(args):
         if cov_kinds:
             ck_dom = max(cov_kinds, key=lambda k: profs["shared"][k][0])
             lines["covariance_pass"] = rl("shared", ck_dom, "covariance (Riccati) pass, once per call")
+    if "per_chain_square_root" in profs:
+        pq = profs["per_chain_square_root"]
+        kq = max((k for k in ("reduce", "apply") if pq.get(k, (0, 0))[1]), key=lambda k: pq[k][0])
+        lines["square_root_path"] = rl("per_chain_sqrt", kq, "square-root form of the per-chain filter "
+                                       "(dominant kernel)", "per_chain_square_root")
     if "cached_bridging" in profs:
         lines["bridging_sampler"] = rl("cached", "bridge", "divide-and-conquer sampler: offsets up, "
                                        "split points down, MH terms (tables shared)", "cached_bridging")

@@ -74,7 +74,7 @@ extern "C" {
 /* emission models */
 #define AUX_EMIS_LINEAR_GAUSSIAN 0
 #define AUX_EMIS_SV              1
-#define AUX_EMIS_STUDENT_T       2  /* multivariate t, scale R_y, nu degrees of freedom (Section 4.3) */
+#define AUX_EMIS_STUDENT_T       2  /* multivariate t, scale R_y, nu degrees of freedom (Section 4.2) */
 
 /* Model description (Section 2.2, Eq. (2.5); SV model of Section 4.1).
  * All arrays are HOST pointers to double, copied by aux_init_model. */
@@ -101,7 +101,7 @@ typedef struct {
   double nu;             /* Student-t degrees of freedom (> 0), ignored otherwise */
 } aux_model_desc;
 
-/* Factorised prior (Section 4.3). With AUX_EMIS_STUDENT_T,
+/* Factorised prior (Section 4.2). With AUX_EMIS_STUDENT_T,
  *   log h(y_t | x_t) = log t_nu(y_t; x_t, R_y),
  * which does not factorise over the coordinates, and F, Q, P0 must be diagonal
  * (else AUX_E_UNSUPPORTED). The auxiliary LGSSM then splits into d_x
@@ -218,7 +218,7 @@ int aux_set_proposal(aux_model *m, int32_t order);
 #define AUX_FILTER_SQUARE_ROOT 1  /* the same elements with C and J as triangular factors */
 
 /* Choose the arithmetic form of the per-chain parallel filter of aux_loglik.
- * Section 4.2 reports that the parallel filter diverged in single precision
+ * Section 4.1 reports that the parallel filter diverged in single precision
  * and names the square-root form as the remedy (the paper ran in double
  * precision instead). AUX_FILTER_SQUARE_ROOT carries every element's C and J
  * as factors U U^T and Z Z^T, forms each new covariance factor by an

@@ -16,6 +16,6 @@ Modules:
   dense   brute-force stacked-path Gaussian (Eq. (2.2)) for tiny T·d.
   bridging  divide-and-conquer (bridging) pathwise sampler (Section 2.4.2,
           Appendix A.2.3).
-  sqrt_filter  square-root form of the parallel filter (the fix Section 4.2
+  sqrt_filter  square-root form of the parallel filter (the fix Section 4.1
           names for its single-precision divergence).
 """

@@ -27,7 +27,7 @@ One step (Algorithm 2 with Gaussian dynamics, so F, b, Q are the model's):
 Emission models (gamma and its gradient):
   linear-Gaussian  log h(y|x) = log N(y; x, R_y)           (Appendix A, Eq. (A.1))
   stochastic vol.  log h(y|x) = sum_i log N(y_i; 0, exp(x_i))  (Section 4.1)
-  Student-t        log h(y|x) = log t_nu(y; x, Sigma)      (Section 4.3)
+  Student-t        log h(y|x) = log t_nu(y; x, Sigma)      (Section 4.2)
 An optional observation mask switches gamma_t off (gamma_t = 0, v_t = 0) at
 unobserved steps, as in the two-step model of Section 4.4.
 
@@ -94,7 +94,7 @@ class SVEmission:
 class StudentTEmission:
     """log h(y_t | x_t) = log t_nu(y_t; x_t, Sigma): the multivariate t with nu
     degrees of freedom, location x_t and scale matrix Sigma (the observation
-    model of Section 4.3; it does not factorise over the coordinates)."""
+    model of Section 4.2; it does not factorise over the coordinates)."""
 
     def __init__(self, y, Sigma, nu, mask=None):
         from math import lgamma

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
 package; the product path never does.
 
-Section 4.2 reports that the parallel filter diverged in single precision
+Section 4.1 reports that the parallel filter diverged in single precision
 on the stochastic-volatility model and points to the square-root version of
 the parallel filter (cited there, not printed): every covariance-like block
 of an element is carried as a factor, C = U U^T and J = Z Z^T, and new factors

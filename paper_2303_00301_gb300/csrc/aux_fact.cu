@@ -1,9 +1,9 @@
 // aux_fact.cu — the auxiliary Kalman sampler for models whose prior factorises
 // over the coordinates (F, Q, P0 diagonal), with the multivariate Student-t
-// observation model of Section 4.3, which does not factorise.
+// observation model of Section 4.2, which does not factorise.
 //
 // With R = (delta/2) I the auxiliary LGSSM of Eq. (2.7) then splits into d_x
-// independent one-dimensional LGSSMs (Section 4.3): every filtering, gain and
+// independent one-dimensional LGSSMs (Section 4.2): every filtering, gain and
 // backward-sampling quantity is a scalar per coordinate, and the covariance
 // recursion (a scalar Riccati recursion per coordinate) does not depend on
 // the chain. Layout: coordinates are the fastest index everywhere ([.][T][d]

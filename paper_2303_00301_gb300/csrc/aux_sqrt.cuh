@@ -1,6 +1,6 @@
 // aux_sqrt.cuh — square-root form of the per-chain parallel filter.
 //
-// Section 4.2 traces the single-precision divergence of the parallel filter
+// Section 4.1 traces the single-precision divergence of the parallel filter
 // to the covariance recursions and names the square-root form as the fix.
 // Here every covariance-like block of an element is carried as a factor,
 // C = U U^T and J = Z Z^T (Appendix A.2.1's elements (A, b, C, eta, J)), and a

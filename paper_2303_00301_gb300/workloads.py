@@ -16,7 +16,7 @@ Models (all with Gaussian dynamics x_t = F x_{t-1} + b + N(0, Q), x_0 ~ N(m0, P0
   is diagonal), y_t(i) = exp(x_t(i) / 2) eta_t(i), eta ~ N(0, 1). The paper's
   SV datasets are simulated from the model itself; this simulation stands in
   for them.
-* ``spatio_temporal``: the lattice model of Section 4.3: independent random
+* ``spatio_temporal``: the lattice model of Section 4.2: independent random
   walks X_t(i, j) = X_{t-1}(i, j) + N(0, sigma_X^2) on a side x side lattice
   (d = side^2), observed through a multivariate t with nu degrees of freedom
   whose precision matrix has entries tau^D for lattice distance D <= r_y and 0

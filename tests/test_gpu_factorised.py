@@ -1,4 +1,4 @@
-"""Factorised-prior path (Student-t emission, Section 4.3) against the dense FP64 oracle.
+"""Factorised-prior path (Student-t emission, Section 4.2) against the dense FP64 oracle.
 
 The library runs d independent scalar LGSSMs; the oracle runs the same auxiliary
 LGSSM as one dense d-dimensional model, so agreement also checks the factorisation.
@@ -93,7 +93,7 @@ def test_kalman_step_f32():
 
 
 def test_kalman_step_full_size_8x8_T1024_f32():
-    """The lattice model of Section 4.3 at its size (d = 64, T = 1024), one chain."""
+    """The lattice model of Section 4.2 at its size (d = 64, T = 1024), one chain."""
     wl = workloads.spatio_temporal(side=8, T=1024, n_chains=1, delta=0.05)
     _steps(wl, "f32", L=0, n_iters=1, chains=[0], tol_x=1e-4, tol_la=TOL_LA32)
 

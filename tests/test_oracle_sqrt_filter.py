@@ -1,6 +1,6 @@
 """Pins of the oracle's square-root parallel filter (oracle/sqrt_filter.py).
 
-The square-root formulas are derived, not printed by the paper (Section 4.2
+The square-root formulas are derived, not printed by the paper (Section 4.1
 names the method only), so every one is pinned against the covariance form
 (oracle/kalman.py, itself pinned to closed forms and the dense Gaussian):
 - tria: lower triangular, positive diagonal, L L^T = X X^T, also for X of

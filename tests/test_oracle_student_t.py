@@ -1,4 +1,4 @@
-"""Pins of the Student-t emission (Section 4.3) and the spatio-temporal workload."""
+"""Pins of the Student-t emission (Section 4.2) and the spatio-temporal workload."""
 import numpy as np
 import pytest
 
