@@ -478,10 +478,16 @@ int aux_set_mode(aux_model* m, int32_t mode) {
     if (!rc) rc = dev_alloc(m, &m->ms, (size_t)m->C * m->nb * m->DP * es);
     if (!rc) rc = dev_alloc(m, (void**)&m->cov_ld, (size_t)m->nb * sizeof(double));
     if (!rc) rc = dev_alloc(m, (void**)&m->cov_status, sizeof(int32_t));
+    if (!rc) rc = dev_alloc(m, (void**)&m->cov_kmap, 3 * sizeof(int));
+    if (!rc) {
+      const int km[3] = {0, 1, m->nbc - 1};
+      if (cudaMemcpy(m->cov_kmap, km, sizeof(km), cudaMemcpyHostToDevice) != cudaSuccess) rc = AUX_E_CUDA;
+    }
     if (rc) {
       m->tab = m->btab = m->zb = m->ms = m->cagg0 = m->cagg1 = nullptr;
       m->cov_ld = m->cov_ldt = nullptr;
       m->cov_status = nullptr;
+      m->cov_kmap = nullptr;
       return rc;
     }
   }

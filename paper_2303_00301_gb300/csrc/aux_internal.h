@@ -64,6 +64,7 @@ struct aux_model {
   void *cagg0 = nullptr, *cagg1 = nullptr;   // covariance scan buffers [nbc][3 DP^2]
   double *cov_ld = nullptr, *cov_ldt = nullptr;
   int32_t *cov_status = nullptr;
+  int *cov_kmap = nullptr;   // [3] blocks 0, 1, nbc - 1: the distinct covariance block aggregates
   int Lc = 0, nbc = 0;       // block length and block count of the covariance scan
   int cov_valid = 0;         // the tables match the current model
   // divide-and-conquer sampler (aux_set_sampler, aux_bridge.cuh)
