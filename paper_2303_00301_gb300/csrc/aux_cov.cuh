@@ -51,7 +51,7 @@ template <typename Real, int DP> struct CovSizes {
   static constexpr size_t MODEL = (3 * MAT + 2 * VEC) * sizeof(Real);
   static constexpr size_t RED_SMEM = MODEL + (6 * MAT + 3 * VEC) * sizeof(Real);
   static constexpr size_t SCAN_SMEM = (9 * MAT + VEC) * sizeof(Real);
-  static constexpr size_t APP_SMEM = MODEL + (10 * MAT + 3 * VEC) * sizeof(Real);
+  static constexpr size_t APP_SMEM = MODEL + (13 * MAT + 2 * VEC) * sizeof(Real);
   static constexpr int FIX_WPC = 8;
   static constexpr size_t PROD_SMEM = (2 * MAT) * sizeof(Real);
   static constexpr size_t FIX_SMEM = FIX_WPC * 2 * MAT * sizeof(Real);
@@ -438,10 +438,17 @@ __global__ void __launch_bounds__(32 * CW_SCAN)
 }
 
 // ---------------------------------------------------------------------------
-// In-block covariance filter from the prefix P^f_{s-1}, with the per-step tables.
+// In-block covariance filter from the prefix P^f_{s-1}, with the per-step tables,
+// three warps per covariance block. Per step t, after the prediction P^p_t
+// (warp 0): warp 0 factors P^p_t and warp 1 factors S_t = P^p_t + R; then
+// warp 0 forms the backward elements of step t - 1 (G_{t-1}, chol Sigma_{t-1})
+// and the running G product, warp 1 the gain tables of step t (W_t, K'_t, M_t
+// and the running M product), warp 2 the update P^f_t = P^p_t - Y^T Y. The
+// three chains share only read-only factors; P^f is double buffered so that
+// the update of step t and the epilogue of step t - 1 run side by side.
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
-__global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a) {
+__global__ void __launch_bounds__(96, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a) {
   refresh_delta(p);
   using Z = CovSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
@@ -453,27 +460,28 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
   Real* sQ = sFT + MAT;
   Real* sb = sQ + MAT;
   load_model_slots<Real, DP>(p, sF, sFT, sQ, sb);
+  __syncthreads();
   const Real* sphi = sb + VEC;
-  Real* SP = sb + 2 * VEC;     // P^f
-  Real* SX = SP + MAT;         // F P^f, then G
-  Real* SL = SX + MAT;         // chol(P^p) (LS form), scratch
+  Real* SPb = sb + 2 * VEC;    // P^f, two buffers (step t and step t - 1)
+  Real* SPP = SPb + 2 * MAT;   // P^p of the current step
+  Real* SX = SPP + MAT;        // F P^f_{t-1}, then G_{t-1}
+  Real* SL = SX + MAT;         // chol(P^p) (LS form), then Sigma, then chol(Sigma) (LS)
   Real* SLR = SL + MAT;        // chol(P^p) (right-aligned), then chol(Sigma) row-major
-  Real* SY = SLR + MAT;        // L_S^{-1} P^p, scratch
-  Real* SG = SY + MAT;         // chol(S) (LS form)
-  Real* SWm = SG + MAT;        // W_t
-  Real* SGh = SWm + MAT;       // G_s ... G_{t-1} of this covariance block
+  Real* SY0 = SLR + MAT;       // warp 0 scratch
+  Real* SG = SY0 + MAT;        // chol(S) (LS form)
+  Real* SWm = SG + MAT;        // W_t (warp 1)
+  Real* SA1 = SWm + MAT;       // warp 1 scratch
+  Real* SY2 = SA1 + MAT;       // warp 2 scratch
+  Real* SGh = SY2 + MAT;       // G_s ... G_{t-1} of this covariance block
   Real* SAH = SGh + MAT;       // M_t ... M_s of this covariance block
-  Real* SA1 = SAH + MAT;       // scratch
-  Real* vdA = SA1 + MAT;
+  Real* vdA = SAH + MAT;
   Real* vdB = vdA + VEC;
-  __syncwarp();
-  const int lane = threadIdx.x & 31, k = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, k = blockIdx.x;
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
   int bad = 0;
-  Real pprow[DP];
-  {
+  if (warp == 0) {
     Real gi[DP];
 #pragma unroll
     for (int j = 0; j < DP; ++j) gi[j] = (j == lane) ? (Real)1 : (Real)0;
@@ -486,7 +494,9 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
     ld_row<Real, DP>(S, row, r);
     st_vec<Real, DP>(a.tab + ((long)tb * p.nT + t) * DD + row * DP, r);
   };
-  auto predict = [&]() {   // P^p (pprow) and X = F P^f (SX) from P^f (SP)
+  // warp 0: P^p -> SPP and X = F P^f -> SX from P^f in SP
+  auto predict = [&](const Real* SP) {
+    Real pprow[DP];
     if (p.fdiag) {
       Real pr[DP], ph[DP], qr[DP];
       ld_row<Real, DP>(SP, row, pr);
@@ -500,64 +510,65 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
       }
       __syncwarp();
       st_row<Real, DP>(SX, row, pr, act);
+    } else {
+      Real xr[DP];
+      mm_row<Real, DP>(sF + row * LD, SP, xr);
       __syncwarp();
-      return;
-    }
-    Real xr[DP];
-    mm_row<Real, DP>(sF + row * LD, SP, xr);
-    __syncwarp();
-    st_row<Real, DP>(SX, row, xr, act);
-    __syncwarp();
-    mm_row<Real, DP>(SX + row * LD, sFT, pprow);
-    Real qr[DP];
-    ld_row<Real, DP>(sQ, row, qr);
+      st_row<Real, DP>(SX, row, xr, act);
+      __syncwarp();
+      mm_row<Real, DP>(SX + row * LD, sFT, pprow);
+      Real qr[DP];
+      ld_row<Real, DP>(sQ, row, qr);
 #pragma unroll
-    for (int j = 0; j < DP; ++j) pprow[j] += qr[j];
-    symmetrise_store<Real, DP>(SY, pprow, lane);
+      for (int j = 0; j < DP; ++j) pprow[j] += qr[j];
+      symmetrise_store<Real, DP>(SY0, pprow, lane);
+    }
+    st_row<Real, DP>(SPP, row, pprow, act);
+    __syncwarp();
   };
+  // warp 0: chol(P^p) -> SL / SLR / vdA
+  auto factor_P = [&]() {
+    Real a_[DP];
+    ld_row<Real, DP>(SPP, row, a_);
+    chol_rot<Real, DP>(a_, SL, nullptr, SLR, vdA, nullptr, p.d, lane, &bad);
+  };
+  // warp 1: chol(S), S = P^p + R -> SG / vdB
   auto factor_S = [&]() {
     Real s_[DP];
+    ld_row<Real, DP>(SPP, row, s_);
 #pragma unroll
-    for (int j = 0; j < DP; ++j) s_[j] = pprow[j] + ((j == lane && j < p.d) ? p.r : (Real)0);
+    for (int j = 0; j < DP; ++j) s_[j] += (j == lane && j < p.d) ? p.r : (Real)0;
     chol_rot<Real, DP>(s_, SG, nullptr, nullptr, vdB, nullptr, p.d, lane, &bad);
   };
-  auto factor_2 = [&]() {
-    Real a_[DP], s_[DP];
-#pragma unroll
-    for (int j = 0; j < DP; ++j) {
-      a_[j] = pprow[j];
-      s_[j] = pprow[j] + ((j == lane && j < p.d) ? p.r : (Real)0);
-    }
-    chol_rot2<Real, DP>(a_, SL, SLR, vdA, s_, SG, vdB, p.d, lane, &bad);
-  };
-  // after the factor of P^p_{t+1} (SL / SLR / vdA): G_t -> SX, chol(Sigma_t) -> SLR
-  auto epilogue = [&](int t) {
+  // warp 0, after the factor of P^p_{t+1} (SL / SLR / vdA), with P^f_t in SP and
+  // X = F P^f_t in SX: G_t -> SX, chol(Sigma_t) -> SLR
+  auto epilogue = [&](int t, const Real* SP) {
     {
       Real rr[DP];
       ld_col<Real, DP>(SX, row, rr);
-      fsolve_rot<Real, DP, true>(SL, vdA, rr, SY, lane);
+      fsolve_rot<Real, DP, true>(SL, vdA, rr, SY0, lane);
     }
     __syncwarp();
     Real sig[DP];
     if constexpr (DP >= 16) {
-      mm_tile_to_slot<Real, DP, true, true>(SY, SY, SP, SL, lane);
+      mm_tile_to_slot<Real, DP, true, true>(SY0, SY0, SP, SL, lane);
       __syncwarp();
       ld_row<Real, DP>(SL, row, sig);
     } else {
       ld_row<Real, DP>(SP, row, sig);
-      mm_col<Real, DP, true, true>(SY, row, SY, sig);
+      mm_col<Real, DP, true, true>(SY0, row, SY0, sig);
     }
     {
       Real rr[DP];
-      ld_col<Real, DP>(SY, row, rr);
+      ld_col<Real, DP>(SY0, row, rr);
       bsolve_rot<Real, DP>(SLR, vdA, rr, SX, lane);
     }
     chol_rot<Real, DP>(sig, SL, SLR, nullptr, vdA, nullptr, p.d, lane, &bad);
     store_row(TG, t, SX);
     store_row(TLS, t, SLR);
   };
-  // K'_t = r S_t^{-1} = r W^T W with W = L_S^{-1} (columns of the identity through the
-  // forward solve); M_t = (I - K_t) F = K'_t F, then SAH <- M_t SAH
+  // warp 1: K'_t = r S_t^{-1} = r W^T W with W = L_S^{-1} (columns of the identity
+  // through the forward solve); M_t = (I - K_t) F = K'_t F, then SAH <- M_t SAH
   auto gain_tables = [&](int t) {
     {
       Real r[DP];
@@ -593,31 +604,34 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
     st_row<Real, DP>(SAH, row, ah, act);
     __syncwarp();
   };
-  auto ghat = [&]() {      // SGh <- SGh G_t (G_t in SX)
+  // warp 0: SGh <- SGh G_t (G_t in SX)
+  auto ghat = [&]() {
     Real gn[DP];
     mm_row<Real, DP>(SGh + row * LD, SX, gn);
     __syncwarp();
     st_row<Real, DP>(SGh, row, gn, act);
     __syncwarp();
   };
-  // Y = L_S^{-1} P^p (columns of SY), P^f -> SP
-  auto update = [&](int t) {
+  // warp 2: Y = L_S^{-1} P^p (columns of SY2), P^f = P^p - Y^T Y -> SP
+  auto update = [&](int t, Real* SP) {
+    Real pprow[DP];
+    ld_row<Real, DP>(SPP, row, pprow);
     {
       Real rr[DP];
 #pragma unroll
       for (int j = 0; j < DP; ++j) rr[j] = pprow[j];
-      fsolve_rot<Real, DP, true>(SG, vdB, rr, SY, lane);
+      fsolve_rot<Real, DP, true>(SG, vdB, rr, SY2, lane);
     }
     __syncwarp();
     if constexpr (DP >= 16) {
       st_row<Real, DP>(SP, row, pprow, act);
       __syncwarp();
-      mm_tile_to_slot<Real, DP, true, true>(SY, SY, SP, SP, lane);
+      mm_tile_to_slot<Real, DP, true, true>(SY2, SY2, SP, SP, lane);
     } else {
       Real pf[DP];
 #pragma unroll
       for (int j = 0; j < DP; ++j) pf[j] = pprow[j];
-      mm_col<Real, DP, true, true>(SY, row, SY, pf);
+      mm_col<Real, DP, true, true>(SY2, row, SY2, pf);
       __syncwarp();
       st_row<Real, DP>(SP, row, pf, act);
     }
@@ -626,53 +640,71 @@ __global__ void __launch_bounds__(32, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
     __syncwarp();
   };
 
-  // ---- block start
-  if (k == 0) {
-    ld_vec<Real, DP>(p.P0 + row * DP, pprow);
-  } else {
-    Real r[DP];
-    ld_vec<Real, DP>(a.prefix + (long)(k - 1) * 3 * DP * DP + DP * DP + row * DP, r);
-    st_row<Real, DP>(SP, row, r, act);
-    __syncwarp();
-    predict();
+  // ---- block start: P^p_s
+  if (warp == 0) {
+    if (k == 0) {
+      Real pp[DP];
+      ld_vec<Real, DP>(p.P0 + row * DP, pp);
+      st_row<Real, DP>(SPP, row, pp, act);
+    } else {
+      Real r[DP];
+      ld_vec<Real, DP>(a.prefix + (long)(k - 1) * 3 * DP * DP + DP * DP + row * DP, r);
+      st_row<Real, DP>(SPb + MAT, row, r, act);
+      __syncwarp();
+      predict(SPb + MAT);
+    }
   }
-  factor_S();
-  store_row(TGP, s, SGh);
-  gain_tables(s);
-  update(s);
-  for (int t = s + 1; t <= e; ++t) {
-    predict();
-    factor_2();
-    epilogue(t - 1);
+  __syncthreads();
+  int cur = 0;   // P^f_t -> SPb[cur], P^f_{t-1} in SPb[cur ^ 1]
+  for (int t = s; t <= e; ++t) {
+    Real* SPc = SPb + cur * MAT;
+    Real* SPo = SPb + (cur ^ 1) * MAT;
+    if (t > s) {
+      if (warp == 0) predict(SPo);
+      __syncthreads();
+    }
+    if (warp == 0 && t > s) factor_P();
+    if (warp == 1) factor_S();
+    __syncthreads();
+    if (warp == 0) {
+      if (t > s) {
+        epilogue(t - 1, SPo);
+        ghat();
+      }
+      store_row(TGP, t, SGh);
+    } else if (warp == 1) {
+      gain_tables(t);
+    } else {
+      update(t, SPc);
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  // ---- block end: P^f_e in SPb[cur ^ 1]
+  if (warp == 0) {
+    const Real* SPe = SPb + (cur ^ 1) * MAT;
+    if (e < p.nT - 1) {
+      predict(SPe);
+      factor_P();
+      epilogue(e, SPe);
+    } else {
+      Real pf[DP], z0[DP];
+      ld_row<Real, DP>(SPe, row, pf);
+      chol_rot<Real, DP>(pf, SL, SLR, nullptr, vdA, nullptr, p.d, lane, &bad);
+      zero<Real, DP>(z0);
+      st_row<Real, DP>(SX, row, z0, act);
+      __syncwarp();
+      store_row(TG, e, SX);
+      store_row(TLS, e, SLR);
+    }
     ghat();
-    store_row(TGP, t, SGh);
-    gain_tables(t);
-    update(t);
-  }
-  if (e < p.nT - 1) {
-    predict();
-    Real a_[DP];
-#pragma unroll
-    for (int j = 0; j < DP; ++j) a_[j] = pprow[j];
-    chol_rot<Real, DP>(a_, SL, nullptr, SLR, vdA, nullptr, p.d, lane, &bad);
-    epilogue(e);
-  } else {
-    Real pf[DP], z0[DP];
-    ld_row<Real, DP>(SP, row, pf);
-    chol_rot<Real, DP>(pf, SL, SLR, nullptr, vdA, nullptr, p.d, lane, &bad);
-    zero<Real, DP>(z0);
-    st_row<Real, DP>(SX, row, z0, act);
-    __syncwarp();
-    store_row(TG, e, SX);
-    store_row(TLS, e, SLR);
-  }
-  ghat();
-  if (act) {
-    Real r[DP];
-    ld_row<Real, DP>(SGh, row, r);
-    st_vec<Real, DP>(a.cblk + (long)k * DD + row * DP, r);
-    ld_row<Real, DP>(SAH, row, r);
-    st_vec<Real, DP>(a.cblk + ((long)p.nb + k) * DD + row * DP, r);
+    if (act) {
+      Real r[DP];
+      ld_row<Real, DP>(SGh, row, r);
+      st_vec<Real, DP>(a.cblk + (long)k * DD + row * DP, r);
+      ld_row<Real, DP>(SAH, row, r);
+      st_vec<Real, DP>(a.cblk + ((long)p.nb + k) * DD + row * DP, r);
+    }
   }
   if (bad && lane == 0) atomicOr(a.status, ST_NOT_PD);
 }

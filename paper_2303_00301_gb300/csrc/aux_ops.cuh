@@ -237,7 +237,7 @@ struct Ops {
     a.R = m->L / m->Lc;
     {
       ProfScope ps(m, PK_COV_APPLY, st);
-      k_cov_apply<Real, DP><<<m->nbc, 32, CZ::APP_SMEM, st>>>(pc, a);
+      k_cov_apply<Real, DP><<<m->nbc, 96, CZ::APP_SMEM, st>>>(pc, a);
     }
     {
       ProfScope ps(m, PK_COV_PRODUCTS, st, 2);
