@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="shared", choices=["per_chain", "shared", "cached"],
                     help="execution mode of the headline number (aux_set_mode)")
+    ap.add_argument("--sampler", default="scan", choices=["scan", "bridging"],
+                    help="pathwise sampler of the headline mode (aux_set_sampler)")
+    ap.add_argument("--filter-form", default="covariance", choices=["covariance", "square_root"],
+                    help="filter form of the headline mode (aux_set_filter_form; per_chain only)")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the measurements of the other execution modes")
     ap.add_argument("--ess-iters", type=int, default=5000,
@@ -132,12 +136,6 @@ def means_flops_per_step(kind, d, fdiag, epilogue=True):
     return 2.0 * d ** 2 + fm + ((2.0 + 1.0 + 2.0) * d ** 2 if epilogue else 0.0)
 
 
-def scan_rounds(nb):
-    """(number of Hillis-Steele rounds, combines over all rounds) for nb blocks."""
-    offs = [2 ** j for j in range(max(0, math.ceil(math.log2(nb))))] if nb > 1 else []
-    return len(offs), sum(nb - o for o in offs)
-
-
 def bridge_tree_shape(T):
     """(levels J, internal nodes NN) of the dyadic tree over T - 1 unit intervals."""
     cnt, levels, nodes = T - 1, 0, 0
@@ -194,11 +192,17 @@ def kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz):
         # T1 E_l^T, chol(L), G by two triangular solves, Gamma, V and chol(V)
         levels, nodes = bridge_tree_shape(T)
         return ((T - 1) * d ** 3 + nodes * (6 + 1.0 / 3 + 2 + 4 + 1.0 / 3) * d ** 3) / (levels + 1), None
+    Lc = (T + nbc - 1) // nbc
+    ragged = nbc >= 3 and T % Lc != 0
     if kind == "cov_reduce":
-        return T * reduce_flops_per_step(d, fdiag), None
+        # the distinct block aggregates only: the first block, a generic one, a short last one
+        return min(nbc, 3 if ragged else 2) * Lc * reduce_flops_per_step(d, fdiag), None
     if kind == "cov_scan":
-        rounds, combines = scan_rounds(nbc)
-        return (combines * combine_flops(d) / max(1, rounds)), None
+        # prefixes by doubling: one operator per prefix plus one power per level but the last
+        n_end = nbc - 1 if ragged else nbc
+        levels = max(0, math.ceil(math.log2(n_end))) if n_end > 1 else 0
+        combines = (n_end - 1) + max(0, levels - 1) + (1 if ragged else 0)
+        return combines * combine_flops(d) / max(1, levels + (1 if ragged else 0)), None
     if kind == "cov_apply":
         return T * cov_apply_flops_per_step(d, fdiag), None
     if kind == "cov_products":
@@ -215,7 +219,7 @@ KERNEL_NAMES = {
                        "backward": "k_sample_backward", "mh": "k_mh + k_commit", "linearise": "k_linearise"},
     "table": {"reduce": "k_mf_reduce", "apply": "k_mf_apply", "scan": "k_mean_cross",
               "backward": "k_mean_cross + k_mb_apply", "mh": "k_mh + k_commit",
-              "cov_reduce": "k_cov_reduce", "cov_scan": "k_cov_scan_level_mw",
+              "cov_reduce": "k_cov_reduce", "cov_scan": "k_cov_scan_double_mw",
               "cov_apply": "k_cov_apply", "cov_products": "k_cov_products",
               "bridge": "k_bg_up + k_bx_root + k_bx_down + k_b_mh", "bridge_tree": "k_br_leaf + k_br_node"},
 }
@@ -598,7 +602,8 @@ def run_ours(args):
                "gpu_launches": int(sum(v[1] for v in prof.values())) + args.steps}
         return sm, xm, lam, itm, prof, ck, res
 
-    s, x, la, it, prof, ck, head = run_mode(args.mode, True)
+    s, x, la, it, prof, ck, head = run_mode(args.mode, True, sampler=args.sampler,
+                                            filter_form=args.filter_form)
     value = head["value"]
     total_ms = head["ms_per_step"] * args.steps
     accept_rate = head["accept_rate"]
