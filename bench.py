@@ -682,9 +682,10 @@ def run_ours(args):
         nbm, nbcm = shape_for("per_chain" if mode.startswith("per_chain") else mode)
         return roofline_line(mode, kind, profs[key or mode], w, d, T, C, nbm, nbcm, fdiag, esz, peaks,
                              args.steps, path)
-    roofline = rl(args.mode, dom, f"dominant kernel of the {args.mode} mode")
+    head_work = "per_chain_sqrt" if args.filter_form == "square_root" else args.mode
+    roofline = rl(head_work, dom, f"dominant kernel of the {args.mode} mode", args.mode)
     lines = {}
-    if "per_chain" in profs:
+    if "per_chain" in profs and not (args.mode == "per_chain" and args.filter_form == "square_root"):
         lines["general_path"] = rl("per_chain", "apply", "per-chain element scan (general path)")
     tmode = args.mode if args.mode != "per_chain" else ("cached" if "cached" in profs else None)
     if tmode:
