@@ -180,13 +180,13 @@ def kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz):
     if kind == "backward":  # G table, U in, x* out, MH inputs x, u, v, y in, ytilde* out (2 launches)
         return C * T * 2.0 * d ** 2 / 2, (tab + 7 * vec) / 2
     if kind == "bridge":
-        # divide-and-conquer sampler, 2 J + 2 launches per step: node offsets up the tree
+        # divide-and-conquer sampler, 2 launches per step: node offsets up the tree
         # (E_l once per node; g_l, g_r in, g out per chain-node; 2 d^2), the two ends, the
         # split points down the tree (G, Gamma, chol V once per node; x_k, x_m, g, g_r in,
         # x_l out per chain-node; 5 d^2) and the MH terms (x*, x, u, v, y in, ytilde* out)
         levels, nodes = bridge_tree_shape(T)
         byt = (4 * nodes * d * d + 8 * C * nodes * d) * esz + 6 * vec
-        return C * nodes * 7.0 * d ** 2 / (2 * levels + 2), byt / (2 * levels + 2)
+        return C * nodes * 7.0 * d ** 2 / 2, byt / 2   # k_b_sample + k_b_mh
     if kind == "bridge_tree":
         # leaf covariances LS LS^T (d^3 per step) and, per node, E_l L_r, E_l E_r,
         # T1 E_l^T, chol(L), G by two triangular solves, Gamma, V and chol(V)
@@ -221,7 +221,7 @@ KERNEL_NAMES = {
               "backward": "k_mean_cross + k_mb_apply", "mh": "k_mh + k_commit",
               "cov_reduce": "k_cov_reduce", "cov_scan": "k_cov_scan_double_mw",
               "cov_apply": "k_cov_apply", "cov_products": "k_cov_products",
-              "bridge": "k_bg_up + k_bx_root + k_bx_down + k_b_mh", "bridge_tree": "k_br_leaf + k_br_node"},
+              "bridge": "k_b_sample + k_b_mh", "bridge_tree": "k_br_leaf + k_br_node"},
 }
 
 

@@ -19,10 +19,11 @@
 //   k_br_leaf   leaf covariances Sigma_t = LS_t LS_t^T from the Cholesky table;
 //   k_br_node   one warp per node (and chain): E, L and the bridge (G, Gamma,
 //               chol V), level by level from the leaves up;
-//   k_bg_up     one warp per (chain, node): g of the node, leaves up;
-//   k_bx_root   one warp per chain: x_{T-1} = m^f + chol(P^f) eps_{T-1},
+//   k_b_sample  one cluster of 8 CTAs per chain, tree levels separated by
+//               cluster barriers: g of every node, leaves up; the two ends,
+//               x_{T-1} = m^f + chol(P^f) eps_{T-1} and
 //               x_0 = E x_{T-1} + g + chol(L) eps_0 with the root's (E, g, L);
-//   k_bx_down   one warp per (chain, node): x_l from x_k and x_m, root down;
+//               the split points x_l from x_k and x_m, root down;
 //   k_b_mh      one warp per (chain, block): the MH terms at x* (as in the
 //               scan sampler's last kernel).
 // State t draws eps_t of the backward stream (or row t of the given eps), at
@@ -64,9 +65,9 @@ struct BrLevel {
 template <typename Real, int DP> struct BrSizes {
   static constexpr int MAT = Lay<Real, DP>::MAT, VEC = Lay<Real, DP>::VEC;
   static constexpr size_t NODE_SMEM = (8 * MAT + 2 * VEC) * sizeof(Real);
-  static constexpr int WPC = 8;   // warps per CTA of the vector kernels
-  static constexpr size_t VEC_SMEM = WPC * 3 * VEC * sizeof(Real);
-  static constexpr size_t ROOT_SMEM = (2 * MAT + 3 * VEC) * sizeof(Real);
+  static constexpr int WPC = 8;   // warps per CTA of the MH-terms kernel
+  // k_b_sample: 8 warps x 3 vectors, the ends' Cholesky slot and 3 vectors
+  static constexpr size_t SAMPLE_SMEM = (8 * 3 * VEC + MAT + 3 * VEC) * sizeof(Real);
 };
 
 // E and L of node idx of level j (j == 0: a leaf) of chain c
@@ -201,36 +202,6 @@ __global__ void __launch_bounds__(32, 1) k_br_node(KP<Real> p, BrTree<Real> tr, 
   if (bad && lane == 0) atomicOr(tr.status + (tr.per_chain_status ? c : 0), ST_NOT_PD);
 }
 
-// ---------------------------------------------------------------------------
-// g of the nodes of level lv.j: g = E_l g_r + g_l (one warp per (chain, node)).
-// ---------------------------------------------------------------------------
-template <typename Real, int DP>
-__global__ void __launch_bounds__(32 * BrSizes<Real, DP>::WPC) k_bg_up(KP<Real> p, BrTree<Real> tr,
-                                                                      BrMeans<Real> mv, BrLevel lv) {
-  using Z = BrSizes<Real, DP>;
-  constexpr int VEC = Z::VEC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  Real* vg = reinterpret_cast<Real*>(smem_raw) + warp * 3 * VEC;
-  const long item = (long)blockIdx.x * Z::WPC + warp;
-  if (item >= (long)p.C * lv.cnt) return;
-  const int c = (int)(item / lv.cnt), a = (int)(item % lv.cnt);
-  const bool act = lane < DP;
-  const int row = act ? lane : 0;
-  const int jc = lv.j - 1;
-  const Real gl = node_g<Real, DP>(mv, p.nT, jc, lv.coff, 2 * a, c)[row];
-  Real out = gl;
-  if (2 * a + 1 < lv.ccnt) {
-    const Real* gr = node_g<Real, DP>(mv, p.nT, jc, lv.coff, 2 * a + 1, c);
-    if (act) vg[lane] = gr[lane];
-    __syncwarp();
-    Real e[DP];
-    ld_vec<Real, DP>(node_E<Real, DP>(tr, jc, lv.coff, 2 * a, c) + row * DP, e);
-    out = dot_rv<Real, DP>(e, vg) + gl;
-  }
-  if (act) mv.gN[((long)c * mv.NN + lv.off + a) * DP + lane] = out;
-}
-
 // the backward-stream normal of state t for the lane (0 past d)
 template <typename Real>
 __device__ __forceinline__ Real br_eps(const KP<Real>& p, const BrMeans<Real>& mv, int c, int t, int lane) {
@@ -239,21 +210,35 @@ __device__ __forceinline__ Real br_eps(const KP<Real>& p, const BrMeans<Real>& m
                 : philox_normal<Real>(p.seed, (uint32_t)c, iter_of(p, mv.iter), PURPOSE_BACKWARD, (uint32_t)t, lane);
 }
 
-// ---------------------------------------------------------------------------
-// The two ends of the path, one warp per chain (CTA): x_{T-1} | y, then x_0 | x_{T-1}, y.
-// root: level and index of the root among the internal nodes (n >= 2), or the leaf 0 (n == 1).
-// ---------------------------------------------------------------------------
+// g of node a of level lv.j for chain c: g = E_l g_r + g_l (one warp; vg: warp-private vector)
 template <typename Real, int DP>
-__global__ void __launch_bounds__(32, 1) k_bx_root(KP<Real> p, BrTree<Real> tr, BrMeans<Real> mv,
-                                                   int root_j, int root_off) {
-  using Z = BrSizes<Real, DP>;
-  constexpr int MAT = Z::MAT, VEC = Z::VEC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* SLS = reinterpret_cast<Real*>(smem_raw);
-  Real* invd = SLS + 2 * MAT;
-  Real* ve = invd + VEC;
-  Real* vx = ve + VEC;
-  const int c = blockIdx.x, lane = threadIdx.x;
+__device__ __forceinline__ void br_up_node(const KP<Real>& p, const BrTree<Real>& tr, const BrMeans<Real>& mv,
+                                           const BrLevel& lv, int c, int a, Real* vg, int lane) {
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  const int jc = lv.j - 1;
+  const bool two = 2 * a + 1 < lv.ccnt;
+  // every global load of the node first, so that their latencies overlap
+  Real e[DP];
+  if (two) ld_vec<Real, DP>(node_E<Real, DP>(tr, jc, lv.coff, 2 * a, c) + row * DP, e);
+  const Real gl = node_g<Real, DP>(mv, p.nT, jc, lv.coff, 2 * a, c)[row];
+  const Real grv = two ? node_g<Real, DP>(mv, p.nT, jc, lv.coff, 2 * a + 1, c)[row] : (Real)0;
+  Real out = gl;
+  if (two) {
+    __syncwarp();
+    if (act) vg[lane] = grv;
+    __syncwarp();
+    out = dot_rv<Real, DP>(e, vg) + gl;
+  }
+  if (act) mv.gN[((long)c * mv.NN + lv.off + a) * DP + lane] = out;
+}
+
+// the two ends of chain c's path (one warp): x_{T-1} | y, then x_0 | x_{T-1}, y.
+// root: level and index of the root among the internal nodes (n >= 2), or the leaf 0 (n == 1).
+template <typename Real, int DP>
+__device__ __forceinline__ void br_root(const KP<Real>& p, const BrTree<Real>& tr, const BrMeans<Real>& mv,
+                                        int root_j, int root_off, int c, Real* SLS, Real* invd, Real* ve,
+                                        Real* vx, int lane) {
   const bool act = lane < DP;
   const int row = act ? lane : 0;
   const int n = p.nT - 1;
@@ -279,49 +264,91 @@ __global__ void __launch_bounds__(32, 1) k_bx_root(KP<Real> p, BrTree<Real> tr, 
     if (lane < p.d) mv.xs[(long)c * p.nT * p.d + lane] = x0;
   }
   if (bad && lane == 0) atomicOr(&p.status_iter[c], ST_NOT_PD);
-  (void)MAT;
 }
 
-// ---------------------------------------------------------------------------
-// Split points of level lv.j: x_l = G (x_k - g) + Gamma x_m + g_r + chol(V) eps_l
-// (one warp per (chain, node)).
-// ---------------------------------------------------------------------------
+// split point of node a of level lv.j for chain c (one warp):
+// x_l = G (x_k - g) + Gamma x_m + g_r + chol(V) eps_l
 template <typename Real, int DP>
-__global__ void __launch_bounds__(32 * BrSizes<Real, DP>::WPC) k_bx_down(KP<Real> p, BrTree<Real> tr,
-                                                                        BrMeans<Real> mv, BrLevel lv) {
-  using Z = BrSizes<Real, DP>;
-  constexpr int VEC = Z::VEC;
+__device__ __forceinline__ void br_down_node(const KP<Real>& p, const BrTree<Real>& tr, const BrMeans<Real>& mv,
+                                             const BrLevel& lv, int c, int a, Real* v1, Real* v2, Real* v3,
+                                             int lane) {
   constexpr long DD = (long)DP * DP;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  Real* v1 = reinterpret_cast<Real*>(smem_raw) + warp * 3 * VEC;
-  Real* v2 = v1 + VEC;
-  Real* v3 = v2 + VEC;
-  const long item = (long)blockIdx.x * Z::WPC + warp;
-  if (item >= (long)p.C * lv.cnt) return;
-  const int c = (int)(item / lv.cnt), a = (int)(item % lv.cnt);
-  if (2 * a + 1 >= lv.ccnt) return;   // no split point
+  if (2 * a + 1 >= lv.ccnt) return;   // no split point (warp-uniform)
   const int n = p.nT - 1;
   const int k = a << lv.j, l = (2 * a + 1) << (lv.j - 1), m = min((a + 1) << lv.j, n);
   const bool act = lane < DP;
   const int row = act ? lane : 0;
   const long cx = (long)c * p.nT * p.d;
+  // every global load of the node first, so that their latencies overlap
+  const Real* Bn = tr.B + 3 * c * tr.nn_cs + 3 * (long)(lv.off + a) * DD;
+  Real rg[DP], rm[DP], rv[DP];
+  ld_vec<Real, DP>(Bn + row * DP, rg);
+  ld_vec<Real, DP>(Bn + DD + row * DP, rm);
+  ld_vec<Real, DP>(Bn + 2 * DD + row * DP, rv);
   const Real g = node_g<Real, DP>(mv, p.nT, lv.j, lv.off, a, c)[row];
   const Real gr = node_g<Real, DP>(mv, p.nT, lv.j - 1, lv.coff, 2 * a + 1, c)[row];
   const Real xk = lane < p.d ? mv.xs[cx + (long)k * p.d + lane] : (Real)0;
   const Real xm = lane < p.d ? mv.xs[cx + (long)m * p.d + lane] : (Real)0;
   const Real el = br_eps<Real>(p, mv, c, l, lane);
+  __syncwarp();
   if (act) { v1[lane] = xk - g; v2[lane] = xm; v3[lane] = el; }
   __syncwarp();
-  const Real* Bn = tr.B + 3 * c * tr.nn_cs + 3 * (long)(lv.off + a) * DD;
-  Real r[DP];
-  ld_vec<Real, DP>(Bn + row * DP, r);
-  Real x = dot_rv<Real, DP>(r, v1) + gr;
-  ld_vec<Real, DP>(Bn + DD + row * DP, r);
-  x += dot_rv<Real, DP>(r, v2);
-  ld_vec<Real, DP>(Bn + 2 * DD + row * DP, r);
-  x += dot_rv<Real, DP>(r, v3);
+  Real x = dot_rv<Real, DP>(rg, v1) + gr;
+  x += dot_rv<Real, DP>(rm, v2);
+  x += dot_rv<Real, DP>(rv, v3);
   if (lane < p.d) mv.xs[cx + (long)l * p.d + lane] = x;
+}
+
+// all levels of the tree, in kernel parameters
+constexpr int BR_MAX_LEVELS = 30;
+struct BrLevels {
+  BrLevel l[BR_MAX_LEVELS];
+  int n;
+};
+
+// one cluster of BR_CLUSTER CTAs per chain; a cluster barrier (hardware,
+// release / acquire at cluster scope, so the global writes of one level are
+// visible to the next level's readers) separates the tree levels
+constexpr int BR_CLUSTER = 8, BR_WARPS = 8;
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// The draw of one chain per cluster: node offsets g up the tree (level by
+// level), the two ends (CTA 0, warp 0), the split points down the tree. The
+// warps of the cluster share the nodes of a level; every thread reaches every
+// barrier.
+// ---------------------------------------------------------------------------
+template <typename Real, int DP>
+__global__ void __cluster_dims__(BR_CLUSTER, 1, 1) __launch_bounds__(32 * BR_WARPS)
+    k_b_sample(KP<Real> p, BrTree<Real> tr, BrMeans<Real> mv, BrLevels lv, int root_j, int root_off) {
+  using Z = BrSizes<Real, DP>;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Real* v1 = sm + warp * 3 * VEC;
+  Real* v2 = v1 + VEC;
+  Real* v3 = v2 + VEC;
+  Real* SLS = sm + BR_WARPS * 3 * VEC;     // the ends: Cholesky slot and vectors
+  Real* invd = SLS + MAT;
+  Real* ve = invd + VEC;
+  Real* vx = ve + VEC;
+  const int c = blockIdx.x / BR_CLUSTER, rank = blockIdx.x % BR_CLUSTER;
+  const int gw = rank * BR_WARPS + warp, nw = BR_CLUSTER * BR_WARPS;
+  for (int j = 0; j < lv.n; ++j) {
+    const BrLevel L = lv.l[j];
+    for (int a = gw; a < L.cnt; a += nw) br_up_node<Real, DP>(p, tr, mv, L, c, a, v1, lane);
+    cluster_barrier();
+  }
+  if (rank == 0 && warp == 0) br_root<Real, DP>(p, tr, mv, root_j, root_off, c, SLS, invd, ve, vx, lane);
+  cluster_barrier();
+  for (int j = lv.n - 1; j >= 0; --j) {
+    const BrLevel L = lv.l[j];
+    for (int a = gw; a < L.cnt; a += nw) br_down_node<Real, DP>(p, tr, mv, L, c, a, v1, v2, v3, lane);
+    cluster_barrier();
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -312,6 +312,7 @@ int fact_init(aux_model* m, const aux_model_desc* desc, const std::vector<double
 // buffers of the bridging sampler for the handle's current mode (aux_set_sampler)
 int br_alloc(aux_model* m) {
   if (m->sampler != AUX_SAMPLER_BRIDGING) return AUX_OK;
+  if (m->T - 1 > (1 << 29)) return AUX_E_UNSUPPORTED;   // tree depth beyond the kernel's level table
   const size_t es = m->esz, DP = (size_t)m->DP, DD = DP * DP;
   const int n = m->T - 1;
   int NN = 0;

@@ -361,27 +361,19 @@ struct Ops {
     m->br_valid = 1;
   }
 
-  // node offsets up the tree, the two ends, the split points down the tree
+  // node offsets up the tree, the two ends, the split points down the tree:
+  // one cluster per chain (k_b_sample)
   static void br_sample(aux_model* m, const KP<Real>& p, const BrTree<Real>& tr, BrMeans<Real> mv,
                         cudaStream_t st) {
     const std::vector<BrLevel> lv = br_levels(m);
     mv.gN = (Real*)m->br_g;
     mv.NN = std::max(m->br_NN, 1);
-    for (const BrLevel& l : lv) {
-      ProfScope ps(m, PK_BRIDGE, st);
-      const long items = (long)m->C * l.cnt;
-      k_bg_up<Real, DP><<<(int)((items + BZ::WPC - 1) / BZ::WPC), 32 * BZ::WPC, BZ::VEC_SMEM, st>>>(p, tr, mv, l);
-    }
-    {
-      ProfScope ps(m, PK_BRIDGE, st);
-      const int rj = lv.empty() ? 0 : lv.back().j, ro = lv.empty() ? 0 : lv.back().off;
-      k_bx_root<Real, DP><<<m->C, 32, BZ::ROOT_SMEM, st>>>(p, tr, mv, rj, ro);
-    }
-    for (auto it = lv.rbegin(); it != lv.rend(); ++it) {
-      ProfScope ps(m, PK_BRIDGE, st);
-      const long items = (long)m->C * it->cnt;
-      k_bx_down<Real, DP><<<(int)((items + BZ::WPC - 1) / BZ::WPC), 32 * BZ::WPC, BZ::VEC_SMEM, st>>>(p, tr, mv, *it);
-    }
+    BrLevels L{};
+    L.n = (int)lv.size();
+    for (int i = 0; i < L.n && i < BR_MAX_LEVELS; ++i) L.l[i] = lv[i];
+    const int rj = lv.empty() ? 0 : lv.back().j, ro = lv.empty() ? 0 : lv.back().off;
+    ProfScope ps(m, PK_BRIDGE, st);
+    k_b_sample<Real, DP><<<m->C * BR_CLUSTER, 32 * BR_WARPS, BZ::SAMPLE_SMEM, st>>>(p, tr, mv, L, rj, ro);
   }
 
   static void br_mh_terms(aux_model* m, const KP<Real>& p, const BackArgs<Real>& b, cudaStream_t st) {
