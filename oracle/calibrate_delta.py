@@ -39,7 +39,8 @@ def calibrate(wl_model, x0, delta0, n_iters, target=0.5, seed=1, c=1.0):
     return float(np.mean(hist[half:])), float(np.mean(acc[half:]))
 
 
-def run_chains_adaptive(x0, model, delta0, n_iters, target=0.5, c=1.0, seed=1, order=1, iter0=0):
+def run_chains_adaptive(x0, model, delta0, n_iters, target=0.5, c=1.0, seed=1, order=1, iter0=0,
+                        sampler="rts"):
     """Chains that share one delta adapted on line by the rule of `calibrate`,
     with a_k the mean over the chains of min(1, exp(log alpha_k)) (a
     non-finite log alpha counts as 0). Step k of every chain uses the delta
@@ -55,7 +56,7 @@ def run_chains_adaptive(x0, model, delta0, n_iters, target=0.5, c=1.0, seed=1, o
         delta = float(np.exp(log_d))
         acc = 0.0
         for ch in range(C):
-            st = mcmc.aux_step_philox(x[ch], model, delta, seed, ch, iter0 + k, order=order)
+            st = mcmc.aux_step_philox(x[ch], model, delta, seed, ch, iter0 + k, order=order, sampler=sampler)
             x[ch] = st["x_new"]
             las[k, ch] = st["log_alpha"]
             acc += float(np.exp(min(0.0, st["log_alpha"]))) if np.isfinite(st["log_alpha"]) else 0.0

@@ -199,6 +199,26 @@ def test_samplers_agree_in_law_at_full_size():
     assert np.mean(np.abs(ma - mb)) < 0.15, np.mean(np.abs(ma - mb))
 
 
+@pytest.mark.parametrize("mode", ["per_chain", "cached"])
+def test_bridging_with_delta_adaptation_follows_the_oracle(mode):
+    """On-device delta adaptation with the bridging sampler: delta trajectory and states
+    against the oracle's pooled Robbins-Monro rule with the same sampler (FP64)."""
+    from oracle import calibrate_delta
+    wl = workloads.stochastic_volatility(d=3, T=21, n_chains=3, delta=0.3)
+    s = AuxKalman(wl, dtype="f64", block_len=4, mode=mode, sampler="bridging")
+    s.adapt_delta(True, target=0.5, gain=1.0)
+    x = _tt(wl.x_init, torch.float64)
+    n = 5
+    s.step(x, n, iter0=0)
+    torch.cuda.synchronize()
+    xo, deltas, _ = calibrate_delta.run_chains_adaptive(wl.x_init, _oracle_model(wl), wl.delta, n,
+                                                        seed=wl.mcmc_seed, sampler="bridging")
+    log_d = np.log(deltas[-1])
+    assert abs(s.delta() - float(np.exp(log_d))) < 1e-9 * float(np.exp(log_d))
+    assert _rel(x.cpu().numpy(), xo) < 1e-9
+    s.close()
+
+
 def test_bridging_is_unsupported_on_the_factorised_path():
     wl = workloads.spatio_temporal(side=2, T=8, n_chains=1, delta=0.3)
     from paper_2303_00301_gb300 import _binding as B

@@ -26,12 +26,12 @@ def _tt(a, dtype):
     return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-def _eager_and_replayed(wl, dt, L, mode="per_chain", proposal=1, adapt=False, n=3, reps=3):
+def _eager_and_replayed(wl, dt, L, mode="per_chain", proposal=1, adapt=False, n=3, reps=3, **kw):
     tdt = torch.float64 if dt == "f64" else torch.float32
     C = wl.n_chains
     out = []
     for graph in (False, True):
-        s = AuxKalman(wl, dtype=dt, block_len=L, mode=mode, proposal=proposal)
+        s = AuxKalman(wl, dtype=dt, block_len=L, mode=mode, proposal=proposal, **kw)
         if adapt:
             s.adapt_delta(True, target=0.5, gain=1.0)
         x = _tt(wl.x_init, tdt)
@@ -85,6 +85,19 @@ def test_replay_factorised_path(dt):
     (xa, aa, la, _, _), (xb, ab, lb, _, itb) = _eager_and_replayed(wl, dt, 6)
     assert torch.equal(xa, xb) and torch.equal(aa, ab) and torch.equal(la, lb)
     assert itb == 10
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_replay_with_the_bridging_sampler(mode):
+    wl = workloads.stochastic_volatility(d=5, T=37, n_chains=3, delta=0.05)
+    (xa, aa, la, _, _), (xb, ab, lb, _, _) = _eager_and_replayed(wl, "f32", 6, mode, sampler="bridging")
+    assert torch.equal(xa, xb) and torch.equal(aa, ab) and torch.equal(la, lb)
+
+
+def test_replay_with_the_square_root_filter():
+    wl = workloads.stochastic_volatility(d=4, T=30, n_chains=2, delta=0.05)
+    (xa, aa, la, _, _), (xb, ab, lb, _, _) = _eager_and_replayed(wl, "f32", 5, filter_form="square_root")
+    assert torch.equal(xa, xb) and torch.equal(aa, ab) and torch.equal(la, lb)
 
 
 def test_counter_can_be_reset_and_disabled():

@@ -91,6 +91,29 @@ def test_loglik_filter_parity(d, T, C, L, dt, mode):
     s.close()
 
 
+@pytest.mark.parametrize("mode", ["shared", "cached"])
+@pytest.mark.parametrize("T,L", [(8, 8), (5, 4), (9, 4), (10, 4), (12, 4), (21, 4), (64, 4)])
+def test_covariance_doubling_scan_shapes(T, L, mode):
+    """p = 16 covariance pass (distinct block aggregates, prefixes by doubling) over
+    2, 3 and more covariance blocks with and without a short last block."""
+    d, C = 16, 2
+    wl = _lgssm_workload(d, T, C, seed=40 + T)
+    yt = np.random.default_rng(T).standard_normal((C, T, d))
+    s = AuxKalman(wl, dtype="f64", block_len=L, mode=mode)
+    logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
+    mf = torch.zeros((C, T, d), dtype=torch.float64, device="cuda")
+    Pf = torch.zeros((C, T, d, d), dtype=torch.float64, device="cuda")
+    s.loglik(_tt(yt, torch.float64), logZ, mf, Pf)
+    torch.cuda.synchronize()
+    R = 0.5 * wl.delta * np.eye(d)
+    for c in range(C):
+        kf = kalman.kalman_filter(yt[c], wl.m0, wl.P0, wl.F, wl.b, wl.Q, R)
+        assert abs(logZ[c].item() - kf["logZ"]) <= 1e-9 * abs(kf["logZ"])
+        assert _rel(mf[c].cpu().numpy(), kf["mf"]) < 1e-9
+        assert _rel(Pf[c].cpu().numpy(), kf["Pf"]) < 1e-9
+    s.close()
+
+
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("d,T,C,L,dt", FILTER_CASES)
 def test_sample_path_parity(d, T, C, L, dt, mode):
