@@ -69,7 +69,8 @@ template <typename Real, int DP> struct MeanSizes {
   static constexpr size_t smem(int nt) {
     return (size_t)(NBUF * nt * MAT + MAT + MEAN_CHAINS * 3 * VEC) * sizeof(Real);
   }
-  static constexpr size_t RED = smem(1), APP = smem(4), BWD = smem(1), CROSS = smem(1);
+  static constexpr size_t RED = smem(1), APP = smem(4), BWD = smem(1);
+  static constexpr size_t CROSS = (size_t)((NBUF + 1) * MAT + 3 * VEC) * sizeof(Real);   // one warp
 };
 
 // lane value -> vector slot (all lanes of the warp call it)
@@ -229,10 +230,13 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_reduce(KP<Real> p
 //            m^f_{e_0} = in[c][0] and m^f_{e_k} = AH_k m^f_{e_{k-1}} + in[c][k];
 //   backward (mats = GH): out[c][k] = x*_{e_k + 1}, k = nb-1 .. 0, from
 //            out[c][nb-1] = 0 and x*_{e_{k-1} + 1} = GH_k out[c][k] + in[c][k].
-// Grid: ceil(C / MEAN_CHAINS) CTAs.
+// Grid: C CTAs of one warp. The recursion is one dependent matrix-vector
+// product per block; a CTA per chain keeps each step's copy, barrier and
+// product on its own SM (eight chains per CTA put eight chains' steps
+// behind one barrier on four SMs).
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
-__global__ void __launch_bounds__(32 * MEAN_CHAINS)
+__global__ void __launch_bounds__(32)
     k_mean_cross(KP<Real> p, const Real* __restrict__ mats, const Real* __restrict__ in,
                  Real* __restrict__ out, int backward) {
   using Z = MeanSizes<Real, DP>;
@@ -240,9 +244,9 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS)
   constexpr long DD = (long)DP * DP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* buf = reinterpret_cast<Real*>(smem_raw);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  Real* vq = buf + (NBUF + 1) * MAT + warp * 3 * VEC;
-  const int c = blockIdx.x * MEAN_CHAINS + warp;
+  const int lane = threadIdx.x;
+  Real* vq = buf + (NBUF + 1) * MAT;
+  const int c = blockIdx.x;
   const bool valid = c < p.C;
   const bool act = lane < DP;
   const int row = act ? lane : 0;

@@ -273,7 +273,7 @@ struct Ops {
       k_mf_reduce<Real, DP, MEAN_CPW><<<grid, MEAN_THREADS, MZ::RED, st>>>(p, a); }
     a.x = nullptr;
     { ProfScope ps(m, PK_SCAN, st);
-      k_mean_cross<Real, DP><<<(m->C + MEAN_CHAINS - 1) / MEAN_CHAINS, 32 * MEAN_CHAINS, MZ::CROSS, st>>>(
+      k_mean_cross<Real, DP><<<m->C, 32, MZ::CROSS, st>>>(
           p, (const Real*)m->btab + (long)BAH * m->nb * DD, a.z, (Real*)m->ms, 0); }
     a.mstart = (const Real*)m->ms;
     { ProfScope ps(m, PK_APPLY, st);
@@ -294,7 +294,7 @@ struct Ops {
   static void backward_tab(aux_model* m, const KP<Real>& p, BackArgs<Real> b, cudaStream_t st) {
     ProfScope ps(m, PK_BACKWARD, st, 2);
     Real* xnext = (Real*)m->zb;
-    k_mean_cross<Real, DP><<<(m->C + MEAN_CHAINS - 1) / MEAN_CHAINS, 32 * MEAN_CHAINS, MZ::CROSS, st>>>(
+    k_mean_cross<Real, DP><<<m->C, 32, MZ::CROSS, st>>>(
         p, b.gum, b.guv, xnext, 1);
     k_mb_apply<Real, DP, MEAN_CPW><<<mean_grid(m), MEAN_THREADS, MZ::BWD, st>>>(p, b, xnext);
   }
