@@ -67,6 +67,8 @@ __global__ void __launch_bounds__(32, 1) k_cov_reduce(KP<Real> p, Real* __restri
                                                      int32_t* __restrict__ status,
                                                      const int* __restrict__ kmap, Real* __restrict__ dst1,
                                                      Real* __restrict__ dst2) {
+  pdl_wait();
+  pdl_trigger();
   refresh_delta(p);
   using Z = CovSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
@@ -429,6 +431,8 @@ template <typename Real, int DP>
 __global__ void __launch_bounds__(32 * CW_SCAN)
     k_cov_scan_double_mw(KP<Real> p, Real* __restrict__ P, const Real* __restrict__ Gk,
                          Real* __restrict__ Gk2, int src, int dst, int cnt, int32_t* __restrict__ status) {
+  pdl_wait();
+  pdl_trigger();
   constexpr long DD = (long)DP * DP;
   const int i = blockIdx.x;
   if (i < cnt)
@@ -449,6 +453,8 @@ __global__ void __launch_bounds__(32 * CW_SCAN)
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
 __global__ void __launch_bounds__(96, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a) {
+  pdl_wait();
+  pdl_trigger();
   refresh_delta(p);
   using Z = CovSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
@@ -718,6 +724,8 @@ __global__ void __launch_bounds__(96, 1) k_cov_apply(KP<Real> p, CovArgs<Real> a
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32) k_cov_products(KP<Real> p, CovArgs<Real> a, int nbc) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int MAT = CovSizes<Real, DP>::MAT, LD = Lay<Real, DP>::LD;
   constexpr long DD = (long)DP * DP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -769,6 +777,8 @@ __global__ void __launch_bounds__(32) k_cov_products(KP<Real> p, CovArgs<Real> a
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32 * CovSizes<Real, DP>::FIX_WPC)
     k_cov_gp_fix(KP<Real> p, CovArgs<Real> a, int Lc, int nbc) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int MAT = CovSizes<Real, DP>::MAT, LD = Lay<Real, DP>::LD;
   constexpr int WPC = CovSizes<Real, DP>::FIX_WPC;
   constexpr long DD = (long)DP * DP;

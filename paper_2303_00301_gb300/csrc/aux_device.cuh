@@ -22,6 +22,17 @@ namespace auxk {
 
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
+// ---------------------------------------------------------------- launch order
+// Programmatic dependent launch (sm_90 and later). A kernel launched with the
+// programmatic-serialization attribute may be scheduled before its
+// predecessor in the stream has finished: pdl_wait() blocks until the
+// predecessor grid has completed and its memory writes are visible (it returns
+// at once for a kernel launched without the attribute), and pdl_trigger()
+// lets the successor be scheduled. Kernels on the table-mode step call both
+// first thing, so their reads always follow the predecessor's writes.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------- Philox
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 #pragma unroll

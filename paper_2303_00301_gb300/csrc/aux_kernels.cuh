@@ -59,7 +59,11 @@ __device__ __forceinline__ uint64_t iter_of(const KP<Real>& p, uint64_t iter) {
 }
 
 // advance the device iteration counter (last launch of an MCMC iteration)
-static __global__ void k_iter_next(uint64_t* iter_dev) { *iter_dev += 1; }
+static __global__ void k_iter_next(uint64_t* iter_dev) {
+  pdl_wait();
+  pdl_trigger();
+  *iter_dev += 1;
+}
 
 // With on-device delta adaptation the kernels take r = delta / 2 from device
 // memory (written by k_adapt_delta of the previous iteration).
@@ -1091,6 +1095,8 @@ __global__ void k_mh(KP<Real> p, const double* __restrict__ mh_part,
                      const double* __restrict__ lz_part, uint64_t iter, uint32_t* acc_count,
                      double* log_alpha, int32_t* status, int32_t* __restrict__ accept,
                      double* __restrict__ la_all) {
+  pdl_wait();
+  pdl_trigger();
   const int c = blockIdx.x;
   __shared__ double red[32];
   double sacc = 0.0;
@@ -1126,6 +1132,8 @@ __global__ void k_mh(KP<Real> p, const double* __restrict__ mh_part,
 // ---------------------------------------------------------------------------
 static __global__ void k_adapt_delta(const double* __restrict__ la_all, int C, double* __restrict__ delta,
                                      int* __restrict__ count, double target, double gain) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double red[32];
   double s = 0.0;
   for (int c = threadIdx.x; c < C; c += blockDim.x) {
@@ -1150,6 +1158,8 @@ static __global__ void k_adapt_delta(const double* __restrict__ la_all, int C, d
 template <typename Real>
 __global__ void k_commit(KP<Real> p, Real* __restrict__ x, const Real* __restrict__ xs,
                          const int32_t* __restrict__ accept) {
+  pdl_wait();
+  pdl_trigger();
   const long per_chain = (long)p.nT * p.d;
   const long n = (long)p.C * per_chain;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)

@@ -117,6 +117,8 @@ __device__ __forceinline__ void load_ryinv(const KP<Real>& p, Real* sRy) {
 // ---------------------------------------------------------------------------
 template <typename Real, int DP, int CPW>
 __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_reduce(KP<Real> p, MeanArgs<Real> a) {
+  pdl_wait();
+  pdl_trigger();
   refresh_delta(p);
   using Z = MeanSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
@@ -239,6 +241,8 @@ template <typename Real, int DP>
 __global__ void __launch_bounds__(32)
     k_mean_cross(KP<Real> p, const Real* __restrict__ mats, const Real* __restrict__ in,
                  Real* __restrict__ out, int backward) {
+  pdl_wait();
+  pdl_trigger();
   using Z = MeanSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
   constexpr long DD = (long)DP * DP;
@@ -291,6 +295,8 @@ __global__ void __launch_bounds__(32)
 // ---------------------------------------------------------------------------
 template <typename Real, int DP, int CPW>
 __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_apply(KP<Real> p, MeanArgs<Real> a) {
+  pdl_wait();
+  pdl_trigger();
   refresh_delta(p);
   using Z = MeanSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
@@ -445,6 +451,8 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_apply(KP<Real> p,
 template <typename Real, int DP, int CPW>
 __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW)
     k_mb_apply(KP<Real> p, BackArgs<Real> b, const Real* __restrict__ xnext) {
+  pdl_wait();
+  pdl_trigger();
   refresh_delta(p);
   using Z = MeanSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;

@@ -50,6 +50,29 @@ KP<Real> make_kp(const aux_model* m) {
   return p;
 }
 
+// Launch with programmatic stream serialisation when the stream is not being
+// captured: the kernel may then be scheduled while its predecessor in the
+// stream runs, and waits for it in pdl_wait(). Under stream capture the launch
+// is an ordinary one (measured: inside a CUDA graph the programmatic edges
+// made the step slower, 0.569 -> 0.590 ms, while eager steps gained 5 %).
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = cs == cudaStreamCaptureStatusNone ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <typename Real, int DP>
 struct Ops {
   using Z = Sizes<Real, DP>;
@@ -108,15 +131,15 @@ struct Ops {
   static void mh_commit(aux_model* m, const KP<Real>& p, Real* x, uint64_t iter, uint32_t* acc,
                         double* log_alpha, cudaStream_t st) {
     ProfScope ps(m, PK_MH, st, 2 + (m->adapt ? 1 : 0) + (m->dev_iter ? 1 : 0));
-    k_mh<Real><<<m->C, 128, 0, st>>>(p, m->mh_part, m->lz_part, iter, acc, log_alpha, m->status,
-                                     m->accept, m->la_all);
+    launch_pdl(k_mh<Real>, m->C, 128, 0, st, p, (const double*)m->mh_part, (const double*)m->lz_part, iter,
+               acc, log_alpha, m->status, m->accept, m->la_all);
     const long n = (long)m->C * m->T * m->d;
     const int grid = (int)std::min<long>((n + 255) / 256, 152L * 8);
-    k_commit<Real><<<grid, 256, 0, st>>>(p, x, (const Real*)m->xs, m->accept);
+    launch_pdl(k_commit<Real>, grid, 256, 0, st, p, x, (const Real*)m->xs, (const int32_t*)m->accept);
     if (m->adapt)
-      k_adapt_delta<<<1, 256, 0, st>>>(m->la_all, m->C, m->delta_dev, m->adapt_count, m->adapt_target,
-                                       m->adapt_gain);
-    if (m->dev_iter) k_iter_next<<<1, 1, 0, st>>>(m->iter_dev);
+      launch_pdl(k_adapt_delta, 1, 256, 0, st, (const double*)m->la_all, m->C, m->delta_dev, m->adapt_count,
+                 m->adapt_target, m->adapt_gain);
+    if (m->dev_iter) launch_pdl(k_iter_next, 1, 1, 0, st, m->iter_dev);
   }
 
 
@@ -198,8 +221,8 @@ struct Ops {
       {
         ProfScope ps(m, PK_COV_REDUCE, st);
         cudaMemsetAsync(m->cov_status, 0, sizeof(int32_t), st);
-        k_cov_reduce<Real, DP><<<nbc == 1 ? 1 : (rag ? 3 : 2), 32, CZ::RED_SMEM, st>>>(
-            pc, b0, m->cov_status, m->cov_kmap, Q0, tail);
+        launch_pdl(k_cov_reduce<Real, DP>, nbc == 1 ? 1 : (rag ? 3 : 2), 32, CZ::RED_SMEM, st, pc, b0,
+                   m->cov_status, (const int*)m->cov_kmap, Q0, tail);
       }
       const int n_end = rag ? nbc - 1 : nbc;
       Real *gk = Q0, *gk2 = Q1;
@@ -207,14 +230,14 @@ struct Ops {
         ProfScope ps(m, PK_COV_SCAN, st);
         const int cnt = std::min(pow2, n_end - pow2);
         const int next = 2 * pow2 < n_end ? 1 : 0;
-        k_cov_scan_double_mw<Real, DP><<<cnt + next, 32 * CW_SCAN, CovScanMW<Real, DP>::SMEM, st>>>(
-            pc, b0, gk, gk2, 0, pow2, cnt, m->cov_status);
+        launch_pdl(k_cov_scan_double_mw<Real, DP>, cnt + next, 32 * CW_SCAN, CovScanMW<Real, DP>::SMEM, st, pc,
+                   b0, (const Real*)gk, gk2, 0, pow2, cnt, m->cov_status);
         Real* tmp = gk; gk = gk2; gk2 = tmp;
       }
       if (rag) {
         ProfScope ps(m, PK_COV_SCAN, st);
-        k_cov_scan_double_mw<Real, DP><<<1, 32 * CW_SCAN, CovScanMW<Real, DP>::SMEM, st>>>(
-            pc, b0, tail, nullptr, nbc - 2, nbc - 1, 1, m->cov_status);
+        launch_pdl(k_cov_scan_double_mw<Real, DP>, 1, 32 * CW_SCAN, CovScanMW<Real, DP>::SMEM, st, pc, b0,
+                   (const Real*)tail, (Real*)nullptr, nbc - 2, nbc - 1, 1, m->cov_status);
       }
     } else {
       {
@@ -237,13 +260,13 @@ struct Ops {
     a.R = m->L / m->Lc;
     {
       ProfScope ps(m, PK_COV_APPLY, st);
-      k_cov_apply<Real, DP><<<m->nbc, 96, CZ::APP_SMEM, st>>>(pc, a);
+      launch_pdl(k_cov_apply<Real, DP>, m->nbc, 96, CZ::APP_SMEM, st, pc, a);
     }
     {
       ProfScope ps(m, PK_COV_PRODUCTS, st, 2);
-      k_cov_products<Real, DP><<<m->nb, 32, CZ::PROD_SMEM, st>>>(p, a, m->nbc);
-      k_cov_gp_fix<Real, DP><<<(m->T + CZ::FIX_WPC - 1) / CZ::FIX_WPC, 32 * CZ::FIX_WPC, CZ::FIX_SMEM,
-                               st>>>(p, a, m->Lc, m->nbc);
+      launch_pdl(k_cov_products<Real, DP>, m->nb, 32, CZ::PROD_SMEM, st, p, a, m->nbc);
+      launch_pdl(k_cov_gp_fix<Real, DP>, (m->T + CZ::FIX_WPC - 1) / CZ::FIX_WPC, 32 * CZ::FIX_WPC, CZ::FIX_SMEM,
+                 st, p, a, m->Lc, m->nbc);
     }
   }
 
@@ -270,14 +293,14 @@ struct Ops {
   static void means_filter(aux_model* m, const KP<Real>& p, MeanArgs<Real> a, cudaStream_t st) {
     const int grid = mean_grid(m);
     { ProfScope ps(m, PK_REDUCE, st);
-      k_mf_reduce<Real, DP, MEAN_CPW><<<grid, MEAN_THREADS, MZ::RED, st>>>(p, a); }
+      launch_pdl(k_mf_reduce<Real, DP, MEAN_CPW>, grid, MEAN_THREADS, MZ::RED, st, p, a); }
     a.x = nullptr;
     { ProfScope ps(m, PK_SCAN, st);
-      k_mean_cross<Real, DP><<<m->C, 32, MZ::CROSS, st>>>(
+      launch_pdl(k_mean_cross<Real, DP>, m->C, 32, MZ::CROSS, st,
           p, (const Real*)m->btab + (long)BAH * m->nb * DD, a.z, (Real*)m->ms, 0); }
     a.mstart = (const Real*)m->ms;
     { ProfScope ps(m, PK_APPLY, st);
-      k_mf_apply<Real, DP, MEAN_CPW><<<grid, MEAN_THREADS, MZ::APP, st>>>(p, a); }
+      launch_pdl(k_mf_apply<Real, DP, MEAN_CPW>, grid, MEAN_THREADS, MZ::APP, st, p, a); }
   }
 
   static BackArgs<Real> back_args_tab(aux_model* m) {
@@ -294,9 +317,10 @@ struct Ops {
   static void backward_tab(aux_model* m, const KP<Real>& p, BackArgs<Real> b, cudaStream_t st) {
     ProfScope ps(m, PK_BACKWARD, st, 2);
     Real* xnext = (Real*)m->zb;
-    k_mean_cross<Real, DP><<<m->C, 32, MZ::CROSS, st>>>(
+    launch_pdl(k_mean_cross<Real, DP>, m->C, 32, MZ::CROSS, st,
         p, b.gum, b.guv, xnext, 1);
-    k_mb_apply<Real, DP, MEAN_CPW><<<mean_grid(m), MEAN_THREADS, MZ::BWD, st>>>(p, b, xnext);
+    launch_pdl(k_mb_apply<Real, DP, MEAN_CPW>, mean_grid(m), MEAN_THREADS, MZ::BWD, st, p, b,
+               (const Real*)xnext);
   }
 
   // ---- divide-and-conquer (bridging) sampler (aux_bridge.cuh)
