@@ -397,24 +397,6 @@ __device__ void cov_combine_mw(const KP<Real>& p, const Real* __restrict__ left,
   if (bad && lane == 0 && warp == 0) atomicOr(status, ST_NOT_PD);
 }
 
-template <typename Real, int DP>
-__global__ void __launch_bounds__(32 * CW_SCAN)
-    k_cov_scan_level_mw(KP<Real> p, const Real* __restrict__ in_m, Real* __restrict__ out_m, int off,
-                        int32_t* __restrict__ status) {
-  constexpr long DD = (long)DP * DP;
-  const int k = blockIdx.x;
-  if (k < off) {
-    using V = typename Vec16<Real>::V;
-    constexpr int NV = 3 * (int)DD / Vec16<Real>::N;
-    const V* src = reinterpret_cast<const V*>(in_m + (long)k * 3 * DD);
-    V* dst = reinterpret_cast<V*>(out_m + (long)k * 3 * DD);
-    for (int q = threadIdx.x; q < NV; q += blockDim.x) dst[q] = src[q];
-    return;
-  }
-  cov_combine_mw<Real, DP>(p, in_m + (long)(k - off) * 3 * DD, in_m + (long)k * 3 * DD,
-                           out_m + (long)k * 3 * DD, status);
-}
-
 // ---------------------------------------------------------------------------
 // Prefix scan of the covariance blocks by doubling. With homogeneous dynamics
 // and R = r I every element with t >= 1 is the same, so every covariance

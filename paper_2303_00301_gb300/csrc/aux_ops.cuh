@@ -100,8 +100,6 @@ struct Ops {
     e = cudaFuncSetAttribute(k_cov_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::APP_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
     if constexpr (DP >= 16) {
-      e = cudaFuncSetAttribute(k_cov_scan_level_mw<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovScanMW<Real, DP>::SMEM);
-      if (e != cudaSuccess) return AUX_E_CUDA;
       e = cudaFuncSetAttribute(k_cov_scan_double_mw<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovScanMW<Real, DP>::SMEM);
       if (e != cudaSuccess) return AUX_E_CUDA;
     }
