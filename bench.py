@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--sampler", default="scan", choices=["scan", "bridging"],
                     help="pathwise sampler of the headline mode (aux_set_sampler)")
     ap.add_argument("--filter-form", default="covariance", choices=["covariance", "square_root"],
-                    help="filter form of the headline mode (aux_set_filter_form; per_chain only)")
+                    help="filter form of the headline mode (aux_set_filter_form)")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the measurements of the other execution modes")
     ap.add_argument("--ess-iters", type=int, default=5000,
@@ -196,6 +196,18 @@ def kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz):
         return ((T - 1) * d ** 3 + nodes * (6 + 1.0 / 3 + 2 + 4 + 1.0 / 3) * d ** 3) / (levels + 1), None
     Lc = (T + nbc - 1) // nbc
     ragged = nbc >= 3 and T % Lc != 0
+    if mode == "table_sqrt" and kind in ("cov_reduce", "cov_scan", "cov_apply"):
+        # the covariance pass on factors: one square-root operator (29.3 d^3, as above)
+        # per element folded and per prefix; the in-block step 17.3 d^3, its epilogue
+        # 17.7 d^3, P^f = U U^T (d^3), M_t = K' F and the two running products (6 d^3)
+        n_end = nbc - 1 if ragged else nbc
+        levels = max(0, math.ceil(math.log2(n_end))) if n_end > 1 else 0
+        if kind == "cov_reduce":
+            return min(nbc, 3 if ragged else 2) * Lc * 29.3 * d ** 3, None
+        if kind == "cov_scan":
+            combines = (n_end - 1) + max(0, levels - 1) + (1 if ragged else 0)
+            return combines * 29.3 * d ** 3 / max(1, levels + (1 if ragged else 0)), None
+        return T * (17.3 + 17.7 + 1 + 6) * d ** 3, None
     if kind == "cov_reduce":
         # the distinct block aggregates only: the first block, a generic one, a short last one
         return min(nbc, 3 if ragged else 2) * Lc * reduce_flops_per_step(d, fdiag), None
@@ -225,6 +237,10 @@ KERNEL_NAMES = {
               "cov_apply": "k_cov_apply", "cov_products": "k_cov_products",
               "bridge": "k_b_sample + k_b_mh", "bridge_tree": "k_br_leaf + k_br_node"},
 }
+
+
+KERNEL_NAMES["table_sqrt"] = dict(KERNEL_NAMES["table"], cov_reduce="k_srcov_reduce",
+                                  cov_scan="k_srcov_scan_double", cov_apply="k_srcov_apply")
 
 
 def source_hash():
@@ -261,7 +277,7 @@ def roofline_line(mode, kind, prof, w, d, T, C, nb, nbc, fdiag, esz, peaks, step
     avg_ms = ms / launches
     flops, bytes_ = kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    name = KERNEL_NAMES[mode if mode in ("per_chain", "per_chain_sqrt") else "table"].get(kind, kind)
+    name = KERNEL_NAMES[mode if mode in ("per_chain", "per_chain_sqrt", "table_sqrt") else "table"].get(kind, kind)
     line = {"path": path, "kernel": name, "launches": launches, "avg_launch_ms": avg_ms}
     if bytes_ is not None and "hbm_gbs" in peaks:
         achieved = bytes_ / (avg_ms / 1e3) / 1e9
@@ -707,6 +723,12 @@ def run_ours(args):
         so.close()
         others["per_chain_square_root"] = r
         profs["per_chain_square_root"] = po
+        # the square-root form of the table modes' covariance pass
+        if not (args.mode == "shared" and args.filter_form == "square_root"):
+            so, _, _, _, po, _, r = run_mode("shared", False, filter_form="square_root")
+            so.close()
+            others["shared_square_root"] = r
+            profs["shared_square_root"] = po
 
     spatial = None
     batched = None
@@ -752,10 +774,13 @@ def run_ours(args):
         return (T + Lm - 1) // Lm, (T + Lc - 1) // Lc
     dom = max((k for k in prof if prof[k][1]), key=lambda k: prof[k][0])
     def rl(mode, kind, path, key=None):
-        nbm, nbcm = shape_for("per_chain" if mode.startswith("per_chain") else mode)
+        nbm, nbcm = shape_for("per_chain" if mode.startswith("per_chain") else
+                              ("shared" if mode == "table_sqrt" else mode))
         return roofline_line(mode, kind, profs[key or mode], w, d, T, C, nbm, nbcm, fdiag, esz, peaks,
                              args.steps, path)
-    head_work = "per_chain_sqrt" if args.filter_form == "square_root" else args.mode
+    head_work = args.mode
+    if args.filter_form == "square_root":
+        head_work = "per_chain_sqrt" if args.mode == "per_chain" else "table_sqrt"
     roofline = rl(head_work, dom, f"dominant kernel of the {args.mode} mode", args.mode)
     lines = {}
     if "per_chain" in profs and not (args.mode == "per_chain" and args.filter_form == "square_root"):
@@ -773,6 +798,13 @@ def run_ours(args):
         kq = max((k for k in ("reduce", "apply") if pq.get(k, (0, 0))[1]), key=lambda k: pq[k][0])
         lines["square_root_path"] = rl("per_chain_sqrt", kq, "square-root form of the per-chain filter "
                                        "(dominant kernel)", "per_chain_square_root")
+    if "shared_square_root" in profs:
+        pq = profs["shared_square_root"]
+        kq = [k for k in ("cov_reduce", "cov_scan", "cov_apply") if pq.get(k, (0, 0))[1]]
+        if kq:
+            kq = max(kq, key=lambda k: pq[k][0])
+            lines["square_root_covariance_pass"] = rl("table_sqrt", kq, "square-root form of the covariance "
+                                                      "pass (dominant kernel)", "shared_square_root")
     if "cached_bridging" in profs:
         lines["bridging_sampler"] = rl("cached", "bridge", "divide-and-conquer sampler: offsets up, "
                                        "split points down, MH terms (tables shared)", "cached_bridging")

@@ -229,10 +229,16 @@ int aux_set_proposal(aux_model *m, int32_t order);
  * more. With it the in-block filter also forms the backward elements of the
  * (G, U) scan, chol(Sigma_t) by triangularisation in Joseph form, so that
  * aux_kalman_step and aux_sample_path run on the square-root filter too.
- * Scope: AUX_MODE_PER_CHAIN, first-order proposal, AUX_SAMPLER_SCAN; other
- * combinations return AUX_E_UNSUPPORTED from the calls that need them (every
- * call in a table mode). Not available for the factorised-prior model
- * (UNSUPPORTED). Errors: INVALID_ARG, UNSUPPORTED. */
+ * In the table modes (AUX_MODE_SHARED_COV, AUX_MODE_CACHED_COV) the form
+ * applies to the covariance pass: the shared block aggregates, their prefixes
+ * and the in-block Riccati steps that write the per-step tables run on
+ * factors, so that the tables (gains, filtering covariances, backward gains
+ * and chol(Sigma_t)) are accurate in single precision; the per-chain means
+ * passes are linear in the means and unchanged. Scope: in AUX_MODE_PER_CHAIN,
+ * first-order proposal and AUX_SAMPLER_SCAN (other combinations return
+ * AUX_E_UNSUPPORTED from the calls that need them); in a table mode, every
+ * sampler. Not available for the factorised-prior model (UNSUPPORTED).
+ * Errors: INVALID_ARG, UNSUPPORTED. */
 int aux_set_filter_form(aux_model *m, int32_t form);
 
 /* Pathwise samplers (aux_set_sampler) */

@@ -504,7 +504,12 @@ int aux_set_mode(aux_model* m, int32_t mode) {
 int aux_set_filter_form(aux_model* m, int32_t form) {
   if (!m || (form != AUX_FILTER_COVARIANCE && form != AUX_FILTER_SQUARE_ROOT)) return AUX_E_INVALID_ARG;
   if (m->fact) return form == AUX_FILTER_COVARIANCE ? AUX_OK : AUX_E_UNSUPPORTED;
-  m->sqrt_form = form == AUX_FILTER_SQUARE_ROOT ? 1 : 0;
+  const int f = form == AUX_FILTER_SQUARE_ROOT ? 1 : 0;
+  if (f != m->sqrt_form) {   // the cached tables were made by the other form
+    m->cov_valid = 0;
+    m->br_valid = 0;
+  }
+  m->sqrt_form = f;
   return AUX_OK;
 }
 

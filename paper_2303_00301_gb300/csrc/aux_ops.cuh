@@ -120,6 +120,12 @@ struct Ops {
     e = cudaFuncSetAttribute(k_sr_scan_level<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SrSizes<Real, DP>::RED_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_sr_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SrSizes<Real, DP>::APP_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_srcov_reduce<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SrSizes<Real, DP>::RED_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_srcov_scan_double<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SrSizes<Real, DP>::RED_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_srcov_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SrSizes<Real, DP>::COVAPP_SMEM);
     return cuda_ok(e);
   }
 
@@ -209,7 +215,36 @@ struct Ops {
     Real* b0 = (Real*)m->cagg0;
     Real* b1 = (Real*)m->cagg1;
     const int nbc = m->nbc;
-    if constexpr (DP >= 16) {
+    if (m->sqrt_form) {
+      // square-root form (aux_sqrt.cuh): the same distinct aggregates and doubling
+      // on (A, U, Z) factors, for every padded width
+      using SZ = SrSizes<Real, DP>;
+      const bool rag = nbc >= 3 && (m->T % m->Lc) != 0;
+      Real* Q0 = b1;
+      Real* Q1 = b1 + 3 * DD;
+      Real* tail = b1 + 6 * DD;
+      {
+        ProfScope ps(m, PK_COV_REDUCE, st);
+        cudaMemsetAsync(m->cov_status, 0, sizeof(int32_t), st);
+        k_srcov_reduce<Real, DP><<<nbc == 1 ? 1 : (rag ? 3 : 2), 32, SZ::RED_SMEM, st>>>(
+            pc, b0, m->cov_status, (const int*)m->cov_kmap, Q0, tail);
+      }
+      const int n_end = rag ? nbc - 1 : nbc;
+      Real *gk = Q0, *gk2 = Q1;
+      for (int pow2 = 1; pow2 < n_end; pow2 *= 2) {
+        ProfScope ps(m, PK_COV_SCAN, st);
+        const int cnt = std::min(pow2, n_end - pow2);
+        const int next = 2 * pow2 < n_end ? 1 : 0;
+        k_srcov_scan_double<Real, DP><<<cnt + next, 32, SZ::RED_SMEM, st>>>(pc, b0, (const Real*)gk, gk2, 0, pow2,
+                                                                            cnt, m->cov_status);
+        Real* tmp = gk; gk = gk2; gk2 = tmp;
+      }
+      if (rag) {
+        ProfScope ps(m, PK_COV_SCAN, st);
+        k_srcov_scan_double<Real, DP><<<1, 32, SZ::RED_SMEM, st>>>(pc, b0, (const Real*)tail, (Real*)nullptr,
+                                                                  nbc - 2, nbc - 1, 1, m->cov_status);
+      }
+    } else if constexpr (DP >= 16) {
       // distinct block aggregates only (block 0, a generic block, a short last
       // block), then the prefixes by doubling (k_cov_scan_double_mw)
       const bool rag = nbc >= 3 && (m->T % m->Lc) != 0;
@@ -258,7 +293,10 @@ struct Ops {
     a.R = m->L / m->Lc;
     {
       ProfScope ps(m, PK_COV_APPLY, st);
-      launch_pdl(k_cov_apply<Real, DP>, m->nbc, 96, CZ::APP_SMEM, st, pc, a);
+      if (m->sqrt_form)
+        k_srcov_apply<Real, DP><<<m->nbc, 32, SrSizes<Real, DP>::COVAPP_SMEM, st>>>(pc, a);
+      else
+        launch_pdl(k_cov_apply<Real, DP>, m->nbc, 96, CZ::APP_SMEM, st, pc, a);
     }
     {
       ProfScope ps(m, PK_COV_PRODUCTS, st, 2);
@@ -458,7 +496,7 @@ struct Ops {
 
   static int kalman_step(aux_model* m, void* xv, int n_iters, uint64_t iter0, uint32_t* acc,
                          double* log_alpha, cudaStream_t st) {
-    if (m->sqrt_form && (m->mode != AUX_MODE_PER_CHAIN || m->order != 1 || m->sampler != AUX_SAMPLER_SCAN))
+    if (m->sqrt_form && m->mode == AUX_MODE_PER_CHAIN && (m->order != 1 || m->sampler != AUX_SAMPLER_SCAN))
       return AUX_E_UNSUPPORTED;
     if (m->mode != AUX_MODE_PER_CHAIN) {
       // the tables assume R = (delta/2) I; the second-order variances depend on the chain's state
@@ -506,7 +544,6 @@ struct Ops {
 
   static int loglik(aux_model* m, const void* yt, double* logZ, void* mf, void* Pf, cudaStream_t st) {
     const KP<Real> p = make_kp<Real>(m);
-    if (m->sqrt_form && m->mode != AUX_MODE_PER_CHAIN) return AUX_E_UNSUPPORTED;
     if (m->mode != AUX_MODE_PER_CHAIN) {
       ensure_cov(m, p, st);
       MeanArgs<Real> a = mean_args(m);
@@ -527,7 +564,7 @@ struct Ops {
 
   static int sample_path(aux_model* m, const void* yt, const void* eps, uint64_t iter, void* xs,
                          double* logZ, cudaStream_t st) {
-    if (m->sqrt_form && (m->mode != AUX_MODE_PER_CHAIN || m->sampler != AUX_SAMPLER_SCAN))
+    if (m->sqrt_form && m->mode == AUX_MODE_PER_CHAIN && m->sampler != AUX_SAMPLER_SCAN)
       return AUX_E_UNSUPPORTED;
     const KP<Real> p = make_kp<Real>(m);
     if (m->mode != AUX_MODE_PER_CHAIN) {

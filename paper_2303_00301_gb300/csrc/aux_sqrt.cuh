@@ -36,7 +36,7 @@
 //                    (G, U) scan, chol(Sigma_t) from tria in Joseph form.
 // The aggregates use the covariance form's layout [A, U, Z, b, eta] (same size).
 #pragma once
-#include "aux_kernels.cuh"
+#include "aux_cov.cuh"
 
 namespace auxk {
 
@@ -48,6 +48,8 @@ template <typename Real, int DP> struct SrSizes {
   // state (A, U, Z), 7 scratch slots; vectors: 2 inverse diagonals, 3 temporaries,
   // b, eta of the state and of the element, signs, tria row
   static constexpr size_t RED_SMEM = (17 * MAT + 10 * VEC + VROW) * sizeof(Real);
+  // covariance apply of the table modes: 15 slots, 3 vectors
+  static constexpr size_t COVAPP_SMEM = (15 * MAT + 2 * VEC + VROW) * sizeof(Real);
   // apply: F, chol Q, U^f, U^p, K, K', Ls (LS + LR), P^p, 3 scratch, G, G product;
   // vectors: inverse diagonal, m^f, m^p, innovation / noise, z, U_t, signs, tria row
   static constexpr size_t APP_SMEM = (14 * MAT + 7 * VEC + VROW) * sizeof(Real);
@@ -366,9 +368,10 @@ __device__ __forceinline__ void sr_condition(const KP<Real>& p, const Real* SP, 
 // ---------------------------------------------------------------------------
 // Phase 1: the block's elements folded with the square-root operator.
 // ---------------------------------------------------------------------------
-template <typename Real, int DP>
-__global__ void __launch_bounds__(32, 1) k_sr_reduce(KP<Real> p, const Real* __restrict__ yt,
-                                                     Real* __restrict__ agg) {
+template <typename Real, int DP, bool COV>
+__device__ __forceinline__ void sr_reduce_body(KP<Real> p, const Real* __restrict__ yt, Real* __restrict__ agg,
+                                               const int* __restrict__ kmap, Real* __restrict__ dst1,
+                                               Real* __restrict__ dst2, int32_t* __restrict__ cstatus) {
   refresh_delta(p);
   using Z = SrSizes<Real, DP>;
   constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
@@ -395,11 +398,14 @@ __global__ void __launch_bounds__(32, 1) k_sr_reduce(KP<Real> p, const Real* __r
   Real* vee = vbe + VEC;
   w.vrow = vee + VEC;
   const int lane = threadIdx.x;
-  const int c = blockIdx.x / p.nb, k = blockIdx.x % p.nb;
+  // COV: matrix parts only (the covariance pass of the table modes), CTA b reduces
+  // covariance block kmap[b] (or b) of the shared model; else block k of chain c
+  const int c = COV ? 0 : blockIdx.x / p.nb;
+  const int k = COV ? (kmap ? kmap[blockIdx.x] : blockIdx.x) : blockIdx.x % p.nb;
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
-  const Real* ytc = yt + (long)c * p.nT * p.d;
+  const Real* ytc = COV ? nullptr : yt + (long)c * p.nT * p.d;
   int bad = 0;
   Real r[DP], x[2 * DP];
   // model: F, chol Q (zero padded)
@@ -439,6 +445,11 @@ __global__ void __launch_bounds__(32, 1) k_sr_reduce(KP<Real> p, const Real* __r
   // the block's first element
   const Real bdyn = p.b[row];
   auto elem_vecs = [&](int t, Real* vbo, Real* veo) {   // b and eta of element t >= 1
+    if (COV) {
+      if (act) { vbo[lane] = (Real)0; veo[lane] = (Real)0; }
+      __syncwarp();
+      return;
+    }
     const Real yi = lane < p.d ? ytc[(long)t * p.d + lane] : (Real)0;
     __syncwarp();
     if (act) w.v1[lane] = lane < p.d ? yi - bdyn : (Real)0;
@@ -469,9 +480,9 @@ __global__ void __launch_bounds__(32, 1) k_sr_reduce(KP<Real> p, const Real* __r
     st_row<Real, DP>(SA, row, u, act);
     st_row<Real, DP>(SZ, row, u, act);
     const Real m0 = p.m0[row];
-    const Real yi = lane < p.d ? ytc[lane] : (Real)0;
+    const Real yi = (!COV && lane < p.d) ? ytc[lane] : (Real)0;
     __syncwarp();
-    if (act) w.v1[lane] = lane < p.d ? yi - m0 : (Real)0;
+    if (act) w.v1[lane] = (!COV && lane < p.d) ? yi - m0 : (Real)0;
     __syncwarp();
     if (act) { vb[lane] = m0 + dot_row_vec<Real, DP>(w.T3 + row * LD, w.v1); ve[lane] = (Real)0; }
     __syncwarp();
@@ -489,8 +500,97 @@ __global__ void __launch_bounds__(32, 1) k_sr_reduce(KP<Real> p, const Real* __r
     elem_vecs(t, vbe, vee);
     sr_combine<Real, DP>(SA, SU, SZ, vb, ve, SAe, SUe, SZe, vbe, vee, w, p.d, lane, &bad);
   }
-  sr_store<Real, DP>(agg + (long)blockIdx.x * Z::ES, SA, SU, SZ, vb, ve, lane);
-  if (bad && lane == 0) atomicOr(&p.status_iter[c], ST_NOT_PD);
+  if (COV) {   // (A, U, Z): the covariance form's (A, C, J) slots
+    constexpr long DD = (long)DP * DP;
+    Real* g = !kmap || blockIdx.x == 0 ? agg + (long)k * 3 * DD : (blockIdx.x == 1 ? dst1 : dst2);
+    __syncwarp();
+    Real q[DP];
+    ld_row<Real, DP>(SA, row, q);
+    if (act) st_vec<Real, DP>(g + row * DP, q);
+    ld_row<Real, DP>(SU, row, q);
+    if (act) st_vec<Real, DP>(g + DD + row * DP, q);
+    ld_row<Real, DP>(SZ, row, q);
+    if (act) st_vec<Real, DP>(g + 2 * DD + row * DP, q);
+    if (bad && lane == 0) atomicOr(cstatus, ST_NOT_PD);
+  } else {
+    sr_store<Real, DP>(agg + (long)blockIdx.x * Z::ES, SA, SU, SZ, vb, ve, lane);
+    if (bad && lane == 0) atomicOr(&p.status_iter[c], ST_NOT_PD);
+  }
+}
+
+template <typename Real, int DP>
+__global__ void __launch_bounds__(32, 1) k_sr_reduce(KP<Real> p, const Real* __restrict__ yt,
+                                                     Real* __restrict__ agg) {
+  sr_reduce_body<Real, DP, false>(p, yt, agg, nullptr, nullptr, nullptr, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Square-root covariance pass of the table modes (matrix parts only, layout
+// (A, U, Z) in the covariance form's (A, C, J) slots): the distinct block
+// aggregates (kmap), the prefixes by doubling, the in-block step with the
+// per-step tables. Same tables as aux_cov.cuh's pass, from factors.
+// ---------------------------------------------------------------------------
+template <typename Real, int DP>
+__global__ void __launch_bounds__(32, 1) k_srcov_reduce(KP<Real> p, Real* __restrict__ aggm,
+                                                        int32_t* __restrict__ status, const int* __restrict__ kmap,
+                                                        Real* __restrict__ dst1, Real* __restrict__ dst2) {
+  sr_reduce_body<Real, DP, true>(p, nullptr, aggm, kmap, dst1, dst2, status);
+}
+
+// P[dst + i] = P[src + i] (x) Gk for CTA i < cnt; CTA cnt: Gk2 = Gk (x) Gk
+template <typename Real, int DP>
+__global__ void __launch_bounds__(32, 1) k_srcov_scan_double(KP<Real> p, Real* __restrict__ P,
+                                                             const Real* __restrict__ Gk, Real* __restrict__ Gk2,
+                                                             int src, int dst, int cnt, int32_t* __restrict__ status) {
+  using Z = SrSizes<Real, DP>;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC;
+  constexpr long DD = (long)DP * DP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  const int lane = threadIdx.x, i = blockIdx.x;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  Real* SA = sm;
+  Real* SU = SA + MAT;
+  Real* SZ = SU + MAT;
+  Real* SAe = SZ + MAT;
+  Real* SUe = SAe + MAT;
+  Real* SZe = SUe + MAT;
+  SrWork<Real, DP> w;
+  w.T0 = SZe + MAT; w.T1 = w.T0 + MAT; w.T2 = w.T1 + MAT; w.T3 = w.T2 + MAT;
+  w.T4 = w.T3 + MAT; w.T5 = w.T4 + MAT; w.T6 = w.T5 + MAT;
+  w.vx = w.T6 + MAT; w.vx2 = w.vx + VEC; w.v1 = w.vx2 + VEC; w.v2 = w.v1 + VEC; w.v3 = w.v2 + VEC;
+  w.vsg = w.v3 + VEC;
+  Real* vb = w.vsg + VEC;
+  Real* ve = vb + VEC;
+  Real* vbe = ve + VEC;
+  Real* vee = vbe + VEC;
+  w.vrow = vee + VEC;
+  const Real* L = i < cnt ? P + (long)(src + i) * 3 * DD : Gk;
+  Real* out = i < cnt ? P + (long)(dst + i) * 3 * DD : Gk2;
+  auto load3 = [&](const Real* g, Real* A, Real* U, Real* Zs) {
+    Real q[DP];
+    ld_vec<Real, DP>(g + row * DP, q);
+    st_row<Real, DP>(A, row, q, act);
+    ld_vec<Real, DP>(g + DD + row * DP, q);
+    st_row<Real, DP>(U, row, q, act);
+    ld_vec<Real, DP>(g + 2 * DD + row * DP, q);
+    st_row<Real, DP>(Zs, row, q, act);
+  };
+  load3(L, SA, SU, SZ);
+  load3(Gk, SAe, SUe, SZe);
+  if (act) { vb[lane] = ve[lane] = vbe[lane] = vee[lane] = (Real)0; }
+  __syncwarp();
+  int bad = 0;
+  sr_combine<Real, DP>(SA, SU, SZ, vb, ve, SAe, SUe, SZe, vbe, vee, w, p.d, lane, &bad);
+  Real q[DP];
+  ld_row<Real, DP>(SA, row, q);
+  if (act) st_vec<Real, DP>(out + row * DP, q);
+  ld_row<Real, DP>(SU, row, q);
+  if (act) st_vec<Real, DP>(out + DD + row * DP, q);
+  ld_row<Real, DP>(SZ, row, q);
+  if (act) st_vec<Real, DP>(out + 2 * DD + row * DP, q);
+  if (bad && lane == 0) atomicOr(status, ST_NOT_PD);
 }
 
 // ---------------------------------------------------------------------------
@@ -784,6 +884,211 @@ __global__ void __launch_bounds__(32, 1) k_sr_apply(KP<Real> p, ApplyArgs<Real> 
   }
   if ((a.flags & (APPLY_LOGZ | APPLY_REV_DIFF)) && lane == 0) a.lz_part[(long)c * p.nb + k] = lz;
   if (bad && lane == 0) atomicOr(&p.status_iter[c], ST_NOT_PD);
+}
+
+// ---------------------------------------------------------------------------
+// In-block square-root covariance filter of covariance block k (one warp) from
+// the prefix factor U^f_{s-1}, writing the per-step tables of aux_cov.cuh:
+//   TK[t] = K'_t = r S_t^{-1}, ldt[t] = log det S_t, TPF[t] = U^f_t U^f_t^T,
+//   TG[t] = G_t, TLS[t] = chol(Sigma_t) = tria([(I - G_t F) U^f_t, G_t chol Q]),
+//   TGP[t] = G_s ... G_{t-1}; and the block products G_s ... G_e and
+//   M_e ... M_s (M_t = K'_t F) into cblk, as k_cov_apply does.
+// Per step: the prediction U^p_t = tria([F U^f_{t-1}, chol Q]); the epilogue of
+// step t - 1 (it needs P^p_t); the conditioning on y_t (U^f_t by tria in
+// Joseph form); the running products.
+// ---------------------------------------------------------------------------
+template <typename Real, int DP>
+__global__ void __launch_bounds__(32, 1) k_srcov_apply(KP<Real> p, CovArgs<Real> a) {
+  refresh_delta(p);
+  using Z = SrSizes<Real, DP>;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
+  constexpr long DD = (long)DP * DP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  Real* SF = sm;
+  Real* SCQ = SF + MAT;
+  Real* SUf = SCQ + MAT;
+  Real* SUp = SUf + MAT;
+  Real* SK = SUp + MAT;
+  Real* SKp = SK + MAT;
+  Real* SLS = SKp + MAT;
+  Real* SLR = SLS + MAT;
+  Real* SP = SLR + MAT;
+  Real* SY = SP + MAT;
+  Real* SW = SY + MAT;
+  Real* SB = SW + MAT;
+  Real* SG = SB + MAT;
+  Real* SGh = SG + MAT;
+  Real* SAH = SGh + MAT;
+  Real* vx = SAH + MAT;
+  Real* vsg = vx + VEC;
+  Real* vrow = vsg + VEC;
+  const int lane = threadIdx.x, k = blockIdx.x;
+  const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  int bad = 0;
+  Real r[DP], x[2 * DP];
+  ld_vec<Real, DP>(p.F + row * DP, r);
+  st_row<Real, DP>(SF, row, r, act);
+  ld_vec<Real, DP>(p.Q + row * DP, r);
+  chol_rot<Real, DP>(r, SLS, SCQ, nullptr, vx, nullptr, p.d, lane, &bad);
+  __syncwarp();
+  ld_row<Real, DP>(SCQ, row, r);
+  zero_pad_row<Real, DP>(r, p.d, lane);
+  __syncwarp();
+  st_row<Real, DP>(SCQ, row, r, act);
+#pragma unroll
+  for (int j = 0; j < DP; ++j) r[j] = (j == lane) ? (Real)1 : (Real)0;
+  st_row<Real, DP>(SGh, row, r, act);
+  st_row<Real, DP>(SAH, row, r, act);
+  __syncwarp();
+  auto store_row = [&](int tb, int t, const Real* S) {
+    Real q[DP];
+    ld_row<Real, DP>(S, row, q);
+    if (act) st_vec<Real, DP>(a.tab + ((long)tb * p.nT + t) * DD + row * DP, q);
+  };
+  auto form_pp = [&]() {   // SP <- U^p U^p^T
+    Real u[DP], pr[DP];
+    ld_row<Real, DP>(SUp, row, u);
+    row_matT<Real, DP>(u, SUp, pr);
+    __syncwarp();
+    st_row<Real, DP>(SP, row, pr, act);
+    __syncwarp();
+  };
+  auto predict = [&]() {   // U^p = tria([F U^f, chol Q]), P^p
+    Real fu[DP], cq[DP];
+    mm_row<Real, DP>(SF + row * LD, SUf, fu);
+    ld_row<Real, DP>(SCQ, row, cq);
+    tria_row<Real, DP>(fu, cq, x);
+    tria_reg<Real, DP>(x, vrow, vsg, lane);
+    Real up[DP];
+#pragma unroll
+    for (int cc = 0; cc < DP; ++cc) up[cc] = x[cc];
+    st_row<Real, DP>(SUp, row, up, act);
+    __syncwarp();
+    form_pp();
+  };
+  // with U^f_t in SUf and P^p_{t+1} in SP: G_t -> TG, chol(Sigma_t) -> TLS, SGh <- SGh G_t
+  auto epilogue = [&](int t) {
+    {
+      Real pp[DP];
+      ld_row<Real, DP>(SP, row, pp);
+      chol_rot<Real, DP>(pp, SLS, nullptr, SLR, vx, nullptr, p.d, lane, &bad);
+    }
+    {
+      Real pf[DP], fp[DP], uf[DP];
+      ld_row<Real, DP>(SUf, row, uf);
+      row_matT<Real, DP>(uf, SUf, pf);
+      __syncwarp();
+      st_row<Real, DP>(SW, row, pf, act);
+      __syncwarp();
+      mm_row<Real, DP>(SF + row * LD, SW, fp);
+      st_row<Real, DP>(SB, row, fp, act);
+      __syncwarp();
+    }
+    solve_cols<Real, DP>(SLS, SLR, vx, SB, SY, SG, lane);   // G = P^f F^T (P^p)^{-1}
+    {
+      Real gf[DP];
+      mm_row<Real, DP>(SG + row * LD, SF, gf);
+      __syncwarp();
+      st_row<Real, DP>(SW, row, gf, act);
+      __syncwarp();
+    }
+    {
+      Real a1[DP], a2[DP];
+      ld_row<Real, DP>(SUf, row, a1);
+      mm_row<Real, DP, true, true>(SW + row * LD, SUf, a1);
+      mm_row<Real, DP>(SG + row * LD, SCQ, a2);
+      tria_row<Real, DP>(a1, a2, x);
+    }
+    tria_reg<Real, DP>(x, vrow, vsg, lane);
+    {
+      Real ls[DP];
+#pragma unroll
+      for (int cc = 0; cc < DP; ++cc) ls[cc] = x[cc];
+      if (act) st_vec<Real, DP>(a.tab + ((long)TLS * p.nT + t) * DD + row * DP, ls);
+    }
+    store_row(TG, t, SG);
+    Real gn[DP];
+    mm_row<Real, DP>(SGh + row * LD, SG, gn);
+    __syncwarp();
+    st_row<Real, DP>(SGh, row, gn, act);
+    __syncwarp();
+  };
+  // ---- block start: U^p_s
+  if (k > 0) {
+    ld_vec<Real, DP>(a.prefix + (long)(k - 1) * 3 * DD + DD + row * DP, r);
+    st_row<Real, DP>(SUf, row, r, act);
+    __syncwarp();
+    predict();
+  } else {
+    ld_vec<Real, DP>(p.P0 + row * DP, r);
+    chol_rot<Real, DP>(r, SLS, SUp, nullptr, vx, nullptr, p.d, lane, &bad);
+    __syncwarp();
+    ld_row<Real, DP>(SUp, row, r);
+    zero_pad_row<Real, DP>(r, p.d, lane);
+    __syncwarp();
+    st_row<Real, DP>(SUp, row, r, act);
+    __syncwarp();
+    form_pp();
+  }
+  for (int t = s; t <= e; ++t) {
+    if (t > s) {
+      predict();          // U^p_t, P^p_t from U^f_{t-1}
+      epilogue(t - 1);    // G_{t-1}, chol(Sigma_{t-1})
+    }
+    store_row(TGP, t, SGh);
+    // conditioning on y_t
+    sr_condition<Real, DP>(p, SP, SUp, SLS, SLR, vx, SK, SKp, SY, vrow, vsg, x, lane, &bad);
+    double lg = (lane < p.d) ? -log((double)vx[lane]) : 0.0;
+    lg = warp_sum<double>(lg);
+    if (lane == 0) a.ldt[t] = 2.0 * lg;
+    store_row(TK, t, SKp);
+    {
+      Real uf[DP], pf[DP];
+#pragma unroll
+      for (int cc = 0; cc < DP; ++cc) uf[cc] = x[cc];
+      __syncwarp();
+      st_row<Real, DP>(SUf, row, uf, act);
+      __syncwarp();
+      row_matT<Real, DP>(uf, SUf, pf);
+      if (act) st_vec<Real, DP>(a.tab + ((long)TPF * p.nT + t) * DD + row * DP, pf);
+    }
+    // M_t = K'_t F, SAH <- M_t SAH
+    {
+      Real mr[DP], ah[DP];
+      mm_row<Real, DP>(SKp + row * LD, SF, mr);
+      __syncwarp();
+      st_row<Real, DP>(SW, row, mr, act);
+      __syncwarp();
+      mm_row<Real, DP>(SW + row * LD, SAH, ah);
+      __syncwarp();
+      st_row<Real, DP>(SAH, row, ah, act);
+      __syncwarp();
+    }
+  }
+  // ---- block end
+  if (e < p.nT - 1) {
+    predict();
+    epilogue(e);
+  } else {
+    Real z0[DP];
+    zero<Real, DP>(z0);
+    if (act) st_vec<Real, DP>(a.tab + ((long)TG * p.nT + e) * DD + row * DP, z0);
+    store_row(TLS, e, SUf);
+    __syncwarp();
+    st_row<Real, DP>(SGh, row, z0, act);
+    __syncwarp();
+  }
+  {
+    Real q[DP];
+    ld_row<Real, DP>(SGh, row, q);
+    if (act) st_vec<Real, DP>(a.cblk + (long)k * DD + row * DP, q);
+    ld_row<Real, DP>(SAH, row, q);
+    if (act) st_vec<Real, DP>(a.cblk + ((long)p.nb + k) * DD + row * DP, q);
+  }
+  if (bad && lane == 0) atomicOr(a.status, ST_NOT_PD);
 }
 
 }  // namespace auxk

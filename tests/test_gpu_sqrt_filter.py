@@ -1,6 +1,6 @@
-"""Square-root form of the per-chain parallel filter (aux_set_filter_form) against
-the FP64 oracle (oracle/sqrt_filter.py, pinned to the covariance form and the
-Kalman filter in test_oracle_sqrt_filter.py).
+"""Square-root form (aux_set_filter_form) of the per-chain parallel filter and of
+the table modes' covariance pass against the FP64 oracle (oracle/sqrt_filter.py,
+pinned to the covariance form and the Kalman filter in test_oracle_sqrt_filter.py).
 
 Tolerances: FP64 1e-9 relative on m^f, P^f and log Z; FP32 1e-4 on m^f and P^f,
 1e-5 on log Z (normwise per chain), as for the covariance form.
@@ -40,10 +40,10 @@ def _workload(d, T, C, seed, delta=0.5, Q=None):
                               x_init=np.zeros((C, T, d)), Ry=np.eye(d))
 
 
-def _run(wl, dt, L, yt, form):
+def _run(wl, dt, L, yt, form, mode="per_chain"):
     C, T, d = wl.n_chains, wl.T, wl.d
     tdt = torch.float64 if dt == "f64" else torch.float32
-    s = AuxKalman(wl, dtype=dt, block_len=L, filter_form=form)
+    s = AuxKalman(wl, dtype=dt, block_len=L, filter_form=form, mode=mode)
     logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
     mf = torch.zeros((C, T, d), dtype=tdt, device="cuda")
     Pf = torch.zeros((C, T, d, d), dtype=tdt, device="cuda")
@@ -123,16 +123,111 @@ def test_single_precision_stays_accurate_where_the_covariance_form_loses_it():
 def test_scope_is_reported():
     wl = _workload(3, 20, 2, seed=1)
     x = _tt(wl.x_init, torch.float64)
-    for kw in (dict(mode="cached"), dict(sampler="bridging")):
-        s = AuxKalman(wl, dtype="f64", block_len=5, filter_form="square_root", **kw)
-        with pytest.raises(B.AuxError):
-            s.step(x, 1)
-        s.close()
-    s = AuxKalman(wl, dtype="f64", block_len=5, mode="cached", filter_form="square_root")
-    logZ = torch.zeros(2, dtype=torch.float64, device="cuda")
+    s = AuxKalman(wl, dtype="f64", block_len=5, filter_form="square_root", sampler="bridging")
     with pytest.raises(B.AuxError):
-        s.loglik(_tt(np.zeros((2, 20, 3)), torch.float64), logZ)
+        s.step(x, 1)
     s.close()
+
+
+# ---- the table modes: the covariance pass on factors (k_srcov_reduce / _scan_double / _apply)
+TAB_CASES = [
+    # d, T, C, block_len, dtype, mode: one covariance block, several, ragged tail, T = 1
+    (2, 64, 2, 8, "f64", "shared"),
+    (1, 37, 3, 8, "f64", "cached"),
+    (3, 37, 3, 5, "f64", "shared"),
+    (4, 300, 2, 20, "f64", "cached"),
+    (3, 1, 2, 1, "f64", "shared"),
+    (16, 133, 2, 16, "f64", "cached"),
+    (13, 257, 2, 32, "f64", "shared"),
+    (30, 257, 2, 32, "f32", "cached"),
+    (8, 65, 2, 8, "f32", "cached"),
+    (30, 1024, 2, 32, "f32", "shared"),
+]
+
+
+@pytest.mark.parametrize("d,T,C,L,dt,mode", TAB_CASES)
+def test_table_modes_square_root_match_the_oracle(d, T, C, L, dt, mode):
+    wl = _workload(d, T, C, seed=300 + d * T)
+    rng = np.random.default_rng(2 * d + T)
+    yt = rng.standard_normal((C, T, d))
+    logZ, mf, Pf, (rc, st) = _run(wl, dt, L, yt, "square_root", mode=mode)
+    tol = 1e-9 if dt == "f64" else 1e-4
+    tol_z = 1e-9 if dt == "f64" else 1e-5
+    R = 0.5 * wl.delta * np.eye(d)
+    for c in range(C):
+        ref = sqrt_filter.sr_filter(yt[c], wl.m0, wl.P0, wl.F, wl.b, wl.Q, R)
+        assert abs(logZ[c] - ref["logZ"]) <= tol_z * abs(ref["logZ"]), (c, logZ[c], ref["logZ"])
+        assert _rel(mf[c], ref["mf"]) < tol
+        assert _rel(Pf[c], np.einsum("tij,tkj->tik", ref["Uf"], ref["Uf"])) < tol
+    assert rc == 0 and not np.any(st)
+
+
+def test_table_modes_square_root_and_covariance_forms_agree():
+    wl = _workload(12, 200, 3, seed=17)
+    yt = np.random.default_rng(3).standard_normal((3, 200, 12))
+    for mode in ("shared", "cached"):
+        a = _run(wl, "f64", 24, yt, "square_root", mode=mode)
+        b = _run(wl, "f64", 24, yt, "covariance", mode=mode)
+        assert np.allclose(a[0], b[0], rtol=1e-12, atol=1e-9)
+        assert _rel(a[1], b[1]) < 1e-11 and _rel(a[2], b[2]) < 1e-11
+
+
+def test_table_modes_single_precision_where_the_covariance_form_loses_it():
+    """The ill-conditioned case of the per-chain test above (r = 1e-6 against Q ~ 1)
+    through the covariance pass of the cached mode."""
+    d, T, C = 8, 128, 2
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((d, d))
+    Q = A @ A.T / d + np.eye(d)
+    wl = _workload(d, T, C, seed=21, delta=2e-6, Q=Q)
+    yt = rng.standard_normal((C, T, d)) * 2.0
+    R = 0.5 * wl.delta * np.eye(d)
+    err = {}
+    for form in ("square_root", "covariance"):
+        logZ, mf, Pf, (rc, st) = _run(wl, "f32", 16, yt, form, mode="cached")
+        e_pf, e_z = [], []
+        for c in range(C):
+            kf = kalman.kalman_filter(yt[c], wl.m0, wl.P0, wl.F, wl.b, wl.Q, R)
+            e_pf.append(_rel(Pf[c], kf["Pf"]))
+            e_z.append(abs(logZ[c] - kf["logZ"]) / abs(kf["logZ"]))
+        err[form] = (max(e_pf), max(e_z), int(np.any(st)))
+    print("cached mode: P^f rel err, log Z rel err, status:", err)
+    assert err["square_root"][0] < 1e-4 and err["square_root"][1] < 1e-5 and err["square_root"][2] == 0
+    assert 100 * err["square_root"][0] < err["covariance"][0]
+
+
+@pytest.mark.parametrize("sampler", ["scan", "bridging"])
+@pytest.mark.parametrize("d,T,C,L,dt,mode", [(3, 37, 3, 5, "f64", "cached"), (16, 133, 2, 16, "f64", "shared"),
+                                             (8, 65, 2, 8, "f32", "shared")])
+def test_table_modes_sample_path(d, T, C, L, dt, mode, sampler):
+    """Both samplers on the tables of the square-root covariance pass, against the
+    same sampler on the covariance form's tables (the bridging sampler maps eps
+    differently, so each form is compared with its own sampler) and, for the
+    (G, U) scan, against the RTS sampler of the oracle."""
+    wl = _workload(d, T, C, seed=40 + d * T)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    tol = 1e-9 if dt == "f64" else 1e-4
+    rng = np.random.default_rng(d + T)
+    yt = rng.standard_normal((C, T, d))
+    eps = rng.standard_normal((C, T, d))
+    out = {}
+    for form in ("square_root", "covariance"):
+        s = AuxKalman(wl, dtype=dt, block_len=L, filter_form=form, mode=mode, sampler=sampler)
+        xs = torch.zeros((C, T, d), dtype=tdt, device="cuda")
+        logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
+        s.sample_path(_tt(yt, tdt), xs, eps=_tt(eps, tdt), logZ=logZ)
+        torch.cuda.synchronize()
+        out[form] = (xs.double().cpu().numpy(), logZ.cpu().numpy())
+        assert s.status()[0] == 0
+        s.close()
+    assert _rel(out["square_root"][0], out["covariance"][0]) < (1e-10 if dt == "f64" else 1e-3)
+    R = 0.5 * wl.delta * np.eye(d)
+    for c in range(C):
+        kf = kalman.kalman_filter(yt[c], wl.m0, wl.P0, wl.F, wl.b, wl.Q, R)
+        assert abs(out["square_root"][1][c] - kf["logZ"]) <= (1e-9 if dt == "f64" else 1e-5) * abs(kf["logZ"])
+        if sampler == "scan":
+            ref = kalman.rts_sample(kf, wl.F, wl.b, wl.Q, eps[c])
+            assert _rel(out["square_root"][0][c], ref) < tol
 
 
 @pytest.mark.parametrize("d,T,C,L,dt", CASES)
@@ -159,11 +254,11 @@ def test_sample_path_matches_the_rts_sampler(d, T, C, L, dt):
     s.close()
 
 
-def _step_parity(wl, dt, L, n_iters, tol_x, tol_la):
+def _step_parity(wl, dt, L, n_iters, tol_x, tol_la, mode="per_chain"):
     from oracle import mcmc, philox
     C = wl.n_chains
     tdt = torch.float64 if dt == "f64" else torch.float32
-    s = AuxKalman(wl, dtype=dt, block_len=L, filter_form="square_root")
+    s = AuxKalman(wl, dtype=dt, block_len=L, filter_form="square_root", mode=mode)
     x = _tt(wl.x_init, tdt)
     la = torch.zeros(C, dtype=torch.float64, device="cuda")
     em = mcmc.SVEmission(wl.y, wl.mask)
@@ -202,10 +297,24 @@ def test_kalman_step_parity_sv_f32():
     _step_parity(wl, "f32", 8, 3, 1e-4, 2e-3)
 
 
+@pytest.mark.parametrize("mode", ["shared", "cached"])
+def test_kalman_step_parity_table_modes_sv(mode):
+    wl = workloads.stochastic_volatility(d=5, T=40, n_chains=3, delta=0.05)
+    assert _step_parity(wl, "f64", 7, 3, 1e-9, 1e-8, mode=mode) > 0
+    wl = workloads.stochastic_volatility(d=8, T=64, n_chains=3, delta=0.05)
+    _step_parity(wl, "f32", 8, 3, 1e-4, 2e-3, mode=mode)
+
+
 def test_kalman_step_full_size_sampled_step():
-    """d = 30, T = 1024, 32 chains, FP32: one step of every chain against the oracle."""
+    """d = 30, T = 1024, 32 chains, FP32: one step of every chain against the oracle,
+    per chain and on the shared tables."""
+    for mode in ("per_chain", "shared"):
+        _full_size_step(mode)
+
+
+def _full_size_step(mode):
     wl = workloads.stochastic_volatility(d=30, T=1024, n_chains=32)
-    s = AuxKalman(wl, dtype="f32", filter_form="square_root")
+    s = AuxKalman(wl, dtype="f32", filter_form="square_root", mode=mode)
     from oracle import mcmc, philox
     x = _tt(wl.x_init, torch.float32)
     la = torch.zeros(32, dtype=torch.float64, device="cuda")
