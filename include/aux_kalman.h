@@ -59,7 +59,7 @@ extern "C" {
 #define AUX_E_CUDA         4  /* a CUDA runtime call failed */
 #define AUX_E_TIMEOUT      5  /* reserved: a bounded device wait gave up */
 #define AUX_E_OOM          6  /* workspace allocation failed */
-#define AUX_E_UNSUPPORTED  7  /* valid but not built (e.g. d_x > 32) */
+#define AUX_E_UNSUPPORTED  7  /* valid but not built (e.g. d_x > 128) */
 #define AUX_E_TOO_LARGE    8  /* the problem does not fit the fixed scratch of aux_loglik_noalloc */
 
 /* compute types */
@@ -81,8 +81,9 @@ extern "C" {
 typedef struct {
   int32_t abi_version;   /* AUX_ABI_VERSION */
   int32_t dtype;         /* AUX_F32 | AUX_F64 */
-  int32_t d_x;           /* state dimension: 1..32 (AUX_F32), 1..16 (AUX_F64); 1..1024 with
-                            AUX_EMIS_STUDENT_T (factorised prior, see below) */
+  int32_t d_x;           /* state dimension: 1..128 (AUX_F32; 33..128 in the table
+                            modes only, see "Wide state dimensions"), 1..16 (AUX_F64);
+                            1..1024 with AUX_EMIS_STUDENT_T (factorised prior, see below) */
   int32_t T;             /* number of states, T >= 1 */
   int32_t n_chains;      /* C >= 1 */
   int32_t emis_kind;     /* AUX_EMIS_* */
@@ -111,6 +112,20 @@ typedef struct {
  * model changes, or recomputed every iteration while delta adapts).
  * aux_loglik takes mf (not Pf); aux_loglik_grad, aux_set_model_params and the
  * second-order proposal return AUX_E_UNSUPPORTED for such a handle. */
+
+/* Wide state dimensions (33 <= d_x <= 128, AUX_F32; padded to 64 or 128).
+ * These run the table modes only (aux_set_mode with AUX_MODE_SHARED_COV or
+ * AUX_MODE_CACHED_COV before the first step): the covariance pass forms the
+ * filtering covariances of every step by doubling over the steps (the prefix
+ * of step t is the first element composed with t copies of the shared
+ * element, Appendix A.2.1), then the per-step gains, backward gains and
+ * chol(Sigma_t) independently per step, with CTA-wide dense routines; the
+ * per-chain means follow the same recursions as for narrow d. In
+ * AUX_MODE_PER_CHAIN aux_kalman_step, aux_loglik and aux_sample_path return
+ * AUX_E_UNSUPPORTED; so do aux_loglik_grad, the second-order proposal, the
+ * square-root form and the bridging sampler (their setters return it). The
+ * first switch to a table mode also allocates 2 * 152 * 8 DP^2 elements of
+ * scratch for the covariance pass. */
 
 typedef struct aux_model aux_model;   /* opaque handle */
 

@@ -16,8 +16,13 @@ int pick_dp(int d) {
   if (d <= 8) return 8;
   if (d <= 16) return 16;
   if (d <= 32) return 32;
+  if (d <= 64) return 64;    // the wide table-mode kernels (aux_wide.cuh), single precision
+  if (d <= 128) return 128;
   return 0;
 }
+
+// the wide kernels: table modes only, first-order proposal, (G, U) scan sampler
+bool wide(const aux_model* m) { return m->DP > 32; }
 
 bool all_finite(const double* a, size_t n) {
   for (size_t i = 0; i < n; ++i)
@@ -383,7 +388,7 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
     *out = m;
     return AUX_OK;
   }
-  m->ops = desc->dtype == AUX_F32 ? aux_ops_f32(DP) : aux_ops_f64(DP);
+  m->ops = desc->dtype == AUX_F32 ? (DP > 32 ? aux_ops_f32_wide(DP) : aux_ops_f32(DP)) : aux_ops_f64(DP);
   if (!m->ops) { release(m); return AUX_E_UNSUPPORTED; }
 
   int rc = desc->dtype == AUX_F32 ? upload_model<float>(m, desc, Ryinv, true)
@@ -407,11 +412,13 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
   if (!rc) rc = dev_alloc(m, &m->yt, path);
   if (!rc) rc = dev_alloc(m, &m->xs, path);
   if (!rc) rc = dev_alloc(m, &m->yts, path);
-  if (!rc) rc = dev_alloc(m, &m->agg0, nbC * aux_es(DP) * es);
-  if (!rc) rc = dev_alloc(m, &m->agg1, nbC * aux_es(DP) * es);
-  if (!rc) rc = dev_alloc(m, &m->G, (size_t)C * T * DP * DP * es);
+  if (DP <= 32) {   // the per-chain element scan (not offered by the wide kernels)
+    if (!rc) rc = dev_alloc(m, &m->agg0, nbC * aux_es(DP) * es);
+    if (!rc) rc = dev_alloc(m, &m->agg1, nbC * aux_es(DP) * es);
+    if (!rc) rc = dev_alloc(m, &m->G, (size_t)C * T * DP * DP * es);
+    if (!rc) rc = dev_alloc(m, &m->gum, nbC * DP * DP * es);
+  }
   if (!rc) rc = dev_alloc(m, &m->U, (size_t)C * T * DP * es);
-  if (!rc) rc = dev_alloc(m, &m->gum, nbC * DP * DP * es);
   if (!rc) rc = dev_alloc(m, &m->guv, nbC * DP * es);
   if (!rc) rc = dev_alloc(m, (void**)&m->fq, (size_t)C * T * sizeof(double));
   if (!rc) rc = dev_alloc(m, (void**)&m->fld, (size_t)C * T * sizeof(double));
@@ -471,8 +478,13 @@ int aux_set_mode(aux_model* m, int32_t mode) {
       if (m->L % c == 0) { m->Lc = c; break; }
     m->nbc = (m->T + m->Lc - 1) / m->Lc;
     int rc = dev_alloc(m, &m->tab, (size_t)6 * m->T * DD * es);
-    if (!rc) rc = dev_alloc(m, &m->cagg0, (size_t)m->nbc * 3 * DD * es);
-    if (!rc) rc = dev_alloc(m, &m->cagg1, (size_t)m->nbc * 3 * DD * es);
+    if (wide(m)) {   // E^(2^k), double-buffered; per-CTA scratch of the dense routines
+      if (!rc) rc = dev_alloc(m, &m->cagg0, (size_t)6 * DD * es);
+      if (!rc) rc = dev_alloc(m, &m->cagg1, aux_wide_scratch_elems(m->DP) * es);
+    } else {
+      if (!rc) rc = dev_alloc(m, &m->cagg0, (size_t)m->nbc * 3 * DD * es);
+      if (!rc) rc = dev_alloc(m, &m->cagg1, (size_t)m->nbc * 3 * DD * es);
+    }
     if (!rc) rc = dev_alloc(m, (void**)&m->cov_ldt, (size_t)m->T * sizeof(double));
     if (!rc) rc = dev_alloc(m, &m->btab, (size_t)2 * m->nb * DD * es);
     if (!rc) rc = dev_alloc(m, &m->zb, (size_t)m->C * m->nb * m->DP * es);
@@ -503,7 +515,7 @@ int aux_set_mode(aux_model* m, int32_t mode) {
 
 int aux_set_filter_form(aux_model* m, int32_t form) {
   if (!m || (form != AUX_FILTER_COVARIANCE && form != AUX_FILTER_SQUARE_ROOT)) return AUX_E_INVALID_ARG;
-  if (m->fact) return form == AUX_FILTER_COVARIANCE ? AUX_OK : AUX_E_UNSUPPORTED;
+  if (m->fact || wide(m)) return form == AUX_FILTER_COVARIANCE ? AUX_OK : AUX_E_UNSUPPORTED;
   const int f = form == AUX_FILTER_SQUARE_ROOT ? 1 : 0;
   if (f != m->sqrt_form) {   // the cached tables were made by the other form
     m->cov_valid = 0;
@@ -515,7 +527,7 @@ int aux_set_filter_form(aux_model* m, int32_t form) {
 
 int aux_set_sampler(aux_model* m, int32_t sampler) {
   if (!m || (sampler != AUX_SAMPLER_SCAN && sampler != AUX_SAMPLER_BRIDGING)) return AUX_E_INVALID_ARG;
-  if (m->fact) return sampler == AUX_SAMPLER_SCAN ? AUX_OK : AUX_E_UNSUPPORTED;
+  if (m->fact || wide(m)) return sampler == AUX_SAMPLER_SCAN ? AUX_OK : AUX_E_UNSUPPORTED;
   const int old = m->sampler;
   m->sampler = sampler;
   const int rc = br_alloc(m);
@@ -528,7 +540,7 @@ int aux_set_proposal(aux_model* m, int32_t order) {
   if (!m || (order != AUX_PROPOSAL_FIRST_ORDER && order != AUX_PROPOSAL_SECOND_ORDER))
     return AUX_E_INVALID_ARG;
   if (order == AUX_PROPOSAL_SECOND_ORDER) {
-    if (!m->diag_hess || m->fact) return AUX_E_UNSUPPORTED;
+    if (!m->diag_hess || m->fact || wide(m)) return AUX_E_UNSUPPORTED;
     if (!m->rho) {
       const size_t path = (size_t)m->C * m->T * m->d * m->esz;
       int rc = dev_alloc(m, &m->rho, path);
@@ -634,7 +646,7 @@ int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {
 int aux_loglik_grad(aux_model* m, const void* ytilde, double* logZ, double* g_mu, double* g_Phi,
                     double* g_cholSigma, double* g_delta, void* stream) {
   if (!m || !ytilde || !g_mu || !g_Phi || !g_cholSigma || !g_delta) return AUX_E_INVALID_ARG;
-  if (!m->grad_ok || m->fact) return AUX_E_UNSUPPORTED;
+  if (!m->grad_ok || m->fact || wide(m)) return AUX_E_UNSUPPORTED;
   m->stream = (cudaStream_t)stream;
   const size_t es = m->esz, DP = m->DP, nbC = (size_t)m->C * m->nb;
   int rc = AUX_OK;

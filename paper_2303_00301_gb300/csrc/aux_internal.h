@@ -134,6 +134,8 @@ int aux_fact_sample_path(aux_model *m, const void *yt, const void *eps, uint64_t
 
 const AuxOps *aux_ops_f32(int DP);
 const AuxOps *aux_ops_f64(int DP);
+const AuxOps *aux_ops_f32_wide(int DP);   // padded dimensions 64 and 128 (aux_wide.cu)
+size_t aux_wide_scratch_elems(int DP);      // per-CTA scratch of the wide covariance pass
 
 // element counts of the per-block buffers for a padded dimension DP
 inline size_t aux_es(int DP) { return 3u * DP * DP + 2u * DP; }

@@ -1,0 +1,875 @@
+// aux_wide.cuh — the table modes (a covariance pass shared by all chains, then
+// per-chain means) for padded dimensions 64 and 128.
+//
+// The narrow kernels give each row of a DP x DP matrix to one lane of a warp,
+// which holds for DP <= 32 only. Here every dense step is a CTA-level routine
+// of WT threads on matrices in global memory (L2-resident working sets):
+//   w_gemm    C = alpha op(A) op(B) + beta C0, k-chunks staged in shared memory,
+//             (DP/16)^2 outputs per thread;
+//   w_chol    right-looking Cholesky in shared memory (one barrier per column);
+//   w_trinv   the inverse of the triangular factor, right-looking by rows.
+// Covariance pass (homogeneous dynamics, R = r I, Appendix A.2.1 elements):
+//   k_w_elem    the two distinct elements: t = 0, (0, C_0, 0), and every t >= 1,
+//               (A, C, J), with S = Q + R:  A = r S^{-1} F, C = Q - Q S^{-1} Q,
+//               J = F^T S^{-1} F; the prefix of t = 0 is its own C_0;
+//   k_w_double  prefixes by doubling at step granularity: the prefix of t has
+//               A = 0 and J = 0 (the first element has both zero), so
+//               P_t = P_{t - 2^k} (x) E^(2^k) needs the C part only,
+//               C = C_e + A_e B B^T A_e^T with B = U chol(N)^{-T}, U = chol(C_i),
+//               N = I + U^T J_e U (SPD, eigenvalues >= 1); one CTA also squares
+//               E^(2^k) with the full operator for the next level;
+//   k_w_epi     per step, from P^f_{t-1} and P^f_t (embarrassingly parallel):
+//               P^p_t, S_t, K'_t = r S_t^{-1}, log det S_t, and the backward
+//               quantities of step t - 1, G = P^f F^T (P^p)^{-1} and
+//               chol(Sigma), Sigma = P^f - G P^p G^T = P^f - W W^T with
+//               W = (chol(P^p)^{-1} F P^f)^T;
+//   k_w_prod    per means block, M_e ... M_s (M_t = K'_t F), G_s ... G_e and the
+//               sum of log det S_t.
+// Tables read by the means kernels with one row index per thread are stored
+// transposed (G^T, chol(Sigma)^T, the block products), so that a warp reads
+// consecutive entries; K' and P^f are symmetric.
+// Means (one CTA per block and group of chains, thread = (row, chain slot)):
+//   k_wmf_reduce, k_wmean_cross, k_wmf_apply, k_wmb_apply: the recursions of
+//   aux_means.cuh (filtering means, cross-block composition, likelihood
+//   terms, backward elements U_t and the block aggregate of the (G, U) scan,
+//   backward sampling with the MH terms); the block aggregate
+//   sum_t (G_s ... G_{t-1}) U_t is formed by Horner's rule backwards over the
+//   block instead of from a table of prefix products.
+#pragma once
+#include "aux_means.cuh"
+
+namespace auxk {
+
+constexpr int WT = 256;          // threads of every wide kernel
+constexpr int W_SLOTS = 2 * 152; // CTAs with their own scratch (2 per SM)
+constexpr int W_SCR = 8;         // scratch matrices per slot
+constexpr int W_CPT = 4;         // chains per thread in the means kernels
+
+template <typename Real, int DP> struct WSz {
+  static constexpr int LDS = DP + 1;                 // shared row stride (odd: column access is conflict-free)
+  static constexpr int KC = 32;                      // k-chunk of w_gemm
+  static constexpr int R = DP / 16;                  // outputs per thread and dimension in w_gemm
+  static constexpr int NRG = WT / DP;                // row groups of the means kernels
+  static constexpr int CPC = NRG * W_CPT;            // chains per CTA of the means kernels
+  static constexpr long DD = (long)DP * DP;
+  static constexpr size_t FULL = (size_t)DP * LDS;   // one padded matrix
+  // two padded matrices (factor and inverse), or the two k-chunks of w_gemm; scalars
+  static constexpr size_t SMEM = 2 * FULL * sizeof(Real) + (DP + 64) * sizeof(double);
+  // means: three vector slots per chain (smem) and per-chain FP64 sums
+  static constexpr size_t MSMEM = (size_t)3 * CPC * DP * sizeof(Real) + 2 * CPC * sizeof(double);
+};
+
+// ---------------------------------------------------------------------------
+// CTA-level dense routines. Matrices are DP x DP, row-major, in global memory;
+// every routine starts and ends with a CTA barrier, so that its outputs are
+// visible to the whole CTA when it returns.
+// ---------------------------------------------------------------------------
+// C = alpha op(A) op(B) + beta C0 (+ I when addI), op = transpose for TA / TB.
+// bscale: the rows of op(B) scaled by bscale[k] (a diagonal left factor of B).
+// C may alias A, B or C0: every read of A and B precedes every store.
+template <typename Real, int DP>
+__device__ void w_gemm(const Real* A, bool ta, const Real* B, bool tb, Real* C, const Real* C0, Real alpha,
+                       Real beta, Real* sm, const Real* bscale = nullptr, bool addI = false) {
+  using Z = WSz<Real, DP>;
+  constexpr int KC = Z::KC, LDS = Z::LDS, R = Z::R;
+  Real* As = sm;              // As[kk][i] = op(A)[i][k0 + kk]
+  Real* Bs = sm + KC * LDS;   // Bs[kk][j] = op(B)[k0 + kk][j]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  Real acc[R][R];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) acc[i][j] = (Real)0;
+  for (int k0 = 0; k0 < DP; k0 += KC) {
+    __syncthreads();
+    for (int q = tid; q < DP * KC; q += WT) {
+      if (!ta) {
+        const int i = q / KC, kk = q % KC;
+        As[kk * LDS + i] = A[(long)i * DP + k0 + kk];
+      } else {
+        const int kk = q / DP, i = q % DP;
+        As[kk * LDS + i] = A[(long)(k0 + kk) * DP + i];
+      }
+      int kb, j;
+      Real bv;
+      if (!tb) {
+        kb = q / DP; j = q % DP;
+        bv = B[(long)(k0 + kb) * DP + j];
+      } else {
+        j = q / KC; kb = q % KC;
+        bv = B[(long)j * DP + k0 + kb];
+      }
+      if (bscale) bv *= bscale[k0 + kb];
+      Bs[kb * LDS + j] = bv;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      Real a[R], b[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) a[i] = As[kk * LDS + ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < R; ++j) b[j] = Bs[kk * LDS + tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+  }
+  __syncthreads();   // every read of A and B is done (C may alias them)
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      Real v = alpha * acc[i][j];
+      if (beta != (Real)0) v = fma(beta, C0[(long)r * DP + c], v);
+      if (addI && r == c) v += (Real)1;
+      C[(long)r * DP + c] = v;
+    }
+  __syncthreads();
+}
+
+// out = alpha * X (+ beta * Y) elementwise, optionally transposed X (out must not alias X then)
+template <typename Real, int DP>
+__device__ void w_axpby(const Real* X, bool tx, Real alpha, const Real* Y, Real beta, Real* out) {
+  __syncthreads();
+  for (int q = threadIdx.x; q < DP * DP; q += WT) {
+    const int i = q / DP, j = q % DP;
+    Real v = alpha * (tx ? X[(long)j * DP + i] : X[q]);
+    if (Y) v = fma(beta, Y[q], v);
+    out[q] = v;
+  }
+  __syncthreads();
+}
+
+// symmetric part (X + X^T) / 2 into out (out must not alias X)
+template <typename Real, int DP>
+__device__ void w_sym(const Real* X, Real* out) {
+  __syncthreads();
+  for (int q = threadIdx.x; q < DP * DP; q += WT) {
+    const int i = q / DP, j = q % DP;
+    out[q] = (Real)0.5 * (X[q] + X[(long)j * DP + i]);
+  }
+  __syncthreads();
+}
+
+// Lower Cholesky factor of the symmetric (A + addiag I) into the shared slot S
+// (row-major, stride LDS, zero above the diagonal). Rows and columns >= d are
+// the identity (the padding). A pivot below d that is not positive and finite
+// sets *bad and is replaced by 1. Returns sum_{k<d} log L_kk (valid in every thread).
+// piv: DP doubles of shared scratch.
+template <typename Real, int DP>
+__device__ double w_chol(const Real* A, Real addiag, int d, Real* S, double* piv, int* bad) {
+  using Z = WSz<Real, DP>;
+  constexpr int LDS = Z::LDS, P = WT / DP;
+  __syncthreads();
+  for (int q = threadIdx.x; q < DP * DP; q += WT) {
+    const int i = q / DP, j = q % DP;
+    Real v;
+    if (i >= d || j >= d) v = (i == j) ? (Real)1 : (Real)0;
+    else v = A[q] + (i == j ? addiag : (Real)0);
+    S[i * LDS + j] = v;
+  }
+  const int i = threadIdx.x % DP, part = threadIdx.x / DP;
+  for (int k = 0; k < d; ++k) {
+    __syncthreads();
+    Real pk = S[k * LDS + k];
+    const bool ok = pk > (Real)0 && pk < (Real)INFINITY;
+    if (!ok) pk = (Real)1;
+    if (threadIdx.x == 0) {
+      piv[k] = (double)pk;
+      if (!ok) *bad = 1;
+    }
+    if (i > k) {
+      const Real lik = S[i * LDS + k] / pk;
+      for (int j = k + 1 + part; j <= i; j += P) S[i * LDS + j] = fma(-lik, S[j * LDS + k], S[i * LDS + j]);
+    }
+  }
+  __syncthreads();
+  // scale: L_ik = S_ik / sqrt(p_k) (i > k), L_kk = sqrt(p_k); zero above the diagonal
+  for (int q = threadIdx.x; q < DP * DP; q += WT) {
+    const int r = q / DP, c = q % DP;
+    if (c >= d) { S[r * LDS + c] = (r == c) ? (Real)1 : (Real)0; continue; }
+    const Real sp = (Real)sqrt(piv[c]);
+    Real v = (Real)0;
+    if (r == c) v = sp;
+    else if (r > c) v = S[r * LDS + c] / sp;
+    S[r * LDS + c] = v;
+  }
+  __syncthreads();
+  double ld = 0.0;
+  for (int k = 0; k < d; ++k) ld += 0.5 * log(piv[k]);
+  return ld;
+}
+
+// X = L^{-1} into the shared slot X (lower triangular), L lower triangular in S.
+// Right-looking by rows: X = I; for k: X_k <- X_k / L_kk; X_i <- X_i - L_ik X_k (i > k).
+template <typename Real, int DP>
+__device__ void w_trinv(const Real* S, Real* X) {
+  constexpr int LDS = WSz<Real, DP>::LDS;
+  __syncthreads();
+  for (int q = threadIdx.x; q < DP * DP; q += WT) {
+    const int i = q / DP, j = q % DP;
+    X[i * LDS + j] = (i == j) ? (Real)1 / S[i * LDS + i] : (Real)0;
+  }
+  for (int k = 0; k < DP - 1; ++k) {
+    __syncthreads();
+    // rows i > k, columns c <= k (row k is final: its diagonal was divided at the start)
+    const int nr = DP - 1 - k, nc = k + 1;
+    for (int q = threadIdx.x; q < nr * nc; q += WT) {
+      const int i = k + 1 + q / nc, c = q % nc;
+      const Real f = S[i * LDS + k] / S[i * LDS + i];
+      X[i * LDS + c] = fma(-f, X[k * LDS + c], X[i * LDS + c]);
+    }
+  }
+  __syncthreads();
+}
+
+// shared slot (stride LDS) -> global, optionally transposed
+template <typename Real, int DP>
+__device__ void w_store(const Real* S, Real* g, bool transpose) {
+  constexpr int LDS = WSz<Real, DP>::LDS;
+  __syncthreads();
+  for (int q = threadIdx.x; q < DP * DP; q += WT) {
+    const int i = q / DP, j = q % DP;
+    g[q] = transpose ? S[j * LDS + i] : S[i * LDS + j];
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Covariance pass
+// ---------------------------------------------------------------------------
+template <typename Real> struct WCovArgs {
+  Real* tab;          // [NTAB][T][DP][DP]: TK, TG^T, TLS^T, (unused), TPF
+  Real* btab;         // [2][nb][DP][DP]: (M_e ... M_s)^T, (G_s ... G_e)^T per means block
+  double* ldt;        // [T] log det S_t
+  double* ld;         // [nb] per means block
+  int32_t* status;    // [1] ST_NOT_PD
+  Real* gk;           // [2][3][DP][DP] E^(2^k) (A, C, J), double-buffered
+  Real* scr;          // [W_SLOTS][W_SCR][DP][DP]
+};
+
+template <typename Real, int DP>
+__device__ __forceinline__ Real* w_slot(const WCovArgs<Real>& a, int s, int i) {
+  return a.scr + ((long)s * W_SCR + i) * WSz<Real, DP>::DD;
+}
+
+// the distinct elements: prefix 0 = C_0 into TPF[0]; E = (A, C, J) into gk[0]
+template <typename Real, int DP>
+__global__ void __launch_bounds__(WT) k_w_elem(KP<Real> p, WCovArgs<Real> a) {
+  refresh_delta(p);
+  using Z = WSz<Real, DP>;
+  constexpr long DD = Z::DD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* S0 = reinterpret_cast<Real*>(smem_raw);
+  Real* S1 = S0 + Z::FULL;
+  double* piv = reinterpret_cast<double*>(S1 + Z::FULL);
+  Real* s0 = w_slot<Real, DP>(a, 0, 0);
+  Real* s1 = w_slot<Real, DP>(a, 0, 1);
+  Real* s2 = w_slot<Real, DP>(a, 0, 2);
+  int bad = 0;
+  const long tstride = (long)p.nT * DD;
+  // t = 0: C_0 = P0 - Y^T Y, Y = chol(P0 + R)^{-1} P0
+  w_chol<Real, DP>(p.P0, p.r, p.d, S0, piv, &bad);
+  w_trinv<Real, DP>(S0, S1);
+  w_store<Real, DP>(S1, s0, false);
+  w_gemm<Real, DP>(s0, false, p.P0, false, s1, nullptr, (Real)1, (Real)0, S0);
+  w_gemm<Real, DP>(s1, true, s1, false, a.tab + (long)TPF * tstride, p.P0, (Real)-1, (Real)1, S0);
+  // t >= 1: S = Q + R = L L^T, Y = L^{-1} Q, W = L^{-1} F
+  Real* EA = a.gk;
+  Real* EC = EA + DD;
+  Real* EJ = EC + DD;
+  w_chol<Real, DP>(p.Q, p.r, p.d, S0, piv, &bad);
+  w_trinv<Real, DP>(S0, S1);
+  w_store<Real, DP>(S1, s0, false);
+  w_gemm<Real, DP>(s0, false, p.Q, false, s1, nullptr, (Real)1, (Real)0, S0);
+  w_gemm<Real, DP>(s1, true, s1, false, EC, p.Q, (Real)-1, (Real)1, S0);       // C = Q - Y^T Y
+  w_gemm<Real, DP>(s0, false, p.F, false, s2, nullptr, (Real)1, (Real)0, S0);  // W = L^{-1} F
+  w_gemm<Real, DP>(s2, true, s2, false, EJ, nullptr, (Real)1, (Real)0, S0);    // J = W^T W
+  w_gemm<Real, DP>(s0, true, s2, false, EA, nullptr, p.r, (Real)0, S0);        // A = r L^{-T} W
+  if (bad && threadIdx.x == 0) atomicOr(a.status, ST_NOT_PD);
+}
+
+// C part of (0, C_i, 0) (x) (A_e, C_e, J_e) into out; with full (A_i, J_i also given,
+// Ao / Jo not null) the whole operator. Scratch: slot s.
+template <typename Real, int DP>
+__device__ void w_combine(const KP<Real>& p, const WCovArgs<Real>& a, int s, const Real* Ai, const Real* Ci,
+                          const Real* Ji, const Real* Ae, const Real* Ce, const Real* Je, Real* Ao, Real* Co,
+                          Real* Jo, Real* S0, Real* S1, double* piv, int* bad) {
+  Real* U = w_slot<Real, DP>(a, s, 0);
+  Real* X = w_slot<Real, DP>(a, s, 1);
+  Real* N = w_slot<Real, DP>(a, s, 2);
+  Real* B = w_slot<Real, DP>(a, s, 3);
+  Real* Pm = w_slot<Real, DP>(a, s, 4);
+  w_chol<Real, DP>(Ci, (Real)0, p.d, S0, piv, bad);                    // U = chol(C_i)
+  w_store<Real, DP>(S0, U, false);
+  w_gemm<Real, DP>(Je, false, U, false, X, nullptr, (Real)1, (Real)0, S0);         // J_e U
+  w_gemm<Real, DP>(U, true, X, false, N, nullptr, (Real)1, (Real)0, S0, nullptr, true);   // N = I + U^T J_e U
+  w_chol<Real, DP>(N, (Real)0, p.d, S0, piv, bad);
+  w_trinv<Real, DP>(S0, S1);
+  w_store<Real, DP>(S1, N, false);                                      // chol(N)^{-1}
+  w_gemm<Real, DP>(U, false, N, true, B, nullptr, (Real)1, (Real)0, S0);           // B = U chol(N)^{-T}
+  w_gemm<Real, DP>(Ae, false, B, false, Pm, nullptr, (Real)1, (Real)0, S0);        // P = A_e B
+  if (Ao) {
+    Real* X1 = w_slot<Real, DP>(a, s, 5);
+    Real* Zm = w_slot<Real, DP>(a, s, 6);
+    Real* Jt = w_slot<Real, DP>(a, s, 7);
+    w_gemm<Real, DP>(Je, false, Ai, false, X1, nullptr, (Real)1, (Real)0, S0);     // X1 = J_e A_i
+    w_gemm<Real, DP>(B, true, X1, false, Zm, nullptr, (Real)1, (Real)0, S0);       // Z = B^T X1
+    w_gemm<Real, DP>(Ai, true, X1, false, Jt, Ji, (Real)1, (Real)1, S0);          // J_i + A_i^T X1
+    w_gemm<Real, DP>(Zm, true, Zm, false, Jt, Jt, (Real)-1, (Real)1, S0);         // - Z^T Z
+    w_sym<Real, DP>(Jt, Jo);
+    w_gemm<Real, DP>(Ae, false, Ai, false, Ao, nullptr, (Real)1, (Real)0, S0);     // A_e A_i
+    w_gemm<Real, DP>(Pm, false, Zm, false, Ao, Ao, (Real)-1, (Real)1, S0);        // - P Z
+  }
+  w_gemm<Real, DP>(Pm, false, Pm, true, Co, Ce, (Real)1, (Real)1, S0);            // C = C_e + P P^T
+}
+
+// one doubling level: prefixes TPF[pow2 + i] = TPF[i] (x) E^(pow2), i < cnt; item cnt
+// (when sq): E^(2 pow2) = E^(pow2) (x) E^(pow2) into gk2
+template <typename Real, int DP>
+__global__ void __launch_bounds__(WT) k_w_double(KP<Real> p, WCovArgs<Real> a, int pow2, int cnt, int sq,
+                                                  const Real* __restrict__ gk, Real* __restrict__ gk2) {
+  using Z = WSz<Real, DP>;
+  constexpr long DD = Z::DD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* S0 = reinterpret_cast<Real*>(smem_raw);
+  Real* S1 = S0 + Z::FULL;
+  double* piv = reinterpret_cast<double*>(S1 + Z::FULL);
+  int bad = 0;
+  Real* PF = a.tab + (long)TPF * p.nT * DD;
+  const int n = cnt + (sq ? 1 : 0);
+  // the squaring first: it alone is on the path to the next level
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const int item = sq ? (it == 0 ? cnt : it - 1) : it;
+    if (item == cnt)
+      w_combine<Real, DP>(p, a, blockIdx.x, gk, gk + DD, gk + 2 * DD, gk, gk + DD, gk + 2 * DD, gk2, gk2 + DD,
+                          gk2 + 2 * DD, S0, S1, piv, &bad);
+    else
+      w_combine<Real, DP>(p, a, blockIdx.x, nullptr, PF + (long)item * DD, nullptr, gk, gk + DD, gk + 2 * DD,
+                          nullptr, PF + (long)(pow2 + item) * DD, nullptr, S0, S1, piv, &bad);
+  }
+  if (bad && threadIdx.x == 0) atomicOr(a.status, ST_NOT_PD);
+}
+
+// per step t = 0 .. T (item T: the last step's backward quantities only)
+template <typename Real, int DP>
+__global__ void __launch_bounds__(WT) k_w_epi(KP<Real> p, WCovArgs<Real> a) {
+  refresh_delta(p);
+  using Z = WSz<Real, DP>;
+  constexpr long DD = Z::DD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* S0 = reinterpret_cast<Real*>(smem_raw);
+  Real* S1 = S0 + Z::FULL;
+  double* piv = reinterpret_cast<double*>(S1 + Z::FULL);
+  const long ts = (long)p.nT * DD;
+  Real* TKt = a.tab + (long)TK * ts;
+  Real* TGt = a.tab + (long)TG * ts;
+  Real* TLt = a.tab + (long)TLS * ts;
+  const Real* PF = a.tab + (long)TPF * ts;
+  const int s = blockIdx.x;
+  Real* Pp = w_slot<Real, DP>(a, s, 0);
+  Real* Li = w_slot<Real, DP>(a, s, 1);
+  Real* X = w_slot<Real, DP>(a, s, 2);
+  Real* Y = w_slot<Real, DP>(a, s, 3);
+  Real* Sg = w_slot<Real, DP>(a, s, 4);
+  int bad = 0;
+  for (int t = blockIdx.x; t <= p.nT; t += gridDim.x) {
+    if (t < p.nT) {
+      // P^p_t
+      if (t == 0) {
+        w_axpby<Real, DP>(p.P0, false, (Real)1, nullptr, (Real)0, Pp);
+      } else if (p.fdiag) {
+        __syncthreads();
+        const Real* Pf = PF + (long)(t - 1) * DD;
+        for (int q = threadIdx.x; q < DP * DP; q += WT) {
+          const int i = q / DP, j = q % DP;
+          Pp[q] = fma(p.F[i * DP + i] * p.F[j * DP + j], Pf[q], p.Q[q]);
+        }
+        __syncthreads();
+      } else {
+        w_gemm<Real, DP>(p.F, false, PF + (long)(t - 1) * DD, false, X, nullptr, (Real)1, (Real)0, S0);
+        w_gemm<Real, DP>(X, false, p.F, true, Pp, p.Q, (Real)1, (Real)1, S0);
+      }
+      // S_t = P^p_t + R: K'_t = r L^{-T} L^{-1}, log det S_t
+      const double ld = w_chol<Real, DP>(Pp, p.r, p.d, S0, piv, &bad);
+      if (threadIdx.x == 0) a.ldt[t] = 2.0 * ld;
+      w_trinv<Real, DP>(S0, S1);
+      w_store<Real, DP>(S1, Li, false);
+      w_gemm<Real, DP>(Li, true, Li, false, TKt + (long)t * DD, nullptr, p.r, (Real)0, S0);
+    }
+    if (t >= 1) {
+      // backward quantities of step t - 1
+      const Real* Pf = PF + (long)(t - 1) * DD;
+      if (t < p.nT) {
+        w_chol<Real, DP>(Pp, (Real)0, p.d, S0, piv, &bad);
+        w_trinv<Real, DP>(S0, S1);
+        w_store<Real, DP>(S1, Li, false);                         // chol(P^p_t)^{-1}
+        if (p.fdiag) {
+          __syncthreads();
+          for (int q = threadIdx.x; q < DP * DP; q += WT) X[q] = p.F[(q / DP) * DP + q / DP] * Pf[q];
+          __syncthreads();
+        } else {
+          w_gemm<Real, DP>(p.F, false, Pf, false, X, nullptr, (Real)1, (Real)0, S0);   // F P^f
+        }
+        w_gemm<Real, DP>(Li, false, X, false, Y, nullptr, (Real)1, (Real)0, S0);       // Y = W^T
+        w_gemm<Real, DP>(Li, true, Y, false, TGt + (long)(t - 1) * DD, nullptr, (Real)1, (Real)0, S0);   // G^T
+        w_gemm<Real, DP>(Y, true, Y, false, Sg, Pf, (Real)-1, (Real)1, S0);            // Sigma
+        w_chol<Real, DP>(Sg, (Real)0, p.d, S0, piv, &bad);
+      } else {
+        w_axpby<Real, DP>(Pf, false, (Real)0, nullptr, (Real)0, TGt + (long)(t - 1) * DD);   // G_{T-1} = 0
+        w_chol<Real, DP>(Pf, (Real)0, p.d, S0, piv, &bad);
+      }
+      w_store<Real, DP>(S0, TLt + (long)(t - 1) * DD, true);      // chol(Sigma)^T
+    }
+  }
+  if (bad && threadIdx.x == 0) atomicOr(a.status, ST_NOT_PD);
+}
+
+// per means block k: (M_e ... M_s)^T, (G_s ... G_e)^T, sum of log det S_t
+template <typename Real, int DP>
+__global__ void __launch_bounds__(WT) k_w_prod(KP<Real> p, WCovArgs<Real> a) {
+  using Z = WSz<Real, DP>;
+  constexpr long DD = Z::DD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* S0 = reinterpret_cast<Real*>(smem_raw);
+  const long ts = (long)p.nT * DD;
+  const Real* TKt = a.tab + (long)TK * ts;
+  const Real* TGt = a.tab + (long)TG * ts;
+  for (int k = blockIdx.x; k < p.nb; k += gridDim.x) {
+    const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
+    Real* AH = w_slot<Real, DP>(a, blockIdx.x, 0);
+    Real* GH = w_slot<Real, DP>(a, blockIdx.x, 1);
+    Real* X = w_slot<Real, DP>(a, blockIdx.x, 2);
+    Real* Fd = w_slot<Real, DP>(a, blockIdx.x, 3);   // diag(F) when F is diagonal
+    __syncthreads();
+    for (int q = threadIdx.x; q < DP * DP; q += WT) {
+      const Real id = (q / DP == q % DP) ? (Real)1 : (Real)0;
+      AH[q] = id;
+      GH[q] = id;
+    }
+    if (threadIdx.x < DP) Fd[threadIdx.x] = p.F[threadIdx.x * DP + threadIdx.x];
+    __syncthreads();
+    for (int t = s; t <= e; ++t) {
+      if (p.fdiag) {
+        w_gemm<Real, DP>(TKt + (long)t * DD, false, AH, false, AH, nullptr, (Real)1, (Real)0, S0, Fd);
+      } else {
+        w_gemm<Real, DP>(p.F, false, AH, false, X, nullptr, (Real)1, (Real)0, S0);
+        w_gemm<Real, DP>(TKt + (long)t * DD, false, X, false, AH, nullptr, (Real)1, (Real)0, S0);
+      }
+      w_gemm<Real, DP>(GH, false, TGt + (long)t * DD, true, GH, nullptr, (Real)1, (Real)0, S0);
+    }
+    w_axpby<Real, DP>(AH, true, (Real)1, nullptr, (Real)0, a.btab + (long)k * DD);
+    w_axpby<Real, DP>(GH, true, (Real)1, nullptr, (Real)0, a.btab + ((long)p.nb + k) * DD);
+    if (threadIdx.x == 0) {
+      double sl = 0.0;
+      for (int t = s; t <= e; ++t) sl += a.ldt[t];
+      a.ld[k] = sl;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Means. CTA (k, grp): block k, chains grp * CPC + g * W_CPT + j (thread row
+// r = tid % DP, row group g = tid / DP, j < W_CPT). vs: three vector slots
+// per chain slot, [3][CPC][DP].
+// ---------------------------------------------------------------------------
+// out[j] = sum_k Mt[k][r] v[slot(j)][k] (Mt: the transposed matrix, so that the
+// threads of a warp read consecutive entries)
+template <typename Real, int DP>
+__device__ __forceinline__ void w_matvec(const Real* __restrict__ Mt, const Real* v, int g, int r,
+                                         Real (&out)[W_CPT]) {
+#pragma unroll
+  for (int j = 0; j < W_CPT; ++j) out[j] = (Real)0;
+#pragma unroll 8
+  for (int k = 0; k < DP; ++k) {
+    const Real m = __ldg(Mt + (long)k * DP + r);
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j) out[j] = fma(m, v[(g * W_CPT + j) * DP + k], out[j]);
+  }
+}
+
+// m^p = F m + b for the thread's row (dense F: m in the vector slot vm)
+template <typename Real, int DP>
+__device__ __forceinline__ void w_predict(const KP<Real>& p, const Real (&m)[W_CPT], Real* vm, int g, int r,
+                                          Real (&mp)[W_CPT]) {
+  if (p.fdiag) {
+    const Real phi = p.F[r * DP + r], bb = p.b[r];
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j) mp[j] = fma(phi, m[j], bb);
+    return;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < W_CPT; ++j) vm[(g * W_CPT + j) * DP + r] = m[j];
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < W_CPT; ++j) {
+    Real s = p.b[r];
+    for (int k = 0; k < DP; ++k) s = fma(p.F[r * DP + k], vm[(g * W_CPT + j) * DP + k], s);
+    mp[j] = s;
+  }
+}
+
+// block-local filtering means from a zero start (block 0: from m0), with the
+// linearisation and the auxiliary draw when a.x is given
+template <typename Real, int DP>
+__global__ void __launch_bounds__(WT) k_wmf_reduce(KP<Real> p, MeanArgs<Real> a) {
+  refresh_delta(p);
+  using Z = WSz<Real, DP>;
+  constexpr int CPC = Z::CPC;
+  constexpr long DD = Z::DD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* v0 = reinterpret_cast<Real*>(smem_raw);
+  Real* v1 = v0 + CPC * DP;
+  Real* v2 = v1 + CPC * DP;
+  const int k = blockIdx.x % p.nb, grp = blockIdx.x / p.nb;
+  const int r = threadIdx.x % DP, g = threadIdx.x / DP;
+  const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
+  const Real* TKt = a.tab + (long)TK * p.nT * DD;
+  int cidx[W_CPT];
+  bool valid[W_CPT];
+#pragma unroll
+  for (int j = 0; j < W_CPT; ++j) {
+    cidx[j] = grp * CPC + g * W_CPT + j;
+    valid[j] = cidx[j] < p.C;
+  }
+  const bool lg = a.x && p.emis == AUX_EMIS_LINEAR_GAUSSIAN;
+  Real m[W_CPT];
+#pragma unroll
+  for (int j = 0; j < W_CPT; ++j) m[j] = (Real)0;
+  for (int t = s; t <= e; ++t) {
+    Real yti[W_CPT], xi[W_CPT], yv[W_CPT];
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j) {
+      yti[j] = xi[j] = yv[j] = (Real)0;
+      if (valid[j] && r < p.d) {
+        const long ct = (long)cidx[j] * p.nT + t;
+        if (a.x) {
+          xi[j] = a.x[ct * p.d + r];
+          yv[j] = p.y[(p.y_per_chain ? ct : (long)t) * p.d + r];
+        } else {
+          yti[j] = a.yt[ct * p.d + r];
+        }
+      }
+    }
+    if (a.x) {
+      Real vi[W_CPT];
+      if (lg) {   // v = R_y^{-1} (y - x)
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < W_CPT; ++j) v1[(g * W_CPT + j) * DP + r] = (r < p.d) ? yv[j] - xi[j] : (Real)0;
+        __syncthreads();
+        w_matvec<Real, DP>(p.Ryinv, v1, g, r, vi);
+      }
+      const bool obs = !p.mask || p.mask[t];
+#pragma unroll
+      for (int j = 0; j < W_CPT; ++j) {
+        if (!lg) vi[j] = (r < p.d) ? (Real)-0.5 + (Real)0.5 * yv[j] * yv[j] * exp(-xi[j]) : (Real)0;
+        if (!obs) vi[j] = (Real)0;
+        if (valid[j] && r < p.d) {
+          const long ct = (long)cidx[j] * p.nT + t;
+          const Real ep = philox_normal<Real>(p.seed, (uint32_t)cidx[j], iter_of(p, a.iter), PURPOSE_AUX,
+                                              (uint32_t)t, r);
+          const Real ui = xi[j] + p.sqrt_r * ep;
+          yti[j] = ui + p.r * vi[j];
+          a.u[ct * p.d + r] = ui;
+          a.v[ct * p.d + r] = vi[j];
+          a.yt[ct * p.d + r] = yti[j];
+        }
+      }
+    }
+    Real mp[W_CPT];
+    if (t == 0) {
+#pragma unroll
+      for (int j = 0; j < W_CPT; ++j) mp[j] = p.m0[r];
+    } else {
+      w_predict<Real, DP>(p, m, v2, g, r, mp);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j) v0[(g * W_CPT + j) * DP + r] = (r < p.d) ? yti[j] - mp[j] : (Real)0;
+    __syncthreads();
+    Real kv[W_CPT];
+    w_matvec<Real, DP>(TKt + (long)t * DD, v0, g, r, kv);
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j) m[j] = (r < p.d) ? yti[j] - kv[j] : (Real)0;
+  }
+#pragma unroll
+  for (int j = 0; j < W_CPT; ++j) {
+    if (valid[j]) a.z[((long)cidx[j] * p.nb + k) * DP + r] = m[j];
+    if (valid[j] && a.x && k == 0 && r == 0) p.status_iter[cidx[j]] = *a.cov_status;
+  }
+}
+
+// composition over the blocks, one CTA of DP threads per chain (the recursions of k_mean_cross);
+// matsT: the transposed block products
+template <typename Real, int DP>
+__global__ void __launch_bounds__(DP) k_wmean_cross(KP<Real> p, const Real* __restrict__ matsT,
+                                                    const Real* __restrict__ in, Real* __restrict__ out,
+                                                    int backward) {
+  constexpr long DD = WSz<Real, DP>::DD;
+  __shared__ Real vb[2][DP];
+  const int c = blockIdx.x, r = threadIdx.x;
+  const long cb = (long)c * p.nb;
+  const int n = backward ? p.nb - 1 : max(0, p.nb - 2);
+  Real m = (Real)0;
+  if (backward) {
+    out[(cb + p.nb - 1) * DP + r] = (Real)0;
+  } else {
+    m = in[cb * DP + r];
+    if (p.nb > 1) out[(cb + 1) * DP + r] = m;
+  }
+  for (int j = 0; j < n; ++j) {
+    const int kk = backward ? p.nb - 1 - j : 1 + j;
+    Real* v = vb[j & 1];
+    v[r] = m;
+    __syncthreads();
+    const Real* M = matsT + (long)kk * DD;
+    Real sacc = in[(cb + kk) * DP + r];
+#pragma unroll 8
+    for (int q = 0; q < DP; ++q) sacc = fma(__ldg(M + (long)q * DP + r), v[q], sacc);
+    m = sacc;
+    out[(cb + (backward ? kk - 1 : kk + 1)) * DP + r] = m;
+  }
+}
+
+// sum over the rows of the CTA's chain slots into red[CPC] (FP64), then
+// the chain slot's value is red[slot] after the barrier
+template <typename Real, int DP>
+__device__ __forceinline__ void w_rowsum(double* red, int slot, double v) {
+  v = warp_sum<double>(v);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&red[slot], v);
+}
+
+// filtering means from the true block start, likelihood terms, and (APPLY_EPI) the
+// backward elements U_t with the block aggregate of the (G, U) scan
+template <typename Real, int DP>
+__global__ void __launch_bounds__(WT) k_wmf_apply(KP<Real> p, MeanArgs<Real> a) {
+  refresh_delta(p);
+  using Z = WSz<Real, DP>;
+  constexpr int CPC = Z::CPC;
+  constexpr long DD = Z::DD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* v0 = reinterpret_cast<Real*>(smem_raw);
+  Real* v1 = v0 + CPC * DP;
+  Real* v2 = v1 + CPC * DP;
+  double* red = reinterpret_cast<double*>(v2 + CPC * DP);
+  const int k = blockIdx.x % p.nb, grp = blockIdx.x / p.nb;
+  const int r = threadIdx.x % DP, g = threadIdx.x / DP;
+  const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
+  const long ts = (long)p.nT * DD;
+  const Real* TKt = a.tab + (long)TK * ts;
+  const Real* TGt = a.tab + (long)TG * ts;
+  const Real* TLt = a.tab + (long)TLS * ts;
+  const Real* PF = a.tab + (long)TPF * ts;
+  const bool epi = a.flags & APPLY_EPI;
+  if (threadIdx.x < CPC) red[threadIdx.x] = 0.0;
+  int cidx[W_CPT];
+  bool valid[W_CPT];
+  Real mp[W_CPT];
+  double qacc[W_CPT];
+#pragma unroll
+  for (int j = 0; j < W_CPT; ++j) {
+    cidx[j] = grp * CPC + g * W_CPT + j;
+    valid[j] = cidx[j] < p.C;
+    qacc[j] = 0.0;
+  }
+  if (k == 0) {
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j) mp[j] = p.m0[r];
+  } else {
+    Real ms[W_CPT];
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j) ms[j] = valid[j] ? a.mstart[((long)cidx[j] * p.nb + k) * DP + r] : (Real)0;
+    w_predict<Real, DP>(p, ms, v2, g, r, mp);
+  }
+  for (int t = s; t <= e; ++t) {
+    Real yti[W_CPT];
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j)
+      yti[j] = (valid[j] && r < p.d) ? a.yt[((long)cidx[j] * p.nT + t) * p.d + r] : (Real)0;
+    Real ej[W_CPT];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j) {
+      ej[j] = (r < p.d) ? yti[j] - mp[j] : (Real)0;
+      v0[(g * W_CPT + j) * DP + r] = ej[j];
+    }
+    __syncthreads();
+    Real kv[W_CPT], m[W_CPT];
+    w_matvec<Real, DP>(TKt + (long)t * DD, v0, g, r, kv);
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j) {
+      qacc[j] += (double)ej[j] * (double)kv[j];
+      m[j] = (r < p.d) ? yti[j] - kv[j] : (Real)0;
+      const long ct = (long)cidx[j] * p.nT + t;
+      if (valid[j] && a.mf && r < p.d) a.mf[ct * p.d + r] = m[j];
+      if (valid[j] && a.Pf && r < p.d)
+        for (int jj = 0; jj < p.d; ++jj) a.Pf[(ct * p.d + r) * p.d + jj] = PF[t * DD + (long)r * DP + jj];
+    }
+    Real mpn[W_CPT];
+    if (t < p.nT - 1) w_predict<Real, DP>(p, m, v2, g, r, mpn);
+    else {
+#pragma unroll
+      for (int j = 0; j < W_CPT; ++j) mpn[j] = (Real)0;
+    }
+    if (epi) {
+      // U_t = m^f_t - G_t m^p_{t+1} + chol(Sigma_t) eps_t
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < W_CPT; ++j) {
+        Real ei = (Real)0;
+        if (r < p.d && valid[j] && !(a.flags & APPLY_SMOOTH))
+          ei = a.eps ? a.eps[((long)cidx[j] * p.nT + t) * p.d + r]
+                     : philox_normal<Real>(p.seed, (uint32_t)cidx[j], iter_of(p, a.iter), PURPOSE_BACKWARD,
+                                           (uint32_t)t, r);
+        v1[(g * W_CPT + j) * DP + r] = mpn[j];
+        v2[(g * W_CPT + j) * DP + r] = ei;
+      }
+      __syncthreads();
+      Real gm[W_CPT], ln[W_CPT];
+      w_matvec<Real, DP>(TGt + (long)t * DD, v1, g, r, gm);
+      w_matvec<Real, DP>(TLt + (long)t * DD, v2, g, r, ln);
+#pragma unroll
+      for (int j = 0; j < W_CPT; ++j)
+        if (valid[j]) a.U[((long)cidx[j] * p.nT + t) * DP + r] = m[j] - gm[j] + ln[j];
+    }
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j) mp[j] = mpn[j];
+  }
+  if (epi) {
+    // block aggregate sum_t (G_s ... G_{t-1}) U_t by Horner's rule from the block end
+    Real ub[W_CPT];
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j) ub[j] = valid[j] ? a.U[((long)cidx[j] * p.nT + e) * DP + r] : (Real)0;
+    for (int t = e - 1; t >= s; --t) {
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < W_CPT; ++j) v1[(g * W_CPT + j) * DP + r] = ub[j];
+      __syncthreads();
+      Real gu[W_CPT];
+      w_matvec<Real, DP>(TGt + (long)t * DD, v1, g, r, gu);
+#pragma unroll
+      for (int j = 0; j < W_CPT; ++j)
+        ub[j] = gu[j] + (valid[j] ? a.U[((long)cidx[j] * p.nT + t) * DP + r] : (Real)0);
+    }
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j)
+      if (valid[j]) a.guv[((long)cidx[j] * p.nb + k) * DP + r] = ub[j];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < W_CPT; ++j) w_rowsum<Real, DP>(red, g * W_CPT + j, qacc[j]);
+  __syncthreads();
+  if (r == 0) {
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j) {
+      if (!valid[j]) continue;
+      const double q = red[g * W_CPT + j] / (double)p.r;
+      const int c = cidx[j];
+      const long ck = (long)c * p.nb + k;
+      if (a.flags & APPLY_STORE_Q) a.fqb[ck] = q;
+      if (a.flags & APPLY_REV_DIFF) a.lz_part[ck] = -0.5 * (a.fqb[ck] - q);
+      if (a.flags & APPLY_LOGZ) {
+        const double half_dlog2pi = 0.5 * p.d * 1.8378770664093454835606594728112;
+        a.lz_part[ck] = -((double)(e - s + 1) * half_dlog2pi + 0.5 * (a.ld[k] + q));
+      }
+      if (a.status && k == 0 && *a.cov_status) atomicOr(&a.status[c], *a.cov_status);
+    }
+  }
+}
+
+// backward sampling inside each block from x*_{e+1}: x*_t = G_t x*_{t+1} + U_t, with the MH
+// terms of mh_step_terms (first-order proposal) when b.mh
+template <typename Real, int DP>
+__global__ void __launch_bounds__(WT) k_wmb_apply(KP<Real> p, BackArgs<Real> b, const Real* __restrict__ xnext) {
+  refresh_delta(p);
+  using Z = WSz<Real, DP>;
+  constexpr int CPC = Z::CPC;
+  constexpr long DD = Z::DD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* v0 = reinterpret_cast<Real*>(smem_raw);
+  Real* v1 = v0 + CPC * DP;
+  double* red = reinterpret_cast<double*>(v1 + 2 * CPC * DP);
+  const int k = blockIdx.x % p.nb, grp = blockIdx.x / p.nb;
+  const int r = threadIdx.x % DP, g = threadIdx.x / DP;
+  const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
+  const bool lg = b.mh && p.emis == AUX_EMIS_LINEAR_GAUSSIAN;
+  if (threadIdx.x < CPC) red[threadIdx.x] = 0.0;
+  int cidx[W_CPT];
+  bool valid[W_CPT];
+  Real xi[W_CPT];
+  double acc[W_CPT];
+#pragma unroll
+  for (int j = 0; j < W_CPT; ++j) {
+    cidx[j] = grp * CPC + g * W_CPT + j;
+    valid[j] = cidx[j] < p.C;
+    xi[j] = valid[j] ? xnext[((long)cidx[j] * p.nb + k) * DP + r] : (Real)0;
+    acc[j] = 0.0;
+  }
+  for (int t = e; t >= s; --t) {
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j) v0[(g * W_CPT + j) * DP + r] = xi[j];
+    __syncthreads();
+    Real gx[W_CPT];
+    w_matvec<Real, DP>(b.G + (long)t * DD, v0, g, r, gx);
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j) {
+      xi[j] = gx[j] + (valid[j] ? b.U[((long)cidx[j] * p.nT + t) * DP + r] : (Real)0);
+      if (valid[j] && r < p.d) b.xs[((long)cidx[j] * p.nT + t) * p.d + r] = xi[j];
+    }
+    if (!b.mh) continue;
+    Real vsi[W_CPT];
+    if (lg) {
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < W_CPT; ++j) {
+        const long ct = (long)cidx[j] * p.nT + t;
+        const Real yi = (valid[j] && r < p.d) ? p.y[(p.y_per_chain ? ct : (long)t) * p.d + r] : (Real)0;
+        v1[(g * W_CPT + j) * DP + r] = (r < p.d) ? yi - xi[j] : (Real)0;
+      }
+      __syncthreads();
+      w_matvec<Real, DP>(p.Ryinv, v1, g, r, vsi);
+    }
+    const bool obs = !p.mask || p.mask[t];
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j) {
+      if (!valid[j] || r >= p.d) continue;
+      const long ct = (long)cidx[j] * p.nT + t, idx = ct * p.d + r;
+      const Real xo = b.x[idx], ui = b.u[idx], vi = b.v[idx];
+      const Real yi = p.y[(p.y_per_chain ? ct : (long)t) * p.d + r];
+      const Real xs = xi[j];
+      Real vs = lg ? vsi[j] : (Real)0, gdiff = (Real)0;
+      if (obs) {
+        if (p.emis == AUX_EMIS_SV) {
+          vs = (Real)-0.5 + (Real)0.5 * yi * yi * exp(-xs);
+          gdiff = (Real)-0.5 * (xs - xo) - (Real)0.5 * yi * yi * (exp(-xs) - exp(-xo));
+        } else {
+          gdiff = (Real)-0.5 * (yi - xs) * vs + (Real)0.5 * (yi - xo) * vi;
+        }
+      } else {
+        vs = (Real)0;
+      }
+      const Real fwd = vi * (ui - xs) + (Real)0.5 * p.r * vi * vi;
+      const Real rev = vs * (ui - xo) + (Real)0.5 * p.r * vs * vs;
+      acc[j] += (double)gdiff + (double)fwd - (double)rev;
+      b.yts[idx] = ui + p.r * vs;
+    }
+  }
+  if (!b.mh) return;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < W_CPT; ++j) w_rowsum<Real, DP>(red, g * W_CPT + j, acc[j]);
+  __syncthreads();
+  if (r == 0) {
+#pragma unroll
+    for (int j = 0; j < W_CPT; ++j)
+      if (valid[j]) b.mh_part[(long)cidx[j] * p.nb + k] = red[g * W_CPT + j];
+  }
+}
+
+}  // namespace auxk

@@ -1,0 +1,177 @@
+"""Wide state dimensions (33 <= d <= 128, padded to 64 or 128): the table modes'
+covariance pass by doubling over the steps and the per-chain means kernels of
+aux_wide.cuh, through the C ABI, against the FP64 oracle.
+
+Tolerances: 1e-4 normwise on filtering means, covariances and sampled paths and
+1e-5 on log Z (the FP32 targets); log alpha within an absolute bound that grows
+with the number T * d of FP32 per-element terms summed (2e-3 at T * d = 3e4, as
+in the narrow parity tests; 4e-2 at T * d = 5e5 for the full-size step).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import kalman, mcmc, philox  # noqa: E402
+from paper_2303_00301_gb300 import AuxKalman, workloads  # noqa: E402
+from paper_2303_00301_gb300 import _binding as B  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_00301_gb300 import build
+    build.build()
+
+
+def _tt(a, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300)
+
+
+def _workload(d, T, C, seed, delta=0.5, dense_f=False):
+    m = workloads.random_lgssm(d, T, seed=seed)
+    F = m["F"]
+    if not dense_f:
+        F = np.diag(np.diag(F))
+    return workloads.Workload(name="rand", d=d, T=T, n_chains=C, m0=m["m0"], P0=m["P0"],
+                              F=F, b=m["b"], Q=m["Q"], y=m["y"],
+                              emission=workloads.EMIS_LINEAR_GAUSSIAN, delta=delta,
+                              x_init=np.zeros((C, T, d)), Ry=np.eye(d))
+
+
+CASES = [
+    # d, T, C, block_len, mode, dense F: both widths, ragged blocks and chain groups, T = 1, 2
+    (40, 50, 3, 7, "cached", False),
+    (64, 33, 17, 8, "shared", False),
+    (64, 2, 2, 1, "cached", False),
+    (33, 1, 2, 1, "shared", False),
+    (100, 70, 9, 16, "cached", False),
+    (128, 129, 2, 32, "shared", False),
+    (48, 40, 3, 6, "shared", True),
+    (128, 20, 2, 5, "cached", True),
+]
+
+
+@pytest.mark.parametrize("d,T,C,L,mode,dense", CASES)
+def test_loglik_matches_the_kalman_filter(d, T, C, L, mode, dense):
+    wl = _workload(d, T, C, seed=7 * d + T, dense_f=dense)
+    yt = np.random.default_rng(d + T).standard_normal((C, T, d))
+    s = AuxKalman(wl, dtype="f32", block_len=L, mode=mode)
+    logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
+    mf = torch.zeros((C, T, d), dtype=torch.float32, device="cuda")
+    Pf = torch.zeros((C, T, d, d), dtype=torch.float32, device="cuda")
+    s.loglik(_tt(yt), logZ, mf, Pf)
+    torch.cuda.synchronize()
+    rc, st = s.status()
+    s.close()
+    R = 0.5 * wl.delta * np.eye(d)
+    lz, mfg, Pfg = logZ.cpu().numpy(), mf.double().cpu().numpy(), Pf.double().cpu().numpy()
+    for c in range(C):
+        kf = kalman.kalman_filter(yt[c], wl.m0, wl.P0, wl.F, wl.b, wl.Q, R)
+        assert abs(lz[c] - kf["logZ"]) <= 1e-5 * abs(kf["logZ"]), (c, lz[c], kf["logZ"])
+        assert _rel(mfg[c], kf["mf"]) < 1e-4
+        assert _rel(Pfg[c], kf["Pf"]) < 1e-4
+    assert rc == 0 and not np.any(st)
+
+
+@pytest.mark.parametrize("d,T,C,L,mode", [(40, 50, 3, 7, "cached"), (64, 33, 17, 8, "shared"),
+                                          (128, 45, 2, 16, "cached")])
+def test_sample_path_matches_the_rts_sampler(d, T, C, L, mode):
+    wl = _workload(d, T, C, seed=3 * d + T)
+    rng = np.random.default_rng(d * T)
+    yt = rng.standard_normal((C, T, d))
+    eps = rng.standard_normal((C, T, d))
+    s = AuxKalman(wl, dtype="f32", block_len=L, mode=mode)
+    xs = torch.zeros((C, T, d), dtype=torch.float32, device="cuda")
+    logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
+    s.sample_path(_tt(yt), xs, eps=_tt(eps), logZ=logZ)
+    torch.cuda.synchronize()
+    assert s.status()[0] == 0
+    s.close()
+    R = 0.5 * wl.delta * np.eye(d)
+    for c in range(C):
+        kf = kalman.kalman_filter(yt[c], wl.m0, wl.P0, wl.F, wl.b, wl.Q, R)
+        ref = kalman.rts_sample(kf, wl.F, wl.b, wl.Q, eps[c])
+        assert _rel(xs[c].double().cpu().numpy(), ref) < 1e-4
+        assert abs(logZ[c].item() - kf["logZ"]) <= 1e-5 * abs(kf["logZ"])
+
+
+def _step_parity(wl, L, mode, n_iters, tol_x, tol_la, chains=None):
+    C = wl.n_chains
+    s = AuxKalman(wl, dtype="f32", block_len=L, mode=mode)
+    x = _tt(wl.x_init)
+    la = torch.zeros(C, dtype=torch.float64, device="cuda")
+    if wl.emission == workloads.EMIS_SV:
+        em = mcmc.SVEmission(wl.y, wl.mask)
+    else:
+        em = mcmc.LinearGaussianEmission(wl.y, wl.Ry, wl.mask)
+    model = dict(m0=wl.m0, P0=wl.P0, F=wl.F, b=wl.b, Q=wl.Q, emission=em)
+    moved, worst = 0, 0.0
+    for it in range(n_iters):
+        x_before = x.double().cpu().numpy()
+        s.step(x, 1, iter0=it, log_alpha=la)
+        torch.cuda.synchronize()
+        xg = x.double().cpu().numpy()
+        for c in (range(C) if chains is None else chains):
+            ref = mcmc.aux_step_philox(x_before[c], model, wl.delta, wl.mcmc_seed, c, it)
+            lu = np.log(philox.mh_uniform(wl.mcmc_seed, c, it))
+            worst = max(worst, abs(la[c].item() - ref["log_alpha"]))
+            near = abs(ref["log_alpha"] - lu) < tol_la
+            assert abs(la[c].item() - ref["log_alpha"]) < tol_la or near
+            if bool(lu < la[c].item()) != ref["accepted"]:
+                assert near
+                continue
+            if ref["accepted"]:
+                moved += 1
+                assert _rel(xg[c], ref["x_star"]) < tol_x
+            else:
+                assert np.array_equal(xg[c], x_before[c])
+    assert s.status()[0] == 0
+    s.close()
+    return moved, worst
+
+
+@pytest.mark.parametrize("mode", ["shared", "cached"])
+def test_kalman_step_parity_sv(mode):
+    wl = workloads.stochastic_volatility(d=40, T=48, n_chains=3, delta=0.02)
+    moved, worst = _step_parity(wl, 8, mode, 3, 1e-4, 2e-3)
+    print("d = 40: moves", moved, "max |d log alpha|", worst)
+    assert moved > 0
+
+
+def test_kalman_step_parity_linear_gaussian_dense_dynamics():
+    wl = _workload(72, 30, 3, seed=5, delta=0.3, dense_f=True)
+    _step_parity(wl, 6, "cached", 2, 1e-4, 2e-3)
+
+
+def test_kalman_step_full_size_sampled_chains():
+    """d = 128, T = 4096, 16 chains (the mixed-precision workload's shape), cached
+    tables: one step of every chain, chains 0 and 15 against the oracle."""
+    wl = workloads.stochastic_volatility(d=128, T=4096, n_chains=16)
+    moved, worst = _step_parity(wl, 0, "cached", 1, 1e-4, 4e-2, chains=(0, 15))
+    print("d = 128, T = 4096: max |d log alpha|", worst)
+
+
+def test_scope_is_reported():
+    wl = _workload(40, 12, 2, seed=1)
+    x = _tt(wl.x_init)
+    s = AuxKalman(wl, dtype="f32", block_len=4)          # per-chain mode
+    with pytest.raises(B.AuxError):
+        s.step(x, 1)
+    logZ = torch.zeros(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.AuxError):
+        s.loglik(_tt(np.zeros((2, 12, 40))), logZ)
+    s.close()
+    for kw in (dict(sampler="bridging"), dict(filter_form="square_root"), dict(proposal=2)):
+        with pytest.raises(B.AuxError):
+            AuxKalman(wl, dtype="f32", block_len=4, mode="cached", **kw)
+    with pytest.raises(B.AuxError):
+        AuxKalman(workloads.stochastic_volatility(d=129, T=8, n_chains=1), dtype="f32")
+    with pytest.raises(B.AuxError):
+        AuxKalman(wl, dtype="f64", block_len=4, mode="cached")
