@@ -66,8 +66,10 @@ def _desc_kwargs(**over):
     (dict(n_chains=0), 1),
     (dict(emis_kind=7), 1),
     (dict(dtype=5), 1),
-    (dict(d_x=33, m0=np.zeros(33), P0=np.eye(33), F=np.eye(33), b=np.zeros(33), Q=np.eye(33),
-          y=np.zeros((8, 33)), R_y=np.eye(33)), 7),            # beyond the built sizes
+    (dict(d_x=129, m0=np.zeros(129), P0=np.eye(129), F=np.eye(129), b=np.zeros(129), Q=np.eye(129),
+          y=np.zeros((8, 129)), R_y=np.eye(129)), 7),          # beyond the built sizes
+    (dict(dtype=1, d_x=33, m0=np.zeros(33), P0=np.eye(33), F=np.eye(33), b=np.zeros(33), Q=np.eye(33),
+          y=np.zeros((8, 33)), R_y=np.eye(33)), 7),            # FP64 stops at 16
     (dict(emis_kind=2, nu=1.0, Q=np.array([[0.1, 0.02], [0.02, 0.1]])), 7),   # Student-t needs a diagonal prior
     (dict(emis_kind=2, nu=0.0), 1),                            # Student-t needs nu > 0
     (dict(emis_kind=2, nu=1.0, R_y=None), 1),                  # and a scale matrix
