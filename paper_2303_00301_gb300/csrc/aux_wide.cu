@@ -24,6 +24,7 @@ struct WOps {
     AUX_W_ATTR((k_wmf_reduce<Real, DP>), Z::MSMEM)
     AUX_W_ATTR((k_wmf_apply<Real, DP>), Z::MSMEM)
     AUX_W_ATTR((k_wmb_apply<Real, DP>), Z::MSMEM)
+    AUX_W_ATTR((k_wmean_cross<Real, DP>), Z::XSMEM)
 #undef AUX_W_ATTR
     return AUX_OK;
   }
@@ -84,7 +85,7 @@ struct WOps {
       k_wmf_reduce<Real, DP><<<grid, WT, Z::MSMEM, st>>>(p, a); }
     a.x = nullptr;
     { ProfScope ps(m, PK_SCAN, st);
-      k_wmean_cross<Real, DP><<<m->C, DP, 0, st>>>(p, (const Real*)m->btab, a.z, (Real*)m->ms, 0); }
+      k_wmean_cross<Real, DP><<<m->C, DP, Z::XSMEM, st>>>(p, (const Real*)m->btab, a.z, (Real*)m->ms, 0); }
     a.mstart = (const Real*)m->ms;
     { ProfScope ps(m, PK_APPLY, st);
       k_wmf_apply<Real, DP><<<grid, WT, Z::MSMEM, st>>>(p, a); }
@@ -102,7 +103,7 @@ struct WOps {
   static void backward(aux_model* m, const KP<Real>& p, BackArgs<Real> b, cudaStream_t st) {
     ProfScope ps(m, PK_BACKWARD, st, 2);
     Real* xnext = (Real*)m->zb;
-    k_wmean_cross<Real, DP><<<m->C, DP, 0, st>>>(p, b.gum, b.guv, xnext, 1);
+    k_wmean_cross<Real, DP><<<m->C, DP, Z::XSMEM, st>>>(p, b.gum, b.guv, xnext, 1);
     k_wmb_apply<Real, DP><<<mean_grid(m), WT, Z::MSMEM, st>>>(p, b, (const Real*)xnext);
   }
 

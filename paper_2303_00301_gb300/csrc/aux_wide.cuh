@@ -43,20 +43,27 @@ namespace auxk {
 constexpr int WT = 256;          // threads of every wide kernel
 constexpr int W_SLOTS = 2 * 152; // CTAs with their own scratch (2 per SM)
 constexpr int W_SCR = 8;         // scratch matrices per slot
-constexpr int W_CPT = 4;         // chains per thread in the means kernels
+// chains per thread in the means kernels (8 chains per CTA at DP = 128, 16 at 64)
+template <int DP> constexpr int WCPT = 4;
 
 template <typename Real, int DP> struct WSz {
   static constexpr int LDS = DP + 1;                 // shared row stride (odd: column access is conflict-free)
   static constexpr int KC = 32;                      // k-chunk of w_gemm
   static constexpr int R = DP / 16;                  // outputs per thread and dimension in w_gemm
   static constexpr int NRG = WT / DP;                // row groups of the means kernels
-  static constexpr int CPC = NRG * W_CPT;            // chains per CTA of the means kernels
+  static constexpr int CPC = NRG * WCPT<DP>;            // chains per CTA of the means kernels
   static constexpr long DD = (long)DP * DP;
   static constexpr size_t FULL = (size_t)DP * LDS;   // one padded matrix
-  // two padded matrices (factor and inverse), or the two k-chunks of w_gemm; scalars
-  static constexpr size_t SMEM = 2 * FULL * sizeof(Real) + (DP + 64) * sizeof(double);
-  // means: three vector slots per chain (smem) and per-chain FP64 sums
-  static constexpr size_t MSMEM = (size_t)3 * CPC * DP * sizeof(Real) + 2 * CPC * sizeof(double);
+  // one padded matrix (factor, inverted in place) or the two k-chunks of w_gemm; the
+  // pivots (FP64) and a column (two CTAs per SM at DP = 128)
+  static constexpr size_t GEMM = 2 * (size_t)KC * LDS;
+  static constexpr size_t SMEM = (FULL > GEMM ? FULL : GEMM) * sizeof(Real) + (2 * DP + 8) * sizeof(double);
+  // matrix staging buffers of the means kernels (one copy in flight while one is read)
+  static constexpr int NBUF = 2;
+  // means: NBUF matrix staging buffers, three vector slots per chain, per-chain FP64 sums
+  static constexpr size_t MSMEM = (size_t)(NBUF * DD + 3 * CPC * DP) * sizeof(Real) + 2 * CPC * sizeof(double);
+  // composition over the blocks: the staging buffers, two vector slots
+  static constexpr size_t XSMEM = (size_t)(NBUF * DD + 2 * DP) * sizeof(Real);
 };
 
 // ---------------------------------------------------------------------------
@@ -203,25 +210,30 @@ __device__ double w_chol(const Real* A, Real addiag, int d, Real* S, double* piv
   return ld;
 }
 
-// X = L^{-1} into the shared slot X (lower triangular), L lower triangular in S.
-// Right-looking by rows: X = I; for k: X_k <- X_k / L_kk; X_i <- X_i - L_ik X_k (i > k).
+// L^{-1} in place of the lower-triangular L in the shared slot S, by columns from
+// the last: with the trailing block already inverted,
+//   (L^{-1})_jj = 1 / L_jj,  (L^{-1})_ij = -(1 / L_jj) sum_{k=j+1..i} (L^{-1})_ik L_kj  (i > j),
+// one thread per row; col: DP elements of shared scratch (the old column j).
 template <typename Real, int DP>
-__device__ void w_trinv(const Real* S, Real* X) {
+__device__ void w_trinv(Real* S, Real* col) {
   constexpr int LDS = WSz<Real, DP>::LDS;
-  __syncthreads();
-  for (int q = threadIdx.x; q < DP * DP; q += WT) {
-    const int i = q / DP, j = q % DP;
-    X[i * LDS + j] = (i == j) ? (Real)1 / S[i * LDS + i] : (Real)0;
-  }
-  for (int k = 0; k < DP - 1; ++k) {
+  for (int j = DP - 1; j >= 0; --j) {
     __syncthreads();
-    // rows i > k, columns c <= k (row k is final: its diagonal was divided at the start)
-    const int nr = DP - 1 - k, nc = k + 1;
-    for (int q = threadIdx.x; q < nr * nc; q += WT) {
-      const int i = k + 1 + q / nc, c = q % nc;
-      const Real f = S[i * LDS + k] / S[i * LDS + i];
-      X[i * LDS + c] = fma(-f, X[k * LDS + c], X[i * LDS + c]);
+    if (threadIdx.x < DP) col[threadIdx.x] = S[threadIdx.x * LDS + j];
+    __syncthreads();
+    const Real ajj = (Real)1 / col[j];
+    const int i = threadIdx.x;
+    if (i > j && i < DP) {
+      Real a0 = (Real)0, a1 = (Real)0;
+      int k = j + 1;
+      for (; k + 1 <= i; k += 2) {
+        a0 = fma(S[i * LDS + k], col[k], a0);
+        a1 = fma(S[i * LDS + k + 1], col[k + 1], a1);
+      }
+      if (k <= i) a0 = fma(S[i * LDS + k], col[k], a0);
+      S[i * LDS + j] = -ajj * (a0 + a1);
     }
+    if (threadIdx.x == 0) S[j * LDS + j] = ajj;
   }
   __syncthreads();
 }
@@ -258,14 +270,14 @@ __device__ __forceinline__ Real* w_slot(const WCovArgs<Real>& a, int s, int i) {
 
 // the distinct elements: prefix 0 = C_0 into TPF[0]; E = (A, C, J) into gk[0]
 template <typename Real, int DP>
-__global__ void __launch_bounds__(WT) k_w_elem(KP<Real> p, WCovArgs<Real> a) {
+__global__ void __launch_bounds__(WT, 2) k_w_elem(KP<Real> p, WCovArgs<Real> a) {
   refresh_delta(p);
   using Z = WSz<Real, DP>;
   constexpr long DD = Z::DD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* S0 = reinterpret_cast<Real*>(smem_raw);
-  Real* S1 = S0 + Z::FULL;
-  double* piv = reinterpret_cast<double*>(S1 + Z::FULL);
+  double* piv = reinterpret_cast<double*>(S0 + (Z::FULL > Z::GEMM ? Z::FULL : Z::GEMM));
+  Real* S1 = reinterpret_cast<Real*>(piv + DP + 8);   // a column
   Real* s0 = w_slot<Real, DP>(a, 0, 0);
   Real* s1 = w_slot<Real, DP>(a, 0, 1);
   Real* s2 = w_slot<Real, DP>(a, 0, 2);
@@ -274,7 +286,7 @@ __global__ void __launch_bounds__(WT) k_w_elem(KP<Real> p, WCovArgs<Real> a) {
   // t = 0: C_0 = P0 - Y^T Y, Y = chol(P0 + R)^{-1} P0
   w_chol<Real, DP>(p.P0, p.r, p.d, S0, piv, &bad);
   w_trinv<Real, DP>(S0, S1);
-  w_store<Real, DP>(S1, s0, false);
+  w_store<Real, DP>(S0, s0, false);
   w_gemm<Real, DP>(s0, false, p.P0, false, s1, nullptr, (Real)1, (Real)0, S0);
   w_gemm<Real, DP>(s1, true, s1, false, a.tab + (long)TPF * tstride, p.P0, (Real)-1, (Real)1, S0);
   // t >= 1: S = Q + R = L L^T, Y = L^{-1} Q, W = L^{-1} F
@@ -283,7 +295,7 @@ __global__ void __launch_bounds__(WT) k_w_elem(KP<Real> p, WCovArgs<Real> a) {
   Real* EJ = EC + DD;
   w_chol<Real, DP>(p.Q, p.r, p.d, S0, piv, &bad);
   w_trinv<Real, DP>(S0, S1);
-  w_store<Real, DP>(S1, s0, false);
+  w_store<Real, DP>(S0, s0, false);
   w_gemm<Real, DP>(s0, false, p.Q, false, s1, nullptr, (Real)1, (Real)0, S0);
   w_gemm<Real, DP>(s1, true, s1, false, EC, p.Q, (Real)-1, (Real)1, S0);       // C = Q - Y^T Y
   w_gemm<Real, DP>(s0, false, p.F, false, s2, nullptr, (Real)1, (Real)0, S0);  // W = L^{-1} F
@@ -309,7 +321,7 @@ __device__ void w_combine(const KP<Real>& p, const WCovArgs<Real>& a, int s, con
   w_gemm<Real, DP>(U, true, X, false, N, nullptr, (Real)1, (Real)0, S0, nullptr, true);   // N = I + U^T J_e U
   w_chol<Real, DP>(N, (Real)0, p.d, S0, piv, bad);
   w_trinv<Real, DP>(S0, S1);
-  w_store<Real, DP>(S1, N, false);                                      // chol(N)^{-1}
+  w_store<Real, DP>(S0, N, false);                                      // chol(N)^{-1}
   w_gemm<Real, DP>(U, false, N, true, B, nullptr, (Real)1, (Real)0, S0);           // B = U chol(N)^{-T}
   w_gemm<Real, DP>(Ae, false, B, false, Pm, nullptr, (Real)1, (Real)0, S0);        // P = A_e B
   if (Ao) {
@@ -330,14 +342,14 @@ __device__ void w_combine(const KP<Real>& p, const WCovArgs<Real>& a, int s, con
 // one doubling level: prefixes TPF[pow2 + i] = TPF[i] (x) E^(pow2), i < cnt; item cnt
 // (when sq): E^(2 pow2) = E^(pow2) (x) E^(pow2) into gk2
 template <typename Real, int DP>
-__global__ void __launch_bounds__(WT) k_w_double(KP<Real> p, WCovArgs<Real> a, int pow2, int cnt, int sq,
+__global__ void __launch_bounds__(WT, 2) k_w_double(KP<Real> p, WCovArgs<Real> a, int pow2, int cnt, int sq,
                                                   const Real* __restrict__ gk, Real* __restrict__ gk2) {
   using Z = WSz<Real, DP>;
   constexpr long DD = Z::DD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* S0 = reinterpret_cast<Real*>(smem_raw);
-  Real* S1 = S0 + Z::FULL;
-  double* piv = reinterpret_cast<double*>(S1 + Z::FULL);
+  double* piv = reinterpret_cast<double*>(S0 + (Z::FULL > Z::GEMM ? Z::FULL : Z::GEMM));
+  Real* S1 = reinterpret_cast<Real*>(piv + DP + 8);   // a column
   int bad = 0;
   Real* PF = a.tab + (long)TPF * p.nT * DD;
   const int n = cnt + (sq ? 1 : 0);
@@ -356,14 +368,14 @@ __global__ void __launch_bounds__(WT) k_w_double(KP<Real> p, WCovArgs<Real> a, i
 
 // per step t = 0 .. T (item T: the last step's backward quantities only)
 template <typename Real, int DP>
-__global__ void __launch_bounds__(WT) k_w_epi(KP<Real> p, WCovArgs<Real> a) {
+__global__ void __launch_bounds__(WT, 2) k_w_epi(KP<Real> p, WCovArgs<Real> a) {
   refresh_delta(p);
   using Z = WSz<Real, DP>;
   constexpr long DD = Z::DD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* S0 = reinterpret_cast<Real*>(smem_raw);
-  Real* S1 = S0 + Z::FULL;
-  double* piv = reinterpret_cast<double*>(S1 + Z::FULL);
+  double* piv = reinterpret_cast<double*>(S0 + (Z::FULL > Z::GEMM ? Z::FULL : Z::GEMM));
+  Real* S1 = reinterpret_cast<Real*>(piv + DP + 8);   // a column
   const long ts = (long)p.nT * DD;
   Real* TKt = a.tab + (long)TK * ts;
   Real* TGt = a.tab + (long)TG * ts;
@@ -397,7 +409,7 @@ __global__ void __launch_bounds__(WT) k_w_epi(KP<Real> p, WCovArgs<Real> a) {
       const double ld = w_chol<Real, DP>(Pp, p.r, p.d, S0, piv, &bad);
       if (threadIdx.x == 0) a.ldt[t] = 2.0 * ld;
       w_trinv<Real, DP>(S0, S1);
-      w_store<Real, DP>(S1, Li, false);
+      w_store<Real, DP>(S0, Li, false);
       w_gemm<Real, DP>(Li, true, Li, false, TKt + (long)t * DD, nullptr, p.r, (Real)0, S0);
     }
     if (t >= 1) {
@@ -406,7 +418,7 @@ __global__ void __launch_bounds__(WT) k_w_epi(KP<Real> p, WCovArgs<Real> a) {
       if (t < p.nT) {
         w_chol<Real, DP>(Pp, (Real)0, p.d, S0, piv, &bad);
         w_trinv<Real, DP>(S0, S1);
-        w_store<Real, DP>(S1, Li, false);                         // chol(P^p_t)^{-1}
+        w_store<Real, DP>(S0, Li, false);                         // chol(P^p_t)^{-1}
         if (p.fdiag) {
           __syncthreads();
           for (int q = threadIdx.x; q < DP * DP; q += WT) X[q] = p.F[(q / DP) * DP + q / DP] * Pf[q];
@@ -430,7 +442,7 @@ __global__ void __launch_bounds__(WT) k_w_epi(KP<Real> p, WCovArgs<Real> a) {
 
 // per means block k: (M_e ... M_s)^T, (G_s ... G_e)^T, sum of log det S_t
 template <typename Real, int DP>
-__global__ void __launch_bounds__(WT) k_w_prod(KP<Real> p, WCovArgs<Real> a) {
+__global__ void __launch_bounds__(WT, 2) k_w_prod(KP<Real> p, WCovArgs<Real> a) {
   using Z = WSz<Real, DP>;
   constexpr long DD = Z::DD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -472,43 +484,77 @@ __global__ void __launch_bounds__(WT) k_w_prod(KP<Real> p, WCovArgs<Real> a) {
 }
 
 // ---------------------------------------------------------------------------
-// Means. CTA (k, grp): block k, chains grp * CPC + g * W_CPT + j (thread row
-// r = tid % DP, row group g = tid / DP, j < W_CPT). vs: three vector slots
+// Means. CTA (k, grp): block k, chains grp * CPC + g * WCPT<DP> + j (thread row
+// r = tid % DP, row group g = tid / DP, j < WCPT<DP>). vs: three vector slots
 // per chain slot, [3][CPC][DP].
 // ---------------------------------------------------------------------------
-// out[j] = sum_k Mt[k][r] v[slot(j)][k] (Mt: the transposed matrix, so that the
-// threads of a warp read consecutive entries)
+// out[j] = sum_k Mt[k][r] v[slot(j)][k] (Mt: the transposed matrix, in shared or
+// global memory, so that the threads of a warp read consecutive entries)
 template <typename Real, int DP>
-__device__ __forceinline__ void w_matvec(const Real* __restrict__ Mt, const Real* v, int g, int r,
-                                         Real (&out)[W_CPT]) {
+__device__ __forceinline__ void w_matvec(const Real* Mt, const Real* v, int g, int r, Real (&out)[WCPT<DP>]) {
 #pragma unroll
-  for (int j = 0; j < W_CPT; ++j) out[j] = (Real)0;
-#pragma unroll 8
+  for (int j = 0; j < WCPT<DP>; ++j) out[j] = (Real)0;
+#pragma unroll 16
   for (int k = 0; k < DP; ++k) {
-    const Real m = __ldg(Mt + (long)k * DP + r);
+    const Real m = Mt[k * DP + r];
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j) out[j] = fma(m, v[(g * W_CPT + j) * DP + k], out[j]);
+    for (int j = 0; j < WCPT<DP>; ++j) out[j] = fma(m, v[(g * WCPT<DP> + j) * DP + k], out[j]);
   }
 }
 
+// A sequence of DP x DP matrices read in a fixed order, src(0), src(1), ...
+// (src(j) null past the end), staged into NB shared buffers with NB - 1 copies
+// in flight. get(src) waits for matrix i, then (after a CTA barrier, so that
+// every thread sees the whole copy and is done with matrix i - 1, whose
+// buffer is refilled next) issues the copy of matrix i + NB - 1 and returns
+// matrix i's buffer.
+template <typename Real, int DP>
+struct WStream {
+  static constexpr int NB = WSz<Real, DP>::NBUF;
+  Real* buf;
+  int i;
+  __device__ __forceinline__ void fetch(int j, const Real* src) {
+    constexpr int N = Vec16<Real>::N, NV = DP * DP / N;
+    Real* dst = buf + (long)(j % NB) * DP * DP;
+    if (src)
+      for (int q = threadIdx.x; q < NV; q += blockDim.x) cp_async16(dst + q * N, src + q * N);
+    cp_async_commit();
+  }
+  template <typename F>
+  __device__ __forceinline__ void begin(Real* b, F&& src) {
+    buf = b;
+    i = 0;
+    for (int j = 0; j < NB - 1; ++j) fetch(j, src(j));
+  }
+  template <typename F>
+  __device__ __forceinline__ const Real* get(F&& src) {
+    cp_async_wait<NB - 2>();
+    __syncthreads();
+    const Real* cur = buf + (long)(i % NB) * DP * DP;
+    fetch(i + NB - 1, src(i + NB - 1));
+    ++i;
+    return cur;
+  }
+};
+
 // m^p = F m + b for the thread's row (dense F: m in the vector slot vm)
 template <typename Real, int DP>
-__device__ __forceinline__ void w_predict(const KP<Real>& p, const Real (&m)[W_CPT], Real* vm, int g, int r,
-                                          Real (&mp)[W_CPT]) {
+__device__ __forceinline__ void w_predict(const KP<Real>& p, const Real (&m)[WCPT<DP>], Real* vm, int g, int r,
+                                          Real (&mp)[WCPT<DP>]) {
   if (p.fdiag) {
     const Real phi = p.F[r * DP + r], bb = p.b[r];
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j) mp[j] = fma(phi, m[j], bb);
+    for (int j = 0; j < WCPT<DP>; ++j) mp[j] = fma(phi, m[j], bb);
     return;
   }
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < W_CPT; ++j) vm[(g * W_CPT + j) * DP + r] = m[j];
+  for (int j = 0; j < WCPT<DP>; ++j) vm[(g * WCPT<DP> + j) * DP + r] = m[j];
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < W_CPT; ++j) {
+  for (int j = 0; j < WCPT<DP>; ++j) {
     Real s = p.b[r];
-    for (int k = 0; k < DP; ++k) s = fma(p.F[r * DP + k], vm[(g * W_CPT + j) * DP + k], s);
+    for (int k = 0; k < DP; ++k) s = fma(p.F[r * DP + k], vm[(g * WCPT<DP> + j) * DP + k], s);
     mp[j] = s;
   }
 }
@@ -522,51 +568,67 @@ __global__ void __launch_bounds__(WT) k_wmf_reduce(KP<Real> p, MeanArgs<Real> a)
   constexpr int CPC = Z::CPC;
   constexpr long DD = Z::DD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* v0 = reinterpret_cast<Real*>(smem_raw);
+  Real* sbuf = reinterpret_cast<Real*>(smem_raw);
+  Real* v0 = sbuf + Z::NBUF * DD;
   Real* v1 = v0 + CPC * DP;
   Real* v2 = v1 + CPC * DP;
   const int k = blockIdx.x % p.nb, grp = blockIdx.x / p.nb;
   const int r = threadIdx.x % DP, g = threadIdx.x / DP;
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const Real* TKt = a.tab + (long)TK * p.nT * DD;
-  int cidx[W_CPT];
-  bool valid[W_CPT];
+  auto src = [&](int j) -> const Real* { return s + j <= e ? TKt + (long)(s + j) * DD : nullptr; };
+  WStream<Real, DP> mq;
+  mq.begin(sbuf, src);
+  int cidx[WCPT<DP>];
+  bool valid[WCPT<DP>];
 #pragma unroll
-  for (int j = 0; j < W_CPT; ++j) {
-    cidx[j] = grp * CPC + g * W_CPT + j;
+  for (int j = 0; j < WCPT<DP>; ++j) {
+    cidx[j] = grp * CPC + g * WCPT<DP> + j;
     valid[j] = cidx[j] < p.C;
   }
   const bool lg = a.x && p.emis == AUX_EMIS_LINEAR_GAUSSIAN;
-  Real m[W_CPT];
+  Real m[WCPT<DP>];
 #pragma unroll
-  for (int j = 0; j < W_CPT; ++j) m[j] = (Real)0;
-  for (int t = s; t <= e; ++t) {
-    Real yti[W_CPT], xi[W_CPT], yv[W_CPT];
+  for (int j = 0; j < WCPT<DP>; ++j) m[j] = (Real)0;
+  // the thread's inputs of step t (x_t and y_t, or ytilde_t), fetched one step ahead
+  auto fetch_in = [&](int t, Real (&xa)[WCPT<DP>], Real (&ya)[WCPT<DP>]) {
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j) {
-      yti[j] = xi[j] = yv[j] = (Real)0;
-      if (valid[j] && r < p.d) {
+    for (int j = 0; j < WCPT<DP>; ++j) {
+      xa[j] = ya[j] = (Real)0;
+      if (t <= e && valid[j] && r < p.d) {
         const long ct = (long)cidx[j] * p.nT + t;
         if (a.x) {
-          xi[j] = a.x[ct * p.d + r];
-          yv[j] = p.y[(p.y_per_chain ? ct : (long)t) * p.d + r];
+          xa[j] = a.x[ct * p.d + r];
+          ya[j] = p.y[(p.y_per_chain ? ct : (long)t) * p.d + r];
         } else {
-          yti[j] = a.yt[ct * p.d + r];
+          ya[j] = a.yt[ct * p.d + r];
         }
       }
     }
+  };
+  Real xnx[WCPT<DP>], ynx[WCPT<DP>];
+  fetch_in(s, xnx, ynx);
+  for (int t = s; t <= e; ++t) {
+    Real yti[WCPT<DP>], xi[WCPT<DP>], yv[WCPT<DP>];
+#pragma unroll
+    for (int j = 0; j < WCPT<DP>; ++j) {
+      xi[j] = xnx[j];
+      yv[j] = a.x ? ynx[j] : (Real)0;
+      yti[j] = a.x ? (Real)0 : ynx[j];
+    }
+    fetch_in(t + 1, xnx, ynx);
     if (a.x) {
-      Real vi[W_CPT];
+      Real vi[WCPT<DP>];
       if (lg) {   // v = R_y^{-1} (y - x)
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < W_CPT; ++j) v1[(g * W_CPT + j) * DP + r] = (r < p.d) ? yv[j] - xi[j] : (Real)0;
+        for (int j = 0; j < WCPT<DP>; ++j) v1[(g * WCPT<DP> + j) * DP + r] = (r < p.d) ? yv[j] - xi[j] : (Real)0;
         __syncthreads();
         w_matvec<Real, DP>(p.Ryinv, v1, g, r, vi);
       }
       const bool obs = !p.mask || p.mask[t];
 #pragma unroll
-      for (int j = 0; j < W_CPT; ++j) {
+      for (int j = 0; j < WCPT<DP>; ++j) {
         if (!lg) vi[j] = (r < p.d) ? (Real)-0.5 + (Real)0.5 * yv[j] * yv[j] * exp(-xi[j]) : (Real)0;
         if (!obs) vi[j] = (Real)0;
         if (valid[j] && r < p.d) {
@@ -581,24 +643,24 @@ __global__ void __launch_bounds__(WT) k_wmf_reduce(KP<Real> p, MeanArgs<Real> a)
         }
       }
     }
-    Real mp[W_CPT];
+    Real mp[WCPT<DP>];
     if (t == 0) {
 #pragma unroll
-      for (int j = 0; j < W_CPT; ++j) mp[j] = p.m0[r];
+      for (int j = 0; j < WCPT<DP>; ++j) mp[j] = p.m0[r];
     } else {
       w_predict<Real, DP>(p, m, v2, g, r, mp);
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j) v0[(g * W_CPT + j) * DP + r] = (r < p.d) ? yti[j] - mp[j] : (Real)0;
-    __syncthreads();
-    Real kv[W_CPT];
-    w_matvec<Real, DP>(TKt + (long)t * DD, v0, g, r, kv);
+    for (int j = 0; j < WCPT<DP>; ++j) v0[(g * WCPT<DP> + j) * DP + r] = (r < p.d) ? yti[j] - mp[j] : (Real)0;
+    const Real* sK = mq.get(src);
+    Real kv[WCPT<DP>];
+    w_matvec<Real, DP>(sK, v0, g, r, kv);
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j) m[j] = (r < p.d) ? yti[j] - kv[j] : (Real)0;
+    for (int j = 0; j < WCPT<DP>; ++j) m[j] = (r < p.d) ? yti[j] - kv[j] : (Real)0;
   }
 #pragma unroll
-  for (int j = 0; j < W_CPT; ++j) {
+  for (int j = 0; j < WCPT<DP>; ++j) {
     if (valid[j]) a.z[((long)cidx[j] * p.nb + k) * DP + r] = m[j];
     if (valid[j] && a.x && k == 0 && r == 0) p.status_iter[cidx[j]] = *a.cov_status;
   }
@@ -611,10 +673,16 @@ __global__ void __launch_bounds__(DP) k_wmean_cross(KP<Real> p, const Real* __re
                                                     const Real* __restrict__ in, Real* __restrict__ out,
                                                     int backward) {
   constexpr long DD = WSz<Real, DP>::DD;
-  __shared__ Real vb[2][DP];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sbuf = reinterpret_cast<Real*>(smem_raw);
+  Real* vb = sbuf + WSz<Real, DP>::NBUF * DD;   // two vector slots
   const int c = blockIdx.x, r = threadIdx.x;
   const long cb = (long)c * p.nb;
   const int n = backward ? p.nb - 1 : max(0, p.nb - 2);
+  auto kk_of = [&](int j) { return backward ? p.nb - 1 - j : 1 + j; };
+  auto src = [&](int j) -> const Real* { return j < n ? matsT + (long)kk_of(j) * DD : nullptr; };
+  WStream<Real, DP> mq;
+  mq.begin(sbuf, src);
   Real m = (Real)0;
   if (backward) {
     out[(cb + p.nb - 1) * DP + r] = (Real)0;
@@ -623,14 +691,13 @@ __global__ void __launch_bounds__(DP) k_wmean_cross(KP<Real> p, const Real* __re
     if (p.nb > 1) out[(cb + 1) * DP + r] = m;
   }
   for (int j = 0; j < n; ++j) {
-    const int kk = backward ? p.nb - 1 - j : 1 + j;
-    Real* v = vb[j & 1];
+    const int kk = kk_of(j);
+    Real* v = vb + (j & 1) * DP;
     v[r] = m;
-    __syncthreads();
-    const Real* M = matsT + (long)kk * DD;
+    const Real* M = mq.get(src);
     Real sacc = in[(cb + kk) * DP + r];
-#pragma unroll 8
-    for (int q = 0; q < DP; ++q) sacc = fma(__ldg(M + (long)q * DP + r), v[q], sacc);
+#pragma unroll 16
+    for (int q = 0; q < DP; ++q) sacc = fma(M[q * DP + r], v[q], sacc);
     m = sacc;
     out[(cb + (backward ? kk - 1 : kk + 1)) * DP + r] = m;
   }
@@ -653,7 +720,8 @@ __global__ void __launch_bounds__(WT) k_wmf_apply(KP<Real> p, MeanArgs<Real> a) 
   constexpr int CPC = Z::CPC;
   constexpr long DD = Z::DD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* v0 = reinterpret_cast<Real*>(smem_raw);
+  Real* sbuf = reinterpret_cast<Real*>(smem_raw);
+  Real* v0 = sbuf + Z::NBUF * DD;
   Real* v1 = v0 + CPC * DP;
   Real* v2 = v1 + CPC * DP;
   double* red = reinterpret_cast<double*>(v2 + CPC * DP);
@@ -666,43 +734,65 @@ __global__ void __launch_bounds__(WT) k_wmf_apply(KP<Real> p, MeanArgs<Real> a) 
   const Real* TLt = a.tab + (long)TLS * ts;
   const Real* PF = a.tab + (long)TPF * ts;
   const bool epi = a.flags & APPLY_EPI;
+  // matrices in the order of use: per step K' (, G, chol(Sigma)^T); then G_{e-1} .. G_s
+  const int n = e - s + 1, per = epi ? 3 : 1, nfwd = n * per, ntot = nfwd + (epi ? n - 1 : 0);
+  auto src = [&](int i) -> const Real* {
+    if (i >= ntot) return nullptr;
+    if (i >= nfwd) return TGt + (long)(e - 1 - (i - nfwd)) * DD;
+    const long t = s + i / per;
+    const int w = i % per;
+    return (w == 0 ? TKt : (w == 1 ? TGt : TLt)) + t * DD;
+  };
+  WStream<Real, DP> mq;
+  mq.begin(sbuf, src);
   if (threadIdx.x < CPC) red[threadIdx.x] = 0.0;
-  int cidx[W_CPT];
-  bool valid[W_CPT];
-  Real mp[W_CPT];
-  double qacc[W_CPT];
+  int cidx[WCPT<DP>];
+  bool valid[WCPT<DP>];
+  Real mp[WCPT<DP>];
+  double qacc[WCPT<DP>];
 #pragma unroll
-  for (int j = 0; j < W_CPT; ++j) {
-    cidx[j] = grp * CPC + g * W_CPT + j;
+  for (int j = 0; j < WCPT<DP>; ++j) {
+    cidx[j] = grp * CPC + g * WCPT<DP> + j;
     valid[j] = cidx[j] < p.C;
     qacc[j] = 0.0;
   }
   if (k == 0) {
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j) mp[j] = p.m0[r];
+    for (int j = 0; j < WCPT<DP>; ++j) mp[j] = p.m0[r];
   } else {
-    Real ms[W_CPT];
+    Real ms[WCPT<DP>];
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j) ms[j] = valid[j] ? a.mstart[((long)cidx[j] * p.nb + k) * DP + r] : (Real)0;
+    for (int j = 0; j < WCPT<DP>; ++j) ms[j] = valid[j] ? a.mstart[((long)cidx[j] * p.nb + k) * DP + r] : (Real)0;
     w_predict<Real, DP>(p, ms, v2, g, r, mp);
   }
-  for (int t = s; t <= e; ++t) {
-    Real yti[W_CPT];
+  // the thread's ytilde_t and (given) eps_t, fetched one step ahead
+  auto fetch_in = [&](int t, Real (&ya)[WCPT<DP>], Real (&ea)[WCPT<DP>]) {
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j)
-      yti[j] = (valid[j] && r < p.d) ? a.yt[((long)cidx[j] * p.nT + t) * p.d + r] : (Real)0;
-    Real ej[W_CPT];
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < W_CPT; ++j) {
-      ej[j] = (r < p.d) ? yti[j] - mp[j] : (Real)0;
-      v0[(g * W_CPT + j) * DP + r] = ej[j];
+    for (int j = 0; j < WCPT<DP>; ++j) {
+      const bool ok = t <= e && valid[j] && r < p.d;
+      const long idx = ((long)cidx[j] * p.nT + t) * p.d + r;
+      ya[j] = ok ? a.yt[idx] : (Real)0;
+      ea[j] = (ok && epi && a.eps) ? a.eps[idx] : (Real)0;
     }
-    __syncthreads();
-    Real kv[W_CPT], m[W_CPT];
-    w_matvec<Real, DP>(TKt + (long)t * DD, v0, g, r, kv);
+  };
+  Real ynx[WCPT<DP>], enx[WCPT<DP>];
+  fetch_in(s, ynx, enx);
+  for (int t = s; t <= e; ++t) {
+    Real yti[WCPT<DP>], egv[WCPT<DP>];
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j) {
+    for (int j = 0; j < WCPT<DP>; ++j) { yti[j] = ynx[j]; egv[j] = enx[j]; }
+    fetch_in(t + 1, ynx, enx);
+    Real ej[WCPT<DP>];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < WCPT<DP>; ++j) {
+      ej[j] = (r < p.d) ? yti[j] - mp[j] : (Real)0;
+      v0[(g * WCPT<DP> + j) * DP + r] = ej[j];
+    }
+    Real kv[WCPT<DP>], m[WCPT<DP>];
+    w_matvec<Real, DP>(mq.get(src), v0, g, r, kv);
+#pragma unroll
+    for (int j = 0; j < WCPT<DP>; ++j) {
       qacc[j] += (double)ej[j] * (double)kv[j];
       m[j] = (r < p.d) ? yti[j] - kv[j] : (Real)0;
       const long ct = (long)cidx[j] * p.nT + t;
@@ -710,65 +800,72 @@ __global__ void __launch_bounds__(WT) k_wmf_apply(KP<Real> p, MeanArgs<Real> a) 
       if (valid[j] && a.Pf && r < p.d)
         for (int jj = 0; jj < p.d; ++jj) a.Pf[(ct * p.d + r) * p.d + jj] = PF[t * DD + (long)r * DP + jj];
     }
-    Real mpn[W_CPT];
+    Real mpn[WCPT<DP>];
     if (t < p.nT - 1) w_predict<Real, DP>(p, m, v2, g, r, mpn);
     else {
 #pragma unroll
-      for (int j = 0; j < W_CPT; ++j) mpn[j] = (Real)0;
+      for (int j = 0; j < WCPT<DP>; ++j) mpn[j] = (Real)0;
     }
     if (epi) {
       // U_t = m^f_t - G_t m^p_{t+1} + chol(Sigma_t) eps_t
       __syncthreads();
 #pragma unroll
-      for (int j = 0; j < W_CPT; ++j) {
+      for (int j = 0; j < WCPT<DP>; ++j) {
         Real ei = (Real)0;
         if (r < p.d && valid[j] && !(a.flags & APPLY_SMOOTH))
-          ei = a.eps ? a.eps[((long)cidx[j] * p.nT + t) * p.d + r]
+          ei = a.eps ? egv[j]
                      : philox_normal<Real>(p.seed, (uint32_t)cidx[j], iter_of(p, a.iter), PURPOSE_BACKWARD,
                                            (uint32_t)t, r);
-        v1[(g * W_CPT + j) * DP + r] = mpn[j];
-        v2[(g * W_CPT + j) * DP + r] = ei;
+        v1[(g * WCPT<DP> + j) * DP + r] = mpn[j];
+        v2[(g * WCPT<DP> + j) * DP + r] = ei;
       }
-      __syncthreads();
-      Real gm[W_CPT], ln[W_CPT];
-      w_matvec<Real, DP>(TGt + (long)t * DD, v1, g, r, gm);
-      w_matvec<Real, DP>(TLt + (long)t * DD, v2, g, r, ln);
+      Real gm[WCPT<DP>], ln[WCPT<DP>];
+      w_matvec<Real, DP>(mq.get(src), v1, g, r, gm);
+      w_matvec<Real, DP>(mq.get(src), v2, g, r, ln);
 #pragma unroll
-      for (int j = 0; j < W_CPT; ++j)
+      for (int j = 0; j < WCPT<DP>; ++j)
         if (valid[j]) a.U[((long)cidx[j] * p.nT + t) * DP + r] = m[j] - gm[j] + ln[j];
     }
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j) mp[j] = mpn[j];
+    for (int j = 0; j < WCPT<DP>; ++j) mp[j] = mpn[j];
   }
   if (epi) {
     // block aggregate sum_t (G_s ... G_{t-1}) U_t by Horner's rule from the block end
-    Real ub[W_CPT];
+    Real ub[WCPT<DP>];
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j) ub[j] = valid[j] ? a.U[((long)cidx[j] * p.nT + e) * DP + r] : (Real)0;
+    for (int j = 0; j < WCPT<DP>; ++j) ub[j] = valid[j] ? a.U[((long)cidx[j] * p.nT + e) * DP + r] : (Real)0;
+    Real un[WCPT<DP>];
+#pragma unroll
+    for (int j = 0; j < WCPT<DP>; ++j)
+      un[j] = (valid[j] && e - 1 >= s) ? a.U[((long)cidx[j] * p.nT + e - 1) * DP + r] : (Real)0;
     for (int t = e - 1; t >= s; --t) {
+      Real uc[WCPT<DP>];
+#pragma unroll
+      for (int j = 0; j < WCPT<DP>; ++j) {
+        uc[j] = un[j];
+        un[j] = (valid[j] && t - 1 >= s) ? a.U[((long)cidx[j] * p.nT + t - 1) * DP + r] : (Real)0;
+      }
       __syncthreads();
 #pragma unroll
-      for (int j = 0; j < W_CPT; ++j) v1[(g * W_CPT + j) * DP + r] = ub[j];
-      __syncthreads();
-      Real gu[W_CPT];
-      w_matvec<Real, DP>(TGt + (long)t * DD, v1, g, r, gu);
+      for (int j = 0; j < WCPT<DP>; ++j) v1[(g * WCPT<DP> + j) * DP + r] = ub[j];
+      Real gu[WCPT<DP>];
+      w_matvec<Real, DP>(mq.get(src), v1, g, r, gu);
 #pragma unroll
-      for (int j = 0; j < W_CPT; ++j)
-        ub[j] = gu[j] + (valid[j] ? a.U[((long)cidx[j] * p.nT + t) * DP + r] : (Real)0);
+      for (int j = 0; j < WCPT<DP>; ++j) ub[j] = gu[j] + uc[j];
     }
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j)
+    for (int j = 0; j < WCPT<DP>; ++j)
       if (valid[j]) a.guv[((long)cidx[j] * p.nb + k) * DP + r] = ub[j];
   }
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < W_CPT; ++j) w_rowsum<Real, DP>(red, g * W_CPT + j, qacc[j]);
+  for (int j = 0; j < WCPT<DP>; ++j) w_rowsum<Real, DP>(red, g * WCPT<DP> + j, qacc[j]);
   __syncthreads();
   if (r == 0) {
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j) {
+    for (int j = 0; j < WCPT<DP>; ++j) {
       if (!valid[j]) continue;
-      const double q = red[g * W_CPT + j] / (double)p.r;
+      const double q = red[g * WCPT<DP> + j] / (double)p.r;
       const int c = cidx[j];
       const long ck = (long)c * p.nb + k;
       if (a.flags & APPLY_STORE_Q) a.fqb[ck] = q;
@@ -791,57 +888,78 @@ __global__ void __launch_bounds__(WT) k_wmb_apply(KP<Real> p, BackArgs<Real> b, 
   constexpr int CPC = Z::CPC;
   constexpr long DD = Z::DD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* v0 = reinterpret_cast<Real*>(smem_raw);
+  Real* sbuf = reinterpret_cast<Real*>(smem_raw);
+  Real* v0 = sbuf + Z::NBUF * DD;
   Real* v1 = v0 + CPC * DP;
   double* red = reinterpret_cast<double*>(v1 + 2 * CPC * DP);
   const int k = blockIdx.x % p.nb, grp = blockIdx.x / p.nb;
   const int r = threadIdx.x % DP, g = threadIdx.x / DP;
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
+  auto src = [&](int j) -> const Real* { return e - j >= s ? b.G + (long)(e - j) * DD : nullptr; };
+  WStream<Real, DP> mq;
+  mq.begin(sbuf, src);
   const bool lg = b.mh && p.emis == AUX_EMIS_LINEAR_GAUSSIAN;
   if (threadIdx.x < CPC) red[threadIdx.x] = 0.0;
-  int cidx[W_CPT];
-  bool valid[W_CPT];
-  Real xi[W_CPT];
-  double acc[W_CPT];
+  int cidx[WCPT<DP>];
+  bool valid[WCPT<DP>];
+  Real xi[WCPT<DP>];
+  double acc[WCPT<DP>];
 #pragma unroll
-  for (int j = 0; j < W_CPT; ++j) {
-    cidx[j] = grp * CPC + g * W_CPT + j;
+  for (int j = 0; j < WCPT<DP>; ++j) {
+    cidx[j] = grp * CPC + g * WCPT<DP> + j;
     valid[j] = cidx[j] < p.C;
     xi[j] = valid[j] ? xnext[((long)cidx[j] * p.nb + k) * DP + r] : (Real)0;
     acc[j] = 0.0;
   }
+  // the thread's U_t and MH inputs (x_t, u_t, v_t, y_t) of step t, fetched one step ahead
+  constexpr int CPT = WCPT<DP>;
+  auto fetch_in = [&](int t, Real (&ua)[CPT], Real (&xa)[CPT], Real (&uia)[CPT], Real (&va)[CPT],
+                      Real (&ya)[CPT]) {
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      ua[j] = xa[j] = uia[j] = va[j] = ya[j] = (Real)0;
+      if (t < s || !valid[j]) continue;
+      const long ct = (long)cidx[j] * p.nT + t;
+      ua[j] = b.U[ct * DP + r];
+      if (b.mh && r < p.d) {
+        const long idx = ct * p.d + r;
+        xa[j] = b.x[idx]; uia[j] = b.u[idx]; va[j] = b.v[idx];
+        ya[j] = p.y[(p.y_per_chain ? ct : (long)t) * p.d + r];
+      }
+    }
+  };
+  Real un[CPT], xon[CPT], uin[CPT], vin[CPT], yin[CPT];
+  fetch_in(e, un, xon, uin, vin, yin);
   for (int t = e; t >= s; --t) {
+    Real uc[CPT], xoc[CPT], uic[CPT], vic[CPT], yic[CPT];
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) { uc[j] = un[j]; xoc[j] = xon[j]; uic[j] = uin[j]; vic[j] = vin[j]; yic[j] = yin[j]; }
+    fetch_in(t - 1, un, xon, uin, vin, yin);
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j) v0[(g * W_CPT + j) * DP + r] = xi[j];
-    __syncthreads();
-    Real gx[W_CPT];
-    w_matvec<Real, DP>(b.G + (long)t * DD, v0, g, r, gx);
+    for (int j = 0; j < WCPT<DP>; ++j) v0[(g * WCPT<DP> + j) * DP + r] = xi[j];
+    Real gx[WCPT<DP>];
+    w_matvec<Real, DP>(mq.get(src), v0, g, r, gx);
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j) {
-      xi[j] = gx[j] + (valid[j] ? b.U[((long)cidx[j] * p.nT + t) * DP + r] : (Real)0);
+    for (int j = 0; j < WCPT<DP>; ++j) {
+      xi[j] = gx[j] + uc[j];
       if (valid[j] && r < p.d) b.xs[((long)cidx[j] * p.nT + t) * p.d + r] = xi[j];
     }
     if (!b.mh) continue;
-    Real vsi[W_CPT];
+    Real vsi[WCPT<DP>];
     if (lg) {
       __syncthreads();
 #pragma unroll
-      for (int j = 0; j < W_CPT; ++j) {
-        const long ct = (long)cidx[j] * p.nT + t;
-        const Real yi = (valid[j] && r < p.d) ? p.y[(p.y_per_chain ? ct : (long)t) * p.d + r] : (Real)0;
-        v1[(g * W_CPT + j) * DP + r] = (r < p.d) ? yi - xi[j] : (Real)0;
-      }
+      for (int j = 0; j < WCPT<DP>; ++j) v1[(g * WCPT<DP> + j) * DP + r] = (r < p.d) ? yic[j] - xi[j] : (Real)0;
       __syncthreads();
       w_matvec<Real, DP>(p.Ryinv, v1, g, r, vsi);
     }
     const bool obs = !p.mask || p.mask[t];
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j) {
+    for (int j = 0; j < WCPT<DP>; ++j) {
       if (!valid[j] || r >= p.d) continue;
       const long ct = (long)cidx[j] * p.nT + t, idx = ct * p.d + r;
-      const Real xo = b.x[idx], ui = b.u[idx], vi = b.v[idx];
-      const Real yi = p.y[(p.y_per_chain ? ct : (long)t) * p.d + r];
+      const Real xo = xoc[j], ui = uic[j], vi = vic[j], yi = yic[j];
       const Real xs = xi[j];
       Real vs = lg ? vsi[j] : (Real)0, gdiff = (Real)0;
       if (obs) {
@@ -863,12 +981,12 @@ __global__ void __launch_bounds__(WT) k_wmb_apply(KP<Real> p, BackArgs<Real> b, 
   if (!b.mh) return;
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < W_CPT; ++j) w_rowsum<Real, DP>(red, g * W_CPT + j, acc[j]);
+  for (int j = 0; j < WCPT<DP>; ++j) w_rowsum<Real, DP>(red, g * WCPT<DP> + j, acc[j]);
   __syncthreads();
   if (r == 0) {
 #pragma unroll
-    for (int j = 0; j < W_CPT; ++j)
-      if (valid[j]) b.mh_part[(long)cidx[j] * p.nb + k] = red[g * W_CPT + j];
+    for (int j = 0; j < WCPT<DP>; ++j)
+      if (valid[j]) b.mh_part[(long)cidx[j] * p.nb + k] = red[g * WCPT<DP> + j];
   }
 }
 

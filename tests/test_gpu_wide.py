@@ -54,7 +54,7 @@ CASES = [
     (100, 70, 9, 16, "cached", False),
     (128, 129, 2, 32, "shared", False),
     (48, 40, 3, 6, "shared", True),
-    (128, 20, 2, 5, "cached", True),
+    (128, 20, 17, 5, "cached", True),
 ]
 
 
