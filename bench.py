@@ -64,6 +64,8 @@ def parse():
                     help="run only the lattice-model line (Section 4.2) and print it")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched multi-instance line and print it")
+    ap.add_argument("--wide-only", action="store_true",
+                    help="run only the d = 128, T = 4096 line (wide kernels) and print it")
     ap.add_argument("--cpu-sample-chains", type=int, default=0,
                     help="chain-steps in the CPU baseline sample (0 = 2 per core)")
     return ap.parse_args()
@@ -504,24 +506,115 @@ def run_spatial(args, flush, stream):
     return out
 
 
+def run_wide(args, flush, stream, peaks):
+    """The mixed-precision workload's shape (SV, d = 128, T = 4096, 16 chains) on the wide
+    table-mode kernels, single precision throughout (FP64 only in the log-determinants and
+    the likelihood sums): delta adapted on the device to 50 % acceptance during warm-up (the
+    covariance pass reruns at every adaptation step), then frozen; cached covariance tables;
+    the MH iteration captured in a CUDA graph and replayed, L2 flushed before each replay.
+    The shared mode (the covariance pass rerun every step) is timed beside it, eager."""
+    import numpy as np
+    import torch
+    from paper_2303_00301_gb300 import AuxKalman
+    from paper_2303_00301_gb300 import _binding as B
+    from paper_2303_00301_gb300 import workloads as W
+    d, T, C = 128, 4096, 16
+    wl = W.stochastic_volatility(d=d, T=T, n_chains=C)
+    h = AuxKalman(wl, dtype="f32", mode="cached")
+    x = torch.tensor(wl.x_init, dtype=torch.float32, device="cuda")
+    n_adapt = 150
+    h.adapt_delta(True, target=0.5, gain=1.0)
+    h.step(x, n_adapt, iter0=0)
+    h.adapt_delta(False)
+    delta = h.delta()
+    it = n_adapt
+    h.step(x, 3, iter0=it)
+    it += 3
+    acc = torch.zeros(C, dtype=torch.int32, device="cuda")
+    n = max(args.steps // 10, 30)
+    B.aux_set_profiling(h.handle, True)
+    for k in range(n):
+        flush.zero_()
+        h.step(x, 1, iter0=it + k, accept_count=acc)
+    torch.cuda.synchronize()
+    B.aux_set_profiling(h.handle, False)
+    prof = B.aux_read_profile(h.handle)
+    it += n
+    rate = acc.float().mean().item() / n
+    h.device_iteration(True, it)
+    g = h.capture(x, 1)
+    g.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for k in range(n):
+        flush.zero_()
+        ev[k][0].record(stream)
+        g.replay()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / n
+    h.device_iteration(False)
+    del g
+    rc = h.status()[0]
+    h.close()
+    # the shared mode: the covariance pass every step
+    ws = W.stochastic_volatility(d=d, T=T, n_chains=C, delta=delta)
+    hs = AuxKalman(ws, dtype="f32", mode="shared")
+    xs = torch.tensor(ws.x_init, dtype=torch.float32, device="cuda")
+    hs.step(xs, 2, iter0=0)
+    B.aux_set_profiling(hs.handle, True)
+    ns = 5
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ns)]
+    for k in range(ns):
+        flush.zero_()
+        evs[k][0].record(stream)
+        hs.step(xs, 1, iter0=2 + k)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    B.aux_set_profiling(hs.handle, False)
+    profs = B.aux_read_profile(hs.handle)
+    ms_sh = sum(a.elapsed_time(b) for a, b in evs) / ns
+    hs.close()
+    L = math.ceil(math.sqrt(T))
+    nb = (T + L - 1) // L
+    w = {"dtype": "f32"}
+    dom = max((k for k in prof if prof[k][1]), key=lambda k: prof[k][0])
+    line = roofline_line("cached", dom, prof, w, d, T, C, nb, T, True, 4, peaks, n,
+                         "dominant kernel (cached tables, per-chain means)")
+    if line:
+        line["kernel"] = {"reduce": "k_wmf_reduce", "apply": "k_wmf_apply", "scan": "k_wmean_cross",
+                          "backward": "k_wmean_cross + k_wmb_apply"}.get(dom, dom)
+        line["traffic"] = dram_traffic(line["kernel"])
+    return {"workload": f"sv_d{d}_T{T}_C{C} (SV, d = 128, T = 4096, 16 chains)",
+            "precision": "FP32 tables and means; FP64 log-determinants and likelihood sums",
+            "mode": "cached", "launch": "CUDA graph replay", "ms_per_step": ms,
+            "value": C * T / (ms / 1e3), "unit": UNIT, "delta": delta, "delta_adaptation_steps": n_adapt,
+            "accept_rate": rate, "status": int(rc), "steps": n,
+            "kernel_ms_per_step": {k: v[0] / n for k, v in prof.items() if v[1]},
+            "roofline": line,
+            "shared_mode": {"ms_per_step": ms_sh, "value": C * T / (ms_sh / 1e3), "launch": "eager",
+                            "kernel_ms_per_step": {k: v[0] / ns for k, v in profs.items() if v[1]}}}
+
+
 def run_batched(args, flush, stream, n_streams=32):
     """A batch of independent SV instances, one chain each, in the manner of a batched
-    multi-instance workload: T_k ~ U{128..4096}, d_k cycling through 8, 16 and 32 (the
-    p <= 32 part; d = 64 needs p > 32), per-instance phi, data and seeds, cached covariance
-    tables, delta_k = 0.0183 (30 * 1024 / (d_k T_k))^(1/2) (the d = 30, T = 1024 value
-    scaled by the pseudo-observation precision per state). One step = one MH iteration of
-    every instance; the instances' steps are captured in one CUDA graph on 32 streams
-    (independent branches; 4 / 16 / 32 / 64 measured 9.8 / 4.1 / 3.9 / 3.9 ms per step)
-    and replayed, L2 flushed before each replay."""
+    multi-instance workload: 256 instances, T_k ~ U{128..4096}, d_k cycling through 8, 16,
+    32 and 64 (the last on the wide kernels), per-instance phi, data and seeds, cached
+    covariance tables, delta_k = 0.0183 (30 * 1024 / (d_k T_k))^(1/2) (the d = 30,
+    T = 1024 value scaled by the pseudo-observation precision per state). One step = one
+    MH iteration of every instance; the instances' steps are captured in one CUDA graph on
+    32 streams (independent branches; for the 192 instances with d <= 32, 4 / 16 / 32 / 64
+    streams measured 9.8 / 4.1 / 3.9 / 3.9 ms per step) and replayed, L2 flushed before
+    each replay. The d <= 32 subset is timed the same way beside it."""
     import numpy as np
     import torch
     from paper_2303_00301_gb300 import AuxKalman
     from paper_2303_00301_gb300 import workloads as W
     rng = np.random.default_rng(3)
-    n_inst, dims = 192, (8, 16, 32)
+    n_inst, dims = 256, (8, 16, 32, 64)
     inst = []
     for k in range(n_inst):
-        d = dims[k % 3]
+        d = dims[k % 4]
         T = int(rng.integers(128, 4097))
         delta = 0.0183 * math.sqrt(30 * 1024 / (d * T))
         wl = W.stochastic_volatility(d=d, T=T, n_chains=1, sim_seed=100 + k, mcmc_seed=1000 + k, delta=delta)
@@ -536,41 +629,50 @@ def run_batched(args, flush, stream, n_streams=32):
     for h, x, acc, T, d in inst:
         h.device_iteration(True, 3)
     streams = [torch.cuda.Stream() for _ in range(n_streams)]
-    g = torch.cuda.CUDAGraph()
-    cap = torch.cuda.Stream()
-    cap.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.graph(g, stream=cap):
-        for st in streams:
-            st.wait_stream(cap)
-        for i, (h, x, acc, T, d) in enumerate(inst):
-            with torch.cuda.stream(streams[i % n_streams]):
-                h.step(x, 1, 0, accept_count=acc)
-        for st in streams:
-            cap.wait_stream(st)
-    torch.cuda.current_stream().wait_stream(cap)
-    g.replay()
-    torch.cuda.synchronize()
-    for h, x, acc, T, d in inst:
-        acc.zero_()
-    n = max(args.steps // 10, 20)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
-    for k in range(n):
-        flush.zero_()
-        ev[k][0].record(stream)
+
+    def time_subset(sub):
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream()
+        cap.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(g, stream=cap):
+            for st in streams:
+                st.wait_stream(cap)
+            for i, (h, x, acc, T, d) in enumerate(sub):
+                with torch.cuda.stream(streams[i % n_streams]):
+                    h.step(x, 1, 0, accept_count=acc)
+            for st in streams:
+                cap.wait_stream(st)
+        torch.cuda.current_stream().wait_stream(cap)
         g.replay()
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / n
-    steps_total = sum(T for _, _, _, T, _ in inst)
-    rate = sum(acc.item() for _, _, acc, _, _ in inst) / (n * n_inst)
+        torch.cuda.synchronize()
+        for h, x, acc, T, d in sub:
+            acc.zero_()
+        n = max(args.steps // 10, 20)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for k in range(n):
+            flush.zero_()
+            ev[k][0].record(stream)
+            g.replay()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / n
+        steps_total = sum(T for _, _, _, T, _ in sub)
+        rate = sum(acc.item() for _, _, acc, _, _ in sub) / (n * len(sub))
+        del g
+        return {"instances": len(sub), "timesteps_per_step": steps_total, "ms_per_step": ms,
+                "value": steps_total / (ms / 1e3), "accept_rate": rate, "steps": n}
+
+    full = time_subset(inst)
+    narrow = time_subset([q for q in inst if q[4] <= 32])
     rc = max(h.status()[0] for h, _, _, _, _ in inst)
     for h, _, _, _, _ in inst:
         h.close()
-    del g
-    return {"workload": f"{n_inst} SV instances, one chain each, T ~ U{{128..4096}}, d in {list(dims)}",
-            "timesteps_per_step": steps_total, "ms_per_step": ms, "value": steps_total / (ms / 1e3),
-            "unit": UNIT, "mode": "cached", "launch": f"one CUDA graph, {n_streams} stream branches",
-            "accept_rate": rate, "status": int(rc), "steps": n}
+    out = {"workload": f"{n_inst} SV instances, one chain each, T ~ U{{128..4096}}, d in {list(dims)}",
+           "unit": UNIT, "mode": "cached", "launch": f"one CUDA graph, {n_streams} stream branches",
+           "status": int(rc)}
+    out.update(full)
+    out["d_le_32_subset"] = narrow
+    return out
 
 
 def run_ours(args):
@@ -732,9 +834,12 @@ def run_ours(args):
 
     spatial = None
     batched = None
+    wide = None
     if not args.headline_only and rank == 0:
         spatial = run_spatial(args, flush, stream)
         batched = run_batched(args, flush, stream)
+        pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        wide = run_wide(args, flush, stream, json.load(open(pk)) if os.path.exists(pk) else {})
 
     # end to end through the public API from pinned host buffers
     x_host = torch.tensor(wl.x_init, dtype=tdt).pin_memory()
@@ -877,7 +982,7 @@ def run_ours(args):
                 "ms_per_step_eager_profiled": head["ms_per_step_eager_profiled"],
                 "accept_rate": accept_rate, "status": int(rc),
                 "step_ms_median": head["step_ms_median"], "other_modes": others,
-                "spatio_temporal": spatial, "batched_instances": batched}
+                "spatio_temporal": spatial, "batched_instances": batched, "wide_d128": wide}
         print(json.dumps(line), flush=True)
     s.close()
     if world > 1:
@@ -892,6 +997,15 @@ def main():
         build.build()
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         print(json.dumps(run_spatial(args, flush, torch.cuda.current_stream())), flush=True)
+        return
+    if args.wide_only:
+        import torch
+        from paper_2303_00301_gb300 import build
+        build.build()
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        peaks = json.load(open(pp)) if os.path.exists(pp) else {}
+        print(json.dumps(run_wide(args, flush, torch.cuda.current_stream(), peaks)), flush=True)
         return
     if args.batched_only:
         import torch

@@ -77,18 +77,26 @@ struct WOps {
     return a;
   }
 
-  static int mean_grid(const aux_model* m) { return m->nb * ((m->C + Z::CPC - 1) / Z::CPC); }
+  // row groups of a means CTA: as many as the chains need (one chain per instance uses one)
+  static int mean_threads(const aux_model* m) {
+    const int groups = (m->C + WCPT<DP> - 1) / WCPT<DP>;
+    return DP * std::min(Z::NRG, groups);
+  }
+  static int mean_grid(const aux_model* m) {
+    const int cpc = mean_threads(m) / DP * WCPT<DP>;
+    return m->nb * ((m->C + cpc - 1) / cpc);
+  }
 
   static void means_filter(aux_model* m, const KP<Real>& p, MeanArgs<Real> a, cudaStream_t st) {
     const int grid = mean_grid(m);
     { ProfScope ps(m, PK_REDUCE, st);
-      k_wmf_reduce<Real, DP><<<grid, WT, Z::MSMEM, st>>>(p, a); }
+      k_wmf_reduce<Real, DP><<<grid, mean_threads(m), Z::MSMEM, st>>>(p, a); }
     a.x = nullptr;
     { ProfScope ps(m, PK_SCAN, st);
       k_wmean_cross<Real, DP><<<m->C, DP, Z::XSMEM, st>>>(p, (const Real*)m->btab, a.z, (Real*)m->ms, 0); }
     a.mstart = (const Real*)m->ms;
     { ProfScope ps(m, PK_APPLY, st);
-      k_wmf_apply<Real, DP><<<grid, WT, Z::MSMEM, st>>>(p, a); }
+      k_wmf_apply<Real, DP><<<grid, mean_threads(m), Z::MSMEM, st>>>(p, a); }
   }
 
   static BackArgs<Real> back_args(aux_model* m) {
@@ -104,7 +112,7 @@ struct WOps {
     ProfScope ps(m, PK_BACKWARD, st, 2);
     Real* xnext = (Real*)m->zb;
     k_wmean_cross<Real, DP><<<m->C, DP, Z::XSMEM, st>>>(p, b.gum, b.guv, xnext, 1);
-    k_wmb_apply<Real, DP><<<mean_grid(m), WT, Z::MSMEM, st>>>(p, b, (const Real*)xnext);
+    k_wmb_apply<Real, DP><<<mean_grid(m), mean_threads(m), Z::MSMEM, st>>>(p, b, (const Real*)xnext);
   }
 
   static void mh_commit(aux_model* m, const KP<Real>& p, Real* x, uint64_t iter, uint32_t* acc,

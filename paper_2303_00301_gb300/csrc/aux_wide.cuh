@@ -484,8 +484,9 @@ __global__ void __launch_bounds__(WT, 2) k_w_prod(KP<Real> p, WCovArgs<Real> a) 
 }
 
 // ---------------------------------------------------------------------------
-// Means. CTA (k, grp): block k, chains grp * CPC + g * WCPT<DP> + j (thread row
-// r = tid % DP, row group g = tid / DP, j < WCPT<DP>). vs: three vector slots
+// Means. CTA (k, grp): block k, chains grp * cpc + g * WCPT<DP> + j (thread row
+// r = tid % DP, row group g = tid / DP, j < WCPT<DP>; cpc = WCPT<DP> * blockDim.x / DP,
+// the CTA has as many row groups as its chains need, at most WT / DP). vs: three vector slots
 // per chain slot, [3][CPC][DP].
 // ---------------------------------------------------------------------------
 // out[j] = sum_k Mt[k][r] v[slot(j)][k] (Mt: the transposed matrix, in shared or
@@ -565,7 +566,8 @@ template <typename Real, int DP>
 __global__ void __launch_bounds__(WT) k_wmf_reduce(KP<Real> p, MeanArgs<Real> a) {
   refresh_delta(p);
   using Z = WSz<Real, DP>;
-  constexpr int CPC = Z::CPC;
+  constexpr int CPC = Z::CPC;   // shared-memory layout (the largest CTA)
+  const int cpc = (int)(blockDim.x / DP) * WCPT<DP>;   // chains of this CTA
   constexpr long DD = Z::DD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sbuf = reinterpret_cast<Real*>(smem_raw);
@@ -583,7 +585,7 @@ __global__ void __launch_bounds__(WT) k_wmf_reduce(KP<Real> p, MeanArgs<Real> a)
   bool valid[WCPT<DP>];
 #pragma unroll
   for (int j = 0; j < WCPT<DP>; ++j) {
-    cidx[j] = grp * CPC + g * WCPT<DP> + j;
+    cidx[j] = grp * cpc + g * WCPT<DP> + j;
     valid[j] = cidx[j] < p.C;
   }
   const bool lg = a.x && p.emis == AUX_EMIS_LINEAR_GAUSSIAN;
@@ -717,7 +719,8 @@ template <typename Real, int DP>
 __global__ void __launch_bounds__(WT) k_wmf_apply(KP<Real> p, MeanArgs<Real> a) {
   refresh_delta(p);
   using Z = WSz<Real, DP>;
-  constexpr int CPC = Z::CPC;
+  constexpr int CPC = Z::CPC;   // shared-memory layout (the largest CTA)
+  const int cpc = (int)(blockDim.x / DP) * WCPT<DP>;   // chains of this CTA
   constexpr long DD = Z::DD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sbuf = reinterpret_cast<Real*>(smem_raw);
@@ -752,7 +755,7 @@ __global__ void __launch_bounds__(WT) k_wmf_apply(KP<Real> p, MeanArgs<Real> a) 
   double qacc[WCPT<DP>];
 #pragma unroll
   for (int j = 0; j < WCPT<DP>; ++j) {
-    cidx[j] = grp * CPC + g * WCPT<DP> + j;
+    cidx[j] = grp * cpc + g * WCPT<DP> + j;
     valid[j] = cidx[j] < p.C;
     qacc[j] = 0.0;
   }
@@ -885,7 +888,8 @@ template <typename Real, int DP>
 __global__ void __launch_bounds__(WT) k_wmb_apply(KP<Real> p, BackArgs<Real> b, const Real* __restrict__ xnext) {
   refresh_delta(p);
   using Z = WSz<Real, DP>;
-  constexpr int CPC = Z::CPC;
+  constexpr int CPC = Z::CPC;   // shared-memory layout (the largest CTA)
+  const int cpc = (int)(blockDim.x / DP) * WCPT<DP>;   // chains of this CTA
   constexpr long DD = Z::DD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sbuf = reinterpret_cast<Real*>(smem_raw);
@@ -906,7 +910,7 @@ __global__ void __launch_bounds__(WT) k_wmb_apply(KP<Real> p, BackArgs<Real> b, 
   double acc[WCPT<DP>];
 #pragma unroll
   for (int j = 0; j < WCPT<DP>; ++j) {
-    cidx[j] = grp * CPC + g * WCPT<DP> + j;
+    cidx[j] = grp * cpc + g * WCPT<DP> + j;
     valid[j] = cidx[j] < p.C;
     xi[j] = valid[j] ? xnext[((long)cidx[j] * p.nb + k) * DP + r] : (Real)0;
     acc[j] = 0.0;
