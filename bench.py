@@ -65,7 +65,11 @@ def parse():
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched multi-instance line and print it")
     ap.add_argument("--wide-only", action="store_true",
-                    help="run only the d = 128, T = 4096 line (wide kernels) and print it")
+                    help="run only the d = 128 line (wide kernels) and print it")
+    ap.add_argument("--wide-T", type=int, default=4096, help="T of the d = 128 line")
+    ap.add_argument("--wide-L", type=int, default=0, help="block length of the d = 128 line (0: default)")
+    ap.add_argument("--wide-adapt", type=int, default=150,
+                    help="delta adaptation steps before the d = 128 line is timed (0: the workload's delta)")
     ap.add_argument("--cpu-sample-chains", type=int, default=0,
                     help="chain-steps in the CPU baseline sample (0 = 2 per core)")
     return ap.parse_args()
@@ -518,14 +522,15 @@ def run_wide(args, flush, stream, peaks):
     from paper_2303_00301_gb300 import AuxKalman
     from paper_2303_00301_gb300 import _binding as B
     from paper_2303_00301_gb300 import workloads as W
-    d, T, C = 128, 4096, 16
+    d, T, C = 128, args.wide_T, 16
     wl = W.stochastic_volatility(d=d, T=T, n_chains=C)
-    h = AuxKalman(wl, dtype="f32", mode="cached")
+    h = AuxKalman(wl, dtype="f32", mode="cached", block_len=args.wide_L)
     x = torch.tensor(wl.x_init, dtype=torch.float32, device="cuda")
-    n_adapt = 150
-    h.adapt_delta(True, target=0.5, gain=1.0)
-    h.step(x, n_adapt, iter0=0)
-    h.adapt_delta(False)
+    n_adapt = args.wide_adapt
+    if n_adapt > 0:
+        h.adapt_delta(True, target=0.5, gain=1.0)
+        h.step(x, n_adapt, iter0=0)
+        h.adapt_delta(False)
     delta = h.delta()
     it = n_adapt
     h.step(x, 3, iter0=it)
@@ -559,7 +564,7 @@ def run_wide(args, flush, stream, peaks):
     h.close()
     # the shared mode: the covariance pass every step
     ws = W.stochastic_volatility(d=d, T=T, n_chains=C, delta=delta)
-    hs = AuxKalman(ws, dtype="f32", mode="shared")
+    hs = AuxKalman(ws, dtype="f32", mode="shared", block_len=args.wide_L)
     xs = torch.tensor(ws.x_init, dtype=torch.float32, device="cuda")
     hs.step(xs, 2, iter0=0)
     B.aux_set_profiling(hs.handle, True)
@@ -575,7 +580,7 @@ def run_wide(args, flush, stream, peaks):
     profs = B.aux_read_profile(hs.handle)
     ms_sh = sum(a.elapsed_time(b) for a, b in evs) / ns
     hs.close()
-    L = math.ceil(math.sqrt(T))
+    L = args.wide_L or math.ceil(math.sqrt(T))
     nb = (T + L - 1) // L
     w = {"dtype": "f32"}
     dom = max((k for k in prof if prof[k][1]), key=lambda k: prof[k][0])
@@ -584,10 +589,10 @@ def run_wide(args, flush, stream, peaks):
     if line:
         line["kernel"] = {"reduce": "k_wmf_reduce", "apply": "k_wmf_apply", "scan": "k_wmean_cross",
                           "backward": "k_wmean_cross + k_wmb_apply"}.get(dom, dom)
-        line["traffic"] = dram_traffic(line["kernel"])
-    return {"workload": f"sv_d{d}_T{T}_C{C} (SV, d = 128, T = 4096, 16 chains)",
+        line["traffic"] = dram_traffic(f"{line['kernel']}@sv_d{d}_T{T}_C{C}")
+    return {"workload": f"sv_d{d}_T{T}_C{C} (SV, d = {d}, T = {T}, {C} chains)",
             "precision": "FP32 tables and means; FP64 log-determinants and likelihood sums",
-            "mode": "cached", "launch": "CUDA graph replay", "ms_per_step": ms,
+            "mode": "cached", "block_len": L, "launch": "CUDA graph replay", "ms_per_step": ms,
             "value": C * T / (ms / 1e3), "unit": UNIT, "delta": delta, "delta_adaptation_steps": n_adapt,
             "accept_rate": rate, "status": int(rc), "steps": n,
             "kernel_ms_per_step": {k: v[0] / n for k, v in prof.items() if v[1]},
