@@ -100,6 +100,26 @@ def test_replay_with_the_square_root_filter():
     assert torch.equal(xa, xb) and torch.equal(aa, ab) and torch.equal(la, lb)
 
 
+@pytest.mark.parametrize("mode", ["shared", "cached"])
+def test_replay_with_square_root_tables(mode):
+    wl = workloads.stochastic_volatility(d=6, T=45, n_chains=3, delta=0.05)
+    (xe, ae, le, _, _), (xg, ag, lg, _, it) = _eager_and_replayed(wl, "f32", 8, mode=mode,
+                                                                   filter_form="square_root")
+    assert torch.equal(xe, xg) and torch.equal(ae, ag) and torch.equal(le, lg) and it == 10
+
+
+@pytest.mark.parametrize("mode", ["shared", "cached"])
+def test_replay_on_the_wide_kernels(mode):
+    """d = 40 (padded to 64) and d = 72 (to 128). The wide kernels add the warps'
+    FP64 partial sums of the likelihood and MH terms with shared-memory atomics, in
+    no fixed order, so log alpha agrees to rounding; paths and decisions are equal."""
+    for d in (40, 72):
+        wl = workloads.stochastic_volatility(d=d, T=30, n_chains=3, delta=0.02)
+        (xe, ae, le, _, _), (xg, ag, lg, _, it) = _eager_and_replayed(wl, "f32", 6, mode=mode)
+        assert torch.equal(xe, xg) and torch.equal(ae, ag) and it == 10
+        assert torch.allclose(le, lg, rtol=0, atol=1e-9)
+
+
 def test_counter_can_be_reset_and_disabled():
     wl = workloads.stochastic_volatility(d=3, T=16, n_chains=2, delta=0.05)
     s = AuxKalman(wl, dtype="f64", block_len=4)
