@@ -61,7 +61,8 @@ template <typename Real, int DP> struct WSz {
   // matrix staging buffers of the means kernels (one copy in flight while one is read)
   static constexpr int NBUF = 2;
   // means: NBUF matrix staging buffers, three vector slots per chain, per-chain FP64 sums
-  static constexpr size_t MSMEM = (size_t)(NBUF * DD + 3 * CPC * DP) * sizeof(Real) + 2 * CPC * sizeof(double);
+  static constexpr int WPG = DP / 32;   // warps per row group
+  static constexpr size_t MSMEM = (size_t)(NBUF * DD + 3 * CPC * DP) * sizeof(Real) + (size_t)CPC * WPG * sizeof(double);
   // composition over the blocks: the staging buffers, two vector slots
   static constexpr size_t XSMEM = (size_t)(NBUF * DD + 2 * DP) * sizeof(Real);
 };
@@ -493,13 +494,22 @@ __global__ void __launch_bounds__(WT, 2) k_w_prod(KP<Real> p, WCovArgs<Real> a) 
 // global memory, so that the threads of a warp read consecutive entries)
 template <typename Real, int DP>
 __device__ __forceinline__ void w_matvec(const Real* Mt, const Real* v, int g, int r, Real (&out)[WCPT<DP>]) {
+  using V = typename Vec16<Real>::V;
+  constexpr int N = Vec16<Real>::N;   // k per 16-byte word of a chain vector
 #pragma unroll
   for (int j = 0; j < WCPT<DP>; ++j) out[j] = (Real)0;
-#pragma unroll 16
-  for (int k = 0; k < DP; ++k) {
-    const Real m = Mt[k * DP + r];
+#pragma unroll 4
+  for (int k = 0; k < DP; k += N) {
+    Real m[N];
 #pragma unroll
-    for (int j = 0; j < WCPT<DP>; ++j) out[j] = fma(m, v[(g * WCPT<DP> + j) * DP + k], out[j]);
+    for (int q = 0; q < N; ++q) m[q] = Mt[(k + q) * DP + r];
+#pragma unroll
+    for (int j = 0; j < WCPT<DP>; ++j) {
+      Real vv[N];
+      unpack<Real>(*reinterpret_cast<const V*>(v + (g * WCPT<DP> + j) * DP + k), vv);
+#pragma unroll
+      for (int q = 0; q < N; ++q) out[j] = fma(m[q], vv[q], out[j]);
+    }
   }
 }
 
@@ -705,12 +715,20 @@ __global__ void __launch_bounds__(DP) k_wmean_cross(KP<Real> p, const Real* __re
   }
 }
 
-// sum over the rows of the CTA's chain slots into red[CPC] (FP64), then
-// the chain slot's value is red[slot] after the barrier
+// sum over the rows of a chain slot (FP64): each warp of the row group stores its
+// partial in red[slot][warp]; after a barrier w_rowsum_get adds them in warp order,
+// so the result does not depend on the warps' timing
 template <typename Real, int DP>
 __device__ __forceinline__ void w_rowsum(double* red, int slot, double v) {
   v = warp_sum<double>(v);
-  if ((threadIdx.x & 31) == 0) atomicAdd(&red[slot], v);
+  if ((threadIdx.x & 31) == 0) red[slot * (DP / 32) + (threadIdx.x % DP) / 32] = v;
+}
+template <int DP>
+__device__ __forceinline__ double w_rowsum_get(const double* red, int slot) {
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < DP / 32; ++w) s += red[slot * (DP / 32) + w];
+  return s;
 }
 
 // filtering means from the true block start, likelihood terms, and (APPLY_EPI) the
@@ -748,7 +766,6 @@ __global__ void __launch_bounds__(WT) k_wmf_apply(KP<Real> p, MeanArgs<Real> a) 
   };
   WStream<Real, DP> mq;
   mq.begin(sbuf, src);
-  if (threadIdx.x < CPC) red[threadIdx.x] = 0.0;
   int cidx[WCPT<DP>];
   bool valid[WCPT<DP>];
   Real mp[WCPT<DP>];
@@ -868,7 +885,7 @@ __global__ void __launch_bounds__(WT) k_wmf_apply(KP<Real> p, MeanArgs<Real> a) 
 #pragma unroll
     for (int j = 0; j < WCPT<DP>; ++j) {
       if (!valid[j]) continue;
-      const double q = red[g * WCPT<DP> + j] / (double)p.r;
+      const double q = w_rowsum_get<DP>(red, g * WCPT<DP> + j) / (double)p.r;
       const int c = cidx[j];
       const long ck = (long)c * p.nb + k;
       if (a.flags & APPLY_STORE_Q) a.fqb[ck] = q;
@@ -903,7 +920,6 @@ __global__ void __launch_bounds__(WT) k_wmb_apply(KP<Real> p, BackArgs<Real> b, 
   WStream<Real, DP> mq;
   mq.begin(sbuf, src);
   const bool lg = b.mh && p.emis == AUX_EMIS_LINEAR_GAUSSIAN;
-  if (threadIdx.x < CPC) red[threadIdx.x] = 0.0;
   int cidx[WCPT<DP>];
   bool valid[WCPT<DP>];
   Real xi[WCPT<DP>];
@@ -990,7 +1006,7 @@ __global__ void __launch_bounds__(WT) k_wmb_apply(KP<Real> p, BackArgs<Real> b, 
   if (r == 0) {
 #pragma unroll
     for (int j = 0; j < WCPT<DP>; ++j)
-      if (valid[j]) b.mh_part[(long)cidx[j] * p.nb + k] = red[g * WCPT<DP> + j];
+      if (valid[j]) b.mh_part[(long)cidx[j] * p.nb + k] = w_rowsum_get<DP>(red, g * WCPT<DP> + j);
   }
 }
 

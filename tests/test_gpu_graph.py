@@ -110,14 +110,12 @@ def test_replay_with_square_root_tables(mode):
 
 @pytest.mark.parametrize("mode", ["shared", "cached"])
 def test_replay_on_the_wide_kernels(mode):
-    """d = 40 (padded to 64) and d = 72 (to 128). The wide kernels add the warps'
-    FP64 partial sums of the likelihood and MH terms with shared-memory atomics, in
-    no fixed order, so log alpha agrees to rounding; paths and decisions are equal."""
-    for d in (40, 72):
+    """d = 40 (padded to 64) and d = 72 (to 128), with and without delta adaptation."""
+    for d, adapt in ((40, False), (72, True)):
         wl = workloads.stochastic_volatility(d=d, T=30, n_chains=3, delta=0.02)
-        (xe, ae, le, _, _), (xg, ag, lg, _, it) = _eager_and_replayed(wl, "f32", 6, mode=mode)
-        assert torch.equal(xe, xg) and torch.equal(ae, ag) and it == 10
-        assert torch.allclose(le, lg, rtol=0, atol=1e-9)
+        (xe, ae, le, de, _), (xg, ag, lg, dg, it) = _eager_and_replayed(wl, "f32", 6, mode=mode, adapt=adapt)
+        assert torch.equal(xe, xg) and torch.equal(ae, ag) and torch.equal(le, lg) and it == 10
+        assert de == dg
 
 
 def test_counter_can_be_reset_and_disabled():
