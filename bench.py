@@ -339,8 +339,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")):
-            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        out_dir = os.environ.get("AUX_BENCH_CLOCK_DIR")   # keep the raw samples there when set
+        if out_dir and os.path.isdir(out_dir):
+            self.path = os.path.join(out_dir, f"clocks_rank{gpu_index}.csv")
         else:
             import tempfile
             fd, self.path = tempfile.mkstemp(suffix=".csv", prefix="clocks_")

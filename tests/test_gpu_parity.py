@@ -3,9 +3,9 @@
 Tolerances (relative errors are normwise over each chain's whole array):
   FP64 path: 1e-9 on means, covariances, paths and log Z; 1e-8 absolute on log alpha.
   FP32 path: 1e-4 on filtering means/covariances and sampled paths, 1e-5 on log Z
-  (the stated accuracy targets); log alpha within TOL_LA32 absolute, derived in
-  the design doc from FP32 rounding of T*d per-element terms; MH decisions must agree
-  except where |log alpha_oracle - log U| < TOL_LA32.
+  (the stated accuracy targets); log alpha within TOL_LA32 absolute, a bound on
+  the FP32 rounding of the T*d per-element terms summed into it; MH decisions must
+  agree except where |log alpha_oracle - log U| < TOL_LA32.
 """
 import numpy as np
 import pytest
