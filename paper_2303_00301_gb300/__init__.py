@@ -29,8 +29,10 @@ class AuxKalman:
     per-chain mode only). ``sampler`` draws the path from the smoothing law
     (``aux_set_sampler``): "scan" ((G, U) suffix scan) or "bridging"
     (divide-and-conquer tree of bridging conditionals). ``filter_form``
-    (``aux_set_filter_form``): "covariance" or "square_root" (per-chain
-    ``loglik`` only).
+    (``aux_set_filter_form``): "covariance" or "square_root" (per chain with
+    the first-order proposal and the scan sampler, or the covariance pass of
+    the table modes). State dimensions 33..128 (FP32) run the table modes only
+    ("shared" or "cached"), first order, scan sampler, covariance form.
     """
 
     def __init__(self, workload, dtype="f32", seed=None, n_chains=None, block_len=0, stream=None,
