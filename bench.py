@@ -37,7 +37,29 @@ WORKLOADS = {
     "lg_d2_T64": dict(kind="lg", d=2, T=64, C=1, dtype="f64"),
 }
 FP32_LANES_PER_SM = 128
-N_SM = 152
+_DEVICE_CAPS = {}
+
+
+def device_caps(peaks):
+    """(multiprocessor count, maximum SM clock in MHz, where the clock came from) of
+    the current device: the SM count from the device properties, the clock from
+    nvidia-smi's clocks.max.sm, else the measured peaks file."""
+    if not _DEVICE_CAPS:
+        import torch
+        dev = torch.cuda.current_device()
+        _DEVICE_CAPS["n_sm"] = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz, src = None, None
+        try:
+            out = subprocess.run(["nvidia-smi", "-i", str(dev), "--query-gpu=clocks.max.sm",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                 timeout=20).stdout.strip()
+            mhz, src = float(out.splitlines()[0]), "nvidia-smi clocks.max.sm"
+        except Exception:
+            pass
+        if mhz is None:
+            mhz, src = float(peaks.get("sm_max_mhz", 2070.0)), "MEASURED_PEAKS.json sm_max_mhz"
+        _DEVICE_CAPS["sm_max_mhz"], _DEVICE_CAPS["clock_source"] = mhz, src
+    return _DEVICE_CAPS["n_sm"], _DEVICE_CAPS["sm_max_mhz"], _DEVICE_CAPS["clock_source"]
 
 
 def parse():
@@ -282,7 +304,6 @@ def roofline_line(mode, kind, prof, w, d, T, C, nb, nbc, fdiag, esz, peaks, step
     ms, launches = prof[kind]
     avg_ms = ms / launches
     flops, bytes_ = kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz)
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     name = KERNEL_NAMES[mode if mode in ("per_chain", "per_chain_sqrt", "table_sqrt") else "table"].get(kind, kind)
     line = {"path": path, "kernel": name, "launches": launches, "avg_launch_ms": avg_ms}
     if bytes_ is not None and "hbm_gbs" in peaks:
@@ -296,8 +317,10 @@ def roofline_line(mode, kind, prof, w, d, T, C, nb, nbc, fdiag, esz, peaks, step
     if flops is None:
         return None
     if w["dtype"] == "f32":
-        peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        basis = f"{N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz"
+        n_sm, sm_max, src = device_caps(peaks)
+        peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        basis = (f"{n_sm} SMs (device properties) x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                 f"{sm_max:.0f} MHz ({src})")
     else:
         peak = 1.25
         basis = "nominal GB300 FP64 rate"
@@ -406,6 +429,68 @@ def _oracle_chain_step(args):
     t0 = time.perf_counter()
     mcmc.aux_step_philox(wl.x_init[chain % wl.n_chains], model, wl.delta, wl.mcmc_seed, chain, it)
     return time.perf_counter() - t0
+
+
+def _oracle_replay(args):
+    """One oracle step of chain `chain` at iteration `it` from the GPU's state x_before:
+    (log alpha, accepted, x*, smoothing sd of x*)."""
+    from oracle import kalman, mcmc
+    name, chain, it, x_before = args
+    wl, _ = make_workload(name)
+    em = mcmc.SVEmission(wl.y, wl.mask) if wl.emission == 1 else \
+        mcmc.LinearGaussianEmission(wl.y, wl.Ry, wl.mask)
+    model = dict(m0=wl.m0, P0=wl.P0, F=wl.F, b=wl.b, Q=wl.Q, emission=em)
+    ref = mcmc.aux_step_philox(x_before, model, wl.delta, wl.mcmc_seed, chain, it)
+    _, Ps = kalman.rts_smoother(ref["kf"], wl.F)
+    import numpy as np
+    sd = np.sqrt(np.maximum(np.einsum("tii->ti", Ps), 0.0))
+    return ref["log_alpha"], ref["accepted"], ref["x_star"], sd
+
+
+def fp32_error_block(name, wl, w, mode, block_len, pool, chains=(0, 9, 22, 31), steps=16):
+    """Error of the FP32 GPU path against the FP64 oracle on sampled chains: each GPU
+    step is replayed on the oracle from the GPU's state before it, on the same Philox
+    draws. Reports the |d log alpha| distribution, MH-decision mismatches (with the
+    near-tie band), and the element-wise error of accepted x* scaled by
+    (|x*_oracle| + smoothing sd)."""
+    import numpy as np
+    import torch
+    from oracle import philox
+    from paper_2303_00301_gb300 import AuxKalman
+    tdt = torch.float32 if w["dtype"] == "f32" else torch.float64
+    chains = [c for c in chains if c < w["C"]]
+    s = AuxKalman(wl, dtype=w["dtype"], block_len=block_len, mode=mode)
+    x = torch.tensor(wl.x_init, dtype=tdt, device="cuda")
+    la = torch.zeros(w["C"], dtype=torch.float64, device="cuda")
+    jobs, gpu = [], []
+    for it in range(steps):
+        xb = x.double().cpu().numpy()
+        s.step(x, 1, iter0=it, log_alpha=la)
+        torch.cuda.synchronize()
+        xa, lag = x.double().cpu().numpy(), la.cpu().numpy()
+        for c in chains:
+            jobs.append((name, c, it, xb[c]))
+            gpu.append((lag[c], xa[c], xb[c]))
+    s.close()
+    refs = pool.map(_oracle_replay, jobs, chunksize=1)
+    band = 2e-3
+    dla, mism, near, xerr = [], 0, 0, 0.0
+    for (nm, c, it, _), (lg, xa, xb), (lr, acc, xs, sd) in zip(jobs, gpu, refs):
+        dla.append(abs(lg - lr))
+        lu = float(np.log(philox.mh_uniform(wl.mcmc_seed, c, it)))
+        if abs(lr - lu) < band:
+            near += 1
+        if bool(lu < lg) != bool(acc):
+            mism += 1
+        elif acc:
+            xerr = max(xerr, float(np.max(np.abs(xa - xs) / (np.abs(xs) + sd))))
+    a = np.asarray(dla)
+    return {"mode": mode, "chains": list(chains), "steps": steps, "chain_steps": len(dla),
+            "against": "FP64 oracle, same Philox draws, each step from the GPU's state",
+            "abs_dlog_alpha": {"p50": float(np.percentile(a, 50)), "p90": float(np.percentile(a, 90)),
+                               "p99": float(np.percentile(a, 99)), "max": float(a.max())},
+            "mh_decision_mismatches": mism, "near_ties_within_band": near, "near_tie_band": band,
+            "x_star_max_err_over_abs_plus_sd": xerr}
 
 
 def cpu_oracle_rate(name, n_chain_steps, pool, cores, it0=0):
@@ -961,6 +1046,9 @@ def run_ours(args):
                "esjd_per_s_median": float(np.median(esjd_t) / sec_per_iter),
                "seconds_per_iteration": sec_per_iter}
 
+    fp32_error = None
+    if pool is not None and w["dtype"] == "f32":
+        fp32_error = fp32_error_block(name, wl, w, args.mode, block_len_for(args.mode), pool)
     cpu = None
     if pool is not None:
         n = args.cpu_sample_chains or 2 * (os.cpu_count() or 1)
@@ -981,7 +1069,7 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                         "d2h_bytes_per_step": bo},
                 "gpu_launches": head["gpu_launches"],
-                "roofline": roofline, "roofline_lines": lines, "ess": ess,
+                "roofline": roofline, "roofline_lines": lines, "ess": ess, "fp32_error": fp32_error,
                 "cpu_baseline": cpu, "clocks": ck,
                 "kernel_ms_per_step": head["kernel_ms_per_step"],
                 "launch": head["launch"], "ms_per_step_eager": head["ms_per_step_eager"],

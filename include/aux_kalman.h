@@ -124,7 +124,7 @@ typedef struct {
  * AUX_MODE_PER_CHAIN aux_kalman_step, aux_loglik and aux_sample_path return
  * AUX_E_UNSUPPORTED; so do aux_loglik_grad, the second-order proposal, the
  * square-root form and the bridging sampler (their setters return it). The
- * first switch to a table mode also allocates 2 * 152 * 8 DP^2 elements of
+ * first switch to a table mode also allocates 2 * (SM count) * 8 DP^2 elements of
  * scratch for the covariance pass. */
 
 typedef struct aux_model aux_model;   /* opaque handle */
@@ -372,12 +372,18 @@ int aux_read_profile(aux_model *m, double *ms_per_kind, int32_t *launches_per_ki
  * process exits. Problems needing more scratch return AUX_E_TOO_LARGE; the
  * scratch needed is about 2 * C * ceil(T / block_len) * (3 p^2 + 2 p) elements,
  * p = d_x rounded up to 4, 8, 16 or 32.
+ * The call is synchronous: it waits for the work already queued on stream,
+ * uploads the model from a host stack buffer, runs the pass, waits for it and
+ * reads back the status words and logZ. It returns AUX_E_NOT_PD when a device
+ * factorisation failed and AUX_E_NONFINITE when a status word or some logZ[c]
+ * is not finite (logZ then holds what the pass produced). Because it
+ * synchronises and reads host memory it cannot be captured: while stream is
+ * capturing it returns AUX_E_UNSUPPORTED and enqueues nothing.
  * The first call on a device does a one-time set-up for that device (it looks
- * up the array's device address and sets kernel attributes); make that first
- * call before any stream capture. Every call shares the array, which keeps the
- * last call's contents: calls whose work overlaps on the GPU (other streams or
- * host threads) race, so serialise them. The call waits for its own model
- * upload (a few kilobytes) before enqueuing the kernels on stream. */
+ * up the array's device address and sets kernel attributes), under a lock, so
+ * first calls from several host threads are safe. Every call shares the
+ * array, which keeps the last call's contents: calls whose work overlaps on
+ * the GPU (other streams or host threads) race, so serialise them. */
 #define AUX_NOALLOC_SCRATCH_BYTES (32u << 20)
 int aux_loglik_noalloc(const aux_model_desc *desc, const void *ytilde, double *logZ, void *stream);
 

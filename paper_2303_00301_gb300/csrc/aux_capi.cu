@@ -382,6 +382,11 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
   m->stream = (cudaStream_t)stream;
   m->esz = desc->dtype == AUX_F32 ? sizeof(float) : sizeof(double);
   cudaGetDevice(&m->device);
+  if (cudaDeviceGetAttribute(&m->n_sm, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess ||
+      m->n_sm < 1) {
+    release(m);
+    return AUX_E_CUDA;
+  }
   if (fact) {
     const int rc = fact_init(m, desc, Ryinv);
     if (rc) { release(m); return rc; }
@@ -480,7 +485,7 @@ int aux_set_mode(aux_model* m, int32_t mode) {
     int rc = dev_alloc(m, &m->tab, (size_t)6 * m->T * DD * es);
     if (wide(m)) {   // E^(2^k), double-buffered; per-CTA scratch of the dense routines
       if (!rc) rc = dev_alloc(m, &m->cagg0, (size_t)6 * DD * es);
-      if (!rc) rc = dev_alloc(m, &m->cagg1, aux_wide_scratch_elems(m->DP) * es);
+      if (!rc) rc = dev_alloc(m, &m->cagg1, aux_wide_scratch_elems(m->DP, m->n_sm) * es);
     } else {
       if (!rc) rc = dev_alloc(m, &m->cagg0, (size_t)m->nbc * 3 * DD * es);
       if (!rc) rc = dev_alloc(m, &m->cagg1, (size_t)m->nbc * 3 * DD * es);

@@ -445,7 +445,7 @@ struct Fact {
       { ProfScope ps(m, PK_MH, st, 2 + (m->adapt ? 1 : 0) + (m->dev_iter ? 1 : 0));
         k_fm_mh<Real><<<m->C, 256, 0, st>>>(p, m->fmh, m->flz, iter, acc, log_alpha, m->status, m->accept,
                                             m->la_all);
-        k_fm_commit<Real><<<(int)std::min<long>(grid(n, 256), 152L * 8), 256, 0, st>>>(
+        k_fm_commit<Real><<<(int)std::min<long>(grid(n, 256), (long)m->n_sm * 8), 256, 0, st>>>(
             (long)m->T * m->d, n, x, (const Real*)m->xs, m->accept);
         if (m->adapt)
           k_adapt_delta<<<1, 256, 0, st>>>(m->la_all, m->C, m->delta_dev, m->adapt_count, m->adapt_target,

@@ -22,6 +22,7 @@ struct aux_model {
   size_t esz = 0;            // bytes per compute-type element
   cudaStream_t stream = nullptr;
   int device = 0;
+  int n_sm = 0;               // multiprocessors of the device (grid caps, scratch slots)
   // model on the device, compute type, padded to DP
   void *F = nullptr, *Q = nullptr, *P0 = nullptr, *m0 = nullptr, *b = nullptr, *Ryinv = nullptr;
   void *y = nullptr;
@@ -135,7 +136,7 @@ int aux_fact_sample_path(aux_model *m, const void *yt, const void *eps, uint64_t
 const AuxOps *aux_ops_f32(int DP);
 const AuxOps *aux_ops_f64(int DP);
 const AuxOps *aux_ops_f32_wide(int DP);   // padded dimensions 64 and 128 (aux_wide.cu)
-size_t aux_wide_scratch_elems(int DP);      // per-CTA scratch of the wide covariance pass
+size_t aux_wide_scratch_elems(int DP, int n_sm);   // per-CTA scratch of the wide covariance pass
 
 // element counts of the per-block buffers for a padded dimension DP
 inline size_t aux_es(int DP) { return 3u * DP * DP + 2u * DP; }

@@ -8,9 +8,14 @@
 // The array is part of the library's module: every GPU that loads the library
 // holds it until the process exits. All calls share it, so calls whose work
 // overlaps on the GPU (different streams, or several host threads) race and
-// must be serialised by the caller.
+// must be serialised by the caller. The per-device set-up (the array's device
+// address, kernel attributes) is guarded by a lock, so first calls from several
+// host threads do not race on it. Each call is synchronous: it returns after
+// its pass has finished and its status words have been read back.
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "aux_internal.h"
 
@@ -20,9 +25,59 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[AUX_NOALLOC_SCR
 
 constexpr int kMaxDevices = 64;
 void* g_scratch_ptr[kMaxDevices] = {};     // device address of the array, per device
-bool g_ready[kMaxDevices] = {};            // set-up done (address known, kernels configured)
-bool g_ready_f32[kMaxDevices][33] = {};
-bool g_ready_f64[kMaxDevices][33] = {};
+// set-up done per device (address known) and per (device, dtype, DP) (kernels
+// configured); written under g_setup_lock, read lock-free once set
+std::atomic<bool> g_ready[kMaxDevices];
+std::atomic<bool> g_ready_ops[kMaxDevices][2][33];
+std::mutex g_setup_lock;
+
+// One-time set-up for the current device `dev` and the kernels of (dtype, DP).
+int setup_device(int dev, int dtype, int DP, const AuxOps* ops) {
+  if (g_ready[dev].load(std::memory_order_acquire) &&
+      g_ready_ops[dev][dtype][DP].load(std::memory_order_acquire))
+    return AUX_OK;
+  std::lock_guard<std::mutex> lock(g_setup_lock);
+  if (!g_ready[dev].load(std::memory_order_relaxed)) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return AUX_E_CUDA;
+    g_scratch_ptr[dev] = p;
+    g_ready[dev].store(true, std::memory_order_release);
+  }
+  if (!g_ready_ops[dev][dtype][DP].load(std::memory_order_relaxed)) {
+    if (ops->prepare() != AUX_OK) return AUX_E_CUDA;
+    g_ready_ops[dev][dtype][DP].store(true, std::memory_order_release);
+  }
+  return AUX_OK;
+}
+
+// After the pass: the OR of the status words [2][C] (per-iteration and latched)
+// and the finiteness of logZ[C], read back in chunks through host stack buffers
+// (waits for the stream). A failed factorisation gives AUX_E_NOT_PD, a
+// non-finite status bit or log-likelihood AUX_E_NONFINITE.
+int read_status(const unsigned char* st_iter, const unsigned char* st, const double* logZ, int C,
+                cudaStream_t s) {
+  constexpr int CH = 512;
+  int32_t h[2][CH];
+  double z[CH];
+  int32_t any = 0;
+  bool finite_z = true;
+  for (int c0 = 0; c0 < C; c0 += CH) {
+    const int n = C - c0 < CH ? C - c0 : CH;
+    const size_t off = (size_t)c0 * sizeof(int32_t);
+    if (cudaMemcpyAsync(h[0], st_iter + off, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(h[1], st + off, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(z, logZ + c0, n * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return AUX_E_CUDA;
+    for (int i = 0; i < n; ++i) {
+      any |= h[0][i] | h[1][i];
+      if (!std::isfinite(z[i])) finite_z = false;
+    }
+  }
+  if (any & 1) return AUX_E_NOT_PD;
+  if ((any & 2) || !finite_z) return AUX_E_NONFINITE;
+  return AUX_OK;
+}
 
 int pick_dp_noalloc(int d) {
   if (d <= 4) return 4;
@@ -156,25 +211,22 @@ extern "C" int aux_loglik_noalloc(const aux_model_desc* desc, const void* ytilde
   const Layout lay = layout(DP, C, nb, esz);
   if (lay.total > (size_t)AUX_NOALLOC_SCRATCH_BYTES) return AUX_E_TOO_LARGE;
 
+  cudaStream_t st = (cudaStream_t)stream;
+  // The call synchronises its stream and reads host stack memory: it cannot be
+  // part of a captured graph. Refuse before anything is enqueued.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+    return AUX_E_UNSUPPORTED;
+
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AUX_E_CUDA;
-  // set-up, once per device (this device is current): the array's device address
-  if (!g_ready[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return AUX_E_CUDA;
-    g_scratch_ptr[dev] = p;
-    g_ready[dev] = true;
-  }
   const AuxOps* ops = desc->dtype == AUX_F32 ? aux_ops_f32(DP) : aux_ops_f64(DP);
   if (!ops) return AUX_E_UNSUPPORTED;
-  bool& configured = desc->dtype == AUX_F32 ? g_ready_f32[dev][DP] : g_ready_f64[dev][DP];
-  if (!configured) {
-    if (ops->prepare() != AUX_OK) return AUX_E_CUDA;
-    configured = true;
-  }
+  // set-up, once per device (this device is current): the array's device address
+  // and the kernels' attributes
+  if (setup_device(dev, desc->dtype, DP, ops) != AUX_OK) return AUX_E_CUDA;
 
   unsigned char* base = static_cast<unsigned char*>(g_scratch_ptr[dev]);
-  cudaStream_t st = (cudaStream_t)stream;
   int rc = desc->dtype == AUX_F32 ? upload_model<float>(desc, DP, base, lay, st)
                                   : upload_model<double>(desc, DP, base, lay, st);
   if (rc) return rc;
@@ -188,6 +240,7 @@ extern "C" int aux_loglik_noalloc(const aux_model_desc* desc, const void* ytilde
   m.emis = desc->emis_kind; m.y_per_chain = 0;
   m.L = L_blk; m.nb = nb; m.delta = desc->delta; m.seed = 0; m.esz = esz;
   m.stream = st; m.device = dev; m.ops = ops;
+  if (cudaDeviceGetAttribute(&m.n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return AUX_E_CUDA;
   m.fdiag = 1;
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < d; ++j)
@@ -198,5 +251,8 @@ extern "C" int aux_loglik_noalloc(const aux_model_desc* desc, const void* ytilde
   m.lz_part = reinterpret_cast<double*>(base + lay.lz);
   m.status_iter = reinterpret_cast<int32_t*>(base + lay.st_iter);
   m.status = reinterpret_cast<int32_t*>(base + lay.st);
-  return ops->loglik(&m, ytilde, logZ, nullptr, nullptr, st);
+  rc = ops->loglik(&m, ytilde, logZ, nullptr, nullptr, st);
+  if (rc) return rc;
+  // wait for the pass and report a failed factorisation or a non-finite value
+  return read_status(base + lay.st_iter, base + lay.st, logZ, C, st);
 }

@@ -138,7 +138,7 @@ struct Ops {
     launch_pdl(k_mh<Real>, m->C, 128, 0, st, p, (const double*)m->mh_part, (const double*)m->lz_part, iter,
                acc, log_alpha, m->status, m->accept, m->la_all);
     const long n = (long)m->C * m->T * m->d;
-    const int grid = (int)std::min<long>((n + 255) / 256, 152L * 8);
+    const int grid = (int)std::min<long>((n + 255) / 256, (long)m->n_sm * 8);
     launch_pdl(k_commit<Real>, grid, 256, 0, st, p, x, (const Real*)m->xs, (const int32_t*)m->accept);
     if (m->adapt)
       launch_pdl(k_adapt_delta, 1, 256, 0, st, (const double*)m->la_all, m->C, m->delta_dev, m->adapt_count,
@@ -510,7 +510,7 @@ struct Ops {
     if (second) { pf.rho = (const Real*)m->rho; pr.rho = (const Real*)m->rhos; }
     Real* x = (Real*)xv;
     const long n = (long)m->C * m->T * m->d;
-    const int lin_grid = (int)std::min<long>((n + 255) / 256, 152L * 16);
+    const int lin_grid = (int)std::min<long>((n + 255) / 256, (long)m->n_sm * 16);
     for (int it = 0; it < n_iters; ++it) {
       const uint64_t iter = iter0 + (uint64_t)it;
       { ProfScope ps(m, PK_LINEARISE, st);

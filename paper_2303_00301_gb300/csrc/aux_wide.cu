@@ -50,16 +50,16 @@ struct WOps {
       ProfScope ps(m, PK_COV_SCAN, st);
       const int cnt = std::min(pow2, m->T - pow2);
       const int sq = 2 * pow2 < m->T ? 1 : 0;
-      k_w_double<Real, DP><<<std::min(cnt + sq, W_SLOTS), WT, Z::SMEM, st>>>(p, a, pow2, cnt, sq, gk, gk2);
+      k_w_double<Real, DP><<<std::min(cnt + sq, W_SLOTS_PER_SM * m->n_sm), WT, Z::SMEM, st>>>(p, a, pow2, cnt, sq, gk, gk2);
       std::swap(gk, gk2);
     }
     {
       ProfScope ps(m, PK_COV_APPLY, st);
-      k_w_epi<Real, DP><<<std::min(m->T + 1, W_SLOTS), WT, Z::SMEM, st>>>(p, a);
+      k_w_epi<Real, DP><<<std::min(m->T + 1, W_SLOTS_PER_SM * m->n_sm), WT, Z::SMEM, st>>>(p, a);
     }
     {
       ProfScope ps(m, PK_COV_PRODUCTS, st);
-      k_w_prod<Real, DP><<<std::min(m->nb, W_SLOTS), WT, Z::SMEM, st>>>(p, a);
+      k_w_prod<Real, DP><<<std::min(m->nb, W_SLOTS_PER_SM * m->n_sm), WT, Z::SMEM, st>>>(p, a);
     }
   }
 
@@ -121,7 +121,7 @@ struct WOps {
     k_mh<Real><<<m->C, 128, 0, st>>>(p, (const double*)m->mh_part, (const double*)m->lz_part, iter, acc,
                                      log_alpha, m->status, m->accept, m->la_all);
     const long n = (long)m->C * m->T * m->d;
-    const int grid = (int)std::min<long>((n + 255) / 256, 152L * 8);
+    const int grid = (int)std::min<long>((n + 255) / 256, (long)m->n_sm * 8);
     k_commit<Real><<<grid, 256, 0, st>>>(p, x, (const Real*)m->xs, (const int32_t*)m->accept);
     if (m->adapt)
       k_adapt_delta<<<1, 256, 0, st>>>((const double*)m->la_all, m->C, m->delta_dev, m->adapt_count,
@@ -198,7 +198,9 @@ struct WOps {
 
 }  // namespace auxk
 
-size_t aux_wide_scratch_elems(int DP) { return (size_t)auxk::W_SLOTS * auxk::W_SCR * DP * DP; }
+size_t aux_wide_scratch_elems(int DP, int n_sm) {
+  return (size_t)auxk::W_SLOTS_PER_SM * n_sm * auxk::W_SCR * DP * DP;
+}
 
 const AuxOps* aux_ops_f32_wide(int DP) {
   switch (DP) {

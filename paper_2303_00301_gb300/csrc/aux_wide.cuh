@@ -41,7 +41,7 @@
 namespace auxk {
 
 constexpr int WT = 256;          // threads of every wide kernel
-constexpr int W_SLOTS = 2 * 152; // CTAs with their own scratch (2 per SM)
+constexpr int W_SLOTS_PER_SM = 2;  // CTAs with their own scratch: 2 per SM of the device
 constexpr int W_SCR = 8;         // scratch matrices per slot
 // chains per thread in the means kernels (8 chains per CTA at DP = 128, 16 at 64)
 template <int DP> constexpr int WCPT = 4;
@@ -261,7 +261,7 @@ template <typename Real> struct WCovArgs {
   double* ld;         // [nb] per means block
   int32_t* status;    // [1] ST_NOT_PD
   Real* gk;           // [2][3][DP][DP] E^(2^k) (A, C, J), double-buffered
-  Real* scr;          // [W_SLOTS][W_SCR][DP][DP]
+  Real* scr;          // [W_SLOTS_PER_SM * SMs][W_SCR][DP][DP]
 };
 
 template <typename Real, int DP>

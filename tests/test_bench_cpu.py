@@ -44,7 +44,9 @@ def test_doubling_scan_counts_one_operator_per_prefix():
     assert flops == pytest.approx(((nbc - 1) + (levels - 1)) * bench.combine_flops(d) / levels)
 
 
-def test_roofline_line_arithmetic():
+def test_roofline_line_arithmetic(monkeypatch):
+    # the device's SM count and maximum clock, as device_caps would read them
+    monkeypatch.setattr(bench, "device_caps", lambda peaks: (152, 2000.0, "test"))
     prof = {"apply": (2.0, 4)}                       # 4 launches in 2 ms
     peaks = {"hbm_gbs": 6000.0, "sm_max_mhz": 2000.0}
     line = bench.roofline_line("cached", "apply", prof, W32, 30, 1024, 32, 32, 256, True, 4, peaks, 2, "p")

@@ -68,3 +68,55 @@ def test_noalloc_rejects_problems_beyond_its_scratch(lib):
         lib.aux_loglik_noalloc(yt, out, d_x=d, T=T, n_chains=C, m0=m["m0"], P0=m["P0"],
                                F=m["F"], b=m["b"], Q=m["Q"], delta=0.5, dtype=lib.AUX_F32)
     assert e.value.code == lib.AUX_E_TOO_LARGE
+
+
+def test_noalloc_reports_a_nonfinite_result(lib):
+    """A NaN in one chain's pseudo-observations gives a non-finite logZ for that
+    chain; the call reports it (AUX_E_NONFINITE) and the other chains still equal
+    aux_loglik. A later clean call on the same scratch returns AUX_OK."""
+    d, T, C = 6, 40, 3
+    m = _model(d, T, seed=3)
+    kw = dict(d_x=d, T=T, n_chains=C, m0=m["m0"], P0=m["P0"], F=m["F"], b=m["b"], Q=m["Q"],
+              delta=0.5, dtype=lib.AUX_F32, block_len=8)
+    yt = torch.tensor(np.random.default_rng(0).standard_normal((C, T, d)), dtype=torch.float32,
+                      device="cuda")
+    ref = torch.zeros(C, dtype=torch.float64, device="cuda")
+    lib.aux_loglik_noalloc(yt, ref, **kw)
+    bad = yt.clone()
+    bad[1, 17, 2] = float("nan")
+    out = torch.zeros(C, dtype=torch.float64, device="cuda")
+    with pytest.raises(lib.AuxError) as e:
+        lib.aux_loglik_noalloc(bad, out, **kw)
+    assert e.value.code == lib.AUX_E_NONFINITE
+    o, r = out.cpu().numpy(), ref.cpu().numpy()
+    assert not np.isfinite(o[1])
+    assert np.all(np.abs(o[[0, 2]] - r[[0, 2]]) <= 1e-5 * np.abs(r[[0, 2]]))
+    out2 = torch.zeros(C, dtype=torch.float64, device="cuda")
+    lib.aux_loglik_noalloc(yt, out2, **kw)
+    assert np.all(np.abs(out2.cpu().numpy() - r) <= 1e-12 * np.abs(r))
+
+
+def test_noalloc_refuses_stream_capture(lib):
+    """The call synchronises its stream, so it refuses a capturing stream up front
+    (AUX_E_UNSUPPORTED, nothing enqueued) and the capture itself stays valid."""
+    d, T, C = 4, 16, 2
+    m = _model(d, T, seed=4)
+    yt = torch.zeros((C, T, d), dtype=torch.float32, device="cuda")
+    out = torch.zeros(C, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    code = None
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        try:
+            lib.aux_loglik_noalloc(yt, out, d_x=d, T=T, n_chains=C, m0=m["m0"], P0=m["P0"],
+                                   F=m["F"], b=m["b"], Q=m["Q"], delta=0.5, dtype=lib.AUX_F32,
+                                   stream=s.cuda_stream)
+        except lib.AuxError as e:
+            code = e.code
+        out.add_(1.0)
+        g.capture_end()
+    assert code == lib.AUX_E_UNSUPPORTED
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.all(out == 1.0)
