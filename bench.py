@@ -131,6 +131,27 @@ def combine_flops(d):
     return (59.0 / 3.0) * d ** 3 + 18.0 * d ** 2
 
 
+def matrix_combine_flops(d):
+    """Matrix part (A, C, J) of the element operator, Cholesky form: Cholesky of C_i
+    and of N = I + U^T J_j U, one triangular solve with d right-hand sides, ten
+    dense products."""
+    return (2.0 / 3.0 + 1.0 + 20.0) * d ** 3
+
+
+def conly_flops(d):
+    """C part of prefix (x) E for a prefix with A = J = 0: two Cholesky, one triangular
+    solve, four dense products (J U, U^T J U, A B, P P^T)."""
+    return (2.0 / 3.0 + 1.0 + 8.0) * d ** 3
+
+
+def cov2_tables_flops_per_step(d, fdiag):
+    """Per-step tables from P^f_(t-1), P^f_t: Cholesky of S_t, W = L^{-1} (triangular
+    solve with d right-hand sides), K' = r W^T W; Cholesky of P^p_(t+1),
+    Y = L^{-1} F P^f_t, Sigma = P^f_t - Y^T Y, G by a triangular solve, Cholesky of
+    Sigma; a dense F adds F P^f F^T twice and F P^f (five products)."""
+    return (1.0 / 3 + 1 + 2 + 1.0 / 3 + 1 + 2 + 1 + 1.0 / 3) * d ** 3 + (0.0 if fdiag else 10.0 * d ** 3)
+
+
 def reduce_flops_per_step(d, fdiag):
     """Conditional Kalman step: Cholesky of S, 2 triangular solves (Y, W), 3 products
     (Y^T Y, Y^T W, W^T W); with a dense F also F C, (F C) F^T and F A."""
@@ -236,21 +257,24 @@ def kernel_work(mode, kind, w, d, T, C, nb, nbc, fdiag, esz):
             combines = (n_end - 1) + max(0, levels - 1) + (1 if ragged else 0)
             return combines * 29.3 * d ** 3 / max(1, levels + (1 if ragged else 0)), None
         return T * (17.3 + 17.7 + 1 + 6) * d ** 3, None
+    # covariance form (aux_cov2.cuh): prefixes by doubling over the steps
     if kind == "cov_reduce":
-        # the distinct block aggregates only: the first block, a generic one, a short last one
-        return min(nbc, 3 if ragged else 2) * Lc * reduce_flops_per_step(d, fdiag), None
+        # P^f_0 (Cholesky of S0, one triangular solve, Y^T Y) and the shared element E
+        # (Cholesky of S, two triangular solves, Y^T Y, Y^T V, V^T V)
+        return (1.0 / 3 + 1 + 2 + 1.0 / 3 + 2 + 6) * d ** 3, None
     if kind == "cov_scan":
-        # prefixes by doubling: one operator per prefix plus one power per level but the last
-        n_end = nbc - 1 if ragged else nbc
-        levels = max(0, math.ceil(math.log2(n_end))) if n_end > 1 else 0
-        combines = (n_end - 1) + max(0, levels - 1) + (1 if ragged else 0)
-        return combines * combine_flops(d) / max(1, levels + (1 if ragged else 0)), None
+        # T - 1 prefix operators (C part only) and one power per level but the last,
+        # averaged over the ceil(log2 T) level launches
+        levels = max(0, math.ceil(math.log2(T))) if T > 1 else 0
+        if levels == 0:
+            return None, None
+        return ((T - 1) * conly_flops(d) + (levels - 1) * matrix_combine_flops(d)) / levels, None
     if kind == "cov_apply":
-        return T * cov_apply_flops_per_step(d, fdiag), None
+        return T * cov2_tables_flops_per_step(d, fdiag), None
     if kind == "cov_products":
-        # composition of the covariance-block products (2 per covariance block) and the
-        # prefix fix-up of G_s..G_{t-1} (one product per step)
-        return (2 * nbc + T) * 2.0 * d ** 3 / 2, None   # 2 launches
+        # one product per step in the G chain and one in the M chain (M_t = K'_t F: one more
+        # product with a dense F)
+        return T * (4.0 + (0.0 if fdiag else 2.0)) * d ** 3, None
     return None, None
 
 
@@ -261,14 +285,15 @@ KERNEL_NAMES = {
                        "backward": "k_sample_backward", "mh": "k_mh + k_commit", "linearise": "k_linearise"},
     "table": {"reduce": "k_mf_reduce", "apply": "k_mf_apply", "scan": "k_mean_cross",
               "backward": "k_mean_cross + k_mb_apply", "mh": "k_mh + k_commit",
-              "cov_reduce": "k_cov_reduce", "cov_scan": "k_cov_scan_double_mw",
-              "cov_apply": "k_cov_apply", "cov_products": "k_cov_products",
+              "cov_reduce": "k_c2_init", "cov_scan": "k_c2_level",
+              "cov_apply": "k_c2_tables", "cov_products": "k_c2_products",
               "bridge": "k_b_sample + k_b_mh", "bridge_tree": "k_br_leaf + k_br_node"},
 }
 
 
 KERNEL_NAMES["table_sqrt"] = dict(KERNEL_NAMES["table"], cov_reduce="k_srcov_reduce",
-                                  cov_scan="k_srcov_scan_double", cov_apply="k_srcov_apply")
+                                  cov_scan="k_srcov_scan_double", cov_apply="k_srcov_apply",
+                                  cov_products="k_cov_products + k_cov_gp_fix")
 
 
 def source_hash():

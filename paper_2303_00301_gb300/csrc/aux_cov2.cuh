@@ -1,0 +1,436 @@
+// aux_cov2.cuh — the covariance pass of the table modes by doubling over the
+// steps (covariance form, padded widths p <= 32).
+//
+// With homogeneous dynamics and R = r I every filtering element with t >= 1
+// has the same matrix part E = (A, C, J) (Appendix A.2.1), and the element of
+// t = 0 is the posterior of x_0 (A = 0, J = 0, C = P^f_0). The inclusive prefix
+// of step t is P_t = e_0 (x) E^t: its C part is the filtering covariance P^f_t
+// and its A and J parts vanish. Level k forms, for every t in
+// [2^k, min(2^(k+1), T)), P_t = P_(t-2^k) (x) E^(2^k) — one operator per step
+// that needs only the C part of its left operand — and, on one more CTA,
+// E^(2^(k+1)) = E^(2^k) (x) E^(2^k) for the next level: ceil(log2 T) operators
+// of depth and T - 1 prefix operators in all. Given every P^f_t the per-step
+// tables depend on P^f_(t-1), P^f_t and the model only, so each step forms its
+// own (k_c2_tables), and the products over the means partition run one chain
+// per means block (k_c2_products). The tables are those of aux_cov.cuh:
+//   tab[TK][t]  = K'_t = r S_t^{-1},  S_t = P^p_t + r I,   ldt[t] = log det S_t
+//   tab[TG][t]  = G_t = P^f_t F^T (P^p_{t+1})^{-1}          (0 at t = T - 1)
+//   tab[TLS][t] = chol(Sigma_t), Sigma_t = P^f_t - G_t P^p_{t+1} G_t^T
+//                 (chol(P^f_{T-1}) at t = T - 1)
+//   tab[TPF][t] = P^f_t
+//   tab[TGP][t] = G_s ... G_{t-1} over the means block s..e of t (I at t = s)
+//   btab[BGH][k] = G_s ... G_e,  btab[BAH][k] = M_e ... M_s (M_t = K'_t F),
+//   ld[k] = sum of ldt over the means block.
+#pragma once
+#include "aux_cov.cuh"
+
+namespace auxk {
+
+template <typename Real> struct Cov2Args {
+  Real* tab;         // [NTAB][T][DP][DP]
+  Real* btab;        // [NBTAB][nb][DP][DP]
+  double* ld;        // [nb]
+  double* ldt;       // [T]
+  Real* pw;          // [2][3 DP^2]: (A, C, J) of E^(2^k), double buffered over the levels
+  int32_t* status;   // [1]: ST_NOT_PD when a factorisation failed
+};
+
+template <typename Real, int DP> struct Cov2Sizes {
+  static constexpr int MAT = Lay<Real, DP>::MAT, VEC = Lay<Real, DP>::VEC;
+  static constexpr size_t MODEL = (3 * MAT + 2 * VEC) * sizeof(Real);
+  // init: model + 2 x (LS, Y, V) + 2 x (2 vectors)
+  static constexpr size_t INIT_SMEM = MODEL + (6 * MAT + 4 * VEC) * sizeof(Real);
+  // tables: model + P^f_(t-1), P^f_t + gain warp (LS, W, X) + backward warp (X, LS, LR, Y, G, LRow)
+  static constexpr size_t TAB_SMEM = MODEL + (11 * MAT + 4 * VEC) * sizeof(Real);
+  // products: running product, two staged tables, M row scratch, F slot
+  static constexpr size_t PROD_SMEM = (5 * MAT + 2 * VEC) * sizeof(Real);
+};
+
+// ---------------------------------------------------------------------------
+// The two elements of the pass: P^f_0 (posterior of x_0: S0 = P0 + R,
+// C = P0 - P0 S0^{-1} P0) on warp 0, and E (conditional Kalman step from the
+// identity element: S = Q + R, Y = L_S^{-1} Q, V = L_S^{-1} F, C = Q - Y^T Y,
+// A = F - Y^T V, J = V^T V) on warp 1.
+// ---------------------------------------------------------------------------
+template <typename Real, int DP>
+__global__ void __launch_bounds__(64, 1) k_c2_init(KP<Real> p, Cov2Args<Real> a) {
+  pdl_wait();
+  pdl_trigger();
+  refresh_delta(p);
+  using Z = Cov2Sizes<Real, DP>;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC;
+  constexpr long DD = (long)DP * DP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  Real* sF = sm;
+  Real* sFT = sF + MAT;
+  Real* sQ = sFT + MAT;
+  Real* sb = sQ + MAT;
+  load_model_slots<Real, DP>(p, sF, sFT, sQ, sb);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  Real* LS = sb + 2 * VEC + warp * 3 * MAT;
+  Real* SY = LS + MAT;
+  Real* SV = SY + MAT;
+  Real* vd = sb + 2 * VEC + 6 * MAT + warp * 2 * VEC;
+  Real* vdummy = vd + VEC;
+  int bad = 0;
+  Real s_[DP];
+  if (warp == 0) {
+    ld_vec<Real, DP>(p.P0 + row * DP, s_);
+  } else {
+    ld_row<Real, DP>(sQ, row, s_);
+  }
+  Real cov[DP];
+#pragma unroll
+  for (int j = 0; j < DP; ++j) cov[j] = s_[j];
+#pragma unroll
+  for (int j = 0; j < DP; ++j) s_[j] += (j == lane && j < p.d) ? p.r : (Real)0;
+  chol_shfl<Real, DP>(s_, LS, nullptr, nullptr, vd, nullptr, p.d, lane, &bad);
+  Real r1[DP], r2[DP], rv[DP];
+#pragma unroll
+  for (int j = 0; j < DP; ++j) r1[j] = cov[j];   // column `row` of the symmetric P0 / Q
+  ld_col<Real, DP>(sF, row, r2);
+  zero<Real, DP>(rv);
+  fsolve_multi<Real, DP, true>(LS, vd, r1, SY, r2, SV, rv, vdummy, lane);
+  __syncwarp();
+  mm_col<Real, DP, true, true>(SY, row, SY, cov);          // C = P - Y^T Y
+  if (warp == 0) {
+    if (act) st_vec<Real, DP>(a.tab + ((long)TPF * p.nT + 0) * DD + row * DP, cov);
+  } else {
+    Real an[DP], jn[DP];
+    ld_row<Real, DP>(sF, row, an);
+    mm_col<Real, DP, true, true>(SY, row, SV, an);          // A = F - Y^T V
+    mm_col<Real, DP>(SV, row, SV, jn);                      // J = V^T V
+    if (act) {
+      st_vec<Real, DP>(a.pw + row * DP, an);
+      st_vec<Real, DP>(a.pw + DD + row * DP, cov);
+      st_vec<Real, DP>(a.pw + 2 * DD + row * DP, jn);
+    }
+  }
+  if (bad && lane == 0) atomicOr(a.status, ST_NOT_PD);
+}
+
+// ---------------------------------------------------------------------------
+// C part of P (x) right for a prefix P = (0, C_i, 0), one CTA of CW_SCAN warps:
+// U = chol(C_i), N = I + U^T J_e U, B = U L_N^{-T}, P = A_e B, C = C_e + P P^T
+// (the operator of Appendix A.2.1 with A_i = 0, J_i = 0, in its Cholesky form;
+// same order of operations per entry as cov_combine_mw).
+// ---------------------------------------------------------------------------
+template <typename Real, int DP>
+__device__ void cov2_conly(const KP<Real>& p, const Real* __restrict__ Ci, const Real* __restrict__ right,
+                           Real* __restrict__ outC, int32_t* __restrict__ status) {
+  using Z = CovScanMW<Real, DP>;
+  constexpr int MAT = Z::MAT, LD = Lay<Real, DP>::LD, NC = Z::NC;
+  constexpr long DD = (long)DP * DP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  const int c0 = warp * NC;
+  Real* SC = sm;
+  Real* SU = SC + MAT;
+  Real* S2 = SU + MAT;
+  Real* S3 = S2 + MAT;
+  Real* S4 = S3 + MAT;
+  Real* SN = S4 + MAT;
+  Real* SAe = SN + MAT;
+  Real* SCe = SAe + MAT;
+  Real* SJe = SCe + MAT;
+  Real* vd1 = SJe + MAT;
+  Real* vd2 = vd1 + Lay<Real, DP>::VEC;
+  stage_mats<Real, DP>(SC, Ci, DD, 1);
+  stage_mats<Real, DP>(SAe, right, DD, 3);
+  cp_async_wait<0>();
+  __syncthreads();
+  int bad = 0;
+  auto put = [&](Real* S, const Real (&v)[NC]) {
+    if (act) stn<Real, NC>(S + row * LD + c0, v);
+  };
+  if (warp == 0) {   // U = chol(C_i): rows in SU
+    Real a_[DP];
+    ld_row<Real, DP>(SC, row, a_);
+    chol_shfl<Real, DP>(a_, S2, SU, nullptr, vd1, nullptr, p.d, lane, &bad);
+  }
+  __syncthreads();
+  Real t1[NC];
+  mm_row_c<Real, DP, NC>(SJe + row * LD, SU, c0, t1);   // J_e U
+  put(S3, t1);
+  __syncthreads();
+  mm_col_c<Real, DP, NC>(SU, row, S3, c0, t1);          // N = I + U^T J_e U
+#pragma unroll
+  for (int j = 0; j < NC; ++j) t1[j] += (c0 + j == lane) ? (Real)1 : (Real)0;
+  put(SN, t1);
+  __syncthreads();
+  if (warp == 0) {   // L_N = chol(N); B = U L_N^{-T} (rows in S2)
+    Real a_[DP];
+    ld_row<Real, DP>(SN, row, a_);
+    chol_shfl<Real, DP>(a_, S4, nullptr, nullptr, vd2, nullptr, p.d, lane, &bad);
+    Real r[DP];
+    ld_row<Real, DP>(SU, row, r);
+    fsolve_rot<Real, DP, false>(S4, vd2, r, S2, lane);
+  }
+  __syncthreads();
+  mm_row_c<Real, DP, NC>(SAe + row * LD, S2, c0, t1);   // P = A_e B, stored transposed in S3
+  if (act) {
+#pragma unroll
+    for (int j = 0; j < NC; ++j) S3[(c0 + j) * LD + row] = t1[j];
+  }
+  __syncthreads();
+  Real cn[NC];
+  ldn<Real, NC>(SCe + row * LD + c0, cn);               // C = C_e + P P^T
+  mm_col_c<Real, DP, NC, true>(S3, row, S3, c0, cn);
+  if (act) stn<Real, NC>(outC + row * DP + c0, cn);
+  if (bad && lane == 0 && warp == 0) atomicOr(status, ST_NOT_PD);
+}
+
+// Level k of the doubling: CTA i < cnt forms P^f_(pow2 + i) from P^f_i and
+// E^pow2 (pin); CTA cnt (when sq) forms E^(2 pow2) into pout.
+template <typename Real, int DP>
+__global__ void __launch_bounds__(32 * CW_SCAN)
+    k_c2_level(KP<Real> p, Cov2Args<Real> a, int pow2, int cnt, const Real* __restrict__ pin,
+               Real* __restrict__ pout) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr long DD = (long)DP * DP;
+  const int i = blockIdx.x;
+  Real* pf = a.tab + (long)TPF * p.nT * DD;
+  if (i < cnt)
+    cov2_conly<Real, DP>(p, pf + (long)i * DD, pin, pf + (long)(pow2 + i) * DD, a.status);
+  else
+    cov_combine_mw<Real, DP>(p, pin, pin, pout, a.status);
+}
+
+// ---------------------------------------------------------------------------
+// Per-step tables, one CTA of two warps per step t.
+//   warp 0 (gain tables): P^p_t = F P^f_(t-1) F^T + Q (P0 at t = 0),
+//     L_S = chol(P^p_t + r I), ldt[t] = 2 sum log (L_S)_ii, W = L_S^{-1},
+//     K'_t = r W^T W.
+//   warp 1 (backward tables): X = F P^f_t, P^p_(t+1) = X F^T + Q,
+//     L_P = chol(P^p_(t+1)), Y = L_P^{-1} X, Sigma_t = P^f_t - Y^T Y,
+//     G_t^T = L_P^{-T} Y, chol(Sigma_t)  (t = T - 1: G = 0, chol(P^f_t)).
+// ---------------------------------------------------------------------------
+template <typename Real, int DP>
+__global__ void __launch_bounds__(64) k_c2_tables(KP<Real> p, Cov2Args<Real> a) {
+  pdl_wait();
+  pdl_trigger();
+  refresh_delta(p);
+  using Z = Cov2Sizes<Real, DP>;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
+  constexpr long DD = (long)DP * DP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  Real* sF = sm;
+  Real* sFT = sF + MAT;
+  Real* sQ = sFT + MAT;
+  Real* sb = sQ + MAT;
+  const Real* sphi = sb + VEC;
+  Real* SPm = sb + 2 * VEC;    // P^f_(t-1)
+  Real* SP = SPm + MAT;        // P^f_t
+  Real* LSg = SP + MAT;        // warp 0: chol(S) (LS form)
+  Real* SW = LSg + MAT;        //         W = L_S^{-1}
+  Real* SXg = SW + MAT;        //         F P^f_(t-1) (dense F), symmetrisation scratch
+  Real* SX = SXg + MAT;        // warp 1: X = F P^f_t, then symmetrisation scratch
+  Real* LSb = SX + MAT;        //         chol(P^p_(t+1)) (LS form), then chol(Sigma) (LS form)
+  Real* LRb = LSb + MAT;       //         chol(P^p_(t+1)) right-aligned rows
+  Real* SY = LRb + MAT;        //         Y = L_P^{-1} X
+  Real* SG = SY + MAT;         //         G_t
+  Real* SLr = SG + MAT;        //         chol(Sigma_t) row-major
+  Real* vdg = SLr + MAT;
+  Real* vdb = vdg + VEC;
+  Real* vdb2 = vdb + VEC;
+  const int t = blockIdx.x;
+  const Real* pf = a.tab + (long)TPF * p.nT * DD;
+  if (t > 0) stage_mats<Real, DP>(SPm, pf + (long)(t - 1) * DD, DD, 1);
+  stage_mats<Real, DP>(SP, pf + (long)t * DD, DD, 1);
+  load_model_slots<Real, DP>(p, sF, sFT, sQ, sb);
+  cp_async_wait<0>();
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  int bad = 0;
+  // P^p of the step after the one whose P^f is in slot SPf (scratch slot SS)
+  auto predict = [&](const Real* SPf, Real* SS, Real (&pp)[DP]) {
+    if (p.fdiag) {
+      Real pr[DP], ph[DP], qr[DP];
+      ld_row<Real, DP>(SPf, row, pr);
+      ld_vec<Real, DP>(sphi, ph);
+      ld_row<Real, DP>(sQ, row, qr);
+      const Real phi = sphi[row];
+#pragma unroll
+      for (int j = 0; j < DP; ++j) pp[j] = fma(pr[j], phi * ph[j], qr[j]);
+    } else {
+      Real xr[DP];
+      mm_row<Real, DP>(sF + row * LD, SPf, xr);
+      __syncwarp();
+      st_row<Real, DP>(SS, row, xr, act);
+      __syncwarp();
+      mm_row<Real, DP>(SS + row * LD, sFT, pp);
+      Real qr[DP];
+      ld_row<Real, DP>(sQ, row, qr);
+#pragma unroll
+      for (int j = 0; j < DP; ++j) pp[j] += qr[j];
+      symmetrise_store<Real, DP>(SS, pp, lane);
+    }
+  };
+  if (warp == 0) {
+    Real pp[DP];
+    if (t == 0) ld_vec<Real, DP>(p.P0 + row * DP, pp);
+    else predict(SPm, SXg, pp);
+#pragma unroll
+    for (int j = 0; j < DP; ++j) pp[j] += (j == lane && j < p.d) ? p.r : (Real)0;
+    chol_shfl<Real, DP>(pp, LSg, nullptr, nullptr, vdg, nullptr, p.d, lane, &bad);
+    double lg = (lane < p.d) ? -log((double)vdg[lane]) : 0.0;
+    lg = warp_sum<double>(lg);
+    if (lane == 0) a.ldt[t] = 2.0 * lg;
+    Real r[DP];
+#pragma unroll
+    for (int j = 0; j < DP; ++j) r[j] = (j == lane) ? (Real)1 : (Real)0;
+    fsolve_rot<Real, DP, true>(LSg, vdg, r, SW, lane);
+    __syncwarp();
+    Real kr[DP];
+    mm_col<Real, DP>(SW, row, SW, kr);
+#pragma unroll
+    for (int j = 0; j < DP; ++j) kr[j] *= p.r;
+    if (act) st_vec<Real, DP>(a.tab + ((long)TK * p.nT + t) * DD + row * DP, kr);
+  } else {
+    Real sig[DP];
+    if (t < p.nT - 1) {
+      // X = F P^f_t
+      Real xr[DP];
+      if (p.fdiag) {
+        ld_row<Real, DP>(SP, row, xr);
+        const Real phi = sphi[row];
+#pragma unroll
+        for (int j = 0; j < DP; ++j) xr[j] *= phi;
+      } else {
+        mm_row<Real, DP>(sF + row * LD, SP, xr);
+      }
+      Real pp[DP];
+      predict(SP, SY, pp);   // SY: scratch until Y is formed
+      chol_shfl<Real, DP>(pp, LSb, nullptr, LRb, vdb, nullptr, p.d, lane, &bad);
+      st_row<Real, DP>(SX, row, xr, act);
+      __syncwarp();
+      Real rr[DP];
+      ld_col<Real, DP>(SX, row, rr);
+      fsolve_rot<Real, DP, true>(LSb, vdb, rr, SY, lane);   // Y = L_P^{-1} X (column `lane`)
+      __syncwarp();
+      ld_row<Real, DP>(SP, row, sig);
+      mm_col<Real, DP, true, true>(SY, row, SY, sig);       // Sigma = P^f - Y^T Y
+      ld_col<Real, DP>(SY, row, rr);
+      bsolve_rot<Real, DP>(LRb, vdb, rr, SG, lane);         // row `lane` of G = L_P^{-T} Y column
+      __syncwarp();
+      Real g[DP];
+      ld_row<Real, DP>(SG, row, g);
+      if (act) st_vec<Real, DP>(a.tab + ((long)TG * p.nT + t) * DD + row * DP, g);
+    } else {
+      Real z[DP];
+      zero<Real, DP>(z);
+      if (act) st_vec<Real, DP>(a.tab + ((long)TG * p.nT + t) * DD + row * DP, z);
+      ld_row<Real, DP>(SP, row, sig);
+    }
+    chol_shfl<Real, DP>(sig, LSb, SLr, nullptr, vdb2, nullptr, p.d, lane, &bad);
+    Real lr[DP];
+    ld_row<Real, DP>(SLr, row, lr);
+    if (act) st_vec<Real, DP>(a.tab + ((long)TLS * p.nT + t) * DD + row * DP, lr);
+  }
+  if (bad && lane == 0) atomicOr(a.status, ST_NOT_PD);
+}
+
+// ---------------------------------------------------------------------------
+// Products over the means partition, two CTAs of CW_SCAN warps per means block
+// k (steps s..e), products split by output columns across the warps, the next
+// step's table staged while the current product runs:
+//   CTA 2k:     TGP[t] = G_s ... G_(t-1) for t = s..e, BGH[k] = G_s ... G_e,
+//               ld[k] = sum of ldt[t];
+//   CTA 2k + 1: BAH[k] = M_e ... M_s, M_t = K'_t F.
+// ---------------------------------------------------------------------------
+template <typename Real, int DP>
+__global__ void __launch_bounds__(32 * CW_SCAN) k_c2_products(KP<Real> p, Cov2Args<Real> a) {
+  pdl_wait();
+  pdl_trigger();
+  using Z = Cov2Sizes<Real, DP>;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD, NC = DP / CW_SCAN;
+  constexpr long DD = (long)DP * DP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  Real* SACC = sm;             // running product
+  Real* STb = SACC + MAT;      // two staged tables
+  Real* SM = STb + 2 * MAT;    // M_t = K'_t F (dense F)
+  Real* sF = SM + MAT;
+  Real* sphi = sF + MAT;
+  const int k = blockIdx.x >> 1, which = blockIdx.x & 1;
+  const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  const int c0 = warp * NC;
+  const Real* src = a.tab + (long)(which == 0 ? TG : TK) * p.nT * DD;
+  stage_mats<Real, DP>(STb, src + (long)s * DD, DD, 1);
+  for (int q = threadIdx.x; q < DP * DP; q += blockDim.x) {
+    const int i = q / DP, j = q % DP;
+    SACC[i * LD + j] = (i == j) ? (Real)1 : (Real)0;
+    sF[i * LD + j] = p.F[q];
+  }
+  if (threadIdx.x < DP) sphi[threadIdx.x] = p.F[threadIdx.x * DP + threadIdx.x];
+  for (int t = s; t <= e; ++t) {
+    Real* cur = STb + ((t - s) & 1) * MAT;
+    if (t < e) stage_mats<Real, DP>(STb + ((t - s + 1) & 1) * MAT, src + (long)(t + 1) * DD, DD, 1);
+    if (t < e) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    __syncthreads();
+    Real out[NC];
+    if (which == 0) {
+      if (act && warp == 0) {   // TGP[t] = running product before G_t
+        Real r[DP];
+        ld_row<Real, DP>(SACC, row, r);
+        st_vec<Real, DP>(a.tab + ((long)TGP * p.nT + t) * DD + row * DP, r);
+      }
+      mm_row_c<Real, DP, NC>(SACC + row * LD, cur, c0, out);   // ACC G_t
+    } else {
+      if (p.fdiag) {   // M_t row = K'_t row scaled by diag F; ACC <- M_t ACC
+        Real kr[DP], ph[DP], mr[DP];
+        ld_row<Real, DP>(cur, row, kr);
+        ld_vec<Real, DP>(sphi, ph);
+#pragma unroll
+        for (int j = 0; j < DP; ++j) mr[j] = kr[j] * ph[j];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) out[j] = (Real)0;
+        // out[j] = sum_q M[row][q] ACC[q][c0 + j]
+#pragma unroll
+        for (int q = 0; q < DP; ++q) {
+          Real b[NC];
+          ldn<Real, NC>(SACC + q * LD + c0, b);
+          fma_row<Real, NC>(mr[q], b, out);
+        }
+      } else {
+        Real mr[NC];
+        mm_row_c<Real, DP, NC>(cur + row * LD, sF, c0, mr);   // M_t = K'_t F
+        if (act) stn<Real, NC>(SM + row * LD + c0, mr);
+        __syncthreads();
+        mm_row_c<Real, DP, NC>(SM + row * LD, SACC, c0, out);  // M_t ACC
+      }
+    }
+    __syncthreads();
+    if (act) stn<Real, NC>(SACC + row * LD + c0, out);
+    __syncthreads();
+  }
+  if (act && warp == 0) {
+    Real r[DP];
+    ld_row<Real, DP>(SACC, row, r);
+    st_vec<Real, DP>(a.btab + ((long)(which == 0 ? BGH : BAH) * p.nb + k) * DD + row * DP, r);
+  }
+  if (which == 0 && warp == 1) {
+    double acc = 0.0;
+    for (int t = s + lane; t <= e; t += 32) acc += a.ldt[t];
+    acc = warp_sum<double>(acc);
+    if (lane == 0) a.ld[k] = acc;
+  }
+  (void)VEC;
+}
+
+}  // namespace auxk

@@ -428,6 +428,56 @@ __device__ T chol_rot(T (&a)[DP], T* LS, T* LRow, T* LR, T* inv_diag, const T* e
   return acc;
 }
 
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+
+// chol_rot with the pivot column broadcast by warp shuffles instead of a
+// shared-memory round trip: no __syncwarp() inside the loop, and the pivot's
+// reciprocal square root from one rsqrt (the factor's diagonal is the pivot
+// times it). Same inputs, outputs and padding rules as chol_rot; the slots are
+// only written, never read back, so the loop carries no shared-memory latency.
+template <typename T, int DP>
+__device__ T chol_shfl(T (&a)[DP], T* LS, T* LRow, T* LR, T* inv_diag, const T* eps, int d,
+                       int lane, int* bad) {
+  constexpr int LD = Lay<T, DP>::LD;
+  const bool act = lane < DP;
+  T acc = 0;
+  __syncwarp();
+  if (act) {
+    T z[DP];
+    zero<T, DP>(z);
+    if (LR) st_vec<T, DP>(LR + lane * LD, z);
+    if (LRow) st_vec<T, DP>(LRow + lane * LD, z);
+  }
+#pragma unroll 1
+  for (int k = 0; k < DP; ++k) {
+    T akk = __shfl_sync(FULL_MASK, a[0], k);
+    T piv = (T)1, inv = (T)1;
+    if (k < d) {
+      if (!(akk > (T)0) || !(akk < (T)INFINITY)) { *bad = 1; akk = (T)1; }
+      inv = rsqrt_t(akk);
+      piv = akk * inv;
+    }
+    const T l = (lane == k) ? piv : ((lane > k) ? a[0] * inv : (T)0);
+    if (act && lane >= k) {
+      LS[k * LD + (lane - k)] = l;
+      if (LRow) LRow[lane * LD + k] = l;
+      if (LR) LR[lane * LD + (DP - 1) - (lane - k)] = l;
+    }
+    if (lane == 0) inv_diag[k] = inv;
+    if (eps) acc = fma(l, eps[k], acc);
+    // row update a[i][k+1+j] -= L[i][k] L[k+1+j][k]; entries past DP-1-k are dead
+#pragma unroll
+    for (int j = 0; j < DP - 1; ++j) {
+      const T lj = __shfl_sync(FULL_MASK, l, (k + 1 + j) & 31);
+      a[j] = fma(-l, lj, a[j + 1]);
+    }
+    a[DP - 1] = (T)0;
+  }
+  __syncwarp();
+  return acc;
+}
+
 // Two independent factorizations interleaved (ILP); outputs as in chol_rot.
 template <typename T, int DP>
 __device__ void chol_rot2(T (&a)[DP], T* LS, T* LR, T* invd, T (&b)[DP], T* LS2, T* invd2,

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "aux_bridge.cuh"
+#include "aux_cov2.cuh"
 #include "aux_grad.cuh"
 #include "aux_means.cuh"
 #include "aux_sqrt.cuh"
@@ -104,6 +105,14 @@ struct Ops {
       if (e != cudaSuccess) return AUX_E_CUDA;
     }
     e = cudaFuncSetAttribute(k_cov_gp_fix<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::FIX_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_c2_init<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cov2Sizes<Real, DP>::INIT_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_c2_level<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovScanMW<Real, DP>::SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_c2_tables<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cov2Sizes<Real, DP>::TAB_SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_c2_products<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cov2Sizes<Real, DP>::PROD_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_mf_reduce<Real, DP, MEAN_CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::RED);
     if (e != cudaSuccess) return AUX_E_CUDA;
@@ -207,8 +216,45 @@ struct Ops {
   using CZ = CovSizes<Real, DP>;
   static constexpr long DD = (long)DP * DP;
 
+  // Covariance form: prefixes by doubling over the steps, then every step's
+  // tables and the products of the means partition (aux_cov2.cuh).
+  static void cov2_pass(aux_model* m, const KP<Real>& p, cudaStream_t st) {
+    Cov2Args<Real> a{};
+    a.tab = (Real*)m->tab; a.btab = (Real*)m->btab; a.ld = m->cov_ld; a.ldt = m->cov_ldt;
+    a.pw = (Real*)m->cagg0;
+    a.status = m->cov_status;
+    using C2 = Cov2Sizes<Real, DP>;
+    {
+      ProfScope ps(m, PK_COV_REDUCE, st);
+      cudaMemsetAsync(m->cov_status, 0, sizeof(int32_t), st);
+      launch_pdl(k_c2_init<Real, DP>, 1, 64, C2::INIT_SMEM, st, p, a);
+    }
+    int lvl = 0;
+    for (int pow2 = 1; pow2 < m->T; pow2 *= 2, ++lvl) {
+      ProfScope ps(m, PK_COV_SCAN, st);
+      const int cnt = std::min(pow2, m->T - pow2);
+      const int sq = 2 * pow2 < m->T ? 1 : 0;
+      const Real* pin = a.pw + (lvl & 1) * 3 * DD;
+      Real* pout = a.pw + ((lvl + 1) & 1) * 3 * DD;
+      launch_pdl(k_c2_level<Real, DP>, cnt + sq, 32 * CW_SCAN, CovScanMW<Real, DP>::SMEM, st, p, a, pow2, cnt,
+                 pin, pout);
+    }
+    {
+      ProfScope ps(m, PK_COV_APPLY, st);
+      launch_pdl(k_c2_tables<Real, DP>, m->T, 64, C2::TAB_SMEM, st, p, a);
+    }
+    {
+      ProfScope ps(m, PK_COV_PRODUCTS, st);
+      launch_pdl(k_c2_products<Real, DP>, 2 * m->nb, 32 * CW_SCAN, C2::PROD_SMEM, st, p, a);
+    }
+  }
+
   static void cov_pass(aux_model* m, const KP<Real>& p, cudaStream_t st) {
     m->br_valid = 0;
+    if (!m->sqrt_form) {
+      cov2_pass(m, p, st);
+      return;
+    }
     KP<Real> pc = p;   // the covariance scan runs on its own partition (block length Lc)
     pc.L = m->Lc;
     pc.nb = m->nbc;

@@ -35,13 +35,14 @@ def test_means_path_bytes_are_the_tables_and_vectors_once():
 
 
 def test_doubling_scan_counts_one_operator_per_prefix():
-    """nbc blocks (no short last block): nbc - 1 prefixes plus the powers of all levels but
-    the last, spread over ceil(log2 nbc) launches."""
+    """Doubling over the T steps: T - 1 prefix operators (C part only) plus the powers
+    of all levels but the last, spread over ceil(log2 T) launches."""
     d, T = 30, 1024
-    nbc = 256
-    flops, _ = bench.kernel_work("shared", "cov_scan", W32, d, T, 32, 32, nbc, True, 4)
-    levels = math.ceil(math.log2(nbc))
-    assert flops == pytest.approx(((nbc - 1) + (levels - 1)) * bench.combine_flops(d) / levels)
+    flops, _ = bench.kernel_work("shared", "cov_scan", W32, d, T, 32, 32, 256, True, 4)
+    levels = math.ceil(math.log2(T))
+    assert levels == 10
+    assert flops == pytest.approx(((T - 1) * bench.conly_flops(d)
+                                   + (levels - 1) * bench.matrix_combine_flops(d)) / levels)
 
 
 def test_roofline_line_arithmetic(monkeypatch):
