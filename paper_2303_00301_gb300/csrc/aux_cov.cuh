@@ -330,7 +330,7 @@ __device__ void cov_combine_mw(const KP<Real>& p, const Real* __restrict__ left,
   if (warp == 0) {
     Real a[DP];
     ld_row<Real, DP>(SC, row, a);
-    chol_shfl<Real, DP>(a, S2, SU, nullptr, vd1, nullptr, p.d, lane, &bad);
+    chol_la<Real, DP>(a, S2, SU, nullptr, vd1, nullptr, p.d, lane, &bad);
   }
   __syncthreads();
   Real t1[NC];
@@ -345,10 +345,10 @@ __device__ void cov_combine_mw(const KP<Real>& p, const Real* __restrict__ left,
   if (warp == 0) {   // L_N = chol(N) (LS form in S4); B = U L_N^{-T} (rows in S2)
     Real a[DP];
     ld_row<Real, DP>(SN, row, a);
-    chol_shfl<Real, DP>(a, S4, nullptr, nullptr, vd2, nullptr, p.d, lane, &bad);
+    chol_la<Real, DP>(a, S4, nullptr, nullptr, vd2, nullptr, p.d, lane, &bad);
     Real r[DP];
     ld_row<Real, DP>(SU, row, r);
-    fsolve_rot<Real, DP, false>(S4, vd2, r, S2, lane);
+    fsolve_pf<Real, DP, false>(S4, vd2, r, S2, lane);
   }
   __syncthreads();
   mm_row_c<Real, DP, NC>(SAe + row * LD, S2, c0, t1);   // P = A_e B, stored transposed in S3

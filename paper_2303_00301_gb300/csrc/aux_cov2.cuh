@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(64, 1) k_c2_init(KP<Real> p, Cov2Args<Real> a)
   for (int j = 0; j < DP; ++j) cov[j] = s_[j];
 #pragma unroll
   for (int j = 0; j < DP; ++j) s_[j] += (j == lane && j < p.d) ? p.r : (Real)0;
-  chol_shfl<Real, DP>(s_, LS, nullptr, nullptr, vd, nullptr, p.d, lane, &bad);
+  chol_la<Real, DP>(s_, LS, nullptr, nullptr, vd, nullptr, p.d, lane, &bad);
   Real r1[DP], r2[DP], rv[DP];
 #pragma unroll
   for (int j = 0; j < DP; ++j) r1[j] = cov[j];   // column `row` of the symmetric P0 / Q
@@ -153,7 +153,7 @@ __device__ void cov2_conly(const KP<Real>& p, const Real* __restrict__ Ci, const
   if (warp == 0) {   // U = chol(C_i): rows in SU
     Real a_[DP];
     ld_row<Real, DP>(SC, row, a_);
-    chol_shfl<Real, DP>(a_, S2, SU, nullptr, vd1, nullptr, p.d, lane, &bad);
+    chol_la<Real, DP>(a_, S2, SU, nullptr, vd1, nullptr, p.d, lane, &bad);
   }
   __syncthreads();
   Real t1[NC];
@@ -168,10 +168,10 @@ __device__ void cov2_conly(const KP<Real>& p, const Real* __restrict__ Ci, const
   if (warp == 0) {   // L_N = chol(N); B = U L_N^{-T} (rows in S2)
     Real a_[DP];
     ld_row<Real, DP>(SN, row, a_);
-    chol_shfl<Real, DP>(a_, S4, nullptr, nullptr, vd2, nullptr, p.d, lane, &bad);
+    chol_la<Real, DP>(a_, S4, nullptr, nullptr, vd2, nullptr, p.d, lane, &bad);
     Real r[DP];
     ld_row<Real, DP>(SU, row, r);
-    fsolve_rot<Real, DP, false>(S4, vd2, r, S2, lane);
+    fsolve_pf<Real, DP, false>(S4, vd2, r, S2, lane);
   }
   __syncthreads();
   mm_row_c<Real, DP, NC>(SAe + row * LD, S2, c0, t1);   // P = A_e B, stored transposed in S3
@@ -283,14 +283,14 @@ __global__ void __launch_bounds__(64) k_c2_tables(KP<Real> p, Cov2Args<Real> a) 
     else predict(SPm, SXg, pp);
 #pragma unroll
     for (int j = 0; j < DP; ++j) pp[j] += (j == lane && j < p.d) ? p.r : (Real)0;
-    chol_shfl<Real, DP>(pp, LSg, nullptr, nullptr, vdg, nullptr, p.d, lane, &bad);
+    chol_la<Real, DP>(pp, LSg, nullptr, nullptr, vdg, nullptr, p.d, lane, &bad);
     double lg = (lane < p.d) ? -log((double)vdg[lane]) : 0.0;
     lg = warp_sum<double>(lg);
     if (lane == 0) a.ldt[t] = 2.0 * lg;
     Real r[DP];
 #pragma unroll
     for (int j = 0; j < DP; ++j) r[j] = (j == lane) ? (Real)1 : (Real)0;
-    fsolve_rot<Real, DP, true>(LSg, vdg, r, SW, lane);
+    fsolve_pf<Real, DP, true>(LSg, vdg, r, SW, lane);
     __syncwarp();
     Real kr[DP];
     mm_col<Real, DP>(SW, row, SW, kr);
@@ -312,12 +312,12 @@ __global__ void __launch_bounds__(64) k_c2_tables(KP<Real> p, Cov2Args<Real> a) 
       }
       Real pp[DP];
       predict(SP, SY, pp);   // SY: scratch until Y is formed
-      chol_shfl<Real, DP>(pp, LSb, nullptr, LRb, vdb, nullptr, p.d, lane, &bad);
+      chol_la<Real, DP>(pp, LSb, nullptr, LRb, vdb, nullptr, p.d, lane, &bad);
       st_row<Real, DP>(SX, row, xr, act);
       __syncwarp();
       Real rr[DP];
       ld_col<Real, DP>(SX, row, rr);
-      fsolve_rot<Real, DP, true>(LSb, vdb, rr, SY, lane);   // Y = L_P^{-1} X (column `lane`)
+      fsolve_pf<Real, DP, true>(LSb, vdb, rr, SY, lane);   // Y = L_P^{-1} X (column `lane`)
       __syncwarp();
       ld_row<Real, DP>(SP, row, sig);
       mm_col<Real, DP, true, true>(SY, row, SY, sig);       // Sigma = P^f - Y^T Y
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(64) k_c2_tables(KP<Real> p, Cov2Args<Real> a) 
       if (act) st_vec<Real, DP>(a.tab + ((long)TG * p.nT + t) * DD + row * DP, z);
       ld_row<Real, DP>(SP, row, sig);
     }
-    chol_shfl<Real, DP>(sig, LSb, SLr, nullptr, vdb2, nullptr, p.d, lane, &bad);
+    chol_la<Real, DP>(sig, LSb, SLr, nullptr, vdb2, nullptr, p.d, lane, &bad);
     Real lr[DP];
     ld_row<Real, DP>(SLr, row, lr);
     if (act) st_vec<Real, DP>(a.tab + ((long)TLS * p.nT + t) * DD + row * DP, lr);

@@ -431,14 +431,15 @@ __device__ T chol_rot(T (&a)[DP], T* LS, T* LRow, T* LR, T* inv_diag, const T* e
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 
-// chol_rot with the pivot column broadcast by warp shuffles instead of a
-// shared-memory round trip: no __syncwarp() inside the loop, and the pivot's
-// reciprocal square root from one rsqrt (the factor's diagonal is the pivot
-// times it). Same inputs, outputs and padding rules as chol_rot; the slots are
-// only written, never read back, so the loop carries no shared-memory latency.
+// chol_rot with a one-column lookahead and a reciprocal square root: the
+// pivot of column k + 1 is updated and broadcast (two shuffles) before the
+// rest of column k's rank-1 update, whose shared-memory row load and fused
+// multiply-adds then hide the broadcast's latency, and the pivot's
+// reciprocal square root comes from one rsqrt (the diagonal of the factor is
+// the pivot times it). Same inputs, outputs and padding rules as chol_rot.
 template <typename T, int DP>
-__device__ T chol_shfl(T (&a)[DP], T* LS, T* LRow, T* LR, T* inv_diag, const T* eps, int d,
-                       int lane, int* bad) {
+__device__ T chol_la(T (&a)[DP], T* LS, T* LRow, T* LR, T* inv_diag, const T* eps, int d, int lane,
+                     int* bad) {
   constexpr int LD = Lay<T, DP>::LD;
   const bool act = lane < DP;
   T acc = 0;
@@ -449,15 +450,16 @@ __device__ T chol_shfl(T (&a)[DP], T* LS, T* LRow, T* LR, T* inv_diag, const T* 
     if (LR) st_vec<T, DP>(LR + lane * LD, z);
     if (LRow) st_vec<T, DP>(LRow + lane * LD, z);
   }
+  // pivot of column 0
+  T pk = __shfl_sync(FULL_MASK, a[0], 0);
+  T piv = (T)1, inv = (T)1;
+  if (0 < d) {
+    if (!(pk > (T)0) || !(pk < (T)INFINITY)) { *bad = 1; pk = (T)1; }
+    inv = rsqrt_t(pk);
+    piv = pk * inv;
+  }
 #pragma unroll 1
   for (int k = 0; k < DP; ++k) {
-    T akk = __shfl_sync(FULL_MASK, a[0], k);
-    T piv = (T)1, inv = (T)1;
-    if (k < d) {
-      if (!(akk > (T)0) || !(akk < (T)INFINITY)) { *bad = 1; akk = (T)1; }
-      inv = rsqrt_t(akk);
-      piv = akk * inv;
-    }
     const T l = (lane == k) ? piv : ((lane > k) ? a[0] * inv : (T)0);
     if (act && lane >= k) {
       LS[k * LD + (lane - k)] = l;
@@ -466,16 +468,59 @@ __device__ T chol_shfl(T (&a)[DP], T* LS, T* LRow, T* LR, T* inv_diag, const T* 
     }
     if (lane == 0) inv_diag[k] = inv;
     if (eps) acc = fma(l, eps[k], acc);
-    // row update a[i][k+1+j] -= L[i][k] L[k+1+j][k]; entries past DP-1-k are dead
+    // lookahead: entry (i, k + 1) and the pivot of column k + 1
+    const T lk1 = __shfl_sync(FULL_MASK, l, (k + 1) & 31);
+    const T a1 = fma(-l, lk1, a[1]);
+    T pn = __shfl_sync(FULL_MASK, a1, (k + 1) & 31);
+    __syncwarp();
+    T lk[DP];
+    ld_vec<T, DP>(LS + k * LD, lk);
 #pragma unroll
-    for (int j = 0; j < DP - 1; ++j) {
-      const T lj = __shfl_sync(FULL_MASK, l, (k + 1 + j) & 31);
-      a[j] = fma(-l, lj, a[j + 1]);
-    }
+    for (int j = 1; j < DP - 1; ++j) a[j] = fma(-l, lk[j + 1], a[j + 1]);
+    a[0] = a1;
     a[DP - 1] = (T)0;
+    piv = (T)1;
+    inv = (T)1;
+    if (k + 1 < d) {
+      if (!(pn > (T)0) || !(pn < (T)INFINITY)) { *bad = 1; pn = (T)1; }
+      inv = rsqrt_t(pn);
+      piv = pn * inv;
+    }
   }
   __syncwarp();
   return acc;
+}
+
+// Forward solve L y = r as fsolve_rot, with the factor's next row loaded while
+// the current one is applied (two register buffers, two steps per trip).
+template <typename T, int DP, bool AS_COLUMN>
+__device__ __forceinline__ void fsolve_pf(const T* LS, const T* inv_diag, T (&r)[DP], T* Y, int lane) {
+  constexpr int LD = Lay<T, DP>::LD;
+  static_assert(DP % 2 == 0, "two steps per trip");
+  const bool act = lane < DP;
+  T l0[DP], l1[DP];
+  ld_vec<T, DP>(LS, l0);
+#pragma unroll 1
+  for (int k = 0; k < DP; k += 2) {
+    ld_vec<T, DP>(LS + (k + 1) * LD, l1);
+    const T y0 = r[0] * inv_diag[k];
+    if (act) {
+      if (AS_COLUMN) Y[k * LD + lane] = y0;
+      else Y[lane * LD + k] = y0;
+    }
+#pragma unroll
+    for (int j = 0; j < DP - 1; ++j) r[j] = fma(-y0, l0[j + 1], r[j + 1]);
+    r[DP - 1] = (T)0;
+    if (k + 2 < DP) ld_vec<T, DP>(LS + (k + 2) * LD, l0);
+    const T y1 = r[0] * inv_diag[k + 1];
+    if (act) {
+      if (AS_COLUMN) Y[(k + 1) * LD + lane] = y1;
+      else Y[lane * LD + k + 1] = y1;
+    }
+#pragma unroll
+    for (int j = 0; j < DP - 1; ++j) r[j] = fma(-y1, l1[j + 1], r[j + 1]);
+    r[DP - 1] = (T)0;
+  }
 }
 
 // Two independent factorizations interleaved (ILP); outputs as in chol_rot.
