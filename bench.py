@@ -472,6 +472,73 @@ def _oracle_replay(args):
     return ref["log_alpha"], ref["accepted"], ref["x_star"], sd
 
 
+def _oracle_wide_step(args):
+    """The oracle's step of chain `chain` (iteration 0, from the workload's initial state)
+    on the d = 128 SV workload with step size delta, with everything the error report of
+    the wide line compares: log alpha, the decision, ytilde, log Z, m^f and its sd, x* and
+    its smoothing sd."""
+    import numpy as np
+    from oracle import kalman, mcmc
+    d, T, C, delta, chain = args
+    from paper_2303_00301_gb300 import workloads as W
+    wl = W.stochastic_volatility(d=d, T=T, n_chains=C, delta=delta)
+    model = dict(m0=wl.m0, P0=wl.P0, F=wl.F, b=wl.b, Q=wl.Q, emission=mcmc.SVEmission(wl.y, wl.mask))
+    ref = mcmc.aux_step_philox(wl.x_init[chain], model, wl.delta, wl.mcmc_seed, chain, 0)
+    kf = ref["kf"]
+    _, Ps = kalman.rts_smoother(kf, wl.F)
+    sd = lambda P: np.sqrt(np.maximum(np.einsum("tii->ti", P), 0.0))
+    return dict(log_alpha=ref["log_alpha"], accepted=ref["accepted"], ytilde=ref["ytilde"],
+                logZ=kf["logZ"], mf=kf["mf"], sd_f=sd(kf["Pf"]), x_star=ref["x_star"], sd_s=sd(Ps))
+
+
+def wide_error_block(refs, wl, dtype, delta, chains):
+    """Errors of one dtype's wide path against the FP64 oracle on sampled chains: the
+    step's |d log alpha| and MH decision (iteration 0 from the initial state), log Z and
+    m^f of aux_loglik on the oracle's ytilde, and x* of aux_sample_path on the same ytilde
+    with the step's backward noise; element-wise errors scaled by (|oracle| + sd)."""
+    import numpy as np
+    import torch
+    from oracle import philox
+    from paper_2303_00301_gb300 import AuxKalman
+    from paper_2303_00301_gb300 import workloads as W
+    C, T, d = wl.n_chains, wl.T, wl.d
+    ws = W.stochastic_volatility(d=d, T=T, n_chains=C, delta=delta)
+    h = AuxKalman(ws, dtype=dtype, mode="cached")
+    x = torch.tensor(ws.x_init, dtype=torch.float32, device="cuda")
+    la = torch.zeros(C, dtype=torch.float64, device="cuda")
+    h.step(x, 1, iter0=0, log_alpha=la)
+    yt = np.zeros((C, T, d))
+    for c in chains:
+        yt[c] = refs[c]["ytilde"]
+    ytg = torch.tensor(yt, dtype=torch.float32, device="cuda")
+    logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
+    mf = torch.zeros((C, T, d), dtype=torch.float32, device="cuda")
+    h.loglik(ytg, logZ, mf)
+    xs = torch.zeros((C, T, d), dtype=torch.float32, device="cuda")
+    h.sample_path(ytg, xs, eps=None, iteration=0)
+    torch.cuda.synchronize()
+    rc = h.status()[0]
+    h.close()
+    lag, lzg, mfg, xsg = la.cpu().numpy(), logZ.cpu().numpy(), mf.double().cpu().numpy(), xs.double().cpu().numpy()
+    out = {"dla": [], "logZ_rel": [], "mf_elem": [], "x_star_elem": [], "decision_mismatches": 0}
+    for c in chains:
+        r = refs[c]
+        out["dla"].append(abs(lag[c] - r["log_alpha"]))
+        lu = float(np.log(philox.mh_uniform(ws.mcmc_seed, c, 0)))
+        if bool(lu < lag[c]) != bool(r["accepted"]):
+            out["decision_mismatches"] += 1
+        out["logZ_rel"].append(abs(lzg[c] - r["logZ"]) / abs(r["logZ"]))
+        out["mf_elem"].append(float(np.max(np.abs(mfg[c] - r["mf"]) / (np.abs(r["mf"]) + r["sd_f"]))))
+        out["x_star_elem"].append(float(np.max(np.abs(xsg[c] - r["x_star"]) / (np.abs(r["x_star"]) + r["sd_s"]))))
+    return {"against": "FP64 oracle (iteration 0 from the initial state; aux_loglik and aux_sample_path "
+                       "on the oracle's ytilde with the step's backward noise)",
+            "chains": list(chains), "status": int(rc),
+            "abs_dlog_alpha_max": float(max(out["dla"])), "mh_decision_mismatches": out["decision_mismatches"],
+            "logZ_rel_max": float(max(out["logZ_rel"])),
+            "mf_max_err_over_abs_plus_sd": float(max(out["mf_elem"])),
+            "x_star_max_err_over_abs_plus_sd": float(max(out["x_star_elem"]))}
+
+
 def fp32_error_block(name, wl, w, mode, block_len, pool, chains=(0, 9, 22, 31), steps=16):
     """Error of the FP32 GPU path against the FP64 oracle on sampled chains: each GPU
     step is replayed on the oracle from the GPU's state before it, on the same Philox
@@ -621,13 +688,17 @@ def run_spatial(args, flush, stream):
     return out
 
 
-def run_wide(args, flush, stream, peaks):
+def run_wide(args, flush, stream, peaks, pool=None):
     """The mixed-precision workload's shape (SV, d = 128, T = 4096, 16 chains) on the wide
-    table-mode kernels, single precision throughout (FP64 only in the log-determinants and
-    the likelihood sums): delta adapted on the device to 50 % acceptance during warm-up (the
-    covariance pass reruns at every adaptation step), then frozen; cached covariance tables;
-    the MH iteration captured in a CUDA graph and replayed, L2 flushed before each replay.
-    The shared mode (the covariance pass rerun every step) is timed beside it, eager."""
+    table-mode kernels, in two forms: single precision throughout ("f32": FP64 only in the
+    log-determinants and the likelihood sums) and mixed precision ("mixed": the covariance
+    pass's products on the tensor cores in split TF32 with FP32 accumulation, the
+    factorisations of the element operator in FP64). delta is adapted on the device to 50 %
+    acceptance during warm-up of the f32 form (the covariance pass reruns at every
+    adaptation step) and frozen for both; cached covariance tables; the MH iteration
+    captured in a CUDA graph and replayed, L2 flushed before each replay. The shared mode
+    (the covariance pass rerun every step) is timed beside it, eager. With a process pool,
+    each form's error against the FP64 oracle on two sampled chains is reported."""
     import numpy as np
     import torch
     from paper_2303_00301_gb300 import AuxKalman
@@ -635,81 +706,99 @@ def run_wide(args, flush, stream, peaks):
     from paper_2303_00301_gb300 import workloads as W
     d, T, C = 128, args.wide_T, 16
     wl = W.stochastic_volatility(d=d, T=T, n_chains=C)
-    h = AuxKalman(wl, dtype="f32", mode="cached", block_len=args.wide_L)
-    x = torch.tensor(wl.x_init, dtype=torch.float32, device="cuda")
+    delta = wl.delta
     n_adapt = args.wide_adapt
     if n_adapt > 0:
+        h = AuxKalman(wl, dtype="f32", mode="cached", block_len=args.wide_L)
+        x = torch.tensor(wl.x_init, dtype=torch.float32, device="cuda")
         h.adapt_delta(True, target=0.5, gain=1.0)
         h.step(x, n_adapt, iter0=0)
         h.adapt_delta(False)
-    delta = h.delta()
-    it = n_adapt
-    h.step(x, 3, iter0=it)
-    it += 3
-    acc = torch.zeros(C, dtype=torch.int32, device="cuda")
-    n = max(args.steps // 10, 30)
-    B.aux_set_profiling(h.handle, True)
-    for k in range(n):
-        flush.zero_()
-        h.step(x, 1, iter0=it + k, accept_count=acc)
-    torch.cuda.synchronize()
-    B.aux_set_profiling(h.handle, False)
-    prof = B.aux_read_profile(h.handle)
-    it += n
-    rate = acc.float().mean().item() / n
-    h.device_iteration(True, it)
-    g = h.capture(x, 1)
-    g.replay()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
-    for k in range(n):
-        flush.zero_()
-        ev[k][0].record(stream)
-        g.replay()
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / n
-    h.device_iteration(False)
-    del g
-    rc = h.status()[0]
-    h.close()
-    # the shared mode: the covariance pass every step
-    ws = W.stochastic_volatility(d=d, T=T, n_chains=C, delta=delta)
-    hs = AuxKalman(ws, dtype="f32", mode="shared", block_len=args.wide_L)
-    xs = torch.tensor(ws.x_init, dtype=torch.float32, device="cuda")
-    hs.step(xs, 2, iter0=0)
-    B.aux_set_profiling(hs.handle, True)
-    ns = 5
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ns)]
-    for k in range(ns):
-        flush.zero_()
-        evs[k][0].record(stream)
-        hs.step(xs, 1, iter0=2 + k)
-        evs[k][1].record(stream)
-    torch.cuda.synchronize()
-    B.aux_set_profiling(hs.handle, False)
-    profs = B.aux_read_profile(hs.handle)
-    ms_sh = sum(a.elapsed_time(b) for a, b in evs) / ns
-    hs.close()
+        delta = h.delta()
+        h.close()
+    chains = (0, C - 1)
+    refs = None
+    if pool is not None:
+        res = pool.map(_oracle_wide_step, [(d, T, C, delta, c) for c in chains], chunksize=1)
+        refs = dict(zip(chains, res))
     L = args.wide_L or math.ceil(math.sqrt(T))
     nb = (T + L - 1) // L
-    w = {"dtype": "f32"}
-    dom = max((k for k in prof if prof[k][1]), key=lambda k: prof[k][0])
-    line = roofline_line("cached", dom, prof, w, d, T, C, nb, T, True, 4, peaks, n,
-                         "dominant kernel (cached tables, per-chain means)")
-    if line:
-        line["kernel"] = {"reduce": "k_wmf_reduce", "apply": "k_wmf_apply", "scan": "k_wmean_cross",
-                          "backward": "k_wmean_cross + k_wmb_apply"}.get(dom, dom)
-        line["traffic"] = dram_traffic(f"{line['kernel']}@sv_d{d}_T{T}_C{C}")
-    return {"workload": f"sv_d{d}_T{T}_C{C} (SV, d = {d}, T = {T}, {C} chains)",
-            "precision": "FP32 tables and means; FP64 log-determinants and likelihood sums",
-            "mode": "cached", "block_len": L, "launch": "CUDA graph replay", "ms_per_step": ms,
-            "value": C * T / (ms / 1e3), "unit": UNIT, "delta": delta, "delta_adaptation_steps": n_adapt,
-            "accept_rate": rate, "status": int(rc), "steps": n,
-            "kernel_ms_per_step": {k: v[0] / n for k, v in prof.items() if v[1]},
-            "roofline": line,
-            "shared_mode": {"ms_per_step": ms_sh, "value": C * T / (ms_sh / 1e3), "launch": "eager",
-                            "kernel_ms_per_step": {k: v[0] / ns for k, v in profs.items() if v[1]}}}
+    n = max(args.steps // 10, 30)
+    out = {}
+    for dt in ("f32", "mixed"):
+        wd = W.stochastic_volatility(d=d, T=T, n_chains=C, delta=delta)
+        h = AuxKalman(wd, dtype=dt, mode="cached", block_len=args.wide_L)
+        x = torch.tensor(wd.x_init, dtype=torch.float32, device="cuda")
+        it = n_adapt
+        h.step(x, 3, iter0=it)
+        it += 3
+        acc = torch.zeros(C, dtype=torch.int32, device="cuda")
+        B.aux_set_profiling(h.handle, True)
+        for k in range(n):
+            flush.zero_()
+            h.step(x, 1, iter0=it + k, accept_count=acc)
+        torch.cuda.synchronize()
+        B.aux_set_profiling(h.handle, False)
+        prof = B.aux_read_profile(h.handle)
+        it += n
+        rate = acc.float().mean().item() / n
+        h.device_iteration(True, it)
+        g = h.capture(x, 1)
+        g.replay()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for k in range(n):
+            flush.zero_()
+            ev[k][0].record(stream)
+            g.replay()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / n
+        h.device_iteration(False)
+        del g
+        rc = h.status()[0]
+        h.close()
+        # the shared mode: the covariance pass every step
+        hs = AuxKalman(wd, dtype=dt, mode="shared", block_len=args.wide_L)
+        xs = torch.tensor(wd.x_init, dtype=torch.float32, device="cuda")
+        hs.step(xs, 2, iter0=0)
+        B.aux_set_profiling(hs.handle, True)
+        ns = 5
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ns)]
+        for k in range(ns):
+            flush.zero_()
+            evs[k][0].record(stream)
+            hs.step(xs, 1, iter0=2 + k)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        B.aux_set_profiling(hs.handle, False)
+        profs = B.aux_read_profile(hs.handle)
+        ms_sh = sum(a.elapsed_time(b) for a, b in evs) / ns
+        hs.close()
+        w = {"dtype": "f32"}
+        dom = max((k for k in prof if prof[k][1]), key=lambda k: prof[k][0])
+        line = roofline_line("cached", dom, prof, w, d, T, C, nb, T, True, 4, peaks, n,
+                             "dominant kernel (cached tables, per-chain means)")
+        if line:
+            line["kernel"] = {"reduce": "k_wmf_reduce", "apply": "k_wmf_apply", "scan": "k_wmean_cross",
+                              "backward": "k_wmean_cross + k_wmb_apply"}.get(dom, dom)
+            line["traffic"] = dram_traffic(f"{line['kernel']}@sv_d{d}_T{T}_C{C}")
+        prec = ("FP32 tables and means; FP64 log-determinants and likelihood sums" if dt == "f32" else
+                "covariance-pass products on the tensor cores (split TF32, FP32 accumulation); FP64 "
+                "factorisations of C_i and N = I + U^T J U and inverse of chol(N); FP32 tables and means; "
+                "FP64 log-determinants and likelihood sums")
+        out[dt] = {"precision": prec, "mode": "cached", "launch": "CUDA graph replay", "ms_per_step": ms,
+                   "value": C * T / (ms / 1e3), "unit": UNIT, "accept_rate": rate, "status": int(rc), "steps": n,
+                   "kernel_ms_per_step": {k: v[0] / n for k, v in prof.items() if v[1]},
+                   "roofline": line,
+                   "shared_mode": {"ms_per_step": ms_sh, "value": C * T / (ms_sh / 1e3), "launch": "eager",
+                                   "kernel_ms_per_step": {k: v[0] / ns for k, v in profs.items() if v[1]}},
+                   "error_vs_fp64_oracle": (wide_error_block(refs, wl, dt, delta, chains) if refs else None)}
+    res = {"workload": f"sv_d{d}_T{T}_C{C} (SV, d = {d}, T = {T}, {C} chains)", "block_len": L,
+           "delta": delta, "delta_adaptation_steps": n_adapt}
+    res.update(out["f32"])
+    res["mixed_precision"] = out["mixed"]
+    return res
 
 
 def run_batched(args, flush, stream, n_streams=32):
@@ -955,7 +1044,7 @@ def run_ours(args):
         spatial = run_spatial(args, flush, stream)
         batched = run_batched(args, flush, stream)
         pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-        wide = run_wide(args, flush, stream, json.load(open(pk)) if os.path.exists(pk) else {})
+        wide = run_wide(args, flush, stream, json.load(open(pk)) if os.path.exists(pk) else {}, pool)
 
     # end to end through the public API from pinned host buffers
     x_host = torch.tensor(wl.x_init, dtype=tdt).pin_memory()
@@ -1118,13 +1207,20 @@ def main():
         print(json.dumps(run_spatial(args, flush, torch.cuda.current_stream())), flush=True)
         return
     if args.wide_only:
+        pool = None
+        if not args.no_cpu_baseline:   # the oracle's error reference, started before any CUDA call
+            _cpu_env()
+            import multiprocessing as mp
+            pool = mp.get_context("spawn").Pool(2)
         import torch
         from paper_2303_00301_gb300 import build
         build.build()
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
         peaks = json.load(open(pp)) if os.path.exists(pp) else {}
-        print(json.dumps(run_wide(args, flush, torch.cuda.current_stream(), peaks)), flush=True)
+        print(json.dumps(run_wide(args, flush, torch.cuda.current_stream(), peaks, pool)), flush=True)
+        if pool is not None:
+            pool.close()
         return
     if args.batched_only:
         import torch

@@ -65,6 +65,18 @@ extern "C" {
 /* compute types */
 #define AUX_F32 0
 #define AUX_F64 1
+/* Mixed precision (33 <= d_x <= 128, the table modes; see "Wide state
+ * dimensions"): buffers, tables and per-chain means in FP32 as AUX_F32; the
+ * covariance pass's dense products on the tensor cores with TF32 operands and
+ * FP32 accumulation, each product split into three TF32 products
+ * (a_hi b_hi + a_hi b_lo + a_lo b_hi, x_hi = tf32(x), x_lo = tf32(x - x_hi));
+ * the factorisations in the element operator's (I + C_i J_j) solve, chol(C_i)
+ * and chol(N), N = I + U^T J_j U, and the inverse of chol(N), in FP64; log
+ * determinants and likelihood sums in FP64 as in every dtype. The device
+ * buffers passed to the entry points are float. Other sizes, the per-chain
+ * mode, the factorised prior and aux_loglik_noalloc return AUX_E_UNSUPPORTED
+ * (aux_loglik_noalloc: AUX_E_INVALID_ARG). */
+#define AUX_MIXED 2
 
 /* execution modes (aux_set_mode) */
 #define AUX_MODE_PER_CHAIN  0  /* every chain runs its own covariance recursion (default) */
@@ -80,7 +92,7 @@ extern "C" {
  * All arrays are HOST pointers to double, copied by aux_init_model. */
 typedef struct {
   int32_t abi_version;   /* AUX_ABI_VERSION */
-  int32_t dtype;         /* AUX_F32 | AUX_F64 */
+  int32_t dtype;         /* AUX_F32 | AUX_F64 | AUX_MIXED */
   int32_t d_x;           /* state dimension: 1..128 (AUX_F32; 33..128 in the table
                             modes only, see "Wide state dimensions"), 1..16 (AUX_F64);
                             1..1024 with AUX_EMIS_STUDENT_T (factorised prior, see below) */

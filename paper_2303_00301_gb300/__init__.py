@@ -32,7 +32,9 @@ class AuxKalman:
     (``aux_set_filter_form``): "covariance" or "square_root" (per chain with
     the first-order proposal and the scan sampler, or the covariance pass of
     the table modes). State dimensions 33..128 (FP32) run the table modes only
-    ("shared" or "cached"), first order, scan sampler, covariance form.
+    ("shared" or "cached"), first order, scan sampler, covariance form; there
+    ``dtype="mixed"`` runs the covariance pass's products on the tensor cores
+    (split TF32, FP32 accumulation) with its factorisations in FP64.
     """
 
     def __init__(self, workload, dtype="f32", seed=None, n_chains=None, block_len=0, stream=None,
@@ -43,8 +45,11 @@ class AuxKalman:
         self.wl = workload
         self.C = int(n_chains if n_chains is not None else workload.n_chains)
         self.T, self.d = workload.T, workload.d
-        self.dtype_code = b.AUX_F32 if dtype == "f32" else b.AUX_F64
-        self.torch_dtype = torch.float32 if dtype == "f32" else torch.float64
+        codes = {"f32": b.AUX_F32, "f64": b.AUX_F64, "mixed": b.AUX_MIXED}
+        if dtype not in codes:
+            raise ValueError(f"dtype must be one of {sorted(codes)}")
+        self.dtype_code = codes[dtype]
+        self.torch_dtype = torch.float64 if dtype == "f64" else torch.float32
         self.seed = workload.mcmc_seed if seed is None else seed
         self.handle = b.aux_init_model(
             d_x=self.d, T=self.T, n_chains=self.C, m0=workload.m0, P0=workload.P0,

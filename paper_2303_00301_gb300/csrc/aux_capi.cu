@@ -158,7 +158,7 @@ int upload_model(aux_model* m, const aux_model_desc* d, const std::vector<double
 int validate_desc(const aux_model_desc* desc, std::vector<double>& Ryinv) {
   if (!desc) return AUX_E_INVALID_ARG;
   if (desc->abi_version != AUX_ABI_VERSION) return AUX_E_INVALID_ARG;
-  if (desc->dtype != AUX_F32 && desc->dtype != AUX_F64) return AUX_E_INVALID_ARG;
+  if (desc->dtype != AUX_F32 && desc->dtype != AUX_F64 && desc->dtype != AUX_MIXED) return AUX_E_INVALID_ARG;
   if (desc->emis_kind != AUX_EMIS_LINEAR_GAUSSIAN && desc->emis_kind != AUX_EMIS_SV &&
       desc->emis_kind != AUX_EMIS_STUDENT_T)
     return AUX_E_INVALID_ARG;
@@ -171,7 +171,7 @@ int validate_desc(const aux_model_desc* desc, std::vector<double>& Ryinv) {
   if (!(desc->delta > 0.0) || !std::isfinite(desc->delta)) return AUX_E_INVALID_ARG;
   if (st && (!(desc->nu > 0.0) || !std::isfinite(desc->nu))) return AUX_E_INVALID_ARG;
   if (st) {
-    if (d > 1024) return AUX_E_UNSUPPORTED;
+    if (d > 1024 || desc->dtype == AUX_MIXED) return AUX_E_UNSUPPORTED;
     for (int i = 0; i < d; ++i)   // the factorised path needs diagonal F, Q, P0
       for (int j = 0; j < d; ++j)
         if (i != j && (desc->F[i * d + j] != 0.0 || desc->Q[i * d + j] != 0.0 || desc->P0[i * d + j] != 0.0))
@@ -180,6 +180,7 @@ int validate_desc(const aux_model_desc* desc, std::vector<double>& Ryinv) {
     const int DP = pick_dp(d);
     if (DP == 0) return AUX_E_UNSUPPORTED;
     if (desc->dtype == AUX_F64 && DP > 16) return AUX_E_UNSUPPORTED;
+    if (desc->dtype == AUX_MIXED && DP <= 32) return AUX_E_UNSUPPORTED;   // the wide widths only
   }
   if ((long long)C * T * d > (1LL << 31)) return AUX_E_UNSUPPORTED;
   const size_t dd = (size_t)d * d;
@@ -380,7 +381,7 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
   m->fdiag = diag_flag(desc);
   m->diag_hess = hess_diag_flag(desc);
   m->stream = (cudaStream_t)stream;
-  m->esz = desc->dtype == AUX_F32 ? sizeof(float) : sizeof(double);
+  m->esz = desc->dtype == AUX_F64 ? sizeof(double) : sizeof(float);   // AUX_MIXED stores FP32
   cudaGetDevice(&m->device);
   if (cudaDeviceGetAttribute(&m->n_sm, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess ||
       m->n_sm < 1) {
@@ -393,10 +394,11 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
     *out = m;
     return AUX_OK;
   }
-  m->ops = desc->dtype == AUX_F32 ? (DP > 32 ? aux_ops_f32_wide(DP) : aux_ops_f32(DP)) : aux_ops_f64(DP);
+  if (desc->dtype == AUX_MIXED) m->ops = aux_ops_mixed_wide(DP);
+  else m->ops = desc->dtype == AUX_F32 ? (DP > 32 ? aux_ops_f32_wide(DP) : aux_ops_f32(DP)) : aux_ops_f64(DP);
   if (!m->ops) { release(m); return AUX_E_UNSUPPORTED; }
 
-  int rc = desc->dtype == AUX_F32 ? upload_model<float>(m, desc, Ryinv, true)
+  int rc = desc->dtype != AUX_F64 ? upload_model<float>(m, desc, Ryinv, true)
                                   : upload_model<double>(m, desc, Ryinv, true);
   std::vector<double> gc;
   m->grad_ok = theta_constants(desc, gc) ? 1 : 0;
@@ -628,7 +630,7 @@ int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {
   if (vrc) return vrc;
   if (m->order == AUX_PROPOSAL_SECOND_ORDER && !hess_diag_flag(desc)) return AUX_E_UNSUPPORTED;
   if (cudaStreamSynchronize(m->stream) != cudaSuccess) return AUX_E_CUDA;
-  const int rc = m->dtype == AUX_F32 ? upload_model<float>(m, desc, Ryinv, false)
+  const int rc = m->dtype != AUX_F64 ? upload_model<float>(m, desc, Ryinv, false)
                                      : upload_model<double>(m, desc, Ryinv, false);
   if (rc) return rc;
   m->delta = desc->delta;

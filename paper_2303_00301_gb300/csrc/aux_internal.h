@@ -136,6 +136,7 @@ int aux_fact_sample_path(aux_model *m, const void *yt, const void *eps, uint64_t
 const AuxOps *aux_ops_f32(int DP);
 const AuxOps *aux_ops_f64(int DP);
 const AuxOps *aux_ops_f32_wide(int DP);   // padded dimensions 64 and 128 (aux_wide.cu)
+const AuxOps *aux_ops_mixed_wide(int DP); // the same, mixed precision (AUX_MIXED)
 size_t aux_wide_scratch_elems(int DP, int n_sm);   // per-CTA scratch of the wide covariance pass
 
 // element counts of the per-block buffers for a padded dimension DP

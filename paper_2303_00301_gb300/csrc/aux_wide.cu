@@ -7,7 +7,10 @@
 
 namespace auxk {
 
-template <typename Real, int DP>
+// MX: the mixed-precision form (AUX_MIXED): the covariance pass's products on
+// the tensor cores in split TF32 with FP32 accumulation, the factorisations of
+// C_i and N = I + U^T J_e U in the doubling in FP64; the means are unchanged.
+template <typename Real, int DP, bool MX>
 struct WOps {
   using Z = WSz<Real, DP>;
   static constexpr long DD = Z::DD;
@@ -17,10 +20,10 @@ struct WOps {
 #define AUX_W_ATTR(K, S)                                                             \
     if ((e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(S))) != cudaSuccess) \
       return AUX_E_CUDA;
-    AUX_W_ATTR((k_w_elem<Real, DP>), Z::SMEM)
-    AUX_W_ATTR((k_w_double<Real, DP>), Z::SMEM)
-    AUX_W_ATTR((k_w_epi<Real, DP>), Z::SMEM)
-    AUX_W_ATTR((k_w_prod<Real, DP>), Z::SMEM)
+    AUX_W_ATTR((k_w_elem<Real, DP, MX>), Z::SMEM)
+    AUX_W_ATTR((k_w_double<Real, DP, MX>), MX ? Z::SMEM_MX : Z::SMEM)
+    AUX_W_ATTR((k_w_epi<Real, DP, MX>), Z::SMEM)
+    AUX_W_ATTR((k_w_prod<Real, DP, MX>), Z::SMEM)
     AUX_W_ATTR((k_wmf_reduce<Real, DP>), Z::MSMEM)
     AUX_W_ATTR((k_wmf_apply<Real, DP>), Z::MSMEM)
     AUX_W_ATTR((k_wmb_apply<Real, DP>), Z::MSMEM)
@@ -42,7 +45,7 @@ struct WOps {
     {
       ProfScope ps(m, PK_COV_REDUCE, st);
       cudaMemsetAsync(m->cov_status, 0, sizeof(int32_t), st);
-      k_w_elem<Real, DP><<<1, WT, Z::SMEM, st>>>(p, a);
+      k_w_elem<Real, DP, MX><<<1, WT, Z::SMEM, st>>>(p, a);
     }
     Real* gk = a.gk;
     Real* gk2 = a.gk + 3 * DD;
@@ -50,16 +53,17 @@ struct WOps {
       ProfScope ps(m, PK_COV_SCAN, st);
       const int cnt = std::min(pow2, m->T - pow2);
       const int sq = 2 * pow2 < m->T ? 1 : 0;
-      k_w_double<Real, DP><<<std::min(cnt + sq, W_SLOTS_PER_SM * m->n_sm), WT, Z::SMEM, st>>>(p, a, pow2, cnt, sq, gk, gk2);
+      k_w_double<Real, DP, MX><<<std::min(cnt + sq, W_SLOTS_PER_SM * m->n_sm), WT, MX ? Z::SMEM_MX : Z::SMEM, st>>>(
+          p, a, pow2, cnt, sq, gk, gk2);
       std::swap(gk, gk2);
     }
     {
       ProfScope ps(m, PK_COV_APPLY, st);
-      k_w_epi<Real, DP><<<std::min(m->T + 1, W_SLOTS_PER_SM * m->n_sm), WT, Z::SMEM, st>>>(p, a);
+      k_w_epi<Real, DP, MX><<<std::min(m->T + 1, W_SLOTS_PER_SM * m->n_sm), WT, Z::SMEM, st>>>(p, a);
     }
     {
       ProfScope ps(m, PK_COV_PRODUCTS, st);
-      k_w_prod<Real, DP><<<std::min(m->nb, W_SLOTS_PER_SM * m->n_sm), WT, Z::SMEM, st>>>(p, a);
+      k_w_prod<Real, DP, MX><<<std::min(m->nb, W_SLOTS_PER_SM * m->n_sm), WT, Z::SMEM, st>>>(p, a);
     }
   }
 
@@ -204,8 +208,16 @@ size_t aux_wide_scratch_elems(int DP, int n_sm) {
 
 const AuxOps* aux_ops_f32_wide(int DP) {
   switch (DP) {
-    case 64: return auxk::WOps<float, 64>::table();
-    case 128: return auxk::WOps<float, 128>::table();
+    case 64: return auxk::WOps<float, 64, false>::table();
+    case 128: return auxk::WOps<float, 128, false>::table();
+    default: return nullptr;
+  }
+}
+
+const AuxOps* aux_ops_mixed_wide(int DP) {
+  switch (DP) {
+    case 64: return auxk::WOps<float, 64, true>::table();
+    case 128: return auxk::WOps<float, 128, true>::table();
     default: return nullptr;
   }
 }

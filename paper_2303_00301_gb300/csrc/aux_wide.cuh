@@ -46,6 +46,16 @@ constexpr int W_SCR = 8;         // scratch matrices per slot
 // chains per thread in the means kernels (8 chains per CTA at DP = 128, 16 at 64)
 template <int DP> constexpr int WCPT = 4;
 
+// k-chunk and shared-memory layout of the tensor-core product (w_gemm_tc, below)
+constexpr int TCK = 32;   // k per staged chunk
+template <int DP> struct TcSz {
+  static constexpr int LK = TCK + 4;     // row stride of a chunk stored k-contiguous
+  static constexpr int LM = DP + 8;      // row stride of a chunk stored m/n-contiguous
+  static constexpr int CH = (DP * LK > TCK * LM ? DP * LK : TCK * LM);   // floats per operand chunk
+  static constexpr size_t SMEM = 2 * (size_t)CH * sizeof(float);
+  static constexpr int MT = DP / 64, NT = DP / 16;   // m16 and n8 tiles per warp
+};
+
 template <typename Real, int DP> struct WSz {
   static constexpr int LDS = DP + 1;                 // shared row stride (odd: column access is conflict-free)
   static constexpr int KC = 32;                      // k-chunk of w_gemm
@@ -57,7 +67,14 @@ template <typename Real, int DP> struct WSz {
   // one padded matrix (factor, inverted in place) or the two k-chunks of w_gemm; the
   // pivots (FP64) and a column (two CTAs per SM at DP = 128)
   static constexpr size_t GEMM = 2 * (size_t)KC * LDS;
-  static constexpr size_t SMEM = (FULL > GEMM ? FULL : GEMM) * sizeof(Real) + (2 * DP + 8) * sizeof(double);
+  // bytes of the working area: the factor slot, or the staged chunks of w_gemm / w_gemm_tc
+  static constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+  static constexpr size_t WORK = cmax(cmax(FULL * sizeof(Real), GEMM * sizeof(Real)), TcSz<DP>::SMEM);
+  static constexpr size_t SMEM = WORK + (2 * DP + 8) * sizeof(double);
+  // the mixed-precision doubling: the working area holds one FP64 slot (the
+  // factorisations of C_i and N); then the pivots and an FP64 column
+  static constexpr size_t WORK_MX = cmax(FULL * sizeof(double), TcSz<DP>::SMEM);
+  static constexpr size_t SMEM_MX = WORK_MX + (2 * DP + 8) * sizeof(double) + DP * sizeof(double);
   // matrix staging buffers of the means kernels (one copy in flight while one is read)
   static constexpr int NBUF = 2;
   // means: NBUF matrix staging buffers, three vector slots per chain, per-chain FP64 sums
@@ -138,6 +155,154 @@ __device__ void w_gemm(const Real* A, bool ta, const Real* B, bool tb, Real* C, 
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// The same product on the tensor cores (mixed precision, AUX_MIXED):
+// mma.sync m16n8k8 with TF32 operands and FP32 accumulation, each product
+// split into three TF32 products, a_hi b_hi + a_hi b_lo + a_lo b_hi with
+// x_hi = tf32(x) and x_lo = tf32(x - x_hi), so that the result keeps about
+// single-precision accuracy. The 8 warps tile the DP x DP output 4 x 2
+// (warp tile DP/4 x DP/2); k-chunks of TCK columns of op(A) and rows of op(B)
+// are staged by cp.async in the layout that makes the fragment loads
+// conflict-free: rows of length TCK (+4) when op(A) (op(B)) is read along k
+// in memory, rows of length DP (+8) otherwise. Same contract as w_gemm.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_of(x);
+  lo = tf32_of(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// stage chunk k0 of op(X) (X row-major DP x DP): k-contiguous rows (kmajor: element
+// (m, kk) at m * LK + kk, read from X[m][k0 + kk]) or m-contiguous rows (element
+// (kk, m) at kk * LM + m, read from X[k0 + kk][m])
+template <int DP>
+__device__ __forceinline__ void tc_stage(float* dst, const float* X, int k0, bool kmajor) {
+  using Z = TcSz<DP>;
+  if (kmajor) {
+    constexpr int CPR = TCK / 4;
+    for (int q = threadIdx.x; q < DP * CPR; q += WT) {
+      const int m = q / CPR, c = q % CPR;
+      cp_async16(dst + m * Z::LK + c * 4, X + (long)m * DP + k0 + c * 4);
+    }
+  } else {
+    constexpr int CPR = DP / 4;
+    for (int q = threadIdx.x; q < TCK * CPR; q += WT) {
+      const int kk = q / CPR, c = q % CPR;
+      cp_async16(dst + kk * Z::LM + c * 4, X + (long)(k0 + kk) * DP + c * 4);
+    }
+  }
+  cp_async_commit();
+}
+
+template <int DP>
+__device__ void w_gemm_tc(const float* A, bool ta, const float* B, bool tb, float* C, const float* C0, float alpha,
+                          float beta, float* sm, const float* bscale = nullptr, bool addI = false) {
+  using Z = TcSz<DP>;
+  constexpr int MT = Z::MT, NT = Z::NT, LK = Z::LK, LM = Z::LM;
+  float* As = sm;
+  float* Bs = sm + Z::CH;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int m0 = (warp >> 1) * (DP / 4), n0 = (warp & 1) * (DP / 2);
+  // op(A)[i][k] = A[i][k] (k-contiguous) or A[k][i]; op(B)[k][j] = B[k][j] (j-contiguous) or B[j][k]
+  const bool akm = !ta, bkm = tb;
+  float acc[MT][NT][4];
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+  for (int k0 = 0; k0 < DP; k0 += TCK) {
+    __syncthreads();   // the previous chunk is consumed
+    tc_stage<DP>(As, A, k0, akm);
+    tc_stage<DP>(Bs, B, k0, bkm);
+    cp_async_wait<0>();
+    __syncthreads();
+#pragma unroll 1
+    for (int ks = 0; ks < TCK; ks += 8) {
+      uint32_t ah[MT][4], al[MT][4];
+#pragma unroll
+      for (int i = 0; i < MT; ++i) {
+        const int r0 = m0 + i * 16 + g;
+        float av[4];
+        if (akm) {
+          av[0] = As[r0 * LK + ks + t];
+          av[1] = As[(r0 + 8) * LK + ks + t];
+          av[2] = As[r0 * LK + ks + t + 4];
+          av[3] = As[(r0 + 8) * LK + ks + t + 4];
+        } else {
+          av[0] = As[(ks + t) * LM + r0];
+          av[1] = As[(ks + t) * LM + r0 + 8];
+          av[2] = As[(ks + t + 4) * LM + r0];
+          av[3] = As[(ks + t + 4) * LM + r0 + 8];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tf32_split(av[q], ah[i][q], al[i][q]);
+      }
+      float s0 = 1.f, s1 = 1.f;
+      if (bscale) {
+        s0 = bscale[k0 + ks + t];
+        s1 = bscale[k0 + ks + t + 4];
+      }
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const int c = n0 + j * 8 + g;
+        float b0, b1;
+        if (bkm) {
+          b0 = Bs[c * LK + ks + t];
+          b1 = Bs[c * LK + ks + t + 4];
+        } else {
+          b0 = Bs[(ks + t) * LM + c];
+          b1 = Bs[(ks + t + 4) * LM + c];
+        }
+        b0 *= s0;
+        b1 *= s1;
+        uint32_t bh0, bl0, bh1, bl1;
+        tf32_split(b0, bh0, bl0);
+        tf32_split(b1, bh1, bl1);
+#pragma unroll
+        for (int i = 0; i < MT; ++i) {
+          mma_tf32(acc[i][j], al[i], bh0, bh1);
+          mma_tf32(acc[i][j], ah[i], bl0, bl1);
+          mma_tf32(acc[i][j], ah[i], bh0, bh1);
+        }
+      }
+    }
+  }
+  __syncthreads();   // every read of A and B is done (C may alias them)
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = m0 + i * 16 + g + 8 * h, c = n0 + j * 8 + 2 * t;
+        float v0 = alpha * acc[i][j][2 * h], v1 = alpha * acc[i][j][2 * h + 1];
+        if (beta != 0.f) {
+          v0 = fmaf(beta, C0[(long)r * DP + c], v0);
+          v1 = fmaf(beta, C0[(long)r * DP + c + 1], v1);
+        }
+        if (addI) {
+          if (r == c) v0 += 1.f;
+          if (r == c + 1) v1 += 1.f;
+        }
+        *reinterpret_cast<float2*>(C + (long)r * DP + c) = make_float2(v0, v1);
+      }
+  __syncthreads();
+}
+
 // out = alpha * X (+ beta * Y) elementwise, optionally transposed X (out must not alias X then)
 template <typename Real, int DP>
 __device__ void w_axpby(const Real* X, bool tx, Real alpha, const Real* Y, Real beta, Real* out) {
@@ -167,30 +332,30 @@ __device__ void w_sym(const Real* X, Real* out) {
 // the identity (the padding). A pivot below d that is not positive and finite
 // sets *bad and is replaced by 1. Returns sum_{k<d} log L_kk (valid in every thread).
 // piv: DP doubles of shared scratch.
-template <typename Real, int DP>
-__device__ double w_chol(const Real* A, Real addiag, int d, Real* S, double* piv, int* bad) {
+template <typename Real, int DP, typename SlotT = Real>
+__device__ double w_chol(const Real* A, Real addiag, int d, SlotT* S, double* piv, int* bad) {
   using Z = WSz<Real, DP>;
   constexpr int LDS = Z::LDS, P = WT / DP;
   __syncthreads();
   for (int q = threadIdx.x; q < DP * DP; q += WT) {
     const int i = q / DP, j = q % DP;
-    Real v;
-    if (i >= d || j >= d) v = (i == j) ? (Real)1 : (Real)0;
-    else v = A[q] + (i == j ? addiag : (Real)0);
+    SlotT v;
+    if (i >= d || j >= d) v = (i == j) ? (SlotT)1 : (SlotT)0;
+    else v = (SlotT)A[q] + (i == j ? (SlotT)addiag : (SlotT)0);
     S[i * LDS + j] = v;
   }
   const int i = threadIdx.x % DP, part = threadIdx.x / DP;
   for (int k = 0; k < d; ++k) {
     __syncthreads();
-    Real pk = S[k * LDS + k];
-    const bool ok = pk > (Real)0 && pk < (Real)INFINITY;
-    if (!ok) pk = (Real)1;
+    SlotT pk = S[k * LDS + k];
+    const bool ok = pk > (SlotT)0 && pk < (SlotT)INFINITY;
+    if (!ok) pk = (SlotT)1;
     if (threadIdx.x == 0) {
       piv[k] = (double)pk;
       if (!ok) *bad = 1;
     }
     if (i > k) {
-      const Real lik = S[i * LDS + k] / pk;
+      const SlotT lik = S[i * LDS + k] / pk;
       for (int j = k + 1 + part; j <= i; j += P) S[i * LDS + j] = fma(-lik, S[j * LDS + k], S[i * LDS + j]);
     }
   }
@@ -198,9 +363,9 @@ __device__ double w_chol(const Real* A, Real addiag, int d, Real* S, double* piv
   // scale: L_ik = S_ik / sqrt(p_k) (i > k), L_kk = sqrt(p_k); zero above the diagonal
   for (int q = threadIdx.x; q < DP * DP; q += WT) {
     const int r = q / DP, c = q % DP;
-    if (c >= d) { S[r * LDS + c] = (r == c) ? (Real)1 : (Real)0; continue; }
-    const Real sp = (Real)sqrt(piv[c]);
-    Real v = (Real)0;
+    if (c >= d) { S[r * LDS + c] = (r == c) ? (SlotT)1 : (SlotT)0; continue; }
+    const SlotT sp = (SlotT)sqrt(piv[c]);
+    SlotT v = (SlotT)0;
     if (r == c) v = sp;
     else if (r > c) v = S[r * LDS + c] / sp;
     S[r * LDS + c] = v;
@@ -217,7 +382,7 @@ __device__ double w_chol(const Real* A, Real addiag, int d, Real* S, double* piv
 // one thread per row; col: DP elements of shared scratch (the old column j).
 template <typename Real, int DP>
 __device__ void w_trinv(Real* S, Real* col) {
-  constexpr int LDS = WSz<Real, DP>::LDS;
+  constexpr int LDS = WSz<float, DP>::LDS;
   for (int j = DP - 1; j >= 0; --j) {
     __syncthreads();
     if (threadIdx.x < DP) col[threadIdx.x] = S[threadIdx.x * LDS + j];
@@ -240,13 +405,13 @@ __device__ void w_trinv(Real* S, Real* col) {
 }
 
 // shared slot (stride LDS) -> global, optionally transposed
-template <typename Real, int DP>
-__device__ void w_store(const Real* S, Real* g, bool transpose) {
+template <typename Real, int DP, typename SlotT = Real>
+__device__ void w_store(const SlotT* S, Real* g, bool transpose) {
   constexpr int LDS = WSz<Real, DP>::LDS;
   __syncthreads();
   for (int q = threadIdx.x; q < DP * DP; q += WT) {
     const int i = q / DP, j = q % DP;
-    g[q] = transpose ? S[j * LDS + i] : S[i * LDS + j];
+    g[q] = (Real)(transpose ? S[j * LDS + i] : S[i * LDS + j]);
   }
   __syncthreads();
 }
@@ -254,6 +419,16 @@ __device__ void w_store(const Real* S, Real* g, bool transpose) {
 // ---------------------------------------------------------------------------
 // Covariance pass
 // ---------------------------------------------------------------------------
+// the product of the covariance pass: CUDA-core FP32 (w_gemm) or, in the
+// mixed-precision form, split-TF32 tensor cores (w_gemm_tc)
+template <typename Real, int DP, bool MX>
+__device__ __forceinline__ void w_mm(const Real* A, bool ta, const Real* B, bool tb, Real* C, const Real* C0,
+                                     Real alpha, Real beta, Real* sm, const Real* bscale = nullptr,
+                                     bool addI = false) {
+  if constexpr (MX) w_gemm_tc<DP>(A, ta, B, tb, C, C0, alpha, beta, sm, bscale, addI);
+  else w_gemm<Real, DP>(A, ta, B, tb, C, C0, alpha, beta, sm, bscale, addI);
+}
+
 template <typename Real> struct WCovArgs {
   Real* tab;          // [NTAB][T][DP][DP]: TK, TG^T, TLS^T, (unused), TPF
   Real* btab;         // [2][nb][DP][DP]: (M_e ... M_s)^T, (G_s ... G_e)^T per means block
@@ -270,14 +445,14 @@ __device__ __forceinline__ Real* w_slot(const WCovArgs<Real>& a, int s, int i) {
 }
 
 // the distinct elements: prefix 0 = C_0 into TPF[0]; E = (A, C, J) into gk[0]
-template <typename Real, int DP>
+template <typename Real, int DP, bool MX>
 __global__ void __launch_bounds__(WT, 2) k_w_elem(KP<Real> p, WCovArgs<Real> a) {
   refresh_delta(p);
   using Z = WSz<Real, DP>;
   constexpr long DD = Z::DD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* S0 = reinterpret_cast<Real*>(smem_raw);
-  double* piv = reinterpret_cast<double*>(S0 + (Z::FULL > Z::GEMM ? Z::FULL : Z::GEMM));
+  double* piv = reinterpret_cast<double*>(smem_raw + Z::WORK);
   Real* S1 = reinterpret_cast<Real*>(piv + DP + 8);   // a column
   Real* s0 = w_slot<Real, DP>(a, 0, 0);
   Real* s1 = w_slot<Real, DP>(a, 0, 1);
@@ -288,8 +463,8 @@ __global__ void __launch_bounds__(WT, 2) k_w_elem(KP<Real> p, WCovArgs<Real> a) 
   w_chol<Real, DP>(p.P0, p.r, p.d, S0, piv, &bad);
   w_trinv<Real, DP>(S0, S1);
   w_store<Real, DP>(S0, s0, false);
-  w_gemm<Real, DP>(s0, false, p.P0, false, s1, nullptr, (Real)1, (Real)0, S0);
-  w_gemm<Real, DP>(s1, true, s1, false, a.tab + (long)TPF * tstride, p.P0, (Real)-1, (Real)1, S0);
+  w_mm<Real, DP, MX>(s0, false, p.P0, false, s1, nullptr, (Real)1, (Real)0, S0);
+  w_mm<Real, DP, MX>(s1, true, s1, false, a.tab + (long)TPF * tstride, p.P0, (Real)-1, (Real)1, S0);
   // t >= 1: S = Q + R = L L^T, Y = L^{-1} Q, W = L^{-1} F
   Real* EA = a.gk;
   Real* EC = EA + DD;
@@ -297,17 +472,17 @@ __global__ void __launch_bounds__(WT, 2) k_w_elem(KP<Real> p, WCovArgs<Real> a) 
   w_chol<Real, DP>(p.Q, p.r, p.d, S0, piv, &bad);
   w_trinv<Real, DP>(S0, S1);
   w_store<Real, DP>(S0, s0, false);
-  w_gemm<Real, DP>(s0, false, p.Q, false, s1, nullptr, (Real)1, (Real)0, S0);
-  w_gemm<Real, DP>(s1, true, s1, false, EC, p.Q, (Real)-1, (Real)1, S0);       // C = Q - Y^T Y
-  w_gemm<Real, DP>(s0, false, p.F, false, s2, nullptr, (Real)1, (Real)0, S0);  // W = L^{-1} F
-  w_gemm<Real, DP>(s2, true, s2, false, EJ, nullptr, (Real)1, (Real)0, S0);    // J = W^T W
-  w_gemm<Real, DP>(s0, true, s2, false, EA, nullptr, p.r, (Real)0, S0);        // A = r L^{-T} W
+  w_mm<Real, DP, MX>(s0, false, p.Q, false, s1, nullptr, (Real)1, (Real)0, S0);
+  w_mm<Real, DP, MX>(s1, true, s1, false, EC, p.Q, (Real)-1, (Real)1, S0);       // C = Q - Y^T Y
+  w_mm<Real, DP, MX>(s0, false, p.F, false, s2, nullptr, (Real)1, (Real)0, S0);  // W = L^{-1} F
+  w_mm<Real, DP, MX>(s2, true, s2, false, EJ, nullptr, (Real)1, (Real)0, S0);    // J = W^T W
+  w_mm<Real, DP, MX>(s0, true, s2, false, EA, nullptr, p.r, (Real)0, S0);        // A = r L^{-T} W
   if (bad && threadIdx.x == 0) atomicOr(a.status, ST_NOT_PD);
 }
 
 // C part of (0, C_i, 0) (x) (A_e, C_e, J_e) into out; with full (A_i, J_i also given,
 // Ao / Jo not null) the whole operator. Scratch: slot s.
-template <typename Real, int DP>
+template <typename Real, int DP, bool MX>
 __device__ void w_combine(const KP<Real>& p, const WCovArgs<Real>& a, int s, const Real* Ai, const Real* Ci,
                           const Real* Ji, const Real* Ae, const Real* Ce, const Real* Je, Real* Ao, Real* Co,
                           Real* Jo, Real* S0, Real* S1, double* piv, int* bad) {
@@ -316,40 +491,56 @@ __device__ void w_combine(const KP<Real>& p, const WCovArgs<Real>& a, int s, con
   Real* N = w_slot<Real, DP>(a, s, 2);
   Real* B = w_slot<Real, DP>(a, s, 3);
   Real* Pm = w_slot<Real, DP>(a, s, 4);
-  w_chol<Real, DP>(Ci, (Real)0, p.d, S0, piv, bad);                    // U = chol(C_i)
-  w_store<Real, DP>(S0, U, false);
-  w_gemm<Real, DP>(Je, false, U, false, X, nullptr, (Real)1, (Real)0, S0);         // J_e U
-  w_gemm<Real, DP>(U, true, X, false, N, nullptr, (Real)1, (Real)0, S0, nullptr, true);   // N = I + U^T J_e U
-  w_chol<Real, DP>(N, (Real)0, p.d, S0, piv, bad);
-  w_trinv<Real, DP>(S0, S1);
-  w_store<Real, DP>(S0, N, false);                                      // chol(N)^{-1}
-  w_gemm<Real, DP>(U, false, N, true, B, nullptr, (Real)1, (Real)0, S0);           // B = U chol(N)^{-T}
-  w_gemm<Real, DP>(Ae, false, B, false, Pm, nullptr, (Real)1, (Real)0, S0);        // P = A_e B
+  // the factorisations of C_i and of N = I + U^T J_e U, and the inverse of chol(N):
+  // in FP64 in the mixed-precision form (the slot S0 then holds doubles)
+  if constexpr (MX) {
+    double* D0 = reinterpret_cast<double*>(S0);
+    w_chol<Real, DP, double>(Ci, (Real)0, p.d, D0, piv, bad);            // U = chol(C_i)
+    w_store<Real, DP, double>(D0, U, false);
+  } else {
+    w_chol<Real, DP>(Ci, (Real)0, p.d, S0, piv, bad);                    // U = chol(C_i)
+    w_store<Real, DP>(S0, U, false);
+  }
+  w_mm<Real, DP, MX>(Je, false, U, false, X, nullptr, (Real)1, (Real)0, S0);         // J_e U
+  w_mm<Real, DP, MX>(U, true, X, false, N, nullptr, (Real)1, (Real)0, S0, nullptr, true);   // N = I + U^T J_e U
+  if constexpr (MX) {
+    double* D0 = reinterpret_cast<double*>(S0);
+    double* D1 = reinterpret_cast<double*>(S1);
+    w_chol<Real, DP, double>(N, (Real)0, p.d, D0, piv, bad);
+    w_trinv<double, DP>(D0, D1);
+    w_store<Real, DP, double>(D0, N, false);                             // chol(N)^{-1}
+  } else {
+    w_chol<Real, DP>(N, (Real)0, p.d, S0, piv, bad);
+    w_trinv<Real, DP>(S0, S1);
+    w_store<Real, DP>(S0, N, false);                                      // chol(N)^{-1}
+  }
+  w_mm<Real, DP, MX>(U, false, N, true, B, nullptr, (Real)1, (Real)0, S0);           // B = U chol(N)^{-T}
+  w_mm<Real, DP, MX>(Ae, false, B, false, Pm, nullptr, (Real)1, (Real)0, S0);        // P = A_e B
   if (Ao) {
     Real* X1 = w_slot<Real, DP>(a, s, 5);
     Real* Zm = w_slot<Real, DP>(a, s, 6);
     Real* Jt = w_slot<Real, DP>(a, s, 7);
-    w_gemm<Real, DP>(Je, false, Ai, false, X1, nullptr, (Real)1, (Real)0, S0);     // X1 = J_e A_i
-    w_gemm<Real, DP>(B, true, X1, false, Zm, nullptr, (Real)1, (Real)0, S0);       // Z = B^T X1
-    w_gemm<Real, DP>(Ai, true, X1, false, Jt, Ji, (Real)1, (Real)1, S0);          // J_i + A_i^T X1
-    w_gemm<Real, DP>(Zm, true, Zm, false, Jt, Jt, (Real)-1, (Real)1, S0);         // - Z^T Z
+    w_mm<Real, DP, MX>(Je, false, Ai, false, X1, nullptr, (Real)1, (Real)0, S0);     // X1 = J_e A_i
+    w_mm<Real, DP, MX>(B, true, X1, false, Zm, nullptr, (Real)1, (Real)0, S0);       // Z = B^T X1
+    w_mm<Real, DP, MX>(Ai, true, X1, false, Jt, Ji, (Real)1, (Real)1, S0);          // J_i + A_i^T X1
+    w_mm<Real, DP, MX>(Zm, true, Zm, false, Jt, Jt, (Real)-1, (Real)1, S0);         // - Z^T Z
     w_sym<Real, DP>(Jt, Jo);
-    w_gemm<Real, DP>(Ae, false, Ai, false, Ao, nullptr, (Real)1, (Real)0, S0);     // A_e A_i
-    w_gemm<Real, DP>(Pm, false, Zm, false, Ao, Ao, (Real)-1, (Real)1, S0);        // - P Z
+    w_mm<Real, DP, MX>(Ae, false, Ai, false, Ao, nullptr, (Real)1, (Real)0, S0);     // A_e A_i
+    w_mm<Real, DP, MX>(Pm, false, Zm, false, Ao, Ao, (Real)-1, (Real)1, S0);        // - P Z
   }
-  w_gemm<Real, DP>(Pm, false, Pm, true, Co, Ce, (Real)1, (Real)1, S0);            // C = C_e + P P^T
+  w_mm<Real, DP, MX>(Pm, false, Pm, true, Co, Ce, (Real)1, (Real)1, S0);            // C = C_e + P P^T
 }
 
 // one doubling level: prefixes TPF[pow2 + i] = TPF[i] (x) E^(pow2), i < cnt; item cnt
 // (when sq): E^(2 pow2) = E^(pow2) (x) E^(pow2) into gk2
-template <typename Real, int DP>
-__global__ void __launch_bounds__(WT, 2) k_w_double(KP<Real> p, WCovArgs<Real> a, int pow2, int cnt, int sq,
+template <typename Real, int DP, bool MX>
+__global__ void __launch_bounds__(WT, MX ? 1 : 2) k_w_double(KP<Real> p, WCovArgs<Real> a, int pow2, int cnt, int sq,
                                                   const Real* __restrict__ gk, Real* __restrict__ gk2) {
   using Z = WSz<Real, DP>;
   constexpr long DD = Z::DD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* S0 = reinterpret_cast<Real*>(smem_raw);
-  double* piv = reinterpret_cast<double*>(S0 + (Z::FULL > Z::GEMM ? Z::FULL : Z::GEMM));
+  double* piv = reinterpret_cast<double*>(smem_raw + (MX ? Z::WORK_MX : Z::WORK));
   Real* S1 = reinterpret_cast<Real*>(piv + DP + 8);   // a column
   int bad = 0;
   Real* PF = a.tab + (long)TPF * p.nT * DD;
@@ -358,24 +549,24 @@ __global__ void __launch_bounds__(WT, 2) k_w_double(KP<Real> p, WCovArgs<Real> a
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const int item = sq ? (it == 0 ? cnt : it - 1) : it;
     if (item == cnt)
-      w_combine<Real, DP>(p, a, blockIdx.x, gk, gk + DD, gk + 2 * DD, gk, gk + DD, gk + 2 * DD, gk2, gk2 + DD,
+      w_combine<Real, DP, MX>(p, a, blockIdx.x, gk, gk + DD, gk + 2 * DD, gk, gk + DD, gk + 2 * DD, gk2, gk2 + DD,
                           gk2 + 2 * DD, S0, S1, piv, &bad);
     else
-      w_combine<Real, DP>(p, a, blockIdx.x, nullptr, PF + (long)item * DD, nullptr, gk, gk + DD, gk + 2 * DD,
+      w_combine<Real, DP, MX>(p, a, blockIdx.x, nullptr, PF + (long)item * DD, nullptr, gk, gk + DD, gk + 2 * DD,
                           nullptr, PF + (long)(pow2 + item) * DD, nullptr, S0, S1, piv, &bad);
   }
   if (bad && threadIdx.x == 0) atomicOr(a.status, ST_NOT_PD);
 }
 
 // per step t = 0 .. T (item T: the last step's backward quantities only)
-template <typename Real, int DP>
+template <typename Real, int DP, bool MX>
 __global__ void __launch_bounds__(WT, 2) k_w_epi(KP<Real> p, WCovArgs<Real> a) {
   refresh_delta(p);
   using Z = WSz<Real, DP>;
   constexpr long DD = Z::DD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* S0 = reinterpret_cast<Real*>(smem_raw);
-  double* piv = reinterpret_cast<double*>(S0 + (Z::FULL > Z::GEMM ? Z::FULL : Z::GEMM));
+  double* piv = reinterpret_cast<double*>(smem_raw + Z::WORK);
   Real* S1 = reinterpret_cast<Real*>(piv + DP + 8);   // a column
   const long ts = (long)p.nT * DD;
   Real* TKt = a.tab + (long)TK * ts;
@@ -403,15 +594,15 @@ __global__ void __launch_bounds__(WT, 2) k_w_epi(KP<Real> p, WCovArgs<Real> a) {
         }
         __syncthreads();
       } else {
-        w_gemm<Real, DP>(p.F, false, PF + (long)(t - 1) * DD, false, X, nullptr, (Real)1, (Real)0, S0);
-        w_gemm<Real, DP>(X, false, p.F, true, Pp, p.Q, (Real)1, (Real)1, S0);
+        w_mm<Real, DP, MX>(p.F, false, PF + (long)(t - 1) * DD, false, X, nullptr, (Real)1, (Real)0, S0);
+        w_mm<Real, DP, MX>(X, false, p.F, true, Pp, p.Q, (Real)1, (Real)1, S0);
       }
       // S_t = P^p_t + R: K'_t = r L^{-T} L^{-1}, log det S_t
       const double ld = w_chol<Real, DP>(Pp, p.r, p.d, S0, piv, &bad);
       if (threadIdx.x == 0) a.ldt[t] = 2.0 * ld;
       w_trinv<Real, DP>(S0, S1);
       w_store<Real, DP>(S0, Li, false);
-      w_gemm<Real, DP>(Li, true, Li, false, TKt + (long)t * DD, nullptr, p.r, (Real)0, S0);
+      w_mm<Real, DP, MX>(Li, true, Li, false, TKt + (long)t * DD, nullptr, p.r, (Real)0, S0);
     }
     if (t >= 1) {
       // backward quantities of step t - 1
@@ -425,11 +616,11 @@ __global__ void __launch_bounds__(WT, 2) k_w_epi(KP<Real> p, WCovArgs<Real> a) {
           for (int q = threadIdx.x; q < DP * DP; q += WT) X[q] = p.F[(q / DP) * DP + q / DP] * Pf[q];
           __syncthreads();
         } else {
-          w_gemm<Real, DP>(p.F, false, Pf, false, X, nullptr, (Real)1, (Real)0, S0);   // F P^f
+          w_mm<Real, DP, MX>(p.F, false, Pf, false, X, nullptr, (Real)1, (Real)0, S0);   // F P^f
         }
-        w_gemm<Real, DP>(Li, false, X, false, Y, nullptr, (Real)1, (Real)0, S0);       // Y = W^T
-        w_gemm<Real, DP>(Li, true, Y, false, TGt + (long)(t - 1) * DD, nullptr, (Real)1, (Real)0, S0);   // G^T
-        w_gemm<Real, DP>(Y, true, Y, false, Sg, Pf, (Real)-1, (Real)1, S0);            // Sigma
+        w_mm<Real, DP, MX>(Li, false, X, false, Y, nullptr, (Real)1, (Real)0, S0);       // Y = W^T
+        w_mm<Real, DP, MX>(Li, true, Y, false, TGt + (long)(t - 1) * DD, nullptr, (Real)1, (Real)0, S0);   // G^T
+        w_mm<Real, DP, MX>(Y, true, Y, false, Sg, Pf, (Real)-1, (Real)1, S0);            // Sigma
         w_chol<Real, DP>(Sg, (Real)0, p.d, S0, piv, &bad);
       } else {
         w_axpby<Real, DP>(Pf, false, (Real)0, nullptr, (Real)0, TGt + (long)(t - 1) * DD);   // G_{T-1} = 0
@@ -442,7 +633,7 @@ __global__ void __launch_bounds__(WT, 2) k_w_epi(KP<Real> p, WCovArgs<Real> a) {
 }
 
 // per means block k: (M_e ... M_s)^T, (G_s ... G_e)^T, sum of log det S_t
-template <typename Real, int DP>
+template <typename Real, int DP, bool MX>
 __global__ void __launch_bounds__(WT, 2) k_w_prod(KP<Real> p, WCovArgs<Real> a) {
   using Z = WSz<Real, DP>;
   constexpr long DD = Z::DD;
@@ -467,12 +658,12 @@ __global__ void __launch_bounds__(WT, 2) k_w_prod(KP<Real> p, WCovArgs<Real> a) 
     __syncthreads();
     for (int t = s; t <= e; ++t) {
       if (p.fdiag) {
-        w_gemm<Real, DP>(TKt + (long)t * DD, false, AH, false, AH, nullptr, (Real)1, (Real)0, S0, Fd);
+        w_mm<Real, DP, MX>(TKt + (long)t * DD, false, AH, false, AH, nullptr, (Real)1, (Real)0, S0, Fd);
       } else {
-        w_gemm<Real, DP>(p.F, false, AH, false, X, nullptr, (Real)1, (Real)0, S0);
-        w_gemm<Real, DP>(TKt + (long)t * DD, false, X, false, AH, nullptr, (Real)1, (Real)0, S0);
+        w_mm<Real, DP, MX>(p.F, false, AH, false, X, nullptr, (Real)1, (Real)0, S0);
+        w_mm<Real, DP, MX>(TKt + (long)t * DD, false, X, false, AH, nullptr, (Real)1, (Real)0, S0);
       }
-      w_gemm<Real, DP>(GH, false, TGt + (long)t * DD, true, GH, nullptr, (Real)1, (Real)0, S0);
+      w_mm<Real, DP, MX>(GH, false, TGt + (long)t * DD, true, GH, nullptr, (Real)1, (Real)0, S0);
     }
     w_axpby<Real, DP>(AH, true, (Real)1, nullptr, (Real)0, a.btab + (long)k * DD);
     w_axpby<Real, DP>(GH, true, (Real)1, nullptr, (Real)0, a.btab + ((long)p.nb + k) * DD);

@@ -63,11 +63,12 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("dt", ["f32", "mixed"])
 @pytest.mark.parametrize("d,T,C,L,mode,dense", CASES)
-def test_loglik_matches_the_kalman_filter(d, T, C, L, mode, dense):
+def test_loglik_matches_the_kalman_filter(d, T, C, L, mode, dense, dt):
     wl = _workload(d, T, C, seed=7 * d + T, dense_f=dense)
     yt = np.random.default_rng(d + T).standard_normal((C, T, d))
-    s = AuxKalman(wl, dtype="f32", block_len=L, mode=mode)
+    s = AuxKalman(wl, dtype=dt, block_len=L, mode=mode)
     logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
     mf = torch.zeros((C, T, d), dtype=torch.float32, device="cuda")
     Pf = torch.zeros((C, T, d, d), dtype=torch.float32, device="cuda")
@@ -83,20 +84,22 @@ def test_loglik_matches_the_kalman_filter(d, T, C, L, mode, dense):
         assert _rel(mfg[c], kf["mf"]) < 1e-4
         assert _rel(Pfg[c], kf["Pf"]) < 1e-4
         em, eP = pm.vec_err(mfg[c], kf["mf"], kf["Pf"]), pm.mat_err(Pfg[c], kf["Pf"], kf["Pf"])
-        pm.note("mf", f"wide_f32_{mode}", em)
-        pm.note("Pf", f"wide_f32_{mode}", eP)
+        pm.note("mf", f"wide_{dt}_{mode}", em)
+        pm.note("Pf", f"wide_{dt}_{mode}", eP)
+        pm.note("logZ", f"wide_{dt}_{mode}", abs(lz[c] - kf["logZ"]) / abs(kf["logZ"]))
         assert em < 1e-4 and eP < 1e-4, (c, em, eP)
     assert rc == 0 and not np.any(st)
 
 
+@pytest.mark.parametrize("dt", ["f32", "mixed"])
 @pytest.mark.parametrize("d,T,C,L,mode", [(40, 50, 3, 7, "cached"), (64, 33, 17, 8, "shared"),
                                           (128, 45, 2, 16, "cached")])
-def test_sample_path_matches_the_rts_sampler(d, T, C, L, mode):
+def test_sample_path_matches_the_rts_sampler(d, T, C, L, mode, dt):
     wl = _workload(d, T, C, seed=3 * d + T)
     rng = np.random.default_rng(d * T)
     yt = rng.standard_normal((C, T, d))
     eps = rng.standard_normal((C, T, d))
-    s = AuxKalman(wl, dtype="f32", block_len=L, mode=mode)
+    s = AuxKalman(wl, dtype=dt, block_len=L, mode=mode)
     xs = torch.zeros((C, T, d), dtype=torch.float32, device="cuda")
     logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
     s.sample_path(_tt(yt), xs, eps=_tt(eps), logZ=logZ)
@@ -110,14 +113,14 @@ def test_sample_path_matches_the_rts_sampler(d, T, C, L, mode):
         xg = xs[c].double().cpu().numpy()
         assert _rel(xg, ref) < 1e-4
         e = pm.vec_err(xg, ref, kalman.rts_smoother(kf, wl.F)[1])
-        pm.note("x_star", f"wide_f32_{mode}", e)
+        pm.note("x_star", f"wide_{dt}_{mode}", e)
         assert e < 1e-4, (c, e)
         assert abs(logZ[c].item() - kf["logZ"]) <= 1e-5 * abs(kf["logZ"])
 
 
-def _step_parity(wl, L, mode, n_iters, tol_x, tol_la, chains=None):
+def _step_parity(wl, L, mode, n_iters, tol_x, tol_la, chains=None, dt="f32"):
     C = wl.n_chains
-    s = AuxKalman(wl, dtype="f32", block_len=L, mode=mode)
+    s = AuxKalman(wl, dtype=dt, block_len=L, mode=mode)
     x = _tt(wl.x_init)
     la = torch.zeros(C, dtype=torch.float64, device="cuda")
     if wl.emission == workloads.EMIS_SV:
@@ -146,20 +149,21 @@ def _step_parity(wl, L, mode, n_iters, tol_x, tol_la, chains=None):
                 moved += 1
                 assert _rel(xg[c], ref["x_star"]) < tol_x
                 e = pm.vec_err(xg[c], ref["x_star"], kalman.rts_smoother(ref["kf"], wl.F)[1])
-                pm.note("x_star", f"wide_{wl.name}_d{wl.d}_T{wl.T}_{mode}", e)
+                pm.note("x_star", f"wide_{dt}_{wl.name}_d{wl.d}_T{wl.T}_{mode}", e)
                 assert e < TOL_ELEM_WIDE, (it, c, e)
             else:
                 assert np.array_equal(xg[c], x_before[c])
     assert s.status()[0] == 0
     s.close()
-    pm.note_log_alpha(f"wide_{wl.name}_d{wl.d}_T{wl.T}_{mode}", dlas, mism, tol_la)
+    pm.note_log_alpha(f"wide_{dt}_{wl.name}_d{wl.d}_T{wl.T}_{mode}", dlas, mism, tol_la)
     return moved, worst
 
 
+@pytest.mark.parametrize("dt", ["f32", "mixed"])
 @pytest.mark.parametrize("mode", ["shared", "cached"])
-def test_kalman_step_parity_sv(mode):
+def test_kalman_step_parity_sv(mode, dt):
     wl = workloads.stochastic_volatility(d=40, T=48, n_chains=3, delta=0.02)
-    moved, worst = _step_parity(wl, 8, mode, 3, 1e-4, 2e-3)
+    moved, worst = _step_parity(wl, 8, mode, 3, 1e-4, 2e-3, dt=dt)
     print("d = 40: moves", moved, "max |d log alpha|", worst)
     assert moved > 0
 
@@ -169,11 +173,12 @@ def test_kalman_step_parity_linear_gaussian_dense_dynamics():
     _step_parity(wl, 6, "cached", 2, 1e-4, 2e-3)
 
 
-def test_kalman_step_full_size_sampled_chains():
+@pytest.mark.parametrize("dt", ["f32", "mixed"])
+def test_kalman_step_full_size_sampled_chains(dt):
     """d = 128, T = 4096, 16 chains (the mixed-precision workload's shape), cached
     tables: one step of every chain, chains 0 and 15 against the oracle."""
     wl = workloads.stochastic_volatility(d=128, T=4096, n_chains=16)
-    moved, worst = _step_parity(wl, 0, "cached", 1, 1e-4, 4e-2, chains=(0, 15))
+    moved, worst = _step_parity(wl, 0, "cached", 1, 1e-4, 4e-2, chains=(0, 15), dt=dt)
     print("d = 128, T = 4096: max |d log alpha|", worst)
 
 
@@ -194,3 +199,10 @@ def test_scope_is_reported():
         AuxKalman(workloads.stochastic_volatility(d=129, T=8, n_chains=1), dtype="f32")
     with pytest.raises(B.AuxError):
         AuxKalman(wl, dtype="f64", block_len=4, mode="cached")
+    # mixed precision: the wide widths in the table modes only
+    with pytest.raises(B.AuxError):
+        AuxKalman(_workload(30, 12, 2, seed=1), dtype="mixed", block_len=4, mode="cached")
+    sm = AuxKalman(wl, dtype="mixed", block_len=4)          # per-chain mode
+    with pytest.raises(B.AuxError):
+        sm.step(x, 1)
+    sm.close()
