@@ -193,6 +193,44 @@ int aux_sample_path(aux_model *m, const void *ytilde, const void *eps, uint64_t 
  * call (it allocates C*T*d^2 elements for the backward covariances). */
 int aux_loglik_grad(aux_model *m, const void *ytilde, double *logZ, double *g_mu, double *g_Phi,
                     double *g_cholSigma, double *g_delta, void *stream);
+/* (ytilde may be NULL: the pseudo-observations of the last aux_kalman_step's
+ * proposal, ytilde_t = u_t + (delta/2) v_t at the state before that step, kept in
+ * the handle's workspace.) */
+
+/* The SV parameterisation theta = (mu, phi, L = chol Sigma) behind the C ABI
+ * (Section 4.1): F = diag(phi), b = (1 - phi) mu, Q = L L^T, p_0 the stationary
+ * law (m0 = mu, P0_ij = Q_ij / (1 - phi_i phi_j)). The handle keeps theta on the
+ * device beside the constants aux_loglik_grad needs (Q^{-1}, P0^{-1}); one warp
+ * rebuilds the padded model and those constants from theta, in FP64.
+ *
+ * aux_set_sv_theta: host theta (mu [d], phi [d] with |phi_i| < 1, L [d][d] lower
+ * triangular with positive diagonal; its upper part is ignored) and delta > 0;
+ * synchronises the handle's stream, writes the model (y, R_y and the mask are
+ * kept) and marks cached tables stale. Errors: INVALID_ARG, NONFINITE, NOT_PD
+ * (a diagonal entry of L <= 0), UNSUPPORTED (factorised prior, d_x > 32), CUDA.
+ *
+ * aux_sv_theta_step: the gradient-based theta-update inside the Gibbs sweep.
+ * The paper updates its static parameters inside the sampler (Section 4.3)
+ * without stating a rule; this one is a projected gradient-ascent step on the
+ * mean over chains of log p(ytilde_c | theta):
+ *   mu <- mu + lr mean_c g_mu[c],  phi <- clip(phi + lr mean_c g_phi[c], -0.999, 0.999),
+ *   L  <- tril(L + lr mean_c g_L[c]),  diag(L) <- max(diag(L), 1e-6),
+ * then the model is rebuilt from theta; delta is left to the sampler. The
+ * gradients are device arrays laid out as aux_loglik_grad writes them
+ * ([C][d], [C][d], [C][d][d]). Everything stays on the device (no host
+ * synchronisation), so a sweep aux_kalman_step -> aux_loglik_grad(ytilde = NULL)
+ * -> aux_sv_theta_step can be captured in a CUDA graph once aux_loglik_grad's
+ * first call has allocated its buffers. Requires the SV parameterisation
+ * (set by aux_init_model / aux_set_model_params / aux_set_sv_theta).
+ * Errors: INVALID_ARG, UNSUPPORTED (no SV parameterisation, factorised prior,
+ * d_x > 32, or AUX_MODE_CACHED_COV, whose kept tables would go stale), CUDA.
+ *
+ * aux_get_sv_theta: the current theta (host arrays mu [d], phi [d], L [d][d];
+ * synchronises). Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+int aux_set_sv_theta(aux_model *m, const double *mu, const double *phi, const double *L, double delta);
+int aux_sv_theta_step(aux_model *m, const double *g_mu, const double *g_phi, const double *g_L, double lr,
+                      void *stream);
+int aux_get_sv_theta(aux_model *m, double *mu, double *phi, double *L);
 
 /* Choose how the filter and the backward sampler are executed. All modes
  * compute the same quantities (the same x*, log Z and log alpha up to

@@ -112,3 +112,29 @@ def loglik_grad(theta, ytilde):
     O = np.sum((ytilde - ms) ** 2) + np.einsum("tii->", Ps)
     g_delta = -T * d / (2.0 * delta) + O / delta ** 2
     return g_mu, g_phi, g_L, float(g_delta), kf["logZ"]
+
+
+# ---------------------------------------------------------------------------
+# The gradient-based theta-update inside the Gibbs sweep. The paper updates its
+# static parameters inside the sampler (Section 4.3) without stating a rule;
+# this one is a projected gradient-ascent step on the mean over chains of the
+# auxiliary marginal log-likelihood log p(ytilde_c | theta) (Fisher's identity
+# above), applied to (mu, phi, L) with delta left to the sampler:
+#   mu  <- mu  + lr * mean_c g_mu[c]
+#   phi <- clip(phi + lr * mean_c g_phi[c], -PHI_MAX, PHI_MAX)
+#   L   <- tril(L + lr * mean_c g_L[c]),  diag(L) <- max(diag(L), L_MIN)
+# then the model is rebuilt from theta by sv_model (stationary p_0).
+# ---------------------------------------------------------------------------
+PHI_MAX = 0.999
+L_MIN = 1e-6
+
+
+def sv_theta_update(mu, phi, L, g_mu, g_phi, g_L, lr):
+    """One theta-update from per-chain gradients g_mu [C][d], g_phi [C][d], g_L [C][d][d]."""
+    mu = np.asarray(mu, dtype=np.float64) + lr * np.mean(np.asarray(g_mu, dtype=np.float64), axis=0)
+    phi = np.asarray(phi, dtype=np.float64) + lr * np.mean(np.asarray(g_phi, dtype=np.float64), axis=0)
+    phi = np.clip(phi, -PHI_MAX, PHI_MAX)
+    L = np.tril(np.asarray(L, dtype=np.float64) + lr * np.mean(np.asarray(g_L, dtype=np.float64), axis=0))
+    idx = np.arange(len(mu))
+    L[idx, idx] = np.maximum(L[idx, idx], L_MIN)
+    return mu, phi, L

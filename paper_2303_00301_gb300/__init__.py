@@ -122,6 +122,20 @@ class AuxKalman:
         torch.cuda.current_stream().wait_stream(s)
         return g
 
+    def grad(self, ytilde, g_mu, g_phi, g_L, g_delta, logZ=None, stream=None):
+        """aux_loglik_grad; ytilde None: the last step's pseudo-observations."""
+        self.b.aux_loglik_grad(self.handle, ytilde, g_mu, g_phi, g_L, g_delta, logZ, stream)
+
+    def theta_step(self, g_mu, g_phi, g_L, lr, stream=None):
+        """The on-device theta-update inside the sweep (aux_sv_theta_step)."""
+        self.b.aux_sv_theta_step(self.handle, g_mu, g_phi, g_L, lr, stream)
+
+    def set_theta(self, mu, phi, L, delta):
+        self.b.aux_set_sv_theta(self.handle, mu, phi, L, delta)
+
+    def theta(self):
+        return self.b.aux_get_sv_theta(self.handle, self.d)
+
     def close(self):
         if getattr(self, "handle", None) is not None:
             self.b.aux_free_model(self.handle)

@@ -104,6 +104,13 @@ def _load():
     lib.aux_loglik_grad.restype = ctypes.c_int
     lib.aux_set_model_params.argtypes = [vp, ctypes.POINTER(aux_model_desc)]
     lib.aux_set_model_params.restype = ctypes.c_int
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.aux_set_sv_theta.argtypes = [vp, dp, dp, dp, ctypes.c_double]
+    lib.aux_set_sv_theta.restype = ctypes.c_int
+    lib.aux_sv_theta_step.argtypes = [vp, vp, vp, vp, ctypes.c_double, vp]
+    lib.aux_sv_theta_step.restype = ctypes.c_int
+    lib.aux_get_sv_theta.argtypes = [vp, dp, dp, dp]
+    lib.aux_get_sv_theta.restype = ctypes.c_int
     lib.aux_loglik_noalloc.argtypes = [ctypes.POINTER(aux_model_desc), vp, vp, vp]
     lib.aux_loglik_noalloc.restype = ctypes.c_int
     lib.aux_status_string.argtypes = [ctypes.c_int]
@@ -225,6 +232,28 @@ def aux_loglik_grad(handle, ytilde, g_mu, g_Phi, g_cholSigma, g_delta, logZ=None
     rc = LIB.aux_loglik_grad(handle, _ptr(ytilde), _ptr(logZ), _ptr(g_mu), _ptr(g_Phi),
                              _ptr(g_cholSigma), _ptr(g_delta), _stream(stream))
     _check(rc, "aux_loglik_grad")
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def aux_set_sv_theta(handle, mu, phi, L, delta):
+    """Write theta = (mu, phi, L = chol Sigma) and delta (host values) into the handle."""
+    mu, phi, L = _as_c(mu), _as_c(phi), _as_c(L)
+    _check(LIB.aux_set_sv_theta(handle, _dptr(mu), _dptr(phi), _dptr(L), float(delta)), "aux_set_sv_theta")
+
+
+def aux_sv_theta_step(handle, g_mu, g_phi, g_L, lr, stream=None):
+    """The on-device theta-update from per-chain gradients (device tensors)."""
+    rc = LIB.aux_sv_theta_step(handle, _ptr(g_mu), _ptr(g_phi), _ptr(g_L), float(lr), _stream(stream))
+    _check(rc, "aux_sv_theta_step")
+
+
+def aux_get_sv_theta(handle, d):
+    mu, phi, L = np.zeros(d), np.zeros(d), np.zeros((d, d))
+    _check(LIB.aux_get_sv_theta(handle, _dptr(mu), _dptr(phi), _dptr(L)), "aux_get_sv_theta")
+    return mu, phi, L
 
 
 def aux_set_model_params(handle, *, d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind,

@@ -653,8 +653,9 @@ int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {
 
 int aux_loglik_grad(aux_model* m, const void* ytilde, double* logZ, double* g_mu, double* g_Phi,
                     double* g_cholSigma, double* g_delta, void* stream) {
-  if (!m || !ytilde || !g_mu || !g_Phi || !g_cholSigma || !g_delta) return AUX_E_INVALID_ARG;
+  if (!m || !g_mu || !g_Phi || !g_cholSigma || !g_delta) return AUX_E_INVALID_ARG;
   if (!m->grad_ok || m->fact || wide(m)) return AUX_E_UNSUPPORTED;
+  if (!ytilde) ytilde = m->yt;   // the last aux_kalman_step's pseudo-observations
   m->stream = (cudaStream_t)stream;
   const size_t es = m->esz, DP = m->DP, nbC = (size_t)m->C * m->nb;
   int rc = AUX_OK;

@@ -3,9 +3,10 @@
 theta = (mu, phi, L, delta) of the multivariate stochastic-volatility model
 (Section 4.1): F = diag(phi), b = (I - F) mu, Q = L L^T, stationary p_0,
 R = (delta/2) I; the pseudo-observations ytilde are held fixed. The forward
-pass and the gradient both run in the CUDA library (aux_loglik_grad); this
-module only moves theta to the model handle and applies the chain rule to the
-upstream gradient.
+pass, the gradient and the theta -> model map all run in the CUDA library
+(aux_loglik_grad, aux_set_sv_theta); this module marshals theta and applies the
+chain rule to the upstream gradient. sv_model_arrays states the same map on the
+host for callers that build a model description themselves.
 """
 import numpy as np
 import torch
@@ -24,13 +25,9 @@ def sv_model_arrays(mu, phi, L, delta):
 
 
 def set_theta(sampler, mu, phi, L, delta):
-    """Write theta into an existing AuxKalman handle (same sizes)."""
-    m = sv_model_arrays(mu, phi, L, delta)
-    wl = sampler.wl
-    B.aux_set_model_params(sampler.handle, d_x=sampler.d, T=sampler.T, n_chains=sampler.C,
-                           m0=m["m0"], P0=m["P0"], F=m["F"], b=m["b"], Q=m["Q"], y=wl.y,
-                           delta=m["delta"], emis_kind=wl.emission, dtype=sampler.dtype_code,
-                           R_y=wl.Ry, obs_mask=wl.mask)
+    """Write theta into an existing AuxKalman handle (aux_set_sv_theta: the library
+    forms F, b, Q and the stationary p_0 on the device)."""
+    B.aux_set_sv_theta(sampler.handle, mu, phi, L, delta)
 
 
 class SVLogZ(torch.autograd.Function):
