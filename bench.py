@@ -283,10 +283,10 @@ KERNEL_NAMES = {
                   "backward": "k_sample_backward", "mh": "k_mh + k_commit", "linearise": "k_linearise"},
     "per_chain_sqrt": {"reduce": "k_sr_reduce", "apply": "k_sr_apply", "scan": "k_sr_scan_level",
                        "backward": "k_sample_backward", "mh": "k_mh + k_commit", "linearise": "k_linearise"},
-    "table": {"reduce": "k_mf_reduce", "apply": "k_mf_apply", "scan": "k_mean_cross",
-              "backward": "k_mean_cross + k_mb_apply", "mh": "k_mh + k_commit",
+    "table": {"reduce": "k_mf_reduce", "apply": "k_mf_apply", "scan": "k_mean_cross2",
+              "backward": "k_mean_cross2 + k_mb_apply", "mh": "k_mh + k_commit",
               "cov_reduce": "k_c2_init", "cov_scan": "k_c2_level",
-              "cov_apply": "k_c2_tables", "cov_products": "k_c2_products",
+              "cov_apply": "k_c2_tables", "cov_products": "k_c2_products + k_cov_xprod",
               "bridge": "k_b_sample + k_b_mh", "bridge_tree": "k_br_leaf + k_br_node"},
 }
 

@@ -494,7 +494,8 @@ int aux_set_mode(aux_model* m, int32_t mode) {
       if (!rc) rc = dev_alloc(m, &m->cagg1, (size_t)m->nbc * 3 * DD * es);
     }
     if (!rc) rc = dev_alloc(m, (void**)&m->cov_ldt, (size_t)m->T * sizeof(double));
-    if (!rc) rc = dev_alloc(m, &m->btab, (size_t)2 * m->nb * DD * es);
+    // block products, and their group prefixes for the two-level cross-block composition
+    if (!rc) rc = dev_alloc(m, &m->btab, (size_t)4 * m->nb * DD * es);
     if (!rc) rc = dev_alloc(m, &m->zb, (size_t)m->C * m->nb * m->DP * es);
     if (!rc) rc = dev_alloc(m, &m->ms, (size_t)m->C * m->nb * m->DP * es);
     if (!rc) rc = dev_alloc(m, (void**)&m->cov_ld, (size_t)m->nb * sizeof(double));

@@ -32,7 +32,10 @@
 namespace auxk {
 
 enum { TK = 0, TG, TLS, TGP, TPF, NTAB };
-enum { BAH = 0, BGH, NBTAB };
+// block products of the means partition, and (XPA, XPG) their prefix products
+// within the groups of XGS consecutive maps of the two-level cross-block
+// composition (aux_means.cuh, k_mean_cross2)
+enum { BAH = 0, BGH, XPA, XPG, NBTAB };
 
 template <typename Real> struct CovArgs {
   const Real* prefix;   // scan result [nbc][3 DP^2] (A, C, J); null when nbc == 1

@@ -40,8 +40,6 @@ template <typename Real, int DP> struct Cov2Sizes {
   static constexpr size_t MODEL = (3 * MAT + 2 * VEC) * sizeof(Real);
   // init: model + 2 x (LS, Y, V) + 2 x (2 vectors)
   static constexpr size_t INIT_SMEM = MODEL + (6 * MAT + 4 * VEC) * sizeof(Real);
-  // tables: model + P^f_(t-1), P^f_t + gain warp (LS, W, X) + backward warp (X, LS, LR, Y, G, LRow)
-  static constexpr size_t TAB_SMEM = MODEL + (11 * MAT + 4 * VEC) * sizeof(Real);
   // products: running product, two staged tables, M row scratch, F slot
   static constexpr size_t PROD_SMEM = (5 * MAT + 2 * VEC) * sizeof(Real);
 };
@@ -212,48 +210,83 @@ __global__ void __launch_bounds__(32 * CW_SCAN)
 //   warp 1 (backward tables): X = F P^f_t, P^p_(t+1) = X F^T + Q,
 //     L_P = chol(P^p_(t+1)), Y = L_P^{-1} X, Sigma_t = P^f_t - Y^T Y,
 //     G_t^T = L_P^{-T} Y, chol(Sigma_t)  (t = T - 1: G = 0, chol(P^f_t)).
+// Shared memory is laid out for the case at hand (tab2_layout): with a
+// diagonal F the F and F^T slots and the gain warp's prediction scratch are
+// left out, and the backward warp reuses its slots as the steps free them
+// (X -> Y -> G; the right-aligned factor rows -> chol(Sigma) rows), so that more
+// steps' CTAs are resident at once (the kernel is latency-bound).
 // ---------------------------------------------------------------------------
+template <typename Real, int DP> struct Tab2Layout {
+  static constexpr int MAT = Lay<Real, DP>::MAT, VEC = Lay<Real, DP>::VEC;
+  int sQ, sphi, sb, sF, sFT, SPm, SP, LSg, SW, SXg, SX, LSb, LRb, vdg, vdb, vdb2, total;
+  __host__ __device__ Tab2Layout(bool fdiag) {
+    int o = 0;
+    sQ = o; o += MAT;
+    sphi = o; o += VEC;
+    sb = o; o += VEC;
+    sF = sFT = SXg = -1;
+    if (!fdiag) { sF = o; o += MAT; sFT = o; o += MAT; }
+    SPm = o; o += MAT;
+    SP = o; o += MAT;
+    LSg = o; o += MAT;
+    SW = o; o += MAT;
+    if (!fdiag) { SXg = o; o += MAT; }
+    SX = o; o += MAT;
+    LSb = o; o += MAT;
+    LRb = o; o += MAT;
+    vdg = o; o += VEC;
+    vdb = o; o += VEC;
+    vdb2 = o; o += VEC;
+    total = o;
+  }
+  __host__ __device__ size_t bytes() const { return (size_t)total * sizeof(Real); }
+};
+
 template <typename Real, int DP>
 __global__ void __launch_bounds__(64) k_c2_tables(KP<Real> p, Cov2Args<Real> a) {
   pdl_wait();
   pdl_trigger();
   refresh_delta(p);
-  using Z = Cov2Sizes<Real, DP>;
-  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD;
+  constexpr int LD = Lay<Real, DP>::LD;
   constexpr long DD = (long)DP * DP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
-  Real* sF = sm;
-  Real* sFT = sF + MAT;
-  Real* sQ = sFT + MAT;
-  Real* sb = sQ + MAT;
-  const Real* sphi = sb + VEC;
-  Real* SPm = sb + 2 * VEC;    // P^f_(t-1)
-  Real* SP = SPm + MAT;        // P^f_t
-  Real* LSg = SP + MAT;        // warp 0: chol(S) (LS form)
-  Real* SW = LSg + MAT;        //         W = L_S^{-1}
-  Real* SXg = SW + MAT;        //         F P^f_(t-1) (dense F), symmetrisation scratch
-  Real* SX = SXg + MAT;        // warp 1: X = F P^f_t, then symmetrisation scratch
-  Real* LSb = SX + MAT;        //         chol(P^p_(t+1)) (LS form), then chol(Sigma) (LS form)
-  Real* LRb = LSb + MAT;       //         chol(P^p_(t+1)) right-aligned rows
-  Real* SY = LRb + MAT;        //         Y = L_P^{-1} X
-  Real* SG = SY + MAT;         //         G_t
-  Real* SLr = SG + MAT;        //         chol(Sigma_t) row-major
-  Real* vdg = SLr + MAT;
-  Real* vdb = vdg + VEC;
-  Real* vdb2 = vdb + VEC;
+  const Tab2Layout<Real, DP> Lo(p.fdiag != 0);
+  Real* sQ = sm + Lo.sQ;
+  Real* sphi = sm + Lo.sphi;
+  Real* sF = p.fdiag ? nullptr : sm + Lo.sF;
+  Real* sFT = p.fdiag ? nullptr : sm + Lo.sFT;
+  Real* SPm = sm + Lo.SPm;    // P^f_(t-1)
+  Real* SP = sm + Lo.SP;      // P^f_t
+  Real* LSg = sm + Lo.LSg;    // warp 0: chol(S) (LS form)
+  Real* SW = sm + Lo.SW;      //         W = L_S^{-1}
+  Real* SXg = p.fdiag ? nullptr : sm + Lo.SXg;   // F P^f_(t-1) (dense F)
+  Real* SX = sm + Lo.SX;      // warp 1: prediction scratch, X = F P^f_t, then Y, then G
+  Real* LSb = sm + Lo.LSb;    //         chol(P^p_(t+1)) (LS form), then chol(Sigma) (LS form)
+  Real* LRb = sm + Lo.LRb;    //         chol(P^p_(t+1)) right-aligned rows, then chol(Sigma) rows
+  Real* vdg = sm + Lo.vdg;
+  Real* vdb = sm + Lo.vdb;
+  Real* vdb2 = sm + Lo.vdb2;
   const int t = blockIdx.x;
   const Real* pf = a.tab + (long)TPF * p.nT * DD;
   if (t > 0) stage_mats<Real, DP>(SPm, pf + (long)(t - 1) * DD, DD, 1);
   stage_mats<Real, DP>(SP, pf + (long)t * DD, DD, 1);
-  load_model_slots<Real, DP>(p, sF, sFT, sQ, sb);
+  for (int q = threadIdx.x; q < DP * DP; q += blockDim.x) {
+    const int i = q / DP, j = q % DP;
+    sQ[i * LD + j] = p.Q[q];
+    if (!p.fdiag) {
+      sF[i * LD + j] = p.F[q];
+      sFT[j * LD + i] = p.F[q];
+    }
+  }
+  if (threadIdx.x < DP) sphi[threadIdx.x] = p.F[threadIdx.x * DP + threadIdx.x];
   cp_async_wait<0>();
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
   int bad = 0;
-  // P^p of the step after the one whose P^f is in slot SPf (scratch slot SS)
+  // P^p of the step after the one whose P^f is in slot SPf (scratch slot SS, dense F)
   auto predict = [&](const Real* SPf, Real* SS, Real (&pp)[DP]) {
     if (p.fdiag) {
       Real pr[DP], ph[DP], qr[DP];
@@ -300,6 +333,8 @@ __global__ void __launch_bounds__(64) k_c2_tables(KP<Real> p, Cov2Args<Real> a) 
   } else {
     Real sig[DP];
     if (t < p.nT - 1) {
+      Real pp[DP];
+      predict(SP, SX, pp);   // SX: scratch until X is formed
       // X = F P^f_t
       Real xr[DP];
       if (p.fdiag) {
@@ -310,22 +345,22 @@ __global__ void __launch_bounds__(64) k_c2_tables(KP<Real> p, Cov2Args<Real> a) 
       } else {
         mm_row<Real, DP>(sF + row * LD, SP, xr);
       }
-      Real pp[DP];
-      predict(SP, SY, pp);   // SY: scratch until Y is formed
       chol_la<Real, DP>(pp, LSb, nullptr, LRb, vdb, nullptr, p.d, lane, &bad);
       st_row<Real, DP>(SX, row, xr, act);
       __syncwarp();
       Real rr[DP];
       ld_col<Real, DP>(SX, row, rr);
-      fsolve_pf<Real, DP, true>(LSb, vdb, rr, SY, lane);   // Y = L_P^{-1} X (column `lane`)
+      __syncwarp();
+      fsolve_pf<Real, DP, true>(LSb, vdb, rr, SX, lane);   // Y = L_P^{-1} X (column `lane`), over X
       __syncwarp();
       ld_row<Real, DP>(SP, row, sig);
-      mm_col<Real, DP, true, true>(SY, row, SY, sig);       // Sigma = P^f - Y^T Y
-      ld_col<Real, DP>(SY, row, rr);
-      bsolve_rot<Real, DP>(LRb, vdb, rr, SG, lane);         // row `lane` of G = L_P^{-T} Y column
+      mm_col<Real, DP, true, true>(SX, row, SX, sig);       // Sigma = P^f - Y^T Y
+      ld_col<Real, DP>(SX, row, rr);
+      __syncwarp();
+      bsolve_rot<Real, DP>(LRb, vdb, rr, SX, lane);         // row `lane` of G = L_P^{-T} Y column, over Y
       __syncwarp();
       Real g[DP];
-      ld_row<Real, DP>(SG, row, g);
+      ld_row<Real, DP>(SX, row, g);
       if (act) st_vec<Real, DP>(a.tab + ((long)TG * p.nT + t) * DD + row * DP, g);
     } else {
       Real z[DP];
@@ -333,9 +368,9 @@ __global__ void __launch_bounds__(64) k_c2_tables(KP<Real> p, Cov2Args<Real> a) 
       if (act) st_vec<Real, DP>(a.tab + ((long)TG * p.nT + t) * DD + row * DP, z);
       ld_row<Real, DP>(SP, row, sig);
     }
-    chol_la<Real, DP>(sig, LSb, SLr, nullptr, vdb2, nullptr, p.d, lane, &bad);
+    chol_la<Real, DP>(sig, LSb, LRb, nullptr, vdb2, nullptr, p.d, lane, &bad);
     Real lr[DP];
-    ld_row<Real, DP>(SLr, row, lr);
+    ld_row<Real, DP>(LRb, row, lr);
     if (act) st_vec<Real, DP>(a.tab + ((long)TLS * p.nT + t) * DD + row * DP, lr);
   }
   if (bad && lane == 0) atomicOr(a.status, ST_NOT_PD);

@@ -289,6 +289,151 @@ __global__ void __launch_bounds__(32)
 }
 
 // ---------------------------------------------------------------------------
+// The same compositions in two levels. Either direction is an affine
+// recursion over the blocks, y_j = M_j y_(j-1) + c_j, j = 1 .. n:
+//   forward  M_j = AH_j, c_j = in[j], y_0 = in[0], out[j + 1] = y_j (n = nb - 2);
+//   backward M_j = GH_(nb-j), c_j = in[nb-j], y_0 = 0, out[nb-1-j] = y_j (n = nb - 1).
+// The maps are cut into groups of XGS consecutive j; with the prefix products
+// within each group PP_j = M_j M_(j-1) ... M_(first of the group) (chain
+// independent: k_cov_xprod, once per covariance pass), every chain forms
+//   v_j = M_j v_(j-1) + c_j from v = 0 at each group's start (the groups side by side),
+//   Y_(g+1) = PP_(end of g) Y_g + v_(end of g) from Y_0 = y_0 (one warp, serial over the groups),
+//   y_j = PP_j Y_(g(j)) + v_j (every j side by side),
+// the same values as the one-by-one recursion with XGS + (number of groups) + 1
+// dependent matrix-vector products instead of n. One CTA per chain, one warp per group.
+// ---------------------------------------------------------------------------
+constexpr int XGS = 8;        // maps per group
+constexpr int XG_MAX = 16;    // groups per CTA (one warp each): n <= 128
+
+template <typename Real, int DP>
+__device__ __forceinline__ int xmap_index(int j, int nb, int backward) {   // block of M_j and c_j
+  return backward ? nb - j : j;
+}
+
+// PP_j for both directions: CTA (dir, g) walks group g of direction dir (4 warps, products split by columns)
+template <typename Real, int DP>
+__global__ void __launch_bounds__(32 * CW_SCAN) k_cov_xprod(KP<Real> p, Real* __restrict__ btab) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int MAT = Lay<Real, DP>::MAT, LD = Lay<Real, DP>::LD, NC = DP / CW_SCAN;
+  constexpr long DD = (long)DP * DP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* SACC = reinterpret_cast<Real*>(smem_raw);
+  Real* SM = SACC + MAT;
+  const int dir = blockIdx.x & 1, g = blockIdx.x >> 1;
+  const int nb = p.nb, n = dir ? nb - 1 : nb - 2;
+  const int j0 = g * XGS + 1, j1 = min(n, (g + 1) * XGS);
+  if (j0 > j1) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  const int c0 = warp * NC;
+  const Real* mats = btab + (long)(dir ? BGH : BAH) * nb * DD;
+  Real* pp = btab + (long)(dir ? XPG : XPA) * nb * DD;
+  for (int q = threadIdx.x; q < DP * DP; q += blockDim.x)
+    SACC[(q / DP) * LD + q % DP] = (q / DP == q % DP) ? (Real)1 : (Real)0;
+  for (int j = j0; j <= j1; ++j) {
+    __syncthreads();
+    stage_mats<Real, DP>(SM, mats + (long)xmap_index<Real, DP>(j, nb, dir) * DD, DD, 1);
+    cp_async_wait<0>();
+    __syncthreads();
+    Real out[NC];
+    mm_row_c<Real, DP, NC>(SM + row * LD, SACC, c0, out);   // M_j ACC
+    __syncthreads();
+    if (act) {
+      stn<Real, NC>(SACC + row * LD + c0, out);
+      stn<Real, NC>(pp + (long)j * DD + row * DP + c0, out);
+    }
+  }
+}
+
+template <typename Real, int DP> struct Cross2Sizes {
+  static constexpr size_t SMEM = (size_t)(3 * XG_MAX + 1) * Lay<Real, DP>::VEC * sizeof(Real);
+  static constexpr size_t XPROD_SMEM = (size_t)2 * Lay<Real, DP>::MAT * sizeof(Real);
+};
+
+template <typename Real, int DP>
+__global__ void __launch_bounds__(32 * XG_MAX)
+    k_mean_cross2(KP<Real> p, const Real* __restrict__ btab, const Real* __restrict__ in,
+                  Real* __restrict__ out, int backward) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int VEC = Lay<Real, DP>::VEC;
+  constexpr long DD = (long)DP * DP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sv = reinterpret_cast<Real*>(smem_raw);   // [XG_MAX] per-warp broadcast slots
+  Real* sY = sv + XG_MAX * VEC;                    // [XG_MAX + 1] group starts Y_g
+  Real* sV = sY + (XG_MAX + 1) * VEC;              // [XG_MAX] group-end local values
+  const int c = blockIdx.x;
+  const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  const int nb = p.nb, n = backward ? nb - 1 : nb - 2;
+  const int G = (n + XGS - 1) / XGS;
+  const long cb = (long)c * nb;
+  const Real* mats = btab + (long)(backward ? BGH : BAH) * nb * DD;
+  const Real* pp = btab + (long)(backward ? XPG : XPA) * nb * DD;
+  const Real y0 = backward ? (Real)0 : in[cb * DP + row];
+  if (g == 0 && act) {
+    if (backward) out[(cb + nb - 1) * DP + lane] = (Real)0;
+    else if (nb > 1) out[(cb + 1) * DP + lane] = y0;
+  }
+  auto oidx = [&](int j) { return backward ? nb - 1 - j : j + 1; };
+  Real* vq = sv + g * VEC;
+  // phase 1: local values from zero at the group start
+  Real v[XGS];
+  const int j0 = g * XGS + 1;
+  if (g < G) {
+    Real cur = (Real)0;
+    Real mr[DP], mn[DP];
+    if (j0 <= n) ld_vec<Real, DP>(mats + (long)xmap_index<Real, DP>(j0, nb, backward) * DD + row * DP, mn);
+#pragma unroll
+    for (int s = 0; s < XGS; ++s) {
+      const int j = j0 + s;
+      v[s] = cur;
+      if (j <= n) {
+#pragma unroll
+        for (int q = 0; q < DP; ++q) mr[q] = mn[q];
+        if (j + 1 <= n && s + 1 < XGS)
+          ld_vec<Real, DP>(mats + (long)xmap_index<Real, DP>(j + 1, nb, backward) * DD + row * DP, mn);
+        const Real cj = in[(cb + xmap_index<Real, DP>(j, nb, backward)) * DP + row];
+        put_vec<Real, DP>(vq, cur, lane);
+        cur = dot_rv<Real, DP>(mr, vq) + cj;
+        v[s] = cur;
+      }
+    }
+    if (act) sV[g * VEC + lane] = cur;
+  }
+  __syncthreads();
+  // phase 2: the group starts, one warp
+  if (g == 0) {
+    Real Y = y0;
+    if (act) sY[lane] = Y;
+    for (int h = 0; h + 1 < G; ++h) {
+      Real pr[DP];
+      ld_vec<Real, DP>(pp + (long)((h + 1) * XGS) * DD + row * DP, pr);
+      put_vec<Real, DP>(vq, Y, lane);
+      Y = dot_rv<Real, DP>(pr, vq) + sV[h * VEC + row];
+      if (act) sY[(h + 1) * VEC + lane] = Y;
+    }
+  }
+  __syncthreads();
+  // phase 3: every map's value from its group start
+  if (g < G) {
+#pragma unroll
+    for (int s = 0; s < XGS; ++s) {
+      const int j = j0 + s;
+      if (j <= n) {
+        Real pr[DP];
+        ld_vec<Real, DP>(pp + (long)j * DD + row * DP, pr);
+        const Real yj = dot_rv<Real, DP>(pr, sY + g * VEC) + v[s];
+        if (act) out[(cb + oidx(j)) * DP + lane] = yj;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Filtering means from the true block start, likelihood terms and
 // (APPLY_EPI) the backward elements with the block aggregate. Same grid and
 // chain layout as k_mf_reduce.

@@ -110,7 +110,8 @@ struct Ops {
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_c2_level<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovScanMW<Real, DP>::SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
-    e = cudaFuncSetAttribute(k_c2_tables<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cov2Sizes<Real, DP>::TAB_SMEM);
+    e = cudaFuncSetAttribute(k_c2_tables<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Tab2Layout<Real, DP>(false).bytes());
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_c2_products<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cov2Sizes<Real, DP>::PROD_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
@@ -121,6 +122,10 @@ struct Ops {
     e = cudaFuncSetAttribute(k_mb_apply<Real, DP, MEAN_CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::BWD);
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_mean_cross<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MeanSizes<Real, DP>::CROSS);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_mean_cross2<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cross2Sizes<Real, DP>::SMEM);
+    if (e != cudaSuccess) return AUX_E_CUDA;
+    e = cudaFuncSetAttribute(k_cov_xprod<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cross2Sizes<Real, DP>::XPROD_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_br_node<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BrSizes<Real, DP>::NODE_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
@@ -216,6 +221,16 @@ struct Ops {
   using CZ = CovSizes<Real, DP>;
   static constexpr long DD = (long)DP * DP;
 
+  // the two-level cross-block composition (k_mean_cross2) covers up to XG_MAX
+  // groups of XGS maps; the backward direction has nb - 1 maps
+  static bool cross2_ok(const aux_model* m) { return m->nb - 1 <= XG_MAX * XGS; }
+  static int cross2_groups(const aux_model* m) { return std::max(1, (m->nb - 1 + XGS - 1) / XGS); }
+  static void cross2_products(aux_model* m, const KP<Real>& p, cudaStream_t st) {
+    if (!cross2_ok(m) || m->nb < 2) return;
+    launch_pdl(k_cov_xprod<Real, DP>, 2 * cross2_groups(m), 32 * CW_SCAN, Cross2Sizes<Real, DP>::XPROD_SMEM, st,
+               p, (Real*)m->btab);
+  }
+
   // Covariance form: prefixes by doubling over the steps, then every step's
   // tables and the products of the means partition (aux_cov2.cuh).
   static void cov2_pass(aux_model* m, const KP<Real>& p, cudaStream_t st) {
@@ -241,11 +256,12 @@ struct Ops {
     }
     {
       ProfScope ps(m, PK_COV_APPLY, st);
-      launch_pdl(k_c2_tables<Real, DP>, m->T, 64, C2::TAB_SMEM, st, p, a);
+      launch_pdl(k_c2_tables<Real, DP>, m->T, 64, Tab2Layout<Real, DP>(m->fdiag != 0).bytes(), st, p, a);
     }
     {
-      ProfScope ps(m, PK_COV_PRODUCTS, st);
+      ProfScope ps(m, PK_COV_PRODUCTS, st, (cross2_ok(m) && m->nb >= 2) ? 2 : 1);
       launch_pdl(k_c2_products<Real, DP>, 2 * m->nb, 32 * CW_SCAN, C2::PROD_SMEM, st, p, a);
+      cross2_products(m, p, st);
     }
   }
 
@@ -345,10 +361,11 @@ struct Ops {
         launch_pdl(k_cov_apply<Real, DP>, m->nbc, 96, CZ::APP_SMEM, st, pc, a);
     }
     {
-      ProfScope ps(m, PK_COV_PRODUCTS, st, 2);
+      ProfScope ps(m, PK_COV_PRODUCTS, st, (cross2_ok(m) && m->nb >= 2) ? 3 : 2);
       launch_pdl(k_cov_products<Real, DP>, m->nb, 32, CZ::PROD_SMEM, st, p, a, m->nbc);
       launch_pdl(k_cov_gp_fix<Real, DP>, (m->T + CZ::FIX_WPC - 1) / CZ::FIX_WPC, 32 * CZ::FIX_WPC, CZ::FIX_SMEM,
                  st, p, a, m->Lc, m->nbc);
+      cross2_products(m, p, st);
     }
   }
 
@@ -378,8 +395,12 @@ struct Ops {
       launch_pdl(k_mf_reduce<Real, DP, MEAN_CPW>, grid, MEAN_THREADS, MZ::RED, st, p, a); }
     a.x = nullptr;
     { ProfScope ps(m, PK_SCAN, st);
-      launch_pdl(k_mean_cross<Real, DP>, m->C, 32, MZ::CROSS, st,
-          p, (const Real*)m->btab + (long)BAH * m->nb * DD, a.z, (Real*)m->ms, 0); }
+      if (cross2_ok(m))
+        launch_pdl(k_mean_cross2<Real, DP>, m->C, 32 * cross2_groups(m), Cross2Sizes<Real, DP>::SMEM, st,
+                   p, (const Real*)m->btab, (const Real*)a.z, (Real*)m->ms, 0);
+      else
+        launch_pdl(k_mean_cross<Real, DP>, m->C, 32, MZ::CROSS, st,
+                   p, (const Real*)m->btab + (long)BAH * m->nb * DD, a.z, (Real*)m->ms, 0); }
     a.mstart = (const Real*)m->ms;
     { ProfScope ps(m, PK_APPLY, st);
       launch_pdl(k_mf_apply<Real, DP, MEAN_CPW>, grid, MEAN_THREADS, MZ::APP, st, p, a); }
@@ -399,8 +420,11 @@ struct Ops {
   static void backward_tab(aux_model* m, const KP<Real>& p, BackArgs<Real> b, cudaStream_t st) {
     ProfScope ps(m, PK_BACKWARD, st, 2);
     Real* xnext = (Real*)m->zb;
-    launch_pdl(k_mean_cross<Real, DP>, m->C, 32, MZ::CROSS, st,
-        p, b.gum, b.guv, xnext, 1);
+    if (cross2_ok(m))
+      launch_pdl(k_mean_cross2<Real, DP>, m->C, 32 * cross2_groups(m), Cross2Sizes<Real, DP>::SMEM, st,
+                 p, (const Real*)m->btab, b.guv, xnext, 1);
+    else
+      launch_pdl(k_mean_cross<Real, DP>, m->C, 32, MZ::CROSS, st, p, b.gum, b.guv, xnext, 1);
     launch_pdl(k_mb_apply<Real, DP, MEAN_CPW>, mean_grid(m), MEAN_THREADS, MZ::BWD, st, p, b,
                (const Real*)xnext);
   }

@@ -176,9 +176,12 @@ def test_kalman_step_parity_linear_gaussian_dense_dynamics():
 @pytest.mark.parametrize("dt", ["f32", "mixed"])
 def test_kalman_step_full_size_sampled_chains(dt):
     """d = 128, T = 4096, 16 chains (the mixed-precision workload's shape), cached
-    tables: one step of every chain, chains 0 and 15 against the oracle."""
+    tables: one step of every chain, chains 0 and 15 against the oracle. The log-alpha
+    band of the mixed form is the FP32 band times 4: its split-TF32 products round
+    at about 2^-22 relative instead of FP32's 2^-24."""
     wl = workloads.stochastic_volatility(d=128, T=4096, n_chains=16)
-    moved, worst = _step_parity(wl, 0, "cached", 1, 1e-4, 4e-2, chains=(0, 15), dt=dt)
+    band = 4e-2 if dt == "f32" else 1.6e-1
+    moved, worst = _step_parity(wl, 0, "cached", 1, 1e-4, band, chains=(0, 15), dt=dt)
     print("d = 128, T = 4096: max |d log alpha|", worst)
 
 
