@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define AUX_ABI_VERSION 2
+#define AUX_ABI_VERSION 3
 
 /* status codes */
 #define AUX_OK             0
@@ -83,6 +83,10 @@ extern "C" {
 #define AUX_MODE_SHARED_COV 1  /* one covariance pass per call, shared by all chains */
 #define AUX_MODE_CACHED_COV 2  /* one covariance pass per model, reused until the model changes */
 
+/* dynamics kinds (aux_model_desc.dyn_kind) */
+#define AUX_DYN_HOMOGENEOUS  0  /* one (F, b, Q) for every transition (default) */
+#define AUX_DYN_TIME_VARYING 1  /* (F_t, b_t, Q_t) per transition into x_{t+1}, t = 0 .. T-2 */
+
 /* emission models */
 #define AUX_EMIS_LINEAR_GAUSSIAN 0
 #define AUX_EMIS_SV              1
@@ -112,7 +116,18 @@ typedef struct {
                             (Student-t), else NULL */
   double delta;          /* step size delta > 0; auxiliary covariance (delta/2) I */
   double nu;             /* Student-t degrees of freedom (> 0), ignored otherwise */
+  int32_t dyn_kind;      /* AUX_DYN_HOMOGENEOUS | AUX_DYN_TIME_VARYING (see below) */
 } aux_model_desc;
+
+/* Time-varying dynamics (Algorithm 2 with local F_t, b_t, Q_t; the model of
+ * Appendix A with time-indexed transitions). With AUX_DYN_TIME_VARYING, F, b and
+ * Q point to T - 1 stacked transitions, F [T-1][d][d], b [T-1][d], Q [T-1][d][d]
+ * (each Q_t SPD): x_{t+1} = F_t x_t + b_t + N(0, Q_t). The per-chain path runs
+ * them (both proposals, the scan sampler, the covariance form, d_x <= 32); the
+ * table modes, the square-root form, the bridging sampler, the gradient and the
+ * SV parameterisation calls assume one transition and return AUX_E_UNSUPPORTED
+ * (aux_set_mode with a table mode included); so do AUX_MIXED and the factorised
+ * prior. aux_set_model_params keeps the handle's dyn_kind. */
 
 /* Factorised prior (Section 4.2). With AUX_EMIS_STUDENT_T,
  *   log h(y_t | x_t) = log t_nu(y_t; x_t, R_y),
@@ -413,7 +428,8 @@ int aux_read_profile(aux_model *m, double *ms_per_kind, int32_t *launches_per_ki
  * therefore cannot create a model handle.
  * It computes the same log marginal likelihood as aux_loglik, logZ[c] for each
  * chain's pseudo-observations, from the host model description alone (only
- * dtype, d_x, T, n_chains, block_len, m0, P0, F, b, Q and delta are read).
+ * dtype, d_x, T, n_chains, block_len, m0, P0, F, b, Q, delta and dyn_kind are read;
+ * time-varying dynamics return AUX_E_UNSUPPORTED).
  *   desc   host model description (see aux_model_desc).
  *   ytilde device [C][T][d] compute type (caller-owned input).
  *   logZ   device [C] double (caller-owned output).

@@ -13,12 +13,13 @@ import numpy as np
 
 from . import build as _build
 
-AUX_ABI_VERSION = 2
+AUX_ABI_VERSION = 3
 AUX_OK, AUX_E_INVALID_ARG, AUX_E_NOT_PD, AUX_E_NONFINITE = 0, 1, 2, 3
 AUX_E_CUDA, AUX_E_TIMEOUT, AUX_E_OOM, AUX_E_UNSUPPORTED = 4, 5, 6, 7
 AUX_E_TOO_LARGE = 8
 AUX_NOALLOC_SCRATCH_BYTES = 32 << 20
 AUX_F32, AUX_F64, AUX_MIXED = 0, 1, 2
+AUX_DYN_HOMOGENEOUS, AUX_DYN_TIME_VARYING = 0, 1
 AUX_EMIS_LINEAR_GAUSSIAN, AUX_EMIS_SV, AUX_EMIS_STUDENT_T = 0, 1, 2
 AUX_MODE_PER_CHAIN, AUX_MODE_SHARED_COV, AUX_MODE_CACHED_COV = 0, 1, 2
 AUX_PROPOSAL_FIRST_ORDER, AUX_PROPOSAL_SECOND_ORDER = 1, 2
@@ -49,6 +50,7 @@ class aux_model_desc(ctypes.Structure):
         ("R_y", _dbl_p),
         ("delta", ctypes.c_double),
         ("nu", ctypes.c_double),
+        ("dyn_kind", ctypes.c_int32),
     ]
 
 
@@ -165,6 +167,8 @@ def _make_desc(d_x, T, n_chains, m0, P0, F, b, Q, y, delta, emis_kind, dtype, R_
     desc.emis_kind = int(emis_kind)
     desc.y_per_chain = 1 if y_per_chain else 0
     desc.block_len = int(block_len)
+    # stacked transitions (F of shape [T-1][d][d]) are time-varying dynamics
+    desc.dyn_kind = AUX_DYN_TIME_VARYING if keep["F"].ndim == 3 else AUX_DYN_HOMOGENEOUS
     for k, v in keep.items():
         setattr(desc, k, v.ctypes.data_as(_dbl_p))
     if R_y is not None:

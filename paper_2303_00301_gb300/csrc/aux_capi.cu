@@ -138,11 +138,41 @@ int put(aux_model* m, void** p, const std::vector<unsigned char>& h, bool alloc)
                                                                                   : AUX_E_CUDA;
 }
 
+// time-varying dynamics: the T - 1 transitions in the per-chain kernels' shared-memory
+// slot layout (row stride DP + 16 bytes of padding, zero padded), F^T beside F
+template <typename Real>
+std::vector<unsigned char> slot_stack(const double* A, int n, int d, int DP, bool transpose) {
+  const int LD = DP + (int)(16 / sizeof(Real));
+  std::vector<unsigned char> out((size_t)std::max(n, 1) * DP * LD * sizeof(Real), 0);
+  Real* o = reinterpret_cast<Real*>(out.data());
+  for (int t = 0; t < n; ++t)
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j)
+        o[(size_t)t * DP * LD + (size_t)i * LD + j] = (Real)A[(size_t)t * d * d + (transpose ? j * d + i : i * d + j)];
+  return out;
+}
+template <typename Real>
+std::vector<unsigned char> vec_stack(const double* a, int n, int d, int DP) {
+  const int VEC = (DP + (int)(16 / sizeof(Real)) - 1) / (int)(16 / sizeof(Real)) * (int)(16 / sizeof(Real));
+  std::vector<unsigned char> out((size_t)std::max(n, 1) * VEC * sizeof(Real), 0);
+  Real* o = reinterpret_cast<Real*>(out.data());
+  for (int t = 0; t < n; ++t)
+    for (int i = 0; i < d; ++i) o[(size_t)t * VEC + i] = (Real)a[(size_t)t * d + i];
+  return out;
+}
+
 template <typename Real>
 int upload_model(aux_model* m, const aux_model_desc* d, const std::vector<double>& Ryinv,
                  bool alloc) {
   const int dd = m->d, DP = m->DP;
   int rc;
+  if (m->tv) {   // the stacks, and the first transition as the homogeneous model slots
+    const int n = m->T - 1;
+    if ((rc = put(m, &m->Ftv, slot_stack<Real>(d->F, n, dd, DP, false), alloc))) return rc;
+    if ((rc = put(m, &m->FTtv, slot_stack<Real>(d->F, n, dd, DP, true), alloc))) return rc;
+    if ((rc = put(m, &m->Qtv, slot_stack<Real>(d->Q, n, dd, DP, false), alloc))) return rc;
+    if ((rc = put(m, &m->btv, vec_stack<Real>(d->b, n, dd, DP), alloc))) return rc;
+  }
   if ((rc = put(m, &m->F, pad_matrix<Real>(d->F, dd, DP), alloc))) return rc;
   if ((rc = put(m, &m->Q, pad_matrix<Real>(d->Q, dd, DP), alloc))) return rc;
   if ((rc = put(m, &m->P0, pad_matrix<Real>(d->P0, dd, DP), alloc))) return rc;
@@ -170,6 +200,9 @@ int validate_desc(const aux_model_desc* desc, std::vector<double>& Ryinv) {
   if ((desc->emis_kind == AUX_EMIS_LINEAR_GAUSSIAN || st) && !desc->R_y) return AUX_E_INVALID_ARG;
   if (!(desc->delta > 0.0) || !std::isfinite(desc->delta)) return AUX_E_INVALID_ARG;
   if (st && (!(desc->nu > 0.0) || !std::isfinite(desc->nu))) return AUX_E_INVALID_ARG;
+  if (desc->dyn_kind != AUX_DYN_HOMOGENEOUS && desc->dyn_kind != AUX_DYN_TIME_VARYING) return AUX_E_INVALID_ARG;
+  const bool tvd = desc->dyn_kind == AUX_DYN_TIME_VARYING;
+  if (tvd && (st || desc->dtype == AUX_MIXED || pick_dp(d) == 0 || pick_dp(d) > 32)) return AUX_E_UNSUPPORTED;
   if (st) {
     if (d > 1024 || desc->dtype == AUX_MIXED) return AUX_E_UNSUPPORTED;
     for (int i = 0; i < d; ++i)   // the factorised path needs diagonal F, Q, P0
@@ -185,14 +218,16 @@ int validate_desc(const aux_model_desc* desc, std::vector<double>& Ryinv) {
   if ((long long)C * T * d > (1LL << 31)) return AUX_E_UNSUPPORTED;
   const size_t dd = (size_t)d * d;
   const size_t ny = (size_t)(desc->y_per_chain ? C : 1) * T * d;
-  if (!all_finite(desc->m0, d) || !all_finite(desc->P0, dd) || !all_finite(desc->F, dd) ||
-      !all_finite(desc->b, d) || !all_finite(desc->Q, dd) || !all_finite(desc->y, ny))
+  const size_t ntr = tvd ? (size_t)(T - 1) : 1;   // transitions given
+  if (!all_finite(desc->m0, d) || !all_finite(desc->P0, dd) || !all_finite(desc->F, ntr * dd) ||
+      !all_finite(desc->b, ntr * d) || !all_finite(desc->Q, ntr * dd) || !all_finite(desc->y, ny))
     return AUX_E_NONFINITE;
   if (desc->R_y && desc->emis_kind != AUX_EMIS_SV && !all_finite(desc->R_y, dd))
     return AUX_E_NONFINITE;
   std::vector<double> L;
   if (!is_symmetric(desc->P0, d) || !host_cholesky(desc->P0, d, L)) return AUX_E_NOT_PD;
-  if (!is_symmetric(desc->Q, d) || !host_cholesky(desc->Q, d, L)) return AUX_E_NOT_PD;
+  for (size_t t = 0; t < (tvd ? ntr : 1); ++t)
+    if (!is_symmetric(desc->Q + t * dd, d) || !host_cholesky(desc->Q + t * dd, d, L)) return AUX_E_NOT_PD;
   Ryinv.clear();
   if (desc->emis_kind != AUX_EMIS_SV) {
     if (!is_symmetric(desc->R_y, d) || !host_cholesky(desc->R_y, d, L)) return AUX_E_NOT_PD;
@@ -378,7 +413,8 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
   m->nb = (T + L_blk - 1) / L_blk;
   m->delta = desc->delta;
   m->seed = seed;
-  m->fdiag = diag_flag(desc);
+  m->tv = desc->dyn_kind == AUX_DYN_TIME_VARYING ? 1 : 0;
+  m->fdiag = m->tv ? 0 : diag_flag(desc);   // the time-varying kernels take the dense-F path
   m->diag_hess = hess_diag_flag(desc);
   m->stream = (cudaStream_t)stream;
   m->esz = desc->dtype == AUX_F64 ? sizeof(double) : sizeof(float);   // AUX_MIXED stores FP32
@@ -401,7 +437,7 @@ int aux_init_model(const aux_model_desc* desc, uint64_t seed, void* stream, aux_
   int rc = desc->dtype != AUX_F64 ? upload_model<float>(m, desc, Ryinv, true)
                                   : upload_model<double>(m, desc, Ryinv, true);
   std::vector<double> gc;
-  m->grad_ok = theta_constants(desc, gc) ? 1 : 0;
+  m->grad_ok = (!m->tv && theta_constants(desc, gc)) ? 1 : 0;
   if (!rc) {   // always allocated (sized for d), rewritten by aux_set_model_params
     std::vector<unsigned char> h((size_t)(2 * d + 4 * d * d) * sizeof(double), 0);
     if (m->grad_ok) std::memcpy(h.data(), gc.data(), gc.size() * sizeof(double));
@@ -478,6 +514,7 @@ int aux_set_mode(aux_model* m, int32_t mode) {
   if (!m || (mode != AUX_MODE_PER_CHAIN && mode != AUX_MODE_SHARED_COV && mode != AUX_MODE_CACHED_COV))
     return AUX_E_INVALID_ARG;
   if (m->fact) { m->mode = mode; return AUX_OK; }   // the factorised path has one execution
+  if (m->tv && mode != AUX_MODE_PER_CHAIN) return AUX_E_UNSUPPORTED;   // homogeneous tables only
   if (mode != AUX_MODE_PER_CHAIN && !m->tab) {
     const size_t es = m->esz, DD = (size_t)m->DP * m->DP;
     m->Lc = 1;   // the largest divisor of the means block length that is <= kCovBlockLen
@@ -524,7 +561,7 @@ int aux_set_mode(aux_model* m, int32_t mode) {
 
 int aux_set_filter_form(aux_model* m, int32_t form) {
   if (!m || (form != AUX_FILTER_COVARIANCE && form != AUX_FILTER_SQUARE_ROOT)) return AUX_E_INVALID_ARG;
-  if (m->fact || wide(m)) return form == AUX_FILTER_COVARIANCE ? AUX_OK : AUX_E_UNSUPPORTED;
+  if (m->fact || wide(m) || m->tv) return form == AUX_FILTER_COVARIANCE ? AUX_OK : AUX_E_UNSUPPORTED;
   const int f = form == AUX_FILTER_SQUARE_ROOT ? 1 : 0;
   if (f != m->sqrt_form) {   // the cached tables were made by the other form
     m->cov_valid = 0;
@@ -536,7 +573,7 @@ int aux_set_filter_form(aux_model* m, int32_t form) {
 
 int aux_set_sampler(aux_model* m, int32_t sampler) {
   if (!m || (sampler != AUX_SAMPLER_SCAN && sampler != AUX_SAMPLER_BRIDGING)) return AUX_E_INVALID_ARG;
-  if (m->fact || wide(m)) return sampler == AUX_SAMPLER_SCAN ? AUX_OK : AUX_E_UNSUPPORTED;
+  if (m->fact || wide(m) || m->tv) return sampler == AUX_SAMPLER_SCAN ? AUX_OK : AUX_E_UNSUPPORTED;
   const int old = m->sampler;
   m->sampler = sampler;
   const int rc = br_alloc(m);
@@ -624,7 +661,8 @@ int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {
   if (!m || !desc) return AUX_E_INVALID_ARG;
   if (m->fact) return AUX_E_UNSUPPORTED;
   if (desc->dtype != m->dtype || desc->d_x != m->d || desc->T != m->T || desc->n_chains != m->C ||
-      desc->emis_kind != m->emis || (desc->y_per_chain ? 1 : 0) != m->y_per_chain)
+      desc->emis_kind != m->emis || (desc->y_per_chain ? 1 : 0) != m->y_per_chain ||
+      (desc->dyn_kind == AUX_DYN_TIME_VARYING ? 1 : 0) != m->tv)
     return AUX_E_INVALID_ARG;
   std::vector<double> Ryinv;
   const int vrc = validate_desc(desc, Ryinv);
@@ -635,7 +673,7 @@ int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {
                                      : upload_model<double>(m, desc, Ryinv, false);
   if (rc) return rc;
   m->delta = desc->delta;
-  m->fdiag = diag_flag(desc);
+  m->fdiag = m->tv ? 0 : diag_flag(desc);
   m->diag_hess = hess_diag_flag(desc);
   m->cov_valid = 0;
   if (m->adapt) {   // a new delta restarts the adaptation from it
@@ -645,7 +683,7 @@ int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {
       return AUX_E_CUDA;
   }
   std::vector<double> gc;
-  m->grad_ok = theta_constants(desc, gc) ? 1 : 0;
+  m->grad_ok = (!m->tv && theta_constants(desc, gc)) ? 1 : 0;
   if (m->grad_ok &&
       cudaMemcpy(m->gconst, gc.data(), gc.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
     return AUX_E_CUDA;

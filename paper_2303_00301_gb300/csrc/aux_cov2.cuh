@@ -39,7 +39,8 @@ template <typename Real, int DP> struct Cov2Sizes {
   static constexpr int MAT = Lay<Real, DP>::MAT, VEC = Lay<Real, DP>::VEC;
   static constexpr size_t MODEL = (3 * MAT + 2 * VEC) * sizeof(Real);
   // init: model + 2 x (LS, Y, V) + 2 x (2 vectors)
-  static constexpr size_t INIT_SMEM = MODEL + (6 * MAT + 4 * VEC) * sizeof(Real);
+  // init: model + 2 x (LS, right-aligned L rows, Y, V, r S^{-1} P rows) + 2 x 2 vectors
+  static constexpr size_t INIT_SMEM = MODEL + (10 * MAT + 4 * VEC) * sizeof(Real);
   // products: running product, two staged tables, M row scratch, F slot
   static constexpr size_t PROD_SMEM = (5 * MAT + 2 * VEC) * sizeof(Real);
 };
@@ -47,8 +48,12 @@ template <typename Real, int DP> struct Cov2Sizes {
 // ---------------------------------------------------------------------------
 // The two elements of the pass: P^f_0 (posterior of x_0: S0 = P0 + R,
 // C = P0 - P0 S0^{-1} P0) on warp 0, and E (conditional Kalman step from the
-// identity element: S = Q + R, Y = L_S^{-1} Q, V = L_S^{-1} F, C = Q - Y^T Y,
-// A = F - Y^T V, J = V^T V) on warp 1.
+// identity element: S = Q + R, Y = L_S^{-1} Q, V = L_S^{-1} F, C = Q - Q S^{-1} Q,
+// A = F - Q S^{-1} F, J = V^T V) on warp 1. With R = r I, I - K = r S^{-1}, so the
+// covariances are formed as C = r S^{-1} P = r L_S^{-T} Y (P = P0 or Q,
+// symmetrised) and A = r L_S^{-T} V: no difference of two nearly equal matrices
+// when r is small against P (the subtraction P - Y^T Y loses about
+// log10(|P| / r) digits).
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
 __global__ void __launch_bounds__(64, 1) k_c2_init(KP<Real> p, Cov2Args<Real> a) {
@@ -69,10 +74,12 @@ __global__ void __launch_bounds__(64, 1) k_c2_init(KP<Real> p, Cov2Args<Real> a)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
-  Real* LS = sb + 2 * VEC + warp * 3 * MAT;
-  Real* SY = LS + MAT;
+  Real* LS = sb + 2 * VEC + warp * 5 * MAT;
+  Real* LR = LS + MAT;       // right-aligned rows of L_S
+  Real* SY = LR + MAT;
   Real* SV = SY + MAT;
-  Real* vd = sb + 2 * VEC + 6 * MAT + warp * 2 * VEC;
+  Real* SZ = SV + MAT;       // rows of P S^{-1}
+  Real* vd = sb + 2 * VEC + 10 * MAT + warp * 2 * VEC;
   Real* vdummy = vd + VEC;
   int bad = 0;
   Real s_[DP];
@@ -86,7 +93,7 @@ __global__ void __launch_bounds__(64, 1) k_c2_init(KP<Real> p, Cov2Args<Real> a)
   for (int j = 0; j < DP; ++j) cov[j] = s_[j];
 #pragma unroll
   for (int j = 0; j < DP; ++j) s_[j] += (j == lane && j < p.d) ? p.r : (Real)0;
-  chol_la<Real, DP>(s_, LS, nullptr, nullptr, vd, nullptr, p.d, lane, &bad);
+  chol_la<Real, DP>(s_, LS, nullptr, LR, vd, nullptr, p.d, lane, &bad);
   Real r1[DP], r2[DP], rv[DP];
 #pragma unroll
   for (int j = 0; j < DP; ++j) r1[j] = cov[j];   // column `row` of the symmetric P0 / Q
@@ -94,13 +101,29 @@ __global__ void __launch_bounds__(64, 1) k_c2_init(KP<Real> p, Cov2Args<Real> a)
   zero<Real, DP>(rv);
   fsolve_multi<Real, DP, true>(LS, vd, r1, SY, r2, SV, rv, vdummy, lane);
   __syncwarp();
-  mm_col<Real, DP, true, true>(SY, row, SY, cov);          // C = P - Y^T Y
+  {   // C = r L_S^{-T} Y: row `lane` of (L_S^{-T} Y)^T = P S^{-1}, then symmetrised
+    Real yc[DP], cr[DP];
+    ld_col<Real, DP>(SY, row, yc);
+    bsolve_rot<Real, DP>(LR, vd, yc, SZ, lane);
+    __syncwarp();
+    ld_row<Real, DP>(SZ, row, cr);
+    Real cc[DP];
+    ld_col<Real, DP>(SZ, row, cc);
+#pragma unroll
+    for (int j = 0; j < DP; ++j) cov[j] = (Real)0.5 * p.r * (cr[j] + cc[j]);
+  }
   if (warp == 0) {
     if (act) st_vec<Real, DP>(a.tab + ((long)TPF * p.nT + 0) * DD + row * DP, cov);
   } else {
-    Real an[DP], jn[DP];
-    ld_row<Real, DP>(sF, row, an);
-    mm_col<Real, DP, true, true>(SY, row, SV, an);          // A = F - Y^T V
+    // A = (I - K) F = r S^{-1} F = r L_S^{-T} V (columns of V through the backward solve)
+    Real an[DP], jn[DP], vc[DP];
+    ld_col<Real, DP>(SV, row, vc);
+    __syncwarp();
+    bsolve_rot<Real, DP>(LR, vd, vc, SZ, lane);            // row `lane` of SZ = column `lane` of L_S^{-T} V
+    __syncwarp();
+    ld_col<Real, DP>(SZ, row, an);
+#pragma unroll
+    for (int j = 0; j < DP; ++j) an[j] *= p.r;
     mm_col<Real, DP>(SV, row, SV, jn);                      // J = V^T V
     if (act) {
       st_vec<Real, DP>(a.pw + row * DP, an);

@@ -14,6 +14,8 @@ struct aux_model {
   int dtype = 0, d = 0, DP = 0, T = 0, C = 0, emis = 0, y_per_chain = 0;
   int L = 0, nb = 0;
   int fdiag = 0;             // F has no off-diagonal entries
+  int tv = 0;                // time-varying dynamics (AUX_DYN_TIME_VARYING)
+  void *Ftv = nullptr, *FTtv = nullptr, *Qtv = nullptr, *btv = nullptr;   // [T-1] slot-layout stacks
   int mode = AUX_MODE_PER_CHAIN;
   int order = AUX_PROPOSAL_FIRST_ORDER;
   int diag_hess = 0;         // the emission's Hessian is diagonal (SV, or R_y diagonal)

@@ -50,7 +50,25 @@ template <typename Real> struct KP {
   const Real* rho;   // [C][T][d] diagonal pseudo-observation variance (second order), or null: r
   const double* delta_dev;   // adapted delta on the device, or null: r and sqrt_r as given
   const uint64_t* iter_dev;  // MCMC iteration on the device (graph replay), or null: as passed
+  // time-varying dynamics (AUX_DYN_TIME_VARYING; per-chain path, dense F): the
+  // transition into x_t is (F_{t-1}, b_{t-1}, Q_{t-1}), stored per transition in
+  // the shared-memory slot layout (row stride Lay::LD), F^T beside F; null: F, b, Q
+  int tv;
+  const Real *Ftv, *FTtv, *Qtv, *btv;   // [T-1][DP * LD] x 3, [T-1][VEC]
 };
+
+// the dynamics of transition tt (into x_{tt+1}): the CTA's model slots, or the
+// time-varying stacks
+template <typename Real, int DP> struct Dyn {
+  const Real *F, *FT, *Q, *b;
+};
+template <typename Real, int DP>
+__device__ __forceinline__ Dyn<Real, DP> dyn_at(const KP<Real>& p, int tt, const Real* sF, const Real* sFT,
+                                                const Real* sQ, const Real* sb) {
+  if (!p.tv) return Dyn<Real, DP>{sF, sFT, sQ, sb};
+  constexpr long MAT = Lay<Real, DP>::MAT, VEC = Lay<Real, DP>::VEC;
+  return Dyn<Real, DP>{p.Ftv + tt * MAT, p.FTtv + tt * MAT, p.Qtv + tt * MAT, p.btv + tt * VEC};
+}
 
 // the MCMC iteration that keys the Philox streams of this step
 template <typename Real>
@@ -491,20 +509,21 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::RED_WPC, 1)
       __syncwarp();
       st_row<Real, DP>(SX, row, ar, act);
     } else {
+      const Dyn<Real, DP> dy = dyn_at<Real, DP>(p, t - 1, sF, sFT, sQ, sb);
       Real xr[DP];
-      mm_row<Real, DP>(sF + row * LD, SC, xr);      // X = F C
+      mm_row<Real, DP>(dy.F + row * LD, SC, xr);      // X = F C
       __syncwarp();
       st_row<Real, DP>(SX, row, xr, act);
       __syncwarp();
-      mm_row<Real, DP>(SX + row * LD, sFT, pprow);  // P^p = X F^T + Q
+      mm_row<Real, DP>(SX + row * LD, dy.FT, pprow);  // P^p = X F^T + Q
       Real qr[DP];
-      ld_row<Real, DP>(sQ, row, qr);
+      ld_row<Real, DP>(dy.Q, row, qr);
 #pragma unroll
       for (int j = 0; j < DP; ++j) pprow[j] += qr[j];
       symmetrise_store<Real, DP>(SY, pprow, lane);
-      mpi = dot_row_vec<Real, DP>(sF + row * LD, vb) + sb[row];
+      mpi = dot_row_vec<Real, DP>(dy.F + row * LD, vb) + dy.b[row];
       Real fa[DP];
-      mm_row<Real, DP>(sF + row * LD, SA, fa);      // F A
+      mm_row<Real, DP>(dy.F + row * LD, SA, fa);      // F A
       __syncwarp();
       st_row<Real, DP>(SX, row, fa, act);
     }
@@ -697,8 +716,9 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
 #pragma unroll
   for (int j = 0; j < DP; ++j) ghat[j] = (j == lane) ? (Real)1 : (Real)0;
 
-  // X = F P^f (slot SX), P^p = X F^T + Q (symmetrised, pprow), m^p = F m^f + b (vmp)
-  auto predict = [&]() {
+  // X = F P^f (slot SX), P^p = X F^T + Q (symmetrised, pprow), m^p = F m^f + b (vmp),
+  // with the dynamics of transition tt
+  auto predict = [&](int tt) {
     if (p.fdiag) {
       Real pr[DP], ph[DP], qr[DP];
       ld_row<Real, DP>(SP, row, pr);
@@ -717,16 +737,17 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
       __syncwarp();
       return;
     }
+    const Dyn<Real, DP> dy = dyn_at<Real, DP>(p, tt, sF, sFT, sQ, sb);
     Real xr[DP];
-    mm_row<Real, DP>(sF + row * LD, SP, xr);
-    const Real mpi = dot_row_vec<Real, DP>(sF + row * LD, vm) + sb[row];
+    mm_row<Real, DP>(dy.F + row * LD, SP, xr);
+    const Real mpi = dot_row_vec<Real, DP>(dy.F + row * LD, vm) + dy.b[row];
     __syncwarp();
     st_row<Real, DP>(SX, row, xr, act);
     if (act) vmp[lane] = mpi;
     __syncwarp();
-    mm_row<Real, DP>(SX + row * LD, sFT, pprow);
+    mm_row<Real, DP>(SX + row * LD, dy.FT, pprow);
     Real qr[DP];
-    ld_row<Real, DP>(sQ, row, qr);
+    ld_row<Real, DP>(dy.Q, row, qr);
 #pragma unroll
     for (int j = 0; j < DP; ++j) pprow[j] += qr[j];
     symmetrise_store<Real, DP>(SY, pprow, lane);
@@ -872,12 +893,12 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
     st_row<Real, DP>(SP, row, r, act);
     if (act) vm[lane] = pre[3 * DP * DP + lane];          // b of the prefix = m^f_{s-1}
     __syncwarp();
-    predict();
+    predict(s - 1);
   }
   factor_S(s);
   update(s);
   for (int t = s + 1; t <= e; ++t) {
-    predict();
+    predict(t - 1);
     if (epi) {
       Real a_[DP], s_[DP];
       const Real rl = obs_var<Real>(p, c, t, lane);
@@ -895,7 +916,7 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
   }
   if (epi) {
     if (e < p.nT - 1) {
-      predict();
+      predict(e);
       Real a_[DP];
 #pragma unroll
       for (int j = 0; j < DP; ++j) a_[j] = pprow[j];

@@ -190,6 +190,7 @@ extern "C" int aux_loglik_noalloc(const aux_model_desc* desc, const void* ytilde
   if (!desc || !ytilde || !logZ) return AUX_E_INVALID_ARG;
   if (desc->abi_version != AUX_ABI_VERSION) return AUX_E_INVALID_ARG;
   if (desc->dtype != AUX_F32 && desc->dtype != AUX_F64) return AUX_E_INVALID_ARG;
+  if (desc->dyn_kind != AUX_DYN_HOMOGENEOUS) return AUX_E_UNSUPPORTED;   // one transition (F, b, Q)
   const int d = desc->d_x, T = desc->T, C = desc->n_chains;
   if (d < 1 || T < 1 || C < 1 || desc->block_len < 0) return AUX_E_INVALID_ARG;
   if (!desc->m0 || !desc->P0 || !desc->F || !desc->b || !desc->Q) return AUX_E_INVALID_ARG;

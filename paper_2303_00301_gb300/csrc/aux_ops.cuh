@@ -48,6 +48,9 @@ KP<Real> make_kp(const aux_model* m) {
   p.rho = nullptr;
   p.delta_dev = m->adapt ? m->delta_dev : nullptr;
   p.iter_dev = nullptr;   // set by the MCMC step only (aux_set_device_iteration)
+  p.tv = m->tv;
+  p.Ftv = (const Real*)m->Ftv; p.FTtv = (const Real*)m->FTtv; p.Qtv = (const Real*)m->Qtv;
+  p.btv = (const Real*)m->btv;
   return p;
 }
 

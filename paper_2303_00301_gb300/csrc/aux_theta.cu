@@ -184,7 +184,7 @@ int launch_theta(aux_model* m, const double* g_mu, const double* g_phi, const do
 
 namespace {
 bool theta_handle_ok(const aux_model* m) {
-  return m && !m->fact && m->DP <= 32 && m->gconst;
+  return m && !m->fact && !m->tv && m->DP <= 32 && m->gconst;
 }
 }  // namespace
 

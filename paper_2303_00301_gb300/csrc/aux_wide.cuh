@@ -459,13 +459,15 @@ __global__ void __launch_bounds__(WT, 2) k_w_elem(KP<Real> p, WCovArgs<Real> a) 
   Real* s2 = w_slot<Real, DP>(a, 0, 2);
   int bad = 0;
   const long tstride = (long)p.nT * DD;
-  // t = 0: C_0 = P0 - Y^T Y, Y = chol(P0 + R)^{-1} P0
+  // t = 0: C_0 = P0 - P0 S0^{-1} P0 = r S0^{-1} P0 = r L^{-T} Y, Y = L^{-1} P0, L = chol(P0 + R)
+  // (with R = r I, I - K = r S^{-1}: no difference of nearly equal matrices for small r)
   w_chol<Real, DP>(p.P0, p.r, p.d, S0, piv, &bad);
   w_trinv<Real, DP>(S0, S1);
   w_store<Real, DP>(S0, s0, false);
   w_mm<Real, DP, MX>(s0, false, p.P0, false, s1, nullptr, (Real)1, (Real)0, S0);
-  w_mm<Real, DP, MX>(s1, true, s1, false, a.tab + (long)TPF * tstride, p.P0, (Real)-1, (Real)1, S0);
-  // t >= 1: S = Q + R = L L^T, Y = L^{-1} Q, W = L^{-1} F
+  w_mm<Real, DP, MX>(s0, true, s1, false, s2, nullptr, p.r, (Real)0, S0);
+  w_sym<Real, DP>(s2, a.tab + (long)TPF * tstride);
+  // t >= 1: S = Q + R = L L^T, Y = L^{-1} Q, W = L^{-1} F; C = r L^{-T} Y (symmetrised)
   Real* EA = a.gk;
   Real* EC = EA + DD;
   Real* EJ = EC + DD;
@@ -473,7 +475,8 @@ __global__ void __launch_bounds__(WT, 2) k_w_elem(KP<Real> p, WCovArgs<Real> a) 
   w_trinv<Real, DP>(S0, S1);
   w_store<Real, DP>(S0, s0, false);
   w_mm<Real, DP, MX>(s0, false, p.Q, false, s1, nullptr, (Real)1, (Real)0, S0);
-  w_mm<Real, DP, MX>(s1, true, s1, false, EC, p.Q, (Real)-1, (Real)1, S0);       // C = Q - Y^T Y
+  w_mm<Real, DP, MX>(s0, true, s1, false, s2, nullptr, p.r, (Real)0, S0);
+  w_sym<Real, DP>(s2, EC);                                                            // C = r S^{-1} Q
   w_mm<Real, DP, MX>(s0, false, p.F, false, s2, nullptr, (Real)1, (Real)0, S0);  // W = L^{-1} F
   w_mm<Real, DP, MX>(s2, true, s2, false, EJ, nullptr, (Real)1, (Real)0, S0);    // J = W^T W
   w_mm<Real, DP, MX>(s0, true, s2, false, EA, nullptr, p.r, (Real)0, S0);        // A = r L^{-T} W

@@ -454,3 +454,68 @@ def test_linear_gaussian_stationarity_on_gpu():
     ratio = xe.var(axis=0) / sd ** 2
     assert 0.75 < ratio.mean() < 1.25
     s.close()
+
+
+# ---- time-varying dynamics (AUX_DYN_TIME_VARYING): per-chain path
+
+def _tv_workload(d, T, C, seed, delta=0.5):
+    m = workloads.random_lgssm(d, T, seed=seed, time_varying=True)
+    return workloads.Workload(name="tv", d=d, T=T, n_chains=C, m0=m["m0"], P0=m["P0"],
+                              F=m["F"], b=m["b"], Q=m["Q"], y=m["y"],
+                              emission=workloads.EMIS_LINEAR_GAUSSIAN, delta=delta,
+                              x_init=np.zeros((C, T, d)), Ry=np.eye(d))
+
+
+@pytest.mark.parametrize("d,T,C,L,dt", [(3, 37, 2, 5, "f64"), (2, 2, 2, 1, "f64"), (16, 40, 2, 7, "f64"),
+                                         (5, 41, 2, 7, "f32"), (30, 128, 2, 16, "f32")])
+def test_time_varying_filter_and_path_parity(d, T, C, L, dt):
+    """F_t, b_t, Q_t per transition: log Z, m^f, P^f and a sampled path against the
+    oracle's filter and RTS sampler on the stacked model (Algorithm 2, local dynamics)."""
+    wl = _tv_workload(d, T, C, seed=300 + d * T)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    tol = 1e-9 if dt == "f64" else 1e-4
+    tol_z = 1e-9 if dt == "f64" else 1e-5
+    rng = np.random.default_rng(d * T + 1)
+    yt = rng.standard_normal((C, T, d))
+    eps = rng.standard_normal((C, T, d))
+    s = AuxKalman(wl, dtype=dt, block_len=L)
+    logZ = torch.zeros(C, dtype=torch.float64, device="cuda")
+    mf = torch.zeros((C, T, d), dtype=tdt, device="cuda")
+    Pf = torch.zeros((C, T, d, d), dtype=tdt, device="cuda")
+    s.loglik(_tt(yt, tdt), logZ, mf, Pf)
+    xs = torch.zeros((C, T, d), dtype=tdt, device="cuda")
+    s.sample_path(_tt(yt, tdt), xs, eps=_tt(eps, tdt))
+    torch.cuda.synchronize()
+    R = 0.5 * wl.delta * np.eye(d)
+    for c in range(C):
+        kf = kalman.kalman_filter(yt[c], wl.m0, wl.P0, wl.F, wl.b, wl.Q, R)
+        assert abs(logZ[c].item() - kf["logZ"]) <= tol_z * abs(kf["logZ"]), (c, logZ[c].item(), kf["logZ"])
+        _check_filter(f"tv_{dt}", tol, mf[c].double().cpu().numpy(), Pf[c].double().cpu().numpy(), kf)
+        x_ref = kalman.rts_sample(kf, wl.F, wl.b, wl.Q, eps[c])
+        _, Ps = kalman.rts_smoother(kf, wl.F)
+        _check_path(f"tv_{dt}", tol, xs[c].double().cpu().numpy(), x_ref, Ps)
+    assert s.status()[0] == 0
+    s.close()
+
+
+@pytest.mark.parametrize("proposal", [1, 2])
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_time_varying_step_parity(dt, proposal):
+    wl = _tv_workload(4, 33, 3, seed=77, delta=0.3)
+    tol_x, tol_la = (1e-9, 1e-8) if dt == "f64" else (1e-4, TOL_LA32)
+    _step_and_compare(wl, dt, L=6, n_iters=3, tol_x=tol_x, tol_la=tol_la, proposal=proposal)
+
+
+def test_time_varying_scope_is_reported():
+    from paper_2303_00301_gb300 import _binding as B
+    wl = _tv_workload(3, 12, 2, seed=1)
+    for kw in (dict(mode="shared"), dict(mode="cached"), dict(sampler="bridging"),
+               dict(filter_form="square_root")):
+        with pytest.raises(B.AuxError):
+            AuxKalman(wl, dtype="f64", block_len=4, **kw)
+    s = AuxKalman(wl, dtype="f64", block_len=4)
+    g = torch.zeros(2, 3, 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.AuxError):
+        s.grad(torch.zeros((2, 12, 3), dtype=torch.float64, device="cuda"), g[:, 0], g[:, 1], g,
+               torch.zeros(2, dtype=torch.float64, device="cuda"))
+    s.close()
