@@ -97,16 +97,6 @@ struct Ops {
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_grad_final<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     if (e != cudaSuccess) return AUX_E_CUDA;
-    e = cudaFuncSetAttribute(k_cov_reduce<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::RED_SMEM);
-    if (e != cudaSuccess) return AUX_E_CUDA;
-    e = cudaFuncSetAttribute(k_cov_scan_level<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::SCAN_SMEM);
-    if (e != cudaSuccess) return AUX_E_CUDA;
-    e = cudaFuncSetAttribute(k_cov_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::APP_SMEM);
-    if (e != cudaSuccess) return AUX_E_CUDA;
-    if constexpr (DP >= 16) {
-      e = cudaFuncSetAttribute(k_cov_scan_double_mw<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovScanMW<Real, DP>::SMEM);
-      if (e != cudaSuccess) return AUX_E_CUDA;
-    }
     e = cudaFuncSetAttribute(k_cov_gp_fix<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::FIX_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_c2_init<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cov2Sizes<Real, DP>::INIT_SMEM);
@@ -280,75 +270,33 @@ struct Ops {
     Real* b0 = (Real*)m->cagg0;
     Real* b1 = (Real*)m->cagg1;
     const int nbc = m->nbc;
-    if (m->sqrt_form) {
-      // square-root form (aux_sqrt.cuh): the same distinct aggregates and doubling
-      // on (A, U, Z) factors, for every padded width
-      using SZ = SrSizes<Real, DP>;
-      const bool rag = nbc >= 3 && (m->T % m->Lc) != 0;
-      Real* Q0 = b1;
-      Real* Q1 = b1 + 3 * DD;
-      Real* tail = b1 + 6 * DD;
-      {
-        ProfScope ps(m, PK_COV_REDUCE, st);
-        cudaMemsetAsync(m->cov_status, 0, sizeof(int32_t), st);
-        k_srcov_reduce<Real, DP><<<nbc == 1 ? 1 : (rag ? 3 : 2), 32, SZ::RED_SMEM, st>>>(
-            pc, b0, m->cov_status, (const int*)m->cov_kmap, Q0, tail);
-      }
-      const int n_end = rag ? nbc - 1 : nbc;
-      Real *gk = Q0, *gk2 = Q1;
-      for (int pow2 = 1; pow2 < n_end; pow2 *= 2) {
-        ProfScope ps(m, PK_COV_SCAN, st);
-        const int cnt = std::min(pow2, n_end - pow2);
-        const int next = 2 * pow2 < n_end ? 1 : 0;
-        k_srcov_scan_double<Real, DP><<<cnt + next, 32, SZ::RED_SMEM, st>>>(pc, b0, (const Real*)gk, gk2, 0, pow2,
-                                                                            cnt, m->cov_status);
-        Real* tmp = gk; gk = gk2; gk2 = tmp;
-      }
-      if (rag) {
-        ProfScope ps(m, PK_COV_SCAN, st);
-        k_srcov_scan_double<Real, DP><<<1, 32, SZ::RED_SMEM, st>>>(pc, b0, (const Real*)tail, (Real*)nullptr,
-                                                                  nbc - 2, nbc - 1, 1, m->cov_status);
-      }
-    } else if constexpr (DP >= 16) {
-      // distinct block aggregates only (block 0, a generic block, a short last
-      // block), then the prefixes by doubling (k_cov_scan_double_mw)
-      const bool rag = nbc >= 3 && (m->T % m->Lc) != 0;
-      Real* Q0 = b1;
-      Real* Q1 = b1 + 3 * DD;
-      Real* tail = b1 + 6 * DD;
-      {
-        ProfScope ps(m, PK_COV_REDUCE, st);
-        cudaMemsetAsync(m->cov_status, 0, sizeof(int32_t), st);
-        launch_pdl(k_cov_reduce<Real, DP>, nbc == 1 ? 1 : (rag ? 3 : 2), 32, CZ::RED_SMEM, st, pc, b0,
-                   m->cov_status, (const int*)m->cov_kmap, Q0, tail);
-      }
-      const int n_end = rag ? nbc - 1 : nbc;
-      Real *gk = Q0, *gk2 = Q1;
-      for (int pow2 = 1; pow2 < n_end; pow2 *= 2) {
-        ProfScope ps(m, PK_COV_SCAN, st);
-        const int cnt = std::min(pow2, n_end - pow2);
-        const int next = 2 * pow2 < n_end ? 1 : 0;
-        launch_pdl(k_cov_scan_double_mw<Real, DP>, cnt + next, 32 * CW_SCAN, CovScanMW<Real, DP>::SMEM, st, pc,
-                   b0, (const Real*)gk, gk2, 0, pow2, cnt, m->cov_status);
-        Real* tmp = gk; gk = gk2; gk2 = tmp;
-      }
-      if (rag) {
-        ProfScope ps(m, PK_COV_SCAN, st);
-        launch_pdl(k_cov_scan_double_mw<Real, DP>, 1, 32 * CW_SCAN, CovScanMW<Real, DP>::SMEM, st, pc, b0,
-                   (const Real*)tail, (Real*)nullptr, nbc - 2, nbc - 1, 1, m->cov_status);
-      }
-    } else {
-      {
-        ProfScope ps(m, PK_COV_REDUCE, st);
-        cudaMemsetAsync(m->cov_status, 0, sizeof(int32_t), st);
-        k_cov_reduce<Real, DP><<<nbc, 32, CZ::RED_SMEM, st>>>(pc, b0, m->cov_status, nullptr, nullptr,
-                                                             nullptr);
-      }
-      for (int off = 1; off < nbc; off *= 2) {
-        ProfScope ps(m, PK_COV_SCAN, st);
-        k_cov_scan_level<Real, DP><<<nbc, 32, CZ::SCAN_SMEM, st>>>(pc, b0, b1, off, m->cov_status);
-        Real* tmp = b0; b0 = b1; b1 = tmp;
-      }
+    // square-root form (aux_sqrt.cuh): distinct block aggregates and doubling
+    // on (A, U, Z) factors, for every padded width
+    using SZ = SrSizes<Real, DP>;
+    const bool rag = nbc >= 3 && (m->T % m->Lc) != 0;
+    Real* Q0 = b1;
+    Real* Q1 = b1 + 3 * DD;
+    Real* tail = b1 + 6 * DD;
+    {
+      ProfScope ps(m, PK_COV_REDUCE, st);
+      cudaMemsetAsync(m->cov_status, 0, sizeof(int32_t), st);
+      k_srcov_reduce<Real, DP><<<nbc == 1 ? 1 : (rag ? 3 : 2), 32, SZ::RED_SMEM, st>>>(
+          pc, b0, m->cov_status, (const int*)m->cov_kmap, Q0, tail);
+    }
+    const int n_end = rag ? nbc - 1 : nbc;
+    Real *gk = Q0, *gk2 = Q1;
+    for (int pow2 = 1; pow2 < n_end; pow2 *= 2) {
+      ProfScope ps(m, PK_COV_SCAN, st);
+      const int cnt = std::min(pow2, n_end - pow2);
+      const int next = 2 * pow2 < n_end ? 1 : 0;
+      k_srcov_scan_double<Real, DP><<<cnt + next, 32, SZ::RED_SMEM, st>>>(pc, b0, (const Real*)gk, gk2, 0, pow2,
+                                                                          cnt, m->cov_status);
+      Real* tmp = gk; gk = gk2; gk2 = tmp;
+    }
+    if (rag) {
+      ProfScope ps(m, PK_COV_SCAN, st);
+      k_srcov_scan_double<Real, DP><<<1, 32, SZ::RED_SMEM, st>>>(pc, b0, (const Real*)tail, (Real*)nullptr,
+                                                                nbc - 2, nbc - 1, 1, m->cov_status);
     }
     CovArgs<Real> a{};
     a.prefix = (m->nbc > 1) ? b0 : nullptr;
@@ -358,10 +306,7 @@ struct Ops {
     a.R = m->L / m->Lc;
     {
       ProfScope ps(m, PK_COV_APPLY, st);
-      if (m->sqrt_form)
-        k_srcov_apply<Real, DP><<<m->nbc, 32, SrSizes<Real, DP>::COVAPP_SMEM, st>>>(pc, a);
-      else
-        launch_pdl(k_cov_apply<Real, DP>, m->nbc, 96, CZ::APP_SMEM, st, pc, a);
+      k_srcov_apply<Real, DP><<<m->nbc, 32, SrSizes<Real, DP>::COVAPP_SMEM, st>>>(pc, a);
     }
     {
       ProfScope ps(m, PK_COV_PRODUCTS, st, (cross2_ok(m) && m->nb >= 2) ? 3 : 2);
