@@ -526,8 +526,8 @@ int aux_set_mode(aux_model* m, int32_t mode) {
       if (!rc) rc = dev_alloc(m, &m->cagg0, (size_t)6 * DD * es);
       if (!rc) rc = dev_alloc(m, &m->cagg1, aux_wide_scratch_elems(m->DP, m->n_sm) * es);
     } else {
-      // the covariance scan's buffers; at least two elements (the doubling's powers)
-      if (!rc) rc = dev_alloc(m, &m->cagg0, (size_t)std::max(m->nbc, 2) * 3 * DD * es);
+      // the covariance scan's buffers; at least the doubling's two powers (A, C, J, chol C)
+      if (!rc) rc = dev_alloc(m, &m->cagg0, (size_t)std::max(3 * m->nbc, 8) * DD * es);
       if (!rc) rc = dev_alloc(m, &m->cagg1, (size_t)m->nbc * 3 * DD * es);
     }
     if (!rc) rc = dev_alloc(m, (void**)&m->cov_ldt, (size_t)m->T * sizeof(double));

@@ -23,10 +23,10 @@
 // term uses (ytilde_t - m^p_t)^T S_t^{-1} (ytilde_t - m^p_t) = r^{-1} e^T K'_t e
 // and log det S_t: the per-chain work that remains (aux_means.cuh) is
 // matrix-vector only, one product per step for the filter.
-// This file holds the element operator's matrix part on one CTA
-// (cov_combine_mw, the squaring of the doubling levels) and the composition of
-// the square-root pass's covariance-block products into the means partition
-// (k_cov_products, k_cov_gp_fix).
+// This file holds the table layout, the CTA shape of the operators of the
+// doubling levels (CovScanMW, cov_fw) and the composition of the square-root pass's
+// covariance-block products into the means partition (k_cov_products,
+// k_cov_gp_fix).
 #pragma once
 #include "aux_kernels.cuh"
 
@@ -58,129 +58,26 @@ template <typename Real, int DP> struct CovSizes {
 };
 
 // ---------------------------------------------------------------------------
-// The matrix part (A, C, J) of the element operator (Appendix A.2.1) on one CTA
-// of CW_SCAN warps: the ten d x d products are split by output columns across
-// the warps, the two Cholesky factorisations and the triangular solve run on
-// warp 0.
+// One CTA of CW_SCAN warps per element operator of the doubling levels
+// (aux_cov2.cuh): the d x d products are split by output columns across the
+// warps and the Cholesky factorisations and triangular solves run on one warp,
+// fw. The SM runs warp w of a CTA on its sub-partition w mod 4, so with several
+// CTAs on one SM a fixed fw would queue all of their (latency-bound)
+// factorisations on one sub-partition while the other three idle at the
+// barrier; cov_fw spreads fw over the CTAs.
 // ---------------------------------------------------------------------------
 constexpr int CW_SCAN = 4;
+
+// Factorising warp of CTA b when CTAs are dispatched breadth-first over nsm
+// SMs: the CTAs that share an SM (b, b + nsm, b + 2 nsm, ...) get different
+// warps, and so different sub-partitions, whenever nsm is a multiple of 4.
+__device__ __forceinline__ int cov_fw(int b, int nsm) { return (b + b / nsm) & (CW_SCAN - 1); }
 
 template <typename Real, int DP> struct CovScanMW {
   static constexpr int MAT = Lay<Real, DP>::MAT, VEC = Lay<Real, DP>::VEC;
   static constexpr int NC = DP / CW_SCAN;   // output columns per warp
-  // SA SC SJ SU S2 S3 S4 SN SAe SCe SJe + 2 vectors
   static constexpr size_t SMEM = (11 * MAT + 2 * VEC) * sizeof(Real);
 };
-
-// (A, C, J) of left (x) right into out (one CTA of CW_SCAN warps; products split
-// by columns, Cholesky factorisations and solves on warp 0)
-template <typename Real, int DP>
-__device__ void cov_combine_mw(const KP<Real>& p, const Real* __restrict__ left,
-                               const Real* __restrict__ right, Real* __restrict__ out,
-                               int32_t* __restrict__ status) {
-  using Z = CovScanMW<Real, DP>;
-  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD, NC = Z::NC;
-  constexpr long DD = (long)DP * DP;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* sm = reinterpret_cast<Real*>(smem_raw);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nth = blockDim.x;
-  const bool act = lane < DP;
-  const int row = act ? lane : 0;
-  const int c0 = warp * NC;
-  Real* SA = sm;
-  Real* SC = SA + MAT;
-  Real* SJ = SC + MAT;
-  Real* SU = SJ + MAT;
-  Real* S2 = SU + MAT;
-  Real* S3 = S2 + MAT;
-  Real* S4 = S3 + MAT;
-  Real* SN = S4 + MAT;
-  Real* SAe = SN + MAT;
-  Real* SCe = SAe + MAT;
-  Real* SJe = SCe + MAT;
-  Real* vd1 = SJe + MAT;
-  Real* vd2 = vd1 + VEC;
-  // (A, C, J) of both operands straight into the padded slots (SA SC SJ and SAe SCe SJe
-  // are consecutive), all copies in flight at once
-  stage_mats<Real, DP>(SA, left, DD, 3);
-  stage_mats<Real, DP>(SAe, right, DD, 3);
-  cp_async_wait<0>();
-  __syncthreads();
-  int bad = 0;
-  auto put = [&](Real* S, const Real (&v)[NC]) {   // the warp's column slice of row `row`
-    if (act) stn<Real, NC>(S + row * LD + c0, v);
-  };
-  // U = chol(C_i): LS form in S2, rows in SU
-  if (warp == 0) {
-    Real a[DP];
-    ld_row<Real, DP>(SC, row, a);
-    chol_la<Real, DP>(a, S2, SU, nullptr, vd1, nullptr, p.d, lane, &bad);
-  }
-  __syncthreads();
-  Real t1[NC];
-  mm_row_c<Real, DP, NC>(SJe + row * LD, SU, c0, t1);   // J_e U
-  put(S3, t1);
-  __syncthreads();
-  mm_col_c<Real, DP, NC>(SU, row, S3, c0, t1);          // N = I + U^T J_e U
-#pragma unroll
-  for (int j = 0; j < NC; ++j) t1[j] += (c0 + j == lane) ? (Real)1 : (Real)0;
-  put(SN, t1);
-  __syncthreads();
-  if (warp == 0) {   // L_N = chol(N) (LS form in S4); B = U L_N^{-T} (rows in S2)
-    Real a[DP];
-    ld_row<Real, DP>(SN, row, a);
-    chol_la<Real, DP>(a, S4, nullptr, nullptr, vd2, nullptr, p.d, lane, &bad);
-    Real r[DP];
-    ld_row<Real, DP>(SU, row, r);
-    fsolve_pf<Real, DP, false>(S4, vd2, r, S2, lane);
-  }
-  __syncthreads();
-  mm_row_c<Real, DP, NC>(SAe + row * LD, S2, c0, t1);   // P = A_e B, stored transposed in S3
-  if (act) {
-#pragma unroll
-    for (int j = 0; j < NC; ++j) S3[(c0 + j) * LD + row] = t1[j];
-  }
-  mm_row_c<Real, DP, NC>(SJe + row * LD, SA, c0, t1);   // X1 = J_e A_i
-  put(S4, t1);
-  __syncthreads();
-  mm_col_c<Real, DP, NC>(S2, row, S4, c0, t1);          // Z = B^T X1
-  put(SU, t1);
-  __syncthreads();
-  Real jn[NC], an[NC], cn[NC];
-  ldn<Real, NC>(SJ + row * LD + c0, jn);                // J = J_i + A_i^T X1 - Z^T Z
-  mm_col_c<Real, DP, NC, true>(SA, row, S4, c0, jn);
-  mm_col_c<Real, DP, NC, true, true>(SU, row, SU, c0, jn);
-  mm_row_c<Real, DP, NC>(SAe + row * LD, SA, c0, an);   // A = A_e A_i - P Z
-  mm_col_c<Real, DP, NC, true, true>(S3, row, SU, c0, an);
-  ldn<Real, NC>(SCe + row * LD + c0, cn);               // C = C_e + P P^T
-  mm_col_c<Real, DP, NC, true>(S3, row, S3, c0, cn);
-  __syncthreads();
-  put(SA, an);
-  put(SC, cn);
-  put(SJ, jn);
-  __syncthreads();
-  {   // J symmetrised
-    Real jc[NC];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) jc[j] = SJ[(c0 + j) * LD + row];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) jn[j] = (Real)0.5 * (jn[j] + jc[j]);
-  }
-  __syncthreads();
-  put(SJ, jn);
-  __syncthreads();
-  {   // SA SC SJ -> (A, C, J), 16-byte chunks
-    using V = typename Vec16<Real>::V;
-    constexpr int N = Vec16<Real>::N, CPR = DP / N, PER = DP * CPR;
-    V* g = reinterpret_cast<V*>(out);
-    for (int q = threadIdx.x; q < 3 * PER; q += nth) {
-      const int m = q / PER, rem = q - m * PER, r = rem / CPR, cc = rem - r * CPR;
-      g[q] = *reinterpret_cast<const V*>(SA + m * MAT + r * LD + cc * N);
-    }
-  }
-  if (bad && lane == 0 && warp == 0) atomicOr(status, ST_NOT_PD);
-}
 
 // ---------------------------------------------------------------------------
 // Block products of the means partition (p.L, p.nb; kc = covariance blocks,

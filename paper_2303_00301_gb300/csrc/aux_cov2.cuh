@@ -8,8 +8,9 @@
 // and its A and J parts vanish. Level k forms, for every t in
 // [2^k, min(2^(k+1), T)), P_t = P_(t-2^k) (x) E^(2^k) — one operator per step
 // that needs only the C part of its left operand — and, on one more CTA,
-// E^(2^(k+1)) = E^(2^k) (x) E^(2^k) for the next level: ceil(log2 T) operators
-// of depth and T - 1 prefix operators in all. Given every P^f_t the per-step
+// E^(2^(k+1)) = E^(2^k) (x) E^(2^k) for the next level (each power with the
+// Cholesky factor of its C part, formed by the squaring that produced it):
+// ceil(log2 T) operators of depth and T - 1 prefix operators in all. Given every P^f_t the per-step
 // tables depend on P^f_(t-1), P^f_t and the model only, so each step forms its
 // own (k_c2_tables), and the products over the means partition run one chain
 // per means block (k_c2_products). The tables are those of aux_cov.cuh:
@@ -31,7 +32,7 @@ template <typename Real> struct Cov2Args {
   Real* btab;        // [NBTAB][nb][DP][DP]
   double* ld;        // [nb]
   double* ldt;       // [T]
-  Real* pw;          // [2][3 DP^2]: (A, C, J) of E^(2^k), double buffered over the levels
+  Real* pw;          // [2][4 DP^2]: (A, C, J, chol(C) rows) of E^(2^k), double buffered over the levels
   int32_t* status;   // [1]: ST_NOT_PD when a factorisation failed
 };
 
@@ -49,7 +50,7 @@ template <typename Real, int DP> struct Cov2Sizes {
 // The two elements of the pass: P^f_0 (posterior of x_0: S0 = P0 + R,
 // C = P0 - P0 S0^{-1} P0) on warp 0, and E (conditional Kalman step from the
 // identity element: S = Q + R, Y = L_S^{-1} Q, V = L_S^{-1} F, C = Q - Q S^{-1} Q,
-// A = F - Q S^{-1} F, J = V^T V) on warp 1. With R = r I, I - K = r S^{-1}, so the
+// A = F - Q S^{-1} F, J = V^T V, and chol(C) for the first squaring) on warp 1. With R = r I, I - K = r S^{-1}, so the
 // covariances are formed as C = r S^{-1} P = r L_S^{-T} Y (P = P0 or Q,
 // symmetrised) and A = r L_S^{-T} V: no difference of two nearly equal matrices
 // when r is small against P (the subtraction P - Y^T Y loses about
@@ -130,6 +131,12 @@ __global__ void __launch_bounds__(64, 1) k_c2_init(KP<Real> p, Cov2Args<Real> a)
       st_vec<Real, DP>(a.pw + DD + row * DP, cov);
       st_vec<Real, DP>(a.pw + 2 * DD + row * DP, jn);
     }
+    // chol(C) rows, carried with the power (SY and SZ are free here)
+    __syncwarp();
+    chol_la<Real, DP>(cov, SY, SZ, nullptr, vdummy, nullptr, p.d, lane, &bad);
+    Real ur[DP];
+    ld_row<Real, DP>(SZ, row, ur);
+    if (act) st_vec<Real, DP>(a.pw + 3 * DD + row * DP, ur);
   }
   if (bad && lane == 0) atomicOr(a.status, ST_NOT_PD);
 }
@@ -138,11 +145,12 @@ __global__ void __launch_bounds__(64, 1) k_c2_init(KP<Real> p, Cov2Args<Real> a)
 // C part of P (x) right for a prefix P = (0, C_i, 0), one CTA of CW_SCAN warps:
 // U = chol(C_i), N = I + U^T J_e U, B = U L_N^{-T}, P = A_e B, C = C_e + P P^T
 // (the operator of Appendix A.2.1 with A_i = 0, J_i = 0, in its Cholesky form;
-// same order of operations per entry as cov_combine_mw).
+// same order of operations per entry as the first factorisation and products
+// of cov2_power; factorisations on warp fw).
 // ---------------------------------------------------------------------------
 template <typename Real, int DP>
 __device__ void cov2_conly(const KP<Real>& p, const Real* __restrict__ Ci, const Real* __restrict__ right,
-                           Real* __restrict__ outC, int32_t* __restrict__ status) {
+                           Real* __restrict__ outC, int32_t* __restrict__ status, int fw) {
   using Z = CovScanMW<Real, DP>;
   constexpr int MAT = Z::MAT, LD = Lay<Real, DP>::LD, NC = Z::NC;
   constexpr long DD = (long)DP * DP;
@@ -171,7 +179,7 @@ __device__ void cov2_conly(const KP<Real>& p, const Real* __restrict__ Ci, const
   auto put = [&](Real* S, const Real (&v)[NC]) {
     if (act) stn<Real, NC>(S + row * LD + c0, v);
   };
-  if (warp == 0) {   // U = chol(C_i): rows in SU
+  if (warp == fw) {   // U = chol(C_i): rows in SU
     Real a_[DP];
     ld_row<Real, DP>(SC, row, a_);
     chol_la<Real, DP>(a_, S2, SU, nullptr, vd1, nullptr, p.d, lane, &bad);
@@ -186,7 +194,7 @@ __device__ void cov2_conly(const KP<Real>& p, const Real* __restrict__ Ci, const
   for (int j = 0; j < NC; ++j) t1[j] += (c0 + j == lane) ? (Real)1 : (Real)0;
   put(SN, t1);
   __syncthreads();
-  if (warp == 0) {   // L_N = chol(N); B = U L_N^{-T} (rows in S2)
+  if (warp == fw) {   // L_N = chol(N); B = U L_N^{-T} (rows in S2)
     Real a_[DP];
     ld_row<Real, DP>(SN, row, a_);
     chol_la<Real, DP>(a_, S4, nullptr, nullptr, vd2, nullptr, p.d, lane, &bad);
@@ -205,24 +213,151 @@ __device__ void cov2_conly(const KP<Real>& p, const Real* __restrict__ Ci, const
   ldn<Real, NC>(SCe + row * LD + c0, cn);               // C = C_e + P P^T
   mm_col_c<Real, DP, NC, true>(S3, row, S3, c0, cn);
   if (act) stn<Real, NC>(outC + row * DP + c0, cn);
-  if (bad && lane == 0 && warp == 0) atomicOr(status, ST_NOT_PD);
+  if (bad && lane == 0 && warp == fw) atomicOr(status, ST_NOT_PD);
 }
 
-// Level k of the doubling: CTA i < cnt forms P^f_(pow2 + i) from P^f_i and
-// E^pow2 (pin); CTA cnt (when sq) forms E^(2 pow2) into pout.
+// ---------------------------------------------------------------------------
+// The squaring E' = E (x) E of the doubling (the operator of Appendix A.2.1
+// with both operands E = (A, C, J)), one CTA of CW_SCAN warps. Every power
+// carries U = chol(C) (rows, lower triangular), so the operator starts at
+// N = I + U^T J U:
+//   L_N = chol(N), B = U L_N^{-T}, P = A B, X1 = J A, Z = B^T X1,
+//   C' = C + P P^T,  J' = J + A^T X1 - Z^T Z (symmetrised),  A' = A A - P Z,
+// and, when the next squaring needs it (fac), U' = chol(C') is factorised on
+// warp fw while the other warps form A' and J': the factorisation that the
+// next squaring would otherwise start with, taken off its critical path (the
+// same routine on the same C', so the carried factor is the one it would
+// compute). in, out: [4][DP][DP] (A, C, J, U).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bar_sync_others(int nthreads) {
+  asm volatile("bar.sync 1, %0;\n" ::"r"(nthreads) : "memory");
+}
+
+template <typename Real, int DP>
+__device__ void cov2_power(const KP<Real>& p, const Real* __restrict__ in, Real* __restrict__ out, bool fac,
+                           int32_t* __restrict__ status, int fw) {
+  using Z = CovScanMW<Real, DP>;
+  constexpr int MAT = Z::MAT, VEC = Z::VEC, LD = Lay<Real, DP>::LD, NC = Z::NC;
+  constexpr long DD = (long)DP * DP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool act = lane < DP;
+  const int row = act ? lane : 0;
+  const int c0 = warp * NC;
+  Real* SA = sm;           // the staged element: A, C, J, U (consecutive slots)
+  Real* SC = SA + MAT;
+  Real* SJ = SC + MAT;
+  Real* SU = SJ + MAT;     // U, then U' = chol(C') rows
+  Real* SB = SU + MAT;     // B rows
+  Real* SP = SB + MAT;     // J U, then P^T
+  Real* SL = SP + MAT;     // chol(N) (LS form), then X1
+  Real* SN = SL + MAT;     // N, then Z
+  Real* SCn = SN + MAT;    // C' rows
+  Real* SJn = SCn + MAT;   // J' before symmetrisation
+  Real* LSc = SJn + MAT;   // chol(C') (LS form)
+  Real* vdn = LSc + MAT;
+  Real* vdc = vdn + VEC;
+  stage_mats<Real, DP>(SA, in, DD, 4);
+  cp_async_wait<0>();
+  __syncthreads();
+  int bad = 0;
+  auto put = [&](Real* S, int cc, const Real (&v)[NC]) {
+    if (act) stn<Real, NC>(S + row * LD + cc, v);
+  };
+  Real t1[NC];
+  mm_row_c<Real, DP, NC>(SJ + row * LD, SU, c0, t1);   // J U
+  put(SP, c0, t1);
+  __syncthreads();
+  mm_col_c<Real, DP, NC>(SU, row, SP, c0, t1);          // N = I + U^T J U
+#pragma unroll
+  for (int j = 0; j < NC; ++j) t1[j] += (c0 + j == lane) ? (Real)1 : (Real)0;
+  put(SN, c0, t1);
+  __syncthreads();
+  if (warp == fw) {   // L_N = chol(N); B = U L_N^{-T}
+    Real a[DP];
+    ld_row<Real, DP>(SN, row, a);
+    chol_la<Real, DP>(a, SL, nullptr, nullptr, vdn, nullptr, p.d, lane, &bad);
+    Real r[DP];
+    ld_row<Real, DP>(SU, row, r);
+    fsolve_pf<Real, DP, false>(SL, vdn, r, SB, lane);
+  }
+  __syncthreads();
+  mm_row_c<Real, DP, NC>(SA + row * LD, SB, c0, t1);   // P = A B, stored transposed
+  if (act) {
+#pragma unroll
+    for (int j = 0; j < NC; ++j) SP[(c0 + j) * LD + row] = t1[j];
+  }
+  mm_row_c<Real, DP, NC>(SJ + row * LD, SA, c0, t1);   // X1 = J A
+  put(SL, c0, t1);
+  __syncthreads();
+  Real cn[NC];
+  ldn<Real, NC>(SC + row * LD + c0, cn);               // C' = C + P P^T
+  mm_col_c<Real, DP, NC, true>(SP, row, SP, c0, cn);
+  put(SCn, c0, cn);
+  mm_col_c<Real, DP, NC>(SB, row, SL, c0, t1);          // Z = B^T X1
+  put(SN, c0, t1);
+  __syncthreads();
+  if (warp == fw) {
+    if (fac) {   // U' = chol(C')
+      Real a[DP];
+      ld_row<Real, DP>(SCn, row, a);
+      chol_la<Real, DP>(a, LSc, SU, nullptr, vdc, nullptr, p.d, lane, &bad);
+      Real r[DP];
+      ld_row<Real, DP>(SU, row, r);
+      if (act) st_vec<Real, DP>(out + 3 * DD + row * DP, r);
+    }
+  } else {
+    // column block k of A', C', J' on warp k, block fw on the warp after it
+    const int helper = (fw + 1) & (CW_SCAN - 1);
+    for (int k = 0; k < CW_SCAN; ++k) {
+      if (k == fw ? warp != helper : warp != k) continue;
+      const int cc = k * NC;
+      Real jn[NC], an[NC];
+      ldn<Real, NC>(SJ + row * LD + cc, jn);            // J + A^T X1 - Z^T Z
+      mm_col_c<Real, DP, NC, true>(SA, row, SL, cc, jn);
+      mm_col_c<Real, DP, NC, true, true>(SN, row, SN, cc, jn);
+      mm_row_c<Real, DP, NC>(SA + row * LD, SA, cc, an);   // A A - P Z
+      mm_col_c<Real, DP, NC, true, true>(SP, row, SN, cc, an);
+      put(SJn, cc, jn);
+      ldn<Real, NC>(SCn + row * LD + cc, cn);
+      if (act) {
+        stn<Real, NC>(out + row * DP + cc, an);
+        stn<Real, NC>(out + DD + row * DP + cc, cn);
+      }
+    }
+    bar_sync_others(32 * (CW_SCAN - 1));
+    for (int k = 0; k < CW_SCAN; ++k) {   // J' symmetrised
+      if (k == fw ? warp != helper : warp != k) continue;
+      const int cc = k * NC;
+      Real jn[NC];
+      ldn<Real, NC>(SJn + row * LD + cc, jn);
+#pragma unroll
+      for (int j = 0; j < NC; ++j) jn[j] = (Real)0.5 * (jn[j] + SJn[(cc + j) * LD + row]);
+      if (act) stn<Real, NC>(out + 2 * DD + row * DP + cc, jn);
+    }
+  }
+  if (bad && lane == 0 && warp == fw) atomicOr(status, ST_NOT_PD);
+}
+
+// Level k of the doubling. With sq, CTA 0 forms E^(2 pow2) into pout (the next
+// level waits for it, so it is dispatched first), with its factor when the
+// next level squares again (fac); CTA sq + i, i < cnt, forms P^f_(pow2 + i)
+// from P^f_i and E^pow2 (pin). nsm: the device's SM count.
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32 * CW_SCAN)
-    k_c2_level(KP<Real> p, Cov2Args<Real> a, int pow2, int cnt, const Real* __restrict__ pin,
-               Real* __restrict__ pout) {
+    k_c2_level(KP<Real> p, Cov2Args<Real> a, int pow2, int cnt, int sq, int fac, int nsm,
+               const Real* __restrict__ pin, Real* __restrict__ pout) {
   pdl_wait();
   pdl_trigger();
   constexpr long DD = (long)DP * DP;
-  const int i = blockIdx.x;
+  const int fw = cov_fw(blockIdx.x, nsm);
+  const int i = blockIdx.x - sq;
   Real* pf = a.tab + (long)TPF * p.nT * DD;
-  if (i < cnt)
-    cov2_conly<Real, DP>(p, pf + (long)i * DD, pin, pf + (long)(pow2 + i) * DD, a.status);
+  if (i >= 0)
+    cov2_conly<Real, DP>(p, pf + (long)i * DD, pin, pf + (long)(pow2 + i) * DD, a.status, fw);
   else
-    cov_combine_mw<Real, DP>(p, pin, pin, pout, a.status);
+    cov2_power<Real, DP>(p, pin, pout, fac != 0, a.status, fw);
 }
 
 // ---------------------------------------------------------------------------
@@ -233,26 +368,27 @@ __global__ void __launch_bounds__(32 * CW_SCAN)
 //   warp 1 (backward tables): X = F P^f_t, P^p_(t+1) = X F^T + Q,
 //     L_P = chol(P^p_(t+1)), Y = L_P^{-1} X, Sigma_t = P^f_t - Y^T Y,
 //     G_t^T = L_P^{-T} Y, chol(Sigma_t)  (t = T - 1: G = 0, chol(P^f_t)).
-// Shared memory is laid out for the case at hand (tab2_layout): with a
+// Shared memory is laid out for the case at hand (Tab2Layout): with a
 // diagonal F the F and F^T slots and the gain warp's prediction scratch are
-// left out, and the backward warp reuses its slots as the steps free them
-// (X -> Y -> G; the right-aligned factor rows -> chol(Sigma) rows), so that more
-// steps' CTAs are resident at once (the kernel is latency-bound).
+// left out, Q is read from L2, the gain warp's W overwrites P^f_(t-1) and the
+// backward warp reuses its slots as the steps free them (X -> Y -> G; the
+// right-aligned factor rows -> chol(Sigma) rows), so that more steps' CTAs are
+// resident at once (the kernel is latency-bound): 6 slots and 4 vectors with a
+// diagonal F, eight CTAs per SM in FP32 at DP = 32 (as many as the registers
+// allow), one wave for T = 1024 on 152 SMs.
 // ---------------------------------------------------------------------------
 template <typename Real, int DP> struct Tab2Layout {
   static constexpr int MAT = Lay<Real, DP>::MAT, VEC = Lay<Real, DP>::VEC;
-  int sQ, sphi, sb, sF, sFT, SPm, SP, LSg, SW, SXg, SX, LSb, LRb, vdg, vdb, vdb2, total;
+  int sphi, sF, sFT, SPm, SP, LSg, SW, SXg, SX, LSb, LRb, vdg, vdb, vdb2, total;
   __host__ __device__ Tab2Layout(bool fdiag) {
     int o = 0;
-    sQ = o; o += MAT;
     sphi = o; o += VEC;
-    sb = o; o += VEC;
     sF = sFT = SXg = -1;
     if (!fdiag) { sF = o; o += MAT; sFT = o; o += MAT; }
     SPm = o; o += MAT;
+    SW = SPm;   // the gain warp's W = L_S^{-1} overwrites P^f_(t-1) once the prediction has read it
     SP = o; o += MAT;
     LSg = o; o += MAT;
-    SW = o; o += MAT;
     if (!fdiag) { SXg = o; o += MAT; }
     SX = o; o += MAT;
     LSb = o; o += MAT;
@@ -275,7 +411,6 @@ __global__ void __launch_bounds__(64) k_c2_tables(KP<Real> p, Cov2Args<Real> a) 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
   const Tab2Layout<Real, DP> Lo(p.fdiag != 0);
-  Real* sQ = sm + Lo.sQ;
   Real* sphi = sm + Lo.sphi;
   Real* sF = p.fdiag ? nullptr : sm + Lo.sF;
   Real* sFT = p.fdiag ? nullptr : sm + Lo.sFT;
@@ -294,10 +429,9 @@ __global__ void __launch_bounds__(64) k_c2_tables(KP<Real> p, Cov2Args<Real> a) 
   const Real* pf = a.tab + (long)TPF * p.nT * DD;
   if (t > 0) stage_mats<Real, DP>(SPm, pf + (long)(t - 1) * DD, DD, 1);
   stage_mats<Real, DP>(SP, pf + (long)t * DD, DD, 1);
-  for (int q = threadIdx.x; q < DP * DP; q += blockDim.x) {
-    const int i = q / DP, j = q % DP;
-    sQ[i * LD + j] = p.Q[q];
-    if (!p.fdiag) {
+  if (!p.fdiag) {
+    for (int q = threadIdx.x; q < DP * DP; q += blockDim.x) {
+      const int i = q / DP, j = q % DP;
       sF[i * LD + j] = p.F[q];
       sFT[j * LD + i] = p.F[q];
     }
@@ -315,7 +449,7 @@ __global__ void __launch_bounds__(64) k_c2_tables(KP<Real> p, Cov2Args<Real> a) 
       Real pr[DP], ph[DP], qr[DP];
       ld_row<Real, DP>(SPf, row, pr);
       ld_vec<Real, DP>(sphi, ph);
-      ld_row<Real, DP>(sQ, row, qr);
+      ld_vec<Real, DP>(p.Q + row * DP, qr);   // Q rows from L2
       const Real phi = sphi[row];
 #pragma unroll
       for (int j = 0; j < DP; ++j) pp[j] = fma(pr[j], phi * ph[j], qr[j]);
@@ -327,7 +461,7 @@ __global__ void __launch_bounds__(64) k_c2_tables(KP<Real> p, Cov2Args<Real> a) 
       __syncwarp();
       mm_row<Real, DP>(SS + row * LD, sFT, pp);
       Real qr[DP];
-      ld_row<Real, DP>(sQ, row, qr);
+      ld_vec<Real, DP>(p.Q + row * DP, qr);   // Q rows from L2
 #pragma unroll
       for (int j = 0; j < DP; ++j) pp[j] += qr[j];
       symmetrise_store<Real, DP>(SS, pp, lane);

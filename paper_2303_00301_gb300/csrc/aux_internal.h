@@ -64,7 +64,7 @@ struct aux_model {
   double *opart = nullptr;
   // covariance tables of the table modes (aux_cov.cuh), allocated on the first switch
   void *tab = nullptr, *btab = nullptr, *zb = nullptr, *ms = nullptr;
-  void *cagg0 = nullptr, *cagg1 = nullptr;   // covariance scan buffers [nbc][3 DP^2]
+  void *cagg0 = nullptr, *cagg1 = nullptr;   // covariance scan buffers [nbc][3 DP^2] (cagg0: >= 8 DP^2)
   double *cov_ld = nullptr, *cov_ldt = nullptr;
   int32_t *cov_status = nullptr;
   int *cov_kmap = nullptr;   // [3] blocks 0, 1, nbc - 1: the distinct covariance block aggregates

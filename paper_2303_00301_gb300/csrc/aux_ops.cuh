@@ -242,10 +242,11 @@ struct Ops {
       ProfScope ps(m, PK_COV_SCAN, st);
       const int cnt = std::min(pow2, m->T - pow2);
       const int sq = 2 * pow2 < m->T ? 1 : 0;
-      const Real* pin = a.pw + (lvl & 1) * 3 * DD;
-      Real* pout = a.pw + ((lvl + 1) & 1) * 3 * DD;
+      const int fac = 4 * pow2 < m->T ? 1 : 0;   // the next level squares E^(2 pow2) again
+      const Real* pin = a.pw + (lvl & 1) * 4 * DD;
+      Real* pout = a.pw + ((lvl + 1) & 1) * 4 * DD;
       launch_pdl(k_c2_level<Real, DP>, cnt + sq, 32 * CW_SCAN, CovScanMW<Real, DP>::SMEM, st, p, a, pow2, cnt,
-                 pin, pout);
+                 sq, fac, m->n_sm, pin, pout);
     }
     {
       ProfScope ps(m, PK_COV_APPLY, st);
