@@ -372,14 +372,14 @@ __global__ void __launch_bounds__(32 * BrSizes<Real, DP>::WPC) k_b_mh(KP<Real> p
   const int c = (int)(item / p.nb), k = (int)(item % p.nb);
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const int row = lane < DP ? lane : 0;
-  double acc = 0.0;
+  TermSum<Real> acc;
   for (int t = s; t <= e; ++t) {
     const long ct = (long)c * p.nT + t;
     const Real xi = lane < p.d ? b.xs[ct * p.d + lane] : (Real)0;
-    acc += mh_step_terms<Real, DP>(p, b, ct, t, xi, mh_load<Real>(p, b, ct, t, lane), sRy, vxs, lane, row);
+    mh_step_terms<Real, DP>(p, b, ct, t, xi, mh_load<Real>(p, b, ct, t, lane), sRy, vxs, lane, row, acc);
   }
-  acc = warp_sum<double>(acc);
-  if (lane == 0) b.mh_part[(long)c * p.nb + k] = acc;
+  const double sum = warp_sum<double>(acc.value());
+  if (lane == 0) b.mh_part[(long)c * p.nb + k] = sum;
 }
 
 }  // namespace auxk

@@ -603,13 +603,15 @@ int aux_set_delta_adaptation(aux_model* m, int32_t enable, double target, double
   if (enable) {
     if (!(target > 0.0 && target < 1.0) || !(gain > 0.0) || !std::isfinite(gain)) return AUX_E_INVALID_ARG;
     if (!m->delta_dev) {
-      int rc = dev_alloc(m, (void**)&m->delta_dev, sizeof(double));
+      int rc = dev_alloc(m, (void**)&m->delta_dev, 4 * sizeof(double));
       if (!rc) rc = dev_alloc(m, (void**)&m->adapt_count, sizeof(int32_t));
       if (rc) { m->delta_dev = nullptr; m->adapt_count = nullptr; return rc; }
     }
     if (cudaStreamSynchronize(m->stream) != cudaSuccess) return AUX_E_CUDA;
     const int32_t zero = 0;
-    if (cudaMemcpy(m->delta_dev, &m->delta, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+    double w[4];
+    delta_words(m->delta, w);
+    if (cudaMemcpy(m->delta_dev, w, sizeof(w), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(m->adapt_count, &zero, sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
       return AUX_E_CUDA;
     m->adapt_target = target;
@@ -678,7 +680,9 @@ int aux_set_model_params(aux_model* m, const aux_model_desc* desc) {
   m->cov_valid = 0;
   if (m->adapt) {   // a new delta restarts the adaptation from it
     const int32_t zero = 0;
-    if (cudaMemcpy(m->delta_dev, &m->delta, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+    double w[4];
+    delta_words(m->delta, w);
+    if (cudaMemcpy(m->delta_dev, w, sizeof(w), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(m->adapt_count, &zero, sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
       return AUX_E_CUDA;
   }

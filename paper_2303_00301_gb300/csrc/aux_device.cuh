@@ -784,6 +784,48 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // ---------------------------------------------------------------------------
+// Per-lane running sums of the per-step log-likelihood and MH terms. FP64
+// arithmetic runs at a small fraction of the FP32 rate on this GPU, and a few
+// FP64 operations per step on every warp of the step loops cost more than the
+// loops' FP32 work, so in single precision the sum is carried as an
+// unevaluated pair of floats hi + lo: each addend enters through Knuth's
+// two-sum (the rounding error of hi + x, exact) and a product x y through its
+// exact split x y = p + fma(x, y, -p), which keeps about 48 significant bits
+// over a block of steps; the pair is converted to FP64 once per block. The
+// intrinsics keep the compiler from contracting the error terms. In double
+// precision the sum is a plain double.
+// ---------------------------------------------------------------------------
+template <typename Real> struct TermSum;
+template <> struct TermSum<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void add_prod(double x, double y) { v += x * y; }
+  __device__ __forceinline__ void add_f64(double x) { v += x; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+template <> struct TermSum<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp)));
+    hi = s;
+  }
+  __device__ __forceinline__ void add_prod(float x, float y) {
+    const float p = __fmul_rn(x, y);
+    add(p);
+    lo = __fadd_rn(lo, __fmaf_rn(x, y, -p));
+  }
+  // an FP64 addend (rare paths): its float head and the float of the remainder
+  __device__ __forceinline__ void add_f64(double x) {
+    const float h = (float)x;
+    add(h);
+    lo = __fadd_rn(lo, (float)(x - (double)h));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// ---------------------------------------------------------------------------
 // Column-sliced products for several warps sharing one d x d product: the
 // lane's row, output columns c0 .. c0 + NC - 1 (c0 a multiple of NC, NC * size
 // a multiple of 16 bytes).

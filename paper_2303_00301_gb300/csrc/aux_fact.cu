@@ -49,10 +49,15 @@ __device__ __forceinline__ uint64_t fiter(const FP<Real>& p, uint64_t iter) {
 
 template <typename Real>
 __device__ __forceinline__ void fp_refresh(FP<Real>& p) {
-  if (p.delta_dev) {
-    const double dl = *p.delta_dev;
-    p.r = (Real)(0.5 * dl);
-    p.sqrt_r = (Real)sqrt(0.5 * dl);
+  if (p.delta_dev) {   // the device words of delta (refresh_delta)
+    if constexpr (sizeof(Real) == 4) {
+      const float2 f = *reinterpret_cast<const float2*>(p.delta_dev + 3);
+      p.r = f.x;
+      p.sqrt_r = f.y;
+    } else {
+      p.r = (Real)p.delta_dev[1];
+      p.sqrt_r = (Real)p.delta_dev[2];
+    }
   }
 }
 

@@ -1,7 +1,9 @@
 // aux_internal.h — the model handle and the per-precision operation table.
 #pragma once
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
+#include <cstring>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -9,6 +11,18 @@
 #include "aux_kalman.h"
 
 struct AuxOps;
+
+// The device words of the adapted delta read by the kernels: delta, r = delta
+// / 2 and sqrt(r) in FP64, then (r, sqrt r) rounded to FP32 in the fourth word
+// (the layout that k_adapt_delta writes on the device).
+inline void delta_words(double delta, double w[4]) {
+  const double r = 0.5 * delta, sr = std::sqrt(r);
+  w[0] = delta;
+  w[1] = r;
+  w[2] = sr;
+  const float f[2] = {(float)r, (float)sr};
+  std::memcpy(&w[3], f, sizeof(f));
+}
 
 struct aux_model {
   int dtype = 0, d = 0, DP = 0, T = 0, C = 0, emis = 0, y_per_chain = 0;
@@ -41,7 +55,7 @@ struct aux_model {
   // on-device delta adaptation (aux_set_delta_adaptation)
   int adapt = 0;
   double adapt_target = 0.5, adapt_gain = 1.0;
-  double *delta_dev = nullptr;
+  double *delta_dev = nullptr;   // [4] words: delta, r, sqrt r (FP64), (r, sqrt r) in FP32 (delta_words)
   int32_t *adapt_count = nullptr;
   // device-resident MCMC iteration (aux_set_device_iteration): replayable steps
   int dev_iter = 0;

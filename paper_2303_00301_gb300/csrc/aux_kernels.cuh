@@ -48,7 +48,7 @@ template <typename Real> struct KP {
   int32_t* status_iter;                      // [C], this step's status bits
   int order;                                 // proposal: 1 first order, 2 second order
   const Real* rho;   // [C][T][d] diagonal pseudo-observation variance (second order), or null: r
-  const double* delta_dev;   // adapted delta on the device, or null: r and sqrt_r as given
+  const double* delta_dev;   // adapted delta on the device ([4] words, refresh_delta), or null: r and sqrt_r as given
   const uint64_t* iter_dev;  // MCMC iteration on the device (graph replay), or null: as passed
   // time-varying dynamics (AUX_DYN_TIME_VARYING; per-chain path, dense F): the
   // transition into x_t is (F_{t-1}, b_{t-1}, Q_{t-1}), stored per transition in
@@ -83,15 +83,31 @@ static __global__ void k_iter_next(uint64_t* iter_dev) {
   *iter_dev += 1;
 }
 
-// With on-device delta adaptation the kernels take r = delta / 2 from device
-// memory (written by k_adapt_delta of the previous iteration).
+// With on-device delta adaptation the kernels take r = delta / 2 and sqrt(r)
+// from device memory, written by k_adapt_delta of the previous iteration as
+// four words: delta, r and sqrt(r) in FP64, and (r, sqrt r) rounded to FP32,
+// so that no kernel spends FP64 operations (a sqrt is a dozen) on them.
 template <typename Real>
 __device__ __forceinline__ void refresh_delta(KP<Real>& p) {
   if (p.delta_dev) {
-    const double dl = *p.delta_dev;
-    p.r = (Real)(0.5 * dl);
-    p.sqrt_r = (Real)sqrt(0.5 * dl);
+    if constexpr (sizeof(Real) == 4) {
+      const float2 f = *reinterpret_cast<const float2*>(p.delta_dev + 3);
+      p.r = f.x;
+      p.sqrt_r = f.y;
+    } else {
+      p.r = (Real)p.delta_dev[1];
+      p.sqrt_r = (Real)p.delta_dev[2];
+    }
   }
+}
+
+// the four device words of delta (see refresh_delta)
+__device__ __forceinline__ void store_delta_words(double* w, double delta) {
+  const double r = 0.5 * delta, sr = sqrt(r);
+  w[0] = delta;
+  w[1] = r;
+  w[2] = sr;
+  *reinterpret_cast<float2*>(w + 3) = make_float2((float)r, (float)sr);
 }
 
 // the lane's diagonal entry of the pseudo-observation covariance at (chain, t)
@@ -1002,9 +1018,10 @@ __device__ __forceinline__ MhIn<Real> mh_load(const KP<Real>& p, const BackArgs<
 // ytilde*_t = u_t + r v*_t. sRy: R_y^{-1} rows (linear-Gaussian emission),
 // vxs: a warp-private vector slot. All lanes of the warp call it.
 template <typename Real, int DP>
-__device__ __forceinline__ double mh_step_terms(const KP<Real>& p, const BackArgs<Real>& a, long ct,
-                                                int t, Real xi, const MhIn<Real>& in,
-                                                const Real* sRy, Real* vxs, int lane, int row) {
+__device__ __forceinline__ void mh_step_terms(const KP<Real>& p, const BackArgs<Real>& a, long ct,
+                                              int t, Real xi, const MhIn<Real>& in,
+                                              const Real* sRy, Real* vxs, int lane, int row,
+                                              TermSum<Real>& acc) {
   const bool act = lane < DP;
   const bool obs = !p.mask || p.mask[t];
   Real vsi = 0;
@@ -1016,7 +1033,6 @@ __device__ __forceinline__ double mh_step_terms(const KP<Real>& p, const BackArg
     ld_row<Real, DP>(sRy, row, ry);
     vsi = dot_rv<Real, DP>(ry, vxs);
   }
-  double acc = 0.0;
   if (lane < p.d) {
     const Real xo = in.xo, ui = in.ui, vi = in.vi, yi = in.yi;
     Real gdiff = 0;
@@ -1037,19 +1053,24 @@ __device__ __forceinline__ double mh_step_terms(const KP<Real>& p, const BackArg
       const Real oms = rs * (ui / p.r + vsi - ls * xi);
       const double du = (double)(ui - xo), dus = (double)(ui - xi);
       const double d1 = (double)(oms - xo), d0 = (double)(in.om - xi);
-      acc = (double)gdiff + (du * du - dus * dus) / (2.0 * (double)p.r) +
-            0.5 * (log((double)in.rh) - log((double)rs)) - d1 * d1 / (2.0 * (double)rs) +
-            d0 * d0 / (2.0 * (double)in.rh);
+      acc.add_f64((double)gdiff + (du * du - dus * dus) / (2.0 * (double)p.r) +
+                  0.5 * (log((double)in.rh) - log((double)rs)) - d1 * d1 / (2.0 * (double)rs) +
+                  d0 * d0 / (2.0 * (double)in.rh));
       a.yts[ct * p.d + lane] = oms;
       a.rhos[ct * p.d + lane] = rs;
     } else {
       const Real fwd = vi * (ui - xi) + (Real)0.5 * p.r * vi * vi;
       const Real rev = vsi * (ui - xo) + (Real)0.5 * p.r * vsi * vsi;
-      acc = (double)gdiff + (double)fwd - (double)rev;
+      if constexpr (sizeof(Real) == 4) {
+        acc.add(gdiff);
+        acc.add(fwd);
+        acc.add(-rev);
+      } else {
+        acc.add((double)gdiff + (double)fwd - (double)rev);
+      }
       a.yts[ct * p.d + lane] = ui + p.r * vsi;
     }
   }
-  return acc;
 }
 
 template <typename Real, int DP>
@@ -1084,7 +1105,7 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::BWD_WPC)
       xi = dot_rv<Real, DP>(g, vx) + a.guv[((long)c * p.nb + kk) * DP + row];
     }
   }
-  double acc = 0.0;
+  TermSum<Real> acc;
   for (int t = e; t >= s; --t) {
     const long ct = (long)c * p.nT + t;
     if (t == p.nT - 1) {
@@ -1098,12 +1119,11 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::BWD_WPC)
       xi = dot_rv<Real, DP>(g, vx) + a.U[ct * DP + row];
     }
     if (lane < p.d) a.xs[ct * p.d + lane] = xi;
-    if (a.mh) acc += mh_step_terms<Real, DP>(p, a, ct, t, xi, mh_load<Real>(p, a, ct, t, lane), sRy,
-                                             vxs, lane, row);
+    if (a.mh) mh_step_terms<Real, DP>(p, a, ct, t, xi, mh_load<Real>(p, a, ct, t, lane), sRy, vxs, lane, row, acc);
   }
   if (a.mh) {
-    acc = warp_sum<double>(acc);
-    if (lane == 0) a.mh_part[(long)c * p.nb + k] = acc;
+    const double sum = warp_sum<double>(acc.value());
+    if (lane == 0) a.mh_part[(long)c * p.nb + k] = sum;
   }
 }
 
@@ -1171,7 +1191,7 @@ static __global__ void k_adapt_delta(const double* __restrict__ la_all, int C, d
     const int k = *count + 1;
     double ld = log(*delta) + gain * pow((double)k, -0.6) * (a - target);
     ld = fmin(40.0, fmax(-40.0, ld));
-    *delta = exp(ld);
+    store_delta_words(delta, exp(ld));
     *count = k;
   }
 }

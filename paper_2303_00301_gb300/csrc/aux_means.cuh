@@ -470,10 +470,10 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_apply(KP<Real> p,
   for (int j = 0; j < CPW; ++j) { cidx[j] = cbase + j; valid[j] = cidx[j] < p.C; }
   const bool any = valid[0];
   Real mp[CPW], ubar[CPW];
-  double qacc[CPW];
+  TermSum<Real> qacc[CPW];
 #pragma unroll
   for (int j = 0; j < CPW; ++j) {
-    ubar[j] = 0; qacc[j] = 0.0; mp[j] = 0;
+    ubar[j] = 0; mp[j] = 0;
     if (valid[j]) {
       if (k == 0) mp[j] = p.m0[row];
       else mp[j] = predict_mean<Real, DP>(p, rd, a.mstart[((long)cidx[j] * p.nb + k) * DP + row],
@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_apply(KP<Real> p,
 #pragma unroll
       for (int j = 0; j < CPW; ++j) {
         const Real kv = dot_rv<Real, DP>(kr, vbase + 3 * j * VEC);
-        qacc[j] += (double)ej[j] * (double)kv;   // e^T K' e, summed over the lanes at the end
+        qacc[j].add_prod(ej[j], kv);   // e^T K' e, summed over the lanes at the end
         m[j] = yti[j] - kv;
         const long ct = (long)cidx[j] * p.nT + t;
         if (valid[j] && a.mf && lane < p.d) a.mf[ct * p.d + lane] = m[j];
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW) k_mf_apply(KP<Real> p,
 #pragma unroll
   for (int j = 0; j < CPW; ++j) {
     if (!valid[j]) continue;
-    const double q = warp_sum<double>(qacc[j]) / (double)p.r;
+    const double q = warp_sum<double>(qacc[j].value()) / (double)p.r;
     const int c = cidx[j];
     if (lane == 0) {
       const long ck = (long)c * p.nb + k;
@@ -621,14 +621,13 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW)
   long cb[CPW];
   Real xi[CPW], u1[CPW], u2[CPW];
   MhIn<Real> q1[CPW], q2[CPW];
-  double acc[CPW];
+  TermSum<Real> acc[CPW];
 #pragma unroll
   for (int j = 0; j < CPW; ++j) {
     const int c = cbase + j;
     valid[j] = c < p.C;
     cb[j] = (long)(valid[j] ? c : 0) * p.nT;
     xi[j] = valid[j] ? xnext[((long)c * p.nb + k) * DP + row] : (Real)0;
-    acc[j] = 0.0;
     // the lane's U_t and MH inputs, fetched two steps ahead
     u1[j] = b.U[(cb[j] + e) * DP + row];
     q1[j] = b.mh ? mh_load<Real>(p, b, cb[j] + e, e, lane) : MhIn<Real>{};
@@ -666,14 +665,14 @@ __global__ void __launch_bounds__(32 * MEAN_CHAINS / CPW)
         const long ct = cb[j] + t;
         if (valid[j] && lane < p.d) b.xs[ct * p.d + lane] = xi[j];
         if (b.mh && valid[j])
-          acc[j] += mh_step_terms<Real, DP>(p, b, ct, t, xi[j], qc[j], sRy, vbase + (3 * j + 1) * VEC, lane, row);
+          mh_step_terms<Real, DP>(p, b, ct, t, xi[j], qc[j], sRy, vbase + (3 * j + 1) * VEC, lane, row, acc[j]);
       }
     }
   }
 #pragma unroll
   for (int j = 0; j < CPW; ++j) {
     if (valid[j] && b.mh) {
-      const double r = warp_sum<double>(acc[j]);
+      const double r = warp_sum<double>(acc[j].value());
       if (lane == 0) b.mh_part[(long)(cbase + j) * p.nb + k] = r;
     }
   }
