@@ -934,17 +934,19 @@ def run_ours(args):
         torch.cuda.synchronize()
         return [e0.elapsed_time(e1) for e0, e1 in ev]
 
-    def run_mode(mode, with_clocks, proposal=1, adapt=False, sampler="scan", filter_form="covariance"):
+    def run_mode(mode, with_clocks, proposal=1, adapt=False, sampler="scan", filter_form="covariance",
+                 dtype=None):
         """Warm-up; one profiled eager pass (per-kernel events: the kernel
         breakdown and roofline durations); then the timed pass: the MCMC
         iteration captured once in a CUDA graph (iteration index on the
         device) and replayed args.steps times; then the same steps eager
         without events, for comparison."""
-        sm = AuxKalman(wl, dtype=w["dtype"], block_len=block_len_for(mode), mode=mode, proposal=proposal,
+        dt_m = dtype or w["dtype"]
+        sm = AuxKalman(wl, dtype=dt_m, block_len=block_len_for(mode), mode=mode, proposal=proposal,
                        sampler=sampler, filter_form=filter_form)
         if adapt:
             sm.adapt_delta(True, target=0.5, gain=1.0)
-        xm = torch.tensor(wl.x_init, dtype=tdt, device="cuda")
+        xm = torch.tensor(wl.x_init, dtype=torch.float64 if dt_m == "f64" else tdt, device="cuda")
         accm = torch.zeros(C, dtype=torch.int32, device="cuda")
         lam = torch.zeros(C, dtype=torch.float64, device="cuda")
         itm = 0
@@ -981,7 +983,7 @@ def run_ours(args):
         eager_ms = timed_steps(lambda k: sm.step(xm, 1, iter0=itm + k, accept_count=accm, log_alpha=lam),
                                args.steps)
         itm += args.steps
-        res = {"mode": mode, "proposal": "second order" if proposal == 2 else "first order",
+        res = {"mode": mode, "dtype": dt_m, "proposal": "second order" if proposal == 2 else "first order",
                "sampler": "divide-and-conquer bridging" if sampler == "bridging" else "(G, U) suffix scan",
                "filter_form": filter_form,
                "delta": sm.delta(), "delta_adaptation": bool(adapt),
@@ -1030,6 +1032,13 @@ def run_ours(args):
         so.close()
         others["per_chain_square_root"] = r
         profs["per_chain_square_root"] = po
+        # the headline mode in FP64 (the precision of the paper's SV runs, Section 4.1)
+        if w["dtype"] == "f32":
+            so, _, _, _, po, _, r = run_mode(args.mode, False, dtype="f64", sampler=args.sampler,
+                                             filter_form=args.filter_form)
+            so.close()
+            others[args.mode + "_f64"] = r
+            profs[args.mode + "_f64"] = po
         # the square-root form of the table modes' covariance pass
         if not (args.mode == "shared" and args.filter_form == "square_root"):
             so, _, _, _, po, _, r = run_mode("shared", False, filter_form="square_root")

@@ -98,7 +98,7 @@ typedef struct {
   int32_t abi_version;   /* AUX_ABI_VERSION */
   int32_t dtype;         /* AUX_F32 | AUX_F64 | AUX_MIXED */
   int32_t d_x;           /* state dimension: 1..128 (AUX_F32; 33..128 in the table
-                            modes only, see "Wide state dimensions"), 1..16 (AUX_F64);
+                            modes only, see "Wide state dimensions"), 1..32 (AUX_F64);
                             1..1024 with AUX_EMIS_STUDENT_T (factorised prior, see below) */
   int32_t T;             /* number of states, T >= 1 */
   int32_t n_chains;      /* C >= 1 */
@@ -204,8 +204,10 @@ int aux_sample_path(aux_model *m, const void *ytilde, const void *eps, uint64_t 
  *   g_cholSigma device [C][d][d] double (lower triangle; upper entries 0);
  *   g_delta     device [C] double.
  * Errors: INVALID_ARG; UNSUPPORTED unless F is diagonal with |phi_i| < 1,
- * m0 = (I - F)^{-1} b and P0 is the stationary covariance; OOM on the first
- * call (it allocates C*T*d^2 elements for the backward covariances). */
+ * m0 = (I - F)^{-1} b and P0 is the stationary covariance, and for AUX_F64
+ * with d_x > 16 (the smoother's per-block staging would exceed a CTA's shared
+ * memory); OOM on the first call (it allocates C*T*d^2 elements for the
+ * backward covariances). */
 int aux_loglik_grad(aux_model *m, const void *ytilde, double *logZ, double *g_mu, double *g_Phi,
                     double *g_cholSigma, double *g_delta, void *stream);
 /* (ytilde may be NULL: the pseudo-observations of the last aux_kalman_step's

@@ -13,8 +13,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libauxkalman.so")
-UNITS = ["aux_f32_d32.cu", "aux_wide.cu", "aux_f32.cu", "aux_f64.cu", "aux_capi.cu", "aux_noalloc.cu", "aux_fact.cu",
-         "aux_theta.cu"]
+UNITS = ["aux_f32_d32.cu", "aux_f64_d32.cu", "aux_wide.cu", "aux_f32.cu", "aux_f64.cu", "aux_capi.cu",
+         "aux_noalloc.cu", "aux_fact.cu", "aux_theta.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -212,7 +212,7 @@ int validate_desc(const aux_model_desc* desc, std::vector<double>& Ryinv) {
   } else {
     const int DP = pick_dp(d);
     if (DP == 0) return AUX_E_UNSUPPORTED;
-    if (desc->dtype == AUX_F64 && DP > 16) return AUX_E_UNSUPPORTED;
+    if (desc->dtype == AUX_F64 && DP > 32) return AUX_E_UNSUPPORTED;
     if (desc->dtype == AUX_MIXED && DP <= 32) return AUX_E_UNSUPPORTED;   // the wide widths only
   }
   if ((long long)C * T * d > (1LL << 31)) return AUX_E_UNSUPPORTED;
@@ -698,6 +698,7 @@ int aux_loglik_grad(aux_model* m, const void* ytilde, double* logZ, double* g_mu
                     double* g_cholSigma, double* g_delta, void* stream) {
   if (!m || !g_mu || !g_Phi || !g_cholSigma || !g_delta) return AUX_E_INVALID_ARG;
   if (!m->grad_ok || m->fact || wide(m)) return AUX_E_UNSUPPORTED;
+  if (m->dtype == AUX_F64 && m->DP > 16) return AUX_E_UNSUPPORTED;   // smoother staging > 227 KB
   if (!ytilde) ytilde = m->yt;   // the last aux_kalman_step's pseudo-observations
   m->stream = (cudaStream_t)stream;
   const size_t es = m->esz, DP = m->DP, nbC = (size_t)m->C * m->nb;

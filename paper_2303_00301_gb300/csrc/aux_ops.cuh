@@ -81,6 +81,7 @@ template <typename Real, int DP>
 struct Ops {
   using Z = Sizes<Real, DP>;
 
+  static constexpr size_t kMaxSmemPerCta = 227 * 1024;   // opt-in dynamic shared memory of one CTA
   static int prepare() {
     cudaError_t e = cudaSuccess;
     e = cudaFuncSetAttribute(k_filter_reduce<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Z::RED_SMEM);
@@ -91,10 +92,14 @@ struct Ops {
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_sample_backward<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Z::BWD_SMEM);
     if (e != cudaSuccess) return AUX_E_CUDA;
-    e = cudaFuncSetAttribute(k_smooth_reduce<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GradSizes<Real, DP>::RED_SMEM);
-    if (e != cudaSuccess) return AUX_E_CUDA;
-    e = cudaFuncSetAttribute(k_smooth_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GradSizes<Real, DP>::APP_SMEM);
-    if (e != cudaSuccess) return AUX_E_CUDA;
+    // the gradient's smoother kernels need more than a CTA's 227 KB of shared
+    // memory in FP64 at DP = 32; aux_loglik_grad refuses that case
+    if constexpr (GradSizes<Real, DP>::RED_SMEM <= kMaxSmemPerCta && GradSizes<Real, DP>::APP_SMEM <= kMaxSmemPerCta) {
+      e = cudaFuncSetAttribute(k_smooth_reduce<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GradSizes<Real, DP>::RED_SMEM);
+      if (e != cudaSuccess) return AUX_E_CUDA;
+      e = cudaFuncSetAttribute(k_smooth_apply<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GradSizes<Real, DP>::APP_SMEM);
+      if (e != cudaSuccess) return AUX_E_CUDA;
+    }
     e = cudaFuncSetAttribute(k_grad_final<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     if (e != cudaSuccess) return AUX_E_CUDA;
     e = cudaFuncSetAttribute(k_cov_gp_fix<Real, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CovSizes<Real, DP>::FIX_SMEM);

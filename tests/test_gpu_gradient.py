@@ -124,3 +124,14 @@ def test_autograd_function_and_theta_ascent():
         m = (m + 1e-3 * m.grad).detach()
     assert all(b > a for a, b in zip(vals, vals[1:]))
     s.close()
+
+
+def test_grad_refuses_f64_at_padded_width_32():
+    """FP64 at d_x > 16: sampling runs, the gradient's smoother does not fit a CTA's
+    shared memory and aux_loglik_grad reports AUX_E_UNSUPPORTED instead."""
+    from paper_2303_00301_gb300._binding import AuxError
+    theta = _theta(20, 3)
+    yt = np.zeros((2, 16, 20))
+    with pytest.raises(AuxError) as ei:
+        _gpu_grad(theta, yt, 4, "f64")
+    assert ei.value.code == 7   # AUX_E_UNSUPPORTED

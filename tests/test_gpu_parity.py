@@ -254,6 +254,21 @@ def test_kalman_step_parity_sv_f32_full_size_sampled_chains(mode):
                       tol_la=TOL_LA32, mode=mode)
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_kalman_step_parity_sv_f64_padded_32(mode):
+    """FP64 at the padded width 32 (d = 30, the SV shape of the paper's Section 4.1
+    runs, which it ran in FP64): the same FP64 bands as the small FP64 cases."""
+    wl = workloads.stochastic_volatility(d=30, T=96, n_chains=3, delta=0.0183)
+    _step_and_compare(wl, "f64", L=8, n_iters=2, tol_x=1e-9, tol_la=1e-8, mode=mode)
+
+
+def test_kalman_step_parity_sv_f64_full_size_sampled_chains():
+    """d=30, T=1024, 32 chains in FP64 in the benchmark's shared-mode launch
+    configuration; oracle on 3 chains."""
+    wl = workloads.stochastic_volatility(d=30, T=1024, n_chains=32)
+    _step_and_compare(wl, "f64", L=0, n_iters=1, chains=[0, 17, 31], tol_x=1e-9, tol_la=1e-8, mode="shared")
+
+
 # ---- second-order proposal (Section 2.2, Eqs. (2.8)-(2.9)), per-chain path
 
 def test_second_order_sv_f64():
