@@ -214,6 +214,20 @@ int aux_loglik_grad(aux_model *m, const void *ytilde, double *logZ, double *g_mu
  * proposal, ytilde_t = u_t + (delta/2) v_t at the state before that step, kept in
  * the handle's workspace.) */
 
+/* Cap on the device memory aux_loglik_grad may use for the backward elements
+ * (G_t, U_t) and covariances Sigma_t that its smoother reads, C*T*(2 p^2 + p)
+ * elements when all are stored (p = d_x rounded up to 4, 8, 16 or 32).
+ * max_bytes = 0 (the default): store them all. Otherwise, when that store
+ * would exceed max_bytes, the gradient recomputes instead of storing: the
+ * in-block filter (Appendix A.2.1, from the stored block prefixes of the
+ * scan) runs over chunks of scan blocks into a scratch of at most max_bytes
+ * (at least one block of every chain), once for the smoother's block
+ * aggregates and once for its backward sweep, so the filter's in-block pass
+ * runs twice. The result is the same as with the full store (the same
+ * arithmetic per block). Errors: INVALID_ARG; UNSUPPORTED where
+ * aux_loglik_grad is. */
+int aux_set_grad_memory(aux_model *m, uint64_t max_bytes);
+
 /* The SV parameterisation theta = (mu, phi, L = chol Sigma) behind the C ABI
  * (Section 4.1): F = diag(phi), b = (1 - phi) mu, Q = L L^T, p_0 the stationary
  * law (m0 = mu, P0_ij = Q_ij / (1 - phi_i phi_j)). The handle keeps theta on the

@@ -126,6 +126,11 @@ class AuxKalman:
         """aux_loglik_grad; ytilde None: the last step's pseudo-observations."""
         self.b.aux_loglik_grad(self.handle, ytilde, g_mu, g_phi, g_L, g_delta, logZ, stream)
 
+    def grad_memory(self, max_bytes):
+        """aux_set_grad_memory: cap the gradient's store of G_t, Sigma_t, U_t
+        (recompute the in-block filter per chunk of blocks above it; 0: store all)."""
+        self.b.aux_set_grad_memory(self.handle, max_bytes)
+
     def theta_step(self, g_mu, g_phi, g_L, lr, stream=None):
         """The on-device theta-update inside the sweep (aux_sv_theta_step)."""
         self.b.aux_sv_theta_step(self.handle, g_mu, g_phi, g_L, lr, stream)

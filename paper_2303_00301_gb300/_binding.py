@@ -104,6 +104,8 @@ def _load():
     lib.aux_get_device_iteration.restype = ctypes.c_int
     lib.aux_loglik_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.aux_loglik_grad.restype = ctypes.c_int
+    lib.aux_set_grad_memory.argtypes = [vp, ctypes.c_uint64]
+    lib.aux_set_grad_memory.restype = ctypes.c_int
     lib.aux_set_model_params.argtypes = [vp, ctypes.POINTER(aux_model_desc)]
     lib.aux_set_model_params.restype = ctypes.c_int
     dp = ctypes.POINTER(ctypes.c_double)
@@ -236,6 +238,11 @@ def aux_loglik_grad(handle, ytilde, g_mu, g_Phi, g_cholSigma, g_delta, logZ=None
     rc = LIB.aux_loglik_grad(handle, _ptr(ytilde), _ptr(logZ), _ptr(g_mu), _ptr(g_Phi),
                              _ptr(g_cholSigma), _ptr(g_delta), _stream(stream))
     _check(rc, "aux_loglik_grad")
+
+
+def aux_set_grad_memory(handle, max_bytes):
+    """Cap aux_loglik_grad's store of G_t, Sigma_t, U_t (bytes; 0: store all)."""
+    _check(LIB.aux_set_grad_memory(handle, int(max_bytes)), "aux_set_grad_memory")
 
 
 def _dptr(a):

@@ -703,13 +703,33 @@ int aux_loglik_grad(aux_model* m, const void* ytilde, double* logZ, double* g_mu
   m->stream = (cudaStream_t)stream;
   const size_t es = m->esz, DP = m->DP, nbC = (size_t)m->C * m->nb;
   int rc = AUX_OK;
-  if (!m->Sig) rc = dev_alloc(m, &m->Sig, (size_t)m->C * m->T * DP * DP * es);
+  // G_t, Sigma_t, U_t of every (chain, step), or of a chunk of blocks (recompute)
+  const size_t per_step = (2 * DP * DP + DP) * es;
+  m->grad_kc = 0;
+  if (m->grad_mem && (size_t)m->C * m->T * per_step > m->grad_mem) {
+    const size_t per_block = (size_t)m->C * m->L * per_step;
+    m->grad_kc = (int)std::min<size_t>((size_t)m->nb, std::max<size_t>(1, m->grad_mem / per_block));
+    const size_t need = (size_t)m->grad_kc * per_block;
+    if (m->gscr_bytes < need) {
+      rc = dev_alloc(m, &m->gscr, need);
+      m->gscr_bytes = rc ? 0 : need;
+    }
+  } else if (!m->Sig) {
+    rc = dev_alloc(m, &m->Sig, (size_t)m->C * m->T * DP * DP * es);
+  }
   if (!rc && !m->sgu) rc = dev_alloc(m, &m->sgu, nbC * (2 * DP * DP + DP) * es);
   if (!rc && !m->gpart) rc = dev_alloc(m, &m->gpart, nbC * (2 * DP * DP + DP) * es);
   if (!rc && !m->opart) rc = dev_alloc(m, (void**)&m->opart, nbC * sizeof(double));
   if (!rc && !m->s0) rc = dev_alloc(m, &m->s0, (size_t)m->C * (DP * DP + DP) * es);
   if (rc) return rc;
   return m->ops->loglik_grad(m, ytilde, logZ, g_mu, g_Phi, g_cholSigma, g_delta, m->stream);
+}
+
+int aux_set_grad_memory(aux_model* m, uint64_t max_bytes) {
+  if (!m) return AUX_E_INVALID_ARG;
+  if (m->fact || wide(m)) return AUX_E_UNSUPPORTED;
+  m->grad_mem = (size_t)max_bytes;
+  return AUX_OK;
 }
 
 int aux_get_status(aux_model* m, int32_t* per_chain_status) {

@@ -30,6 +30,7 @@ template <typename Real> struct SmoothArgs {
   Real* gpart;        // [C][nb][SGS]: M rows, D rows, sum of e-bar
   double* opart;      // [C][nb]: sum |ytilde - m^s|^2 + tr P^s
   Real* s0;           // [C][DP*DP + DP]: S0 rows, a_0
+  BlockRange rg;      // blocks to run; indexing of G, U, Sig (G, U, Sig hold the range only)
 };
 
 template <typename Real, int DP> struct GradSizes {
@@ -51,8 +52,9 @@ __global__ void __launch_bounds__(32 * GradSizes<Real, DP>::WPC)
   Real* sm = reinterpret_cast<Real*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.x * Z::WPC + warp;
-  if (item >= p.C * p.nb) return;
-  const int c = item / p.nb, k = item % p.nb;
+  if (item >= p.C * a.rg.count(p.nb)) return;
+  int c, k;
+  a.rg.item(item, p.nb, c, k);
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(32 * GradSizes<Real, DP>::WPC)
   st_row<Real, DP>(SGhT, row, gi, act);
   Real uh = 0;
   for (int t = s; t <= e; ++t) {
-    const long ct = (long)c * p.nT + t;
+    const long ct = a.rg.ct(c, t, p.nT);
     Real r[DP];
     __syncwarp();
     ld_vec<Real, DP>(a.G + ct * DP * DP + row * DP, r);
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(32 * GradSizes<Real, DP>::WPC)
     st_col<Real, DP>(SGhT, row, gn, act);
   }
   __syncwarp();
-  Real* out = a.sgu + (long)item * Z::SGS;
+  Real* out = a.sgu + ((long)c * p.nb + k) * Z::SGS;
   if (act) {
     Real r[DP];
     ld_row<Real, DP>(SGh, row, r);
@@ -119,8 +121,9 @@ __global__ void __launch_bounds__(32 * GradSizes<Real, DP>::WPC)
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.x * Z::WPC + warp;
-  if (item >= p.C * p.nb) return;
-  const int c = item / p.nb, k = item % p.nb;
+  if (item >= p.C * a.rg.count(p.nb)) return;
+  int c, k;
+  a.rg.item(item, p.nb, c, k);
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const bool act = lane < DP;
   const int row = act ? lane : 0;
@@ -167,7 +170,8 @@ __global__ void __launch_bounds__(32 * GradSizes<Real, DP>::WPC)
   Real ph[DP];
   ld_vec<Real, DP>(sphi, ph);
   for (int t = e; t >= s; --t) {
-    const long ct = (long)c * p.nT + t;
+    const long ct = a.rg.ct(c, t, p.nT);        // G, U, Sigma
+    const long cy = (long)c * p.nT + t;          // ytilde
     __syncwarp();
     if (t == p.nT - 1) {
       Real r[DP];
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(32 * GradSizes<Real, DP>::WPC)
     }
     __syncwarp();
     if (lane < p.d) {
-      const Real r = a.yt[ct * p.d + lane] - vm[lane];
+      const Real r = a.yt[cy * p.d + lane] - vm[lane];
       O += (double)r * (double)r + (double)SP[lane * LD + lane];
     }
   }
@@ -230,14 +234,15 @@ __global__ void __launch_bounds__(32 * GradSizes<Real, DP>::WPC)
       s0[DP * DP + lane] = a0;
     }
   }
-  Real* gp = a.gpart + (long)item * Z::SGS;
+  const long ck = (long)c * p.nb + k;
+  Real* gp = a.gpart + ck * Z::SGS;
   if (act) {
     st_vec<Real, DP>(gp + row * DP, Mr);
     st_vec<Real, DP>(gp + DP * DP + row * DP, Dr);
     gp[2 * DP * DP + lane] = esum;
   }
   O = warp_sum<double>(O);
-  if (lane == 0) a.opart[item] = O;
+  if (lane == 0) a.opart[ck] = O;
 }
 
 // FP64 constants of theta, unpadded: mu[d], phi[d], L[d*d], Q[d*d], Q^{-1}[d*d], P0^{-1}[d*d]

@@ -73,6 +73,13 @@ struct aux_model {
   double *fgam = nullptr, *fmh = nullptr;                // [C][T]
   // gradient (aux_loglik_grad): theta constants and lazily allocated smoother buffers
   int grad_ok = 0;           // the model has the SV parameterisation
+  // gradient memory (aux_set_grad_memory): 0 stores G_t, Sigma_t, U_t for all
+  // steps; otherwise their store is capped and the filter is recomputed per
+  // chunk of grad_kc scan blocks (gscr: the chunk's scratch)
+  size_t grad_mem = 0;
+  int grad_kc = 0;
+  void *gscr = nullptr;
+  size_t gscr_bytes = 0;
   double *gconst = nullptr;  // mu, phi, L, Q, Q^{-1}, P0^{-1} (FP64, unpadded)
   void *Sig = nullptr, *sgu = nullptr, *gpart = nullptr, *s0 = nullptr;
   double *opart = nullptr;

@@ -667,6 +667,23 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::SCAN_WPC, 1)
 // covariance P^p_{t+1} is factorised once for both uses (G_t needs its
 // factor, the update at t+1 needs that of P^p_{t+1} + R): a dual Cholesky.
 // ---------------------------------------------------------------------------
+// A range of scan blocks for the kernels that can run on part of the blocks
+// (the gradient's recompute-not-store path): blocks k_lo .. k_lo + k_cnt - 1
+// of every chain (k_cnt = 0: all blocks), with the per-step backward arrays
+// (G_t, Sigma_t, U_t) of (c, t) at index c * cs + t - t_lo (cs = 0: nT), so that a
+// chunk of blocks fills a scratch of C * cs steps instead of C * T.
+struct BlockRange {
+  int k_lo = 0, k_cnt = 0;
+  long t_lo = 0, cs = 0;
+  __device__ __forceinline__ int count(int nb) const { return k_cnt ? k_cnt : nb; }
+  __device__ __forceinline__ void item(int it, int nb, int& c, int& k) const {
+    const int n = count(nb);
+    c = it / n;
+    k = k_lo + it % n;
+  }
+  __device__ __forceinline__ long ct(int c, int t, int nT) const { return (long)c * (cs ? cs : nT) + (t - t_lo); }
+};
+
 template <typename Real> struct ApplyArgs {
   const Real* yt;
   const Real* prefix;   // inclusive block prefixes [C][nb][ES] (marginals), null if nb == 1
@@ -683,6 +700,7 @@ template <typename Real> struct ApplyArgs {
   const Real* eps;      // [C][T][d] or null
   uint64_t iter;
   Real* Sig;            // [C][T][DP*DP] backward covariances (APPLY_SMOOTH) or null
+  BlockRange rg;        // blocks to run; indexing of G, U, Sig
 };
 
 template <typename Real, int DP>
@@ -703,8 +721,9 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
   const bool act = lane < DP;
   const int row = act ? lane : 0;
   const int item = blockIdx.x * Z::APP_WPC + warp;
-  if (item >= p.C * p.nb) return;
-  const int c = item / p.nb, k = item % p.nb;
+  if (item >= p.C * a.rg.count(p.nb)) return;
+  int c, k;
+  a.rg.item(item, p.nb, c, k);
   const int s = k * p.L, e = min(p.nT, s + p.L) - 1;
   const Real* sphi = sb + VEC;
   Real* SP = sb + 2 * VEC + warp * Z::APP_WARP_ELEMS;
@@ -785,8 +804,8 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
     Real grow[DP];
     ld_row<Real, DP>(SX, row, grow);
     if (act) {
-      st_vec<Real, DP>(a.G + ((long)c * p.nT + t) * DP * DP + row * DP, grow);
-      a.U[((long)c * p.nT + t) * DP + lane] = ui;
+      st_vec<Real, DP>(a.G + a.rg.ct(c, t, p.nT) * DP * DP + row * DP, grow);
+      a.U[a.rg.ct(c, t, p.nT) * DP + lane] = ui;
       vU[lane] = ui;
     }
     __syncwarp();
@@ -821,7 +840,7 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
       mm_col<Real, DP, true, true>(SY, row, SY, sig);
     }
     if ((a.flags & APPLY_SMOOTH) && act)
-      st_vec<Real, DP>(a.Sig + ((long)c * p.nT + t) * DP * DP + row * DP, sig);
+      st_vec<Real, DP>(a.Sig + a.rg.ct(c, t, p.nT) * DP * DP + row * DP, sig);
     {
       Real rr[DP];
       ld_col<Real, DP>(SY, row, rr);
@@ -943,7 +962,7 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
       Real pf[DP];
       ld_row<Real, DP>(SP, row, pf);
       if ((a.flags & APPLY_SMOOTH) && act)
-        st_vec<Real, DP>(a.Sig + ((long)c * p.nT + e) * DP * DP + row * DP, pf);
+        st_vec<Real, DP>(a.Sig + a.rg.ct(c, e, p.nT) * DP * DP + row * DP, pf);
       backward_noise(e);
       const Real le = chol_rot<Real, DP>(pf, SL, nullptr, nullptr, vdA, veps, p.d, lane, &bad);
       Real g0[DP];

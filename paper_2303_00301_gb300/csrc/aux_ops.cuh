@@ -160,8 +160,8 @@ struct Ops {
 
 
   // parallel filter on yt: phase 1, Hillis-Steele rounds, phase 3
-  static void filter(aux_model* m, const KP<Real>& p, const Real* yt, ApplyArgs<Real> a,
-                     cudaStream_t st) {
+  // block aggregates and their scan: the inclusive block prefixes (marginals)
+  static const Real* filter_prefix(aux_model* m, const KP<Real>& p, const Real* yt, cudaStream_t st) {
     const int n = items(m);
     Real* b0 = (Real*)m->agg0;
     Real* b1 = (Real*)m->agg1;
@@ -173,10 +173,21 @@ struct Ops {
       k_filter_scan_level<Real, DP><<<(n + Z::SCAN_WPC - 1) / Z::SCAN_WPC, 32 * Z::SCAN_WPC, Z::SCAN_SMEM, st>>>(p, b0, b1, off); }
       Real* tmp = b0; b0 = b1; b1 = tmp;
     }
-    a.yt = yt;
-    a.prefix = (m->nb > 1) ? b0 : nullptr;
+    return (m->nb > 1) ? b0 : nullptr;
+  }
+
+  // in-block filtering from the block prefixes over the blocks of a.rg
+  static void filter_apply(aux_model* m, const KP<Real>& p, ApplyArgs<Real> a, cudaStream_t st) {
+    const int n = m->C * (a.rg.k_cnt ? a.rg.k_cnt : m->nb);
     ProfScope ps(m, PK_APPLY, st);
     k_filter_apply<Real, DP><<<(n + Z::APP_WPC - 1) / Z::APP_WPC, 32 * Z::APP_WPC, Z::APP_SMEM, st>>>(p, a);
+  }
+
+  static void filter(aux_model* m, const KP<Real>& p, const Real* yt, ApplyArgs<Real> a,
+                     cudaStream_t st) {
+    a.prefix = filter_prefix(m, p, yt, st);
+    a.yt = yt;
+    filter_apply(m, p, a, st);
   }
 
   // square-root form of the per-chain filter (aux_sqrt.cuh): the same three phases
@@ -642,18 +653,47 @@ struct Ops {
     p.delta_dev = nullptr;   // the gradient is taken at the description's delta (a theta component)
     ApplyArgs<Real> a = apply_args(m, APPLY_EPI | APPLY_LOGZ | APPLY_SMOOTH, 0);
     a.Sig = (Real*)m->Sig;
-    filter(m, p, (const Real*)yt, a, st);
-    if (logZ) { ProfScope ps(m, PK_SUM, st); k_sum_parts<<<m->C, 128, 0, st>>>(m->lz_part, m->nb, logZ); }
+    a.yt = (const Real*)yt;
+    a.prefix = filter_prefix(m, p, (const Real*)yt, st);
     SmoothArgs<Real> sa{};
-    sa.G = (const Real*)m->G; sa.U = (const Real*)m->U; sa.Sig = (const Real*)m->Sig;
     sa.yt = (const Real*)yt; sa.sgu = (Real*)m->sgu; sa.gpart = (Real*)m->gpart;
     sa.opart = m->opart; sa.s0 = (Real*)m->s0;
-    const int n = items(m);
-    {
-      ProfScope ps(m, PK_SMOOTH, st, 2);
-      k_smooth_reduce<Real, DP><<<(n + GZ::WPC - 1) / GZ::WPC, 32 * GZ::WPC, GZ::RED_SMEM, st>>>(p, sa);
-      k_smooth_apply<Real, DP><<<(n + GZ::WPC - 1) / GZ::WPC, 32 * GZ::WPC, GZ::APP_SMEM, st>>>(p, sa);
+    auto smooth = [&](bool reduce, const BlockRange& rg) {
+      const int n = m->C * (rg.k_cnt ? rg.k_cnt : m->nb);
+      sa.rg = rg;
+      ProfScope ps(m, PK_SMOOTH, st);
+      if (reduce)
+        k_smooth_reduce<Real, DP><<<(n + GZ::WPC - 1) / GZ::WPC, 32 * GZ::WPC, GZ::RED_SMEM, st>>>(p, sa);
+      else
+        k_smooth_apply<Real, DP><<<(n + GZ::WPC - 1) / GZ::WPC, 32 * GZ::WPC, GZ::APP_SMEM, st>>>(p, sa);
+    };
+    if (!m->grad_kc) {   // G_t, Sigma_t, U_t of every step stored
+      filter_apply(m, p, a, st);
+      sa.G = (const Real*)m->G; sa.U = (const Real*)m->U; sa.Sig = (const Real*)m->Sig;
+      smooth(true, BlockRange{});
+      smooth(false, BlockRange{});
+    } else {
+      // recompute-not-store: chunks of grad_kc blocks; the in-block filter runs
+      // once for the smoother's block aggregates and again for its sweep, each
+      // time into the chunk's scratch (the aggregates of all blocks are small)
+      const long cs = (long)m->grad_kc * m->L, nst = (long)m->C * cs;
+      a.G = (Real*)m->gscr;
+      a.Sig = a.G + nst * DD;
+      a.U = a.Sig + nst * DD;
+      sa.G = a.G; sa.Sig = a.Sig; sa.U = a.U;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int k0 = 0; k0 < m->nb; k0 += m->grad_kc) {
+          BlockRange rg;
+          rg.k_lo = k0;
+          rg.k_cnt = std::min(m->grad_kc, m->nb - k0);
+          rg.t_lo = (long)k0 * m->L;
+          rg.cs = cs;
+          a.rg = rg;
+          filter_apply(m, p, a, st);
+          smooth(pass == 0, rg);
+        }
     }
+    if (logZ) { ProfScope ps(m, PK_SUM, st); k_sum_parts<<<m->C, 128, 0, st>>>(m->lz_part, m->nb, logZ); }
     GradOut go{g_mu, g_phi, g_L, g_delta};
     const size_t fsm = (size_t)(5 * m->d * m->d + 2 * m->d + 32) * sizeof(double);
     {

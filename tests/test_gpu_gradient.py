@@ -41,9 +41,11 @@ def _workload(theta, T, C):
                               x_init=np.zeros((C, T, d)))
 
 
-def _gpu_grad(theta, yt, L_blk, dt):
+def _gpu_grad(theta, yt, L_blk, dt, grad_mem=0):
     C, T, d = yt.shape
     s = AuxKalman(_workload(theta, T, C), dtype=dt, block_len=L_blk)
+    if grad_mem:
+        s.b.aux_set_grad_memory(s.handle, grad_mem)
     tdt = torch.float64 if dt == "f64" else torch.float32
     y = torch.tensor(yt, dtype=tdt, device="cuda")
     out = [torch.zeros(C, d, dtype=torch.float64, device="cuda"),
@@ -135,3 +137,36 @@ def test_grad_refuses_f64_at_padded_width_32():
     with pytest.raises(AuxError) as ei:
         _gpu_grad(theta, yt, 4, "f64")
     assert ei.value.code == 7   # AUX_E_UNSUPPORTED
+
+
+def _store_bytes(C, T, d, es):
+    p = next(w for w in (4, 8, 16, 32) if w >= d)
+    return C * T * (2 * p * p + p) * es
+
+
+@pytest.mark.parametrize("d,T,C,L,dt,blocks", [(5, 200, 3, 16, "f64", 1), (5, 200, 3, 16, "f64", 3),
+                                               (30, 512, 6, 23, "f32", 2), (32, 2048, 64, 46, "f32", 5)])
+def test_grad_recompute_not_store_equals_the_stored_path(d, T, C, L, dt, blocks):
+    """With a memory cap the in-block filter is recomputed per chunk of blocks
+    (twice) instead of storing G_t, Sigma_t, U_t for all steps: the same
+    arithmetic per block, so the same gradient bit for bit; chunks of one, three
+    and two blocks, and five at the differentiation workload (d = 32, T = 2048,
+    64 chains), where the full store is 1.1 GB and the cap 130 MB. The FP64 case
+    is also held to the oracle."""
+    theta = _theta(d, seed=11 * d)
+    rng = np.random.default_rng(d + T)
+    yt = rng.standard_normal((C, T, d)) * 0.5
+    es = 8 if dt == "f64" else 4
+    p = next(w for w in (4, 8, 16, 32) if w >= d)
+    cap = blocks * C * L * (2 * p * p + p) * es          # room for `blocks` blocks per chunk
+    assert cap < _store_bytes(C, T, d, es)
+    g0, z0 = _gpu_grad(theta, yt, L, dt)
+    g1, z1 = _gpu_grad(theta, yt, L, dt, grad_mem=cap)
+    for a, b in zip(g0, g1):
+        assert np.array_equal(a, b)
+    assert np.array_equal(z0, z1)
+    if dt == "f64":
+        for c in range(C):
+            r_mu, r_phi, r_L, r_delta, r_logZ = gradient.loglik_grad(theta, yt[c])
+            assert _rel(g1[0][c], r_mu) < 1e-8 and _rel(g1[1][c], r_phi) < 1e-8
+            assert _rel(g1[2][c], r_L) < 1e-8 and abs(g1[3][c] - r_delta) <= 1e-8 * abs(r_delta)
