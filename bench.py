@@ -801,82 +801,147 @@ def run_wide(args, flush, stream, peaks, pool=None):
     return res
 
 
-def run_batched(args, flush, stream, n_streams=32):
-    """A batch of independent SV instances, one chain each, in the manner of a batched
-    multi-instance workload: 256 instances, T_k ~ U{128..4096}, d_k cycling through 8, 16,
-    32 and 64 (the last on the wide kernels), per-instance phi, data and seeds, cached
-    covariance tables, delta_k = 0.0183 (30 * 1024 / (d_k T_k))^(1/2) (the d = 30,
-    T = 1024 value scaled by the pseudo-observation precision per state). One step = one
-    MH iteration of every instance; the instances' steps are captured in one CUDA graph on
-    32 streams (independent branches; for the 192 instances with d <= 32, 4 / 16 / 32 / 64
-    streams measured 9.8 / 4.1 / 3.9 / 3.9 ms per step) and replayed, L2 flushed before
-    each replay. The d <= 32 subset is timed the same way beside it."""
-    import numpy as np
+def _time_graph(g, flush, stream, n):
+    """Mean device time (ms) of n replays of a captured graph, L2 flushed before each."""
     import torch
-    from paper_2303_00301_gb300 import AuxKalman
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for k in range(n):
+        flush.zero_()
+        ev[k][0].record(stream)
+        g.replay()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / n
+
+
+def _capture(fn):
+    import torch
+    g = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    cap.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(g, stream=cap):
+        fn(cap)
+    torch.cuda.current_stream().wait_stream(cap)
+    torch.cuda.synchronize()
+    return g
+
+
+def batched_instances(n_inst=256, dims=(8, 16, 32, 64), seed=3):
+    """The batched workload: n_inst SV instances, one chain each, T_k ~ U{128..4096},
+    d_k cycling through dims, per-instance phi, data and seeds; delta_k = 0.0183
+    (30 * 1024 / (d_k T_k))^(1/2) (the d = 30, T = 1024 value scaled by the
+    pseudo-observation precision per state)."""
+    import numpy as np
     from paper_2303_00301_gb300 import workloads as W
-    rng = np.random.default_rng(3)
-    n_inst, dims = 256, (8, 16, 32, 64)
-    inst = []
+    rng = np.random.default_rng(seed)
+    out = []
     for k in range(n_inst):
-        d = dims[k % 4]
+        d = dims[k % len(dims)]
         T = int(rng.integers(128, 4097))
         delta = 0.0183 * math.sqrt(30 * 1024 / (d * T))
-        wl = W.stochastic_volatility(d=d, T=T, n_chains=1, sim_seed=100 + k, mcmc_seed=1000 + k, delta=delta)
-        h = AuxKalman(wl, dtype="f32", mode="cached", block_len=max(1, math.ceil(math.sqrt(T) / 2)))
-        x = torch.tensor(wl.x_init, dtype=torch.float32, device="cuda")
-        acc = torch.zeros(1, dtype=torch.int32, device="cuda")
-        inst.append((h, x, acc, T, d))
+        out.append(W.stochastic_volatility(d=d, T=T, n_chains=1, sim_seed=100 + k, mcmc_seed=1000 + k, delta=delta))
+    return out
+
+
+def run_batched(args, flush, stream, n_streams=32):
+    """The batched line: 256 SV instances (batched_instances) advanced by ONE persistent
+    launch per MCMC iteration (aux_batch_step), its launch shape and block lengths
+    picked by the library's autotuner (aux_batch_tune); each step a CUDA-graph replay
+    with L2 flushed before it. Cached mode (tables kept) and shared mode (every
+    instance's covariance pass rerun every step, side by side on the batch's streams)
+    are both timed. For comparison the same instances stepped one handle at a time
+    (11 launches each, one graph with 32 stream branches), the batch's predecessor."""
+    import torch
+    from paper_2303_00301_gb300 import AuxBatch, AuxKalman
+    wls = batched_instances()
+    n = max(args.steps // 2, 10)
+    models = [AuxKalman(wl, dtype="f32", mode="cached") for wl in wls]
+    xs = [torch.tensor(wl.x_init, dtype=torch.float32, device="cuda") for wl in wls]
+    steps_total = sum(wl.T for wl in wls)
+    out = {"workload": f"{len(wls)} SV instances, one chain each, T ~ U{{128..4096}}, d in [8, 16, 32, 64]",
+           "unit": UNIT, "instances": len(wls), "timesteps_per_step": steps_total,
+           "launch": "one persistent kernel per MCMC iteration (aux_batch_step), CUDA graph replay",
+           "l2": "flushed before every step"}
+
+    def batch_line(sub, key):
+        bx = AuxBatch([models[i] for i in sub], [xs[i] for i in sub], iteration=0)
+        t0 = time.perf_counter()
+        tuned_ms = bx.tune(reps=3)
+        tune_s = time.perf_counter() - t0
+        cfg = bx.config()
+        res = {}
+        for mode in ("cached", "shared"):
+            bx.set_mode(mode)
+            acc = torch.zeros(len(sub), dtype=torch.int32, device="cuda")
+            bx.step(2)
+            torch.cuda.synchronize()
+            g = _capture(lambda st: bx.step(1, accept_count=acc, stream=st))
+            g.replay()
+            torch.cuda.synchronize()
+            acc.zero_()
+            nn = n if mode == "cached" else max(n // 4, 5)
+            ms = _time_graph(g, flush, stream, nn)
+            ts = sum(wls[i].T for i in sub)
+            r = {"ms_per_step": ms, "value": ts / (ms / 1e3), "accept_rate": acc.sum().item() / (nn * len(sub)),
+                 "steps": nn}
+            if mode == "cached":
+                r["launches_per_step"] = 2
+            else:
+                # the covariance passes' launches, counted by the handles' profiler on one eager step
+                for i in sub:
+                    models[i].b.aux_set_profiling(models[i].handle, True)
+                bx.step(1)
+                torch.cuda.synchronize()
+                nl = 0
+                for i in sub:
+                    prof = models[i].b.aux_read_profile(models[i].handle)
+                    nl += sum(v[1] for k, v in prof.items() if k.startswith("cov_"))
+                    models[i].b.aux_set_profiling(models[i].handle, False)
+                r["launches_per_step"] = nl + 4   # + table copy, block tables, persistent step, counter
+            del g
+            res[mode] = r
+        rc, ab = bx.status()
+        bx.close()
+        line = dict(res["cached"])
+        line.update({"mode": "cached", "status": int(rc), "aborted": int(ab), "shared_mode": res["shared"],
+                     "tuner": {"best_ms_per_step": tuned_ms, "seconds": tune_s,
+                               "warps_per_cta": cfg["warps_per_cta"], "ctas_per_sm": cfg["ctas_per_sm"],
+                               "item_order": ["longest first", "shortest first"][cfg["order"]],
+                               "block_len_factor_by_width": dict(zip(["p<=8", "p=16", "p=32", "p=64"],
+                                                                     cfg["block_factor"]))}})
+        return line
+
+    out.update(batch_line(list(range(len(wls))), "all"))
+    out["d_le_32_subset"] = batch_line([i for i, wl in enumerate(wls) if wl.d <= 32], "narrow")
+    out["d_le_32_subset"]["instances"] = sum(1 for wl in wls if wl.d <= 32)
+
+    # the same instances one handle at a time (per-instance launches, 32 stream branches)
     for it in range(3):
-        for h, x, acc, T, d in inst:
+        for h, x in zip(models, xs):
             h.step(x, 1, iter0=it)
     torch.cuda.synchronize()
-    for h, x, acc, T, d in inst:
+    for h in models:
         h.device_iteration(True, 3)
     streams = [torch.cuda.Stream() for _ in range(n_streams)]
 
-    def time_subset(sub):
-        g = torch.cuda.CUDAGraph()
-        cap = torch.cuda.Stream()
-        cap.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.graph(g, stream=cap):
-            for st in streams:
-                st.wait_stream(cap)
-            for i, (h, x, acc, T, d) in enumerate(sub):
-                with torch.cuda.stream(streams[i % n_streams]):
-                    h.step(x, 1, 0, accept_count=acc)
-            for st in streams:
-                cap.wait_stream(st)
-        torch.cuda.current_stream().wait_stream(cap)
-        g.replay()
-        torch.cuda.synchronize()
-        for h, x, acc, T, d in sub:
-            acc.zero_()
-        n = max(args.steps // 10, 20)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
-        for k in range(n):
-            flush.zero_()
-            ev[k][0].record(stream)
-            g.replay()
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in ev) / n
-        steps_total = sum(T for _, _, _, T, _ in sub)
-        rate = sum(acc.item() for _, _, acc, _, _ in sub) / (n * len(sub))
-        del g
-        return {"instances": len(sub), "timesteps_per_step": steps_total, "ms_per_step": ms,
-                "value": steps_total / (ms / 1e3), "accept_rate": rate, "steps": n}
+    def per_instance(cap):
+        for st in streams:
+            st.wait_stream(cap)
+        for i, (h, x) in enumerate(zip(models, xs)):
+            with torch.cuda.stream(streams[i % n_streams]):
+                h.step(x, 1, 0)
+        for st in streams:
+            cap.wait_stream(st)
 
-    full = time_subset(inst)
-    narrow = time_subset([q for q in inst if q[4] <= 32])
-    rc = max(h.status()[0] for h, _, _, _, _ in inst)
-    for h, _, _, _, _ in inst:
+    g = _capture(per_instance)
+    g.replay()
+    torch.cuda.synchronize()
+    ms = _time_graph(g, flush, stream, n)
+    del g
+    out["per_instance_launches"] = {"ms_per_step": ms, "value": steps_total / (ms / 1e3), "mode": "cached",
+                                    "launch": f"11 launches per instance, one CUDA graph, {n_streams} stream branches"}
+    for h in models:
         h.close()
-    out = {"workload": f"{n_inst} SV instances, one chain each, T ~ U{{128..4096}}, d in {list(dims)}",
-           "unit": UNIT, "mode": "cached", "launch": f"one CUDA graph, {n_streams} stream branches",
-           "status": int(rc)}
-    out.update(full)
-    out["d_le_32_subset"] = narrow
     return out
 
 

@@ -469,6 +469,84 @@ int aux_read_profile(aux_model *m, double *ms_per_kind, int32_t *launches_per_ki
 #define AUX_NOALLOC_SCRATCH_BYTES (32u << 20)
 int aux_loglik_noalloc(const aux_model_desc *desc, const void *ytilde, double *logZ, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched instances: many independent models (uneven T and d_x, one or more
+ * chains each) advanced by ONE persistent launch per MCMC iteration.
+ * Section 2.4 (parallel-in-time sampling of long series) applied across
+ * instances: every chain of every model runs the MH step of Algorithm 2 with
+ * the table-mode means path (filtering means, (G, U) backward sampling of
+ * Appendix A.2.2 / Proposition A.1, MH test), as a list of warp items that a
+ * persistent grid drains; items wait for their inputs through per-chain
+ * completion counters with bounded waits (no kernel boundary between the
+ * passes, no per-instance launches).
+ *
+ * A batch refers to caller-owned model handles and state buffers; they must
+ * outlive it. Each handle must be FP32, in AUX_MODE_SHARED_COV or
+ * AUX_MODE_CACHED_COV, first-order proposal, scan sampler, homogeneous
+ * dynamics with a diagonal F, no delta adaptation, padded width 4 .. 64
+ * (d_x <= 64), SV or linear-Gaussian emission; each handle at most once.
+ * Otherwise AUX_E_UNSUPPORTED / AUX_E_INVALID_ARG. Chain c of model i draws the
+ * same Philox streams as aux_kalman_step on that handle at the same
+ * iteration. Errors: AUX_E_OOM, AUX_E_CUDA; a device wait that runs out
+ * (2 s) aborts the rest of that launch and is reported by
+ * aux_batch_get_status as AUX_E_TIMEOUT. */
+typedef struct aux_batch aux_batch;
+
+/* Create a batch over models[0 .. n_models) with state buffers x[i] (device,
+ * [C_i][T_i][d_i] FP32, updated in place by every step). Computes each
+ * model's covariance tables if they are not valid, copies them into the
+ * batch's layout and forms the block tables (device memory owned by the
+ * batch: 4 T + 2 ceil(T / L) matrices of p^2 words per model, p the padded
+ * width). iteration: the MCMC iteration of the first step (kept on the
+ * device, incremented by every step). Synchronises stream. */
+int aux_batch_create(aux_model *const *models, void *const *x, int32_t n_models, uint64_t iteration,
+                     void *stream, aux_batch **out);
+
+/* AUX_MODE_CACHED_COV (default): the tables are kept; AUX_MODE_SHARED_COV:
+ * every step first reruns every model's covariance pass (side by side on 16
+ * internal streams, joined back into stream) and re-copies the tables. */
+int aux_batch_set_mode(aux_batch *b, int32_t mode);
+
+/* n_iters MCMC iterations of every chain of every model, stream-ordered and
+ * asynchronous, capturable in a CUDA graph (the iteration is read from device
+ * memory). accept_count: device [total chains] uint32 incremented on
+ * acceptance, or NULL; log_alpha: device [total chains] double, or NULL;
+ * chains are numbered model by model. Per-chain status words go to each
+ * model's handle (aux_get_status). */
+int aux_batch_step(aux_batch *b, int32_t n_iters, uint32_t *accept_count, double *log_alpha, void *stream);
+
+/* Launch shape: warps per CTA (4, 8 or 16), CTAs per SM (0: as many as fit),
+ * item order within a pass (0: longest series first, 1: shortest first) and
+ * the block length factor of each width class (padded width <= 8, 16, 32,
+ * 64): L = round(f sqrt(T)), f snapped to {0.5, 1, 2}; NULL keeps them.
+ * Rebuilds the work list and block tables (synchronises stream). */
+int aux_batch_set_config(aux_batch *b, int32_t warps_per_cta, int32_t ctas_per_sm, int32_t order,
+                         const double *block_factor, void *stream);
+/* The current shape; block_factor: [4] or NULL; block_len: [n_models] or NULL. */
+int aux_batch_get_config(aux_batch *b, int32_t *warps_per_cta, int32_t *ctas_per_sm, int32_t *order,
+                         double *block_factor, int32_t *block_len);
+
+/* The autotuner: times `reps` steps (after one warm-up step) of each candidate
+ * launch shape by coordinate descent (warps per CTA, CTAs per SM, item order,
+ * then the block length factor of each width class present) and keeps the
+ * fastest; best_ms (host, or NULL) receives its time per step. The states
+ * x[i] and the iteration counter are restored afterwards (it allocates one
+ * temporary copy of the states); accept counts are untouched. Synchronous;
+ * AUX_E_UNSUPPORTED under stream capture. */
+int aux_batch_tune(aux_batch *b, int32_t reps, void *stream, double *best_ms);
+
+/* The device iteration counter (set: synchronises stream). */
+int aux_batch_set_iteration(aux_batch *b, uint64_t iteration, void *stream);
+int aux_batch_get_iteration(aux_batch *b, uint64_t *iteration);
+
+/* Synchronous check: AUX_E_TIMEOUT if a device wait ran out (aborted, when
+ * not NULL, receives 1), else AUX_E_NOT_PD / AUX_E_NONFINITE if some chain's
+ * status word is set, else AUX_OK. */
+int aux_batch_get_status(aux_batch *b, int32_t *aborted);
+
+/* Release the batch (synchronises the device); the models are untouched. */
+void aux_batch_free(aux_batch *b);
+
 /* Release the handle and its device memory (synchronises). NULL is a no-op. */
 void aux_free_model(aux_model *m);
 

@@ -151,3 +151,59 @@ class AuxKalman:
             self.close()
         except Exception:
             pass
+
+
+class AuxBatch:
+    """Many ``AuxKalman`` models (uneven T and d) advanced by one persistent launch per
+    MCMC iteration (``aux_batch_*``). The models (FP32, "shared" or "cached" mode) and
+    their state tensors ``xs`` (device, [C][T][d] FP32) must outlive the batch.
+    ``step`` runs every chain of every model; ``tune`` runs the library's autotuner
+    over launch shapes and block lengths (states restored afterwards)."""
+
+    def __init__(self, models, xs, iteration=0, mode="cached", stream=None):
+        b = _load_binding()
+        self.b = b
+        self.models = list(models)
+        self.xs = list(xs)
+        self.n_chains = sum(m.C for m in self.models)
+        self.batch = b.aux_batch_create([m.handle for m in self.models], self.xs, iteration, stream)
+        self.set_mode(mode)
+
+    def set_mode(self, mode):
+        if mode not in ("shared", "cached"):
+            raise ValueError("mode must be 'shared' or 'cached'")
+        self.mode = mode
+        self.b.aux_batch_set_mode(self.batch, self.b.AUX_MODE_SHARED_COV if mode == "shared"
+                                  else self.b.AUX_MODE_CACHED_COV)
+
+    def step(self, n_iters=1, accept_count=None, log_alpha=None, stream=None):
+        self.b.aux_batch_step(self.batch, n_iters, accept_count, log_alpha, stream)
+
+    def tune(self, reps=3, stream=None):
+        return self.b.aux_batch_tune(self.batch, reps, stream)
+
+    def config(self):
+        return self.b.aux_batch_get_config(self.batch, len(self.models))
+
+    def set_config(self, warps_per_cta=8, ctas_per_sm=0, order=0, block_factor=None, stream=None):
+        self.b.aux_batch_set_config(self.batch, warps_per_cta, ctas_per_sm, order, block_factor, stream)
+
+    def iteration(self):
+        return self.b.aux_batch_get_iteration(self.batch)
+
+    def set_iteration(self, it, stream=None):
+        self.b.aux_batch_set_iteration(self.batch, it, stream)
+
+    def status(self):
+        return self.b.aux_batch_get_status(self.batch)
+
+    def close(self):
+        if getattr(self, "batch", None) is not None:
+            self.b.aux_batch_free(self.batch)
+            self.batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -117,6 +117,28 @@ def _load():
     lib.aux_get_sv_theta.restype = ctypes.c_int
     lib.aux_loglik_noalloc.argtypes = [ctypes.POINTER(aux_model_desc), vp, vp, vp]
     lib.aux_loglik_noalloc.restype = ctypes.c_int
+    lib.aux_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_uint64,
+                                     vp, ctypes.POINTER(vp)]
+    lib.aux_batch_create.restype = ctypes.c_int
+    lib.aux_batch_set_mode.argtypes = [vp, ctypes.c_int32]
+    lib.aux_batch_set_mode.restype = ctypes.c_int
+    lib.aux_batch_step.argtypes = [vp, ctypes.c_int32, vp, vp, vp]
+    lib.aux_batch_step.restype = ctypes.c_int
+    lib.aux_batch_set_config.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, dp, vp]
+    lib.aux_batch_set_config.restype = ctypes.c_int
+    ip = ctypes.POINTER(ctypes.c_int32)
+    lib.aux_batch_get_config.argtypes = [vp, ip, ip, ip, dp, ip]
+    lib.aux_batch_get_config.restype = ctypes.c_int
+    lib.aux_batch_tune.argtypes = [vp, ctypes.c_int32, vp, dp]
+    lib.aux_batch_tune.restype = ctypes.c_int
+    lib.aux_batch_set_iteration.argtypes = [vp, ctypes.c_uint64, vp]
+    lib.aux_batch_set_iteration.restype = ctypes.c_int
+    lib.aux_batch_get_iteration.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.aux_batch_get_iteration.restype = ctypes.c_int
+    lib.aux_batch_get_status.argtypes = [vp, ip]
+    lib.aux_batch_get_status.restype = ctypes.c_int
+    lib.aux_batch_free.argtypes = [vp]
+    lib.aux_batch_free.restype = None
     lib.aux_status_string.argtypes = [ctypes.c_int]
     lib.aux_status_string.restype = ctypes.c_char_p
     return lib
@@ -332,3 +354,69 @@ def aux_read_profile(handle):
 
 def aux_free_model(handle):
     LIB.aux_free_model(handle)
+
+
+def aux_batch_create(handles, xs, iteration=0, stream=None):
+    """A batch over model handles and their state tensors (device, FP32)."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    ps = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    out = ctypes.c_void_p()
+    rc = LIB.aux_batch_create(hs, ps, n, ctypes.c_uint64(int(iteration)), _stream(stream), ctypes.byref(out))
+    _check(rc, "aux_batch_create")
+    return out
+
+
+def aux_batch_set_mode(batch, mode):
+    _check(LIB.aux_batch_set_mode(batch, int(mode)), "aux_batch_set_mode")
+
+
+def aux_batch_step(batch, n_iters=1, accept_count=None, log_alpha=None, stream=None):
+    rc = LIB.aux_batch_step(batch, int(n_iters), _ptr(accept_count), _ptr(log_alpha), _stream(stream))
+    _check(rc, "aux_batch_step")
+
+
+def aux_batch_set_config(batch, warps_per_cta, ctas_per_sm, order, block_factor=None, stream=None):
+    bf = None if block_factor is None else _as_c(block_factor)
+    rc = LIB.aux_batch_set_config(batch, int(warps_per_cta), int(ctas_per_sm), int(order),
+                                  None if bf is None else _dptr(bf), _stream(stream))
+    _check(rc, "aux_batch_set_config")
+
+
+def aux_batch_get_config(batch, n_models):
+    w, c, o = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    bf = np.zeros(4)
+    bl = (ctypes.c_int32 * int(n_models))()
+    _check(LIB.aux_batch_get_config(batch, ctypes.byref(w), ctypes.byref(c), ctypes.byref(o), _dptr(bf), bl),
+           "aux_batch_get_config")
+    return dict(warps_per_cta=w.value, ctas_per_sm=c.value, order=o.value, block_factor=bf.tolist(),
+                block_len=list(bl))
+
+
+def aux_batch_tune(batch, reps=3, stream=None):
+    """Run the autotuner; returns the best time per step (ms)."""
+    best = ctypes.c_double(0.0)
+    _check(LIB.aux_batch_tune(batch, int(reps), _stream(stream), ctypes.byref(best)), "aux_batch_tune")
+    return best.value
+
+
+def aux_batch_set_iteration(batch, iteration, stream=None):
+    _check(LIB.aux_batch_set_iteration(batch, ctypes.c_uint64(int(iteration)), _stream(stream)),
+           "aux_batch_set_iteration")
+
+
+def aux_batch_get_iteration(batch):
+    out = ctypes.c_uint64(0)
+    _check(LIB.aux_batch_get_iteration(batch, ctypes.byref(out)), "aux_batch_get_iteration")
+    return out.value
+
+
+def aux_batch_get_status(batch):
+    """Returns (code, aborted)."""
+    ab = ctypes.c_int32(0)
+    rc = LIB.aux_batch_get_status(batch, ctypes.byref(ab))
+    return rc, ab.value
+
+
+def aux_batch_free(batch):
+    LIB.aux_batch_free(batch)

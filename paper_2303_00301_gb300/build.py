@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libauxkalman.so")
 UNITS = ["aux_f32_d32.cu", "aux_f64_d32.cu", "aux_wide.cu", "aux_f32.cu", "aux_f64.cu", "aux_capi.cu",
-         "aux_noalloc.cu", "aux_fact.cu", "aux_theta.cu"]
+         "aux_noalloc.cu", "aux_fact.cu", "aux_theta.cu", "aux_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -147,6 +147,8 @@ struct AuxOps {
                      double *logZ, cudaStream_t);
   int (*loglik_grad)(aux_model *, const void *yt, double *logZ, double *g_mu, double *g_phi,
                      double *g_L, double *g_delta, cudaStream_t);
+  // the covariance tables of a table mode: recomputed when `force` or not valid
+  int (*tables)(aux_model *, int force, cudaStream_t);
 };
 
 int aux_fact_prepare(aux_model *m);

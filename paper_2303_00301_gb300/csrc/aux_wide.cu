@@ -194,8 +194,15 @@ struct WOps {
     return AUX_E_UNSUPPORTED;
   }
 
+  static int tables(aux_model* m, int force, cudaStream_t st) {
+    if (!supported(m)) return AUX_E_UNSUPPORTED;
+    const KP<Real> p = make_kp<Real>(m);
+    if (force || !m->cov_valid) { cov_pass(m, p, st); m->cov_valid = 1; }
+    return cuda_ok(cudaGetLastError());
+  }
+
   static const AuxOps* table() {
-    static const AuxOps t = {&prepare, &kalman_step, &loglik, &sample_path, &loglik_grad};
+    static const AuxOps t = {&prepare, &kalman_step, &loglik, &sample_path, &loglik_grad, &tables};
     return &t;
   }
 };
