@@ -826,6 +826,14 @@ def _capture(fn):
     return g
 
 
+def batch_p(d):
+    """Padded width of the library's narrow (4, 8, 16, 32) and wide (64, 128) kernels."""
+    for p in (4, 8, 16, 32, 64, 128):
+        if d <= p:
+            return p
+    raise ValueError(d)
+
+
 def batched_instances(n_inst=256, dims=(8, 16, 32, 64), seed=3):
     """The batched workload: n_inst SV instances, one chain each, T_k ~ U{128..4096},
     d_k cycling through dims, per-instance phi, data and seeds; delta_k = 0.0183
@@ -863,8 +871,10 @@ def run_batched(args, flush, stream, n_streams=32):
            "launch": "one persistent kernel per MCMC iteration (aux_batch_step), CUDA graph replay",
            "l2": "flushed before every step"}
 
-    def batch_line(sub, key):
-        bx = AuxBatch([models[i] for i in sub], [xs[i] for i in sub], iteration=0)
+    def batch_line(sub, it0):
+        # it0: a fresh range of MCMC iterations (reusing a range on chains that have
+        # already drawn its Philox numbers correlates the draws and depresses acceptance)
+        bx = AuxBatch([models[i] for i in sub], [xs[i] for i in sub], iteration=it0)
         t0 = time.perf_counter()
         tuned_ms = bx.tune(reps=3)
         tune_s = time.perf_counter() - t0
@@ -902,6 +912,18 @@ def run_batched(args, flush, stream, n_streams=32):
             res[mode] = r
         rc, ab = bx.status()
         bx.close()
+        # HBM roofline of the persistent step (cached): per chain-timestep it streams eight
+        # p x p tables (K' in the forward reduce, apply, reverse reduce and reverse apply;
+        # G twice; chol(Sigma); the block prefix GP) and about 17 d + 2 p vector words
+        tb = sum(8 * wls[i].T * batch_p(wls[i].d) ** 2 * 4 + wls[i].T * (17 * wls[i].d + 2 * batch_p(wls[i].d)) * 4
+                 for i in sub)
+        pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        hbm = json.load(open(pk)).get("hbm_gbs") if os.path.exists(pk) else None
+        ach = tb / (res["cached"]["ms_per_step"] * 1e-3) / 1e9
+        res["cached"]["roofline"] = {"kernel": "k_batch_step", "bound": "hbm", "achieved": ach, "peak": hbm,
+                                     "unit": "GB/s", "frac": (ach / hbm) if hbm else None, "traffic": None,
+                                     "bytes_per_step": tb, "peak_basis": "measured HBM copy bandwidth",
+                                     "timing": "graph replay of the step (persistent kernel + counter)"}
         line = dict(res["cached"])
         line.update({"mode": "cached", "status": int(rc), "aborted": int(ab), "shared_mode": res["shared"],
                      "tuner": {"best_ms_per_step": tuned_ms, "seconds": tune_s,
@@ -911,17 +933,17 @@ def run_batched(args, flush, stream, n_streams=32):
                                                                      cfg["block_factor"]))}})
         return line
 
-    out.update(batch_line(list(range(len(wls))), "all"))
-    out["d_le_32_subset"] = batch_line([i for i, wl in enumerate(wls) if wl.d <= 32], "narrow")
+    out.update(batch_line(list(range(len(wls))), 0))
+    out["d_le_32_subset"] = batch_line([i for i, wl in enumerate(wls) if wl.d <= 32], 1 << 20)
     out["d_le_32_subset"]["instances"] = sum(1 for wl in wls if wl.d <= 32)
 
     # the same instances one handle at a time (per-instance launches, 32 stream branches)
     for it in range(3):
         for h, x in zip(models, xs):
-            h.step(x, 1, iter0=it)
+            h.step(x, 1, iter0=(2 << 20) + it)
     torch.cuda.synchronize()
     for h in models:
-        h.device_iteration(True, 3)
+        h.device_iteration(True, (2 << 20) + 3)
     streams = [torch.cuda.Stream() for _ in range(n_streams)]
 
     def per_instance(cap):
