@@ -348,20 +348,28 @@ __global__ void __launch_bounds__(32 * CW_SCAN) k_cov_xprod(KP<Real> p, Real* __
 }
 
 template <typename Real, int DP> struct Cross2Sizes {
-  static constexpr size_t SMEM = (size_t)(3 * XG_MAX + 1) * Lay<Real, DP>::VEC * sizeof(Real);
+  // the group-start maps PP_(h XGS), h = 1 .. XG_MAX - 1, staged at the start; then the vector slots
+  static constexpr size_t SMEM = (size_t)(XG_MAX - 1) * Lay<Real, DP>::MAT * sizeof(Real) +
+                                 (size_t)(3 * XG_MAX + 1) * Lay<Real, DP>::VEC * sizeof(Real);
   static constexpr size_t XPROD_SMEM = (size_t)2 * Lay<Real, DP>::MAT * sizeof(Real);
 };
 
+// Every matrix this kernel reads is known before the chain's vectors are: the
+// serial phase 2 reads its G - 1 group-start maps from shared memory, copied
+// (cp.async) by the whole CTA while phase 1 runs; phase 1 keeps the next two
+// maps' rows in flight and loads its XGS right-hand sides up front; phase 3
+// loads the next map's row before the current product.
 template <typename Real, int DP>
 __global__ void __launch_bounds__(32 * XG_MAX)
     k_mean_cross2(KP<Real> p, const Real* __restrict__ btab, const Real* __restrict__ in,
                   Real* __restrict__ out, int backward) {
   pdl_wait();
   pdl_trigger();
-  constexpr int VEC = Lay<Real, DP>::VEC;
+  constexpr int VEC = Lay<Real, DP>::VEC, MAT = Lay<Real, DP>::MAT, LD = Lay<Real, DP>::LD;
   constexpr long DD = (long)DP * DP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* sv = reinterpret_cast<Real*>(smem_raw);   // [XG_MAX] per-warp broadcast slots
+  Real* sPP = reinterpret_cast<Real*>(smem_raw);   // [XG_MAX - 1] staged group-start maps
+  Real* sv = sPP + (XG_MAX - 1) * MAT;             // [XG_MAX] per-warp broadcast slots
   Real* sY = sv + XG_MAX * VEC;                    // [XG_MAX + 1] group starts Y_g
   Real* sV = sY + (XG_MAX + 1) * VEC;              // [XG_MAX] group-end local values
   const int c = blockIdx.x;
@@ -373,45 +381,51 @@ __global__ void __launch_bounds__(32 * XG_MAX)
   const long cb = (long)c * nb;
   const Real* mats = btab + (long)(backward ? BGH : BAH) * nb * DD;
   const Real* pp = btab + (long)(backward ? XPG : XPA) * nb * DD;
+  if (G > 1) stage_mats<Real, DP>(sPP, pp + (long)XGS * DD, (long)XGS * DD, G - 1);
   const Real y0 = backward ? (Real)0 : in[cb * DP + row];
   if (g == 0 && act) {
     if (backward) out[(cb + nb - 1) * DP + lane] = (Real)0;
     else if (nb > 1) out[(cb + 1) * DP + lane] = y0;
   }
   auto oidx = [&](int j) { return backward ? nb - 1 - j : j + 1; };
+  auto mrow = [&](int j) { return mats + (long)xmap_index<Real, DP>(j, nb, backward) * DD + row * DP; };
   Real* vq = sv + g * VEC;
   // phase 1: local values from zero at the group start
   Real v[XGS];
   const int j0 = g * XGS + 1;
   if (g < G) {
+    Real cjv[XGS];
+#pragma unroll
+    for (int s = 0; s < XGS; ++s)
+      cjv[s] = (j0 + s <= n) ? in[(cb + xmap_index<Real, DP>(j0 + s, nb, backward)) * DP + row] : (Real)0;
     Real cur = (Real)0;
-    Real mr[DP], mn[DP];
-    if (j0 <= n) ld_vec<Real, DP>(mats + (long)xmap_index<Real, DP>(j0, nb, backward) * DD + row * DP, mn);
+    Real mr[DP], m1[DP], m2[DP];
+    if (j0 <= n) ld_vec<Real, DP>(mrow(j0), m1);
+    if (j0 + 1 <= n) ld_vec<Real, DP>(mrow(j0 + 1), m2);
 #pragma unroll
     for (int s = 0; s < XGS; ++s) {
       const int j = j0 + s;
       v[s] = cur;
       if (j <= n) {
 #pragma unroll
-        for (int q = 0; q < DP; ++q) mr[q] = mn[q];
-        if (j + 1 <= n && s + 1 < XGS)
-          ld_vec<Real, DP>(mats + (long)xmap_index<Real, DP>(j + 1, nb, backward) * DD + row * DP, mn);
-        const Real cj = in[(cb + xmap_index<Real, DP>(j, nb, backward)) * DP + row];
+        for (int q = 0; q < DP; ++q) { mr[q] = m1[q]; m1[q] = m2[q]; }
+        if (j + 2 <= n && s + 2 < XGS) ld_vec<Real, DP>(mrow(j + 2), m2);
         put_vec<Real, DP>(vq, cur, lane);
-        cur = dot_rv<Real, DP>(mr, vq) + cj;
+        cur = dot_rv<Real, DP>(mr, vq) + cjv[s];
         v[s] = cur;
       }
     }
     if (act) sV[g * VEC + lane] = cur;
   }
+  cp_async_wait<0>();
   __syncthreads();
-  // phase 2: the group starts, one warp
+  // phase 2: the group starts, one warp, maps from shared memory
   if (g == 0) {
     Real Y = y0;
     if (act) sY[lane] = Y;
     for (int h = 0; h + 1 < G; ++h) {
       Real pr[DP];
-      ld_vec<Real, DP>(pp + (long)((h + 1) * XGS) * DD + row * DP, pr);
+      ld_vec<Real, DP>(sPP + h * MAT + row * LD, pr);
       put_vec<Real, DP>(vq, Y, lane);
       Y = dot_rv<Real, DP>(pr, vq) + sV[h * VEC + row];
       if (act) sY[(h + 1) * VEC + lane] = Y;
@@ -420,12 +434,15 @@ __global__ void __launch_bounds__(32 * XG_MAX)
   __syncthreads();
   // phase 3: every map's value from its group start
   if (g < G) {
+    Real pr[DP], pn[DP];
+    if (j0 <= n) ld_vec<Real, DP>(pp + (long)j0 * DD + row * DP, pn);
 #pragma unroll
     for (int s = 0; s < XGS; ++s) {
       const int j = j0 + s;
       if (j <= n) {
-        Real pr[DP];
-        ld_vec<Real, DP>(pp + (long)j * DD + row * DP, pr);
+#pragma unroll
+        for (int q = 0; q < DP; ++q) pr[q] = pn[q];
+        if (j + 1 <= n && s + 1 < XGS) ld_vec<Real, DP>(pp + (long)(j + 1) * DD + row * DP, pn);
         const Real yj = dot_rv<Real, DP>(pr, sY + g * VEC) + v[s];
         if (act) out[(cb + oidx(j)) * DP + lane] = yj;
       }
