@@ -330,12 +330,16 @@ __device__ void w_sym(const Real* X, Real* out) {
 // Lower Cholesky factor of the symmetric (A + addiag I) into the shared slot S
 // (row-major, stride LDS, zero above the diagonal). Rows and columns >= d are
 // the identity (the padding). A pivot below d that is not positive and finite
-// sets *bad and is replaced by 1. Returns sum_{k<d} log L_kk (valid in every thread).
-// piv: DP doubles of shared scratch.
+// sets *bad and is replaced by 1. Returns sum_{k<d} log L_kk in thread 0 (the
+// only thread that uses it; warp 0 sums the FP64 logarithms, a few per lane).
+// piv: DP doubles of shared scratch. The FP64 work per call is DP square roots
+// and DP logarithms in all: on this GPU FP64 runs at a small fraction of the
+// FP32 rate, so every thread doing its own would dominate the routine.
 template <typename Real, int DP, typename SlotT = Real>
 __device__ double w_chol(const Real* A, Real addiag, int d, SlotT* S, double* piv, int* bad) {
   using Z = WSz<Real, DP>;
   constexpr int LDS = Z::LDS, P = WT / DP;
+  static_assert(WT % DP == 0, "every thread keeps one column in the scaling pass");
   __syncthreads();
   for (int q = threadIdx.x; q < DP * DP; q += WT) {
     const int i = q / DP, j = q % DP;
@@ -356,23 +360,43 @@ __device__ double w_chol(const Real* A, Real addiag, int d, SlotT* S, double* pi
     }
     if (i > k) {
       const SlotT lik = S[i * LDS + k] / pk;
-      for (int j = k + 1 + part; j <= i; j += P) S[i * LDS + j] = fma(-lik, S[j * LDS + k], S[i * LDS + j]);
+      SlotT* Si = S + i * LDS;
+      int j = k + 1 + part;
+      // four columns per round, every load before the stores: the rounds of a row
+      // are independent, so their shared-memory latencies overlap
+      for (; j + 3 * P <= i; j += 4 * P) {
+        const SlotT c0 = S[j * LDS + k], c1 = S[(j + P) * LDS + k], c2 = S[(j + 2 * P) * LDS + k],
+                    c3 = S[(j + 3 * P) * LDS + k];
+        const SlotT r0 = Si[j], r1 = Si[j + P], r2 = Si[j + 2 * P], r3 = Si[j + 3 * P];
+        Si[j] = fma(-lik, c0, r0);
+        Si[j + P] = fma(-lik, c1, r1);
+        Si[j + 2 * P] = fma(-lik, c2, r2);
+        Si[j + 3 * P] = fma(-lik, c3, r3);
+      }
+      for (; j <= i; j += P) Si[j] = fma(-lik, S[j * LDS + k], Si[j]);
     }
   }
   __syncthreads();
-  // scale: L_ik = S_ik / sqrt(p_k) (i > k), L_kk = sqrt(p_k); zero above the diagonal
-  for (int q = threadIdx.x; q < DP * DP; q += WT) {
-    const int r = q / DP, c = q % DP;
-    if (c >= d) { S[r * LDS + c] = (r == c) ? (SlotT)1 : (SlotT)0; continue; }
-    const SlotT sp = (SlotT)sqrt(piv[c]);
-    SlotT v = (SlotT)0;
-    if (r == c) v = sp;
-    else if (r > c) v = S[r * LDS + c] / sp;
-    S[r * LDS + c] = v;
+  // scale: L_ik = S_ik / sqrt(p_k) (i > k), L_kk = sqrt(p_k); zero above the diagonal.
+  // Thread t only touches column t mod DP: one square root per thread.
+  {
+    const int c = threadIdx.x % DP;
+    const SlotT sp = c < d ? (SlotT)sqrt(piv[c]) : (SlotT)1;
+    const SlotT isp = (SlotT)1 / sp;
+    for (int r = threadIdx.x / DP; r < DP; r += P) {
+      if (c >= d) { S[r * LDS + c] = (r == c) ? (SlotT)1 : (SlotT)0; continue; }
+      SlotT v = (SlotT)0;
+      if (r == c) v = sp;
+      else if (r > c) v = (sizeof(SlotT) == 4) ? S[r * LDS + c] / sp : S[r * LDS + c] * isp;
+      S[r * LDS + c] = v;
+    }
   }
   __syncthreads();
   double ld = 0.0;
-  for (int k = 0; k < d; ++k) ld += 0.5 * log(piv[k]);
+  if (threadIdx.x < 32) {
+    for (int k = threadIdx.x; k < d; k += 32) ld += 0.5 * log(piv[k]);
+    ld = warp_sum<double>(ld);
+  }
   return ld;
 }
 

@@ -92,3 +92,16 @@ def test_geyer_ess_of_white_noise_and_of_an_ar1_series():
         y[t] = phi * y[t - 1] + rng.standard_normal()
     # integrated autocorrelation time of an AR(1): (1 + phi) / (1 - phi) = 19
     assert n / 19 * 0.7 < bench.geyer_ess(y) < n / 19 * 1.3
+
+
+def test_batched_workload_and_padded_widths():
+    """The batched workload: T in [128, 4096], widths cycling 8, 16, 32, 64, delta
+    scaled from the calibrated d = 30, T = 1024 value; padded widths of the kernels."""
+    wls = bench.batched_instances(n_inst=8)
+    assert [w.d for w in wls] == [8, 16, 32, 64] * 2
+    assert all(128 <= w.T <= 4096 for w in wls)
+    for w in wls:
+        assert abs(w.delta - 0.0183 * math.sqrt(30 * 1024 / (w.d * w.T))) < 1e-15
+    assert [bench.batch_p(d) for d in (1, 4, 5, 8, 9, 30, 33, 64, 65, 128)] == [4, 4, 8, 8, 16, 32, 64, 64, 128, 128]
+    with pytest.raises(ValueError):
+        bench.batch_p(129)
