@@ -88,6 +88,8 @@ def parse():
                     help="run only the batched multi-instance line and print it")
     ap.add_argument("--wide-only", action="store_true",
                     help="run only the d = 128 line (wide kernels) and print it")
+    ap.add_argument("--batched-instances", type=int, default=256,
+                    help="instances of the batched line (256: the full mix; fewer for profiling)")
     ap.add_argument("--wide-T", type=int, default=4096, help="T of the d = 128 line")
     ap.add_argument("--wide-L", type=int, default=0, help="block length of the d = 128 line (0: default)")
     ap.add_argument("--wide-adapt", type=int, default=150,
@@ -861,7 +863,7 @@ def run_batched(args, flush, stream, n_streams=32):
     (11 launches each, one graph with 32 stream branches), the batch's predecessor."""
     import torch
     from paper_2303_00301_gb300 import AuxBatch, AuxKalman
-    wls = batched_instances()
+    wls = batched_instances(n_inst=args.batched_instances)
     n = max(args.steps // 2, 10)
     models = [AuxKalman(wl, dtype="f32", mode="cached") for wl in wls]
     xs = [torch.tensor(wl.x_init, dtype=torch.float32, device="cuda") for wl in wls]
