@@ -83,6 +83,24 @@ def test_init_rejects_bad_descriptions_on_host(lib, over, code):
     assert e.value.code == code
 
 
+def test_batch_entry_points_reject_bad_arguments_on_host(lib):
+    """The batch calls check their arguments before any device call."""
+    L = lib.LIB
+    out = ctypes.c_void_p()
+    vp = ctypes.c_void_p
+    assert L.aux_batch_create(None, None, 1, 0, None, ctypes.byref(out)) == lib.AUX_E_INVALID_ARG
+    hs = (vp * 1)(None)
+    xs = (vp * 1)(None)
+    assert L.aux_batch_create(hs, xs, 1, 0, None, ctypes.byref(out)) == lib.AUX_E_INVALID_ARG
+    assert L.aux_batch_create(hs, xs, 0, 0, None, ctypes.byref(out)) == lib.AUX_E_INVALID_ARG
+    assert L.aux_batch_step(None, 1, None, None, None) == lib.AUX_E_INVALID_ARG
+    assert L.aux_batch_set_mode(None, lib.AUX_MODE_CACHED_COV) == lib.AUX_E_INVALID_ARG
+    assert L.aux_batch_tune(None, 1, None, None) == lib.AUX_E_INVALID_ARG
+    assert L.aux_batch_set_config(None, 8, 0, 0, None, None) == lib.AUX_E_INVALID_ARG
+    assert L.aux_batch_get_status(None, None) == lib.AUX_E_INVALID_ARG
+    L.aux_batch_free(None)   # a no-op
+
+
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     """The binding has no CPU fallback: a missing library is an import error."""
     import importlib
