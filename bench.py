@@ -88,6 +88,9 @@ def parse():
                     help="run only the batched multi-instance line and print it")
     ap.add_argument("--wide-only", action="store_true",
                     help="run only the d = 128 line (wide kernels) and print it")
+    ap.add_argument("--batched-quick", action="store_true",
+                    help="batched line: the full batch in cached mode only (no subset, shared mode or "
+                         "per-instance comparison; for profiling)")
     ap.add_argument("--batched-instances", type=int, default=256,
                     help="instances of the batched line (256: the full mix; fewer for profiling)")
     ap.add_argument("--wide-T", type=int, default=4096, help="T of the d = 128 line")
@@ -882,7 +885,7 @@ def run_batched(args, flush, stream, n_streams=32):
         tune_s = time.perf_counter() - t0
         cfg = bx.config()
         res = {}
-        for mode in ("cached", "shared"):
+        for mode in (("cached",) if args.batched_quick else ("cached", "shared")):
             bx.set_mode(mode)
             acc = torch.zeros(len(sub), dtype=torch.int32, device="cuda")
             bx.step(2)
@@ -922,12 +925,14 @@ def run_batched(args, flush, stream, n_streams=32):
         pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
         hbm = json.load(open(pk)).get("hbm_gbs") if os.path.exists(pk) else None
         ach = tb / (res["cached"]["ms_per_step"] * 1e-3) / 1e9
+        key = f"k_batch_step@batched{len(sub)}"
         res["cached"]["roofline"] = {"kernel": "k_batch_step", "bound": "hbm", "achieved": ach, "peak": hbm,
-                                     "unit": "GB/s", "frac": (ach / hbm) if hbm else None, "traffic": None,
+                                     "unit": "GB/s", "frac": (ach / hbm) if hbm else None,
+                                     "traffic": dram_traffic(key),
                                      "bytes_per_step": tb, "peak_basis": "measured HBM copy bandwidth",
                                      "timing": "graph replay of the step (persistent kernel + counter)"}
         line = dict(res["cached"])
-        line.update({"mode": "cached", "status": int(rc), "aborted": int(ab), "shared_mode": res["shared"],
+        line.update({"mode": "cached", "status": int(rc), "aborted": int(ab), "shared_mode": res.get("shared"),
                      "tuner": {"best_ms_per_step": tuned_ms, "seconds": tune_s,
                                "warps_per_cta": cfg["warps_per_cta"], "ctas_per_sm": cfg["ctas_per_sm"],
                                "item_order": ["longest first", "shortest first"][cfg["order"]],
@@ -936,6 +941,10 @@ def run_batched(args, flush, stream, n_streams=32):
         return line
 
     out.update(batch_line(list(range(len(wls))), 0))
+    if args.batched_quick:
+        for h in models:
+            h.close()
+        return out
     out["d_le_32_subset"] = batch_line([i for i, wl in enumerate(wls) if wl.d <= 32], 1 << 20)
     out["d_le_32_subset"]["instances"] = sum(1 for wl in wls if wl.d <= 32)
 
