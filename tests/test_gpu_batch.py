@@ -50,6 +50,11 @@ def _mixed_workloads():
         wls.append(workloads.stochastic_volatility(d=d, T=T, n_chains=C, sim_seed=200 + i,
                                                    mcmc_seed=300 + i, delta=delta))
     wls.append(workloads.linear_gaussian(d=2, T=64, n_chains=2, sim_seed=7, mcmc_seed=11))
+    # linear-Gaussian emissions whose R_y^{-1} products run at widths 32 and 64, and the
+    # two-step toy of Section 4.4 (first observation masked)
+    wls.append(workloads.linear_gaussian(d=20, T=40, n_chains=1, sim_seed=9, mcmc_seed=17, delta=0.05))
+    wls.append(workloads.linear_gaussian(d=40, T=20, n_chains=1, sim_seed=10, mcmc_seed=19, delta=0.05))
+    wls.append(workloads.two_step_toy(n_chains=2, mcmc_seed=13))
     return wls
 
 
