@@ -428,6 +428,65 @@ __device__ T chol_rot(T (&a)[DP], T* LS, T* LRow, T* LR, T* inv_diag, const T* e
   return acc;
 }
 
+// chol_rot without the rotation: lane i keeps row i in place (before step k,
+// a[j] for j >= k holds the updated entry (i, j); step k applies
+// a[j] <- a[j] - l_ik L[j][k]), fully unrolled, with the pivot's square root
+// and reciprocal taken speculatively and replaced by a select when the pivot
+// fails or k >= d. Same inputs, outputs and padding rules as chol_rot, and the
+// same values. Faster on the per-chain element kernels; the square-root and
+// bridging kernels keep chol_rot (their larger bodies lose more to the
+// unrolled code than they gain).
+template <typename T, int DP>
+__device__ T chol_ur(T (&a)[DP], T* LS, T* LRow, T* LR, T* inv_diag, const T* eps, int d,
+                      int lane, int* bad) {
+  constexpr int LD = Lay<T, DP>::LD;
+  const bool act = lane < DP;
+  T acc = 0;
+  __syncwarp();
+  if (LR && act) {
+    T z[DP];
+    zero<T, DP>(z);
+    st_vec<T, DP>(LR + lane * LD, z);
+  }
+  if (LRow && act) {
+    T z[DP];
+    zero<T, DP>(z);
+    st_vec<T, DP>(LRow + lane * LD, z);
+  }
+  __syncwarp();
+  // lane i keeps row i unshifted (entry j in a[j]); column k's factor entries
+  // reach the lanes through the LS row just stored, one broadcast read per
+  // update; the pivot's square root and reciprocal are taken speculatively and
+  // a failed pivot (or a padding column) is replaced by a select afterwards,
+  // off the pivot-to-pivot critical path
+#pragma unroll
+  for (int k = 0; k < DP; ++k) {
+    const T akk = __shfl_sync(FULL_MASK, a[k], k);
+    const T piv0 = sqrt(akk);
+    const T inv0 = (T)1 / piv0;
+    const bool ok = akk > (T)0 && akk < (T)INFINITY;
+    if (k < d && !ok) *bad = 1;
+    const bool good = k < d && ok;
+    const T piv = good ? piv0 : (T)1;
+    const T inv = good ? inv0 : (T)1;
+    const T l = (lane == k) ? piv : ((lane > k) ? a[k] * inv : (T)0);
+    if (act && lane >= k) {
+      LS[k * LD + (lane - k)] = l;
+      if (LRow) LRow[lane * LD + k] = l;
+      if (LR) LR[lane * LD + (DP - 1) - (lane - k)] = l;
+    }
+    if (lane == 0) inv_diag[k] = inv;
+    if (eps) acc = fma(l, eps[k], acc);
+    __syncwarp();
+    const T nl = -l;
+#pragma unroll
+    for (int j = k + 1; j < DP; ++j) a[j] = fma(nl, LS[k * LD + (j - k)], a[j]);
+  }
+  zero<T, DP>(a);   // the row is consumed
+  __syncwarp();
+  return acc;
+}
+
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 

@@ -230,7 +230,7 @@ __device__ void combine_matrix_1(const Real* SC, const Real* SAe, const Real* SJ
   {
     Real a[DP];
     ld_row<Real, DP>(SC, row, a);
-    chol_rot<Real, DP>(a, S2, SU, nullptr, vdiag, nullptr, d, lane, bad);
+    chol_ur<Real, DP>(a, S2, SU, nullptr, vdiag, nullptr, d, lane, bad);
   }
   {
     Real t1[DP];
@@ -243,7 +243,7 @@ __device__ void combine_matrix_1(const Real* SC, const Real* SAe, const Real* SJ
     mm_col<Real, DP>(SU, row, S3, n);
 #pragma unroll
     for (int j = 0; j < DP; ++j) n[j] += (j == lane) ? (Real)1 : (Real)0;
-    chol_rot<Real, DP>(n, S4, nullptr, nullptr, vdiag, nullptr, d, lane, bad);
+    chol_ur<Real, DP>(n, S4, nullptr, nullptr, vdiag, nullptr, d, lane, bad);
   }
   {
     Real r[DP];
@@ -549,7 +549,7 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::RED_WPC, 1)
       const Real rl = obs_var<Real>(p, c, t, lane);
 #pragma unroll
       for (int j = 0; j < DP; ++j) s_[j] = pprow[j] + (j == lane ? rl : (Real)0);
-      chol_rot<Real, DP>(s_, SL, nullptr, nullptr, vdiag, nullptr, p.d, lane, &bad);
+      chol_ur<Real, DP>(s_, SL, nullptr, nullptr, vdiag, nullptr, p.d, lane, &bad);
     }
     const Real rres = (lane < p.d) ? ytc[(long)t * p.d + lane] - mpi : (Real)0;
     if (act) vr[lane] = rres;
@@ -847,7 +847,7 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
       bsolve_rot<Real, DP>(SLR, vdA, rr, SX, lane);       // SX = G (rows); X is dead
     }
     backward_noise(t);
-    const Real le = chol_rot<Real, DP>(sig, SL, nullptr, nullptr, vdA, veps, p.d, lane, &bad);
+    const Real le = chol_ur<Real, DP>(sig, SL, nullptr, nullptr, vdA, veps, p.d, lane, &bad);
     const Real ui = vm[row] - dot_row_vec<Real, DP>(SX + row * LD, vmp) + le;
     store_backward(t, ui);
   };
@@ -913,7 +913,7 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
     const Real rl = obs_var<Real>(p, c, t, lane);
 #pragma unroll
     for (int j = 0; j < DP; ++j) s_[j] = pprow[j] + (j == lane ? rl : (Real)0);
-    chol_rot<Real, DP>(s_, SG, nullptr, nullptr, vdB, nullptr, p.d, lane, &bad);
+    chol_ur<Real, DP>(s_, SG, nullptr, nullptr, vdB, nullptr, p.d, lane, &bad);
   };
 
   // ---- block start
@@ -955,7 +955,7 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
       Real a_[DP];
 #pragma unroll
       for (int j = 0; j < DP; ++j) a_[j] = pprow[j];
-      chol_rot<Real, DP>(a_, SL, nullptr, SLR, vdA, nullptr, p.d, lane, &bad);
+      chol_ur<Real, DP>(a_, SL, nullptr, SLR, vdA, nullptr, p.d, lane, &bad);
       epilogue(e);
     } else {
       // last state: G_{T-1} = 0, U_{T-1} = m^f + chol(P^f) eps
@@ -964,7 +964,7 @@ __global__ void __launch_bounds__(32 * Sizes<Real, DP>::APP_WPC, 1)
       if ((a.flags & APPLY_SMOOTH) && act)
         st_vec<Real, DP>(a.Sig + a.rg.ct(c, e, p.nT) * DP * DP + row * DP, pf);
       backward_noise(e);
-      const Real le = chol_rot<Real, DP>(pf, SL, nullptr, nullptr, vdA, veps, p.d, lane, &bad);
+      const Real le = chol_ur<Real, DP>(pf, SL, nullptr, nullptr, vdA, veps, p.d, lane, &bad);
       Real g0[DP];
       zero<Real, DP>(g0);
       __syncwarp();
