@@ -7,7 +7,8 @@
 //   w_gemm    C = alpha op(A) op(B) + beta C0, k-chunks staged in shared memory,
 //             (DP/16)^2 outputs per thread;
 //   w_chol    right-looking Cholesky in shared memory (one barrier per column);
-//   w_trinv   the inverse of the triangular factor, right-looking by rows.
+//   w_trinv   the inverse of the triangular factor, blocked by 32 (diagonal
+//             blocks on separate warps, then each panel as one product pair).
 // Covariance pass (homogeneous dynamics, R = r I, Appendix A.2.1 elements):
 //   k_w_elem    the two distinct elements: t = 0, (0, C_0, 0), and every t >= 1,
 //               (A, C, J), with S = Q + R:  A = r S^{-1} F, C = Q - Q S^{-1} Q,
@@ -400,30 +401,101 @@ __device__ double w_chol(const Real* A, Real addiag, int d, SlotT* S, double* pi
   return ld;
 }
 
-// L^{-1} in place of the lower-triangular L in the shared slot S, by columns from
-// the last: with the trailing block already inverted,
-//   (L^{-1})_jj = 1 / L_jj,  (L^{-1})_ij = -(1 / L_jj) sum_{k=j+1..i} (L^{-1})_ik L_kj  (i > j),
-// one thread per row; col: DP elements of shared scratch (the old column j).
+// One block column of the blocked inverse (w_trinv): rows r0 .. DP - 1 of block
+// column jb (the panel P, still holding L) become -X P D, where X (rows and
+// columns >= r0) and D (the diagonal block of jb) are already inverted. Thread
+// (row, column group) keeps NC of the row's 32 outputs in registers; every
+// read of a stage precedes its stores (a CTA barrier between them). The sums
+// run over k up to the last row of the warp: X is zero above its diagonal.
+template <typename Real, int DP, int TPR>
+__device__ __forceinline__ void w_trinv_panel(Real* S, int jb) {
+  constexpr int LDS = WSz<float, DP>::LDS, NC = 32 / TPR;
+  const int r0 = 32 * (jb + 1), c0 = 32 * jb;
+  const int rr = threadIdx.x / TPR, cg = threadIdx.x % TPR;
+  const int r = r0 + rr;
+  const bool act = r < DP;
+  const int rlast = min(DP - 1, r0 + (int)((threadIdx.x | 31) / TPR));   // last row of this warp
+  Real q[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) q[c] = (Real)0;
+  if (act) {   // Q = X P
+    const Real* Sr = S + r * LDS;
+    for (int k = r0; k <= rlast; ++k) {
+      const Real x = Sr[k];
+      const Real* Lk = S + k * LDS + c0 + cg;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) q[c] = fma(x, Lk[c * TPR], q[c]);
+    }
+  }
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) S[r * LDS + c0 + cg + c * TPR] = q[c];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < NC; ++c) q[c] = (Real)0;
+  if (act) {   // -Q D
+    const Real* Qr = S + r * LDS + c0;
+    const Real* D = S + c0 * LDS + c0 + cg;
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {
+      const Real x = Qr[k];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) q[c] = fma(x, D[k * LDS + c * TPR], q[c]);
+    }
+  }
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) S[r * LDS + c0 + cg + c * TPR] = -q[c];
+  }
+}
+
+// L^{-1} in place of the lower-triangular L in the shared slot S (zero above
+// the diagonal), blocked by 32:
+// (1) the diagonal blocks inverted side by side, warp w on block w, lane = row,
+//     by columns from the last: with the block's trailing columns inverted,
+//     (L^{-1})_jj = 1 / L_jj, (L^{-1})_ij = -(1 / L_jj) sum_{k=j+1..i} (L^{-1})_ik L_kj (i > j),
+//     one warp barrier per column;
+// (2) the block columns from the second last to the first: from X L = I, the
+//     blocks below the diagonal are X_(i,jb) = -(sum_{k=jb+1..i} X_(i,k) L_(k,jb)) X_(jb,jb)
+//     (w_trinv_panel), a few CTA barriers per block column.
+// col: DP elements of shared scratch (the old column j, 32 per diagonal block).
 template <typename Real, int DP>
 __device__ void w_trinv(Real* S, Real* col) {
-  constexpr int LDS = WSz<float, DP>::LDS;
-  for (int j = DP - 1; j >= 0; --j) {
-    __syncthreads();
-    if (threadIdx.x < DP) col[threadIdx.x] = S[threadIdx.x * LDS + j];
-    __syncthreads();
-    const Real ajj = (Real)1 / col[j];
-    const int i = threadIdx.x;
-    if (i > j && i < DP) {
-      Real a0 = (Real)0, a1 = (Real)0;
-      int k = j + 1;
-      for (; k + 1 <= i; k += 2) {
-        a0 = fma(S[i * LDS + k], col[k], a0);
-        a1 = fma(S[i * LDS + k + 1], col[k + 1], a1);
+  constexpr int LDS = WSz<float, DP>::LDS, NB = DP / 32;
+  static_assert(DP % 32 == 0 && WT >= 32 * NB && WT % 32 == 0, "one warp per diagonal block");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (warp < NB) {
+    Real* B = S + (32 * warp) * LDS + 32 * warp;
+    Real* cw = col + 32 * warp;
+    Real* Bi = B + lane * LDS;
+    for (int j = 31; j >= 0; --j) {
+      __syncwarp();
+      cw[lane] = Bi[j];
+      __syncwarp();
+      const Real ajj = (Real)1 / cw[j];
+      if (lane > j) {
+        Real a0 = (Real)0, a1 = (Real)0;
+        int k = j + 1;
+        for (; k + 1 <= lane; k += 2) {
+          a0 = fma(Bi[k], cw[k], a0);
+          a1 = fma(Bi[k + 1], cw[k + 1], a1);
+        }
+        if (k <= lane) a0 = fma(Bi[k], cw[k], a0);
+        Bi[j] = -ajj * (a0 + a1);
       }
-      if (k <= i) a0 = fma(S[i * LDS + k], col[k], a0);
-      S[i * LDS + j] = -ajj * (a0 + a1);
+      if (lane == j) Bi[j] = ajj;
     }
-    if (threadIdx.x == 0) S[j * LDS + j] = ajj;
+  }
+  for (int jb = NB - 2; jb >= 0; --jb) {
+    __syncthreads();
+    const int R = DP - 32 * (jb + 1);   // panel rows: 32, 64 or 96
+    if (R <= WT / 8) w_trinv_panel<Real, DP, 8>(S, jb);
+    else if (R <= WT / 4) w_trinv_panel<Real, DP, 4>(S, jb);
+    else w_trinv_panel<Real, DP, 2>(S, jb);
   }
   __syncthreads();
 }
