@@ -6,7 +6,8 @@
 // of WT threads on matrices in global memory (L2-resident working sets):
 //   w_gemm    C = alpha op(A) op(B) + beta C0, k-chunks staged in shared memory,
 //             (DP/16)^2 outputs per thread;
-//   w_chol    right-looking Cholesky in shared memory (one barrier per column);
+//   w_chol    right-looking Cholesky in shared memory, blocks of 8 columns
+//             (three barriers per block);
 //   w_trinv   the inverse of the triangular factor, blocked by 32 (diagonal
 //             blocks on separate warps, then each panel as one product pair).
 // Covariance pass (homogeneous dynamics, R = r I, Appendix A.2.1 elements):
@@ -333,14 +334,26 @@ __device__ void w_sym(const Real* X, Real* out) {
 // the identity (the padding). A pivot below d that is not positive and finite
 // sets *bad and is replaced by 1. Returns sum_{k<d} log L_kk in thread 0 (the
 // only thread that uses it; warp 0 sums the FP64 logarithms, a few per lane).
-// piv: DP doubles of shared scratch. The FP64 work per call is DP square roots
-// and DP logarithms in all: on this GPU FP64 runs at a small fraction of the
-// FP32 rate, so every thread doing its own would dominate the routine.
+// piv: DP + 8 doubles of shared scratch. The FP64 work per call is DP square
+// roots and DP logarithms in all: on this GPU FP64 runs at a small fraction of
+// the FP32 rate, so every thread doing its own would dominate the routine.
+// Elimination without square roots (S_ik becomes L_ik sqrt(p_k), p_k the
+// pivots), right-looking in blocks of 8 columns with three CTA barriers per
+// block instead of one per column:
+//   (a) the block's 8 x 8 diagonal part, lanes 0..7 of warp 0 (lane = row,
+//       column entries by shuffles), its pivots and their reciprocals;
+//   (b) the panel below it, one thread per row, row-local:
+//       S_i,k+c -= sum_{c'<c} (S_i,k+c' / p_k+c') S_k+c,k+c';
+//   (c) the rank-8 update of the trailing rows,
+//       S_ij -= sum_c (S_i,k+c / p_k+c) S_j,k+c  (k + 8 <= j <= i < d),
+//       each thread some columns of one row, the 8 multipliers of its row in
+//       registers.
 template <typename Real, int DP, typename SlotT = Real>
 __device__ double w_chol(const Real* A, Real addiag, int d, SlotT* S, double* piv, int* bad) {
   using Z = WSz<Real, DP>;
-  constexpr int LDS = Z::LDS, P = WT / DP;
+  constexpr int LDS = Z::LDS, P = WT / DP, NK = 8;
   static_assert(WT % DP == 0, "every thread keeps one column in the scaling pass");
+  static_assert(DP % NK == 0 && WT >= DP, "blocks of 8 columns, one thread per panel row");
   __syncthreads();
   for (int q = threadIdx.x; q < DP * DP; q += WT) {
     const int i = q / DP, j = q % DP;
@@ -349,32 +362,72 @@ __device__ double w_chol(const Real* A, Real addiag, int d, SlotT* S, double* pi
     else v = (SlotT)A[q] + (i == j ? (SlotT)addiag : (SlotT)0);
     S[i * LDS + j] = v;
   }
+  double* rinv = piv + DP;   // the current block's pivot reciprocals
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = threadIdx.x % DP, part = threadIdx.x / DP;
-  for (int k = 0; k < d; ++k) {
+  for (int k = 0; k < d; k += NK) {
     __syncthreads();
-    SlotT pk = S[k * LDS + k];
-    const bool ok = pk > (SlotT)0 && pk < (SlotT)INFINITY;
-    if (!ok) pk = (SlotT)1;
-    if (threadIdx.x == 0) {
-      piv[k] = (double)pk;
-      if (!ok) *bad = 1;
-    }
-    if (i > k) {
-      const SlotT lik = S[i * LDS + k] / pk;
-      SlotT* Si = S + i * LDS;
-      int j = k + 1 + part;
-      // four columns per round, every load before the stores: the rounds of a row
-      // are independent, so their shared-memory latencies overlap
-      for (; j + 3 * P <= i; j += 4 * P) {
-        const SlotT c0 = S[j * LDS + k], c1 = S[(j + P) * LDS + k], c2 = S[(j + 2 * P) * LDS + k],
-                    c3 = S[(j + 3 * P) * LDS + k];
-        const SlotT r0 = Si[j], r1 = Si[j + P], r2 = Si[j + 2 * P], r3 = Si[j + 3 * P];
-        Si[j] = fma(-lik, c0, r0);
-        Si[j + P] = fma(-lik, c1, r1);
-        Si[j + 2 * P] = fma(-lik, c2, r2);
-        Si[j + 3 * P] = fma(-lik, c3, r3);
+    if (warp == 0) {   // (a)
+      const int r = lane < NK ? lane : 0;
+      SlotT w[NK];
+#pragma unroll
+      for (int c = 0; c < NK; ++c) w[c] = (c <= r) ? S[(k + r) * LDS + k + c] : (SlotT)0;
+#pragma unroll
+      for (int c = 0; c < NK; ++c) {
+        SlotT pc = __shfl_sync(FULL_MASK, w[c], c);
+        const bool ok = pc > (SlotT)0 && pc < (SlotT)INFINITY;
+        if (!ok) pc = (SlotT)1;
+        const SlotT ic = (SlotT)1 / pc;
+        if (lane == 0) {
+          piv[k + c] = (double)pc;
+          rinv[c] = (double)ic;
+          if (!ok && k + c < d) *bad = 1;
+        }
+        const SlotT l = w[c] * ic;
+#pragma unroll
+        for (int c2 = c + 1; c2 < NK; ++c2) {
+          const SlotT wc = __shfl_sync(FULL_MASK, w[c], c2);   // S_k+c2,k+c
+          if (lane > c && c2 <= r) w[c2] = fma(-l, wc, w[c2]);
+        }
+        if (lane == c) w[c] = pc;
       }
-      for (; j <= i; j += P) Si[j] = fma(-lik, S[j * LDS + k], Si[j]);
+      if (lane < NK) {
+#pragma unroll
+        for (int c = 0; c < NK; ++c)
+          if (c <= lane) S[(k + lane) * LDS + k + c] = w[c];
+      }
+    }
+    __syncthreads();
+    {   // (b)
+      const int ip = k + NK + (int)threadIdx.x;
+      if (ip < d) {
+        SlotT* Si = S + ip * LDS + k;
+        SlotT x[NK];
+#pragma unroll
+        for (int c = 0; c < NK; ++c) x[c] = Si[c];
+#pragma unroll
+        for (int c = 0; c < NK; ++c) {
+          const SlotT l = x[c] * (SlotT)rinv[c];
+#pragma unroll
+          for (int c2 = c + 1; c2 < NK; ++c2) x[c2] = fma(-l, S[(k + c2) * LDS + k + c], x[c2]);
+        }
+#pragma unroll
+        for (int c = 0; c < NK; ++c) Si[c] = x[c];
+      }
+    }
+    __syncthreads();
+    if (i >= k + NK && i < d) {   // (c)
+      SlotT li[NK];
+      SlotT* Srow = S + i * LDS;
+#pragma unroll
+      for (int c = 0; c < NK; ++c) li[c] = Srow[k + c] * (SlotT)rinv[c];
+      for (int j = k + NK + part; j <= i; j += P) {
+        const SlotT* Sj = S + j * LDS + k;
+        SlotT acc = Srow[j];
+#pragma unroll
+        for (int c = 0; c < NK; ++c) acc = fma(-li[c], Sj[c], acc);
+        Srow[j] = acc;
+      }
     }
   }
   __syncthreads();
