@@ -2,8 +2,10 @@
 against the oracle's definitions (oracle/kalman.py): the covariance-only
 element constants, the C-only operator on prefixes (A = J = 0), the prefixes
 by doubling over the steps, and the per-step tables (K' = r S^{-1}, G, Sigma)
-in the factored forms the kernels use. The GPU parity tests check the kernels
-themselves; these check the algebra they rest on, on the CPU.
+in the factored forms the kernels use, and the blocked recurrences of the CTA
+routines (the triangular inverse by 32 x 32 blocks, the Cholesky factorisation
+without square roots in blocks of 8 columns). The GPU parity tests check the
+kernels themselves; these check the algebra they rest on, on the CPU.
 """
 import numpy as np
 import pytest
@@ -134,3 +136,63 @@ def test_per_step_tables_in_factored_form(d, seed):
         assert np.allclose(G, G_ref, atol=1e-11)
         Sig = kf["Pf"][t] - Y.T @ Y
         assert np.allclose(Sig, kf["Pf"][t] - G_ref @ Pp_next @ G_ref.T, atol=1e-11)
+
+
+def _blocked_trinv(L, nb=32):
+    """w_trinv's recurrence: the diagonal blocks inverted on their own, then the
+    block columns from the second last to the first, X_(i,j) = -(sum_{k=j+1..i}
+    X_(i,k) L_(k,j)) X_(j,j) for the blocks below the diagonal (from X L = I)."""
+    n = L.shape[0]
+    X = np.zeros_like(L)
+    B = n // nb
+    sl = [slice(b * nb, (b + 1) * nb) for b in range(B)]
+    for b in range(B):
+        X[sl[b], sl[b]] = np.linalg.inv(L[sl[b], sl[b]])
+    for j in range(B - 2, -1, -1):
+        below = slice((j + 1) * nb, n)
+        X[below, sl[j]] = -(X[below, below] @ L[below, sl[j]]) @ X[sl[j], sl[j]]
+    return X
+
+
+def _blocked_ldl_chol(A, nk=8):
+    """w_chol's recurrence: elimination without square roots in blocks of nk
+    columns (S_ik -> L_ik sqrt(p_k)), the diagonal block, the panel below it
+    and one rank-nk update of the trailing part per block; then L_ik = S_ik /
+    sqrt(p_k)."""
+    n = A.shape[0]
+    S = np.tril(A.copy())
+    p = np.zeros(n)
+    for k in range(0, n, nk):
+        e = min(n, k + nk)
+        for c in range(k, e):   # diagonal block, column by column
+            p[c] = S[c, c]
+            for c2 in range(c + 1, e):
+                S[c2, c + 1:c2 + 1] -= (S[c2, c] / p[c]) * S[c + 1:c2 + 1, c]
+        for c in range(k, e):   # panel rows, row-locally
+            l = S[e:, c] / p[c]
+            S[e:, c + 1:e] -= np.outer(l, S[c + 1:e, c])
+        Lm = S[e:, k:e] / p[k:e]   # rank-nk trailing update (lower part)
+        S[e:, e:] -= np.tril(Lm @ S[e:, k:e].T)
+    L = np.tril(S, -1) / np.sqrt(p)[None, :] + np.diag(np.sqrt(p))
+    return L, 0.5 * np.sum(np.log(p))
+
+
+@pytest.mark.parametrize("n", [64, 128])
+def test_blocked_triangular_inverse_is_the_inverse(n):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n))
+    L = _chol(A @ A.T / n + np.eye(n))
+    X = _blocked_trinv(L)
+    assert np.allclose(X, np.linalg.inv(L), rtol=0, atol=1e-12 * np.abs(np.linalg.inv(L)).max())
+    assert np.all(np.triu(X, 1) == 0.0)
+
+
+@pytest.mark.parametrize("n", [5, 8, 37, 64, 101, 128])
+def test_blocked_cholesky_without_square_roots_is_the_cholesky_factor(n):
+    rng = np.random.default_rng(100 + n)
+    A = rng.standard_normal((n, n))
+    A = A @ A.T / n + 0.5 * np.eye(n)
+    L, half_logdet = _blocked_ldl_chol(A)
+    Lr = _chol(A)
+    assert np.max(np.abs(L - Lr)) < 1e-12 * np.abs(Lr).max()
+    assert abs(half_logdet - np.sum(np.log(np.diag(Lr)))) < 1e-10
